@@ -1,0 +1,187 @@
+/*
+ * ib_pf.h -- C ABI of the GB300 (sm_103a) hot path of the fully Eulerian hybrid
+ * immersed-boundary / phase-field method for contact lines on complex walls
+ * (Shahmardi, Rosti, Tammisola & Brandt, arXiv 2104.00350).
+ *
+ * One call of ib_pf_step advances every instance of a context by one or more time
+ * steps of the semi-implicit scheme (Sec. 4.2 and Appendix A):
+ *   a1 Cahn-Hilliard right-hand side            (Appendix A.1, Eq. Helmholtz1)
+ *   a2 the two Helmholtz solves, one eigenbasis (Eqs. Helmholtz1, Helmholtz2)
+ *   a3 contact-angle ghost fill of C            (Eqs. interpolationAtWall, ProjectingToNT,
+ *                                                UpdateC, static form of Eq. WallBCS)
+ *   a4 chemical potential + ghost fill          (Eq. Chemical-Potential, Sec. 4.2.2)
+ *   a5 AB2 momentum predictor + penalisation    (Eqs. PredictionExp, Penalization2)
+ *   a6 slip / no-penetration ghost fill         (Eqs. NoPenetration, UpdateVtan, UpdateVandW)
+ *   a7 Dodd-Ferrante pressure Poisson           (Eq. PressurePoisson)
+ *   a8 velocity correction                      (Eq. correction)
+ * The geometry precompute of Sec. 4.1 (volume fractions, normals, ghost / intersect /
+ * mirror / interpolation points, weights W1/W2) runs once on the device in
+ * ib_pf_init_geometry and ib_pf_precompute_weights.
+ *
+ * Grid and layout.  2D uniform staggered Cartesian grid, nx x ny cells of size h
+ * (lx/nx must equal ly/ny), periodic in x1, solid walls (v = 0) at x2 = 0 and x2 = ly.
+ * nx and ny must be powers of two, 8 <= nx <= 4096, 8 <= ny <= 2048.  All fields are
+ * row-major with x1 fastest: cell fields (C, P, phi) are ny x nx; x1-face fields (u, Hu)
+ * are ny x nx with face i the left face of cell i; x2-face fields (v, Hv) are
+ * (ny+1) x nx with rows 0 and ny on the domain walls (always zero).
+ *
+ * Element type.  The element type of every field buffer passed in or out is the
+ * context's arithmetic type: double for IB_PF_FP64, float for IB_PF_FP32.
+ *
+ * Errors.  Every call returns an ib_pf_status; nothing aborts, traps the device or exits.
+ * The last error message of a context is kept (ib_pf_last_error).  Device-detected
+ * non-finite values set a status word that the next synchronising call returns as
+ * IB_PF_E_NUMERIC.  A context is not thread-safe; separate contexts are independent.
+ * All device work is issued on the stream given at creation (0 = legacy default).
+ */
+#ifndef IB_PF_H
+#define IB_PF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ib_pf_ctx ib_pf_ctx;   /* opaque; owned by the library */
+
+typedef enum {
+  IB_PF_OK = 0,
+  IB_PF_E_ARG = -1,          /* invalid argument (sizes, ids, null pointers, params) */
+  IB_PF_E_UNSUPPORTED = -2,  /* valid but not implemented (e.g. dim 3, dynamic angle) */
+  IB_PF_E_CUDA = -3,         /* a CUDA runtime call failed; see ib_pf_last_error */
+  IB_PF_E_NUMERIC = -4,      /* NaN/Inf seen in C or the velocity by the device check */
+  IB_PF_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+  IB_PF_E_STATE = -6,        /* call out of order (e.g. step before precompute) */
+  IB_PF_E_GEOMETRY = -7      /* precompute failed (no intersect point within 10 h) */
+} ib_pf_status;
+
+typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
+
+/* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points
+ * against it).  FLAT: x2 < p[0].  SINUSOID: x2 < p[0] + p[1] sin(2 pi p[2] x1).
+ * NONE: no solid. */
+typedef enum { IB_PF_WALL_FLAT = 0, IB_PF_WALL_SINUSOID = 1, IB_PF_WALL_NONE = 3 } ib_pf_wall_kind;
+
+typedef struct {
+  int dim;        /* 2 (3 returns IB_PF_E_UNSUPPORTED) */
+  int n[3];       /* cells per axis: n[0] = nx, n[1] = ny */
+  double L[3];    /* domain lengths */
+} ib_pf_grid;
+
+typedef struct {
+  int kind;       /* ib_pf_wall_kind */
+  double p[8];    /* wall parameters, see above */
+} ib_pf_geometry;
+
+/* Nondimensional parameters as defined in Sec. 5.1 (Re, Ca, Cn) and Sec. 5.3 (Pe);
+ * S is the stabilisation of Appendix A.1; rho_ratio and mu_ratio are liquid/gas with the
+ * liquid (C = +1) at rho = mu = 1; theta_deg the static contact angle measured through
+ * the liquid; l_s the slip length of Eq. SlipVelocity; mu_f the wall friction of
+ * Eq. WallBCS (must be 0: static angle); d1, d2 the ghost-cell lengths of Sec. 4.1.2
+ * (d1 > half a cell diagonal, 0 < d2 < d1); dt the time step. */
+typedef struct {
+  double Re, Ca, Cn, Pe, S, rho_ratio, mu_ratio, theta_deg, l_s, mu_f, d1, d2, dt;
+  int precision;  /* ib_pf_precision */
+} ib_pf_params;
+
+/* field ids for read / write */
+typedef enum {
+  IB_PF_F_C = 0,        /* C^n            (cells)  read/write */
+  IB_PF_F_C_OLD = 1,    /* C^{n-1}        (cells)  read/write */
+  IB_PF_F_U = 2,        /* u^n            (x1-faces) read/write */
+  IB_PF_F_U_OLD = 3,    /* u^{n-1} */
+  IB_PF_F_V = 4,        /* v^n            (x2-faces) read/write */
+  IB_PF_F_V_OLD = 5,    /* v^{n-1} */
+  IB_PF_F_HU = 6,       /* H_u^{n-1}: AB2 history of Eq. PredictionExp, read/write */
+  IB_PF_F_HV = 7,
+  IB_PF_F_P = 8,        /* P^n            (cells)  read/write */
+  IB_PF_F_P_OLD = 9,    /* P^{n-1} */
+  IB_PF_F_PHI = 10,     /* chemical potential of the last step (cells), read only */
+  IB_PF_F_Q = 11,       /* CH right-hand side of the last step (cells), read only */
+  IB_PF_F_RHS_P = 12    /* Poisson right-hand side of the last step (cells), read only */
+} ib_pf_field;
+
+/* geometry tables for ib_pf_read_table (element type in brackets) */
+typedef enum {
+  IB_PF_T_ALPHA_C = 0,  /* [double] ny x nx      fluid volume fraction, cell volumes */
+  IB_PF_T_ALPHA_U = 1,  /* [double] ny x nx      x1-face volumes */
+  IB_PF_T_ALPHA_V = 2,  /* [double] (ny+1) x nx  x2-face volumes */
+  IB_PF_T_CLASS = 3,    /* [int]    ny x nx      0 fluid, 1 ghost, 2 solid */
+  IB_PF_T_GHOST_CELL = 4, /* [int]  ng           linear cell index j*nx+i, ascending */
+  IB_PF_T_NORMAL = 5,   /* [double] ng x 2       unit normal, solid -> fluid */
+  IB_PF_T_DN = 6,       /* [double] ng           ghost-to-intersect distance */
+  IB_PF_T_GAMMA = 7,    /* [double] ng           d1 / dn */
+  IB_PF_T_AP1 = 8,      /* [int]    ng x 5       averaging cells around IP1 */
+  IB_PF_T_W1 = 9,       /* [double] ng x 5       weights W1 (sum 1) */
+  IB_PF_T_AP2 = 10,     /* [int]    ng x 5 */
+  IB_PF_T_W2 = 11,      /* [double] ng x 5 */
+  IB_PF_T_FACE_U = 12,  /* [int]    nfu          re-interpolated x1-faces (j*nx+i) */
+  IB_PF_T_FACE_V = 13   /* [int]    nfv          re-interpolated x2-faces (j*nx+i) */
+} ib_pf_table;
+
+/* quantities for ib_pf_query */
+typedef enum {
+  IB_PF_Q_MASS = 0,        /* sum of C^n over all cells, FP64, fixed-order reduction */
+  IB_PF_Q_N_GHOST = 1,
+  IB_PF_Q_N_FACE_U = 2,
+  IB_PF_Q_N_FACE_V = 3,
+  IB_PF_Q_STATUS = 4,      /* device status word: 0 ok, 1 non-finite seen */
+  IB_PF_Q_STEPS = 5,       /* steps taken since creation */
+  IB_PF_Q_N_FALLBACK = 6,  /* normals or averaging stencils that used the fallback */
+  IB_PF_Q_LAUNCHES_PER_STEP = 7  /* kernels one step launches */
+} ib_pf_query_id;
+
+/* Create a context for n_instances independent problems (grids[k], geoms[k],
+ * params[k]) and run the first part of the precompute of Sec. 4.1: volume fractions of
+ * the cell and face control volumes by counting 100 x 100 subgrid points (Sec. 4.1.1),
+ * ghost classification (cell centre in the solid with a fluid face neighbour, Sec.
+ * 4.1.2) and compaction, and the list of faces re-interpolated after the velocity ghost
+ * fill.  Fields start at zero.  `cuda_stream` is a cudaStream_t (NULL = default stream);
+ * the call synchronises it.  On success *out owns all device memory of the context. */
+ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_grid* grids,
+                                 const ib_pf_geometry* geoms, const ib_pf_params* params,
+                                 void* cuda_stream);
+
+/* Second part of the precompute (Sec. 4.1.2-4.1.4), in FP64 on the device: normals from
+ * corner gradients of alpha (Eqs. NormalVectors_part1/2), intersect points by marching
+ * h/100 along the normal plus 60 bisections, mirror point M = I + d1 n, interpolation
+ * points IP1 = M + d2 n, IP2 = M + 2 d2 n, averaging points and inverse-squared-distance
+ * weights W1/W2 (Eq. weright averaged).  Synchronises the stream.  Returns
+ * IB_PF_E_GEOMETRY if some ghost has no intersect point within 10 h. */
+ib_pf_status ib_pf_precompute_weights(ib_pf_ctx* ctx);
+
+/* Advance every instance by nsteps time steps (a1..a8 above).  Asynchronous on the
+ * context stream: the steps are replayed from captured CUDA graphs.  Returns
+ * IB_PF_E_STATE before ib_pf_precompute_weights, IB_PF_E_NUMERIC if an earlier step's
+ * device check saw a non-finite value (the check is read back without blocking). */
+ib_pf_status ib_pf_step(ib_pf_ctx* ctx, int nsteps);
+
+/* Copy field `field_id` of `instance` into dst (nbytes must equal the field size in the
+ * context's element type).  dst_on_host != 0: dst is host memory and the call
+ * synchronises the stream; otherwise dst is device memory and the copy is stream-ordered. */
+ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void* dst,
+                               long long nbytes, int dst_on_host);
+
+/* Copy src into state field `field_id` of `instance` (restart / initial condition).
+ * Only the read/write ids above are accepted.  src_on_host as for ib_pf_read_fields.
+ * Rows 0 and ny of v fields are forced to zero. */
+ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
+                                long long nbytes, int src_on_host);
+
+/* Copy geometry table `table_id` of `instance` to host memory.  If dst is NULL only the
+ * element count is returned in *count; otherwise nbytes must match.  Synchronises. */
+ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* dst,
+                              long long nbytes, long long* count);
+
+/* Scalar diagnostics (ib_pf_query_id) of `instance`.  Synchronises the stream. */
+ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out);
+
+/* Last error message of ctx (or of the last failed creation when ctx is NULL). */
+const char* ib_pf_last_error(const ib_pf_ctx* ctx);
+
+/* Free every resource of ctx (device memory, graphs).  Synchronises its stream. */
+void ib_pf_destroy(ib_pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_PF_H */

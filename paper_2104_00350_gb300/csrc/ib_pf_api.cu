@@ -1,0 +1,436 @@
+// C ABI of the ib_pf library: context life cycle, field I/O and step replay through CUDA
+// graphs.  Declarations and argument contracts are in include/ib_pf.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ibpf_internal.h"
+
+using namespace ibpf;
+
+namespace {
+
+std::string g_create_error;
+
+#define CK(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ctx->err = std::string(#call) + " failed: " + cudaGetErrorString(e_);       \
+      return IB_PF_E_CUDA;                                                        \
+    }                                                                             \
+  } while (0)
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg);
+
+size_t field_elems(const Instance& in, int id) {
+  const size_t cells = (size_t)in.nx * in.ny;
+  switch (id) {
+    case IB_PF_F_V: case IB_PF_F_V_OLD: case IB_PF_F_HV: return cells + in.nx;
+    default: return cells;
+  }
+}
+
+void* field_ptr(Ctx& c, Instance& in, int id) {
+  const int n = c.cur, o = 1 - c.cur;
+  switch (id) {
+    case IB_PF_F_C: return in.C[n];
+    case IB_PF_F_C_OLD: return in.C[o];
+    case IB_PF_F_U: return in.U[n];
+    case IB_PF_F_U_OLD: return in.U[o];
+    case IB_PF_F_V: return in.V[n];
+    case IB_PF_F_V_OLD: return in.V[o];
+    case IB_PF_F_HU: return in.Hu;
+    case IB_PF_F_HV: return in.Hv;
+    case IB_PF_F_P: return in.P[n];
+    case IB_PF_F_P_OLD: return in.P[o];
+    case IB_PF_F_PHI: return in.phi;
+    case IB_PF_F_Q: return in.Q;
+    case IB_PF_F_RHS_P: return in.rhs;
+    default: return nullptr;
+  }
+}
+
+void free_instance(Instance& in) {
+  void* ptrs[] = {in.C[0], in.C[1], in.U[0], in.U[1], in.V[0], in.V[1], in.P[0], in.P[1],
+                  in.Hu, in.Hv, in.Q, in.phi, in.rhs, in.phat, in.spec, in.gu, in.gv, in.fval,
+                  in.lamx, in.lamy, in.twx, in.twy, in.wdct, in.partial, in.ticket, in.mass,
+                  in.status, in.tab.alpha_c, in.tab.alpha_u, in.tab.alpha_v, in.tab.solidc,
+                  in.tab.cmap, in.tab.gcell, in.tab.nrm, in.tab.dn, in.tab.gamma, in.tab.ap1,
+                  in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+// order the work stream after everything already queued on the caller's stream
+cudaError_t join_in(Ctx& c) {
+  if (c.work == c.user_stream) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(c.ev_in, c.user_stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(c.work, c.ev_in, 0);
+}
+
+// order the caller's stream after everything queued on the work stream
+cudaError_t join_out(Ctx& c) {
+  if (c.work == c.user_stream) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(c.ev_out, c.work);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(c.user_stream, c.ev_out, 0);
+}
+
+}  // namespace
+
+struct ib_pf_ctx : public Ctx {};
+
+namespace {
+ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_params& p,
+                      std::string& why) {
+  if (g.dim == 3) { why = "dim 3 is not built"; return IB_PF_E_UNSUPPORTED; }
+  if (g.dim != 2) { why = "dim must be 2"; return IB_PF_E_ARG; }
+  const int nx = g.n[0], ny = g.n[1];
+  if (!is_pow2(nx) || !is_pow2(ny) || nx < 8 || ny < 8 || nx > 4096 || ny > 2048) {
+    why = "nx, ny must be powers of two with 8 <= nx <= 4096 and 8 <= ny <= 2048";
+    return IB_PF_E_ARG;
+  }
+  if (!(g.L[0] > 0) || !(g.L[1] > 0)) { why = "domain lengths must be positive"; return IB_PF_E_ARG; }
+  const double hx = g.L[0] / nx, hy = g.L[1] / ny;
+  if (std::fabs(hx - hy) > 1e-12 * hx) { why = "cells must be square (lx/nx == ly/ny)"; return IB_PF_E_ARG; }
+  if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SINUSOID && w.kind != IB_PF_WALL_NONE) {
+    why = "unknown wall kind";
+    return IB_PF_E_ARG;
+  }
+  if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
+  if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }
+  const double vals[] = {p.Re, p.Ca, p.Cn, p.Pe, p.rho_ratio, p.mu_ratio, p.dt, p.d1, p.d2};
+  for (double v : vals)
+    if (!(v > 0) || !std::isfinite(v)) { why = "Re, Ca, Cn, Pe, ratios, dt, d1, d2 must be positive"; return IB_PF_E_ARG; }
+  if (!(p.S >= 0) || !(p.l_s >= 0) || !std::isfinite(p.theta_deg)) { why = "S, l_s must be >= 0"; return IB_PF_E_ARG; }
+  if (!(p.d2 < p.d1) || !(p.d1 > 0.5 * std::sqrt(2.0) * hx)) {
+    why = "need d1 > half the cell diagonal and d2 < d1 (Sec. 4.1.2)";
+    return IB_PF_E_ARG;
+  }
+  return IB_PF_OK;
+}
+
+ib_pf_status capture_graphs(ib_pf_ctx* ctx) {
+  for (int ph = 0; ph < 2; ++ph) {
+    if (ctx->graph[ph]) continue;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    for (Instance& in : ctx->inst) launches += step_instance(in, ctx->precision, ph, ctx->work);
+    for (size_t k = 0; k < ctx->inst.size(); ++k) {
+      cudaMemcpyAsync(ctx->h_status + k, ctx->inst[k].status, sizeof(int), cudaMemcpyDeviceToHost,
+                      ctx->work);
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->work, &g);
+    if (e != cudaSuccess) return fail(ctx, IB_PF_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph[ph], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, IB_PF_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    ctx->launches_per_step = launches;
+  }
+  return IB_PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_grid* grids,
+                                 const ib_pf_geometry* geoms, const ib_pf_params* params,
+                                 void* cuda_stream) {
+  if (!out || n_instances < 1 || !grids || !geoms || !params)
+    return fail(nullptr, IB_PF_E_ARG, "null pointer or n_instances < 1");
+  *out = nullptr;
+  for (int k = 0; k < n_instances; ++k) {
+    std::string why;
+    ib_pf_status st = validate(grids[k], geoms[k], params[k], why);
+    if (st != IB_PF_OK) return fail(nullptr, st, "instance " + std::to_string(k) + ": " + why);
+    if (params[k].precision != params[0].precision)
+      return fail(nullptr, IB_PF_E_ARG, "all instances must share one precision");
+  }
+  ib_pf_ctx* ctx = new (std::nothrow) ib_pf_ctx();
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "out of host memory");
+  ctx->precision = params[0].precision;
+  ctx->esz = ctx->precision == IB_PF_FP64 ? 8 : 4;
+  ctx->user_stream = (cudaStream_t)cuda_stream;
+  auto bail = [&](ib_pf_status st) {
+    g_create_error = ctx->err;
+    ib_pf_destroy(ctx);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&ctx->work, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->h_status, sizeof(int) * n_instances) != cudaSuccess) {
+    ctx->err = "CUDA initialisation failed (stream/event/pinned allocation)";
+    return bail(IB_PF_E_CUDA);
+  }
+  std::memset(ctx->h_status, 0, sizeof(int) * n_instances);
+  if (join_in(*ctx) != cudaSuccess) { ctx->err = "stream join failed"; return bail(IB_PF_E_CUDA); }
+  ctx->inst.resize(n_instances);
+  for (int k = 0; k < n_instances; ++k) {
+    Instance& in = ctx->inst[k];
+    in.nx = grids[k].n[0];
+    in.ny = grids[k].n[1];
+    in.lognx = ilog2(in.nx);
+    in.logny = ilog2(in.ny);
+    in.lx = grids[k].L[0];
+    in.ly = grids[k].L[1];
+    in.h = in.lx / in.nx;
+    in.geom = geoms[k];
+    in.prm = params[k];
+    in.wall.kind = geoms[k].kind;
+    in.wall.p0 = geoms[k].p[0];
+    in.wall.p1 = geoms[k].p[1];
+    in.wall.w = (2.0 * M_PI) * geoms[k].p[2];
+    const size_t cells = (size_t)in.nx * in.ny, vf = cells + in.nx, es = ctx->esz;
+    const size_t nh1 = (size_t)in.nx / 2 + 1;
+    void** cell_fields[] = {&in.C[0], &in.C[1], &in.P[0], &in.P[1], &in.U[0], &in.U[1], &in.Hu,
+                            &in.Q, &in.phi, &in.rhs, &in.phat};
+    for (void** f : cell_fields) {
+      if (cudaMalloc(f, cells * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
+      cudaMemsetAsync(*f, 0, cells * es, ctx->work);
+    }
+    void** vfields[] = {&in.V[0], &in.V[1], &in.Hv};
+    for (void** f : vfields) {
+      if (cudaMalloc(f, vf * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
+      cudaMemsetAsync(*f, 0, vf * es, ctx->work);
+    }
+    if (cudaMalloc(&in.spec, (size_t)in.ny * nh1 * 2 * es) != cudaSuccess) {
+      ctx->err = "spectral workspace allocation failed";
+      return bail(IB_PF_E_CUDA);
+    }
+    const int nblk = ((in.nx + 31) / 32) * ((in.ny + 7) / 8);
+    in.nblk_red = nblk;
+    if (cudaMalloc((void**)&in.partial, sizeof(double) * nblk) != cudaSuccess ||
+        cudaMalloc((void**)&in.ticket, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc((void**)&in.mass, sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&in.status, sizeof(int)) != cudaSuccess) {
+      ctx->err = "reduction buffers allocation failed";
+      return bail(IB_PF_E_CUDA);
+    }
+    cudaMemsetAsync(in.ticket, 0, sizeof(unsigned), ctx->work);
+    cudaMemsetAsync(in.mass, 0, sizeof(double), ctx->work);
+    cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work);
+    if (spectral_tables(in, ctx->precision) != cudaSuccess) {
+      ctx->err = std::string("transform tables: ") + cudaGetErrorString(cudaGetLastError());
+      return bail(IB_PF_E_CUDA);
+    }
+    std::string gerr;
+    if (geometry_init(in, ctx->work, gerr) != cudaSuccess) {
+      ctx->err = "geometry: " + gerr;
+      return bail(IB_PF_E_CUDA);
+    }
+    const Tables& t = in.tab;
+    if (cudaMalloc(&in.gu, (size_t)(t.ng ? t.ng : 1) * es) != cudaSuccess ||
+        cudaMalloc(&in.gv, (size_t)(t.ng ? t.ng : 1) * es) != cudaSuccess ||
+        cudaMalloc(&in.fval, (size_t)(t.nfu + t.nfv + 1) * es) != cudaSuccess) {
+      ctx->err = "ghost scratch allocation failed";
+      return bail(IB_PF_E_CUDA);
+    }
+  }
+  if (cudaStreamSynchronize(ctx->work) != cudaSuccess) {
+    ctx->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
+    return bail(IB_PF_E_CUDA);
+  }
+  join_out(*ctx);
+  ctx->geometry_ready = true;
+  *out = ctx;
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_precompute_weights(ib_pf_ctx* ctx) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (!ctx->geometry_ready) return fail(ctx, IB_PF_E_STATE, "geometry not initialised");
+  CK(join_in(*ctx));
+  int total_fail = 0;
+  for (Instance& in : ctx->inst) {
+    int nf = 0;
+    std::string gerr;
+    if (geometry_weights(in, ctx->work, &nf, gerr) != cudaSuccess)
+      return fail(ctx, IB_PF_E_CUDA, "weights: " + gerr);
+    total_fail += nf;
+  }
+  CK(join_out(*ctx));
+  if (total_fail > 0)
+    return fail(ctx, IB_PF_E_GEOMETRY, std::to_string(total_fail) + " ghost(s) without an intersect point within 10 h");
+  ctx->weights_ready = true;
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_step(ib_pf_ctx* ctx, int nsteps) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (nsteps < 0) return fail(ctx, IB_PF_E_ARG, "nsteps < 0");
+  if (!ctx->weights_ready) return fail(ctx, IB_PF_E_STATE, "ib_pf_precompute_weights has not succeeded");
+  for (size_t k = 0; k < ctx->inst.size(); ++k)
+    if (((volatile int*)ctx->h_status)[k] != 0)
+      return fail(ctx, IB_PF_E_NUMERIC, "non-finite value seen in instance " + std::to_string(k));
+  if (nsteps == 0) return IB_PF_OK;
+  ib_pf_status st = capture_graphs(ctx);
+  if (st != IB_PF_OK) return st;
+  CK(join_in(*ctx));
+  for (int s = 0; s < nsteps; ++s) {
+    CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->work));
+    ctx->cur = 1 - ctx->cur;
+    ++ctx->steps;
+  }
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void* dst,
+                               long long nbytes, int dst_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
+  if (!dst) return fail(ctx, IB_PF_E_ARG, "null destination");
+  Instance& in = ctx->inst[instance];
+  void* src = field_ptr(*ctx, in, field_id);
+  if (!src) return fail(ctx, IB_PF_E_ARG, "bad field id");
+  const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
+  if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
+  CK(join_in(*ctx));
+  CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     ctx->work));
+  if (dst_on_host) CK(cudaStreamSynchronize(ctx->work));
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
+                                long long nbytes, int src_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
+  if (!src) return fail(ctx, IB_PF_E_ARG, "null source");
+  if (field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
+  Instance& in = ctx->inst[instance];
+  void* dst = field_ptr(*ctx, in, field_id);
+  const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
+  if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
+  CK(join_in(*ctx));
+  CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     ctx->work));
+  if (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV) {
+    const size_t row = (size_t)in.nx * ctx->esz;
+    CK(cudaMemsetAsync(dst, 0, row, ctx->work));
+    CK(cudaMemsetAsync((char*)dst + (size_t)in.ny * row, 0, row, ctx->work));
+  }
+  if (src_on_host) CK(cudaStreamSynchronize(ctx->work));
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* dst,
+                              long long nbytes, long long* count) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
+  Instance& in = ctx->inst[instance];
+  const Tables& t = in.tab;
+  const size_t cells = (size_t)in.nx * in.ny;
+  const void* src = nullptr;
+  size_t n = 0, es = 8;
+  switch (table_id) {
+    case IB_PF_T_ALPHA_C: src = t.alpha_c; n = cells; break;
+    case IB_PF_T_ALPHA_U: src = t.alpha_u; n = cells; break;
+    case IB_PF_T_ALPHA_V: src = t.alpha_v; n = cells + in.nx; break;
+    case IB_PF_T_CLASS: src = t.cmap; n = cells; es = 4; break;
+    case IB_PF_T_GHOST_CELL: src = t.gcell; n = t.ng; es = 4; break;
+    case IB_PF_T_NORMAL: src = t.nrm; n = 2 * (size_t)t.ng; break;
+    case IB_PF_T_DN: src = t.dn; n = t.ng; break;
+    case IB_PF_T_GAMMA: src = t.gamma; n = t.ng; break;
+    case IB_PF_T_AP1: src = t.ap1; n = (size_t)t.ng * kNap; es = 4; break;
+    case IB_PF_T_W1: src = t.w1; n = (size_t)t.ng * kNap; break;
+    case IB_PF_T_AP2: src = t.ap2; n = (size_t)t.ng * kNap; es = 4; break;
+    case IB_PF_T_W2: src = t.w2; n = (size_t)t.ng * kNap; break;
+    case IB_PF_T_FACE_U: src = t.fu; n = t.nfu; es = 4; break;
+    case IB_PF_T_FACE_V: src = t.fv; n = t.nfv; es = 4; break;
+    default: return fail(ctx, IB_PF_E_ARG, "bad table id");
+  }
+  if (table_id >= IB_PF_T_NORMAL && table_id <= IB_PF_T_W2 && !ctx->weights_ready)
+    return fail(ctx, IB_PF_E_STATE, "weights not computed");
+  if (count) *count = (long long)n;
+  if (!dst) return IB_PF_OK;
+  if (nbytes != (long long)(n * es)) return fail(ctx, IB_PF_E_ARG, "nbytes does not match the table size");
+  CK(join_in(*ctx));
+  if (n > 0) CK(cudaMemcpyAsync(dst, src, n * es, cudaMemcpyDeviceToHost, ctx->work));
+  CK(cudaStreamSynchronize(ctx->work));
+  if (table_id == IB_PF_T_CLASS) {   // cmap -> 0 fluid, 1 ghost, 2 solid
+    int* c = (int*)dst;
+    for (size_t k = 0; k < n; ++k) c[k] = c[k] >= 0 ? 1 : (c[k] == kCellSolid ? 2 : 0);
+  }
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
+  if (!out) return fail(ctx, IB_PF_E_ARG, "null output");
+  Instance& in = ctx->inst[instance];
+  switch (what) {
+    case IB_PF_Q_MASS: {
+      CK(join_in(*ctx));
+      mass_reduce(in, ctx->precision, in.C[ctx->cur], ctx->work);
+      CK(cudaGetLastError());
+      double m = 0;
+      CK(cudaMemcpyAsync(&m, in.mass, sizeof(double), cudaMemcpyDeviceToHost, ctx->work));
+      CK(cudaStreamSynchronize(ctx->work));
+      *out = m;
+      return IB_PF_OK;
+    }
+    case IB_PF_Q_N_GHOST: *out = in.tab.ng; return IB_PF_OK;
+    case IB_PF_Q_N_FACE_U: *out = in.tab.nfu; return IB_PF_OK;
+    case IB_PF_Q_N_FACE_V: *out = in.tab.nfv; return IB_PF_OK;
+    case IB_PF_Q_STATUS: {
+      CK(join_in(*ctx));
+      int s = 0;
+      CK(cudaMemcpyAsync(&s, in.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->work));
+      CK(cudaStreamSynchronize(ctx->work));
+      *out = s;
+      return IB_PF_OK;
+    }
+    case IB_PF_Q_STEPS: *out = (double)ctx->steps; return IB_PF_OK;
+    case IB_PF_Q_N_FALLBACK: *out = in.tab.n_fallback; return IB_PF_OK;
+    case IB_PF_Q_LAUNCHES_PER_STEP: {
+      ib_pf_status st = ctx->weights_ready ? capture_graphs(ctx) : IB_PF_E_STATE;
+      if (st != IB_PF_OK) return fail(ctx, st, "launch count needs the precompute");
+      *out = ctx->launches_per_step;
+      return IB_PF_OK;
+    }
+    default: return fail(ctx, IB_PF_E_ARG, "bad query id");
+  }
+}
+
+const char* ib_pf_last_error(const ib_pf_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void ib_pf_destroy(ib_pf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->work) cudaStreamSynchronize(ctx->work);
+  for (int ph = 0; ph < 2; ++ph)
+    if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
+  for (Instance& in : ctx->inst) free_instance(in);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+  if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+  if (ctx->work) cudaStreamDestroy(ctx->work);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// Internal declarations of the ib_pf CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ib_pf.h"
+
+namespace ibpf {
+
+constexpr int kNap = 5;            // averaging points per interpolation point (2D)
+constexpr int kNsub = 100;         // subgrid points per direction for alpha (Sec. 4.1.1)
+constexpr int kMarchDiv = 100;     // normal-march step h/100 (Sec. 4.1.2)
+constexpr int kMarchMax = 1000;    // march limit: 10 h
+constexpr int kBisect = 60;        // bisection refinements of the intersect point
+constexpr double kEps0 = 1.0e-30;  // epsilon_0 of Eq. NormalVectors_part2
+
+// cell map codes (cmap >= 0 is the ghost index)
+constexpr int kCellFluid = -1;
+constexpr int kCellSolid = -2;
+
+struct WallDev {       // wall predicate parameters as the device sees them
+  int kind;
+  double p0, p1, w;    // w = (2 pi) * p[2]
+};
+
+// geometry tables of one instance (device pointers, FP64 / int)
+struct Tables {
+  double* alpha_c = nullptr;   // ny x nx
+  double* alpha_u = nullptr;   // ny x nx
+  double* alpha_v = nullptr;   // (ny+1) x nx
+  int* solidc = nullptr;       // ny x nx, 1 where the cell centre is solid
+  int* cmap = nullptr;         // ny x nx, ghost index / kCellFluid / kCellSolid
+  int ng = 0;
+  int* gcell = nullptr;        // ng
+  double* nrm = nullptr;       // ng x 2
+  double* dn = nullptr;        // ng
+  double* gamma = nullptr;     // ng
+  int* ap1 = nullptr;          // ng x kNap
+  double* w1 = nullptr;
+  int* ap2 = nullptr;
+  double* w2 = nullptr;
+  int nfu = 0, nfv = 0;
+  int* fu = nullptr;           // nfu linear x1-face indices
+  int* fv = nullptr;           // nfv linear x2-face indices
+  int n_fallback = 0;
+};
+
+struct Instance {
+  int nx = 0, ny = 0, lognx = 0, logny = 0;
+  double lx = 0, ly = 0, h = 0;
+  ib_pf_geometry geom{};
+  ib_pf_params prm{};
+  WallDev wall{};
+  Tables tab;
+  // state, element type of the context; index cur of each pair is level n
+  void* C[2] = {nullptr, nullptr};
+  void* U[2] = {nullptr, nullptr};
+  void* V[2] = {nullptr, nullptr};
+  void* P[2] = {nullptr, nullptr};
+  void* Hu = nullptr;
+  void* Hv = nullptr;
+  // scratch of one step
+  void* Q = nullptr;       // CH right-hand side (cells)
+  void* phi = nullptr;     // chemical potential (cells)
+  void* rhs = nullptr;     // Poisson right-hand side (cells)
+  void* phat = nullptr;    // 2P^n - P^{n-1} (cells)
+  void* spec = nullptr;    // ny x (nx/2+1) complex spectrum
+  void* gu = nullptr;      // ng ghost-cell velocities
+  void* gv = nullptr;
+  void* fval = nullptr;    // nfu + nfv re-interpolated face values
+  // transform tables
+  double* lamx = nullptr;  // nx/2+1 eigenvalues of the periodic second difference
+  double* lamy = nullptr;  // ny eigenvalues of the Neumann second difference
+  void* twx = nullptr;     // nx/2 complex exp(-2 pi i k/nx), element type
+  void* twy = nullptr;     // ny/2 complex exp(-2 pi i k/ny)
+  void* wdct = nullptr;    // ny complex exp(-i pi m/(2 ny))
+  // reductions
+  double* partial = nullptr;   // per-block partial sums
+  unsigned* ticket = nullptr;  // last-block counter
+  double* mass = nullptr;      // sum of C after the last step
+  int* status = nullptr;       // 1 once a non-finite value was seen
+  int nblk_red = 0;
+};
+
+struct Ctx {
+  std::vector<Instance> inst;
+  int precision = IB_PF_FP64;
+  size_t esz = 8;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t work = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool geometry_ready = false;
+  bool weights_ready = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int cur = 0;
+  long long steps = 0;
+  int launches_per_step = 0;
+  int* h_status = nullptr;   // pinned copy of the status words
+  std::string err;
+};
+
+// ---- geometry.cu
+cudaError_t geometry_init(Instance& in, cudaStream_t s, std::string& err);
+cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::string& err);
+
+// ---- spectral.cu: solve in the real-Fourier (x1) x cosine (x2) basis.
+// mode 0: (L^2 - (S/Cn^2) L + 1.5 Pe/(Cn^2 dt))^{-1};  mode 1: L^{-1} with the mean mode 0.
+int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
+                   cudaStream_t s);
+cudaError_t spectral_tables(Instance& in, int precision);
+
+// ---- step2d.cu: one time step of one instance; returns the number of kernels launched
+int step_instance(Instance& in, int precision, int cur, cudaStream_t s);
+int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s);
+
+}  // namespace ibpf

@@ -1,0 +1,365 @@
+// Separable spectral solves of the hybrid IB / phase-field step (Appendix A.1 and
+// Eq. PressurePoisson): the 5-point Laplacian with periodic x1 and zero-gradient x2 walls
+// is diagonal in the basis  exp(2 pi i k x1 / Lx)  x  cos(pi m (j + 1/2) / ny).
+//
+// A solve is three kernels:
+//   rows_fwd : real FFT of every x1 row (two rows packed into one complex FFT),
+//   cols     : per spectral column k, cosine transform (DCT-II) along x2, division by the
+//              symbol in FP64, inverse cosine transform (the last forward axis and the first
+//              inverse axis fused in shared memory),
+//   rows_inv : inverse real FFT of every row (two rows per complex FFT).
+// FFTs are radix-2 in shared memory: decimation in time on bit-reversed input for the
+// forward transforms, decimation in frequency to bit-reversed output for the inverse ones.
+// The cosine transforms use an N-point complex FFT with the even/odd reordering
+// v_n = x_{2n}, v_{N-1-n} = x_{2n+1} (Makhoul's algorithm).
+#include <cmath>
+#include <vector>
+
+#include "ibpf_internal.h"
+
+namespace ibpf {
+namespace {
+
+template <typename T> struct C2T;
+template <> struct C2T<double> { using type = double2; };
+template <> struct C2T<float> { using type = float2; };
+
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+  C2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C2>
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { C2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C2>
+__device__ __forceinline__ C2 csub(C2 a, C2 b) { C2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C2>
+__device__ __forceinline__ C2 cconj(C2 a) { a.y = -a.y; return a; }
+
+__device__ __forceinline__ int brev(int n, int logn) {
+  return logn == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - logn));
+}
+
+// In-place radix-2 DIT FFT of x[0..N) (input in bit-reversed order, output natural).
+// tw[k] = exp(-2 pi i k/N), k < N/2.  Called by every thread of the block; lt/nt is the
+// thread's rank within the group that owns x.
+template <typename C2>
+__device__ void fft_dit(C2* x, int logn, const C2* __restrict__ tw, int lt, int nt) {
+  const int N = 1 << logn;
+  for (int s = 0; s < logn; ++s) {
+    const int m = 1 << s;
+    const int tstride = N >> (s + 1);
+    for (int p = lt; p < (N >> 1); p += nt) {
+      const int pos = p & (m - 1);
+      const int i0 = ((p >> s) << (s + 1)) + pos;
+      const int i1 = i0 + m;
+      C2 b = cmul(tw[pos * tstride], x[i1]);
+      C2 a = x[i0];
+      x[i0] = cadd(a, b);
+      x[i1] = csub(a, b);
+    }
+    __syncthreads();
+  }
+}
+
+// In-place radix-2 DIF inverse FFT without the 1/N (input natural, output bit-reversed),
+// twiddles exp(+2 pi i k/N).
+template <typename C2>
+__device__ void ifft_dif(C2* x, int logn, const C2* __restrict__ tw, int lt, int nt) {
+  const int N = 1 << logn;
+  for (int s = logn - 1; s >= 0; --s) {
+    const int m = 1 << s;
+    const int tstride = N >> (s + 1);
+    for (int p = lt; p < (N >> 1); p += nt) {
+      const int pos = p & (m - 1);
+      const int i0 = ((p >> s) << (s + 1)) + pos;
+      const int i1 = i0 + m;
+      C2 a = x[i0], b = x[i1];
+      x[i0] = cadd(a, b);
+      x[i1] = cmul(cconj(tw[pos * tstride]), csub(a, b));
+    }
+    __syncthreads();
+  }
+}
+
+// Forward real FFT of rows 2r and 2r+1 of in (ny x nx) into spec (ny x (nx/2+1)).
+// z = row_a + i row_b;  A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
+template <typename T>
+__global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
+                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int nx = 1 << lognx, nh = nx >> 1;
+  const size_t ra = 2 * (size_t)blockIdx.x, rb = ra + 1;
+  for (int n = threadIdx.x; n < nx; n += blockDim.x) {
+    C2 z;
+    z.x = in[ra * nx + n];
+    z.y = in[rb * nx + n];
+    x[brev(n, lognx)] = z;
+  }
+  __syncthreads();
+  fft_dit(x, lognx, tw, threadIdx.x, blockDim.x);
+  for (int k = threadIdx.x; k <= nh; k += blockDim.x) {
+    C2 z = x[k & (nx - 1)], zc = x[(nx - k) & (nx - 1)];
+    C2 A, B;
+    A.x = T(0.5) * (z.x + zc.x);
+    A.y = T(0.5) * (z.y - zc.y);
+    B.x = T(0.5) * (z.y + zc.y);
+    B.y = T(-0.5) * (z.x - zc.x);
+    spec[ra * (nh + 1) + k] = A;
+    spec[rb * (nh + 1) + k] = B;
+  }
+}
+
+// Inverse of k_rows_fwd: Z_k = A_k + i B_k with Hermitian extension (imaginary parts of
+// the k = 0 and k = nx/2 bins dropped), z = IFFT(Z)/nx, row_a = Re z, row_b = Im z.
+template <typename T>
+__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* __restrict__ out,
+                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int nx = 1 << lognx, nh = nx >> 1;
+  const size_t ra = 2 * (size_t)blockIdx.x, rb = ra + 1;
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+    int kk = k <= nh ? k : nx - k;
+    C2 A = spec[ra * (nh + 1) + kk], B = spec[rb * (nh + 1) + kk];
+    if (kk == 0 || kk == nh) {
+      A.y = T(0);
+      B.y = T(0);
+    }
+    if (k > nh) {
+      A = cconj(A);
+      B = cconj(B);
+    }
+    C2 z;
+    z.x = A.x - B.y;
+    z.y = A.y + B.x;
+    x[k] = z;
+  }
+  __syncthreads();
+  ifft_dif(x, lognx, tw, threadIdx.x, blockDim.x);
+  const T inv = T(1) / T(nx);
+  for (int n = threadIdx.x; n < nx; n += blockDim.x) {
+    C2 z = x[brev(n, lognx)];
+    out[ra * nx + n] = z.x * inv;
+    out[rb * nx + n] = z.y * inv;
+  }
+}
+
+struct SymbolArgs {
+  int mode;          // 0: Cahn-Hilliard quartic, 1: Poisson
+  double s_eta2;     // S / Cn^2
+  double c0;         // 1.5 Pe / (Cn^2 dt)
+  const double* lamx;
+  const double* lamy;
+};
+
+// x2 cosine transform, symbol division and inverse cosine transform of KC spectral
+// columns per block (complex data; the transform is real so it acts on Re and Im alike).
+//   forward  X_m = sum_j x_j cos(pi m (2j+1)/(2N)) via V = FFT(v), v the even/odd reorder:
+//            X_m = Re(w_m Vr_m) + i Re(w_m Vi_m), w_m = exp(-i pi m/(2N)),
+//            Vr_m = (V_m + conj V_{N-m})/2, Vi_m = (V_m - conj V_{N-m})/(2i);
+//   divide   X_m /= sigma(k, m) in FP64;
+//   inverse  Z_m = conj(w_m) (X_m - i X_{N-m}) (X_N = 0), z = IFFT(Z)/N,
+//            x_{2n} = z_n, x_{2n+1} = z_{N-1-n}.
+template <typename T, int KC>
+__global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
+                       const typename C2T<T>::type* __restrict__ tw,
+                       const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* xs = reinterpret_cast<C2*>(smem_raw);
+  const int N = 1 << logny;
+  const int k0 = blockIdx.x * KC;
+  const int tpc = blockDim.x / KC;
+  const int c = threadIdx.x / tpc, lt = threadIdx.x % tpc;
+  // load: consecutive threads take consecutive columns of one row (coalesced)
+  for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
+    int cc = idx % KC, r = idx / KC;
+    int k = k0 + cc;
+    C2 val;
+    val.x = T(0);
+    val.y = T(0);
+    if (k < nh1) val = spec[(size_t)r * nh1 + k];
+    int pos = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
+    xs[cc * N + brev(pos, logny)] = val;
+  }
+  __syncthreads();
+  C2* x = xs + c * N;
+  fft_dit(x, logny, tw, lt, tpc);
+  const int k = min(k0 + c, nh1 - 1);
+  const double lx = sym.lamx[k];
+  for (int m = lt; m <= (N >> 1); m += tpc) {
+    const int mm = (N - m) & (N - 1);
+    C2 Vm = x[m], Vmm = x[mm];
+    C2 Xm, Xmm;
+    {
+      C2 vr, vi, w = wd[m];
+      vr.x = T(0.5) * (Vm.x + Vmm.x);
+      vr.y = T(0.5) * (Vm.y - Vmm.y);
+      vi.x = T(0.5) * (Vm.y + Vmm.y);
+      vi.y = T(-0.5) * (Vm.x - Vmm.x);
+      Xm.x = w.x * vr.x - w.y * vr.y;
+      Xm.y = w.x * vi.x - w.y * vi.y;
+    }
+    {
+      C2 vr, vi, w = wd[mm];
+      vr.x = T(0.5) * (Vmm.x + Vm.x);
+      vr.y = T(0.5) * (Vmm.y - Vm.y);
+      vi.x = T(0.5) * (Vmm.y + Vm.y);
+      vi.y = T(-0.5) * (Vmm.x - Vm.x);
+      Xmm.x = w.x * vr.x - w.y * vr.y;
+      Xmm.y = w.x * vi.x - w.y * vi.y;
+    }
+    // symbol (FP64 eigenvalues and denominators)
+    double Lm = sym.lamy[m] + lx, Lmm = sym.lamy[mm] + lx;
+    double sm, smm;
+    if (sym.mode == 0) {
+      sm = Lm * Lm - sym.s_eta2 * Lm + sym.c0;
+      smm = Lmm * Lmm - sym.s_eta2 * Lmm + sym.c0;
+      Xm.x = (T)((double)Xm.x / sm);
+      Xm.y = (T)((double)Xm.y / sm);
+      Xmm.x = (T)((double)Xmm.x / smm);
+      Xmm.y = (T)((double)Xmm.y / smm);
+    } else {
+      if (Lm == 0.0) {
+        Xm.x = T(0);
+        Xm.y = T(0);
+      } else {
+        Xm.x = (T)((double)Xm.x / Lm);
+        Xm.y = (T)((double)Xm.y / Lm);
+      }
+      if (Lmm == 0.0) {
+        Xmm.x = T(0);
+        Xmm.y = T(0);
+      } else {
+        Xmm.x = (T)((double)Xmm.x / Lmm);
+        Xmm.y = (T)((double)Xmm.y / Lmm);
+      }
+    }
+    // inverse pre-processing: Z_m = conj(w_m) (X_m - i X_{N-m})
+    C2 Zm, Zmm;
+    {
+      C2 y;   // X_m - i X_{N-m}; X_N = 0 for m = 0
+      C2 xo = (m == 0) ? C2{T(0), T(0)} : Xmm;
+      y.x = Xm.x + xo.y;
+      y.y = Xm.y - xo.x;
+      Zm = cmul(cconj(wd[m]), y);
+    }
+    {
+      C2 y;
+      C2 xo = (mm == 0) ? C2{T(0), T(0)} : Xm;
+      y.x = Xmm.x + xo.y;
+      y.y = Xmm.y - xo.x;
+      Zmm = cmul(cconj(wd[mm]), y);
+    }
+    x[m] = Zm;
+    if (mm != m) x[mm] = Zmm;
+  }
+  __syncthreads();
+  ifft_dif(x, logny, tw, lt, tpc);
+  const T inv = T(1) / T(N);
+  for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
+    int cc = idx % KC, r = idx / KC;
+    int kk = k0 + cc;
+    int n = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
+    C2 z = xs[cc * N + brev(n, logny)];
+    z.x *= inv;
+    z.y *= inv;
+    if (kk < nh1) spec[(size_t)r * nh1 + kk] = z;
+  }
+}
+
+constexpr int kColsKC = 2;
+
+template <typename T>
+int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream_t s) {
+  using C2 = typename C2T<T>::type;
+  const int nx = in.nx, ny = in.ny, nh1 = nx / 2 + 1;
+  C2* spec = reinterpret_cast<C2*>(in.spec);
+  const C2* twx = reinterpret_cast<const C2*>(in.twx);
+  const C2* twy = reinterpret_cast<const C2*>(in.twy);
+  const C2* wd = reinterpret_cast<const C2*>(in.wdct);
+  const int trow = nx / 2 < 512 ? nx / 2 : 512;
+  const size_t smem_row = sizeof(C2) * nx;
+  k_rows_fwd<T><<<ny / 2, trow, smem_row, s>>>(reinterpret_cast<const T*>(rhs), spec, in.lognx, twx);
+  SymbolArgs sym;
+  sym.mode = mode;
+  sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
+  sym.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
+  sym.lamx = in.lamx;
+  sym.lamy = in.lamy;
+  const int tpc = ny / 2 < 256 ? ny / 2 : 256;
+  const size_t smem_col = sizeof(C2) * ny * kColsKC;
+  k_cols<T, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC, smem_col, s>>>(
+      spec, nh1, in.logny, twy, wd, sym);
+  k_rows_inv<T><<<ny / 2, trow, smem_row, s>>>(spec, reinterpret_cast<T*>(out), in.lognx, twx);
+  return 3;
+}
+
+template <typename T>
+cudaError_t tables_t(Instance& in) {
+  using C2 = typename C2T<T>::type;
+  const int nx = in.nx, ny = in.ny;
+  const double h = in.h;
+  std::vector<double> lx(nx / 2 + 1), ly(ny);
+  for (int k = 0; k <= nx / 2; ++k) {
+    double sn = std::sin(M_PI * (double)k / (double)nx);
+    lx[k] = -(4.0 / (h * h)) * sn * sn;
+  }
+  for (int m = 0; m < ny; ++m) {
+    double sn = std::sin(M_PI * (double)m / (2.0 * (double)ny));
+    ly[m] = -(4.0 / (h * h)) * sn * sn;
+  }
+  std::vector<C2> twx(nx / 2), twy(ny / 2), wd(ny);
+  for (int k = 0; k < nx / 2; ++k) {
+    double a = 2.0 * M_PI * (double)k / (double)nx;
+    twx[k].x = (T)std::cos(a);
+    twx[k].y = (T)(-std::sin(a));
+  }
+  for (int k = 0; k < ny / 2; ++k) {
+    double a = 2.0 * M_PI * (double)k / (double)ny;
+    twy[k].x = (T)std::cos(a);
+    twy[k].y = (T)(-std::sin(a));
+  }
+  for (int m = 0; m < ny; ++m) {
+    double a = M_PI * (double)m / (2.0 * (double)ny);
+    wd[m].x = (T)std::cos(a);
+    wd[m].y = (T)(-std::sin(a));
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&in.lamx, sizeof(double) * lx.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&in.lamy, sizeof(double) * ly.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&in.twx, sizeof(C2) * twx.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&in.twy, sizeof(C2) * twy.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&in.wdct, sizeof(C2) * wd.size())) != cudaSuccess) return e;
+  cudaMemcpy(in.lamx, lx.data(), sizeof(double) * lx.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(in.lamy, ly.data(), sizeof(double) * ly.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(in.twx, twx.data(), sizeof(C2) * twx.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(in.twy, twy.data(), sizeof(C2) * twy.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(in.wdct, wd.data(), sizeof(C2) * wd.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  // rows of up to 4096 points need 64 KiB of shared memory (FP64)
+  cudaFuncSetAttribute(k_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_cols<T, kColsKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
+                   cudaStream_t s) {
+  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, s)
+                                 : solve_t<float>(in, rhs, out, mode, s);
+}
+
+cudaError_t spectral_tables(Instance& in, int precision) {
+  return precision == IB_PF_FP64 ? tables_t<double>(in) : tables_t<float>(in);
+}
+
+}  // namespace ibpf

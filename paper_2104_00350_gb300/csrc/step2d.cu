@@ -1,0 +1,527 @@
+// One time step of the hybrid IB / phase-field method on a 2D staggered grid
+// (Sec. 4.2 and Appendix A of arXiv 2104.00350), as CUDA kernels templated on the field
+// type T (double for the plain path, float for the mixed path).  Geometry tables stay FP64.
+//
+// Discrete operators (second-order central differences on the staggered grid, Sec. 3.1):
+// cell values C, phi, P at centres; u on x1-faces (face i = left face of cell i), v on
+// x2-faces (rows 0 and ny are the walls, v = 0); face values of cell quantities are
+// arithmetic means; corner viscosity uses the mean C of the four surrounding cells;
+// periodic in x1; at the x2 walls cell fields take mirror rows and u the no-slip ghost
+// row -u.
+#include <cmath>
+
+#include "ibpf_internal.h"
+
+namespace ibpf {
+namespace {
+
+constexpr double kKappa = 1.0606601717798212;   // 3 / (2 sqrt 2)
+
+template <typename T>
+struct StepArgs {
+  int nx, ny;
+  T inv_h, inv_h2, dt;
+  // Cahn-Hilliard
+  T S, inv_eta2, pe_eta2, inv_dt, eta2;
+  // fluid properties: rho(C) = rho_a + rho_b C, mu(C) = mu_a + mu_b C
+  T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
+  // contact angle / slip
+  double k_wet;   // kappa Cn
+  double cos_th;
+  double l_s;
+};
+
+__device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : i - 1; }
+__device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
+
+// ---------------------------------------------------------------- a1: CH right-hand side
+// Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2]   (Appendix A.1)
+template <typename T>
+__global__ void k_ch_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Co,
+                         const T* __restrict__ u, const T* __restrict__ uo,
+                         const T* __restrict__ v, const T* __restrict__ vo, T* __restrict__ Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (i >= nx || j >= ny) return;
+  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  const size_t r = (size_t)j * nx;
+  auto ct = [&](size_t idx) { return T(2) * C[idx] - Co[idx]; };
+  const T c0 = ct(r + i), cw = ct(r + im), ce = ct(r + ip);
+  const T cs = ct((size_t)js * nx + i), cn = ct((size_t)jn * nx + i);
+  const T fx_w = (T(2) * u[r + i] - uo[r + i]) * (T(0.5) * (cw + c0));
+  const T fx_e = (T(2) * u[r + ip] - uo[r + ip]) * (T(0.5) * (c0 + ce));
+  T fy_s = T(0), fy_n = T(0);
+  if (j > 0) fy_s = (T(2) * v[r + i] - vo[r + i]) * (T(0.5) * (cs + c0));
+  if (j < ny - 1) fy_n = (T(2) * v[r + nx + i] - vo[r + nx + i]) * (T(0.5) * (c0 + cn));
+  const T div = (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
+  auto g = [&](T c) { return ((c * c * c - c) - a.S * c) * a.inv_eta2; };
+  const T lap = (((g(ce) + g(cw)) + (g(cn) + g(cs))) - T(4) * g(c0)) * a.inv_h2;
+  const T cc = T(2) * C[r + i] - T(0.5) * Co[r + i];
+  Q[r + i] = a.pe_eta2 * (cc * a.inv_dt - div) + lap;
+}
+
+// ------------------------------------------------------------ a3: contact-angle ghost fill
+// Static angle: C_M = 2 C_IP1 - C_IP2 (Eq. extrapolation) gathered with W1/W2; with G, I,
+// M tied by Eq. UpdateC the normal derivative at I is (C_M - C_I)/(gamma dn), and
+// kappa Cn dC/dn + cos(theta) 3/4 (1 - C_I^2) = 0 gives
+//   C_I = 2c / (k + sqrt(max(0, k^2 - 4 a c))),  a = -3/4 cos, c = k C_M + 3/4 cos,
+//   k = kappa Cn / (gamma dn);   C_G = ((gamma + 1) C_I - C_M) / gamma   (Eq. UpdateC).
+template <typename T>
+__device__ __forceinline__ T gather(const T* __restrict__ f, const int* __restrict__ ap,
+                                    const double* __restrict__ w, int g) {
+  T acc = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap; ++q) acc = acc + (T)w[(size_t)g * kNap + q] * f[ap[(size_t)g * kNap + q]];
+  return acc;
+}
+
+template <typename T>
+__global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= t.ng) return;
+  const T cm = T(2) * gather(C, t.ap1, t.w1, g) - gather(C, t.ap2, t.w2, g);
+  const T gam = (T)t.gamma[g], dn = (T)t.dn[g];
+  const T k = (T)a.k_wet / (gam * dn);
+  const T qa = T(-0.75) * (T)a.cos_th;
+  const T qc = k * cm + T(0.75) * (T)a.cos_th;
+  T disc = k * k - T(4) * qa * qc;
+  disc = disc > T(0) ? disc : T(0);
+  const T ci = T(2) * qc / (k + sqrt(disc));
+  C[t.gcell[g]] = ((gam + T(1)) * ci - cm) / gam;
+}
+
+// ------------------------------------------------------------- a4: chemical potential
+// phi = psi'(C) - Cn^2 lap C on every cell (Eq. Chemical-Potential, nondimensional)
+template <typename T>
+__global__ void k_chem_pot(StepArgs<T> a, const T* __restrict__ C, T* __restrict__ phi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (i >= nx || j >= ny) return;
+  const size_t r = (size_t)j * nx;
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  const T c0 = C[r + i];
+  const T lap = (((C[r + wrap_p(i, nx)] + C[r + wrap_m(i, nx)]) +
+                  (C[(size_t)jn * nx + i] + C[(size_t)js * nx + i])) - T(4) * c0) * a.inv_h2;
+  phi[r + i] = (c0 * c0 * c0 - c0) - a.eta2 * lap;
+}
+
+// zero normal gradient of phi at the wall: phi_G = phi_M (Sec. 4.2.2, last paragraph)
+template <typename T>
+__global__ void k_fill_phi(Tables t, T* __restrict__ phi) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= t.ng) return;
+  phi[t.gcell[g]] = T(2) * gather(phi, t.ap1, t.w1, g) - gather(phi, t.ap2, t.w2, g);
+}
+
+// ----------------------------------------------------- a5: AB2 predictor + penalisation
+// H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho_f)
+// u* = u^n + dt (3/2 H^n - 1/2 H^{n-1} + (kappa/(Re Ca Cn)) phi_f dC/dx / rho_f)
+// u** = alpha_f u*                                (Eqs. PredictionExp, Penalization2)
+// Thread (i, j) updates x1-face (i, j) and, for j >= 1, x2-face (i, j).  H is updated in
+// place (read H^{n-1}, write H^n at the same face).
+template <typename T>
+__global__ void k_predict(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ phi,
+                          const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ Hu,
+                          T* __restrict__ Hv, const double* __restrict__ alpha_u,
+                          const double* __restrict__ alpha_v, T* __restrict__ uss,
+                          T* __restrict__ vss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (i >= nx || j >= ny) return;
+  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const size_t r = (size_t)j * nx;
+  auto cell = [&](const T* f, int ii, int jj) -> T {   // mirror rows beyond the walls
+    jj = jj < 0 ? 0 : (jj >= ny ? ny - 1 : jj);
+    return f[(size_t)jj * nx + ii];
+  };
+  auto uext = [&](int ii, int jj) -> T {                 // no-slip ghost rows
+    if (jj < 0) return -u[ii];
+    if (jj >= ny) return -u[(size_t)(ny - 1) * nx + ii];
+    return u[(size_t)jj * nx + ii];
+  };
+  auto mu = [&](T c) { return a.mu_a + a.mu_b * c; };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  // corner (ii, jc) at (ii h, jc h), jc in [0, ny]
+  auto tau_xy = [&](int ii, int jc) -> T {
+    const int iw = wrap_m(ii, nx);
+    const T ce = T(0.25) * (((cell(C, iw, jc - 1) + cell(C, ii, jc - 1)) + cell(C, iw, jc)) +
+                            cell(C, ii, jc));
+    const T dudy = (uext(ii, jc) - uext(ii, jc - 1)) * a.inv_h;
+    const T dvdx = (v[(size_t)jc * nx + ii] - v[(size_t)jc * nx + iw]) * a.inv_h;
+    return mu(ce) * (dudy + dvdx);
+  };
+  auto uv = [&](int ii, int jc) -> T {
+    const int iw = wrap_m(ii, nx);
+    return (T(0.5) * (uext(ii, jc) + uext(ii, jc - 1))) *
+           (T(0.5) * (v[(size_t)jc * nx + ii] + v[(size_t)jc * nx + iw]));
+  };
+  const T k_st = a.k_st;
+  // ---- x1-face (i, j): cells (im, j) and (i, j)
+  {
+    const T cL = C[r + im], cR = C[r + i];
+    const T rho_f = rho(T(0.5) * (cL + cR));
+    const T txx_R = T(2) * mu(cR) * ((u[r + ip] - u[r + i]) * a.inv_h);
+    const T txx_L = T(2) * mu(cL) * ((u[r + i] - u[r + im]) * a.inv_h);
+    const T visc = (txx_R - txx_L) * a.inv_h + (tau_xy(i, j + 1) - tau_xy(i, j)) * a.inv_h;
+    const T ucR = T(0.5) * (u[r + i] + u[r + ip]);
+    const T ucL = T(0.5) * (u[r + im] + u[r + i]);
+    const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(i, j + 1) - uv(i, j)) * a.inv_h;
+    const T H = -conv + visc / (a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (phi[r + i] + phi[r + im])) * ((cR - cL) * a.inv_h) / rho_f;
+    const T ustar = u[r + i] + a.dt * ((T(1.5) * H - T(0.5) * Hu[r + i]) + st);
+    Hu[r + i] = H;
+    uss[r + i] = (T)alpha_u[r + i] * ustar;
+  }
+  // ---- x2-face (i, j), 1 <= j <= ny-1: cells (i, j-1) and (i, j)
+  if (j >= 1) {
+    const size_t rs = r - nx;
+    const T cB = C[rs + i], cA = C[r + i];
+    const T rho_f = rho(T(0.5) * (cB + cA));
+    const T tyy_A = T(2) * mu(cA) * ((v[r + nx + i] - v[r + i]) * a.inv_h);
+    const T tyy_B = T(2) * mu(cB) * ((v[r + i] - v[rs + i]) * a.inv_h);
+    const T visc = (tau_xy(ip, j) - tau_xy(i, j)) * a.inv_h + (tyy_A - tyy_B) * a.inv_h;
+    const T vcA = T(0.5) * (v[r + i] + v[r + nx + i]);
+    const T vcB = T(0.5) * (v[rs + i] + v[r + i]);
+    const T conv = (uv(ip, j) - uv(i, j)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
+    const T H = -conv + visc / (a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (phi[r + i] + phi[rs + i])) * ((cA - cB) * a.inv_h) / rho_f;
+    const T vstar = v[r + i] + a.dt * ((T(1.5) * H - T(0.5) * Hv[r + i]) + st);
+    Hv[r + i] = H;
+    vss[r + i] = (T)alpha_v[r + i] * vstar;
+  }
+}
+
+// ------------------------------------------------------------- a6: velocity ghost fill
+// centred u** at the averaging points, mirror value by Eq. extrapolation, then
+// V_nG = -V_nM / gamma (Eq. NoPenetration), V_tG = V_tM (l_s - dn)/(l_s + gamma dn)
+// (Eq. UpdateVtan with the static-angle bracket zero), t = (n2, -n1), Eq. UpdateVandW.
+template <typename T>
+__device__ __forceinline__ T ucen(const T* __restrict__ u, int nx, int c) {
+  const int i = c % nx;
+  return T(0.5) * (u[c] + u[c - i + wrap_p(i, nx)]);
+}
+template <typename T>
+__device__ __forceinline__ T vcen(const T* __restrict__ v, int nx, int c) {
+  return T(0.5) * (v[c] + v[c + nx]);
+}
+
+template <typename T>
+__global__ void k_fill_u(StepArgs<T> a, Tables t, const T* __restrict__ uss,
+                         const T* __restrict__ vss, T* __restrict__ gu, T* __restrict__ gv) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= t.ng) return;
+  const int nx = a.nx;
+  T u1 = T(0), v1 = T(0), u2 = T(0), v2 = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap; ++q) {
+    const int c1 = t.ap1[(size_t)g * kNap + q], c2 = t.ap2[(size_t)g * kNap + q];
+    const T w1 = (T)t.w1[(size_t)g * kNap + q], w2 = (T)t.w2[(size_t)g * kNap + q];
+    u1 = u1 + w1 * ucen(uss, nx, c1);
+    v1 = v1 + w1 * vcen(vss, nx, c1);
+    u2 = u2 + w2 * ucen(uss, nx, c2);
+    v2 = v2 + w2 * vcen(vss, nx, c2);
+  }
+  const T uM = T(2) * u1 - u2, vM = T(2) * v1 - v2;
+  const T n1 = (T)t.nrm[2 * g], n2 = (T)t.nrm[2 * g + 1];
+  const T gam = (T)t.gamma[g], dn = (T)t.dn[g], ls = (T)a.l_s;
+  const T vnM = uM * n1 + vM * n2;
+  const T vtM = uM * n2 - vM * n1;
+  const T vnG = -vnM / gam;
+  const T vtG = vtM * (ls - dn) / (ls + gam * dn);
+  gu[g] = vnG * n1 + vtG * n2;
+  gv[g] = vnG * n2 - vtG * n1;
+}
+
+// faces with alpha_f < 1 touching a ghost: mean of the two cell-centred values (ghost
+// value, 0 in a solid non-ghost cell, pre-fix centred u** in a fluid cell).  Values go to
+// fval first so that no face is overwritten while a neighbour still reads it.
+template <typename T>
+__global__ void k_face_values(StepArgs<T> a, Tables t, const T* __restrict__ uss,
+                              const T* __restrict__ vss, const T* __restrict__ gu,
+                              const T* __restrict__ gv, T* __restrict__ fval) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nx = a.nx;
+  if (f < t.nfu) {
+    const int c = t.fu[f];
+    const int i = c % nx;
+    const int cl = c - i + wrap_m(i, nx);
+    auto val = [&](int cc) -> T {
+      const int m = t.cmap[cc];
+      return m >= 0 ? gu[m] : (m == kCellSolid ? T(0) : ucen(uss, nx, cc));
+    };
+    fval[f] = T(0.5) * (val(cl) + val(c));
+  } else if (f < t.nfu + t.nfv) {
+    const int c = t.fv[f - t.nfu];
+    const int cb = c - nx;
+    auto val = [&](int cc) -> T {
+      const int m = t.cmap[cc];
+      return m >= 0 ? gv[m] : (m == kCellSolid ? T(0) : vcen(vss, nx, cc));
+    };
+    fval[f] = T(0.5) * (val(cb) + val(c));
+  }
+}
+
+template <typename T>
+__global__ void k_face_scatter(Tables t, const T* __restrict__ fval, T* __restrict__ uss,
+                               T* __restrict__ vss) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f < t.nfu) uss[t.fu[f]] = fval[f];
+  else if (f < t.nfu + t.nfv) vss[t.fv[f - t.nfu]] = fval[f];
+}
+
+// ------------------------------------------------------------------ a7: Poisson RHS
+// rhs = div[(1 - rho0/rho_f) grad P^] + (rho0/dt) div u**,  P^ = 2P^n - P^{n-1}
+// (Eq. PressurePoisson); also stores P^ for the correction.  Zero flux at the x2 walls.
+template <typename T>
+__global__ void k_poisson_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ P,
+                              const T* __restrict__ Po, const T* __restrict__ uss,
+                              const T* __restrict__ vss, T* __restrict__ rhs,
+                              T* __restrict__ phat) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (i >= nx || j >= ny) return;
+  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const size_t r = (size_t)j * nx;
+  auto ph = [&](size_t idx) { return T(2) * P[idx] - Po[idx]; };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  const T p0 = ph(r + i);
+  const T gx_w = (T(1) - a.rho0 / rho(T(0.5) * (C[r + im] + C[r + i]))) * ((p0 - ph(r + im)) * a.inv_h);
+  const T gx_e = (T(1) - a.rho0 / rho(T(0.5) * (C[r + i] + C[r + ip]))) * ((ph(r + ip) - p0) * a.inv_h);
+  T gy_s = T(0), gy_n = T(0);
+  if (j > 0)
+    gy_s = (T(1) - a.rho0 / rho(T(0.5) * (C[r - nx + i] + C[r + i]))) * ((p0 - ph(r - nx + i)) * a.inv_h);
+  if (j < ny - 1)
+    gy_n = (T(1) - a.rho0 / rho(T(0.5) * (C[r + i] + C[r + nx + i]))) * ((ph(r + nx + i) - p0) * a.inv_h);
+  const T div_g = (gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h;
+  const T div_u = (uss[r + ip] - uss[r + i]) * a.inv_h + (vss[r + nx + i] - vss[r + i]) * a.inv_h;
+  rhs[r + i] = div_g + (a.rho0 * a.inv_dt) * div_u;
+  phat[r + i] = p0;
+}
+
+// ------------------------------------------------- a8: correction + status and mass
+// u^{n+1} = u** - dt [ (1/rho0) grad P^{n+1} + (1/rho_f - 1/rho0) grad P^ ]  (Eq. correction)
+// plus a non-finite check of C^{n+1} and u^{n+1} and the FP64 sum of C^{n+1}: block
+// partial sums in a fixed tree, the last block to finish adds the partials in index order.
+template <typename T>
+__global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ P1,
+                          const T* __restrict__ phat, T* __restrict__ uss, T* __restrict__ vss,
+                          double* __restrict__ partial, unsigned* __restrict__ ticket,
+                          double* __restrict__ mass, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  double csum = 0.0;
+  int bad = 0;
+  if (i < nx && j < ny) {
+    const int im = wrap_m(i, nx);
+    const size_t r = (size_t)j * nx;
+    auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+    {
+      const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
+      const T un = uss[r + i] - a.dt * (a.inv_rho0 * ((P1[r + i] - P1[r + im]) * a.inv_h) +
+                                        (T(1) / rho_f - a.inv_rho0) * ((phat[r + i] - phat[r + im]) * a.inv_h));
+      uss[r + i] = un;
+      bad |= !isfinite((double)un);
+    }
+    if (j >= 1) {
+      const size_t rs = r - nx;
+      const T rho_f = rho(T(0.5) * (C[rs + i] + C[r + i]));
+      const T vn = vss[r + i] - a.dt * (a.inv_rho0 * ((P1[r + i] - P1[rs + i]) * a.inv_h) +
+                                        (T(1) / rho_f - a.inv_rho0) * ((phat[r + i] - phat[rs + i]) * a.inv_h));
+      vss[r + i] = vn;
+      bad |= !isfinite((double)vn);
+    }
+    const double c = (double)C[r + i];
+    bad |= !isfinite(c);
+    csum = c;
+  }
+  __shared__ double red[256];
+  red[tid] = csum;
+  __syncthreads();
+  for (int s = nthr / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, 1);
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  __shared__ bool last;
+  if (tid == 0) {
+    partial[bid] = red[0];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == nblk - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned b = tid; b < nblk; b += nthr) s += ((volatile double*)partial)[b];
+    red[tid] = s;
+    __syncthreads();
+    for (int q = nthr / 2; q > 0; q >>= 1) {
+      if (tid < q) red[tid] += red[tid + q];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      *mass = red[0];
+      *ticket = 0u;
+    }
+  }
+}
+
+// stand-alone FP64 sum of a cell field (same reduction as in k_correct)
+template <typename T>
+__global__ void k_mass(int n, const T* __restrict__ C, double* __restrict__ partial,
+                       unsigned* __restrict__ ticket, double* __restrict__ mass) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  double csum = 0.0;
+  for (int k = blockIdx.x * nthr + tid; k < n; k += gridDim.x * nthr) csum += (double)C[k];
+  __shared__ double red[256];
+  red[tid] = csum;
+  __syncthreads();
+  for (int s = nthr / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  __shared__ bool last;
+  if (tid == 0) {
+    partial[blockIdx.x] = red[0];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (unsigned b = tid; b < gridDim.x; b += nthr) s += ((volatile double*)partial)[b];
+    red[tid] = s;
+    __syncthreads();
+    for (int q = nthr / 2; q > 0; q >>= 1) {
+      if (tid < q) red[tid] += red[tid + q];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      *mass = red[0];
+      *ticket = 0u;
+    }
+  }
+}
+
+template <typename T>
+StepArgs<T> make_args(const Instance& in) {
+  const ib_pf_params& p = in.prm;
+  StepArgs<T> a;
+  a.nx = in.nx;
+  a.ny = in.ny;
+  a.inv_h = (T)(1.0 / in.h);
+  a.inv_h2 = (T)(1.0 / (in.h * in.h));
+  a.dt = (T)p.dt;
+  const double eta2 = p.Cn * p.Cn;
+  a.S = (T)p.S;
+  a.inv_eta2 = (T)(1.0 / eta2);
+  a.pe_eta2 = (T)(p.Pe / eta2);
+  a.inv_dt = (T)(1.0 / p.dt);
+  a.eta2 = (T)eta2;
+  const double rho_l = 1.0, rho_g = 1.0 / p.rho_ratio, mu_l = 1.0, mu_g = 1.0 / p.mu_ratio;
+  a.rho_a = (T)(0.5 * (rho_l + rho_g));
+  a.rho_b = (T)(0.5 * (rho_l - rho_g));
+  a.mu_a = (T)(0.5 * (mu_l + mu_g));
+  a.mu_b = (T)(0.5 * (mu_l - mu_g));
+  const double rho0 = rho_l < rho_g ? rho_l : rho_g;
+  a.rho0 = (T)rho0;
+  a.inv_rho0 = (T)(1.0 / rho0);
+  a.Re = (T)p.Re;
+  a.k_st = (T)(kKappa / (p.Re * p.Ca * p.Cn));
+  a.k_wet = kKappa * p.Cn;
+  a.cos_th = std::cos(p.theta_deg * M_PI / 180.0);
+  a.l_s = p.l_s;
+  return a;
+}
+
+template <typename T>
+int step_t(Instance& in, int cur, cudaStream_t s) {
+  const StepArgs<T> a = make_args<T>(in);
+  const int nx = in.nx, ny = in.ny;
+  const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+  const int nw = cur, no = 1 - cur;   // level n and level n-1 slots
+  T* Cn = (T*)in.C[nw];
+  T* Co = (T*)in.C[no];
+  T* un = (T*)in.U[nw];
+  T* uo = (T*)in.U[no];
+  T* vn = (T*)in.V[nw];
+  T* vo = (T*)in.V[no];
+  T* Pn = (T*)in.P[nw];
+  T* Po = (T*)in.P[no];
+  const Tables& t = in.tab;
+  int launches = 0;
+  // a1 + a2: C^{n+1} into the C^{n-1} slot (C^{n-1} is dead after the RHS)
+  k_ch_rhs<T><<<grd, blk, 0, s>>>(a, Cn, Co, un, uo, vn, vo, (T*)in.Q);
+  ++launches;
+  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.Q, Co, 0, s);
+  T* C1 = Co;
+  // a3
+  if (t.ng > 0) {
+    k_fill_C<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, C1);
+    ++launches;
+  }
+  // a4
+  k_chem_pot<T><<<grd, blk, 0, s>>>(a, C1, (T*)in.phi);
+  ++launches;
+  if (t.ng > 0) {
+    k_fill_phi<T><<<(t.ng + 127) / 128, 128, 0, s>>>(t, (T*)in.phi);
+    ++launches;
+  }
+  // a5: u** into the u^{n-1} slot
+  k_predict<T><<<grd, blk, 0, s>>>(a, C1, (const T*)in.phi, un, vn, (T*)in.Hu, (T*)in.Hv,
+                                   t.alpha_u, t.alpha_v, uo, vo);
+  ++launches;
+  // a6
+  if (t.ng > 0) {
+    k_fill_u<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (T*)in.gu, (T*)in.gv);
+    ++launches;
+  }
+  const int nf = t.nfu + t.nfv;
+  if (nf > 0) {
+    k_face_values<T><<<(nf + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (const T*)in.gu,
+                                                      (const T*)in.gv, (T*)in.fval);
+    k_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(t, (const T*)in.fval, uo, vo);
+    launches += 2;
+  }
+  // a7: P^{n+1} into the P^{n-1} slot (P^ is kept in phat)
+  k_poisson_rhs<T><<<grd, blk, 0, s>>>(a, C1, Pn, Po, uo, vo, (T*)in.rhs, (T*)in.phat);
+  ++launches;
+  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.rhs, Po, 1, s);
+  // a8
+  k_correct<T><<<grd, blk, 0, s>>>(a, C1, Po, (const T*)in.phat, uo, vo, in.partial, in.ticket,
+                                   in.mass, in.status);
+  ++launches;
+  return launches;
+}
+
+template <typename T>
+int mass_t(Instance& in, const void* C, cudaStream_t s) {
+  const int n = in.nx * in.ny;
+  int nb = (n + 255) / 256;
+  if (nb > in.nblk_red) nb = in.nblk_red;
+  k_mass<T><<<nb, 256, 0, s>>>(n, (const T*)C, in.partial, in.ticket, in.mass);
+  return 1;
+}
+
+}  // namespace
+
+int step_instance(Instance& in, int precision, int cur, cudaStream_t s) {
+  return precision == IB_PF_FP64 ? step_t<double>(in, cur, s) : step_t<float>(in, cur, s);
+}
+
+int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s) {
+  return precision == IB_PF_FP64 ? mass_t<double>(in, C, s) : mass_t<float>(in, C, s);
+}
+
+}  // namespace ibpf

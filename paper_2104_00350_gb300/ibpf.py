@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the ib_pf C ABI (include/ib_pf.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.  The
+functions below carry the C names; ``Solver`` bundles them for one context.  Loading
+fails loudly (``ImportError``/``OSError``) when the compiled library is missing: there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libibpf.so"
+
+# ---- enums (mirror include/ib_pf.h)
+OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, FP32 = 0, 1
+WALL_FLAT, WALL_SINUSOID, WALL_NONE = 0, 1, 3
+F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P = range(13)
+FIELD_IDS = {"C": F_C, "C_old": F_C_OLD, "u": F_U, "u_old": F_U_OLD, "v": F_V, "v_old": F_V_OLD,
+             "Hu": F_HU, "Hv": F_HV, "P": F_P, "P_old": F_P_OLD, "phi": F_PHI, "Q": F_Q,
+             "rhs_p": F_RHS_P}
+STATE_FIELDS = ("C", "C_old", "u", "u_old", "v", "v_old", "Hu", "Hv", "P", "P_old")
+(T_ALPHA_C, T_ALPHA_U, T_ALPHA_V, T_CLASS, T_GHOST_CELL, T_NORMAL, T_DN, T_GAMMA, T_AP1, T_W1,
+ T_AP2, T_W2, T_FACE_U, T_FACE_V) = range(14)
+_TABLE_DTYPE = {T_ALPHA_C: np.float64, T_ALPHA_U: np.float64, T_ALPHA_V: np.float64,
+                T_CLASS: np.int32, T_GHOST_CELL: np.int32, T_NORMAL: np.float64,
+                T_DN: np.float64, T_GAMMA: np.float64, T_AP1: np.int32, T_W1: np.float64,
+                T_AP2: np.int32, T_W2: np.float64, T_FACE_U: np.int32, T_FACE_V: np.int32}
+Q_MASS, Q_N_GHOST, Q_N_FACE_U, Q_N_FACE_V, Q_STATUS, Q_STEPS, Q_N_FALLBACK, Q_LAUNCHES = range(8)
+
+
+class Grid(ct.Structure):
+    _fields_ = [("dim", ct.c_int), ("n", ct.c_int * 3), ("L", ct.c_double * 3)]
+
+
+class Geometry(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("p", ct.c_double * 8)]
+
+
+PARAM_NAMES = ("Re", "Ca", "Cn", "Pe", "S", "rho_ratio", "mu_ratio", "theta_deg", "l_s", "mu_f",
+               "d1", "d2", "dt")
+
+
+class Params(ct.Structure):
+    _fields_ = [(n, ct.c_double) for n in PARAM_NAMES] + [("precision", ct.c_int)]
+
+
+class IbPfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ib_pf status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not _LIB_PATH.exists():
+        raise ImportError(f"ib_pf CUDA library not built: {_LIB_PATH} is missing "
+                          "(run __graft_entry__.build())")
+    lib = ct.CDLL(str(_LIB_PATH))
+    vp, i, ll = ct.c_void_p, ct.c_int, ct.c_longlong
+    sigs = {
+        "ib_pf_init_geometry": (i, [ct.POINTER(vp), i, ct.POINTER(Grid), ct.POINTER(Geometry),
+                                    ct.POINTER(Params), vp]),
+        "ib_pf_precompute_weights": (i, [vp]),
+        "ib_pf_step": (i, [vp, i]),
+        "ib_pf_read_fields": (i, [vp, i, i, vp, ll, i]),
+        "ib_pf_write_fields": (i, [vp, i, i, vp, ll, i]),
+        "ib_pf_read_table": (i, [vp, i, i, vp, ll, ct.POINTER(ll)]),
+        "ib_pf_query": (i, [vp, i, i, ct.POINTER(ct.c_double)]),
+        "ib_pf_last_error": (ct.c_char_p, [vp]),
+        "ib_pf_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+# ---- C-named wrappers -----------------------------------------------------------
+def ib_pf_last_error(ctx) -> str:
+    s = lib().ib_pf_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def _check(st: int, ctx=None):
+    if st != OK:
+        raise IbPfError(st, ib_pf_last_error(ctx))
+
+
+def ib_pf_init_geometry(grids, geoms, params, stream: int = 0):
+    n = len(grids)
+    G = (Grid * n)(*grids)
+    W = (Geometry * n)(*geoms)
+    P = (Params * n)(*params)
+    out = ct.c_void_p()
+    _check(lib().ib_pf_init_geometry(ct.byref(out), n, G, W, P, ct.c_void_p(stream)))
+    return out
+
+
+def ib_pf_precompute_weights(ctx):
+    _check(lib().ib_pf_precompute_weights(ctx), ctx)
+
+
+def ib_pf_step(ctx, nsteps: int):
+    _check(lib().ib_pf_step(ctx, int(nsteps)), ctx)
+
+
+def ib_pf_read_fields(ctx, instance: int, field_id: int, dst_ptr: int, nbytes: int, dst_on_host: bool):
+    _check(lib().ib_pf_read_fields(ctx, instance, field_id, ct.c_void_p(dst_ptr), nbytes,
+                                   int(dst_on_host)), ctx)
+
+
+def ib_pf_write_fields(ctx, instance: int, field_id: int, src_ptr: int, nbytes: int, src_on_host: bool):
+    _check(lib().ib_pf_write_fields(ctx, instance, field_id, ct.c_void_p(src_ptr), nbytes,
+                                    int(src_on_host)), ctx)
+
+
+def ib_pf_read_table(ctx, instance: int, table_id: int, dst_ptr: int | None, nbytes: int) -> int:
+    cnt = ct.c_longlong(0)
+    _check(lib().ib_pf_read_table(ctx, instance, table_id, ct.c_void_p(dst_ptr or 0), nbytes,
+                                  ct.byref(cnt)), ctx)
+    return cnt.value
+
+
+def ib_pf_query(ctx, instance: int, what: int) -> float:
+    out = ct.c_double(0.0)
+    _check(lib().ib_pf_query(ctx, instance, what, ct.byref(out)), ctx)
+    return out.value
+
+
+def ib_pf_destroy(ctx):
+    lib().ib_pf_destroy(ctx)
+
+
+# ---- convenience --------------------------------------------------------------------
+def make_grid(nx: int, ny: int, lx: float, ly: float) -> Grid:
+    g = Grid()
+    g.dim = 2
+    g.n[0], g.n[1], g.n[2] = nx, ny, 1
+    g.L[0], g.L[1], g.L[2] = lx, ly, 0.0
+    return g
+
+
+def make_geometry(kind: int, p) -> Geometry:
+    w = Geometry()
+    w.kind = kind
+    for k, x in enumerate(p):
+        w.p[k] = float(x)
+    return w
+
+
+def make_params(precision: int = FP64, **kw) -> Params:
+    p = Params()
+    for n in PARAM_NAMES:
+        setattr(p, n, float(kw[n]))
+    p.precision = precision
+    return p
+
+
+class Solver:
+    """One ib_pf context.  Field I/O accepts numpy arrays (host) or torch CUDA tensors."""
+
+    def __init__(self, grids, geoms, params, stream: int = 0):
+        self.ctx = ib_pf_init_geometry(grids, geoms, params, stream)
+        self.precision = params[0].precision
+        self.dtype = np.float64 if self.precision == FP64 else np.float32
+        self.shapes = [(g.n[1], g.n[0]) for g in grids]
+
+    def close(self):
+        if self.ctx:
+            ib_pf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def field_shape(self, name: str, instance: int = 0):
+        ny, nx = self.shapes[instance]
+        return (ny + 1, nx) if name in ("v", "v_old", "Hv") else (ny, nx)
+
+    def precompute_weights(self):
+        ib_pf_precompute_weights(self.ctx)
+
+    def step(self, nsteps: int = 1):
+        ib_pf_step(self.ctx, nsteps)
+
+    def write(self, name: str, arr, instance: int = 0):
+        if hasattr(arr, "data_ptr"):   # torch tensor on the device
+            assert arr.is_cuda and arr.is_contiguous()
+            ib_pf_write_fields(self.ctx, instance, FIELD_IDS[name], arr.data_ptr(),
+                               arr.numel() * arr.element_size(), False)
+            return
+        a = np.ascontiguousarray(arr, dtype=self.dtype)
+        assert a.shape == self.field_shape(name, instance), (name, a.shape)
+        ib_pf_write_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
+
+    def read(self, name: str, instance: int = 0, out=None) -> np.ndarray:
+        if out is not None and hasattr(out, "data_ptr"):
+            ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], out.data_ptr(),
+                              out.numel() * out.element_size(), False)
+            return out
+        a = np.empty(self.field_shape(name, instance), dtype=self.dtype)
+        ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
+        return a
+
+    def table(self, table_id: int, instance: int = 0) -> np.ndarray:
+        n = ib_pf_read_table(self.ctx, instance, table_id, None, 0)
+        a = np.empty(n, dtype=_TABLE_DTYPE[table_id])
+        if n:
+            ib_pf_read_table(self.ctx, instance, table_id, a.ctypes.data, a.nbytes)
+        return a
+
+    def query(self, what: int, instance: int = 0) -> float:
+        return ib_pf_query(self.ctx, instance, what)
+
+    def write_state(self, state: dict, instance: int = 0):
+        for name in STATE_FIELDS:
+            self.write(name, state[name], instance)
+
+    def read_state(self, instance: int = 0) -> dict:
+        return {name: self.read(name, instance) for name in STATE_FIELDS}
+
+
+def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:
+    """Build a Solver from objects carrying nx, ny, lx, ly, geom_kind, geom_p and a
+    ``params`` object with the ib_pf_params fields (duck-typed; no import of callers)."""
+    grids = [make_grid(c.nx, c.ny, c.lx, c.ly) for c in cases]
+    geoms = [make_geometry(c.geom_kind, c.geom_p) for c in cases]
+    params = [make_params(precision, **{n: getattr(c.params, n) for n in PARAM_NAMES})
+              for c in cases]
+    return Solver(grids, geoms, params, stream)

@@ -1,0 +1,70 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every entry point
+declared in include/ib_pf.h, and rejects invalid arguments before touching the device."""
+import ctypes as ct
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+HEADER = ROOT / "include" / "ib_pf.h"
+
+
+def _declared():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ib_pf_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_00350_gb300 import build
+    build.build()
+    from paper_2104_00350_gb300 import ibpf
+    return ibpf
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("ib_pf_init_geometry", "ib_pf_precompute_weights", "ib_pf_step",
+              "ib_pf_read_fields"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ct.CDLL(str(lib.library_path()))
+    missing = [n for n in _declared() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def _args(lib, nx=128, ny=64, **over):
+    kw = dict(Re=10.0, Ca=0.1, Cn=0.02, Pe=5e3, S=2.0, rho_ratio=10.0, mu_ratio=10.0,
+              theta_deg=60.0, l_s=0.0, mu_f=0.0, d1=2 ** 0.5 / 64, d2=2 ** 0.5 / 128, dt=1e-4)
+    kw.update(over)
+    return ([lib.make_grid(nx, ny, 2.0, 1.0)], [lib.make_geometry(lib.WALL_FLAT, [0.1])],
+            [lib.make_params(lib.FP64, **kw)])
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(nx=100), -1),                 # not a power of two
+    (dict(ny=4), -1),                   # too small
+    (dict(Cn=-1.0), -1),                # negative parameter
+    (dict(mu_f=0.5), -2),               # dynamic angle is not built
+    (dict(d1=0.001), -1),               # d1 not beyond half a cell diagonal
+])
+def test_invalid_arguments_rejected_on_host(lib, bad, status):
+    nx = bad.pop("nx", 128)
+    ny = bad.pop("ny", 64)
+    g, w, p = _args(lib, nx=nx, ny=ny, **bad)
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == status
+    assert lib.ib_pf_last_error(None)
+
+
+def test_dim3_is_reported_unsupported(lib):
+    g, w, p = _args(lib)
+    g[0].dim = 3
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_UNSUPPORTED

@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path bar: max |gpu - oracle| / max |oracle| <= 1e-12 per field after one step from a
+common state.  Geometry tables: integer tables identical, FP64 tables within 1e-12.
+"""
+import numpy as np
+import pytest
+
+from oracle import ib_pf2d as O
+from workloads import cases
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+STEP_FIELDS = ("C", "u", "v", "P", "Hu", "Hv", "C_old", "u_old", "v_old", "P_old")
+
+
+@pytest.fixture(scope="module")
+def ibpf():
+    from paper_2104_00350_gb300 import build
+    build.build()
+    from paper_2104_00350_gb300 import ibpf as m
+    return m
+
+
+def _solver(ibpf, case, precision=None):
+    s = ibpf.solver_from_cases([case], ibpf.FP64 if precision is None else precision)
+    s.precompute_weights()
+    return s
+
+
+def _rel(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
+
+SIN_CASES = [(th, ls) for th in (45.0, 90.0, 135.0) for ls in (0.0, 0.01)]
+
+
+def _geometry_parity(ibpf, case):
+    geo = O.build_geometry(case)
+    s = _solver(ibpf, case)
+    ny, nx = case.ny, case.nx
+    assert np.array_equal(s.table(ibpf.T_ALPHA_C).reshape(ny, nx), geo.alpha_c)
+    assert np.array_equal(s.table(ibpf.T_ALPHA_U).reshape(ny, nx), geo.alpha_u)
+    assert np.array_equal(s.table(ibpf.T_ALPHA_V).reshape(ny + 1, nx), geo.alpha_v)
+    assert np.array_equal(s.table(ibpf.T_CLASS).reshape(ny, nx), geo.cls.astype(np.int32))
+    assert np.array_equal(s.table(ibpf.T_GHOST_CELL), geo.gcell)
+    ng = len(geo.gcell)
+    assert np.abs(s.table(ibpf.T_NORMAL).reshape(ng, 2) - geo.n).max() <= 1e-13
+    assert _rel(s.table(ibpf.T_DN), geo.dn) <= 1e-12
+    assert _rel(s.table(ibpf.T_GAMMA), geo.gamma) <= 1e-12
+    assert np.array_equal(s.table(ibpf.T_AP1).reshape(ng, 5), geo.ap1)
+    assert np.array_equal(s.table(ibpf.T_AP2).reshape(ng, 5), geo.ap2)
+    assert np.abs(s.table(ibpf.T_W1).reshape(ng, 5) - geo.w1).max() <= 1e-12
+    assert np.abs(s.table(ibpf.T_W2).reshape(ng, 5) - geo.w2).max() <= 1e-12
+    assert np.array_equal(s.table(ibpf.T_FACE_U), geo.fu)
+    assert np.array_equal(s.table(ibpf.T_FACE_V), geo.fv)
+    s.close()
+    return geo
+
+
+def test_geometry_tables_flat_wall(ibpf):
+    _geometry_parity(ibpf, cases.flat_wall_128x64())
+
+
+def test_geometry_tables_sinusoid_full_size(ibpf):
+    _geometry_parity(ibpf, cases.sinusoid_wall_512x256(theta_deg=45.0, l_s=0.01))
+
+
+def _step_parity(ibpf, case, st, geo=None, tol=TOL64):
+    geo = geo if geo is not None else O.build_geometry(case)
+    ref, info = O.step(case, geo, st)
+    s = _solver(ibpf, case)
+    s.write_state(st)
+    s.step(1)
+    out = s.read_state()
+    errs = {k: _rel(out[k], ref[k]) for k in STEP_FIELDS}
+    errs["phi"] = _rel(s.read("phi"), info["phi"])
+    errs["Q"] = _rel(s.read("Q"), info["Q"])
+    errs["rhs_p"] = _rel(s.read("rhs_p"), info["rhs_p"])
+    mass = s.query(ibpf.Q_MASS)
+    s.close()
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, (case.name, bad)
+    assert abs(mass - ref["C"].sum()) <= 1e-12 * np.abs(ref["C"]).sum()
+    return errs
+
+
+def test_step_parity_flat_wall_initial_state(ibpf):
+    case = cases.flat_wall_128x64()
+    _step_parity(ibpf, case, cases.initial_state(case))
+
+
+def test_step_parity_flat_wall_random_state(ibpf):
+    case = cases.flat_wall_128x64()
+    _step_parity(ibpf, case, cases.random_state(case, seed=11))
+
+
+@pytest.mark.parametrize("theta,l_s", SIN_CASES)
+def test_step_parity_sinusoid_full_size(ibpf, theta, l_s):
+    case = cases.sinusoid_wall_512x256(theta_deg=theta, l_s=l_s)
+    _step_parity(ibpf, case, cases.random_state(case, seed=int(theta) + int(1000 * l_s)))
+
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (16, 8), (64, 16), (32, 64)])
+def test_step_parity_small_and_ragged(ibpf, nx, ny):
+    # grids smaller than one block in x1 or x2, aspect ratios either way
+    case = cases.flat_wall_case(nx=nx, ny=ny, wall_y=0.23 * ny * 2.0 / nx, Cn=4.0 / nx,
+                                drop_r=0.3 * ny * 2.0 / nx)
+    case = cases.Case2D(case.name, nx, ny, 2.0, ny * 2.0 / nx, case.geom_kind, case.geom_p,
+                        (1.0, case.geom_p[0]), case.drop_r, case.params, 1)
+    _step_parity(ibpf, case, cases.random_state(case, seed=nx + ny))
+
+
+def test_step_parity_without_solid(ibpf):
+    case = cases.free_droplet_case(nx=128, ny=64, rho_ratio=10.0, mu_ratio=10.0)
+    _step_parity(ibpf, case, cases.random_state(case, seed=3))
+
+
+def test_step_parity_largest_grid(ibpf):
+    # the largest grid the library accepts (4096 x 2048), flat wall
+    case = cases.flat_wall_case(nx=4096, ny=2048, Cn=0.002, dt=2e-7)
+    _step_parity(ibpf, case, cases.initial_state(case))
+
+
+def test_multi_step_run_tracks_oracle(ibpf):
+    # 200 steps of the 128x64 flat-wall droplet (theta = 60 deg): drift stays at round-off
+    case = cases.flat_wall_128x64()
+    geo = O.build_geometry(case)
+    st = cases.initial_state(case)
+    s = _solver(ibpf, case)
+    s.write_state(st)
+    for _ in range(200):
+        st, _ = O.step(case, geo, st)
+    s.step(200)
+    out = s.read_state()
+    s.close()
+    for k in ("C", "u", "v", "P"):
+        assert _rel(out[k], st[k]) <= 1e-10, k
+
+
+def test_determinism_and_restart(ibpf):
+    case = cases.sinusoid_wall_512x256(theta_deg=45.0, l_s=0.01)
+    st = cases.initial_state(case)
+    a = _solver(ibpf, case)
+    a.write_state(st)
+    a.step(20)
+    ra = a.read_state()
+    b = _solver(ibpf, case)
+    b.write_state(st)
+    b.step(10)
+    mid = b.read_state()
+    b.close()
+    c = _solver(ibpf, case)
+    c.write_state(mid)
+    c.step(10)
+    rc = c.read_state()
+    for k in ra:
+        assert np.array_equal(ra[k], rc[k]), k
+    a.close()
+    c.close()
+
+
+def test_error_paths(ibpf):
+    case = cases.flat_wall_128x64()
+    s = ibpf.solver_from_cases([case])
+    with pytest.raises(ibpf.IbPfError) as ei:
+        s.step(1)
+    assert ei.value.status == ibpf.E_STATE
+    s.precompute_weights()
+    with pytest.raises(ibpf.IbPfError) as ei:
+        ibpf.ib_pf_read_fields(s.ctx, 0, ibpf.F_C, 1, 8, True)
+    assert ei.value.status == ibpf.E_ARG
+    # a non-finite value injected from the host is caught by the device check
+    st = cases.initial_state(case)
+    st["C"][30, 60] = np.nan
+    s.write_state(st)
+    s.step(1)
+    assert s.query(ibpf.Q_STATUS) == 1.0
+    with pytest.raises(ibpf.IbPfError) as ei:
+        s.step(1)
+    assert ei.value.status == ibpf.E_NUMERIC
+    s.close()
+
+
+def test_launch_count_reported(ibpf):
+    case = cases.flat_wall_128x64()
+    s = _solver(ibpf, case)
+    assert s.query(ibpf.Q_LAUNCHES) >= 10
+    s.close()
