@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of the hybrid IB / phase-field step on GB300 (one JSON line on rank 0).
+
+Workload: the sinusoidal-wall droplet, 512 x 256 cells on [0,2] x [0,1], wall
+y = 0.2 + 0.05 sin(4 pi x), R = 0.3, Cn = 0.01, Re = 10, Ca = 0.1, Pe = 1e4, dt from the
+viscous rule; its six runs (theta in {45, 90, 135} deg x l_s in {0, 0.01}) advance
+together, so one bench step is one full time step (a1..a8) of all six instances.
+
+  value     Mcell-steps/s = instances x cells x timed steps / device time of ib_pf_step,
+            inputs resident in HBM, L2 flushed (256 MiB write) before every timed step.
+  e2e       the same metric through the C ABI with host buffers: every step writes the
+            whole state from pinned host memory, steps, and reads C back to the host.
+  roofline  dominant kernel of a second, event-instrumented pass over the same steps.
+  cpu_baseline / --impl reference: the FP64 CPU oracle (test infrastructure) timed on
+            the host cores.
+
+Multi-GPU (torchrun): every rank runs its own copy of the workload (independent problems,
+no data-path collective); value = all ranks' cell-steps / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "Mcell-steps/s per full CH+NS step (plain FP64 vs FP32/split, batched) at stated error"
+UNIT = "Mcell-steps/s"
+THETAS = (45.0, 90.0, 135.0)
+SLIPS = (0.0, 0.01)
+L2_FLUSH_BYTES = 256 << 20
+
+# algorithmic bytes per cell of one launch, in field words (8 B FP64 / 4 B FP32) plus the
+# FP64 geometry words (alpha) each kernel must read; see the design doc for the derivation.
+KERNEL_WORDS = {          # name: (field words per cell, fp64 words per cell)
+    "ch_rhs": (7.0, 0.0),        # C, Co, u, uo, v, vo -> Q
+    "rows_fwd": (2.0, 0.0),      # real row in, half spectrum (complex) out
+    "cols_solve": (2.0, 0.0),    # spectrum in and out
+    "rows_inv": (2.0, 0.0),      # half spectrum in, real row out
+    "chem_pot": (2.0, 0.0),      # C -> phi
+    "predict": (10.0, 2.0),      # C, phi, u, v, Hu, Hv -> Hu, Hv, u**, v**; alpha_u, alpha_v
+    "poisson_rhs": (7.0, 0.0),   # C, P, Po, u**, v** -> rhs, P^
+    "correct": (7.0, 0.0),       # C, P1, P^, u**, v** -> u, v
+}
+
+
+def workload_cases():
+    from workloads import cases
+    return [cases.sinusoid_wall_512x256(theta_deg=t, l_s=s) for t in THETAS for s in SLIPS]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
+    ap.add_argument("--soak-seconds", type=float, default=1.0,
+                    help="busy GPU time before the timed region so clocks settle")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------- CPU oracle timings
+def oracle_rate(case_list, seconds: float, full_steps: int | None = None):
+    """Mcell-steps/s of the FP64 CPU oracle: either `full_steps` steps of every case, or as
+    many steps of the first case as fit in about `seconds`.  Returns (rate, steps, secs)."""
+    from oracle import ib_pf2d as O
+    from workloads import cases as W
+    if full_steps is not None:
+        geos = [O.build_geometry(c) for c in case_list]
+        states = [W.initial_state(c) for c in case_list]
+        t0 = time.perf_counter()
+        for _ in range(full_steps):
+            for k, c in enumerate(case_list):
+                states[k], _ = O.step(c, geos[k], states[k])
+        dt = time.perf_counter() - t0
+        cells = sum(c.cells for c in case_list) * full_steps
+        return cells / dt / 1e6, full_steps, dt
+    c = case_list[0]
+    geo = O.build_geometry(c)
+    st = W.initial_state(c)
+    st, _ = O.step(c, geo, st)                 # first step outside the sample
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        st, _ = O.step(c, geo, st)
+        n += 1
+    dt = time.perf_counter() - t0
+    return c.cells * n / dt / 1e6, n, dt
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload and metric.  One reference step is one
+    oracle time step of one of the six instances, cycling through them (a bounded sample of
+    the bench step, so that the run stays within minutes)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cl = workload_cases()
+    from oracle import ib_pf2d as O
+    from workloads import cases as W
+    geos = [O.build_geometry(c) for c in cl]
+    states = [W.initial_state(c) for c in cl]
+    for i in range(args.warmup):
+        k = i % len(cl)
+        states[k], _ = O.step(cl[k], geos[k], states[k])
+    cells = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        k = i % len(cl)
+        states[k], _ = O.step(cl[k], geos[k], states[k])
+        cells += cl[k].cells
+    dt = time.perf_counter() - t0
+    value = cells / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "sinusoid_wall_512x256_x6", "grid": "512x256", "instances": 6,
+                   "precision": "fp64", "engine": "FP64 CPU oracle (numpy/scipy)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps, one 512x256 instance each, "
+                                   "cycling through the six"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t_start = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        self.t_start = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- our arm
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_2104_00350_gb300" / "csrc").glob("*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    f = ROOT / "profiles" / f"traffic_sinusoid_512x256_{precision}.txt"
+    if not f.exists():
+        return None
+    sha = kernel_sources_sha()
+    for line in f.read_text().splitlines():
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("csrc_sha") == sha:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def measured_peak():
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        d = json.loads(f.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    from paper_2104_00350_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2104_00350_gb300 import ibpf
+    from workloads import cases as W
+
+    prec = ibpf.FP64 if args.precision == "fp64" else ibpf.FP32
+    esz = 8 if prec == ibpf.FP64 else 4
+    cl = workload_cases()
+    stream = torch.cuda.current_stream()
+    solver = ibpf.solver_from_cases(cl, prec, stream=stream.cuda_stream)
+    solver.precompute_weights()
+    init = [W.initial_state(c) for c in cl]
+    for k in range(len(cl)):
+        solver.write_state(init[k], k)
+    cells = sum(c.cells for c in cl)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(n, collect_kernels=False):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n)]
+        ktot = {}
+        kcount = {}
+        for i in range(n):
+            flush.zero_()
+            evs[i][0].record(stream)
+            solver.step(1)
+            evs[i][1].record(stream)
+            if collect_kernels:
+                names, ms = ibpf.ib_pf_kernel_times(solver.ctx)
+                for nm, t in zip(names, ms):
+                    ktot[nm] = ktot.get(nm, 0.0) + t
+                    kcount[nm] = kcount.get(nm, 0) + 1
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), ktot, kcount
+
+    # warm-up: untimed steps, then keep the GPU busy ~1 s so clocks settle
+    for _ in range(args.warmup):
+        flush.zero_()
+        solver.step(1)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    sampler = ClockSampler(gpu_idx)
+    sampler.start()
+    t_soak = time.time()
+    while time.time() - t_soak < args.soak_seconds:
+        solver.step(20)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, _, _ = timed_steps(args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = int(solver.query(ibpf.Q_LAUNCHES))
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * cells * args.steps / (max_ms * 1e-3) / 1e6
+
+    # kernel-timing pass over the same number of steps (event-instrumented graphs)
+    peak, peak_kind = measured_peak()
+    try:
+        ibpf.ib_pf_set_kernel_timing(solver.ctx, True)
+        solver.step(1)
+        torch.cuda.synchronize()
+        _, ktot, kcount = timed_steps(args.steps, collect_kernels=True)
+        ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
+        dom = max(ktot, key=ktot.get)
+        per_launch_ms = ktot[dom] / kcount[dom]
+        fw, gw = KERNEL_WORDS.get(dom, (0.0, 0.0))
+        alg_bytes = (fw * esz + gw * 8) * cl[0].cells
+        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+        tot = sum(ktot.values())
+        share = {k: round(v / tot, 4) for k, v in sorted(ktot.items(), key=lambda x: -x[1])}
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": read_traffic(dom, args.precision),
+                    "alg_bytes_per_launch": alg_bytes, "per_launch_us": per_launch_ms * 1e3,
+                    "kernel_time_share": share}
+    except Exception as exc:   # keep the headline line even if the timing pass fails
+        roofline = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
+                    "frac": None, "traffic": None, "error": str(exc)[:200]}
+
+    # end to end through the C ABI with host buffers
+    pinned = []
+    h2d = 0
+    for k in range(len(cl)):
+        d = {}
+        for name in ibpf.STATE_FIELDS:
+            a = torch.from_numpy(np.ascontiguousarray(init[k][name], dtype=np.float64 if esz == 8 else np.float32))
+            d[name] = a.pin_memory()
+            h2d += d[name].numel() * esz
+        pinned.append(d)
+    outC = [torch.empty(cl[k].ny, cl[k].nx, dtype=torch.float64 if esz == 8 else torch.float32).pin_memory()
+            for k in range(len(cl))]
+    d2h = sum(o.numel() * esz for o in outC)
+    e2e_steps = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k in range(len(cl)):
+            for name in ibpf.STATE_FIELDS:
+                solver.write(name, pinned[k][name], k)
+        solver.step(1)
+        for k in range(len(cl)):
+            solver.read("C", k, out=outC[k])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * e2e_steps / float(te.item()) / 1e6
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, secs = oracle_rate(cl, args.cpu_sample_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} steps of one 512x256 instance (theta 45, l_s 0) in {secs:.1f} s"}
+    solver.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if esz == 8 else "f32", "data": "synthetic",
+            "config": {"workload": "sinusoid_wall_512x256_x6", "grid": "512x256",
+                       "instances": 6, "thetas_deg": list(THETAS), "slip_lengths": list(SLIPS),
+                       "precision": args.precision,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -175,6 +175,17 @@ ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* 
 /* Scalar diagnostics (ib_pf_query_id) of `instance`.  Synchronises the stream. */
 ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out);
 
+/* Per-kernel timing.  enable != 0 recaptures the step graphs with a CUDA event recorded
+ * on the work stream before the first kernel of a step and after every kernel; enable = 0
+ * restores the plain graphs.  Timing adds the event records to the step, nothing else. */
+ib_pf_status ib_pf_set_kernel_timing(ib_pf_ctx* ctx, int enable);
+
+/* Durations (ms) of the kernels of the last completed step, in launch order over all
+ * instances, with their kernel names (static strings owned by the library).  Requires
+ * ib_pf_set_kernel_timing(ctx, 1) before that step; synchronises the stream.  At most cap
+ * entries are written; *n receives the number of kernels of one step. */
+ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char** names, int* n);
+
 /* Last error message of ctx (or of the last failed creation when ctx is NULL). */
 const char* ib_pf_last_error(const ib_pf_ctx* ctx);
 

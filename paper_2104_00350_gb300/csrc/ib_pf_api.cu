@@ -133,13 +133,24 @@ ib_pf_status capture_graphs(ib_pf_ctx* ctx) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->work, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
-    for (Instance& in : ctx->inst) launches += step_instance(in, ctx->precision, ph, ctx->work);
+    Recorder rec;
+    if (ctx->timing) {
+      rec.events = &ctx->tev;
+      rec.names = &ctx->tnames;
+      rec.start(ctx->work);
+    }
+    for (Instance& in : ctx->inst)
+      launches += step_instance(in, ctx->precision, ph, ctx->work, ctx->timing ? &rec : nullptr);
     for (size_t k = 0; k < ctx->inst.size(); ++k) {
       cudaMemcpyAsync(ctx->h_status + k, ctx->inst[k].status, sizeof(int), cudaMemcpyDeviceToHost,
                       ctx->work);
     }
     cudaError_t e = cudaStreamEndCapture(ctx->work, &g);
     if (e != cudaSuccess) return fail(ctx, IB_PF_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (rec.err != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(ctx, IB_PF_E_CUDA, std::string("timing events: ") + cudaGetErrorString(rec.err));
+    }
     e = cudaGraphInstantiate(&ctx->graph[ph], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(ctx, IB_PF_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -416,6 +427,35 @@ ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out) {
   }
 }
 
+ib_pf_status ib_pf_set_kernel_timing(ib_pf_ctx* ctx, int enable) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  const bool want = enable != 0;
+  if (want == ctx->timing) return IB_PF_OK;
+  CK(cudaStreamSynchronize(ctx->work));
+  for (int ph = 0; ph < 2; ++ph) {
+    if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
+    ctx->graph[ph] = nullptr;
+  }
+  ctx->timing = want;
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char** names, int* n) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (!ctx->timing || ctx->steps == 0 || ctx->tev.size() < 2)
+    return fail(ctx, IB_PF_E_STATE, "no timed step: call ib_pf_set_kernel_timing(ctx, 1) and step");
+  CK(cudaStreamSynchronize(ctx->work));
+  const int nk = (int)ctx->tnames.size();
+  if (n) *n = nk;
+  for (int k = 0; k < nk && k < cap; ++k) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->tev[k], ctx->tev[k + 1]));
+    if (ms) ms[k] = (double)t;
+    if (names) names[k] = ctx->tnames[k];
+  }
+  return IB_PF_OK;
+}
+
 const char* ib_pf_last_error(const ib_pf_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }
@@ -426,6 +466,7 @@ void ib_pf_destroy(ib_pf_ctx* ctx) {
   for (int ph = 0; ph < 2; ++ph)
     if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
   for (Instance& in : ctx->inst) free_instance(in);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
   if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);

@@ -85,6 +85,36 @@ struct Instance {
   int nblk_red = 0;
 };
 
+// Optional event recorder: mark(name) is called after every kernel launch of a step.
+struct Recorder {
+  std::vector<cudaEvent_t>* events = nullptr;   // events[0] is recorded before the step
+  std::vector<const char*>* names = nullptr;
+  size_t next = 0;
+  cudaError_t err = cudaSuccess;
+  void start(cudaStream_t s) {
+    if (!events) return;
+    if (events->empty()) {
+      cudaEvent_t e;
+      if ((err = cudaEventCreate(&e)) != cudaSuccess) return;
+      events->push_back(e);
+    }
+    cudaEventRecordWithFlags((*events)[0], s, cudaEventRecordExternal);
+    next = 1;
+  }
+  void mark(const char* name, cudaStream_t s) {
+    if (!events) return;
+    if (events->size() <= next) {
+      cudaEvent_t e;
+      if ((err = cudaEventCreate(&e)) != cudaSuccess) return;
+      events->push_back(e);
+    }
+    if (names->size() < next) names->resize(next, nullptr);
+    (*names)[next - 1] = name;
+    cudaEventRecordWithFlags((*events)[next], s, cudaEventRecordExternal);
+    ++next;
+  }
+};
+
 struct Ctx {
   std::vector<Instance> inst;
   int precision = IB_PF_FP64;
@@ -99,6 +129,9 @@ struct Ctx {
   long long steps = 0;
   int launches_per_step = 0;
   int* h_status = nullptr;   // pinned copy of the status words
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;        // timing events of the step graphs
+  std::vector<const char*> tnames;     // kernel name of interval k (between tev[k], tev[k+1])
   std::string err;
 };
 
@@ -109,11 +142,11 @@ cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::str
 // ---- spectral.cu: solve in the real-Fourier (x1) x cosine (x2) basis.
 // mode 0: (L^2 - (S/Cn^2) L + 1.5 Pe/(Cn^2 dt))^{-1};  mode 1: L^{-1} with the mean mode 0.
 int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   cudaStream_t s);
+                   cudaStream_t s, Recorder* rec);
 cudaError_t spectral_tables(Instance& in, int precision);
 
 // ---- step2d.cu: one time step of one instance; returns the number of kernels launched
-int step_instance(Instance& in, int precision, int cur, cudaStream_t s);
+int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec);
 int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s);
 
 }  // namespace ibpf

@@ -277,7 +277,8 @@ __global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int lo
 constexpr int kColsKC = 2;
 
 template <typename T>
-int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream_t s) {
+int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream_t s,
+            Recorder* rec) {
   using C2 = typename C2T<T>::type;
   const int nx = in.nx, ny = in.ny, nh1 = nx / 2 + 1;
   C2* spec = reinterpret_cast<C2*>(in.spec);
@@ -287,6 +288,7 @@ int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream
   const int trow = nx / 2 < 512 ? nx / 2 : 512;
   const size_t smem_row = sizeof(C2) * nx;
   k_rows_fwd<T><<<ny / 2, trow, smem_row, s>>>(reinterpret_cast<const T*>(rhs), spec, in.lognx, twx);
+  if (rec) rec->mark("rows_fwd", s);
   SymbolArgs sym;
   sym.mode = mode;
   sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
@@ -297,7 +299,9 @@ int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream
   const size_t smem_col = sizeof(C2) * ny * kColsKC;
   k_cols<T, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC, smem_col, s>>>(
       spec, nh1, in.logny, twy, wd, sym);
+  if (rec) rec->mark("cols_solve", s);
   k_rows_inv<T><<<ny / 2, trow, smem_row, s>>>(spec, reinterpret_cast<T*>(out), in.lognx, twx);
+  if (rec) rec->mark("rows_inv", s);
   return 3;
 }
 
@@ -353,9 +357,9 @@ cudaError_t tables_t(Instance& in) {
 }  // namespace
 
 int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   cudaStream_t s) {
-  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, s)
-                                 : solve_t<float>(in, rhs, out, mode, s);
+                   cudaStream_t s, Recorder* rec) {
+  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, s, rec)
+                                 : solve_t<float>(in, rhs, out, mode, s, rec);
 }
 
 cudaError_t spectral_tables(Instance& in, int precision) {

@@ -446,7 +446,7 @@ StepArgs<T> make_args(const Instance& in) {
 }
 
 template <typename T>
-int step_t(Instance& in, int cur, cudaStream_t s) {
+int step_t(Instance& in, int cur, cudaStream_t s, Recorder* rec) {
   const StepArgs<T> a = make_args<T>(in);
   const int nx = in.nx, ny = in.ny;
   const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
@@ -463,44 +463,54 @@ int step_t(Instance& in, int cur, cudaStream_t s) {
   int launches = 0;
   // a1 + a2: C^{n+1} into the C^{n-1} slot (C^{n-1} is dead after the RHS)
   k_ch_rhs<T><<<grd, blk, 0, s>>>(a, Cn, Co, un, uo, vn, vo, (T*)in.Q);
+  if (rec) rec->mark("ch_rhs", s);
   ++launches;
-  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.Q, Co, 0, s);
+  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.Q, Co, 0, s, rec);
   T* C1 = Co;
   // a3
   if (t.ng > 0) {
     k_fill_C<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, C1);
+    if (rec) rec->mark("fill_C", s);
     ++launches;
   }
   // a4
   k_chem_pot<T><<<grd, blk, 0, s>>>(a, C1, (T*)in.phi);
+  if (rec) rec->mark("chem_pot", s);
   ++launches;
   if (t.ng > 0) {
     k_fill_phi<T><<<(t.ng + 127) / 128, 128, 0, s>>>(t, (T*)in.phi);
+    if (rec) rec->mark("fill_phi", s);
     ++launches;
   }
   // a5: u** into the u^{n-1} slot
   k_predict<T><<<grd, blk, 0, s>>>(a, C1, (const T*)in.phi, un, vn, (T*)in.Hu, (T*)in.Hv,
                                    t.alpha_u, t.alpha_v, uo, vo);
+  if (rec) rec->mark("predict", s);
   ++launches;
   // a6
   if (t.ng > 0) {
     k_fill_u<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (T*)in.gu, (T*)in.gv);
+    if (rec) rec->mark("fill_u", s);
     ++launches;
   }
   const int nf = t.nfu + t.nfv;
   if (nf > 0) {
     k_face_values<T><<<(nf + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (const T*)in.gu,
                                                       (const T*)in.gv, (T*)in.fval);
+    if (rec) rec->mark("face_values", s);
     k_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(t, (const T*)in.fval, uo, vo);
+    if (rec) rec->mark("face_scatter", s);
     launches += 2;
   }
   // a7: P^{n+1} into the P^{n-1} slot (P^ is kept in phat)
   k_poisson_rhs<T><<<grd, blk, 0, s>>>(a, C1, Pn, Po, uo, vo, (T*)in.rhs, (T*)in.phat);
+  if (rec) rec->mark("poisson_rhs", s);
   ++launches;
-  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.rhs, Po, 1, s);
+  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.rhs, Po, 1, s, rec);
   // a8
   k_correct<T><<<grd, blk, 0, s>>>(a, C1, Po, (const T*)in.phat, uo, vo, in.partial, in.ticket,
                                    in.mass, in.status);
+  if (rec) rec->mark("correct", s);
   ++launches;
   return launches;
 }
@@ -516,8 +526,8 @@ int mass_t(Instance& in, const void* C, cudaStream_t s) {
 
 }  // namespace
 
-int step_instance(Instance& in, int precision, int cur, cudaStream_t s) {
-  return precision == IB_PF_FP64 ? step_t<double>(in, cur, s) : step_t<float>(in, cur, s);
+int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec) {
+  return precision == IB_PF_FP64 ? step_t<double>(in, cur, s, rec) : step_t<float>(in, cur, s, rec);
 }
 
 int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s) {

@@ -69,6 +69,9 @@ def _load():
         "ib_pf_write_fields": (i, [vp, i, i, vp, ll, i]),
         "ib_pf_read_table": (i, [vp, i, i, vp, ll, ct.POINTER(ll)]),
         "ib_pf_query": (i, [vp, i, i, ct.POINTER(ct.c_double)]),
+        "ib_pf_set_kernel_timing": (i, [vp, i]),
+        "ib_pf_kernel_times": (i, [vp, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_char_p),
+                                   ct.POINTER(i)]),
         "ib_pf_last_error": (ct.c_char_p, [vp]),
         "ib_pf_destroy": (None, [vp]),
     }
@@ -145,6 +148,19 @@ def ib_pf_query(ctx, instance: int, what: int) -> float:
     return out.value
 
 
+def ib_pf_set_kernel_timing(ctx, enable: bool):
+    _check(lib().ib_pf_set_kernel_timing(ctx, int(enable)), ctx)
+
+
+def ib_pf_kernel_times(ctx, cap: int = 4096):
+    ms = (ct.c_double * cap)()
+    names = (ct.c_char_p * cap)()
+    n = ct.c_int(0)
+    _check(lib().ib_pf_kernel_times(ctx, cap, ms, names, ct.byref(n)), ctx)
+    k = min(n.value, cap)
+    return [names[i].decode() for i in range(k)], [ms[i] for i in range(k)]
+
+
 def ib_pf_destroy(ctx):
     lib().ib_pf_destroy(ctx)
 
@@ -205,10 +221,10 @@ class Solver:
         ib_pf_step(self.ctx, nsteps)
 
     def write(self, name: str, arr, instance: int = 0):
-        if hasattr(arr, "data_ptr"):   # torch tensor on the device
-            assert arr.is_cuda and arr.is_contiguous()
+        if hasattr(arr, "data_ptr"):   # torch tensor (device, or pinned host memory)
+            assert arr.is_contiguous()
             ib_pf_write_fields(self.ctx, instance, FIELD_IDS[name], arr.data_ptr(),
-                               arr.numel() * arr.element_size(), False)
+                               arr.numel() * arr.element_size(), not arr.is_cuda)
             return
         a = np.ascontiguousarray(arr, dtype=self.dtype)
         assert a.shape == self.field_shape(name, instance), (name, a.shape)
@@ -217,7 +233,7 @@ class Solver:
     def read(self, name: str, instance: int = 0, out=None) -> np.ndarray:
         if out is not None and hasattr(out, "data_ptr"):
             ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], out.data_ptr(),
-                              out.numel() * out.element_size(), False)
+                              out.numel() * out.element_size(), not out.is_cuda)
             return out
         a = np.empty(self.field_shape(name, instance), dtype=self.dtype)
         ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)

@@ -189,3 +189,19 @@ def test_launch_count_reported(ibpf):
     s = _solver(ibpf, case)
     assert s.query(ibpf.Q_LAUNCHES) >= 10
     s.close()
+
+
+def test_kernel_timing_events(ibpf):
+    case = cases.flat_wall_128x64()
+    s = _solver(ibpf, case)
+    s.write_state(cases.initial_state(case))
+    ibpf.ib_pf_set_kernel_timing(s.ctx, True)
+    s.step(2)
+    names, ms = ibpf.ib_pf_kernel_times(s.ctx)
+    assert len(names) == int(s.query(ibpf.Q_LAUNCHES))
+    assert "cols_solve" in names and "predict" in names
+    assert all(t >= 0.0 for t in ms) and sum(ms) > 0.0
+    ibpf.ib_pf_set_kernel_timing(s.ctx, False)
+    s.step(1)
+    assert s.query(ibpf.Q_STATUS) == 0.0
+    s.close()
