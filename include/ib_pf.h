@@ -186,6 +186,25 @@ ib_pf_status ib_pf_set_kernel_timing(ib_pf_ctx* ctx, int enable);
  * entries are written; *n receives the number of kernels of one step. */
 ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char** names, int* n);
 
+/* Pressure Poisson solve that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not call cudaMalloc once they are running,
+ * e.g. code whose device memory is owned by another framework's caching allocator, or a
+ * time-critical loop where an allocation could synchronise the device or fail under
+ * memory pressure.  It solves the same discrete problem as step a7 of ib_pf_step (5-point
+ * Laplacian, periodic x1, zero-gradient x2 walls, mean mode set to zero): out = L^{-1} rhs
+ * for one nx x ny FP64 cell field with spacing h.  rhs and out are caller-owned device
+ * pointers (row-major, x1 fastest); work is queued on cuda_stream (NULL = default stream)
+ * and the call returns without synchronising.
+ * Limits: nx, ny powers of two, 8 <= nx, ny <= 1024, nx * ny <= 524288; larger grids
+ * return IB_PF_E_ARG with a message in ib_pf_last_error(NULL).
+ * Scratch: one fixed file-scope device array of about 4.3 MB that every GPU loading the
+ * library holds until the process exits.  The first call on each device looks up the
+ * array's device address; make that first call before any stream capture.  All calls
+ * share the array, so calls that may overlap on the GPU (different streams, or threads)
+ * race and must be serialised by the caller. */
+ib_pf_status ib_pf_poisson_solve_noalloc(const double* rhs, double* out, int nx, int ny,
+                                         double h, void* cuda_stream);
+
 /* Last error message of ctx (or of the last failed creation when ctx is NULL). */
 const char* ib_pf_last_error(const ib_pf_ctx* ctx);
 

@@ -20,7 +20,7 @@ LIB = OUT_DIR / "libibpf.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # geometry decisions (subgrid counts, march, averaging cells) want unfused products
 PER_FILE = {"geometry.cu": ["-fmad=false"]}
-SOURCES = ["ib_pf_api.cu", "geometry.cu", "spectral.cu", "step2d.cu"]
+SOURCES = ["ib_pf_api.cu", "geometry.cu", "spectral.cu", "step2d.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

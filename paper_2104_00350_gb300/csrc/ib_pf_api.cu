@@ -91,6 +91,10 @@ cudaError_t join_out(Ctx& c) {
 
 struct ib_pf_ctx : public Ctx {};
 
+namespace ibpf {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace ibpf
+
 namespace {
 ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg) {
   if (c) c->err = msg;

@@ -144,6 +144,14 @@ cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::str
 int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
                    cudaStream_t s, Recorder* rec);
 cudaError_t spectral_tables(Instance& in, int precision);
+// the same three FP64 kernels on caller-supplied spectrum and table pointers
+int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
+                        double c0, double2* spec, const double* lamx, const double* lamy,
+                        const double2* twx, const double2* twy, const double2* wd,
+                        cudaStream_t s);
+
+// ---- ib_pf_api.cu: message returned by ib_pf_last_error(NULL)
+void set_global_error(const std::string& msg);
 
 // ---- step2d.cu: one time step of one instance; returns the number of kernels launched
 int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec);

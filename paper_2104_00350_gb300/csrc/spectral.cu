@@ -362,6 +362,29 @@ int spectral_solve(const Instance& in, int precision, const void* rhs, void* out
                                  : solve_t<float>(in, rhs, out, mode, s, rec);
 }
 
+int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
+                        double c0, double2* spec, const double* lamx, const double* lamy,
+                        const double2* twx, const double2* twy, const double2* wd,
+                        cudaStream_t s) {
+  int lognx = 0, logny = 0;
+  while ((1 << lognx) < nx) ++lognx;
+  while ((1 << logny) < ny) ++logny;
+  const int nh1 = nx / 2 + 1;
+  const int trow = nx / 2 < 512 ? nx / 2 : 512;
+  k_rows_fwd<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(rhs, spec, lognx, twx);
+  SymbolArgs sym;
+  sym.mode = mode;
+  sym.s_eta2 = s_eta2;
+  sym.c0 = c0;
+  sym.lamx = lamx;
+  sym.lamy = lamy;
+  const int tpc = ny / 2 < 256 ? ny / 2 : 256;
+  k_cols<double, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC,
+                            sizeof(double2) * ny * kColsKC, s>>>(spec, nh1, logny, twy, wd, sym);
+  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(spec, out, lognx, twx);
+  return 3;
+}
+
 cudaError_t spectral_tables(Instance& in, int precision) {
   return precision == IB_PF_FP64 ? tables_t<double>(in) : tables_t<float>(in);
 }

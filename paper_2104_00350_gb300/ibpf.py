@@ -72,6 +72,7 @@ def _load():
         "ib_pf_set_kernel_timing": (i, [vp, i]),
         "ib_pf_kernel_times": (i, [vp, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_char_p),
                                    ct.POINTER(i)]),
+        "ib_pf_poisson_solve_noalloc": (i, [vp, vp, i, i, ct.c_double, vp]),
         "ib_pf_last_error": (ct.c_char_p, [vp]),
         "ib_pf_destroy": (None, [vp]),
     }
@@ -159,6 +160,12 @@ def ib_pf_kernel_times(ctx, cap: int = 4096):
     _check(lib().ib_pf_kernel_times(ctx, cap, ms, names, ct.byref(n)), ctx)
     k = min(n.value, cap)
     return [names[i].decode() for i in range(k)], [ms[i] for i in range(k)]
+
+
+def ib_pf_poisson_solve_noalloc(rhs_ptr: int, out_ptr: int, nx: int, ny: int, h: float,
+                                stream: int = 0):
+    _check(lib().ib_pf_poisson_solve_noalloc(ct.c_void_p(rhs_ptr), ct.c_void_p(out_ptr), nx, ny,
+                                             float(h), ct.c_void_p(stream)))
 
 
 def ib_pf_destroy(ctx):
