@@ -96,8 +96,15 @@ typedef enum {
   IB_PF_F_P = 8,        /* P^n            (cells)  read/write */
   IB_PF_F_P_OLD = 9,    /* P^{n-1} */
   IB_PF_F_PHI = 10,     /* chemical potential of the last step (cells), read only */
-  IB_PF_F_Q = 11,       /* CH right-hand side of the last step (cells), read only */
-  IB_PF_F_RHS_P = 12    /* Poisson right-hand side of the last step (cells), read only */
+  IB_PF_F_Q = 11,       /* CH right-hand side of the last step, increment form (cells):
+                           R = Q - (L^2 - (S/Cn^2) L + c0) B, B = (2C^n - C^{n-1}/2)/1.5;
+                           read only */
+  IB_PF_F_RHS_P = 12,   /* Poisson right-hand side of the last step for the increment
+                           P^{n+1} - (2P^n - P^{n-1}) (cells), read only */
+  IB_PF_F_C_LO = 13,    /* FP32 contexts only: low part of the compensated C^n (C^n is held
+                           as the unevaluated sum C + C_LO); read/write, for restarts.
+                           Writing IB_PF_F_C clears it. */
+  IB_PF_F_C_OLD_LO = 14 /* FP32 contexts only: low part of C^{n-1} */
 } ib_pf_field;
 
 /* geometry tables for ib_pf_read_table (element type in brackets) */

@@ -56,13 +56,15 @@ void* field_ptr(Ctx& c, Instance& in, int id) {
     case IB_PF_F_PHI: return in.phi;
     case IB_PF_F_Q: return in.Q;
     case IB_PF_F_RHS_P: return in.rhs;
+    case IB_PF_F_C_LO: return in.Clo[n];
+    case IB_PF_F_C_OLD_LO: return in.Clo[o];
     default: return nullptr;
   }
 }
 
 void free_instance(Instance& in) {
-  void* ptrs[] = {in.C[0], in.C[1], in.U[0], in.U[1], in.V[0], in.V[1], in.P[0], in.P[1],
-                  in.Hu, in.Hv, in.Q, in.phi, in.rhs, in.phat, in.spec, in.gu, in.gv, in.fval,
+  void* ptrs[] = {in.C[0], in.C[1], in.Clo[0], in.Clo[1], in.U[0], in.U[1], in.V[0], in.V[1], in.P[0], in.P[1],
+                  in.Hu, in.Hv, in.Q, in.phi, in.rhs, in.phat, in.dp, in.spec, in.gu, in.gv, in.fval,
                   in.lamx, in.lamy, in.twx, in.twy, in.wdct, in.partial, in.ticket, in.mass,
                   in.status, in.tab.alpha_c, in.tab.alpha_u, in.tab.alpha_v, in.tab.solidc,
                   in.tab.cmap, in.tab.gcell, in.tab.nrm, in.tab.dn, in.tab.gamma, in.tab.ap1,
@@ -218,10 +220,16 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     const size_t cells = (size_t)in.nx * in.ny, vf = cells + in.nx, es = ctx->esz;
     const size_t nh1 = (size_t)in.nx / 2 + 1;
     void** cell_fields[] = {&in.C[0], &in.C[1], &in.P[0], &in.P[1], &in.U[0], &in.U[1], &in.Hu,
-                            &in.Q, &in.phi, &in.rhs, &in.phat};
+                            &in.Q, &in.phi, &in.rhs, &in.phat, &in.dp};
     for (void** f : cell_fields) {
       if (cudaMalloc(f, cells * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
       cudaMemsetAsync(*f, 0, cells * es, ctx->work);
+    }
+    if (ctx->precision == IB_PF_FP32) {
+      for (void** f : {&in.Clo[0], &in.Clo[1]}) {
+        if (cudaMalloc(f, cells * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
+        cudaMemsetAsync(*f, 0, cells * es, ctx->work);
+      }
     }
     void** vfields[] = {&in.V[0], &in.V[1], &in.Hv};
     for (void** f : vfields) {
@@ -317,7 +325,7 @@ ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void*
   if (!dst) return fail(ctx, IB_PF_E_ARG, "null destination");
   Instance& in = ctx->inst[instance];
   void* src = field_ptr(*ctx, in, field_id);
-  if (!src) return fail(ctx, IB_PF_E_ARG, "bad field id");
+  if (!src) return fail(ctx, IB_PF_E_ARG, "bad field id (low parts exist only in FP32 contexts)");
   const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
   if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
   CK(join_in(*ctx));
@@ -333,14 +341,21 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
   if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
   if (!src) return fail(ctx, IB_PF_E_ARG, "null source");
-  if (field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
+  const bool lo_field = field_id == IB_PF_F_C_LO || field_id == IB_PF_F_C_OLD_LO;
+  if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field)
+    return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
   Instance& in = ctx->inst[instance];
   void* dst = field_ptr(*ctx, in, field_id);
+  if (!dst) return fail(ctx, IB_PF_E_ARG, "low parts of C exist only in FP32 contexts");
   const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
   if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
   CK(join_in(*ctx));
   CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                      ctx->work));
+  if ((field_id == IB_PF_F_C || field_id == IB_PF_F_C_OLD) && ctx->precision == IB_PF_FP32) {
+    void* lo = field_ptr(*ctx, in, field_id == IB_PF_F_C ? IB_PF_F_C_LO : IB_PF_F_C_OLD_LO);
+    CK(cudaMemsetAsync(lo, 0, (size_t)nbytes, ctx->work));
+  }
   if (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV) {
     const size_t row = (size_t)in.nx * ctx->esz;
     CK(cudaMemsetAsync(dst, 0, row, ctx->work));
@@ -400,7 +415,7 @@ ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out) {
   switch (what) {
     case IB_PF_Q_MASS: {
       CK(join_in(*ctx));
-      mass_reduce(in, ctx->precision, in.C[ctx->cur], ctx->work);
+      mass_reduce(in, ctx->precision, in.C[ctx->cur], in.Clo[ctx->cur], ctx->work);
       CK(cudaGetLastError());
       double m = 0;
       CK(cudaMemcpyAsync(&m, in.mass, sizeof(double), cudaMemcpyDeviceToHost, ctx->work));

@@ -57,6 +57,7 @@ struct Instance {
   Tables tab;
   // state, element type of the context; index cur of each pair is level n
   void* C[2] = {nullptr, nullptr};
+  void* Clo[2] = {nullptr, nullptr};   // FP32 path: low parts of the compensated C state
   void* U[2] = {nullptr, nullptr};
   void* V[2] = {nullptr, nullptr};
   void* P[2] = {nullptr, nullptr};
@@ -67,6 +68,7 @@ struct Instance {
   void* phi = nullptr;     // chemical potential (cells)
   void* rhs = nullptr;     // Poisson right-hand side (cells)
   void* phat = nullptr;    // 2P^n - P^{n-1} (cells)
+  void* dp = nullptr;      // pressure increment P^{n+1} - P^ (cells)
   void* spec = nullptr;    // ny x (nx/2+1) complex spectrum
   void* gu = nullptr;      // ng ghost-cell velocities
   void* gv = nullptr;
@@ -139,10 +141,24 @@ struct Ctx {
 cudaError_t geometry_init(Instance& in, cudaStream_t s, std::string& err);
 cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::string& err);
 
+// Epilogue of the inverse row transform (see k_rows_inv): kind 0 plain, 1 add the BDF2
+// predictor (2a - b/2)/1.5, 2 store the increment in delta and add a.
+// With a_lo/b_lo/out_lo set (FP32 path), kind 1 updates the compensated pair (hi, lo)
+// of C exactly: C^{n+1} = (a + a_lo) + ((a + a_lo - b - b_lo)/3 + z) with TwoSum.
+struct EpiArgs {
+  int kind = 0;
+  const void* a = nullptr;
+  const void* b = nullptr;
+  void* delta = nullptr;
+  const void* a_lo = nullptr;
+  const void* b_lo = nullptr;
+  void* out_lo = nullptr;
+};
+
 // ---- spectral.cu: solve in the real-Fourier (x1) x cosine (x2) basis.
 // mode 0: (L^2 - (S/Cn^2) L + 1.5 Pe/(Cn^2 dt))^{-1};  mode 1: L^{-1} with the mean mode 0.
 int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   cudaStream_t s, Recorder* rec);
+                   EpiArgs epi, cudaStream_t s, Recorder* rec);
 cudaError_t spectral_tables(Instance& in, int precision);
 // the same three FP64 kernels on caller-supplied spectrum and table pointers
 int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
@@ -155,6 +171,6 @@ void set_global_error(const std::string& msg);
 
 // ---- step2d.cu: one time step of one instance; returns the number of kernels launched
 int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec);
-int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s);
+int mass_reduce(Instance& in, int precision, const void* C, const void* Clo, cudaStream_t s);
 
 }  // namespace ibpf

@@ -114,11 +114,29 @@ __global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __re
   }
 }
 
+// (hi, lo) + inc -> (out_hi, out_lo): TwoSum of hi and inc (Knuth), the rounding error
+// added to lo, then a FastTwoSum renormalisation.  Only additions, so no contraction.
+template <typename T>
+__device__ __forceinline__ void two_sum_into(T hi, T inc, T lo, T& out_hi, T& out_lo) {
+  const T s = hi + inc;
+  const T bb = s - hi;
+  const T err = (hi - (s - bb)) + (inc - bb);
+  const T l = lo + err;
+  const T h2 = s + l;
+  out_hi = h2;
+  out_lo = l - (h2 - s);
+}
+
 // Inverse of k_rows_fwd: Z_k = A_k + i B_k with Hermitian extension (imaginary parts of
 // the k = 0 and k = nx/2 bins dropped), z = IFFT(Z)/nx, row_a = Re z, row_b = Im z.
+// Epilogue (the solves return increments):
+//   kind 0: out = z
+//   kind 1: out = a + ((a - b)/3 + z)    (BDF2 predictor (2a - b/2)/1.5 of C plus the
+//                                          increment, small terms first; out may alias b)
+//   kind 2: delta = z, out = z + a         (pressure increment on top of a = P^)
 template <typename T>
-__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* __restrict__ out,
-                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
+__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
+                           const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* x = reinterpret_cast<C2*>(smem_raw);
@@ -143,10 +161,36 @@ __global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* __
   __syncthreads();
   ifft_dif(x, lognx, tw, threadIdx.x, blockDim.x);
   const T inv = T(1) / T(nx);
+  const T* ea = reinterpret_cast<const T*>(epi.a);
+  const T* eb = reinterpret_cast<const T*>(epi.b);
+  T* ed = reinterpret_cast<T*>(epi.delta);
   for (int n = threadIdx.x; n < nx; n += blockDim.x) {
     C2 z = x[brev(n, lognx)];
-    out[ra * nx + n] = z.x * inv;
-    out[rb * nx + n] = z.y * inv;
+    const size_t ia = ra * nx + n, ib = rb * nx + n;
+    T va = z.x * inv, vb = z.y * inv;
+    if (epi.kind == 1 && epi.out_lo != nullptr) {
+      // compensated state: value = hi + lo; new pair by TwoSum, then renormalised
+      const T* al = reinterpret_cast<const T*>(epi.a_lo);
+      const T* bl = reinterpret_cast<const T*>(epi.b_lo);
+      T* ol = reinterpret_cast<T*>(epi.out_lo);
+      const T third = T(1.0 / 3.0);
+      T lo_a = al[ia], lo_b = al[ib];
+      T inc_a = ((ea[ia] - eb[ia]) + (lo_a - bl[ia])) * third + va;
+      T inc_b = ((ea[ib] - eb[ib]) + (lo_b - bl[ib])) * third + vb;
+      two_sum_into(ea[ia], inc_a, lo_a, va, ol[ia]);
+      two_sum_into(ea[ib], inc_b, lo_b, vb, ol[ib]);
+    } else if (epi.kind == 1) {
+      const T third = T(1.0 / 3.0);
+      va = ea[ia] + ((ea[ia] - eb[ia]) * third + va);
+      vb = ea[ib] + ((ea[ib] - eb[ib]) * third + vb);
+    } else if (epi.kind == 2) {
+      ed[ia] = va;
+      ed[ib] = vb;
+      va = va + ea[ia];
+      vb = vb + ea[ib];
+    }
+    out[ia] = va;
+    out[ib] = vb;
   }
 }
 
@@ -277,7 +321,7 @@ __global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int lo
 constexpr int kColsKC = 2;
 
 template <typename T>
-int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream_t s,
+int solve_t(const Instance& in, const void* rhs, void* out, int mode, EpiArgs epi, cudaStream_t s,
             Recorder* rec) {
   using C2 = typename C2T<T>::type;
   const int nx = in.nx, ny = in.ny, nh1 = nx / 2 + 1;
@@ -300,7 +344,7 @@ int solve_t(const Instance& in, const void* rhs, void* out, int mode, cudaStream
   k_cols<T, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC, smem_col, s>>>(
       spec, nh1, in.logny, twy, wd, sym);
   if (rec) rec->mark("cols_solve", s);
-  k_rows_inv<T><<<ny / 2, trow, smem_row, s>>>(spec, reinterpret_cast<T*>(out), in.lognx, twx);
+  k_rows_inv<T><<<ny / 2, trow, smem_row, s>>>(spec, reinterpret_cast<T*>(out), in.lognx, twx, epi);
   if (rec) rec->mark("rows_inv", s);
   return 3;
 }
@@ -357,9 +401,9 @@ cudaError_t tables_t(Instance& in) {
 }  // namespace
 
 int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   cudaStream_t s, Recorder* rec) {
-  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, s, rec)
-                                 : solve_t<float>(in, rhs, out, mode, s, rec);
+                   EpiArgs epi, cudaStream_t s, Recorder* rec) {
+  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, epi, s, rec)
+                                 : solve_t<float>(in, rhs, out, mode, epi, s, rec);
 }
 
 int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
@@ -381,7 +425,8 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   const int tpc = ny / 2 < 256 ? ny / 2 : 256;
   k_cols<double, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC,
                             sizeof(double2) * ny * kColsKC, s>>>(spec, nh1, logny, twy, wd, sym);
-  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(spec, out, lognx, twx);
+  EpiArgs plain;
+  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(spec, out, lognx, twx, plain);
   return 3;
 }
 

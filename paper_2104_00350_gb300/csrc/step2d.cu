@@ -35,11 +35,42 @@ __device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : 
 __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
 
 // ---------------------------------------------------------------- a1: CH right-hand side
-// Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2]   (Appendix A.1)
+// The combined solve (L^2 - (S/Cn^2) L + c0) C^{n+1} = Q of Appendix A.1, with
+//   Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2],  c0 = 1.5 Pe/(Cn^2 dt),
+// is solved for the increment over the BDF2 predictor B = C_check / 1.5: since
+// c0 B = (Pe/Cn^2) C_check/dt, the increment dC = C^{n+1} - B solves the same operator
+// with right-hand side
+//   R = Q - (L^2 - (S/Cn^2) L + c0) B = -(Pe/Cn^2) div(u~ C~) + lap(h),
+//   h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B),
+// which is small, so the solve's rounding stays relative to the change of C in one step.
+// k_ch_h writes h; k_ch_rhs writes R.
+template <typename T>
+__global__ void k_ch_h(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Co,
+                       T* __restrict__ hout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny;
+  if (i >= nx || j >= ny) return;
+  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  const size_t r = (size_t)j * nx;
+  // B = (2C^n - C^{n-1}/2)/1.5 = C^n + (C^n - C^{n-1})/3 and C~ - B = 2 (C^n - C^{n-1})/3:
+  // only the small difference meets a rounded constant, so B carries no rounding bias
+  const T third = T(1.0 / 3.0);
+  auto bdf = [&](size_t idx) { return C[idx] + (C[idx] - Co[idx]) * third; };
+  const T b0 = bdf(r + i);
+  const T lapb = (((bdf(r + ip) + bdf(r + im)) + (bdf((size_t)jn * nx + i) + bdf((size_t)js * nx + i))) -
+                  T(4) * b0) * a.inv_h2;
+  const T d = C[r + i] - Co[r + i];
+  const T ct = C[r + i] + d;
+  hout[r + i] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+}
+
 template <typename T>
 __global__ void k_ch_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Co,
                          const T* __restrict__ u, const T* __restrict__ uo,
-                         const T* __restrict__ v, const T* __restrict__ vo, T* __restrict__ Q) {
+                         const T* __restrict__ v, const T* __restrict__ vo,
+                         const T* __restrict__ hf, T* __restrict__ Q) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nx = a.nx, ny = a.ny;
@@ -56,10 +87,9 @@ __global__ void k_ch_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __rest
   if (j > 0) fy_s = (T(2) * v[r + i] - vo[r + i]) * (T(0.5) * (cs + c0));
   if (j < ny - 1) fy_n = (T(2) * v[r + nx + i] - vo[r + nx + i]) * (T(0.5) * (c0 + cn));
   const T div = (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
-  auto g = [&](T c) { return ((c * c * c - c) - a.S * c) * a.inv_eta2; };
-  const T lap = (((g(ce) + g(cw)) + (g(cn) + g(cs))) - T(4) * g(c0)) * a.inv_h2;
-  const T cc = T(2) * C[r + i] - T(0.5) * Co[r + i];
-  Q[r + i] = a.pe_eta2 * (cc * a.inv_dt - div) + lap;
+  const T lap = (((hf[r + ip] + hf[r + im]) + (hf[(size_t)jn * nx + i] + hf[(size_t)js * nx + i])) -
+                 T(4) * hf[r + i]) * a.inv_h2;
+  Q[r + i] = lap - a.pe_eta2 * div;
 }
 
 // ------------------------------------------------------------ a3: contact-angle ghost fill
@@ -78,7 +108,7 @@ __device__ __forceinline__ T gather(const T* __restrict__ f, const int* __restri
 }
 
 template <typename T>
-__global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C) {
+__global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C, T* __restrict__ Clo) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= t.ng) return;
   const T cm = T(2) * gather(C, t.ap1, t.w1, g) - gather(C, t.ap2, t.w2, g);
@@ -90,6 +120,7 @@ __global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C) {
   disc = disc > T(0) ? disc : T(0);
   const T ci = T(2) * qc / (k + sqrt(disc));
   C[t.gcell[g]] = ((gam + T(1)) * ci - cm) / gam;
+  if (Clo) Clo[t.gcell[g]] = T(0);   // a ghost value is exact as stored
 }
 
 // ------------------------------------------------------------- a4: chemical potential
@@ -274,8 +305,10 @@ __global__ void k_face_scatter(Tables t, const T* __restrict__ fval, T* __restri
 }
 
 // ------------------------------------------------------------------ a7: Poisson RHS
-// rhs = div[(1 - rho0/rho_f) grad P^] + (rho0/dt) div u**,  P^ = 2P^n - P^{n-1}
-// (Eq. PressurePoisson); also stores P^ for the correction.  Zero flux at the x2 walls.
+// Eq. PressurePoisson, lap P^{n+1} = div[(1 - rho0/rho_f) grad P^] + (rho0/dt) div u**,
+// P^ = 2P^n - P^{n-1}, solved for the increment dP = P^{n+1} - P^:
+//   lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^]     (zero flux at the x2 walls).
+// Also stores P^ for the correction.
 template <typename T>
 __global__ void k_poisson_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ P,
                               const T* __restrict__ Po, const T* __restrict__ uss,
@@ -290,25 +323,27 @@ __global__ void k_poisson_rhs(StepArgs<T> a, const T* __restrict__ C, const T* _
   auto ph = [&](size_t idx) { return T(2) * P[idx] - Po[idx]; };
   auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
   const T p0 = ph(r + i);
-  const T gx_w = (T(1) - a.rho0 / rho(T(0.5) * (C[r + im] + C[r + i]))) * ((p0 - ph(r + im)) * a.inv_h);
-  const T gx_e = (T(1) - a.rho0 / rho(T(0.5) * (C[r + i] + C[r + ip]))) * ((ph(r + ip) - p0) * a.inv_h);
+  const T gx_w = (a.rho0 / rho(T(0.5) * (C[r + im] + C[r + i]))) * ((p0 - ph(r + im)) * a.inv_h);
+  const T gx_e = (a.rho0 / rho(T(0.5) * (C[r + i] + C[r + ip]))) * ((ph(r + ip) - p0) * a.inv_h);
   T gy_s = T(0), gy_n = T(0);
   if (j > 0)
-    gy_s = (T(1) - a.rho0 / rho(T(0.5) * (C[r - nx + i] + C[r + i]))) * ((p0 - ph(r - nx + i)) * a.inv_h);
+    gy_s = (a.rho0 / rho(T(0.5) * (C[r - nx + i] + C[r + i]))) * ((p0 - ph(r - nx + i)) * a.inv_h);
   if (j < ny - 1)
-    gy_n = (T(1) - a.rho0 / rho(T(0.5) * (C[r + i] + C[r + nx + i]))) * ((ph(r + nx + i) - p0) * a.inv_h);
+    gy_n = (a.rho0 / rho(T(0.5) * (C[r + i] + C[r + nx + i]))) * ((ph(r + nx + i) - p0) * a.inv_h);
   const T div_g = (gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h;
   const T div_u = (uss[r + ip] - uss[r + i]) * a.inv_h + (vss[r + nx + i] - vss[r + i]) * a.inv_h;
-  rhs[r + i] = div_g + (a.rho0 * a.inv_dt) * div_u;
+  rhs[r + i] = (a.rho0 * a.inv_dt) * div_u - div_g;
   phat[r + i] = p0;
 }
 
 // ------------------------------------------------- a8: correction + status and mass
-// u^{n+1} = u** - dt [ (1/rho0) grad P^{n+1} + (1/rho_f - 1/rho0) grad P^ ]  (Eq. correction)
-// plus a non-finite check of C^{n+1} and u^{n+1} and the FP64 sum of C^{n+1}: block
+// Eq. correction, u^{n+1} = u** - dt [ (1/rho0) grad P^{n+1} + (1/rho_f - 1/rho0) grad P^ ],
+// written with the increment: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ].
+// Plus a non-finite check of C^{n+1} and u^{n+1} and the FP64 sum of C^{n+1}: block
 // partial sums in a fixed tree, the last block to finish adds the partials in index order.
 template <typename T>
-__global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ P1,
+__global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Clo,
+                          const T* __restrict__ dP,
                           const T* __restrict__ phat, T* __restrict__ uss, T* __restrict__ vss,
                           double* __restrict__ partial, unsigned* __restrict__ ticket,
                           double* __restrict__ mass, int* __restrict__ status) {
@@ -325,20 +360,20 @@ __global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __res
     auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
     {
       const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
-      const T un = uss[r + i] - a.dt * (a.inv_rho0 * ((P1[r + i] - P1[r + im]) * a.inv_h) +
-                                        (T(1) / rho_f - a.inv_rho0) * ((phat[r + i] - phat[r + im]) * a.inv_h));
+      const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
+                                        a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
       uss[r + i] = un;
       bad |= !isfinite((double)un);
     }
     if (j >= 1) {
       const size_t rs = r - nx;
       const T rho_f = rho(T(0.5) * (C[rs + i] + C[r + i]));
-      const T vn = vss[r + i] - a.dt * (a.inv_rho0 * ((P1[r + i] - P1[rs + i]) * a.inv_h) +
-                                        (T(1) / rho_f - a.inv_rho0) * ((phat[r + i] - phat[rs + i]) * a.inv_h));
+      const T vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
+                                        a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
       vss[r + i] = vn;
       bad |= !isfinite((double)vn);
     }
-    const double c = (double)C[r + i];
+    const double c = (double)C[r + i] + (Clo ? (double)Clo[r + i] : 0.0);
     bad |= !isfinite(c);
     csum = c;
   }
@@ -378,11 +413,13 @@ __global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __res
 
 // stand-alone FP64 sum of a cell field (same reduction as in k_correct)
 template <typename T>
-__global__ void k_mass(int n, const T* __restrict__ C, double* __restrict__ partial,
+__global__ void k_mass(int n, const T* __restrict__ C, const T* __restrict__ Clo,
+                       double* __restrict__ partial,
                        unsigned* __restrict__ ticket, double* __restrict__ mass) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   double csum = 0.0;
-  for (int k = blockIdx.x * nthr + tid; k < n; k += gridDim.x * nthr) csum += (double)C[k];
+  for (int k = blockIdx.x * nthr + tid; k < n; k += gridDim.x * nthr)
+    csum += (double)C[k] + (Clo ? (double)Clo[k] : 0.0);
   __shared__ double red[256];
   red[tid] = csum;
   __syncthreads();
@@ -461,15 +498,26 @@ int step_t(Instance& in, int cur, cudaStream_t s, Recorder* rec) {
   T* Po = (T*)in.P[no];
   const Tables& t = in.tab;
   int launches = 0;
-  // a1 + a2: C^{n+1} into the C^{n-1} slot (C^{n-1} is dead after the RHS)
-  k_ch_rhs<T><<<grd, blk, 0, s>>>(a, Cn, Co, un, uo, vn, vo, (T*)in.Q);
+  // a1 + a2: C^{n+1} into the C^{n-1} slot (C^{n-1} is dead once the RHS and the
+  // predictor in the solve epilogue have read it); h goes through the phi buffer
+  const int prec = sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32;
+  k_ch_h<T><<<grd, blk, 0, s>>>(a, Cn, Co, (T*)in.phi);
+  if (rec) rec->mark("ch_h", s);
+  k_ch_rhs<T><<<grd, blk, 0, s>>>(a, Cn, Co, un, uo, vn, vo, (const T*)in.phi, (T*)in.Q);
   if (rec) rec->mark("ch_rhs", s);
-  ++launches;
-  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.Q, Co, 0, s, rec);
+  launches += 2;
+  EpiArgs epi_c;
+  epi_c.kind = 1;
+  epi_c.a = Cn;
+  epi_c.b = Co;
+  epi_c.a_lo = in.Clo[nw];
+  epi_c.b_lo = in.Clo[no];
+  epi_c.out_lo = in.Clo[no];
+  launches += spectral_solve(in, prec, in.Q, Co, 0, epi_c, s, rec);
   T* C1 = Co;
   // a3
   if (t.ng > 0) {
-    k_fill_C<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, C1);
+    k_fill_C<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, C1, (T*)in.Clo[no]);
     if (rec) rec->mark("fill_C", s);
     ++launches;
   }
@@ -502,25 +550,30 @@ int step_t(Instance& in, int cur, cudaStream_t s, Recorder* rec) {
     if (rec) rec->mark("face_scatter", s);
     launches += 2;
   }
-  // a7: P^{n+1} into the P^{n-1} slot (P^ is kept in phat)
+  // a7: P^{n+1} = P^ + dP into the P^{n-1} slot (P^ is kept in phat, dP in dp)
   k_poisson_rhs<T><<<grd, blk, 0, s>>>(a, C1, Pn, Po, uo, vo, (T*)in.rhs, (T*)in.phat);
   if (rec) rec->mark("poisson_rhs", s);
   ++launches;
-  launches += spectral_solve(in, sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32, in.rhs, Po, 1, s, rec);
+  EpiArgs epi_p;
+  epi_p.kind = 2;
+  epi_p.a = in.phat;
+  epi_p.delta = in.dp;
+  launches += spectral_solve(in, prec, in.rhs, Po, 1, epi_p, s, rec);
   // a8
-  k_correct<T><<<grd, blk, 0, s>>>(a, C1, Po, (const T*)in.phat, uo, vo, in.partial, in.ticket,
-                                   in.mass, in.status);
+  k_correct<T><<<grd, blk, 0, s>>>(a, C1, (const T*)in.Clo[no], (const T*)in.dp,
+                                   (const T*)in.phat, uo, vo, in.partial,
+                                   in.ticket, in.mass, in.status);
   if (rec) rec->mark("correct", s);
   ++launches;
   return launches;
 }
 
 template <typename T>
-int mass_t(Instance& in, const void* C, cudaStream_t s) {
+int mass_t(Instance& in, const void* C, const void* Clo, cudaStream_t s) {
   const int n = in.nx * in.ny;
   int nb = (n + 255) / 256;
   if (nb > in.nblk_red) nb = in.nblk_red;
-  k_mass<T><<<nb, 256, 0, s>>>(n, (const T*)C, in.partial, in.ticket, in.mass);
+  k_mass<T><<<nb, 256, 0, s>>>(n, (const T*)C, (const T*)Clo, in.partial, in.ticket, in.mass);
   return 1;
 }
 
@@ -530,8 +583,8 @@ int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder
   return precision == IB_PF_FP64 ? step_t<double>(in, cur, s, rec) : step_t<float>(in, cur, s, rec);
 }
 
-int mass_reduce(Instance& in, int precision, const void* C, cudaStream_t s) {
-  return precision == IB_PF_FP64 ? mass_t<double>(in, C, s) : mass_t<float>(in, C, s);
+int mass_reduce(Instance& in, int precision, const void* C, const void* Clo, cudaStream_t s) {
+  return precision == IB_PF_FP64 ? mass_t<double>(in, C, Clo, s) : mass_t<float>(in, C, Clo, s);
 }
 
 }  // namespace ibpf

@@ -18,10 +18,11 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libibpf.so"
 OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
 WALL_FLAT, WALL_SINUSOID, WALL_NONE = 0, 1, 3
-F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P = range(13)
+(F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P,
+ F_C_LO, F_C_OLD_LO) = range(15)
 FIELD_IDS = {"C": F_C, "C_old": F_C_OLD, "u": F_U, "u_old": F_U_OLD, "v": F_V, "v_old": F_V_OLD,
              "Hu": F_HU, "Hv": F_HV, "P": F_P, "P_old": F_P_OLD, "phi": F_PHI, "Q": F_Q,
-             "rhs_p": F_RHS_P}
+             "rhs_p": F_RHS_P, "C_lo": F_C_LO, "C_old_lo": F_C_OLD_LO}
 STATE_FIELDS = ("C", "C_old", "u", "u_old", "v", "v_old", "Hu", "Hv", "P", "P_old")
 (T_ALPHA_C, T_ALPHA_U, T_ALPHA_V, T_CLASS, T_GHOST_CELL, T_NORMAL, T_DN, T_GAMMA, T_AP1, T_W1,
  T_AP2, T_W2, T_FACE_U, T_FACE_V) = range(14)
@@ -262,6 +263,21 @@ class Solver:
 
     def read_state(self, instance: int = 0) -> dict:
         return {name: self.read(name, instance) for name in STATE_FIELDS}
+
+    def read_checkpoint(self, instance: int = 0) -> dict:
+        """Everything needed for a bit-exact restart (state plus, in FP32 contexts, the
+        low parts of the compensated C)."""
+        d = self.read_state(instance)
+        if self.precision == FP32:
+            d["C_lo"] = self.read("C_lo", instance)
+            d["C_old_lo"] = self.read("C_old_lo", instance)
+        return d
+
+    def write_checkpoint(self, d: dict, instance: int = 0):
+        self.write_state(d, instance)
+        for name in ("C_lo", "C_old_lo"):
+            if name in d:
+                self.write(name, d[name], instance)
 
 
 def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:

@@ -77,10 +77,21 @@ def _step_parity(ibpf, case, st, geo=None, tol=TOL64):
     out = s.read_state()
     errs = {k: _rel(out[k], ref[k]) for k in STEP_FIELDS}
     errs["phi"] = _rel(s.read("phi"), info["phi"])
-    errs["Q"] = _rel(s.read("Q"), info["Q"])
-    errs["rhs_p"] = _rel(s.read("rhs_p"), info["rhs_p"])
+    # the library solves for increments: its CH right-hand side is R = Q - sigma(B) with
+    # B = (2C^n - C^{n-1}/2)/1.5 and its Poisson right-hand side is rhs - lap(P^); both are
+    # rebuilt from the oracle's Q and rhs with the oracle's stencil (the rebuild cancels
+    # large terms, hence the looser bound on these two intermediates)
+    p = case.params
+    lap = lambda f: O.laplacian(f, case.h)
+    B = (2.0 * st["C"] - 0.5 * st["C_old"]) / 1.5
+    sigB = lap(lap(B)) - (p.S / p.Cn ** 2) * lap(B) + 1.5 * p.Pe / (p.Cn ** 2 * p.dt) * B
+    ph = 2.0 * st["P"] - st["P_old"]
+    inter = {"Q": _rel(s.read("Q"), info["Q"] - sigB),
+             "rhs_p": _rel(s.read("rhs_p"), info["rhs_p"] - lap(ph))}
     mass = s.query(ibpf.Q_MASS)
     s.close()
+    bad = {k: e for k, e in inter.items() if not e <= 1e-9}
+    assert not bad, (case.name, bad)
     bad = {k: e for k, e in errs.items() if not e <= tol}
     assert not bad, (case.name, bad)
     assert abs(mass - ref["C"].sum()) <= 1e-12 * np.abs(ref["C"]).sum()

@@ -206,4 +206,7 @@ def random_state(case: Case2D, seed: int = 7, amp_u: float = 0.05) -> dict:
         s[key] = a
     s["P"] = smooth((ny, nx), 1.0)
     s["P_old"] = s["P"] + smooth((ny, nx), 0.1)
+    # the pressure is defined up to a constant; keep the gauge of the solver (zero mean)
+    s["P"] -= s["P"].mean()
+    s["P_old"] -= s["P_old"].mean()
     return s
