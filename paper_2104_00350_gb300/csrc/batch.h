@@ -1,0 +1,96 @@
+// Device-side view of a context for the batched step kernels: one descriptor per
+// instance and, per kernel family, a table mapping each launched block to
+// (instance, block within the instance).  Every sub-step is one launch over all instances.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ibpf_internal.h"
+
+namespace ibpf {
+
+template <typename T> struct C2T;
+template <> struct C2T<double> { using type = double2; };
+template <> struct C2T<float> { using type = float2; };
+
+// kernel families and their work units
+enum Family {
+  kFamCell = 0,    // 32 x 8 tiles of cells / faces
+  kFamRows = 1,    // pairs of x1 rows (row FFTs)
+  kFamCols = 2,    // groups of kColsKC spectral columns (x2 transforms + symbol)
+  kFamGhost = 3,   // chunks of kGhostChunk ghosts
+  kFamFace = 4,    // chunks of kGhostChunk re-interpolated faces
+  kNumFam = 5
+};
+constexpr int kTileX = 32, kTileY = 8;
+constexpr int kColsKC = 2;
+constexpr int kGhostChunk = 128;
+
+template <typename T>
+struct StepArgs {
+  int nx, ny;
+  T inv_h, inv_h2, dt;
+  // Cahn-Hilliard
+  T S, inv_eta2, pe_eta2, inv_dt, eta2;
+  // fluid properties: rho(C) = rho_a + rho_b C, mu(C) = mu_a + mu_b C
+  T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
+  // contact angle / slip
+  double k_wet;   // kappa Cn
+  double cos_th;
+  double l_s;
+};
+
+template <typename T>
+struct InstDev {
+  using C2 = typename C2T<T>::type;
+  int nx, ny, lognx, logny, gx;   // gx: tiles along x1
+  StepArgs<T> a;
+  T* C[2];
+  T* Clo[2];
+  T* U[2];
+  T* V[2];
+  T* P[2];
+  T* Hu;
+  T* Hv;
+  T* Q;
+  T* phi;
+  T* rhs;
+  T* phat;
+  T* dp;
+  C2* spec;
+  T* gu;
+  T* gv;
+  T* fval;
+  Tables tab;
+  const double* lamx;
+  const double* lamy;
+  const C2* twx;
+  const C2* twy;
+  const C2* wd;
+  double s_eta2, c0;          // CH symbol: L^2 - s_eta2 L + c0
+  double* partial;
+  unsigned* ticket;
+  double* mass;
+  int* status;
+};
+
+// host-side bookkeeping of the batched launches (owned by the context)
+struct BatchPlan {
+  void* d_inst = nullptr;              // InstDev<T>[n]
+  int2* d_blk[kNumFam] = {};           // (instance, local block) per launched block
+  int nblk[kNumFam] = {};
+  int rows_threads = 0, cols_threads = 0;
+  size_t rows_smem = 0, cols_smem = 0;
+  int max_nx = 0, max_ny = 0;
+};
+
+cudaError_t batch_setup(Ctx& c, BatchPlan& plan);
+void batch_free(BatchPlan& plan);
+int step_batch(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, Recorder* rec);
+
+// batched spectral kernels (spectral.cu); src selects Q (0) or rhs (1)
+template <typename T>
+int spectral_solve_batch(const BatchPlan& plan, int mode, int cur, cudaStream_t s,
+                         Recorder* rec);
+
+}  // namespace ibpf

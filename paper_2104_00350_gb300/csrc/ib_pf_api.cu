@@ -6,6 +6,7 @@
 #include <new>
 #include <string>
 
+#include "batch.h"
 #include "ibpf_internal.h"
 
 using namespace ibpf;
@@ -145,8 +146,7 @@ ib_pf_status capture_graphs(ib_pf_ctx* ctx) {
       rec.names = &ctx->tnames;
       rec.start(ctx->work);
     }
-    for (Instance& in : ctx->inst)
-      launches += step_instance(in, ctx->precision, ph, ctx->work, ctx->timing ? &rec : nullptr);
+    launches = step_batch(*ctx, *(BatchPlan*)ctx->plan, ph, ctx->work, ctx->timing ? &rec : nullptr);
     for (size_t k = 0; k < ctx->inst.size(); ++k) {
       cudaMemcpyAsync(ctx->h_status + k, ctx->inst[k].status, sizeof(int), cudaMemcpyDeviceToHost,
                       ctx->work);
@@ -272,6 +272,16 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
   if (cudaStreamSynchronize(ctx->work) != cudaSuccess) {
     ctx->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
     return bail(IB_PF_E_CUDA);
+  }
+  {
+    BatchPlan* plan = new (std::nothrow) BatchPlan();
+    if (!plan) { ctx->err = "out of host memory"; return bail(IB_PF_E_ARG); }
+    ctx->plan = plan;
+    cudaError_t e = batch_setup(*ctx, *plan);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("batch plan: ") + cudaGetErrorString(e);
+      return bail(IB_PF_E_CUDA);
+    }
   }
   join_out(*ctx);
   ctx->geometry_ready = true;
@@ -485,6 +495,10 @@ void ib_pf_destroy(ib_pf_ctx* ctx) {
   for (int ph = 0; ph < 2; ++ph)
     if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
   for (Instance& in : ctx->inst) free_instance(in);
+  if (ctx->plan) {
+    batch_free(*(BatchPlan*)ctx->plan);
+    delete (BatchPlan*)ctx->plan;
+  }
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);

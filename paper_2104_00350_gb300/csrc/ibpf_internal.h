@@ -131,6 +131,7 @@ struct Ctx {
   long long steps = 0;
   int launches_per_step = 0;
   int* h_status = nullptr;   // pinned copy of the status words
+  void* plan = nullptr;      // BatchPlan of the batched launches (batch.h)
   bool timing = false;
   std::vector<cudaEvent_t> tev;        // timing events of the step graphs
   std::vector<const char*> tnames;     // kernel name of interval k (between tev[k], tev[k+1])
@@ -157,8 +158,6 @@ struct EpiArgs {
 
 // ---- spectral.cu: solve in the real-Fourier (x1) x cosine (x2) basis.
 // mode 0: (L^2 - (S/Cn^2) L + 1.5 Pe/(Cn^2 dt))^{-1};  mode 1: L^{-1} with the mean mode 0.
-int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   EpiArgs epi, cudaStream_t s, Recorder* rec);
 cudaError_t spectral_tables(Instance& in, int precision);
 // the same three FP64 kernels on caller-supplied spectrum and table pointers
 int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
@@ -169,8 +168,7 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
 // ---- ib_pf_api.cu: message returned by ib_pf_last_error(NULL)
 void set_global_error(const std::string& msg);
 
-// ---- step2d.cu: one time step of one instance; returns the number of kernels launched
-int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec);
+// ---- step2d.cu (batched step: see batch.h)
 int mass_reduce(Instance& in, int precision, const void* C, const void* Clo, cudaStream_t s);
 
 }  // namespace ibpf

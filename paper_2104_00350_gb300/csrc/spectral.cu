@@ -15,14 +15,11 @@
 #include <cmath>
 #include <vector>
 
+#include "batch.h"
 #include "ibpf_internal.h"
 
 namespace ibpf {
 namespace {
-
-template <typename T> struct C2T;
-template <> struct C2T<double> { using type = double2; };
-template <> struct C2T<float> { using type = float2; };
 
 template <typename C2>
 __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
@@ -84,16 +81,15 @@ __device__ void ifft_dif(C2* x, int logn, const C2* __restrict__ tw, int lt, int
   }
 }
 
-// Forward real FFT of rows 2r and 2r+1 of in (ny x nx) into spec (ny x (nx/2+1)).
+// Forward real FFT of rows ra and ra+1 of in (ny x nx) into spec (ny x (nx/2+1)).
 // z = row_a + i row_b;  A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
 template <typename T>
-__global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
-                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
+__device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
+                              int lognx, const typename C2T<T>::type* __restrict__ tw,
+                              size_t ra, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
   const int nx = 1 << lognx, nh = nx >> 1;
-  const size_t ra = 2 * (size_t)blockIdx.x, rb = ra + 1;
+  const size_t rb = ra + 1;
   for (int n = threadIdx.x; n < nx; n += blockDim.x) {
     C2 z;
     z.x = in[ra * nx + n];
@@ -112,6 +108,15 @@ __global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __re
     spec[ra * (nh + 1) + k] = A;
     spec[rb * (nh + 1) + k] = B;
   }
+  __syncthreads();   // the shared buffer may be reused by the caller
+}
+
+template <typename T>
+__global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
+                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_fwd_core<T>(in, spec, lognx, tw, 2 * (size_t)blockIdx.x, reinterpret_cast<C2*>(smem_raw));
 }
 
 // (hi, lo) + inc -> (out_hi, out_lo): TwoSum of hi and inc (Knuth), the rounding error
@@ -135,13 +140,12 @@ __device__ __forceinline__ void two_sum_into(T hi, T inc, T lo, T& out_hi, T& ou
 //                                          increment, small terms first; out may alias b)
 //   kind 2: delta = z, out = z + a         (pressure increment on top of a = P^)
 template <typename T>
-__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
-                           const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
+__device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
+                              const typename C2T<T>::type* __restrict__ tw, const EpiArgs& epi,
+                              size_t ra, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
   const int nx = 1 << lognx, nh = nx >> 1;
-  const size_t ra = 2 * (size_t)blockIdx.x, rb = ra + 1;
+  const size_t rb = ra + 1;
   for (int k = threadIdx.x; k < nx; k += blockDim.x) {
     int kk = k <= nh ? k : nx - k;
     C2 A = spec[ra * (nh + 1) + kk], B = spec[rb * (nh + 1) + kk];
@@ -192,6 +196,15 @@ __global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* ou
     out[ia] = va;
     out[ib] = vb;
   }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
+                           const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  rows_inv_core<T>(spec, out, lognx, tw, epi, 2 * (size_t)blockIdx.x, reinterpret_cast<C2*>(smem_raw));
 }
 
 struct SymbolArgs {
@@ -211,15 +224,13 @@ struct SymbolArgs {
 //   inverse  Z_m = conj(w_m) (X_m - i X_{N-m}) (X_N = 0), z = IFFT(Z)/N,
 //            x_{2n} = z_n, x_{2n+1} = z_{N-1-n}.
 template <typename T, int KC>
-__global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
-                       const typename C2T<T>::type* __restrict__ tw,
-                       const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym) {
+__device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
+                          const typename C2T<T>::type* __restrict__ tw,
+                          const typename C2T<T>::type* __restrict__ wd, const SymbolArgs& sym,
+                          int k0, typename C2T<T>::type* xs) {
   using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* xs = reinterpret_cast<C2*>(smem_raw);
   const int N = 1 << logny;
-  const int k0 = blockIdx.x * KC;
-  const int tpc = blockDim.x / KC;
+  const int tpc = blockDim.x / KC;   // threads per column (>= 1)
   const int c = threadIdx.x / tpc, lt = threadIdx.x % tpc;
   // load: consecutive threads take consecutive columns of one row (coalesced)
   for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
@@ -316,37 +327,78 @@ __global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int lo
     z.y *= inv;
     if (kk < nh1) spec[(size_t)r * nh1 + kk] = z;
   }
+  __syncthreads();
 }
 
-constexpr int kColsKC = 2;
+template <typename T, int KC>
+__global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
+                       const typename C2T<T>::type* __restrict__ tw,
+                       const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cols_core<T, KC>(spec, nh1, logny, tw, wd, sym, blockIdx.x * KC, reinterpret_cast<C2*>(smem_raw));
+}
+
+// ------------------------------------------------------------------ batched launches
+template <typename T>
+__global__ void kb_rows_fwd(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                            int nblk, int src) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int2 w = blk[b];
+    const InstDev<T>& d = I[w.x];
+    rows_fwd_core<T>(src == 0 ? d.Q : d.rhs, d.spec, d.lognx, d.twx, 2 * (size_t)w.y,
+                     reinterpret_cast<C2*>(smem_raw));
+  }
+}
 
 template <typename T>
-int solve_t(const Instance& in, const void* rhs, void* out, int mode, EpiArgs epi, cudaStream_t s,
-            Recorder* rec) {
+__global__ void kb_cols(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                        int mode) {
   using C2 = typename C2T<T>::type;
-  const int nx = in.nx, ny = in.ny, nh1 = nx / 2 + 1;
-  C2* spec = reinterpret_cast<C2*>(in.spec);
-  const C2* twx = reinterpret_cast<const C2*>(in.twx);
-  const C2* twy = reinterpret_cast<const C2*>(in.twy);
-  const C2* wd = reinterpret_cast<const C2*>(in.wdct);
-  const int trow = nx / 2 < 512 ? nx / 2 : 512;
-  const size_t smem_row = sizeof(C2) * nx;
-  k_rows_fwd<T><<<ny / 2, trow, smem_row, s>>>(reinterpret_cast<const T*>(rhs), spec, in.lognx, twx);
-  if (rec) rec->mark("rows_fwd", s);
-  SymbolArgs sym;
-  sym.mode = mode;
-  sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
-  sym.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
-  sym.lamx = in.lamx;
-  sym.lamy = in.lamy;
-  const int tpc = ny / 2 < 256 ? ny / 2 : 256;
-  const size_t smem_col = sizeof(C2) * ny * kColsKC;
-  k_cols<T, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC, smem_col, s>>>(
-      spec, nh1, in.logny, twy, wd, sym);
-  if (rec) rec->mark("cols_solve", s);
-  k_rows_inv<T><<<ny / 2, trow, smem_row, s>>>(spec, reinterpret_cast<T*>(out), in.lognx, twx, epi);
-  if (rec) rec->mark("rows_inv", s);
-  return 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int2 w = blk[b];
+    const InstDev<T>& d = I[w.x];
+    SymbolArgs sym;
+    sym.mode = mode;
+    sym.s_eta2 = d.s_eta2;
+    sym.c0 = d.c0;
+    sym.lamx = d.lamx;
+    sym.lamy = d.lamy;
+    cols_core<T, kColsKC>(d.spec, d.nx / 2 + 1, d.logny, d.twy, d.wd, sym, w.y * kColsKC,
+                          reinterpret_cast<C2*>(smem_raw));
+  }
+}
+
+// kind 1: C^{n+1} into the C^{n-1} slot (compensated in FP32); kind 2: P^{n+1} = P^ + dP
+template <typename T>
+__global__ void kb_rows_inv(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                            int nblk, int kind, int cur) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int2 w = blk[b];
+    const InstDev<T>& d = I[w.x];
+    EpiArgs epi;
+    epi.kind = kind;
+    T* out;
+    if (kind == 1) {
+      epi.a = d.C[cur];
+      epi.b = d.C[1 - cur];
+      epi.a_lo = d.Clo[cur];
+      epi.b_lo = d.Clo[1 - cur];
+      epi.out_lo = d.Clo[1 - cur];
+      out = d.C[1 - cur];
+    } else {
+      epi.a = d.phat;
+      epi.delta = d.dp;
+      out = d.P[1 - cur];
+    }
+    rows_inv_core<T>(d.spec, out, d.lognx, d.twx, epi, 2 * (size_t)w.y,
+                     reinterpret_cast<C2*>(smem_raw));
+  }
 }
 
 template <typename T>
@@ -392,19 +444,31 @@ cudaError_t tables_t(Instance& in) {
   e = cudaMemcpy(in.wdct, wd.data(), sizeof(C2) * wd.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   // rows of up to 4096 points need 64 KiB of shared memory (FP64)
-  cudaFuncSetAttribute(k_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(k_cols<T, kColsKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(kb_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(kb_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(kb_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int spectral_solve(const Instance& in, int precision, const void* rhs, void* out, int mode,
-                   EpiArgs epi, cudaStream_t s, Recorder* rec) {
-  return precision == IB_PF_FP64 ? solve_t<double>(in, rhs, out, mode, epi, s, rec)
-                                 : solve_t<float>(in, rhs, out, mode, epi, s, rec);
+template <typename T>
+int spectral_solve_batch(const BatchPlan& plan, int mode, int cur, cudaStream_t s,
+                         Recorder* rec) {
+  const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
+  kb_rows_fwd<T><<<plan.nblk[kFamRows], plan.rows_threads, plan.rows_smem, s>>>(
+      I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode);
+  if (rec) rec->mark("rows_fwd", s);
+  kb_cols<T><<<plan.nblk[kFamCols], plan.cols_threads, plan.cols_smem, s>>>(
+      I, plan.d_blk[kFamCols], plan.nblk[kFamCols], mode);
+  if (rec) rec->mark("cols_solve", s);
+  kb_rows_inv<T><<<plan.nblk[kFamRows], plan.rows_threads, plan.rows_smem, s>>>(
+      I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode == 0 ? 1 : 2, cur);
+  if (rec) rec->mark("rows_inv", s);
+  return 3;
 }
+template int spectral_solve_batch<double>(const BatchPlan&, int, int, cudaStream_t, Recorder*);
+template int spectral_solve_batch<float>(const BatchPlan&, int, int, cudaStream_t, Recorder*);
 
 int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode, double s_eta2,
                         double c0, double2* spec, const double* lamx, const double* lamy,

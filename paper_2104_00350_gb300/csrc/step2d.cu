@@ -10,26 +10,15 @@
 // row -u.
 #include <cmath>
 
+#include <vector>
+
+#include "batch.h"
 #include "ibpf_internal.h"
 
 namespace ibpf {
 namespace {
 
 constexpr double kKappa = 1.0606601717798212;   // 3 / (2 sqrt 2)
-
-template <typename T>
-struct StepArgs {
-  int nx, ny;
-  T inv_h, inv_h2, dt;
-  // Cahn-Hilliard
-  T S, inv_eta2, pe_eta2, inv_dt, eta2;
-  // fluid properties: rho(C) = rho_a + rho_b C, mu(C) = mu_a + mu_b C
-  T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
-  // contact angle / slip
-  double k_wet;   // kappa Cn
-  double cos_th;
-  double l_s;
-};
 
 __device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : i - 1; }
 __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
@@ -45,12 +34,10 @@ __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : 
 // which is small, so the solve's rounding stays relative to the change of C in one step.
 // k_ch_h writes h; k_ch_rhs writes R.
 template <typename T>
-__global__ void k_ch_h(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Co,
-                       T* __restrict__ hout) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void ch_h_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                          const T* __restrict__ Co, T* __restrict__ hout,
+                                          int i, int j) {
   const int nx = a.nx, ny = a.ny;
-  if (i >= nx || j >= ny) return;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
   const size_t r = (size_t)j * nx;
@@ -67,14 +54,12 @@ __global__ void k_ch_h(StepArgs<T> a, const T* __restrict__ C, const T* __restri
 }
 
 template <typename T>
-__global__ void k_ch_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Co,
-                         const T* __restrict__ u, const T* __restrict__ uo,
-                         const T* __restrict__ v, const T* __restrict__ vo,
-                         const T* __restrict__ hf, T* __restrict__ Q) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void ch_rhs_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                            const T* __restrict__ Co, const T* __restrict__ u,
+                                            const T* __restrict__ uo, const T* __restrict__ v,
+                                            const T* __restrict__ vo, const T* __restrict__ hf,
+                                            T* __restrict__ Q, int i, int j) {
   const int nx = a.nx, ny = a.ny;
-  if (i >= nx || j >= ny) return;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
   const size_t r = (size_t)j * nx;
@@ -108,9 +93,8 @@ __device__ __forceinline__ T gather(const T* __restrict__ f, const int* __restri
 }
 
 template <typename T>
-__global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C, T* __restrict__ Clo) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= t.ng) return;
+__device__ __forceinline__ void fill_C_ghost(const StepArgs<T>& a, const Tables& t, T* __restrict__ C,
+                                             T* __restrict__ Clo, int g) {
   const T cm = T(2) * gather(C, t.ap1, t.w1, g) - gather(C, t.ap2, t.w2, g);
   const T gam = (T)t.gamma[g], dn = (T)t.dn[g];
   const T k = (T)a.k_wet / (gam * dn);
@@ -126,11 +110,9 @@ __global__ void k_fill_C(StepArgs<T> a, Tables t, T* __restrict__ C, T* __restri
 // ------------------------------------------------------------- a4: chemical potential
 // phi = psi'(C) - Cn^2 lap C on every cell (Eq. Chemical-Potential, nondimensional)
 template <typename T>
-__global__ void k_chem_pot(StepArgs<T> a, const T* __restrict__ C, T* __restrict__ phi) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void chem_pot_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                              T* __restrict__ phi, int i, int j) {
   const int nx = a.nx, ny = a.ny;
-  if (i >= nx || j >= ny) return;
   const size_t r = (size_t)j * nx;
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
   const T c0 = C[r + i];
@@ -141,9 +123,7 @@ __global__ void k_chem_pot(StepArgs<T> a, const T* __restrict__ C, T* __restrict
 
 // zero normal gradient of phi at the wall: phi_G = phi_M (Sec. 4.2.2, last paragraph)
 template <typename T>
-__global__ void k_fill_phi(Tables t, T* __restrict__ phi) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= t.ng) return;
+__device__ __forceinline__ void fill_phi_ghost(const Tables& t, T* __restrict__ phi, int g) {
   phi[t.gcell[g]] = T(2) * gather(phi, t.ap1, t.w1, g) - gather(phi, t.ap2, t.w2, g);
 }
 
@@ -154,15 +134,13 @@ __global__ void k_fill_phi(Tables t, T* __restrict__ phi) {
 // Thread (i, j) updates x1-face (i, j) and, for j >= 1, x2-face (i, j).  H is updated in
 // place (read H^{n-1}, write H^n at the same face).
 template <typename T>
-__global__ void k_predict(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ phi,
-                          const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ Hu,
-                          T* __restrict__ Hv, const double* __restrict__ alpha_u,
-                          const double* __restrict__ alpha_v, T* __restrict__ uss,
-                          T* __restrict__ vss) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void predict_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                             const T* __restrict__ phi, const T* __restrict__ u,
+                                             const T* __restrict__ v, T* __restrict__ Hu,
+                                             T* __restrict__ Hv, const double* __restrict__ alpha_u,
+                                             const double* __restrict__ alpha_v, T* __restrict__ uss,
+                                             T* __restrict__ vss, int i, int j) {
   const int nx = a.nx, ny = a.ny;
-  if (i >= nx || j >= ny) return;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const size_t r = (size_t)j * nx;
   auto cell = [&](const T* f, int ii, int jj) -> T {   // mirror rows beyond the walls
@@ -241,10 +219,9 @@ __device__ __forceinline__ T vcen(const T* __restrict__ v, int nx, int c) {
 }
 
 template <typename T>
-__global__ void k_fill_u(StepArgs<T> a, Tables t, const T* __restrict__ uss,
-                         const T* __restrict__ vss, T* __restrict__ gu, T* __restrict__ gv) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= t.ng) return;
+__device__ __forceinline__ void fill_u_ghost(const StepArgs<T>& a, const Tables& t,
+                                             const T* __restrict__ uss, const T* __restrict__ vss,
+                                             T* __restrict__ gu, T* __restrict__ gv, int g) {
   const int nx = a.nx;
   T u1 = T(0), v1 = T(0), u2 = T(0), v2 = T(0);
 #pragma unroll
@@ -271,10 +248,10 @@ __global__ void k_fill_u(StepArgs<T> a, Tables t, const T* __restrict__ uss,
 // value, 0 in a solid non-ghost cell, pre-fix centred u** in a fluid cell).  Values go to
 // fval first so that no face is overwritten while a neighbour still reads it.
 template <typename T>
-__global__ void k_face_values(StepArgs<T> a, Tables t, const T* __restrict__ uss,
-                              const T* __restrict__ vss, const T* __restrict__ gu,
-                              const T* __restrict__ gv, T* __restrict__ fval) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void face_value(const StepArgs<T>& a, const Tables& t,
+                                           const T* __restrict__ uss, const T* __restrict__ vss,
+                                           const T* __restrict__ gu, const T* __restrict__ gv,
+                                           T* __restrict__ fval, int f) {
   const int nx = a.nx;
   if (f < t.nfu) {
     const int c = t.fu[f];
@@ -297,9 +274,8 @@ __global__ void k_face_values(StepArgs<T> a, Tables t, const T* __restrict__ uss
 }
 
 template <typename T>
-__global__ void k_face_scatter(Tables t, const T* __restrict__ fval, T* __restrict__ uss,
-                               T* __restrict__ vss) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void face_scatter(const Tables& t, const T* __restrict__ fval,
+                                             T* __restrict__ uss, T* __restrict__ vss, int f) {
   if (f < t.nfu) uss[t.fu[f]] = fval[f];
   else if (f < t.nfu + t.nfv) vss[t.fv[f - t.nfu]] = fval[f];
 }
@@ -310,14 +286,12 @@ __global__ void k_face_scatter(Tables t, const T* __restrict__ fval, T* __restri
 //   lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^]     (zero flux at the x2 walls).
 // Also stores P^ for the correction.
 template <typename T>
-__global__ void k_poisson_rhs(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ P,
-                              const T* __restrict__ Po, const T* __restrict__ uss,
-                              const T* __restrict__ vss, T* __restrict__ rhs,
-                              T* __restrict__ phat) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void poisson_rhs_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                                 const T* __restrict__ P, const T* __restrict__ Po,
+                                                 const T* __restrict__ uss, const T* __restrict__ vss,
+                                                 T* __restrict__ rhs, T* __restrict__ phat, int i,
+                                                 int j) {
   const int nx = a.nx, ny = a.ny;
-  if (i >= nx || j >= ny) return;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const size_t r = (size_t)j * nx;
   auto ph = [&](size_t idx) { return T(2) * P[idx] - Po[idx]; };
@@ -339,66 +313,61 @@ __global__ void k_poisson_rhs(StepArgs<T> a, const T* __restrict__ C, const T* _
 // ------------------------------------------------- a8: correction + status and mass
 // Eq. correction, u^{n+1} = u** - dt [ (1/rho0) grad P^{n+1} + (1/rho_f - 1/rho0) grad P^ ],
 // written with the increment: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ].
-// Plus a non-finite check of C^{n+1} and u^{n+1} and the FP64 sum of C^{n+1}: block
-// partial sums in a fixed tree, the last block to finish adds the partials in index order.
+// Returns this cell's C^{n+1} (FP64, compensated part included) and flags non-finite values.
 template <typename T>
-__global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __restrict__ Clo,
-                          const T* __restrict__ dP,
-                          const T* __restrict__ phat, T* __restrict__ uss, T* __restrict__ vss,
-                          double* __restrict__ partial, unsigned* __restrict__ ticket,
-                          double* __restrict__ mass, int* __restrict__ status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int nx = a.nx, ny = a.ny;
+__device__ __forceinline__ double correct_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                               const T* __restrict__ Clo, const T* __restrict__ dP,
+                                               const T* __restrict__ phat, T* __restrict__ uss,
+                                               T* __restrict__ vss, int i, int j, int& bad) {
+  const int nx = a.nx;
+  const int im = wrap_m(i, nx);
+  const size_t r = (size_t)j * nx;
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  {
+    const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
+    const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
+                                      a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
+    uss[r + i] = un;
+    bad |= !isfinite((double)un);
+  }
+  if (j >= 1) {
+    const size_t rs = r - nx;
+    const T rho_f = rho(T(0.5) * (C[rs + i] + C[r + i]));
+    const T vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
+                                      a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
+    vss[r + i] = vn;
+    bad |= !isfinite((double)vn);
+  }
+  const double c = (double)C[r + i] + (Clo ? (double)Clo[r + i] : 0.0);
+  bad |= !isfinite(c);
+  return c;
+}
+
+// Block reduction of one tile's FP64 sum (fixed tree), partial written at the tile's
+// index; the last tile of an instance to finish adds the partials in index order.
+__device__ void tile_mass(double csum, int tile, int ntiles, double* __restrict__ partial,
+                          unsigned* __restrict__ ticket, double* __restrict__ mass) {
+  __shared__ double red[kTileX * kTileY];
+  __shared__ bool last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nthr = blockDim.x * blockDim.y;
-  double csum = 0.0;
-  int bad = 0;
-  if (i < nx && j < ny) {
-    const int im = wrap_m(i, nx);
-    const size_t r = (size_t)j * nx;
-    auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
-    {
-      const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
-      const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
-                                        a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
-      uss[r + i] = un;
-      bad |= !isfinite((double)un);
-    }
-    if (j >= 1) {
-      const size_t rs = r - nx;
-      const T rho_f = rho(T(0.5) * (C[rs + i] + C[r + i]));
-      const T vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
-                                        a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
-      vss[r + i] = vn;
-      bad |= !isfinite((double)vn);
-    }
-    const double c = (double)C[r + i] + (Clo ? (double)Clo[r + i] : 0.0);
-    bad |= !isfinite(c);
-    csum = c;
-  }
-  __shared__ double red[256];
   red[tid] = csum;
   __syncthreads();
   for (int s = nthr / 2; s > 0; s >>= 1) {
     if (tid < s) red[tid] += red[tid + s];
     __syncthreads();
   }
-  if (bad) atomicOr(status, 1);
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-  __shared__ bool last;
   if (tid == 0) {
-    partial[bid] = red[0];
+    partial[tile] = red[0];
     __threadfence();
-    last = (atomicAdd(ticket, 1u) == nblk - 1);
+    last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
   }
   __syncthreads();
   if (last) {
     __threadfence();
-    double s = 0.0;
-    for (unsigned b = tid; b < nblk; b += nthr) s += ((volatile double*)partial)[b];
-    red[tid] = s;
+    double sacc = 0.0;
+    for (int b = tid; b < ntiles; b += nthr) sacc += ((volatile double*)partial)[b];
+    red[tid] = sacc;
     __syncthreads();
     for (int q = nthr / 2; q > 0; q >>= 1) {
       if (tid < q) red[tid] += red[tid + q];
@@ -409,6 +378,7 @@ __global__ void k_correct(StepArgs<T> a, const T* __restrict__ C, const T* __res
       *ticket = 0u;
     }
   }
+  __syncthreads();
 }
 
 // stand-alone FP64 sum of a cell field (same reduction as in k_correct)
@@ -482,90 +452,285 @@ StepArgs<T> make_args(const Instance& in) {
   return a;
 }
 
+// ------------------------------------------------------------ batched launches
+// Each kernel walks the block table of its family: entry b = (instance, block within the
+// instance).  Cell families use 32 x 8 tiles; ghost and face families chunks of 128.
 template <typename T>
-int step_t(Instance& in, int cur, cudaStream_t s, Recorder* rec) {
-  const StepArgs<T> a = make_args<T>(in);
-  const int nx = in.nx, ny = in.ny;
-  const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
-  const int nw = cur, no = 1 - cur;   // level n and level n-1 slots
-  T* Cn = (T*)in.C[nw];
-  T* Co = (T*)in.C[no];
-  T* un = (T*)in.U[nw];
-  T* uo = (T*)in.U[no];
-  T* vn = (T*)in.V[nw];
-  T* vo = (T*)in.V[no];
-  T* Pn = (T*)in.P[nw];
-  T* Po = (T*)in.P[no];
-  const Tables& t = in.tab;
+__device__ __forceinline__ bool tile_cell(const InstDev<T>& d, int lb, int& i, int& j) {
+  i = (lb % d.gx) * kTileX + threadIdx.x;
+  j = (lb / d.gx) * kTileY + threadIdx.y;
+  return i < d.nx && j < d.ny;
+}
+
+template <typename T>
+__global__ void kb_ch_h(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                        int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j;
+    if (tile_cell(d, w_.y, i, j)) ch_h_cell(d.a, d.C[cur], d.C[1 - cur], d.phi, i, j);
+  }
+}
+
+template <typename T>
+__global__ void kb_ch_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                          int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j;
+    if (tile_cell(d, w_.y, i, j))
+      ch_rhs_cell(d.a, d.C[cur], d.C[1 - cur], d.U[cur], d.U[1 - cur], d.V[cur], d.V[1 - cur],
+                  d.phi, d.Q, i, j);
+  }
+}
+
+// C^{n+1} sits in slot 1 - cur after the CH solve
+template <typename T>
+__global__ void kb_fill_C(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                          int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    const int g = w_.y * kGhostChunk + threadIdx.x;
+    if (g < d.tab.ng) fill_C_ghost(d.a, d.tab, d.C[1 - cur], d.Clo[1 - cur], g);
+  }
+}
+
+template <typename T>
+__global__ void kb_chem_pot(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                            int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j;
+    if (tile_cell(d, w_.y, i, j)) chem_pot_cell(d.a, d.C[1 - cur], d.phi, i, j);
+  }
+}
+
+template <typename T>
+__global__ void kb_fill_phi(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                            int nblk) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    const int g = w_.y * kGhostChunk + threadIdx.x;
+    if (g < d.tab.ng) fill_phi_ghost(d.tab, d.phi, g);
+  }
+}
+
+// u** goes into the u^{n-1} slot (1 - cur)
+template <typename T>
+__global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                           int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j;
+    if (tile_cell(d, w_.y, i, j))
+      predict_cell(d.a, d.C[1 - cur], d.phi, d.U[cur], d.V[cur], d.Hu, d.Hv, d.tab.alpha_u,
+                   d.tab.alpha_v, d.U[1 - cur], d.V[1 - cur], i, j);
+  }
+}
+
+template <typename T>
+__global__ void kb_fill_u(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                          int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    const int g = w_.y * kGhostChunk + threadIdx.x;
+    if (g < d.tab.ng) fill_u_ghost(d.a, d.tab, d.U[1 - cur], d.V[1 - cur], d.gu, d.gv, g);
+  }
+}
+
+template <typename T>
+__global__ void kb_face_values(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                               int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    const int f = w_.y * kGhostChunk + threadIdx.x;
+    face_value(d.a, d.tab, d.U[1 - cur], d.V[1 - cur], d.gu, d.gv, d.fval, f);
+  }
+}
+
+template <typename T>
+__global__ void kb_face_scatter(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                                int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    const int f = w_.y * kGhostChunk + threadIdx.x;
+    face_scatter(d.tab, d.fval, d.U[1 - cur], d.V[1 - cur], f);
+  }
+}
+
+template <typename T>
+__global__ void kb_poisson_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                               int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j;
+    if (tile_cell(d, w_.y, i, j))
+      poisson_rhs_cell(d.a, d.C[1 - cur], d.P[cur], d.P[1 - cur], d.U[1 - cur], d.V[1 - cur],
+                       d.rhs, d.phat, i, j);
+  }
+}
+
+template <typename T>
+__global__ void kb_correct(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                           int nblk, int cur) {
+  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+    const int2 w_ = blk[b_];
+    const InstDev<T>& d = I[w_.x];
+    int i, j, bad = 0;
+    double c = 0.0;
+    if (tile_cell(d, w_.y, i, j))
+      c = correct_cell(d.a, d.C[1 - cur], d.Clo[1 - cur], d.dp, d.phat, d.U[1 - cur],
+                       d.V[1 - cur], i, j, bad);
+    if (bad) atomicOr(d.status, 1);
+    const int ntiles = d.gx * ((d.ny + kTileY - 1) / kTileY);
+    tile_mass(c, w_.y, ntiles, d.partial, d.ticket, d.mass);
+  }
+}
+
+template <typename T>
+int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, Recorder* rec) {
+  const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
+  const dim3 tile(kTileX, kTileY);
+  const int nc = plan.nblk[kFamCell], ng = plan.nblk[kFamGhost], nf = plan.nblk[kFamFace];
+  const int2* bc = plan.d_blk[kFamCell];
+  const int2* bg = plan.d_blk[kFamGhost];
+  const int2* bf = plan.d_blk[kFamFace];
   int launches = 0;
-  // a1 + a2: C^{n+1} into the C^{n-1} slot (C^{n-1} is dead once the RHS and the
-  // predictor in the solve epilogue have read it); h goes through the phi buffer
-  const int prec = sizeof(T) == 8 ? IB_PF_FP64 : IB_PF_FP32;
-  k_ch_h<T><<<grd, blk, 0, s>>>(a, Cn, Co, (T*)in.phi);
-  if (rec) rec->mark("ch_h", s);
-  k_ch_rhs<T><<<grd, blk, 0, s>>>(a, Cn, Co, un, uo, vn, vo, (const T*)in.phi, (T*)in.Q);
-  if (rec) rec->mark("ch_rhs", s);
-  launches += 2;
-  EpiArgs epi_c;
-  epi_c.kind = 1;
-  epi_c.a = Cn;
-  epi_c.b = Co;
-  epi_c.a_lo = in.Clo[nw];
-  epi_c.b_lo = in.Clo[no];
-  epi_c.out_lo = in.Clo[no];
-  launches += spectral_solve(in, prec, in.Q, Co, 0, epi_c, s, rec);
-  T* C1 = Co;
-  // a3
-  if (t.ng > 0) {
-    k_fill_C<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, C1, (T*)in.Clo[no]);
-    if (rec) rec->mark("fill_C", s);
+  auto mark = [&](const char* n) {
     ++launches;
+    if (rec) rec->mark(n, s);
+  };
+  // a1 + a2: CH right-hand side, then the solve; C^{n+1} lands in slot 1 - cur
+  kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("ch_h");
+  kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("ch_rhs");
+  launches += spectral_solve_batch<T>(plan, 0, cur, s, rec);
+  // a3: contact-angle ghost fill
+  if (ng > 0) {
+    kb_fill_C<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
+    mark("fill_C");
   }
-  // a4
-  k_chem_pot<T><<<grd, blk, 0, s>>>(a, C1, (T*)in.phi);
-  if (rec) rec->mark("chem_pot", s);
-  ++launches;
-  if (t.ng > 0) {
-    k_fill_phi<T><<<(t.ng + 127) / 128, 128, 0, s>>>(t, (T*)in.phi);
-    if (rec) rec->mark("fill_phi", s);
-    ++launches;
+  // a4: chemical potential and its ghost fill
+  kb_chem_pot<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("chem_pot");
+  if (ng > 0) {
+    kb_fill_phi<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng);
+    mark("fill_phi");
   }
-  // a5: u** into the u^{n-1} slot
-  k_predict<T><<<grd, blk, 0, s>>>(a, C1, (const T*)in.phi, un, vn, (T*)in.Hu, (T*)in.Hv,
-                                   t.alpha_u, t.alpha_v, uo, vo);
-  if (rec) rec->mark("predict", s);
-  ++launches;
-  // a6
-  if (t.ng > 0) {
-    k_fill_u<T><<<(t.ng + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (T*)in.gu, (T*)in.gv);
-    if (rec) rec->mark("fill_u", s);
-    ++launches;
+  // a5: predictor + penalisation, u** into slot 1 - cur
+  kb_predict<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("predict");
+  // a6: velocity ghost fill and face re-interpolation
+  if (ng > 0) {
+    kb_fill_u<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
+    mark("fill_u");
   }
-  const int nf = t.nfu + t.nfv;
   if (nf > 0) {
-    k_face_values<T><<<(nf + 127) / 128, 128, 0, s>>>(a, t, uo, vo, (const T*)in.gu,
-                                                      (const T*)in.gv, (T*)in.fval);
-    if (rec) rec->mark("face_values", s);
-    k_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(t, (const T*)in.fval, uo, vo);
-    if (rec) rec->mark("face_scatter", s);
-    launches += 2;
+    kb_face_values<T><<<nf, kGhostChunk, 0, s>>>(I, bf, nf, cur);
+    mark("face_values");
+    kb_face_scatter<T><<<nf, kGhostChunk, 0, s>>>(I, bf, nf, cur);
+    mark("face_scatter");
   }
-  // a7: P^{n+1} = P^ + dP into the P^{n-1} slot (P^ is kept in phat, dP in dp)
-  k_poisson_rhs<T><<<grd, blk, 0, s>>>(a, C1, Pn, Po, uo, vo, (T*)in.rhs, (T*)in.phat);
-  if (rec) rec->mark("poisson_rhs", s);
-  ++launches;
-  EpiArgs epi_p;
-  epi_p.kind = 2;
-  epi_p.a = in.phat;
-  epi_p.delta = in.dp;
-  launches += spectral_solve(in, prec, in.rhs, Po, 1, epi_p, s, rec);
-  // a8
-  k_correct<T><<<grd, blk, 0, s>>>(a, C1, (const T*)in.Clo[no], (const T*)in.dp,
-                                   (const T*)in.phat, uo, vo, in.partial,
-                                   in.ticket, in.mass, in.status);
-  if (rec) rec->mark("correct", s);
-  ++launches;
+  // a7: Poisson right-hand side and solve, P^{n+1} into slot 1 - cur
+  kb_poisson_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("poisson_rhs");
+  launches += spectral_solve_batch<T>(plan, 1, cur, s, rec);
+  // a8: correction, status, mass
+  kb_correct<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  mark("correct");
+  (void)c;
   return launches;
+}
+
+template <typename T>
+cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
+  using C2 = typename C2T<T>::type;
+  const int n = (int)c.inst.size();
+  std::vector<InstDev<T>> host(n);
+  std::vector<int2> fam[kNumFam];
+  plan.max_nx = plan.max_ny = 0;
+  for (int k = 0; k < n; ++k) {
+    Instance& in = c.inst[k];
+    InstDev<T>& d = host[k];
+    d.nx = in.nx;
+    d.ny = in.ny;
+    d.lognx = in.lognx;
+    d.logny = in.logny;
+    d.gx = (in.nx + kTileX - 1) / kTileX;
+    d.a = make_args<T>(in);
+    for (int q = 0; q < 2; ++q) {
+      d.C[q] = (T*)in.C[q];
+      d.Clo[q] = (T*)in.Clo[q];
+      d.U[q] = (T*)in.U[q];
+      d.V[q] = (T*)in.V[q];
+      d.P[q] = (T*)in.P[q];
+    }
+    d.Hu = (T*)in.Hu;
+    d.Hv = (T*)in.Hv;
+    d.Q = (T*)in.Q;
+    d.phi = (T*)in.phi;
+    d.rhs = (T*)in.rhs;
+    d.phat = (T*)in.phat;
+    d.dp = (T*)in.dp;
+    d.spec = (C2*)in.spec;
+    d.gu = (T*)in.gu;
+    d.gv = (T*)in.gv;
+    d.fval = (T*)in.fval;
+    d.tab = in.tab;
+    d.lamx = in.lamx;
+    d.lamy = in.lamy;
+    d.twx = (const C2*)in.twx;
+    d.twy = (const C2*)in.twy;
+    d.wd = (const C2*)in.wdct;
+    d.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
+    d.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
+    d.partial = in.partial;
+    d.ticket = in.ticket;
+    d.mass = in.mass;
+    d.status = in.status;
+    const int ntiles = d.gx * ((in.ny + kTileY - 1) / kTileY);
+    for (int b = 0; b < ntiles; ++b) fam[kFamCell].push_back(make_int2(k, b));
+    for (int b = 0; b < in.ny / 2; ++b) fam[kFamRows].push_back(make_int2(k, b));
+    const int ncg = (in.nx / 2 + 1 + kColsKC - 1) / kColsKC;
+    for (int b = 0; b < ncg; ++b) fam[kFamCols].push_back(make_int2(k, b));
+    for (int b = 0; b < (in.tab.ng + kGhostChunk - 1) / kGhostChunk; ++b)
+      fam[kFamGhost].push_back(make_int2(k, b));
+    const int nf = in.tab.nfu + in.tab.nfv;
+    for (int b = 0; b < (nf + kGhostChunk - 1) / kGhostChunk; ++b)
+      fam[kFamFace].push_back(make_int2(k, b));
+    plan.max_nx = in.nx > plan.max_nx ? in.nx : plan.max_nx;
+    plan.max_ny = in.ny > plan.max_ny ? in.ny : plan.max_ny;
+  }
+  cudaError_t e = cudaMalloc(&plan.d_inst, sizeof(InstDev<T>) * n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(plan.d_inst, host.data(), sizeof(InstDev<T>) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  for (int f = 0; f < kNumFam; ++f) {
+    plan.nblk[f] = (int)fam[f].size();
+    e = cudaMalloc((void**)&plan.d_blk[f], sizeof(int2) * (fam[f].empty() ? 1 : fam[f].size()));
+    if (e != cudaSuccess) return e;
+    if (!fam[f].empty()) {
+      e = cudaMemcpy(plan.d_blk[f], fam[f].data(), sizeof(int2) * fam[f].size(),
+                     cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  plan.rows_threads = plan.max_nx / 2 < 512 ? plan.max_nx / 2 : 512;
+  plan.cols_threads = kColsKC * (plan.max_ny / 2 < 256 ? plan.max_ny / 2 : 256);
+  plan.rows_smem = sizeof(C2) * plan.max_nx;
+  plan.cols_smem = sizeof(C2) * plan.max_ny * kColsKC;
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -579,8 +744,20 @@ int mass_t(Instance& in, const void* C, const void* Clo, cudaStream_t s) {
 
 }  // namespace
 
-int step_instance(Instance& in, int precision, int cur, cudaStream_t s, Recorder* rec) {
-  return precision == IB_PF_FP64 ? step_t<double>(in, cur, s, rec) : step_t<float>(in, cur, s, rec);
+cudaError_t batch_setup(Ctx& c, BatchPlan& plan) {
+  return c.precision == IB_PF_FP64 ? batch_setup_t<double>(c, plan) : batch_setup_t<float>(c, plan);
+}
+
+void batch_free(BatchPlan& plan) {
+  if (plan.d_inst) cudaFree(plan.d_inst);
+  for (int f = 0; f < kNumFam; ++f)
+    if (plan.d_blk[f]) cudaFree(plan.d_blk[f]);
+  plan = BatchPlan();
+}
+
+int step_batch(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, Recorder* rec) {
+  return c.precision == IB_PF_FP64 ? step_batch_t<double>(c, plan, cur, s, rec)
+                                   : step_batch_t<float>(c, plan, cur, s, rec);
 }
 
 int mass_reduce(Instance& in, int precision, const void* C, const void* Clo, cudaStream_t s) {
