@@ -42,10 +42,11 @@ L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per cell of one launch, in field words (8 B FP64 / 4 B FP32) plus the
 # FP64 geometry words (alpha) each kernel must read; see the design doc for the derivation.
 KERNEL_WORDS = {          # name: (field words per cell, fp64 words per cell)
-    "ch_rhs": (7.0, 0.0),        # C, Co, u, uo, v, vo -> Q
+    "ch_h": (3.0, 0.0),          # C, Co -> h
+    "ch_rhs": (8.0, 0.0),        # C, Co, u, uo, v, vo, h -> R
     "rows_fwd": (2.0, 0.0),      # real row in, half spectrum (complex) out
     "cols_solve": (2.0, 0.0),    # spectrum in and out
-    "rows_inv": (2.0, 0.0),      # half spectrum in, real row out
+    "rows_inv": (4.0, 0.0),      # half spectrum in; P^ in, dP and P out (pressure solve)
     "chem_pot": (2.0, 0.0),      # C -> phi
     "predict": (10.0, 2.0),      # C, phi, u, v, Hu, Hv -> Hu, Hv, u**, v**; alpha_u, alpha_v
     "poisson_rhs": (7.0, 0.0),   # C, P, Po, u**, v** -> rhs, P^
@@ -64,7 +65,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--precision", choices=("both", "fp64", "fp32"), default="both",
+                    help="both: FP32 form is the headline, plain FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
@@ -75,6 +77,21 @@ def parse_args():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (the only collective of the bench: the
+    instances of every rank are independent problems)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def aggregate_rate(world: int, cells_per_rank: int, steps: int, max_seconds: float) -> float:
+    """Whole-job Mcell-steps/s: every rank advances its own copy of the workload."""
+    return world * cells_per_rank * steps / max_seconds / 1e6
 
 
 # ----------------------------------------------------------------- CPU oracle timings
@@ -220,6 +237,20 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flops x GHz
+
+
+def kernel_flops64(name: str, nx: int, ny: int) -> float:
+    """Algorithmic FP64 flops per cell of one launch (counted from the discrete formulas,
+    each shared corner / cell quantity once; a division counts as one flop)."""
+    import math
+    table = {"predict": 99.0, "ch_h": 25.0, "ch_rhs": 30.0, "chem_pot": 9.0,
+             "poisson_rhs": 40.0, "correct": 30.0,
+             "rows_fwd": 2.5 * math.log2(nx) + 4.0, "rows_inv": 2.5 * math.log2(nx) + 4.0,
+             "cols_solve": 5.0 * math.log2(ny) + 16.0}
+    return table.get(name, 0.0)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -238,23 +269,29 @@ def run_ours(args):
     from paper_2104_00350_gb300 import ibpf
     from workloads import cases as W
 
-    prec = ibpf.FP64 if args.precision == "fp64" else ibpf.FP32
-    esz = 8 if prec == ibpf.FP64 else 4
     cl = workload_cases()
-    stream = torch.cuda.current_stream()
-    solver = ibpf.solver_from_cases(cl, prec, stream=stream.cuda_stream)
-    solver.precompute_weights()
     init = [W.initial_state(c) for c in cl]
-    for k in range(len(cl)):
-        solver.write_state(init[k], k)
     cells = sum(c.cells for c in cl)
+    stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = measured_peak()
+    forms = ("fp32", "fp64") if args.precision == "both" else (args.precision,)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
+    sampler = ClockSampler(gpu_idx)
+    sampler.start()
 
-    def timed_steps(n, collect_kernels=False):
+    def restart(solver):
+        # every timed pass starts from t = 0 (one of the six runs becomes non-finite near
+        # step 4600)
+        for k in range(len(cl)):
+            solver.write_state(init[k], k)
+        torch.cuda.synchronize()
+
+    def timed_steps(solver, n, collect_kernels=False):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(n)]
-        ktot = {}
-        kcount = {}
+        ktot, kcount = {}, {}
         for i in range(n):
             flush.zero_()
             evs[i][0].record(stream)
@@ -268,112 +305,131 @@ def run_ours(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs), ktot, kcount
 
-    # warm-up: untimed steps, then keep the GPU busy ~1 s so clocks settle
-    for _ in range(args.warmup):
-        flush.zero_()
-        solver.step(1)
-    torch.cuda.synchronize()
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
-    sampler = ClockSampler(gpu_idx)
-    sampler.start()
-    t_soak = time.time()
-    while time.time() - t_soak < args.soak_seconds:
-        solver.step(20)
+    results = {}
+    for form in forms:
+        prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+        esz = 8 if prec == ibpf.FP64 else 4
+        solver = ibpf.solver_from_cases(cl, prec, stream=stream.cuda_stream)
+        solver.precompute_weights()
+        restart(solver)
+        for _ in range(args.warmup):
+            flush.zero_()
+            solver.step(1)
+        # keep the GPU busy so that clocks settle, in chunks that stay far from step 4600
+        t_soak = time.time()
+        while time.time() - t_soak < args.soak_seconds:
+            restart(solver)
+            for _ in range(10):
+                solver.step(100)
+            torch.cuda.synchronize()
+        restart(solver)
+        for _ in range(args.warmup):
+            flush.zero_()
+            solver.step(1)
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    total_ms, _, _ = timed_steps(args.steps)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    launches = int(solver.query(ibpf.Q_LAUNCHES))
+        total_ms, _, _ = timed_steps(solver, args.steps)
+        if dist:
+            dist.barrier()
+        launches = int(solver.query(ibpf.Q_LAUNCHES))
+        max_ms = max_over_ranks([total_ms], dist, "cuda")[0]
+        value = aggregate_rate(world, cells, args.steps, max_ms * 1e-3)
 
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * cells * args.steps / (max_ms * 1e-3) / 1e6
-
-    # kernel-timing pass over the same number of steps (event-instrumented graphs)
-    peak, peak_kind = measured_peak()
-    try:
-        ibpf.ib_pf_set_kernel_timing(solver.ctx, True)
-        solver.step(1)
-        torch.cuda.synchronize()
-        _, ktot, kcount = timed_steps(args.steps, collect_kernels=True)
-        ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
-        dom = max(ktot, key=ktot.get)
-        per_launch_ms = ktot[dom] / kcount[dom]
-        fw, gw = KERNEL_WORDS.get(dom, (0.0, 0.0))
-        alg_bytes = (fw * esz + gw * 8) * cl[0].cells
-        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-        tot = sum(ktot.values())
-        share = {k: round(v / tot, 4) for k, v in sorted(ktot.items(), key=lambda x: -x[1])}
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": read_traffic(dom, args.precision),
-                    "alg_bytes_per_launch": alg_bytes, "per_launch_us": per_launch_ms * 1e3,
-                    "kernel_time_share": share}
-    except Exception as exc:   # keep the headline line even if the timing pass fails
-        roofline = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
+        # kernel-timing pass over the same number of steps (event-instrumented graphs)
+        try:
+            restart(solver)
+            ibpf.ib_pf_set_kernel_timing(solver.ctx, True)
+            solver.step(1)
+            torch.cuda.synchronize()
+            _, ktot, kcount = timed_steps(solver, args.steps, collect_kernels=True)
+            ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
+            dom = max(ktot, key=ktot.get)
+            per_launch_ms = ktot[dom] / kcount[dom]
+            tot = sum(ktot.values())
+            share = {k: round(v / tot, 4) for k, v in sorted(ktot.items(), key=lambda x: -x[1])}
+            launch_cells = cells   # one batched launch covers every instance
+            if prec == ibpf.FP32:
+                fw, gw = KERNEL_WORDS.get(dom, (0.0, 0.0))
+                alg = (fw * esz + gw * 8) * launch_cells
+                achieved = alg / (per_launch_ms * 1e-3) / 1e9
+                roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                        "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": read_traffic(dom, form), "alg_bytes_per_launch": alg}
+            else:
+                alg = kernel_flops64(dom, cl[0].nx, cl[0].ny) * launch_cells
+                achieved = alg / (per_launch_ms * 1e-3) / 1e9
+                roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
+                        "peak": FP64_PEAK_GFLOPS, "peak_kind": "derived (FP64 pipe)",
+                        "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
+                        "traffic": read_traffic(dom, form), "alg_flops_per_launch": alg}
+            roof.update({"per_launch_us": per_launch_ms * 1e3, "kernel_time_share": share})
+        except Exception as exc:   # keep the headline line even if the timing pass fails
+            roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                     "frac": None, "traffic": None, "error": str(exc)[:200]}
 
-    # end to end through the C ABI with host buffers
-    pinned = []
-    h2d = 0
-    for k in range(len(cl)):
-        d = {}
-        for name in ibpf.STATE_FIELDS:
-            a = torch.from_numpy(np.ascontiguousarray(init[k][name], dtype=np.float64 if esz == 8 else np.float32))
-            d[name] = a.pin_memory()
-            h2d += d[name].numel() * esz
-        pinned.append(d)
-    outC = [torch.empty(cl[k].ny, cl[k].nx, dtype=torch.float64 if esz == 8 else torch.float32).pin_memory()
-            for k in range(len(cl))]
-    d2h = sum(o.numel() * esz for o in outC)
-    e2e_steps = max(1, min(args.steps, 50))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        for k in range(len(cl)):
-            for name in ibpf.STATE_FIELDS:
-                solver.write(name, pinned[k][name], k)
-        solver.step(1)
-        for k in range(len(cl)):
-            solver.read("C", k, out=outC[k])
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * e2e_steps / float(te.item()) / 1e6
+        e2e = None
+        if form == forms[0]:
+            # end to end through the C ABI with host buffers: whole state in, C out
+            restart(solver)
+            dt_np = np.float64 if esz == 8 else np.float32
+            dt_t = torch.float64 if esz == 8 else torch.float32
+            pinned, h2d = [], 0
+            for k in range(len(cl)):
+                d = {}
+                for name in ibpf.STATE_FIELDS:
+                    d[name] = torch.from_numpy(np.ascontiguousarray(init[k][name], dtype=dt_np)).pin_memory()
+                    h2d += d[name].numel() * esz
+                pinned.append(d)
+            outC = [torch.empty(c.ny, c.nx, dtype=dt_t).pin_memory() for c in cl]
+            d2h = sum(o.numel() * esz for o in outC)
+            e2e_steps = max(1, min(args.steps, 50))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                for k in range(len(cl)):
+                    for name in ibpf.STATE_FIELDS:
+                        solver.write(name, pinned[k][name], k)
+                solver.step(1)
+                for k in range(len(cl)):
+                    solver.read("C", k, out=outC[k])
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            e2e = {"value": aggregate_rate(world, cells, e2e_steps,
+                                           max_over_ranks([e2e_s], dist, "cuda")[0]),
+                   "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "steps": e2e_steps}
+        results[form] = {"value": value, "ms_per_step": max_ms / args.steps,
+                         "gpu_launches": launches * args.steps, "roofline": roof, "e2e": e2e,
+                         "dtype": "f64" if esz == 8 else "f32"}
+        solver.close()
+    clocks = sampler.stop()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, n, secs = oracle_rate(cl, args.cpu_sample_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} steps of one 512x256 instance (theta 45, l_s 0) in {secs:.1f} s"}
-    solver.close()
     if rank == 0:
+        head = results[forms[0]]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if esz == 8 else "f32", "data": "synthetic",
+            "dtype": head["dtype"], "data": "synthetic",
             "config": {"workload": "sinusoid_wall_512x256_x6", "grid": "512x256",
                        "instances": 6, "thetas_deg": list(THETAS), "slip_lengths": list(SLIPS),
-                       "precision": args.precision,
+                       "form": {"fp32": "FP32 fields and transforms, compensated C, FP64 "
+                                        "geometry/weights/mass (meets C<=1e-5, u<=1e-4, 0.1 deg)",
+                                "fp64": "plain FP64"}[forms[0]],
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
-            "gpu_launches": launches * args.steps,
-            "roofline": roofline,
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"],
+            "roofline": head["roofline"],
             "cpu_baseline": cpu,
+            "forms": {f: {k: v for k, v in r.items() if k != "e2e"} for f, r in results.items()},
         }
         print(json.dumps(line), flush=True)
     if dist:

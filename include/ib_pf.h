@@ -170,7 +170,8 @@ ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void*
 
 /* Copy src into state field `field_id` of `instance` (restart / initial condition).
  * Only the read/write ids above are accepted.  src_on_host as for ib_pf_read_fields.
- * Rows 0 and ny of v fields are forced to zero. */
+ * Rows 0 and ny of v fields are forced to zero.  Clears the instance's non-finite status
+ * and synchronises the stream. */
 ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
                                 long long nbytes, int src_on_host);
 

@@ -64,6 +64,8 @@ struct InstDev {
   Tables tab;
   const double* lamx;
   const double* lamy;
+  const float* lamx_f;
+  const float* lamy_f;
   const C2* twx;
   const C2* twy;
   const C2* wd;

@@ -66,7 +66,7 @@ void* field_ptr(Ctx& c, Instance& in, int id) {
 void free_instance(Instance& in) {
   void* ptrs[] = {in.C[0], in.C[1], in.Clo[0], in.Clo[1], in.U[0], in.U[1], in.V[0], in.V[1], in.P[0], in.P[1],
                   in.Hu, in.Hv, in.Q, in.phi, in.rhs, in.phat, in.dp, in.spec, in.gu, in.gv, in.fval,
-                  in.lamx, in.lamy, in.twx, in.twy, in.wdct, in.partial, in.ticket, in.mass,
+                  in.lamx, in.lamy, in.lamx_f, in.lamy_f, in.twx, in.twy, in.wdct, in.partial, in.ticket, in.mass,
                   in.status, in.tab.alpha_c, in.tab.alpha_u, in.tab.alpha_v, in.tab.solidc,
                   in.tab.cmap, in.tab.gcell, in.tab.nrm, in.tab.dn, in.tab.gamma, in.tab.ap1,
                   in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv};
@@ -371,7 +371,10 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
     CK(cudaMemsetAsync(dst, 0, row, ctx->work));
     CK(cudaMemsetAsync((char*)dst + (size_t)in.ny * row, 0, row, ctx->work));
   }
-  if (src_on_host) CK(cudaStreamSynchronize(ctx->work));
+  // new state: forget an earlier non-finite flag of this instance
+  CK(cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work));
+  CK(cudaStreamSynchronize(ctx->work));
+  ((volatile int*)ctx->h_status)[instance] = 0;
   CK(join_out(*ctx));
   return IB_PF_OK;
 }

@@ -76,6 +76,8 @@ struct Instance {
   // transform tables
   double* lamx = nullptr;  // nx/2+1 eigenvalues of the periodic second difference
   double* lamy = nullptr;  // ny eigenvalues of the Neumann second difference
+  float* lamx_f = nullptr; // the same eigenvalues rounded to FP32 (FP32 path symbol)
+  float* lamy_f = nullptr;
   void* twx = nullptr;     // nx/2 complex exp(-2 pi i k/nx), element type
   void* twy = nullptr;     // ny/2 complex exp(-2 pi i k/ny)
   void* wdct = nullptr;    // ny complex exp(-i pi m/(2 ny))

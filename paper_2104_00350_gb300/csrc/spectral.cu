@@ -213,7 +213,39 @@ struct SymbolArgs {
   double c0;         // 1.5 Pe / (Cn^2 dt)
   const double* lamx;
   const double* lamy;
+  const float* lamx_f;   // FP32 path: eigenvalues computed in FP64, rounded once
+  const float* lamy_f;
 };
+
+// Divide X_m by the symbol at (k, m).  FP64 path: in FP64.  FP32 path: in FP32 -- the
+// three terms of L^2 - (S/Cn^2) L + c0 (L <= 0) and the two of L are all of one sign, so
+// the FP32 evaluation has no cancellation and keeps FP32 relative accuracy (FP64 here
+// would occupy GB300's narrow FP64 pipe for most of the kernel).
+template <typename T, typename C2>
+__device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs& sym) {
+  if constexpr (sizeof(T) == 8) {
+    const double L = sym.lamy[m] + sym.lamx[k];
+    if (sym.mode == 0) {
+      const double sg = L * L - sym.s_eta2 * L + sym.c0;
+      X.x = (T)((double)X.x / sg);
+      X.y = (T)((double)X.y / sg);
+    } else if (L == 0.0) {
+      X.x = T(0);
+      X.y = T(0);
+    } else {
+      X.x = (T)((double)X.x / L);
+      X.y = (T)((double)X.y / L);
+    }
+  } else {
+    const float L = sym.lamy_f[m] + sym.lamx_f[k];
+    float r;
+    if (sym.mode == 0) r = 1.0f / (L * L - (float)sym.s_eta2 * L + (float)sym.c0);
+    else r = (L == 0.0f) ? 0.0f : 1.0f / L;
+    X.x = X.x * r;
+    X.y = X.y * r;
+  }
+  return X;
+}
 
 // x2 cosine transform, symbol division and inverse cosine transform of KC spectral
 // columns per block (complex data; the transform is real so it acts on Re and Im alike).
@@ -247,7 +279,6 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
   C2* x = xs + c * N;
   fft_dit(x, logny, tw, lt, tpc);
   const int k = min(k0 + c, nh1 - 1);
-  const double lx = sym.lamx[k];
   for (int m = lt; m <= (N >> 1); m += tpc) {
     const int mm = (N - m) & (N - 1);
     C2 Vm = x[m], Vmm = x[mm];
@@ -270,32 +301,8 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
       Xmm.x = w.x * vr.x - w.y * vr.y;
       Xmm.y = w.x * vi.x - w.y * vi.y;
     }
-    // symbol (FP64 eigenvalues and denominators)
-    double Lm = sym.lamy[m] + lx, Lmm = sym.lamy[mm] + lx;
-    double sm, smm;
-    if (sym.mode == 0) {
-      sm = Lm * Lm - sym.s_eta2 * Lm + sym.c0;
-      smm = Lmm * Lmm - sym.s_eta2 * Lmm + sym.c0;
-      Xm.x = (T)((double)Xm.x / sm);
-      Xm.y = (T)((double)Xm.y / sm);
-      Xmm.x = (T)((double)Xmm.x / smm);
-      Xmm.y = (T)((double)Xmm.y / smm);
-    } else {
-      if (Lm == 0.0) {
-        Xm.x = T(0);
-        Xm.y = T(0);
-      } else {
-        Xm.x = (T)((double)Xm.x / Lm);
-        Xm.y = (T)((double)Xm.y / Lm);
-      }
-      if (Lmm == 0.0) {
-        Xmm.x = T(0);
-        Xmm.y = T(0);
-      } else {
-        Xmm.x = (T)((double)Xmm.x / Lmm);
-        Xmm.y = (T)((double)Xmm.y / Lmm);
-      }
-    }
+    Xm = divide_symbol<T>(Xm, k, m, sym);
+    Xmm = divide_symbol<T>(Xmm, k, mm, sym);
     // inverse pre-processing: Z_m = conj(w_m) (X_m - i X_{N-m})
     C2 Zm, Zmm;
     {
@@ -367,6 +374,8 @@ __global__ void kb_cols(const InstDev<T>* __restrict__ I, const int2* __restrict
     sym.c0 = d.c0;
     sym.lamx = d.lamx;
     sym.lamy = d.lamy;
+    sym.lamx_f = d.lamx_f;
+    sym.lamy_f = d.lamy_f;
     cols_core<T, kColsKC>(d.spec, d.nx / 2 + 1, d.logny, d.twy, d.wd, sym, w.y * kColsKC,
                           reinterpret_cast<C2*>(smem_raw));
   }
@@ -434,6 +443,11 @@ cudaError_t tables_t(Instance& in) {
   cudaError_t e;
   if ((e = cudaMalloc((void**)&in.lamx, sizeof(double) * lx.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc((void**)&in.lamy, sizeof(double) * ly.size())) != cudaSuccess) return e;
+  std::vector<float> lxf(lx.begin(), lx.end()), lyf(ly.begin(), ly.end());
+  if ((e = cudaMalloc((void**)&in.lamx_f, sizeof(float) * lxf.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc((void**)&in.lamy_f, sizeof(float) * lyf.size())) != cudaSuccess) return e;
+  cudaMemcpy(in.lamx_f, lxf.data(), sizeof(float) * lxf.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(in.lamy_f, lyf.data(), sizeof(float) * lyf.size(), cudaMemcpyHostToDevice);
   if ((e = cudaMalloc(&in.twx, sizeof(C2) * twx.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&in.twy, sizeof(C2) * twy.size())) != cudaSuccess) return e;
   if ((e = cudaMalloc(&in.wdct, sizeof(C2) * wd.size())) != cudaSuccess) return e;

@@ -131,74 +131,96 @@ __device__ __forceinline__ void fill_phi_ghost(const Tables& t, T* __restrict__ 
 // H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho_f)
 // u* = u^n + dt (3/2 H^n - 1/2 H^{n-1} + (kappa/(Re Ca Cn)) phi_f dC/dx / rho_f)
 // u** = alpha_f u*                                (Eqs. PredictionExp, Penalization2)
-// Thread (i, j) updates x1-face (i, j) and, for j >= 1, x2-face (i, j).  H is updated in
-// place (read H^{n-1}, write H^n at the same face).
+// One 32 x 8 tile per block: C, u, v and phi are staged in shared memory with a one-cell
+// halo (periodic in x1; mirror rows of C and phi and no-slip ghost rows -u at the x2
+// walls), then thread (i, j) updates x1-face (i, j) and, for j >= 1, x2-face (i, j).
+// H is updated in place (read H^{n-1}, write H^n at the same face).
+constexpr int kHx = kTileX + 2, kHy = kTileY + 2;   // staged tile with halo
+
 template <typename T>
-__device__ __forceinline__ void predict_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                             const T* __restrict__ phi, const T* __restrict__ u,
-                                             const T* __restrict__ v, T* __restrict__ Hu,
-                                             T* __restrict__ Hv, const double* __restrict__ alpha_u,
-                                             const double* __restrict__ alpha_v, T* __restrict__ uss,
-                                             T* __restrict__ vss, int i, int j) {
+struct PredictSmem {
+  T C[kHy][kHx];
+  T U[kHy][kHx];
+  T V[kHy][kHx];
+  T F[kHy][kHx];   // phi
+};
+
+template <typename T>
+__device__ __forceinline__ void predict_stage(const StepArgs<T>& a, const T* __restrict__ C,
+                                              const T* __restrict__ phi, const T* __restrict__ u,
+                                              const T* __restrict__ v, int i0, int j0,
+                                              PredictSmem<T>& sm) {
   const int nx = a.nx, ny = a.ny;
-  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int idx = tid; idx < kHx * kHy; idx += blockDim.x * blockDim.y) {
+    const int r = idx / kHx, c = idx % kHx;
+    const int gj = j0 - 1 + r;
+    int gi = (i0 - 1 + c) % nx;
+    if (gi < 0) gi += nx;
+    const int cj = gj < 0 ? 0 : (gj >= ny ? ny - 1 : gj);
+    sm.C[r][c] = C[(size_t)cj * nx + gi];
+    sm.F[r][c] = phi[(size_t)cj * nx + gi];
+    const T uu = u[(size_t)cj * nx + gi];
+    sm.U[r][c] = (gj < 0 || gj >= ny) ? -uu : uu;
+    sm.V[r][c] = (gj >= 0 && gj <= ny) ? v[(size_t)gj * nx + gi] : T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void predict_point(const StepArgs<T>& a, const PredictSmem<T>& sm,
+                                              int i, int j, T* __restrict__ Hu,
+                                              T* __restrict__ Hv, const double* __restrict__ alpha_u,
+                                              const double* __restrict__ alpha_v,
+                                              T* __restrict__ uss, T* __restrict__ vss) {
+  const int nx = a.nx;
+  const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;   // this cell in the staged tile
   const size_t r = (size_t)j * nx;
-  auto cell = [&](const T* f, int ii, int jj) -> T {   // mirror rows beyond the walls
-    jj = jj < 0 ? 0 : (jj >= ny ? ny - 1 : jj);
-    return f[(size_t)jj * nx + ii];
-  };
-  auto uext = [&](int ii, int jj) -> T {                 // no-slip ghost rows
-    if (jj < 0) return -u[ii];
-    if (jj >= ny) return -u[(size_t)(ny - 1) * nx + ii];
-    return u[(size_t)jj * nx + ii];
-  };
+  auto Cs = [&](int di, int dj) { return sm.C[ty + dj][tx + di]; };
+  auto Us = [&](int di, int dj) { return sm.U[ty + dj][tx + di]; };
+  auto Vs = [&](int di, int dj) { return sm.V[ty + dj][tx + di]; };
+  auto Fs = [&](int di, int dj) { return sm.F[ty + dj][tx + di]; };
   auto mu = [&](T c) { return a.mu_a + a.mu_b * c; };
   auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
-  // corner (ii, jc) at (ii h, jc h), jc in [0, ny]
-  auto tau_xy = [&](int ii, int jc) -> T {
-    const int iw = wrap_m(ii, nx);
-    const T ce = T(0.25) * (((cell(C, iw, jc - 1) + cell(C, ii, jc - 1)) + cell(C, iw, jc)) +
-                            cell(C, ii, jc));
-    const T dudy = (uext(ii, jc) - uext(ii, jc - 1)) * a.inv_h;
-    const T dvdx = (v[(size_t)jc * nx + ii] - v[(size_t)jc * nx + iw]) * a.inv_h;
+  // corner at (i + di, j + dj) in corner indices (x = (i+di) h, y = (j+dj) h)
+  auto tau_xy = [&](int di, int dj) -> T {
+    const T ce = T(0.25) * (((Cs(di - 1, dj - 1) + Cs(di, dj - 1)) + Cs(di - 1, dj)) + Cs(di, dj));
+    const T dudy = (Us(di, dj) - Us(di, dj - 1)) * a.inv_h;
+    const T dvdx = (Vs(di, dj) - Vs(di - 1, dj)) * a.inv_h;
     return mu(ce) * (dudy + dvdx);
   };
-  auto uv = [&](int ii, int jc) -> T {
-    const int iw = wrap_m(ii, nx);
-    return (T(0.5) * (uext(ii, jc) + uext(ii, jc - 1))) *
-           (T(0.5) * (v[(size_t)jc * nx + ii] + v[(size_t)jc * nx + iw]));
+  auto uv = [&](int di, int dj) -> T {
+    return (T(0.5) * (Us(di, dj) + Us(di, dj - 1))) * (T(0.5) * (Vs(di, dj) + Vs(di - 1, dj)));
   };
   const T k_st = a.k_st;
-  // ---- x1-face (i, j): cells (im, j) and (i, j)
+  // ---- x1-face (i, j): cells (i-1, j) and (i, j)
   {
-    const T cL = C[r + im], cR = C[r + i];
+    const T cL = Cs(-1, 0), cR = Cs(0, 0);
     const T rho_f = rho(T(0.5) * (cL + cR));
-    const T txx_R = T(2) * mu(cR) * ((u[r + ip] - u[r + i]) * a.inv_h);
-    const T txx_L = T(2) * mu(cL) * ((u[r + i] - u[r + im]) * a.inv_h);
-    const T visc = (txx_R - txx_L) * a.inv_h + (tau_xy(i, j + 1) - tau_xy(i, j)) * a.inv_h;
-    const T ucR = T(0.5) * (u[r + i] + u[r + ip]);
-    const T ucL = T(0.5) * (u[r + im] + u[r + i]);
-    const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(i, j + 1) - uv(i, j)) * a.inv_h;
+    const T txx_R = T(2) * mu(cR) * ((Us(1, 0) - Us(0, 0)) * a.inv_h);
+    const T txx_L = T(2) * mu(cL) * ((Us(0, 0) - Us(-1, 0)) * a.inv_h);
+    const T visc = (txx_R - txx_L) * a.inv_h + (tau_xy(0, 1) - tau_xy(0, 0)) * a.inv_h;
+    const T ucR = T(0.5) * (Us(0, 0) + Us(1, 0));
+    const T ucL = T(0.5) * (Us(-1, 0) + Us(0, 0));
+    const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(0, 1) - uv(0, 0)) * a.inv_h;
     const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (phi[r + i] + phi[r + im])) * ((cR - cL) * a.inv_h) / rho_f;
-    const T ustar = u[r + i] + a.dt * ((T(1.5) * H - T(0.5) * Hu[r + i]) + st);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * ((cR - cL) * a.inv_h) / rho_f;
+    const T ustar = Us(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * Hu[r + i]) + st);
     Hu[r + i] = H;
     uss[r + i] = (T)alpha_u[r + i] * ustar;
   }
   // ---- x2-face (i, j), 1 <= j <= ny-1: cells (i, j-1) and (i, j)
   if (j >= 1) {
-    const size_t rs = r - nx;
-    const T cB = C[rs + i], cA = C[r + i];
+    const T cB = Cs(0, -1), cA = Cs(0, 0);
     const T rho_f = rho(T(0.5) * (cB + cA));
-    const T tyy_A = T(2) * mu(cA) * ((v[r + nx + i] - v[r + i]) * a.inv_h);
-    const T tyy_B = T(2) * mu(cB) * ((v[r + i] - v[rs + i]) * a.inv_h);
-    const T visc = (tau_xy(ip, j) - tau_xy(i, j)) * a.inv_h + (tyy_A - tyy_B) * a.inv_h;
-    const T vcA = T(0.5) * (v[r + i] + v[r + nx + i]);
-    const T vcB = T(0.5) * (v[rs + i] + v[r + i]);
-    const T conv = (uv(ip, j) - uv(i, j)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
+    const T tyy_A = T(2) * mu(cA) * ((Vs(0, 1) - Vs(0, 0)) * a.inv_h);
+    const T tyy_B = T(2) * mu(cB) * ((Vs(0, 0) - Vs(0, -1)) * a.inv_h);
+    const T visc = (tau_xy(1, 0) - tau_xy(0, 0)) * a.inv_h + (tyy_A - tyy_B) * a.inv_h;
+    const T vcA = T(0.5) * (Vs(0, 0) + Vs(0, 1));
+    const T vcB = T(0.5) * (Vs(0, -1) + Vs(0, 0));
+    const T conv = (uv(1, 0) - uv(0, 0)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
     const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (phi[r + i] + phi[rs + i])) * ((cA - cB) * a.inv_h) / rho_f;
-    const T vstar = v[r + i] + a.dt * ((T(1.5) * H - T(0.5) * Hv[r + i]) + st);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * ((cA - cB) * a.inv_h) / rho_f;
+    const T vstar = Vs(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * Hv[r + i]) + st);
     Hv[r + i] = H;
     vss[r + i] = (T)alpha_v[r + i] * vstar;
   }
@@ -524,13 +546,18 @@ __global__ void kb_fill_phi(const InstDev<T>* __restrict__ I, const int2* __rest
 template <typename T>
 __global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                            int nblk, int cur) {
+  __shared__ PredictSmem<T> sm;
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j;
-    if (tile_cell(d, w_.y, i, j))
-      predict_cell(d.a, d.C[1 - cur], d.phi, d.U[cur], d.V[cur], d.Hu, d.Hv, d.tab.alpha_u,
-                   d.tab.alpha_v, d.U[1 - cur], d.V[1 - cur], i, j);
+    const int i0 = (w_.y % d.gx) * kTileX, j0 = (w_.y / d.gx) * kTileY;
+    predict_stage(d.a, d.C[1 - cur], d.phi, d.U[cur], d.V[cur], i0, j0, sm);
+    __syncthreads();
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i < d.nx && j < d.ny)
+      predict_point(d.a, sm, i, j, d.Hu, d.Hv, d.tab.alpha_u, d.tab.alpha_v, d.U[1 - cur],
+                    d.V[1 - cur]);
+    __syncthreads();
   }
 }
 
@@ -690,6 +717,8 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.tab = in.tab;
     d.lamx = in.lamx;
     d.lamy = in.lamy;
+    d.lamx_f = in.lamx_f;
+    d.lamy_f = in.lamy_f;
     d.twx = (const C2*)in.twx;
     d.twy = (const C2*)in.twy;
     d.wd = (const C2*)in.wdct;
