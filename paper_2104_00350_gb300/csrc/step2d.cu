@@ -135,7 +135,7 @@ __device__ __forceinline__ void fill_phi_ghost(const Tables& t, T* __restrict__ 
 // halo (periodic in x1; mirror rows of C and phi and no-slip ghost rows -u at the x2
 // walls), then thread (i, j) updates x1-face (i, j) and, for j >= 1, x2-face (i, j).
 // H is updated in place (read H^{n-1}, write H^n at the same face).
-constexpr int kHx = kTileX + 2, kHy = kTileY + 2;   // staged tile with halo
+constexpr int kHx = kTileX + 2, kHy = kTileH + 2;   // staged tile with halo
 
 template <typename T>
 struct PredictSmem {
@@ -166,14 +166,15 @@ __device__ __forceinline__ void predict_stage(const StepArgs<T>& a, const T* __r
   }
 }
 
+// (lx, ly): this cell in the staged tile; hu_old, hv_old, au, av prefetched by the caller
 template <typename T>
 __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const PredictSmem<T>& sm,
-                                              int i, int j, T* __restrict__ Hu,
-                                              T* __restrict__ Hv, const double* __restrict__ alpha_u,
-                                              const double* __restrict__ alpha_v,
-                                              T* __restrict__ uss, T* __restrict__ vss) {
+                                              int i, int j, int lx, int ly, T hu_old, T hv_old,
+                                              double au, double av, T* __restrict__ Hu,
+                                              T* __restrict__ Hv, T* __restrict__ uss,
+                                              T* __restrict__ vss) {
   const int nx = a.nx;
-  const int tx = threadIdx.x + 1, ty = threadIdx.y + 1;   // this cell in the staged tile
+  const int tx = lx + 1, ty = ly + 1;
   const size_t r = (size_t)j * nx;
   auto Cs = [&](int di, int dj) { return sm.C[ty + dj][tx + di]; };
   auto Us = [&](int di, int dj) { return sm.U[ty + dj][tx + di]; };
@@ -204,9 +205,9 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(0, 1) - uv(0, 0)) * a.inv_h;
     const T H = -conv + visc / (a.Re * rho_f);
     const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * ((cR - cL) * a.inv_h) / rho_f;
-    const T ustar = Us(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * Hu[r + i]) + st);
+    const T ustar = Us(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hu_old) + st);
     Hu[r + i] = H;
-    uss[r + i] = (T)alpha_u[r + i] * ustar;
+    uss[r + i] = (T)au * ustar;
   }
   // ---- x2-face (i, j), 1 <= j <= ny-1: cells (i, j-1) and (i, j)
   if (j >= 1) {
@@ -220,9 +221,9 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T conv = (uv(1, 0) - uv(0, 0)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
     const T H = -conv + visc / (a.Re * rho_f);
     const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * ((cA - cB) * a.inv_h) / rho_f;
-    const T vstar = Vs(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * Hv[r + i]) + st);
+    const T vstar = Vs(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hv_old) + st);
     Hv[r + i] = H;
-    vss[r + i] = (T)alpha_v[r + i] * vstar;
+    vss[r + i] = (T)av * vstar;
   }
 }
 
@@ -337,10 +338,10 @@ __device__ __forceinline__ void poisson_rhs_cell(const StepArgs<T>& a, const T* 
 // written with the increment: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ].
 // Returns this cell's C^{n+1} (FP64, compensated part included) and flags non-finite values.
 template <typename T>
-__device__ __forceinline__ double correct_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                               const T* __restrict__ Clo, const T* __restrict__ dP,
-                                               const T* __restrict__ phat, T* __restrict__ uss,
-                                               T* __restrict__ vss, int i, int j, int& bad) {
+__device__ __forceinline__ void correct_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                             const T* __restrict__ dP, const T* __restrict__ phat,
+                                             T* __restrict__ uss, T* __restrict__ vss, int i, int j,
+                                             int& bad) {
   const int nx = a.nx;
   const int im = wrap_m(i, nx);
   const size_t r = (size_t)j * nx;
@@ -350,7 +351,7 @@ __device__ __forceinline__ double correct_cell(const StepArgs<T>& a, const T* __
     const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
                                       a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
     uss[r + i] = un;
-    bad |= !isfinite((double)un);
+    bad |= !isfinite(un);
   }
   if (j >= 1) {
     const size_t rs = r - nx;
@@ -358,29 +359,53 @@ __device__ __forceinline__ double correct_cell(const StepArgs<T>& a, const T* __
     const T vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
                                       a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
     vss[r + i] = vn;
-    bad |= !isfinite((double)vn);
+    bad |= !isfinite(vn);
   }
-  const double c = (double)C[r + i] + (Clo ? (double)Clo[r + i] : 0.0);
-  bad |= !isfinite(c);
-  return c;
+  bad |= !isfinite(C[r + i]);
 }
 
-// Block reduction of one tile's FP64 sum (fixed tree), partial written at the tile's
-// index; the last tile of an instance to finish adds the partials in index order.
-__device__ void tile_mass(double csum, int tile, int ntiles, double* __restrict__ partial,
+// (hi, lo) += (b_hi, b_lo) without rounding loss in FP32 (TwoSum, then renormalise); plain
+// addition in FP64.
+template <typename T>
+__device__ __forceinline__ void pair_add(T& hi, T& lo, T b_hi, T b_lo) {
+  if constexpr (sizeof(T) == 8) {
+    hi = hi + (b_hi + b_lo);
+  } else {
+    const T s = hi + b_hi;
+    const T bb = s - hi;
+    const T e = (hi - (s - bb)) + (b_hi - bb);
+    const T l = (lo + b_lo) + e;
+    hi = s + l;
+    lo = l - (hi - s);
+  }
+}
+
+// Block reduction of one tile's sum of C in a fixed tree (FP64, or compensated FP32 pairs
+// in the FP32 form), written as FP64 at the tile's index; the last tile of an instance to
+// finish adds the partials in index order in FP64.
+template <typename T>
+__device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__ partial,
                           unsigned* __restrict__ ticket, double* __restrict__ mass) {
+  __shared__ T rh[kTileX * kTileY];
+  __shared__ T rl[kTileX * kTileY];
   __shared__ double red[kTileX * kTileY];
   __shared__ bool last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nthr = blockDim.x * blockDim.y;
-  red[tid] = csum;
+  rh[tid] = hi;
+  rl[tid] = lo;
   __syncthreads();
   for (int s = nthr / 2; s > 0; s >>= 1) {
-    if (tid < s) red[tid] += red[tid + s];
+    if (tid < s) {
+      T a_hi = rh[tid], a_lo = rl[tid];
+      pair_add(a_hi, a_lo, rh[tid + s], rl[tid + s]);
+      rh[tid] = a_hi;
+      rl[tid] = a_lo;
+    }
     __syncthreads();
   }
   if (tid == 0) {
-    partial[tile] = red[0];
+    partial[tile] = (double)rh[0] + (double)rl[0];
     __threadfence();
     last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
   }
@@ -476,12 +501,14 @@ StepArgs<T> make_args(const Instance& in) {
 
 // ------------------------------------------------------------ batched launches
 // Each kernel walks the block table of its family: entry b = (instance, block within the
-// instance).  Cell families use 32 x 8 tiles; ghost and face families chunks of 128.
+// instance).  Cell tiles are 32 x 32 cells (32 x 8 threads, 4 rows each); ghost and face
+// families use chunks of 128.
+
+// first cell of this thread in tile lb: column i, rows jb, jb + 8, jb + 16, jb + 24
 template <typename T>
-__device__ __forceinline__ bool tile_cell(const InstDev<T>& d, int lb, int& i, int& j) {
+__device__ __forceinline__ void tile_base(const InstDev<T>& d, int lb, int& i, int& jb) {
   i = (lb % d.gx) * kTileX + threadIdx.x;
-  j = (lb / d.gx) * kTileY + threadIdx.y;
-  return i < d.nx && j < d.ny;
+  jb = (lb / d.gx) * kTileH + threadIdx.y;
 }
 
 template <typename T>
@@ -490,8 +517,13 @@ __global__ void kb_ch_h(const InstDev<T>* __restrict__ I, const int2* __restrict
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j;
-    if (tile_cell(d, w_.y, i, j)) ch_h_cell(d.a, d.C[cur], d.C[1 - cur], d.phi, i, j);
+    int i, jb;
+    tile_base(d, w_.y, i, jb);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) ch_h_cell(d.a, d.C[cur], d.C[1 - cur], d.phi, i, j);
+    }
   }
 }
 
@@ -501,10 +533,15 @@ __global__ void kb_ch_rhs(const InstDev<T>* __restrict__ I, const int2* __restri
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j;
-    if (tile_cell(d, w_.y, i, j))
-      ch_rhs_cell(d.a, d.C[cur], d.C[1 - cur], d.U[cur], d.U[1 - cur], d.V[cur], d.V[1 - cur],
-                  d.phi, d.Q, i, j);
+    int i, jb;
+    tile_base(d, w_.y, i, jb);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny)
+        ch_rhs_cell(d.a, d.C[cur], d.C[1 - cur], d.U[cur], d.U[1 - cur], d.V[cur], d.V[1 - cur],
+                    d.phi, d.Q, i, j);
+    }
   }
 }
 
@@ -526,8 +563,13 @@ __global__ void kb_chem_pot(const InstDev<T>* __restrict__ I, const int2* __rest
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j;
-    if (tile_cell(d, w_.y, i, j)) chem_pot_cell(d.a, d.C[1 - cur], d.phi, i, j);
+    int i, jb;
+    tile_base(d, w_.y, i, jb);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) chem_pot_cell(d.a, d.C[1 - cur], d.phi, i, j);
+    }
   }
 }
 
@@ -550,13 +592,31 @@ __global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restr
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    const int i0 = (w_.y % d.gx) * kTileX, j0 = (w_.y / d.gx) * kTileY;
+    const int i0 = (w_.y % d.gx) * kTileX, j0 = (w_.y / d.gx) * kTileH;
+    const int i = i0 + threadIdx.x;
+    // own-face history and penalisation factors, fetched while the tile is staged
+    T huo[kRowsPerThread], hvo[kRowsPerThread];
+    double au[kRowsPerThread], av[kRowsPerThread];
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = j0 + threadIdx.y + q * kTileY;
+      const bool ok = i < d.nx && j < d.ny;
+      const size_t c = (size_t)j * d.nx + i;
+      huo[q] = ok ? d.Hu[c] : T(0);
+      hvo[q] = ok ? d.Hv[c] : T(0);
+      au[q] = ok ? d.tab.alpha_u[c] : 0.0;
+      av[q] = ok ? d.tab.alpha_v[c] : 0.0;
+    }
     predict_stage(d.a, d.C[1 - cur], d.phi, d.U[cur], d.V[cur], i0, j0, sm);
     __syncthreads();
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (i < d.nx && j < d.ny)
-      predict_point(d.a, sm, i, j, d.Hu, d.Hv, d.tab.alpha_u, d.tab.alpha_v, d.U[1 - cur],
-                    d.V[1 - cur]);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int ly = threadIdx.y + q * kTileY;
+      const int j = j0 + ly;
+      if (i < d.nx && j < d.ny)
+        predict_point(d.a, sm, i, j, threadIdx.x, ly, huo[q], hvo[q], au[q], av[q], d.Hu, d.Hv,
+                      d.U[1 - cur], d.V[1 - cur]);
+    }
     __syncthreads();
   }
 }
@@ -600,10 +660,15 @@ __global__ void kb_poisson_rhs(const InstDev<T>* __restrict__ I, const int2* __r
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j;
-    if (tile_cell(d, w_.y, i, j))
-      poisson_rhs_cell(d.a, d.C[1 - cur], d.P[cur], d.P[1 - cur], d.U[1 - cur], d.V[1 - cur],
-                       d.rhs, d.phat, i, j);
+    int i, jb;
+    tile_base(d, w_.y, i, jb);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny)
+        poisson_rhs_cell(d.a, d.C[1 - cur], d.P[cur], d.P[1 - cur], d.U[1 - cur], d.V[1 - cur],
+                         d.rhs, d.phat, i, j);
+    }
   }
 }
 
@@ -613,14 +678,23 @@ __global__ void kb_correct(const InstDev<T>* __restrict__ I, const int2* __restr
   for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
-    int i, j, bad = 0;
-    double c = 0.0;
-    if (tile_cell(d, w_.y, i, j))
-      c = correct_cell(d.a, d.C[1 - cur], d.Clo[1 - cur], d.dp, d.phat, d.U[1 - cur],
-                       d.V[1 - cur], i, j, bad);
+    int i, jb, bad = 0;
+    tile_base(d, w_.y, i, jb);
+    T s_hi = T(0), s_lo = T(0);
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) {
+        correct_cell(d.a, d.C[1 - cur], d.dp, d.phat, d.U[1 - cur], d.V[1 - cur],
+                     i, j, bad);
+        const size_t c = (size_t)j * d.nx + i;
+        const T lo = d.Clo[1 - cur] ? d.Clo[1 - cur][c] : T(0);
+        pair_add(s_hi, s_lo, d.C[1 - cur][c], lo);
+      }
+    }
     if (bad) atomicOr(d.status, 1);
-    const int ntiles = d.gx * ((d.ny + kTileY - 1) / kTileY);
-    tile_mass(c, w_.y, ntiles, d.partial, d.ticket, d.mass);
+    const int ntiles = d.gx * ((d.ny + kTileH - 1) / kTileH);
+    tile_mass<T>(s_hi, s_lo, w_.y, ntiles, d.partial, d.ticket, d.mass);
   }
 }
 
@@ -728,7 +802,7 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.ticket = in.ticket;
     d.mass = in.mass;
     d.status = in.status;
-    const int ntiles = d.gx * ((in.ny + kTileY - 1) / kTileY);
+    const int ntiles = d.gx * ((in.ny + kTileH - 1) / kTileH);
     for (int b = 0; b < ntiles; ++b) fam[kFamCell].push_back(make_int2(k, b));
     for (int b = 0; b < in.ny / 2; ++b) fam[kFamRows].push_back(make_int2(k, b));
     const int ncg = (in.nx / 2 + 1 + kColsKC - 1) / kColsKC;
