@@ -37,9 +37,12 @@ restatement, with the CUDA path):
       3-point derivative is the slope (C_M - C_I)/(gamma dn) -- the same reduction the
       paper makes for the slip velocity in Eq. UpdateVtan.  (Holding G at the estimate
       2C^n_G - C^{n-1}_G instead makes the ghost update an unstable recursion: at
-      theta = 90 deg it multiplies ghost errors by about 5 per step.)  The quadratic's root
-      continuous with the zero-gradient limit is taken.  The wetting bracket of the slip
-      condition is then zero, so the slip formula has no B term.
+      theta = 90 deg it multiplies ghost errors by about 5 per step.)  g' is taken as zero
+      outside [-1, 1] (g constant beyond the pure phases), so C_I = C_M when |C_M| >= 1 and
+      otherwise the quadratic's root inside [-1, 1] is taken (without this cut-off the
+      quadratic has no real root once C_M overshoots 1 at a dewetting wall and the ghost
+      value feeds the overshoot).  The wetting bracket of the slip condition is then zero,
+      so the slip formula has no B term.
   R5  Tangent t = (n2, -n1); back transform x1 = Vn n1 + Vt n2, x2 = Vn n2 - Vt n1.
   R6  Ghost = solid cell centre with a fluid centre among its 4 face neighbours; averaging
       points = the cell holding the IP plus its 4 face neighbours, solid centres and
@@ -53,6 +56,10 @@ restatement, with the CUDA path):
   R10 Face fix after the velocity ghost fill: faces with alpha_f < 1 touching a ghost cell
       take the mean of the two cell-centred values (ghost value; 0 for a solid non-ghost
       cell; pre-fix centred u** for a fluid cell).
+  R11 rho(C) and mu(C) are evaluated with C clamped to [-1, 1]: the Dodd-Ferrante split of
+      Eq. PressurePoisson rests on rho >= rho0 = min(rho_l, rho_g), which an unclamped
+      linear law breaks wherever C overshoots -1 (observed inside the solid, where it ended
+      runs after ~1e4 steps).
 """
 from __future__ import annotations
 
@@ -403,10 +410,15 @@ def _props(case: Case2D):
     rho_l, rho_g = 1.0, 1.0 / p.rho_ratio
     mu_l, mu_g = 1.0, 1.0 / p.mu_ratio
 
+    # reading R11: C is clamped to [-1, 1] in the property laws, so that rho never falls
+    # below rho0 = min(rho_l, rho_g), the bound the Dodd-Ferrante split of Eq.
+    # PressurePoisson is built on
     def rho(c):
+        c = np.clip(c, -1.0, 1.0)
         return 0.5 * ((1.0 + c) * rho_l + (1.0 - c) * rho_g)
 
     def mu(c):
+        c = np.clip(c, -1.0, 1.0)
         return 0.5 * ((1.0 + c) * mu_l + (1.0 - c) * mu_g)
 
     return rho, mu, min(rho_l, rho_g)
@@ -454,10 +466,13 @@ def contact_angle_ghost(case: Case2D, C_M, gamma, dn):
     On that line the 3-point one-sided derivative of Eq. ProjectingToNT reduces to the
     slope dC/dn = (C_M - C_I)/(gamma dn) (the same reduction that turns Eq. UpdateVtan
     into its closed form).  The static wetting condition of Eq. WallBCS,
-    kappa Cn dC/dn + cos(theta) g'(C_I) = 0 with g'(C) = 3/4 (1 - C^2), is then the
-    quadratic a C_I^2 + b C_I + c = 0, a = -3/4 cos(theta), b = -k, c = k C_M + 3/4 cos(theta),
-    k = kappa Cn/(gamma dn).  Its root 2c/(k + sqrt(max(0, b^2 - 4ac))) is the one that
-    tends to C_M as cos(theta) -> 0 (the zero-gradient limit).  Eq. UpdateC gives C_G.
+    F(C_I) = kappa Cn dC/dn + cos(theta) g'(C_I) = 0, with g'(C) = 3/4 (1 - C^2) on [-1, 1]
+    and g' = 0 outside (g, the wall-energy switch of Eq. FreeEnergySolid, is constant beyond
+    the pure phases), is solved as follows: if |C_M| >= 1, C_I = C_M; otherwise F changes sign
+    on [-1, 1] and its one root there is a root of the quadratic a C_I^2 - k C_I + c = 0,
+    a = -3/4 cos(theta), c = k C_M + 3/4 cos(theta), k = kappa Cn/(gamma dn): of
+    r2 = 2c/(k + sqrt D) and r1 = (k + sqrt D)/(2a) (D = k^2 - 4ac) the one in [-1, 1] is
+    taken (r2 when both qualify).  Eq. UpdateC then gives C_G.
     Returns (C_G, C_I, number of clamped discriminants)."""
     p = case.params
     ct = math.cos(math.radians(p.theta_deg))
@@ -465,8 +480,15 @@ def contact_angle_ghost(case: Case2D, C_M, gamma, dn):
     a = -0.75 * ct
     c = k * C_M + 0.75 * ct
     disc = k * k - 4.0 * a * c
-    clamped = int(np.count_nonzero(disc < 0.0))
-    C_I = 2.0 * c / (k + np.sqrt(np.maximum(disc, 0.0)))
+    clamped = int(np.count_nonzero((disc < 0.0) & (np.abs(C_M) < 1.0)))
+    sq = np.sqrt(np.maximum(disc, 0.0))
+    r2 = 2.0 * c / (k + sq)
+    if a != 0.0:
+        r1 = (k + sq) / (2.0 * a)
+        root = np.where(np.abs(r2) <= 1.0, r2, np.clip(r1, -1.0, 1.0))
+    else:
+        root = r2
+    C_I = np.where(np.abs(C_M) >= 1.0, C_M, root)
     C_G = ((gamma + 1.0) * C_I - C_M) / gamma
     return C_G, C_I, clamped
 

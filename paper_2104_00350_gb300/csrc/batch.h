@@ -16,7 +16,7 @@ template <> struct C2T<float> { using type = float2; };
 // kernel families and their work units
 enum Family {
   kFamCell = 0,    // 32 x 32 tiles of cells / faces (32 x 8 threads, 4 rows each)
-  kFamRows = 1,    // pairs of x1 rows (row FFTs)
+  kFamRows = 1,    // groups of kRowPairs pairs of x1 rows (row FFTs)
   kFamCols = 2,    // groups of kColsKC spectral columns (x2 transforms + symbol)
   kFamGhost = 3,   // chunks of kGhostChunk ghosts
   kFamFace = 4,    // chunks of kGhostChunk re-interpolated faces
@@ -25,7 +25,8 @@ enum Family {
 constexpr int kTileX = 32, kTileY = 8;       // threads of a cell-family block
 constexpr int kRowsPerThread = 4;            // cells per thread along x2
 constexpr int kTileH = kTileY * kRowsPerThread;   // cell tile: 32 x 32
-constexpr int kColsKC = 2;
+constexpr int kColsKC = 4;        // spectral columns per block (x2 transforms)
+constexpr int kRowPairs = 2;      // row pairs per block (x1 transforms)
 constexpr int kGhostChunk = 128;
 
 template <typename T>

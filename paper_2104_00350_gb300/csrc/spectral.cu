@@ -39,74 +39,85 @@ __device__ __forceinline__ int brev(int n, int logn) {
   return logn == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - logn));
 }
 
-// In-place radix-2 DIT FFT of x[0..N) (input in bit-reversed order, output natural).
-// tw[k] = exp(-2 pi i k/N), k < N/2.  Called by every thread of the block; lt/nt is the
-// thread's rank within the group that owns x.
+// cnt independent in-place radix-2 FFTs of length N = 2^logn stored back to back in x;
+// every thread of the block takes butterflies of all of them, so one barrier per stage
+// serves cnt transforms.
+// DIT: input in bit-reversed order, output natural; tw[k] = exp(-2 pi i k/N), k < N/2.
 template <typename C2>
-__device__ void fft_dit(C2* x, int logn, const C2* __restrict__ tw, int lt, int nt) {
-  const int N = 1 << logn;
+__device__ void fft_dit(C2* x, int logn, const C2* __restrict__ tw, int cnt) {
+  const int N = 1 << logn, half = N >> 1;
   for (int s = 0; s < logn; ++s) {
     const int m = 1 << s;
     const int tstride = N >> (s + 1);
-    for (int p = lt; p < (N >> 1); p += nt) {
+    for (int t = threadIdx.x; t < cnt * half; t += blockDim.x) {
+      const int f = t >> (logn - 1), p = t & (half - 1);
+      C2* y = x + f * N;
       const int pos = p & (m - 1);
       const int i0 = ((p >> s) << (s + 1)) + pos;
       const int i1 = i0 + m;
-      C2 b = cmul(tw[pos * tstride], x[i1]);
-      C2 a = x[i0];
-      x[i0] = cadd(a, b);
-      x[i1] = csub(a, b);
+      C2 b = cmul(tw[pos * tstride], y[i1]);
+      C2 a = y[i0];
+      y[i0] = cadd(a, b);
+      y[i1] = csub(a, b);
     }
     __syncthreads();
   }
 }
 
-// In-place radix-2 DIF inverse FFT without the 1/N (input natural, output bit-reversed),
-// twiddles exp(+2 pi i k/N).
+// DIF inverse without the 1/N: input natural, output bit-reversed, twiddles exp(+2 pi i k/N).
 template <typename C2>
-__device__ void ifft_dif(C2* x, int logn, const C2* __restrict__ tw, int lt, int nt) {
-  const int N = 1 << logn;
+__device__ void ifft_dif(C2* x, int logn, const C2* __restrict__ tw, int cnt) {
+  const int N = 1 << logn, half = N >> 1;
   for (int s = logn - 1; s >= 0; --s) {
     const int m = 1 << s;
     const int tstride = N >> (s + 1);
-    for (int p = lt; p < (N >> 1); p += nt) {
+    for (int t = threadIdx.x; t < cnt * half; t += blockDim.x) {
+      const int f = t >> (logn - 1), p = t & (half - 1);
+      C2* y = x + f * N;
       const int pos = p & (m - 1);
       const int i0 = ((p >> s) << (s + 1)) + pos;
       const int i1 = i0 + m;
-      C2 a = x[i0], b = x[i1];
-      x[i0] = cadd(a, b);
-      x[i1] = cmul(cconj(tw[pos * tstride]), csub(a, b));
+      C2 a = y[i0], b = y[i1];
+      y[i0] = cadd(a, b);
+      y[i1] = cmul(cconj(tw[pos * tstride]), csub(a, b));
     }
     __syncthreads();
   }
 }
 
-// Forward real FFT of rows ra and ra+1 of in (ny x nx) into spec (ny x (nx/2+1)).
-// z = row_a + i row_b;  A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
+// Forward real FFT of the cnt row pairs (ra + 2f, ra + 2f + 1), f < cnt, of in (ny x nx)
+// into spec (ny x (nx/2+1)).  Per pair z = row_a + i row_b;
+// A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
 template <typename T>
 __device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
                               int lognx, const typename C2T<T>::type* __restrict__ tw,
-                              size_t ra, typename C2T<T>::type* x) {
+                              size_t ra, int cnt, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
   const int nx = 1 << lognx, nh = nx >> 1;
-  const size_t rb = ra + 1;
-  for (int n = threadIdx.x; n < nx; n += blockDim.x) {
+  C2* tws = x + cnt * nx;   // twiddles staged after the data
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
+    const int f = t >> lognx, n = t & (nx - 1);
+    const size_t r = ra + 2 * f;
     C2 z;
-    z.x = in[ra * nx + n];
-    z.y = in[rb * nx + n];
-    x[brev(n, lognx)] = z;
+    z.x = in[r * nx + n];
+    z.y = in[(r + 1) * nx + n];
+    x[f * nx + brev(n, lognx)] = z;
   }
   __syncthreads();
-  fft_dit(x, lognx, tw, threadIdx.x, blockDim.x);
-  for (int k = threadIdx.x; k <= nh; k += blockDim.x) {
-    C2 z = x[k & (nx - 1)], zc = x[(nx - k) & (nx - 1)];
+  fft_dit(x, lognx, tws, cnt);
+  for (int t = threadIdx.x; t < cnt * (nh + 1); t += blockDim.x) {
+    const int f = t / (nh + 1), k = t - f * (nh + 1);
+    const C2* y = x + f * nx;
+    const size_t r = ra + 2 * f;
+    C2 z = y[k & (nx - 1)], zc = y[(nx - k) & (nx - 1)];
     C2 A, B;
     A.x = T(0.5) * (z.x + zc.x);
     A.y = T(0.5) * (z.y - zc.y);
     B.x = T(0.5) * (z.y + zc.y);
     B.y = T(-0.5) * (z.x - zc.x);
-    spec[ra * (nh + 1) + k] = A;
-    spec[rb * (nh + 1) + k] = B;
+    spec[r * (nh + 1) + k] = A;
+    spec[(r + 1) * (nh + 1) + k] = B;
   }
   __syncthreads();   // the shared buffer may be reused by the caller
 }
@@ -116,7 +127,7 @@ __global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __re
                            int lognx, const typename C2T<T>::type* __restrict__ tw) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_fwd_core<T>(in, spec, lognx, tw, 2 * (size_t)blockIdx.x, reinterpret_cast<C2*>(smem_raw));
+  rows_fwd_core<T>(in, spec, lognx, tw, 2 * (size_t)blockIdx.x, 1, reinterpret_cast<C2*>(smem_raw));
 }
 
 // (hi, lo) + inc -> (out_hi, out_lo): TwoSum of hi and inc (Knuth), the rounding error
@@ -142,13 +153,14 @@ __device__ __forceinline__ void two_sum_into(T hi, T inc, T lo, T& out_hi, T& ou
 template <typename T>
 __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
                               const typename C2T<T>::type* __restrict__ tw, const EpiArgs& epi,
-                              size_t ra, typename C2T<T>::type* x) {
+                              size_t ra, int cnt, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
   const int nx = 1 << lognx, nh = nx >> 1;
-  const size_t rb = ra + 1;
-  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
+    const int f = t >> lognx, k = t & (nx - 1);
+    const size_t r = ra + 2 * f;
     int kk = k <= nh ? k : nx - k;
-    C2 A = spec[ra * (nh + 1) + kk], B = spec[rb * (nh + 1) + kk];
+    C2 A = spec[r * (nh + 1) + kk], B = spec[(r + 1) * (nh + 1) + kk];
     if (kk == 0 || kk == nh) {
       A.y = T(0);
       B.y = T(0);
@@ -160,17 +172,21 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
     C2 z;
     z.x = A.x - B.y;
     z.y = A.y + B.x;
-    x[k] = z;
+    x[f * nx + k] = z;
   }
+  C2* tws = x + cnt * nx;   // twiddles staged after the data
+  for (int t = threadIdx.x; t < nh; t += blockDim.x) tws[t] = tw[t];
   __syncthreads();
-  ifft_dif(x, lognx, tw, threadIdx.x, blockDim.x);
+  ifft_dif(x, lognx, tws, cnt);
   const T inv = T(1) / T(nx);
   const T* ea = reinterpret_cast<const T*>(epi.a);
   const T* eb = reinterpret_cast<const T*>(epi.b);
   T* ed = reinterpret_cast<T*>(epi.delta);
-  for (int n = threadIdx.x; n < nx; n += blockDim.x) {
-    C2 z = x[brev(n, lognx)];
-    const size_t ia = ra * nx + n, ib = rb * nx + n;
+  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
+    const int f = t >> lognx, n = t & (nx - 1);
+    const size_t r = ra + 2 * f;
+    C2 z = x[f * nx + brev(n, lognx)];
+    const size_t ia = r * nx + n, ib = (r + 1) * nx + n;
     T va = z.x * inv, vb = z.y * inv;
     if (epi.kind == 1 && epi.out_lo != nullptr) {
       // compensated state: value = hi + lo; new pair by TwoSum, then renormalised
@@ -204,7 +220,7 @@ __global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* ou
                            const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_inv_core<T>(spec, out, lognx, tw, epi, 2 * (size_t)blockIdx.x, reinterpret_cast<C2*>(smem_raw));
+  rows_inv_core<T>(spec, out, lognx, tw, epi, 2 * (size_t)blockIdx.x, 1, reinterpret_cast<C2*>(smem_raw));
 }
 
 struct SymbolArgs {
@@ -261,9 +277,11 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
                           const typename C2T<T>::type* __restrict__ wd, const SymbolArgs& sym,
                           int k0, typename C2T<T>::type* xs) {
   using C2 = typename C2T<T>::type;
-  const int N = 1 << logny;
-  const int tpc = blockDim.x / KC;   // threads per column (>= 1)
-  const int c = threadIdx.x / tpc, lt = threadIdx.x % tpc;
+  const int N = 1 << logny, half = N >> 1;
+  C2* tws = xs + KC * N;     // FFT twiddles, staged once per block
+  C2* wds = tws + half;      // cosine-transform weights
+  for (int t = threadIdx.x; t < half; t += blockDim.x) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) wds[t] = wd[t];
   // load: consecutive threads take consecutive columns of one row (coalesced)
   for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
     int cc = idx % KC, r = idx / KC;
@@ -276,15 +294,17 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
     xs[cc * N + brev(pos, logny)] = val;
   }
   __syncthreads();
-  C2* x = xs + c * N;
-  fft_dit(x, logny, tw, lt, tpc);
-  const int k = min(k0 + c, nh1 - 1);
-  for (int m = lt; m <= (N >> 1); m += tpc) {
+  fft_dit(xs, logny, tws, KC);
+  // pair tasks (m, N - m), m = 0..N/2, of every column
+  for (int t = threadIdx.x; t < KC * (half + 1); t += blockDim.x) {
+    const int c = t / (half + 1), m = t - c * (half + 1);
+    C2* x = xs + c * N;
+    const int k = min(k0 + c, nh1 - 1);
     const int mm = (N - m) & (N - 1);
     C2 Vm = x[m], Vmm = x[mm];
     C2 Xm, Xmm;
     {
-      C2 vr, vi, w = wd[m];
+      C2 vr, vi, w = wds[m];
       vr.x = T(0.5) * (Vm.x + Vmm.x);
       vr.y = T(0.5) * (Vm.y - Vmm.y);
       vi.x = T(0.5) * (Vm.y + Vmm.y);
@@ -293,7 +313,7 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
       Xm.y = w.x * vi.x - w.y * vi.y;
     }
     {
-      C2 vr, vi, w = wd[mm];
+      C2 vr, vi, w = wds[mm];
       vr.x = T(0.5) * (Vmm.x + Vm.x);
       vr.y = T(0.5) * (Vmm.y - Vm.y);
       vi.x = T(0.5) * (Vmm.y + Vm.y);
@@ -310,20 +330,20 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
       C2 xo = (m == 0) ? C2{T(0), T(0)} : Xmm;
       y.x = Xm.x + xo.y;
       y.y = Xm.y - xo.x;
-      Zm = cmul(cconj(wd[m]), y);
+      Zm = cmul(cconj(wds[m]), y);
     }
     {
       C2 y;
       C2 xo = (mm == 0) ? C2{T(0), T(0)} : Xm;
       y.x = Xmm.x + xo.y;
       y.y = Xmm.y - xo.x;
-      Zmm = cmul(cconj(wd[mm]), y);
+      Zmm = cmul(cconj(wds[mm]), y);
     }
     x[m] = Zm;
     if (mm != m) x[mm] = Zmm;
   }
   __syncthreads();
-  ifft_dif(x, logny, tw, lt, tpc);
+  ifft_dif(xs, logny, tws, KC);
   const T inv = T(1) / T(N);
   for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
     int cc = idx % KC, r = idx / KC;
@@ -355,8 +375,9 @@ __global__ void kb_rows_fwd(const InstDev<T>* __restrict__ I, const int2* __rest
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const int2 w = blk[b];
     const InstDev<T>& d = I[w.x];
-    rows_fwd_core<T>(src == 0 ? d.Q : d.rhs, d.spec, d.lognx, d.twx, 2 * (size_t)w.y,
-                     reinterpret_cast<C2*>(smem_raw));
+    const int cnt = min(kRowPairs, d.ny / 2 - w.y * kRowPairs);
+    rows_fwd_core<T>(src == 0 ? d.Q : d.rhs, d.spec, d.lognx, d.twx, 2 * (size_t)w.y * kRowPairs,
+                     cnt, reinterpret_cast<C2*>(smem_raw));
   }
 }
 
@@ -405,7 +426,8 @@ __global__ void kb_rows_inv(const InstDev<T>* __restrict__ I, const int2* __rest
       epi.delta = d.dp;
       out = d.P[1 - cur];
     }
-    rows_inv_core<T>(d.spec, out, d.lognx, d.twx, epi, 2 * (size_t)w.y,
+    const int cnt = min(kRowPairs, d.ny / 2 - w.y * kRowPairs);
+    rows_inv_core<T>(d.spec, out, d.lognx, d.twx, epi, 2 * (size_t)w.y * kRowPairs, cnt,
                      reinterpret_cast<C2*>(smem_raw));
   }
 }
@@ -458,9 +480,9 @@ cudaError_t tables_t(Instance& in) {
   e = cudaMemcpy(in.wdct, wd.data(), sizeof(C2) * wd.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   // rows of up to 4096 points need 64 KiB of shared memory (FP64)
-  cudaFuncSetAttribute(kb_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(kb_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  cudaFuncSetAttribute(kb_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(kb_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(kb_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(kb_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   return cudaGetLastError();
 }
 
@@ -493,18 +515,20 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   while ((1 << logny) < ny) ++logny;
   const int nh1 = nx / 2 + 1;
   const int trow = nx / 2 < 512 ? nx / 2 : 512;
-  k_rows_fwd<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(rhs, spec, lognx, twx);
+  k_rows_fwd<double><<<ny / 2, trow, sizeof(double2) * (nx + nx / 2), s>>>(rhs, spec, lognx, twx);
   SymbolArgs sym;
   sym.mode = mode;
   sym.s_eta2 = s_eta2;
   sym.c0 = c0;
   sym.lamx = lamx;
   sym.lamy = lamy;
-  const int tpc = ny / 2 < 256 ? ny / 2 : 256;
-  k_cols<double, kColsKC><<<(nh1 + kColsKC - 1) / kColsKC, tpc * kColsKC,
-                            sizeof(double2) * ny * kColsKC, s>>>(spec, nh1, logny, twy, wd, sym);
+  // one column per block: data, twiddles and weights take at most 40 KiB of shared memory
+  // for ny <= 1024, below the default limit, so this path needs no function attributes
+  k_cols<double, 1><<<nh1, 256, sizeof(double2) * (ny + ny / 2 + ny), s>>>(spec, nh1, logny, twy,
+                                                                         wd, sym);
   EpiArgs plain;
-  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * nx, s>>>(spec, out, lognx, twx, plain);
+  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * (nx + nx / 2), s>>>(spec, out, lognx, twx,
+                                                                           plain);
   return 3;
 }
 

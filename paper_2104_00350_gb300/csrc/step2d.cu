@@ -21,6 +21,13 @@ namespace {
 constexpr double kKappa = 1.0606601717798212;   // 3 / (2 sqrt 2)
 
 __device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : i - 1; }
+
+// C clamped to [-1, 1] for the property laws rho(C), mu(C): keeps rho >= rho0 = min(rho_l,
+// rho_g), the bound the Dodd-Ferrante split of Eq. PressurePoisson rests on
+template <typename T>
+__device__ __forceinline__ T clamp1(T c) {
+  return c > T(1) ? T(1) : (c < T(-1) ? T(-1) : c);
+}
 __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
 
 // ---------------------------------------------------------------- a1: CH right-hand side
@@ -79,10 +86,13 @@ __device__ __forceinline__ void ch_rhs_cell(const StepArgs<T>& a, const T* __res
 
 // ------------------------------------------------------------ a3: contact-angle ghost fill
 // Static angle: C_M = 2 C_IP1 - C_IP2 (Eq. extrapolation) gathered with W1/W2; with G, I,
-// M tied by Eq. UpdateC the normal derivative at I is (C_M - C_I)/(gamma dn), and
-// kappa Cn dC/dn + cos(theta) 3/4 (1 - C_I^2) = 0 gives
-//   C_I = 2c / (k + sqrt(max(0, k^2 - 4 a c))),  a = -3/4 cos, c = k C_M + 3/4 cos,
-//   k = kappa Cn / (gamma dn);   C_G = ((gamma + 1) C_I - C_M) / gamma   (Eq. UpdateC).
+// M tied by Eq. UpdateC the normal derivative at I is (C_M - C_I)/(gamma dn), and the
+// wetting condition kappa Cn dC/dn + cos(theta) g'(C_I) = 0 with g'(C) = 3/4 (1 - C^2) on
+// [-1, 1] and 0 outside (the wall energy g is flat beyond the pure phases) gives:
+//   |C_M| >= 1: C_I = C_M;
+//   otherwise the root in [-1, 1] of a C_I^2 - k C_I + c = 0, a = -3/4 cos, c = k C_M + 3/4 cos,
+//   k = kappa Cn / (gamma dn): r2 = 2c/(k + sqrt D) if |r2| <= 1, else r1 = (k + sqrt D)/(2a);
+//   C_G = ((gamma + 1) C_I - C_M) / gamma   (Eq. UpdateC).
 template <typename T>
 __device__ __forceinline__ T gather(const T* __restrict__ f, const int* __restrict__ ap,
                                     const double* __restrict__ w, int g) {
@@ -102,7 +112,13 @@ __device__ __forceinline__ void fill_C_ghost(const StepArgs<T>& a, const Tables&
   const T qc = k * cm + T(0.75) * (T)a.cos_th;
   T disc = k * k - T(4) * qa * qc;
   disc = disc > T(0) ? disc : T(0);
-  const T ci = T(2) * qc / (k + sqrt(disc));
+  const T sq = sqrt(disc);
+  T ci = T(2) * qc / (k + sq);
+  if (!(fabs(ci) <= T(1)) && qa != T(0)) {
+    ci = (k + sq) / (T(2) * qa);
+    ci = ci > T(1) ? T(1) : (ci < T(-1) ? T(-1) : ci);
+  }
+  if (fabs(cm) >= T(1)) ci = cm;
   C[t.gcell[g]] = ((gam + T(1)) * ci - cm) / gam;
   if (Clo) Clo[t.gcell[g]] = T(0);   // a ghost value is exact as stored
 }
@@ -180,8 +196,8 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
   auto Us = [&](int di, int dj) { return sm.U[ty + dj][tx + di]; };
   auto Vs = [&](int di, int dj) { return sm.V[ty + dj][tx + di]; };
   auto Fs = [&](int di, int dj) { return sm.F[ty + dj][tx + di]; };
-  auto mu = [&](T c) { return a.mu_a + a.mu_b * c; };
-  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  auto mu = [&](T c) { return a.mu_a + a.mu_b * clamp1(c); };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * clamp1(c); };
   // corner at (i + di, j + dj) in corner indices (x = (i+di) h, y = (j+dj) h)
   auto tau_xy = [&](int di, int dj) -> T {
     const T ce = T(0.25) * (((Cs(di - 1, dj - 1) + Cs(di, dj - 1)) + Cs(di - 1, dj)) + Cs(di, dj));
@@ -318,7 +334,7 @@ __device__ __forceinline__ void poisson_rhs_cell(const StepArgs<T>& a, const T* 
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const size_t r = (size_t)j * nx;
   auto ph = [&](size_t idx) { return T(2) * P[idx] - Po[idx]; };
-  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * clamp1(c); };
   const T p0 = ph(r + i);
   const T gx_w = (a.rho0 / rho(T(0.5) * (C[r + im] + C[r + i]))) * ((p0 - ph(r + im)) * a.inv_h);
   const T gx_e = (a.rho0 / rho(T(0.5) * (C[r + i] + C[r + ip]))) * ((ph(r + ip) - p0) * a.inv_h);
@@ -345,7 +361,7 @@ __device__ __forceinline__ void correct_cell(const StepArgs<T>& a, const T* __re
   const int nx = a.nx;
   const int im = wrap_m(i, nx);
   const size_t r = (size_t)j * nx;
-  auto rho = [&](T c) { return a.rho_a + a.rho_b * c; };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * clamp1(c); };
   {
     const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
     const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
@@ -804,7 +820,8 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.status = in.status;
     const int ntiles = d.gx * ((in.ny + kTileH - 1) / kTileH);
     for (int b = 0; b < ntiles; ++b) fam[kFamCell].push_back(make_int2(k, b));
-    for (int b = 0; b < in.ny / 2; ++b) fam[kFamRows].push_back(make_int2(k, b));
+    for (int b = 0; b < (in.ny / 2 + kRowPairs - 1) / kRowPairs; ++b)
+      fam[kFamRows].push_back(make_int2(k, b));
     const int ncg = (in.nx / 2 + 1 + kColsKC - 1) / kColsKC;
     for (int b = 0; b < ncg; ++b) fam[kFamCols].push_back(make_int2(k, b));
     for (int b = 0; b < (in.tab.ng + kGhostChunk - 1) / kGhostChunk; ++b)
@@ -829,10 +846,10 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
       if (e != cudaSuccess) return e;
     }
   }
-  plan.rows_threads = plan.max_nx / 2 < 512 ? plan.max_nx / 2 : 512;
-  plan.cols_threads = kColsKC * (plan.max_ny / 2 < 256 ? plan.max_ny / 2 : 256);
-  plan.rows_smem = sizeof(C2) * plan.max_nx;
-  plan.cols_smem = sizeof(C2) * plan.max_ny * kColsKC;
+  plan.rows_threads = 256;
+  plan.cols_threads = 256;
+  plan.rows_smem = sizeof(C2) * (plan.max_nx * kRowPairs + plan.max_nx / 2);
+  plan.cols_smem = sizeof(C2) * (plan.max_ny * kColsKC + plan.max_ny / 2 + plan.max_ny);
   return cudaSuccess;
 }
 

@@ -216,3 +216,28 @@ def test_kernel_timing_events(ibpf):
     s.step(1)
     assert s.query(ibpf.Q_STATUS) == 0.0
     s.close()
+
+
+def test_batched_uneven_ensemble_matches_oracle(ibpf):
+    # the 64-instance ensemble in one context (one launch per sub-step over all
+    # instances of three grid sizes); one step from random states, instances of each size
+    # checked against the oracle
+    ens = cases.ensemble_2d(64)
+    s = ibpf.solver_from_cases(ens, ibpf.FP64)
+    s.precompute_weights()
+    states = [cases.random_state(c, seed=100 + k) for k, c in enumerate(ens)]
+    for k in range(len(ens)):
+        s.write_state(states[k], k)
+    s.step(1)
+    picked = {}
+    for k, c in enumerate(ens):
+        picked.setdefault(c.nx, k)
+    picked[ens[-1].nx] = len(ens) - 1
+    for k in sorted(set(picked.values())):
+        c = ens[k]
+        ref, _ = O.step(c, O.build_geometry(c), states[k])
+        out = s.read_state(k)
+        for f in ("C", "u", "v", "P"):
+            assert _rel(out[f], ref[f]) <= TOL64, (k, c.name, f)
+    assert s.query(ibpf.Q_LAUNCHES) <= 17
+    s.close()

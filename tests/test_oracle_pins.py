@@ -229,6 +229,7 @@ def test_contact_angle_ghost_satisfies_wetting_condition(theta):
     dn = rng.uniform(0.2, 1.0, 64) * case.h
     CG, CI, clamped = O.contact_angle_ghost(case, CM, gamma, dn)
     assert clamped == 0
+    assert np.all(np.abs(CI) <= 1.0)
     # I lies on the straight line between G and M (Eq. interpolationAtWall)
     assert np.allclose(CI, (gamma * CG + CM) / (gamma + 1.0), atol=1e-13)
     ct = math.cos(math.radians(theta))
@@ -238,10 +239,12 @@ def test_contact_angle_ghost_satisfies_wetting_condition(theta):
         assert abs(resid) < 1e-9
     if theta == 90.0:
         assert np.allclose(CG, CM, atol=1e-14)   # zero normal gradient
-    # pure phases are fixed points
-    CG1, _, _ = O.contact_angle_ghost(case, np.array([1.0, -1.0]), np.array([1.5, 1.5]),
-                                      np.array([0.5, 0.5]) * case.h)
-    assert np.allclose(CG1, [1.0, -1.0], atol=1e-14)
+    # pure phases are fixed points; beyond them the wall energy is flat (g' = 0), so an
+    # overshooting mirror value is simply continued (zero normal gradient)
+    CG1, _, _ = O.contact_angle_ghost(case, np.array([1.0, -1.0, 1.07, -1.2]),
+                                      np.array([1.5, 1.5, 1.5, 2.0]),
+                                      np.array([0.5, 0.5, 0.5, 0.7]) * case.h)
+    assert np.allclose(CG1, [1.0, -1.0, 1.07, -1.2], atol=1e-14)
 
 
 def test_contact_angle_fill_reproduces_inclined_tanh_profile():
@@ -315,6 +318,17 @@ def test_slip_ghost_special_cases():
             assert np.allclose(VtG, VtM, atol=1e-12)
         else:
             assert np.allclose(VtI / ls, (VtM - VtG) / ((gamma + 1.0) * dn), rtol=1e-10)
+
+
+def test_properties_stay_within_the_phase_values():
+    # reading R11: rho and mu are bounded by the pure-phase values for any C, so
+    # rho >= rho0 = min(rho_l, rho_g) as the Dodd-Ferrante split requires
+    case = cases.flat_wall_case(rho_ratio=10.0, mu_ratio=20.0)
+    rho, mu, rho0 = O._props(case)
+    c = np.linspace(-1.5, 1.5, 301)
+    assert rho(c).min() >= rho0 - 1e-15 and rho(c).max() <= 1.0 + 1e-15
+    assert mu(c).min() >= 1.0 / 20.0 - 1e-15 and mu(c).max() <= 1.0 + 1e-15
+    assert rho(np.array([0.3]))[0] == pytest.approx(0.5 * (1.3 * 1.0 + 0.7 * 0.1))
 
 
 @pytest.mark.parametrize("ratio", [1.0, 10.0])
