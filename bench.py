@@ -68,6 +68,8 @@ def parse_args():
     ap.add_argument("--precision", choices=("both", "fp64", "fp32"), default="both",
                     help="both: FP32 form is the headline, plain FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="skip the 64-instance batched-ensemble measurement")
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="busy GPU time before the timed region so clocks settle")
@@ -403,6 +405,28 @@ def run_ours(args):
                          "gpu_launches": launches * args.steps, "roofline": roof, "e2e": e2e,
                          "dtype": "f64" if esz == 8 else "f32"}
         solver.close()
+    # batched form at scale: the 64-instance uneven ensemble (grids 256x128 .. 1024x512,
+    # ~14.5M cells, larger than L2) in one context, one launch per sub-step
+    ens = None
+    if not args.no_ensemble:
+        ecl = W.ensemble_2d(64)
+        ecells = sum(c.cells for c in ecl)
+        esolver = ibpf.solver_from_cases(ecl, ibpf.FP32, stream=stream.cuda_stream)
+        esolver.precompute_weights()
+        for k, c in enumerate(ecl):
+            esolver.write_state(W.initial_state(c), k)
+        for _ in range(max(1, args.warmup // 4)):
+            esolver.step(1)
+        torch.cuda.synchronize()
+        esteps = max(1, min(args.steps, 50))
+        ems, _, _ = timed_steps(esolver, esteps)
+        ems = max_over_ranks([ems], dist, "cuda")[0]
+        ens = {"value": aggregate_rate(world, ecells, esteps, ems * 1e-3), "unit": UNIT,
+               "ms_per_step": ems / esteps, "steps": esteps, "instances": len(ecl),
+               "cells": ecells, "dtype": "f32",
+               "gpu_launches": int(esolver.query(ibpf.Q_LAUNCHES)) * esteps,
+               "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls"}
+        esolver.close()
     clocks = sampler.stop()
 
     cpu = None
@@ -430,6 +454,7 @@ def run_ours(args):
             "roofline": head["roofline"],
             "cpu_baseline": cpu,
             "forms": {f: {k: v for k, v in r.items() if k != "e2e"} for f, r in results.items()},
+            "batched_ensemble": ens,
         }
         print(json.dumps(line), flush=True)
     if dist:
