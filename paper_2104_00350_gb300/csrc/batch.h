@@ -16,17 +16,28 @@ template <> struct C2T<float> { using type = float2; };
 // kernel families and their work units
 enum Family {
   kFamCell = 0,    // 32 x 32 tiles of cells / faces (32 x 8 threads, 4 rows each)
-  kFamRows = 1,    // groups of kRowPairs pairs of x1 rows (row FFTs)
-  kFamCols = 2,    // groups of kColsKC spectral columns (x2 transforms + symbol)
+  kFamRows = 1,    // groups of fft_rows_per_block(nx) pairs of x1 rows (row FFTs)
+  kFamCols = 2,    // groups of fft_cols_per_block(ny) spectral columns (x2 transforms + symbol)
   kFamGhost = 3,   // chunks of kGhostChunk ghosts
   kFamFace = 4,    // chunks of kGhostChunk re-interpolated faces
-  kNumFam = 5
+  kFamRowsL = 5,   // as kFamRows for rows of 2048 or 4096 points
+  kFamColsL = 6,   // as kFamCols for columns of 2048 points
+  kNumFam = 7
 };
 constexpr int kTileX = 32, kTileY = 8;       // threads of a cell-family block
 constexpr int kRowsPerThread = 4;            // cells per thread along x2
 constexpr int kTileH = kTileY * kRowsPerThread;   // cell tile: 32 x 32
-constexpr int kColsKC = 4;        // spectral columns per block (x2 transforms)
-constexpr int kRowPairs = 2;      // row pairs per block (x1 transforms)
+// Transform blocks hold 8 complex points per thread in registers during a pass: 128 threads
+// (1024 points: several transforms of up to 1024 points) or, for 2048 and 4096 points, 512
+// threads (4096 points).  Each class is its own launch.
+constexpr int kFftSmallThreads = 128;
+constexpr int kFftLargeThreads = 512;
+__host__ __device__ constexpr int fft_threads(int n) {
+  return n <= 8 * kFftSmallThreads ? kFftSmallThreads : kFftLargeThreads;
+}
+__host__ __device__ constexpr int fft_per_block(int n) { return 8 * fft_threads(n) / n; }
+// shared-memory slots of a transform buffer of e points: one pad slot per 16 points
+__host__ __device__ constexpr int fft_buf(int e) { return e + (e >> 4); }
 constexpr int kGhostChunk = 128;
 
 template <typename T>
@@ -84,8 +95,7 @@ struct BatchPlan {
   void* d_inst = nullptr;              // InstDev<T>[n]
   int2* d_blk[kNumFam] = {};           // (instance, local block) per launched block
   int nblk[kNumFam] = {};
-  int rows_threads = 0, cols_threads = 0;
-  size_t rows_smem = 0, cols_smem = 0;
+  size_t rows_smem[2] = {}, cols_smem[2] = {};   // small / large transform class
   int max_nx = 0, max_ny = 0;
 };
 

@@ -5,11 +5,11 @@
 // A solve is three kernels:
 //   rows_fwd : real FFT of every x1 row (two rows packed into one complex FFT),
 //   cols     : per spectral column k, cosine transform (DCT-II) along x2, division by the
-//              symbol in FP64, inverse cosine transform (the last forward axis and the first
+//              symbol, inverse cosine transform (the last forward axis and the first
 //              inverse axis fused in shared memory),
 //   rows_inv : inverse real FFT of every row (two rows per complex FFT).
-// FFTs are radix-2 in shared memory: decimation in time on bit-reversed input for the
-// forward transforms, decimation in frequency to bit-reversed output for the inverse ones.
+// FFTs are Stockham autosort transforms, radix 8 in registers with one radix-4 or radix-2
+// pass for the remaining factor, exchanging through shared memory between passes.
 // The cosine transforms use an N-point complex FFT with the even/odd reordering
 // v_n = x_{2n}, v_{N-1-n} = x_{2n+1} (Makhoul's algorithm).
 #include <cmath>
@@ -35,82 +35,139 @@ __device__ __forceinline__ C2 csub(C2 a, C2 b) { C2 r; r.x = a.x - b.x; r.y = a.
 template <typename C2>
 __device__ __forceinline__ C2 cconj(C2 a) { a.y = -a.y; return a; }
 
-__device__ __forceinline__ int brev(int n, int logn) {
-  return logn == 0 ? 0 : (int)(__brev((unsigned)n) >> (32 - logn));
+// ------------------------------------------------------------------ Stockham FFT
+// cnt independent FFTs of length N = 2^LOGN, stored back to back in the shared buffer x at
+// padded slots pad(i) (one pad slot per 16 points, so that the strided stores of the early
+// passes and the unit-stride loads of the next pass both spread over the 32 banks).
+// Input and output are in natural order (Stockham autosort).  Each pass of radix R takes
+// groups j < N/R: v_r = x[j + r N/R] times the twiddle W_{Ns R}^{r (j mod Ns)}, an R-point
+// DFT in registers, stored at ((j - j mod Ns) R + j mod Ns) + r Ns, where Ns is the product
+// of the radices of the earlier passes (radix 8, then one radix-4 or radix-2 pass).
+// A pass loads all its groups into registers, synchronises, stores, synchronises.
+// Forward: W = exp(-2 pi i/N); INV: conjugate twiddles, no 1/N.  tw[m] = exp(-2 pi i m/N),
+// m < N/2, the other half by W^{m + N/2} = -W^m.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+template <bool INV, typename C2>
+__device__ __forceinline__ C2 mul_mi(C2 a) {   // a times -i (forward) or +i (inverse)
+  C2 r;
+  if (INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
 }
 
-// cnt independent in-place radix-2 FFTs of length N = 2^logn stored back to back in x;
-// every thread of the block takes butterflies of all of them, so one barrier per stage
-// serves cnt transforms.
-// DIT: input in bit-reversed order, output natural; tw[k] = exp(-2 pi i k/N), k < N/2.
-template <typename C2>
-__device__ void fft_dit(C2* x, int logn, const C2* __restrict__ tw, int cnt) {
-  const int N = 1 << logn, half = N >> 1;
-  for (int s = 0; s < logn; ++s) {
-    const int m = 1 << s;
-    const int tstride = N >> (s + 1);
-    for (int t = threadIdx.x; t < cnt * half; t += blockDim.x) {
-      const int f = t >> (logn - 1), p = t & (half - 1);
-      C2* y = x + f * N;
-      const int pos = p & (m - 1);
-      const int i0 = ((p >> s) << (s + 1)) + pos;
-      const int i1 = i0 + m;
-      C2 b = cmul(tw[pos * tstride], y[i1]);
-      C2 a = y[i0];
-      y[i0] = cadd(a, b);
-      y[i1] = csub(a, b);
+template <int R, bool INV, typename T, typename C2>
+__device__ __forceinline__ void dft_reg(C2* v) {
+  if constexpr (R == 2) {
+    const C2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const C2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const C2 s13 = cadd(v[1], v[3]), d13 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  } else {
+    static_assert(R == 8, "radix 2, 4 or 8");
+    C2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_reg<4, INV, T>(e);
+    dft_reg<4, INV, T>(o);
+    const T c = T(0.70710678118654752440);   // cos(pi/4)
+    C2 w1, w3;                                 // W8^1 o_1 and W8^3 o_3
+    if (INV) {
+      w1.x = c * (o[1].x - o[1].y); w1.y = c * (o[1].x + o[1].y);
+      w3.x = -c * (o[3].x + o[3].y); w3.y = c * (o[3].x - o[3].y);
+    } else {
+      w1.x = c * (o[1].x + o[1].y); w1.y = c * (o[1].y - o[1].x);
+      w3.x = c * (o[3].y - o[3].x); w3.y = -c * (o[3].x + o[3].y);
     }
-    __syncthreads();
+    const C2 w2 = mul_mi<INV>(o[2]);
+    v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);   v[5] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);   v[6] = csub(e[2], w2);
+    v[3] = cadd(e[3], w3);   v[7] = csub(e[3], w3);
   }
 }
 
-// DIF inverse without the 1/N: input natural, output bit-reversed, twiddles exp(+2 pi i k/N).
-template <typename C2>
-__device__ void ifft_dif(C2* x, int logn, const C2* __restrict__ tw, int cnt) {
-  const int N = 1 << logn, half = N >> 1;
-  for (int s = logn - 1; s >= 0; --s) {
-    const int m = 1 << s;
-    const int tstride = N >> (s + 1);
-    for (int t = threadIdx.x; t < cnt * half; t += blockDim.x) {
-      const int f = t >> (logn - 1), p = t & (half - 1);
-      C2* y = x + f * N;
-      const int pos = p & (m - 1);
-      const int i0 = ((p >> s) << (s + 1)) + pos;
-      const int i1 = i0 + m;
-      C2 a = y[i0], b = y[i1];
-      y[i0] = cadd(a, b);
-      y[i1] = cmul(cconj(tw[pos * tstride]), csub(a, b));
+template <int LOGN, int R, int NS, bool INV, int THREADS, typename T, typename C2>
+__device__ __forceinline__ void stockham_pass(C2* x, const C2* __restrict__ tw, int cnt) {
+  constexpr int N = 1 << LOGN, NR = N / R, HALF = N / 2;
+  static_assert(N <= 8 * THREADS, "a block holds 8 points per thread");
+  constexpr int Q = 8 / R;                    // groups per thread
+  constexpr int TSTEP = N / (NS * R);         // twiddle index step
+  const int ng = cnt * NR;
+  C2 v[Q][R];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int g = threadIdx.x + q * THREADS;
+    if (g < ng) {
+      const int f = g / NR, j = g % NR;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = x[pad(f * N + j + r * NR)];
+      if constexpr (NS > 1) {
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const int m = r * k * TSTEP;
+          C2 w = tw[m & (HALF - 1)];
+          if (m >= HALF) { w.x = -w.x; w.y = -w.y; }
+          if (INV) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+      }
+      dft_reg<R, INV, T>(v[q]);
     }
-    __syncthreads();
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int g = threadIdx.x + q * THREADS;
+    if (g < ng) {
+      const int f = g / NR, j = g % NR, k = j % NS;
+      const int d = f * N + (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[pad(d + r * NS)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int LOGN, int DONE, bool INV, int THREADS, typename T, typename C2>
+__device__ __forceinline__ void stockham(C2* x, const C2* __restrict__ tw, int cnt) {
+  if constexpr (DONE < LOGN) {
+    constexpr int LR = (LOGN - DONE) >= 3 ? 3 : (LOGN - DONE);
+    stockham_pass<LOGN, (1 << LR), (1 << DONE), INV, THREADS, T>(x, tw, cnt);
+    stockham<LOGN, DONE + LR, INV, THREADS, T>(x, tw, cnt);
   }
 }
 
 // Forward real FFT of the cnt row pairs (ra + 2f, ra + 2f + 1), f < cnt, of in (ny x nx)
 // into spec (ny x (nx/2+1)).  Per pair z = row_a + i row_b;
 // A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
-template <typename T>
+template <typename T, int LOGN, int THREADS>
 __device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
-                              int lognx, const typename C2T<T>::type* __restrict__ tw,
-                              size_t ra, int cnt, typename C2T<T>::type* x) {
+                              const typename C2T<T>::type* __restrict__ tw, size_t ra, int cnt,
+                              typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
-  const int nx = 1 << lognx, nh = nx >> 1;
-  C2* tws = x + cnt * nx;   // twiddles staged after the data
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) tws[t] = tw[t];
-  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
-    const int f = t >> lognx, n = t & (nx - 1);
+  constexpr int nx = 1 << LOGN, nh = nx >> 1;
+  constexpr int EB = 8 * THREADS;
+  C2* tws = x + fft_buf(EB);   // twiddles staged after the data
+  for (int t = threadIdx.x; t < nh; t += THREADS) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < cnt * nx; t += THREADS) {
+    const int f = t >> LOGN, n = t & (nx - 1);
     const size_t r = ra + 2 * f;
     C2 z;
     z.x = in[r * nx + n];
     z.y = in[(r + 1) * nx + n];
-    x[f * nx + brev(n, lognx)] = z;
+    x[pad(t)] = z;
   }
   __syncthreads();
-  fft_dit(x, lognx, tws, cnt);
-  for (int t = threadIdx.x; t < cnt * (nh + 1); t += blockDim.x) {
+  stockham<LOGN, 0, false, THREADS, T>(x, tws, cnt);
+  for (int t = threadIdx.x; t < cnt * (nh + 1); t += THREADS) {
     const int f = t / (nh + 1), k = t - f * (nh + 1);
-    const C2* y = x + f * nx;
     const size_t r = ra + 2 * f;
-    C2 z = y[k & (nx - 1)], zc = y[(nx - k) & (nx - 1)];
+    C2 z = x[pad(f * nx + (k & (nx - 1)))], zc = x[pad(f * nx + ((nx - k) & (nx - 1)))];
     C2 A, B;
     A.x = T(0.5) * (z.x + zc.x);
     A.y = T(0.5) * (z.y - zc.y);
@@ -120,14 +177,6 @@ __device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* _
     spec[(r + 1) * (nh + 1) + k] = B;
   }
   __syncthreads();   // the shared buffer may be reused by the caller
-}
-
-template <typename T>
-__global__ void k_rows_fwd(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
-                           int lognx, const typename C2T<T>::type* __restrict__ tw) {
-  using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_fwd_core<T>(in, spec, lognx, tw, 2 * (size_t)blockIdx.x, 1, reinterpret_cast<C2*>(smem_raw));
 }
 
 // (hi, lo) + inc -> (out_hi, out_lo): TwoSum of hi and inc (Knuth), the rounding error
@@ -143,21 +192,22 @@ __device__ __forceinline__ void two_sum_into(T hi, T inc, T lo, T& out_hi, T& ou
   out_lo = l - (h2 - s);
 }
 
-// Inverse of k_rows_fwd: Z_k = A_k + i B_k with Hermitian extension (imaginary parts of
+// Inverse of rows_fwd_core: Z_k = A_k + i B_k with Hermitian extension (imaginary parts of
 // the k = 0 and k = nx/2 bins dropped), z = IFFT(Z)/nx, row_a = Re z, row_b = Im z.
 // Epilogue (the solves return increments):
 //   kind 0: out = z
 //   kind 1: out = a + ((a - b)/3 + z)    (BDF2 predictor (2a - b/2)/1.5 of C plus the
 //                                          increment, small terms first; out may alias b)
 //   kind 2: delta = z, out = z + a         (pressure increment on top of a = P^)
-template <typename T>
-__device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
+template <typename T, int LOGN, int THREADS>
+__device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T* out,
                               const typename C2T<T>::type* __restrict__ tw, const EpiArgs& epi,
                               size_t ra, int cnt, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
-  const int nx = 1 << lognx, nh = nx >> 1;
-  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
-    const int f = t >> lognx, k = t & (nx - 1);
+  constexpr int nx = 1 << LOGN, nh = nx >> 1;
+  constexpr int EB = 8 * THREADS;
+  for (int t = threadIdx.x; t < cnt * nx; t += THREADS) {
+    const int f = t >> LOGN, k = t & (nx - 1);
     const size_t r = ra + 2 * f;
     int kk = k <= nh ? k : nx - k;
     C2 A = spec[r * (nh + 1) + kk], B = spec[(r + 1) * (nh + 1) + kk];
@@ -172,20 +222,20 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
     C2 z;
     z.x = A.x - B.y;
     z.y = A.y + B.x;
-    x[f * nx + k] = z;
+    x[pad(t)] = z;
   }
-  C2* tws = x + cnt * nx;   // twiddles staged after the data
-  for (int t = threadIdx.x; t < nh; t += blockDim.x) tws[t] = tw[t];
+  C2* tws = x + fft_buf(EB);   // twiddles staged after the data
+  for (int t = threadIdx.x; t < nh; t += THREADS) tws[t] = tw[t];
   __syncthreads();
-  ifft_dif(x, lognx, tws, cnt);
+  stockham<LOGN, 0, true, THREADS, T>(x, tws, cnt);
   const T inv = T(1) / T(nx);
   const T* ea = reinterpret_cast<const T*>(epi.a);
   const T* eb = reinterpret_cast<const T*>(epi.b);
   T* ed = reinterpret_cast<T*>(epi.delta);
-  for (int t = threadIdx.x; t < cnt * nx; t += blockDim.x) {
-    const int f = t >> lognx, n = t & (nx - 1);
+  for (int t = threadIdx.x; t < cnt * nx; t += THREADS) {
+    const int f = t >> LOGN, n = t & (nx - 1);
     const size_t r = ra + 2 * f;
-    C2 z = x[f * nx + brev(n, lognx)];
+    C2 z = x[pad(t)];
     const size_t ia = r * nx + n, ib = (r + 1) * nx + n;
     T va = z.x * inv, vb = z.y * inv;
     if (epi.kind == 1 && epi.out_lo != nullptr) {
@@ -213,14 +263,6 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
     out[ib] = vb;
   }
   __syncthreads();
-}
-
-template <typename T>
-__global__ void k_rows_inv(const typename C2T<T>::type* __restrict__ spec, T* out, int lognx,
-                           const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
-  using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  rows_inv_core<T>(spec, out, lognx, tw, epi, 2 * (size_t)blockIdx.x, 1, reinterpret_cast<C2*>(smem_raw));
 }
 
 struct SymbolArgs {
@@ -263,45 +305,48 @@ __device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs
   return X;
 }
 
-// x2 cosine transform, symbol division and inverse cosine transform of KC spectral
-// columns per block (complex data; the transform is real so it acts on Re and Im alike).
+// x2 cosine transform, symbol division and inverse cosine transform of the KC =
+// fft_per_block(N) spectral columns k0 .. k0 + KC - 1 (columns at or beyond nh1 are zero and
+// not stored).  The data are complex; the transform is real so it acts on Re and Im alike.
 //   forward  X_m = sum_j x_j cos(pi m (2j+1)/(2N)) via V = FFT(v), v the even/odd reorder:
 //            X_m = Re(w_m Vr_m) + i Re(w_m Vi_m), w_m = exp(-i pi m/(2N)),
 //            Vr_m = (V_m + conj V_{N-m})/2, Vi_m = (V_m - conj V_{N-m})/(2i);
-//   divide   X_m /= sigma(k, m) in FP64;
+//   divide   X_m /= sigma(k, m);
 //   inverse  Z_m = conj(w_m) (X_m - i X_{N-m}) (X_N = 0), z = IFFT(Z)/N,
 //            x_{2n} = z_n, x_{2n+1} = z_{N-1-n}.
-template <typename T, int KC>
-__device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
+template <typename T, int LOGN, int THREADS>
+__device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
                           const typename C2T<T>::type* __restrict__ tw,
                           const typename C2T<T>::type* __restrict__ wd, const SymbolArgs& sym,
                           int k0, typename C2T<T>::type* xs) {
   using C2 = typename C2T<T>::type;
-  const int N = 1 << logny, half = N >> 1;
-  C2* tws = xs + KC * N;     // FFT twiddles, staged once per block
-  C2* wds = tws + half;      // cosine-transform weights
-  for (int t = threadIdx.x; t < half; t += blockDim.x) tws[t] = tw[t];
-  for (int t = threadIdx.x; t < N; t += blockDim.x) wds[t] = wd[t];
-  // load: consecutive threads take consecutive columns of one row (coalesced)
-  for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
-    int cc = idx % KC, r = idx / KC;
-    int k = k0 + cc;
+  constexpr int N = 1 << LOGN, half = N >> 1;
+  constexpr int EB = 8 * THREADS, KC = EB / N;
+  static_assert(KC >= 1, "a block holds 8 points per thread");
+  C2* tws = xs + fft_buf(EB);   // FFT twiddles, staged once per block
+  C2* wds = tws + half;         // cosine-transform weights
+  for (int t = threadIdx.x; t < half; t += THREADS) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < N; t += THREADS) wds[t] = wd[t];
+  // load: consecutive threads take consecutive columns of one row
+  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+    const int cc = idx % KC, r = idx / KC;
+    const int k = k0 + cc;
     C2 val;
     val.x = T(0);
     val.y = T(0);
     if (k < nh1) val = spec[(size_t)r * nh1 + k];
-    int pos = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
-    xs[cc * N + brev(pos, logny)] = val;
+    const int pos = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
+    xs[pad(cc * N + pos)] = val;
   }
   __syncthreads();
-  fft_dit(xs, logny, tws, KC);
+  stockham<LOGN, 0, false, THREADS, T>(xs, tws, KC);
   // pair tasks (m, N - m), m = 0..N/2, of every column
-  for (int t = threadIdx.x; t < KC * (half + 1); t += blockDim.x) {
+  for (int t = threadIdx.x; t < KC * (half + 1); t += THREADS) {
     const int c = t / (half + 1), m = t - c * (half + 1);
-    C2* x = xs + c * N;
     const int k = min(k0 + c, nh1 - 1);
     const int mm = (N - m) & (N - 1);
-    C2 Vm = x[m], Vmm = x[mm];
+    const int im = pad(c * N + m), imm = pad(c * N + mm);
+    const C2 Vm = xs[im], Vmm = xs[imm];
     C2 Xm, Xmm;
     {
       C2 vr, vi, w = wds[m];
@@ -339,17 +384,17 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
       y.y = Xmm.y - xo.x;
       Zmm = cmul(cconj(wds[mm]), y);
     }
-    x[m] = Zm;
-    if (mm != m) x[mm] = Zmm;
+    xs[im] = Zm;
+    if (mm != m) xs[imm] = Zmm;
   }
   __syncthreads();
-  ifft_dif(xs, logny, tws, KC);
+  stockham<LOGN, 0, true, THREADS, T>(xs, tws, KC);
   const T inv = T(1) / T(N);
-  for (int idx = threadIdx.x; idx < KC * N; idx += blockDim.x) {
-    int cc = idx % KC, r = idx / KC;
-    int kk = k0 + cc;
-    int n = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
-    C2 z = xs[cc * N + brev(n, logny)];
+  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+    const int cc = idx % KC, r = idx / KC;
+    const int kk = k0 + cc;
+    const int n = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
+    C2 z = xs[pad(cc * N + n)];
     z.x *= inv;
     z.y *= inv;
     if (kk < nh1) spec[(size_t)r * nh1 + kk] = z;
@@ -357,79 +402,142 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1, int
   __syncthreads();
 }
 
-template <typename T, int KC>
-__global__ void k_cols(typename C2T<T>::type* __restrict__ spec, int nh1, int logny,
-                       const typename C2T<T>::type* __restrict__ tw,
-                       const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym) {
+// Transform lengths select compile-time instantiations: 8 .. 1024 points in 128-thread
+// blocks, 2048 and 4096 points in 512-thread blocks.
+#define IBPF_CASES_128 IBPF_CASE(3) IBPF_CASE(4) IBPF_CASE(5) IBPF_CASE(6) IBPF_CASE(7) \
+  IBPF_CASE(8) IBPF_CASE(9) IBPF_CASE(10)
+#define IBPF_CASES_512 IBPF_CASE(11) IBPF_CASE(12)
+#define IBPF_DISPATCH(THREADS, LOGN_EXPR)                              \
+  if constexpr (THREADS == kFftSmallThreads) {                         \
+    switch (LOGN_EXPR) { IBPF_CASES_128 default: break; }              \
+  } else {                                                             \
+    switch (LOGN_EXPR) { IBPF_CASES_512 default: break; }              \
+  }
+
+// ------------------------------------------------------------------ single-grid launches
+// (allocation-free Poisson entry point, n <= 1024): block b takes the row pairs or the
+// columns b * fft_per_block(n) ..
+template <typename T>
+__global__ void __launch_bounds__(kFftSmallThreads) k_rows_fwd(const T* __restrict__ in,
+    typename C2T<T>::type* __restrict__ spec, int nx, int ny,
+    const typename C2T<T>::type* __restrict__ tw) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cols_core<T, KC>(spec, nh1, logny, tw, wd, sym, blockIdx.x * KC, reinterpret_cast<C2*>(smem_raw));
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int rp = fft_per_block(nx);
+  const int cnt = min(rp, ny / 2 - (int)blockIdx.x * rp);
+  const size_t ra = 2 * (size_t)blockIdx.x * rp;
+#define IBPF_CASE(L) case L: rows_fwd_core<T, L, kFftSmallThreads>(in, spec, tw, ra, cnt, x); break;
+  switch (31 - __clz(nx)) { IBPF_CASES_128 default: break; }
+#undef IBPF_CASE
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftSmallThreads) k_rows_inv(
+    const typename C2T<T>::type* __restrict__ spec, T* out, int nx, int ny,
+    const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int rp = fft_per_block(nx);
+  const int cnt = min(rp, ny / 2 - (int)blockIdx.x * rp);
+  const size_t ra = 2 * (size_t)blockIdx.x * rp;
+#define IBPF_CASE(L) case L: rows_inv_core<T, L, kFftSmallThreads>(spec, out, tw, epi, ra, cnt, x); break;
+  switch (31 - __clz(nx)) { IBPF_CASES_128 default: break; }
+#undef IBPF_CASE
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftSmallThreads) k_cols(
+    typename C2T<T>::type* __restrict__ spec, int nh1, int ny,
+    const typename C2T<T>::type* __restrict__ tw, const typename C2T<T>::type* __restrict__ wd,
+    SymbolArgs sym) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int k0 = blockIdx.x * fft_per_block(ny);
+#define IBPF_CASE(L) case L: cols_core<T, L, kFftSmallThreads>(spec, nh1, tw, wd, sym, k0, x); break;
+  switch (31 - __clz(ny)) { IBPF_CASES_128 default: break; }
+#undef IBPF_CASE
 }
 
 // ------------------------------------------------------------------ batched launches
-template <typename T>
-__global__ void kb_rows_fwd(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
-                            int nblk, int src) {
+// One block per work unit (the grid is nblk blocks); THREADS selects the transform class.
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) kb_rows_fwd(const InstDev<T>* __restrict__ I,
+    const int2* __restrict__ blk, int nblk, int src) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int2 w = blk[b];
-    const InstDev<T>& d = I[w.x];
-    const int cnt = min(kRowPairs, d.ny / 2 - w.y * kRowPairs);
-    rows_fwd_core<T>(src == 0 ? d.Q : d.rhs, d.spec, d.lognx, d.twx, 2 * (size_t)w.y * kRowPairs,
-                     cnt, reinterpret_cast<C2*>(smem_raw));
-  }
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int2 w = blk[b];
+  const InstDev<T>& d = I[w.x];
+  const int rp = fft_per_block(d.nx);
+  const int cnt = min(rp, d.ny / 2 - w.y * rp);
+  const T* in = src == 0 ? d.Q : d.rhs;
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const size_t ra = 2 * (size_t)w.y * rp;
+#define IBPF_CASE(L) case L: rows_fwd_core<T, L, THREADS>(in, d.spec, d.twx, ra, cnt, x); break;
+  IBPF_DISPATCH(THREADS, d.lognx)
+#undef IBPF_CASE
 }
 
-template <typename T>
-__global__ void kb_cols(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
-                        int mode) {
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) kb_cols(const InstDev<T>* __restrict__ I,
+    const int2* __restrict__ blk, int nblk, int mode) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int2 w = blk[b];
-    const InstDev<T>& d = I[w.x];
-    SymbolArgs sym;
-    sym.mode = mode;
-    sym.s_eta2 = d.s_eta2;
-    sym.c0 = d.c0;
-    sym.lamx = d.lamx;
-    sym.lamy = d.lamy;
-    sym.lamx_f = d.lamx_f;
-    sym.lamy_f = d.lamy_f;
-    cols_core<T, kColsKC>(d.spec, d.nx / 2 + 1, d.logny, d.twy, d.wd, sym, w.y * kColsKC,
-                          reinterpret_cast<C2*>(smem_raw));
-  }
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int2 w = blk[b];
+  const InstDev<T>& d = I[w.x];
+  SymbolArgs sym;
+  sym.mode = mode;
+  sym.s_eta2 = d.s_eta2;
+  sym.c0 = d.c0;
+  sym.lamx = d.lamx;
+  sym.lamy = d.lamy;
+  sym.lamx_f = d.lamx_f;
+  sym.lamy_f = d.lamy_f;
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int nh1 = d.nx / 2 + 1, k0 = w.y * fft_per_block(d.ny);
+#define IBPF_CASE(L) case L: cols_core<T, L, THREADS>(d.spec, nh1, d.twy, d.wd, sym, k0, x); break;
+  IBPF_DISPATCH(THREADS, d.logny)
+#undef IBPF_CASE
 }
 
 // kind 1: C^{n+1} into the C^{n-1} slot (compensated in FP32); kind 2: P^{n+1} = P^ + dP
-template <typename T>
-__global__ void kb_rows_inv(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
-                            int nblk, int kind, int cur) {
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restrict__ I,
+    const int2* __restrict__ blk, int nblk, int kind, int cur) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const int2 w = blk[b];
-    const InstDev<T>& d = I[w.x];
-    EpiArgs epi;
-    epi.kind = kind;
-    T* out;
-    if (kind == 1) {
-      epi.a = d.C[cur];
-      epi.b = d.C[1 - cur];
-      epi.a_lo = d.Clo[cur];
-      epi.b_lo = d.Clo[1 - cur];
-      epi.out_lo = d.Clo[1 - cur];
-      out = d.C[1 - cur];
-    } else {
-      epi.a = d.phat;
-      epi.delta = d.dp;
-      out = d.P[1 - cur];
-    }
-    const int cnt = min(kRowPairs, d.ny / 2 - w.y * kRowPairs);
-    rows_inv_core<T>(d.spec, out, d.lognx, d.twx, epi, 2 * (size_t)w.y * kRowPairs, cnt,
-                     reinterpret_cast<C2*>(smem_raw));
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int2 w = blk[b];
+  const InstDev<T>& d = I[w.x];
+  EpiArgs epi;
+  epi.kind = kind;
+  T* out;
+  if (kind == 1) {
+    epi.a = d.C[cur];
+    epi.b = d.C[1 - cur];
+    epi.a_lo = d.Clo[cur];
+    epi.b_lo = d.Clo[1 - cur];
+    epi.out_lo = d.Clo[1 - cur];
+    out = d.C[1 - cur];
+  } else {
+    epi.a = d.phat;
+    epi.delta = d.dp;
+    out = d.P[1 - cur];
   }
+  const int rp = fft_per_block(d.nx);
+  const int cnt = min(rp, d.ny / 2 - w.y * rp);
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const size_t ra = 2 * (size_t)w.y * rp;
+#define IBPF_CASE(L) case L: rows_inv_core<T, L, THREADS>(d.spec, out, d.twx, epi, ra, cnt, x); break;
+  IBPF_DISPATCH(THREADS, d.lognx)
+#undef IBPF_CASE
 }
 
 template <typename T>
@@ -479,10 +587,14 @@ cudaError_t tables_t(Instance& in) {
   cudaMemcpy(in.twy, twy.data(), sizeof(C2) * twy.size(), cudaMemcpyHostToDevice);
   e = cudaMemcpy(in.wdct, wd.data(), sizeof(C2) * wd.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  // rows of up to 4096 points need 64 KiB of shared memory (FP64)
-  cudaFuncSetAttribute(kb_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(kb_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(kb_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  // the 4096-point class needs up to 120 KiB of shared memory (FP64)
+  const int att = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(kb_rows_fwd<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_rows_inv<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_cols<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_rows_fwd<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_rows_inv<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_cols<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   return cudaGetLastError();
 }
 
@@ -492,16 +604,46 @@ template <typename T>
 int spectral_solve_batch(const BatchPlan& plan, int mode, int cur, cudaStream_t s,
                          Recorder* rec) {
   const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
-  kb_rows_fwd<T><<<plan.nblk[kFamRows], plan.rows_threads, plan.rows_smem, s>>>(
-      I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode);
-  if (rec) rec->mark("rows_fwd", s);
-  kb_cols<T><<<plan.nblk[kFamCols], plan.cols_threads, plan.cols_smem, s>>>(
-      I, plan.d_blk[kFamCols], plan.nblk[kFamCols], mode);
-  if (rec) rec->mark("cols_solve", s);
-  kb_rows_inv<T><<<plan.nblk[kFamRows], plan.rows_threads, plan.rows_smem, s>>>(
-      I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode == 0 ? 1 : 2, cur);
-  if (rec) rec->mark("rows_inv", s);
-  return 3;
+  constexpr int S = kFftSmallThreads, L = kFftLargeThreads;
+  const int kind = mode == 0 ? 1 : 2;
+  int n = 0;
+  if (plan.nblk[kFamRows]) {
+    kb_rows_fwd<T, S><<<plan.nblk[kFamRows], S, plan.rows_smem[0], s>>>(
+        I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode);
+    if (rec) rec->mark("rows_fwd", s);
+    ++n;
+  }
+  if (plan.nblk[kFamRowsL]) {
+    kb_rows_fwd<T, L><<<plan.nblk[kFamRowsL], L, plan.rows_smem[1], s>>>(
+        I, plan.d_blk[kFamRowsL], plan.nblk[kFamRowsL], mode);
+    if (rec) rec->mark("rows_fwd", s);
+    ++n;
+  }
+  if (plan.nblk[kFamCols]) {
+    kb_cols<T, S><<<plan.nblk[kFamCols], S, plan.cols_smem[0], s>>>(
+        I, plan.d_blk[kFamCols], plan.nblk[kFamCols], mode);
+    if (rec) rec->mark("cols_solve", s);
+    ++n;
+  }
+  if (plan.nblk[kFamColsL]) {
+    kb_cols<T, L><<<plan.nblk[kFamColsL], L, plan.cols_smem[1], s>>>(
+        I, plan.d_blk[kFamColsL], plan.nblk[kFamColsL], mode);
+    if (rec) rec->mark("cols_solve", s);
+    ++n;
+  }
+  if (plan.nblk[kFamRows]) {
+    kb_rows_inv<T, S><<<plan.nblk[kFamRows], S, plan.rows_smem[0], s>>>(
+        I, plan.d_blk[kFamRows], plan.nblk[kFamRows], kind, cur);
+    if (rec) rec->mark("rows_inv", s);
+    ++n;
+  }
+  if (plan.nblk[kFamRowsL]) {
+    kb_rows_inv<T, L><<<plan.nblk[kFamRowsL], L, plan.rows_smem[1], s>>>(
+        I, plan.d_blk[kFamRowsL], plan.nblk[kFamRowsL], kind, cur);
+    if (rec) rec->mark("rows_inv", s);
+    ++n;
+  }
+  return n;
 }
 template int spectral_solve_batch<double>(const BatchPlan&, int, int, cudaStream_t, Recorder*);
 template int spectral_solve_batch<float>(const BatchPlan&, int, int, cudaStream_t, Recorder*);
@@ -510,25 +652,23 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
                         double c0, double2* spec, const double* lamx, const double* lamy,
                         const double2* twx, const double2* twy, const double2* wd,
                         cudaStream_t s) {
-  int lognx = 0, logny = 0;
-  while ((1 << lognx) < nx) ++lognx;
-  while ((1 << logny) < ny) ++logny;
   const int nh1 = nx / 2 + 1;
-  const int trow = nx / 2 < 512 ? nx / 2 : 512;
-  k_rows_fwd<double><<<ny / 2, trow, sizeof(double2) * (nx + nx / 2), s>>>(rhs, spec, lognx, twx);
+  const int rp = fft_per_block(nx), cp = fft_per_block(ny);
+  constexpr int S = kFftSmallThreads;
+  // nx, ny <= 1024 here: the row buffers take at most 26 KiB and the column buffers 42 KiB
+  // of shared memory, below the default limit, so this path sets no function attributes
+  const size_t rsm = sizeof(double2) * (fft_buf(8 * S) + nx / 2);
+  const size_t csm = sizeof(double2) * (fft_buf(8 * S) + ny / 2 + ny);
+  k_rows_fwd<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(rhs, spec, nx, ny, twx);
   SymbolArgs sym;
   sym.mode = mode;
   sym.s_eta2 = s_eta2;
   sym.c0 = c0;
   sym.lamx = lamx;
   sym.lamy = lamy;
-  // one column per block: data, twiddles and weights take at most 40 KiB of shared memory
-  // for ny <= 1024, below the default limit, so this path needs no function attributes
-  k_cols<double, 1><<<nh1, 256, sizeof(double2) * (ny + ny / 2 + ny), s>>>(spec, nh1, logny, twy,
-                                                                         wd, sym);
+  k_cols<double><<<(nh1 + cp - 1) / cp, S, csm, s>>>(spec, nh1, ny, twy, wd, sym);
   EpiArgs plain;
-  k_rows_inv<double><<<ny / 2, trow, sizeof(double2) * (nx + nx / 2), s>>>(spec, out, lognx, twx,
-                                                                           plain);
+  k_rows_inv<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, ny, twx, plain);
   return 3;
 }
 

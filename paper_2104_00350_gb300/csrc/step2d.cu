@@ -776,6 +776,7 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
   const int n = (int)c.inst.size();
   std::vector<InstDev<T>> host(n);
   std::vector<int2> fam[kNumFam];
+  int rmax[2] = {0, 0}, cmax[2] = {0, 0};   // longest row / column per transform class
   plan.max_nx = plan.max_ny = 0;
   for (int k = 0; k < n; ++k) {
     Instance& in = c.inst[k];
@@ -820,10 +821,14 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.status = in.status;
     const int ntiles = d.gx * ((in.ny + kTileH - 1) / kTileH);
     for (int b = 0; b < ntiles; ++b) fam[kFamCell].push_back(make_int2(k, b));
-    for (int b = 0; b < (in.ny / 2 + kRowPairs - 1) / kRowPairs; ++b)
-      fam[kFamRows].push_back(make_int2(k, b));
-    const int ncg = (in.nx / 2 + 1 + kColsKC - 1) / kColsKC;
-    for (int b = 0; b < ncg; ++b) fam[kFamCols].push_back(make_int2(k, b));
+    const int rp = fft_per_block(in.nx), cp = fft_per_block(in.ny);
+    const int rl = fft_threads(in.nx) == kFftLargeThreads, cl = fft_threads(in.ny) == kFftLargeThreads;
+    for (int b = 0; b < (in.ny / 2 + rp - 1) / rp; ++b)
+      fam[rl ? kFamRowsL : kFamRows].push_back(make_int2(k, b));
+    const int ncg = (in.nx / 2 + 1 + cp - 1) / cp;
+    for (int b = 0; b < ncg; ++b) fam[cl ? kFamColsL : kFamCols].push_back(make_int2(k, b));
+    rmax[rl] = in.nx > rmax[rl] ? in.nx : rmax[rl];
+    cmax[cl] = in.ny > cmax[cl] ? in.ny : cmax[cl];
     for (int b = 0; b < (in.tab.ng + kGhostChunk - 1) / kGhostChunk; ++b)
       fam[kFamGhost].push_back(make_int2(k, b));
     const int nf = in.tab.nfu + in.tab.nfv;
@@ -846,10 +851,11 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
       if (e != cudaSuccess) return e;
     }
   }
-  plan.rows_threads = 256;
-  plan.cols_threads = 256;
-  plan.rows_smem = sizeof(C2) * (plan.max_nx * kRowPairs + plan.max_nx / 2);
-  plan.cols_smem = sizeof(C2) * (plan.max_ny * kColsKC + plan.max_ny / 2 + plan.max_ny);
+  for (int c = 0; c < 2; ++c) {
+    const int eb = 8 * (c ? kFftLargeThreads : kFftSmallThreads);
+    plan.rows_smem[c] = sizeof(C2) * (fft_buf(eb) + rmax[c] / 2);
+    plan.cols_smem[c] = sizeof(C2) * (fft_buf(eb) + cmax[c] / 2 + cmax[c]);
+  }
   return cudaSuccess;
 }
 
