@@ -39,19 +39,27 @@ THETAS = (45.0, 90.0, 135.0)
 SLIPS = (0.0, 0.01)
 L2_FLUSH_BYTES = 256 << 20
 
-# algorithmic bytes per cell of one launch, in field words (8 B FP64 / 4 B FP32) plus the
-# FP64 geometry words (alpha) each kernel must read; see the design doc for the derivation.
-KERNEL_WORDS = {          # name: (field words per cell, fp64 words per cell)
-    "ch_h": (3.0, 0.0),          # C, Co -> h
-    "ch_rhs": (8.0, 0.0),        # C, Co, u, uo, v, vo, h -> R
-    "rows_fwd": (2.0, 0.0),      # real row in, half spectrum (complex) out
-    "cols_solve": (2.0, 0.0),    # spectrum in and out
-    "rows_inv": (4.0, 0.0),      # half spectrum in; P^ in, dP and P out (pressure solve)
-    "chem_pot": (2.0, 0.0),      # C -> phi
-    "predict": (10.0, 2.0),      # C, phi, u, v, Hu, Hv -> Hu, Hv, u**, v**; alpha_u, alpha_v
-    "poisson_rhs": (7.0, 0.0),   # C, P, Po, u**, v** -> rhs, P^
-    "correct": (7.0, 0.0),       # C, P1, P^, u**, v** -> u, v
+# Algorithmic traffic per cell and per step, summed over the launches of each kernel name:
+# field words read once and written once (FP32 form, FP64 form) plus FP64 geometry words.
+# See the design doc for the derivation.
+KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form table words)
+    "ch_h": (3, 3, 0),           # C, Co -> h
+    "ch_rhs": (8, 8, 0),         # C, Co, u, uo, v, vo, h -> R
+    "rows_fwd": (4, 4, 0),       # 2 launches: real rows in, half spectrum out
+    "cols_solve": (4, 4, 0),     # 2 launches: half spectrum in and out
+    "rows_inv": (11, 8, 0),      # CH: spectrum, C, Co (+ lo parts) -> C (+ lo);
+                                 # Poisson: spectrum, P^ -> dP, P
+    "chem_pot": (2, 2, 0),       # C -> phi
+    "predict": (12, 10, 2),      # C, phi, u, v, Hu, Hv -> Hu, Hv, u**, v**; alpha_u, alpha_v
+                                 # (FP32 copies in the FP32 form, FP64 tables otherwise)
+    "poisson_rhs": (7, 7, 0),    # C, P, Po, u**, v** -> rhs, P^
+    "correct": (8, 7, 0),        # C (+ lo for the mass), dP, P^, u**, v** -> u, v
 }
+
+
+def kernel_step_bytes(name: str, esz: int, cells: int) -> float:
+    w32, w64, g = KERNEL_STEP_WORDS.get(name, (0, 0, 0))
+    return float((w32 * 4 if esz == 4 else w64 * 8 + g * 8) * cells)
 
 
 def workload_cases():
@@ -253,6 +261,36 @@ def kernel_flops64(name: str, nx: int, ny: int) -> float:
     return table.get(name, 0.0)
 
 
+def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form):
+    """Roofline of the dominant kernel and per-kernel table from an event-timed pass:
+    ktot[name] = total ms over `steps` steps, kcount[name] = launches."""
+    dom = max(ktot, key=ktot.get)
+    per_launch_ms = ktot[dom] / kcount[dom]
+    tot = sum(ktot.values())
+    table = {}
+    for k, v in sorted(ktot.items(), key=lambda x: -x[1]):
+        ent = {"us_per_step": round(1e3 * v / steps, 2), "share": round(v / tot, 4)}
+        if esz == 4 and k in KERNEL_STEP_WORDS:
+            gbs = kernel_step_bytes(k, esz, cells) * steps / (v * 1e-3) / 1e9
+            ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
+        table[k] = ent
+    if esz == 4:
+        alg = kernel_step_bytes(dom, esz, cells) * steps / kcount[dom]
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": read_traffic(dom, form), "alg_bytes_per_launch": alg}
+    else:
+        alg = kernel_flops64(dom, case0.nx, case0.ny) * cells
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "peak_kind": "derived (FP64 pipe)",
+                "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": read_traffic(dom, form), "alg_flops_per_launch": alg}
+    roof.update({"per_launch_us": per_launch_ms * 1e3, "kernels": table})
+    return roof
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -346,26 +384,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             _, ktot, kcount = timed_steps(solver, args.steps, collect_kernels=True)
             ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
-            dom = max(ktot, key=ktot.get)
-            per_launch_ms = ktot[dom] / kcount[dom]
-            tot = sum(ktot.values())
-            share = {k: round(v / tot, 4) for k, v in sorted(ktot.items(), key=lambda x: -x[1])}
-            launch_cells = cells   # one batched launch covers every instance
-            if prec == ibpf.FP32:
-                fw, gw = KERNEL_WORDS.get(dom, (0.0, 0.0))
-                alg = (fw * esz + gw * 8) * launch_cells
-                achieved = alg / (per_launch_ms * 1e-3) / 1e9
-                roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                        "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                        "traffic": read_traffic(dom, form), "alg_bytes_per_launch": alg}
-            else:
-                alg = kernel_flops64(dom, cl[0].nx, cl[0].ny) * launch_cells
-                achieved = alg / (per_launch_ms * 1e-3) / 1e9
-                roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
-                        "peak": FP64_PEAK_GFLOPS, "peak_kind": "derived (FP64 pipe)",
-                        "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                        "traffic": read_traffic(dom, form), "alg_flops_per_launch": alg}
-            roof.update({"per_launch_us": per_launch_ms * 1e3, "kernel_time_share": share})
+            roof = roofline(ktot, kcount, args.steps, cells, esz, cl[0], peak, peak_kind, form)
         except Exception as exc:   # keep the headline line even if the timing pass fails
             roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                     "frac": None, "traffic": None, "error": str(exc)[:200]}
@@ -421,11 +440,21 @@ def run_ours(args):
         esteps = max(1, min(args.steps, 50))
         ems, _, _ = timed_steps(esolver, esteps)
         ems = max_over_ranks([ems], dist, "cuda")[0]
+        try:
+            ibpf.ib_pf_set_kernel_timing(esolver.ctx, True)
+            esolver.step(1)
+            torch.cuda.synchronize()
+            _, ktot, kcount = timed_steps(esolver, esteps, collect_kernels=True)
+            ibpf.ib_pf_set_kernel_timing(esolver.ctx, False)
+            eroof = roofline(ktot, kcount, esteps, ecells, 4, ecl[0], peak, peak_kind, "fp32")
+        except Exception as exc:
+            eroof = {"error": str(exc)[:200]}
         ens = {"value": aggregate_rate(world, ecells, esteps, ems * 1e-3), "unit": UNIT,
                "ms_per_step": ems / esteps, "steps": esteps, "instances": len(ecl),
                "cells": ecells, "dtype": "f32",
                "gpu_launches": int(esolver.query(ibpf.Q_LAUNCHES)) * esteps,
-               "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls"}
+               "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls",
+               "roofline": eroof}
         esolver.close()
     clocks = sampler.stop()
 

@@ -76,6 +76,8 @@ struct InstDev {
   T* gv;
   T* fval;
   Tables tab;
+  const T* au;                // face fractions alpha_u, alpha_v in the field type
+  const T* av;
   const double* lamx;
   const double* lamy;
   const float* lamx_f;
@@ -93,6 +95,7 @@ struct InstDev {
 // host-side bookkeeping of the batched launches (owned by the context)
 struct BatchPlan {
   void* d_inst = nullptr;              // InstDev<T>[n]
+  void* alpha_f = nullptr;             // FP32 form: FP32 copies of alpha_u, alpha_v
   int2* d_blk[kNumFam] = {};           // (instance, local block) per launched block
   int nblk[kNumFam] = {};
   size_t rows_smem[2] = {}, cols_smem[2] = {};   // small / large transform class

@@ -240,7 +240,11 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
       ctx->err = "spectral workspace allocation failed";
       return bail(IB_PF_E_CUDA);
     }
-    const int nblk = ((in.nx + 31) / 32) * ((in.ny + 7) / 8);
+    // partial sums: one per cell tile of the step's reduction, or per 256-cell block of
+    // the stand-alone reduction, whichever is more
+    const int ntile = ((in.nx + kTileX - 1) / kTileX) * ((in.ny + kTileH - 1) / kTileH);
+    const int nred = (in.nx * in.ny + 255) / 256;
+    const int nblk = ntile > nred ? ntile : nred;
     in.nblk_red = nblk;
     if (cudaMalloc((void**)&in.partial, sizeof(double) * nblk) != cudaSuccess ||
         cudaMalloc((void**)&in.ticket, sizeof(unsigned)) != cudaSuccess ||

@@ -282,18 +282,13 @@ struct SymbolArgs {
 template <typename T, typename C2>
 __device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs& sym) {
   if constexpr (sizeof(T) == 8) {
+    // one reciprocal per point: the quotient is within 1.5 ulp of X / sigma
     const double L = sym.lamy[m] + sym.lamx[k];
-    if (sym.mode == 0) {
-      const double sg = L * L - sym.s_eta2 * L + sym.c0;
-      X.x = (T)((double)X.x / sg);
-      X.y = (T)((double)X.y / sg);
-    } else if (L == 0.0) {
-      X.x = T(0);
-      X.y = T(0);
-    } else {
-      X.x = (T)((double)X.x / L);
-      X.y = (T)((double)X.y / L);
-    }
+    double r;
+    if (sym.mode == 0) r = 1.0 / (L * L - sym.s_eta2 * L + sym.c0);
+    else r = (L == 0.0) ? 0.0 : 1.0 / L;
+    X.x = X.x * r;
+    X.y = X.y * r;
   } else {
     const float L = sym.lamy_f[m] + sym.lamx_f[k];
     float r;

@@ -41,9 +41,8 @@ __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : 
 // which is small, so the solve's rounding stays relative to the change of C in one step.
 // k_ch_h writes h; k_ch_rhs writes R.
 template <typename T>
-__device__ __forceinline__ void ch_h_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                          const T* __restrict__ Co, T* __restrict__ hout,
-                                          int i, int j) {
+__device__ __forceinline__ T ch_h_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                       const T* __restrict__ Co, int i, int j) {
   const int nx = a.nx, ny = a.ny;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
@@ -57,15 +56,15 @@ __device__ __forceinline__ void ch_h_cell(const StepArgs<T>& a, const T* __restr
                   T(4) * b0) * a.inv_h2;
   const T d = C[r + i] - Co[r + i];
   const T ct = C[r + i] + d;
-  hout[r + i] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+  return ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
 }
 
 template <typename T>
-__device__ __forceinline__ void ch_rhs_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                            const T* __restrict__ Co, const T* __restrict__ u,
-                                            const T* __restrict__ uo, const T* __restrict__ v,
-                                            const T* __restrict__ vo, const T* __restrict__ hf,
-                                            T* __restrict__ Q, int i, int j) {
+__device__ __forceinline__ T ch_rhs_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                         const T* __restrict__ Co, const T* __restrict__ u,
+                                         const T* __restrict__ uo, const T* __restrict__ v,
+                                         const T* __restrict__ vo, const T* __restrict__ hf,
+                                         int i, int j) {
   const int nx = a.nx, ny = a.ny;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
@@ -81,7 +80,7 @@ __device__ __forceinline__ void ch_rhs_cell(const StepArgs<T>& a, const T* __res
   const T div = (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
   const T lap = (((hf[r + ip] + hf[r + im]) + (hf[(size_t)jn * nx + i] + hf[(size_t)js * nx + i])) -
                  T(4) * hf[r + i]) * a.inv_h2;
-  Q[r + i] = lap - a.pe_eta2 * div;
+  return lap - a.pe_eta2 * div;
 }
 
 // ------------------------------------------------------------ a3: contact-angle ghost fill
@@ -126,15 +125,15 @@ __device__ __forceinline__ void fill_C_ghost(const StepArgs<T>& a, const Tables&
 // ------------------------------------------------------------- a4: chemical potential
 // phi = psi'(C) - Cn^2 lap C on every cell (Eq. Chemical-Potential, nondimensional)
 template <typename T>
-__device__ __forceinline__ void chem_pot_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                              T* __restrict__ phi, int i, int j) {
+__device__ __forceinline__ T chem_pot_cell(const StepArgs<T>& a, const T* __restrict__ C, int i,
+                                           int j) {
   const int nx = a.nx, ny = a.ny;
   const size_t r = (size_t)j * nx;
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
   const T c0 = C[r + i];
   const T lap = (((C[r + wrap_p(i, nx)] + C[r + wrap_m(i, nx)]) +
                   (C[(size_t)jn * nx + i] + C[(size_t)js * nx + i])) - T(4) * c0) * a.inv_h2;
-  phi[r + i] = (c0 * c0 * c0 - c0) - a.eta2 * lap;
+  return (c0 * c0 * c0 - c0) - a.eta2 * lap;
 }
 
 // zero normal gradient of phi at the wall: phi_G = phi_M (Sec. 4.2.2, last paragraph)
@@ -186,7 +185,7 @@ __device__ __forceinline__ void predict_stage(const StepArgs<T>& a, const T* __r
 template <typename T>
 __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const PredictSmem<T>& sm,
                                               int i, int j, int lx, int ly, T hu_old, T hv_old,
-                                              double au, double av, T* __restrict__ Hu,
+                                              T au, T av, T* __restrict__ Hu,
                                               T* __restrict__ Hv, T* __restrict__ uss,
                                               T* __restrict__ vss) {
   const int nx = a.nx;
@@ -223,7 +222,7 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * ((cR - cL) * a.inv_h) / rho_f;
     const T ustar = Us(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hu_old) + st);
     Hu[r + i] = H;
-    uss[r + i] = (T)au * ustar;
+    uss[r + i] = au * ustar;
   }
   // ---- x2-face (i, j), 1 <= j <= ny-1: cells (i, j-1) and (i, j)
   if (j >= 1) {
@@ -239,7 +238,7 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * ((cA - cB) * a.inv_h) / rho_f;
     const T vstar = Vs(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hv_old) + st);
     Hv[r + i] = H;
-    vss[r + i] = (T)av * vstar;
+    vss[r + i] = av * vstar;
   }
 }
 
@@ -328,8 +327,7 @@ template <typename T>
 __device__ __forceinline__ void poisson_rhs_cell(const StepArgs<T>& a, const T* __restrict__ C,
                                                  const T* __restrict__ P, const T* __restrict__ Po,
                                                  const T* __restrict__ uss, const T* __restrict__ vss,
-                                                 T* __restrict__ rhs, T* __restrict__ phat, int i,
-                                                 int j) {
+                                                 T& rhs, T& phat, int i, int j) {
   const int nx = a.nx, ny = a.ny;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const size_t r = (size_t)j * nx;
@@ -345,36 +343,34 @@ __device__ __forceinline__ void poisson_rhs_cell(const StepArgs<T>& a, const T* 
     gy_n = (a.rho0 / rho(T(0.5) * (C[r + i] + C[r + nx + i]))) * ((ph(r + nx + i) - p0) * a.inv_h);
   const T div_g = (gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h;
   const T div_u = (uss[r + ip] - uss[r + i]) * a.inv_h + (vss[r + nx + i] - vss[r + i]) * a.inv_h;
-  rhs[r + i] = (a.rho0 * a.inv_dt) * div_u - div_g;
-  phat[r + i] = p0;
+  rhs = (a.rho0 * a.inv_dt) * div_u - div_g;
+  phat = p0;
 }
 
 // ------------------------------------------------- a8: correction + status and mass
 // Eq. correction, u^{n+1} = u** - dt [ (1/rho0) grad P^{n+1} + (1/rho_f - 1/rho0) grad P^ ],
 // written with the increment: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ].
-// Returns this cell's C^{n+1} (FP64, compensated part included) and flags non-finite values.
+// Returns u^{n+1} (and v^{n+1} for j >= 1) of this cell's faces; flags non-finite values.
 template <typename T>
 __device__ __forceinline__ void correct_cell(const StepArgs<T>& a, const T* __restrict__ C,
                                              const T* __restrict__ dP, const T* __restrict__ phat,
-                                             T* __restrict__ uss, T* __restrict__ vss, int i, int j,
-                                             int& bad) {
+                                             const T* __restrict__ uss, const T* __restrict__ vss,
+                                             int i, int j, T& un, T& vn, int& bad) {
   const int nx = a.nx;
   const int im = wrap_m(i, nx);
   const size_t r = (size_t)j * nx;
   auto rho = [&](T c) { return a.rho_a + a.rho_b * clamp1(c); };
   {
     const T rho_f = rho(T(0.5) * (C[r + im] + C[r + i]));
-    const T un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
-                                      a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
-    uss[r + i] = un;
+    un = uss[r + i] - a.dt * (((phat[r + i] - phat[r + im]) * a.inv_h) / rho_f +
+                              a.inv_rho0 * ((dP[r + i] - dP[r + im]) * a.inv_h));
     bad |= !isfinite(un);
   }
   if (j >= 1) {
     const size_t rs = r - nx;
     const T rho_f = rho(T(0.5) * (C[rs + i] + C[r + i]));
-    const T vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
-                                      a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
-    vss[r + i] = vn;
+    vn = vss[r + i] - a.dt * (((phat[r + i] - phat[rs + i]) * a.inv_h) / rho_f +
+                              a.inv_rho0 * ((dP[r + i] - dP[rs + i]) * a.inv_h));
     bad |= !isfinite(vn);
   }
   bad |= !isfinite(C[r + i]);
@@ -516,9 +512,11 @@ StepArgs<T> make_args(const Instance& in) {
 }
 
 // ------------------------------------------------------------ batched launches
-// Each kernel walks the block table of its family: entry b = (instance, block within the
-// instance).  Cell tiles are 32 x 32 cells (32 x 8 threads, 4 rows each); ghost and face
+// Block b of a launch takes entry b of its family's block table: (instance, block within
+// the instance).  Cell tiles are 32 x 32 cells (32 x 8 threads, 4 rows each); ghost and face
 // families use chunks of 128.
+
+#define IBPF_CELL_BOUNDS __launch_bounds__(kTileX * kTileY)
 
 // first cell of this thread in tile lb: column i, rows jb, jb + 8, jb + 16, jb + 24
 template <typename T>
@@ -528,35 +526,53 @@ __device__ __forceinline__ void tile_base(const InstDev<T>& d, int lb, int& i, i
 }
 
 template <typename T>
-__global__ void kb_ch_h(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+__global__ void IBPF_CELL_BOUNDS kb_ch_h(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
                         int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     int i, jb;
     tile_base(d, w_.y, i, jb);
+    // all rows are computed before any is stored, so that the loads of every row are in
+    // flight together (a store could alias a later row's loads as far as the compiler knows)
+    T out[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
-      if (i < d.nx && j < d.ny) ch_h_cell(d.a, d.C[cur], d.C[1 - cur], d.phi, i, j);
+      if (i < d.nx && j < d.ny) out[q] = ch_h_cell(d.a, d.C[cur], d.C[1 - cur], i, j);
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) d.phi[(size_t)j * d.nx + i] = out[q];
     }
   }
 }
 
 template <typename T>
-__global__ void kb_ch_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+__global__ void IBPF_CELL_BOUNDS kb_ch_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
                           int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     int i, jb;
     tile_base(d, w_.y, i, jb);
+    T out[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
       if (i < d.nx && j < d.ny)
-        ch_rhs_cell(d.a, d.C[cur], d.C[1 - cur], d.U[cur], d.U[1 - cur], d.V[cur], d.V[1 - cur],
-                    d.phi, d.Q, i, j);
+        out[q] = ch_rhs_cell(d.a, d.C[cur], d.C[1 - cur], d.U[cur], d.U[1 - cur], d.V[cur],
+                             d.V[1 - cur], d.phi, i, j);
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) d.Q[(size_t)j * d.nx + i] = out[q];
     }
   }
 }
@@ -565,7 +581,9 @@ __global__ void kb_ch_rhs(const InstDev<T>* __restrict__ I, const int2* __restri
 template <typename T>
 __global__ void kb_fill_C(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
                           int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int g = w_.y * kGhostChunk + threadIdx.x;
@@ -574,17 +592,25 @@ __global__ void kb_fill_C(const InstDev<T>* __restrict__ I, const int2* __restri
 }
 
 template <typename T>
-__global__ void kb_chem_pot(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+__global__ void IBPF_CELL_BOUNDS kb_chem_pot(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                             int nblk, int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     int i, jb;
     tile_base(d, w_.y, i, jb);
+    T out[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
-      if (i < d.nx && j < d.ny) chem_pot_cell(d.a, d.C[1 - cur], d.phi, i, j);
+      if (i < d.nx && j < d.ny) out[q] = chem_pot_cell(d.a, d.C[1 - cur], i, j);
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) d.phi[(size_t)j * d.nx + i] = out[q];
     }
   }
 }
@@ -592,7 +618,9 @@ __global__ void kb_chem_pot(const InstDev<T>* __restrict__ I, const int2* __rest
 template <typename T>
 __global__ void kb_fill_phi(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                             int nblk) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int g = w_.y * kGhostChunk + threadIdx.x;
@@ -602,17 +630,19 @@ __global__ void kb_fill_phi(const InstDev<T>* __restrict__ I, const int2* __rest
 
 // u** goes into the u^{n-1} slot (1 - cur)
 template <typename T>
-__global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+__global__ void IBPF_CELL_BOUNDS kb_predict(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                            int nblk, int cur) {
   __shared__ PredictSmem<T> sm;
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int i0 = (w_.y % d.gx) * kTileX, j0 = (w_.y / d.gx) * kTileH;
     const int i = i0 + threadIdx.x;
     // own-face history and penalisation factors, fetched while the tile is staged
     T huo[kRowsPerThread], hvo[kRowsPerThread];
-    double au[kRowsPerThread], av[kRowsPerThread];
+    T au[kRowsPerThread], av[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = j0 + threadIdx.y + q * kTileY;
@@ -620,8 +650,8 @@ __global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restr
       const size_t c = (size_t)j * d.nx + i;
       huo[q] = ok ? d.Hu[c] : T(0);
       hvo[q] = ok ? d.Hv[c] : T(0);
-      au[q] = ok ? d.tab.alpha_u[c] : 0.0;
-      av[q] = ok ? d.tab.alpha_v[c] : 0.0;
+      au[q] = ok ? d.au[c] : T(0);
+      av[q] = ok ? d.av[c] : T(0);
     }
     predict_stage(d.a, d.C[1 - cur], d.phi, d.U[cur], d.V[cur], i0, j0, sm);
     __syncthreads();
@@ -640,7 +670,9 @@ __global__ void kb_predict(const InstDev<T>* __restrict__ I, const int2* __restr
 template <typename T>
 __global__ void kb_fill_u(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
                           int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int g = w_.y * kGhostChunk + threadIdx.x;
@@ -651,7 +683,9 @@ __global__ void kb_fill_u(const InstDev<T>* __restrict__ I, const int2* __restri
 template <typename T>
 __global__ void kb_face_values(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                                int nblk, int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int f = w_.y * kGhostChunk + threadIdx.x;
@@ -662,7 +696,9 @@ __global__ void kb_face_values(const InstDev<T>* __restrict__ I, const int2* __r
 template <typename T>
 __global__ void kb_face_scatter(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                                 int nblk, int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int f = w_.y * kGhostChunk + threadIdx.x;
@@ -671,41 +707,63 @@ __global__ void kb_face_scatter(const InstDev<T>* __restrict__ I, const int2* __
 }
 
 template <typename T>
-__global__ void kb_poisson_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+__global__ void IBPF_CELL_BOUNDS kb_poisson_rhs(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                                int nblk, int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     int i, jb;
     tile_base(d, w_.y, i, jb);
+    T o_rhs[kRowsPerThread], o_ph[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
       if (i < d.nx && j < d.ny)
         poisson_rhs_cell(d.a, d.C[1 - cur], d.P[cur], d.P[1 - cur], d.U[1 - cur], d.V[1 - cur],
-                         d.rhs, d.phat, i, j);
+                         o_rhs[q], o_ph[q], i, j);
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) {
+        d.rhs[(size_t)j * d.nx + i] = o_rhs[q];
+        d.phat[(size_t)j * d.nx + i] = o_ph[q];
+      }
     }
   }
 }
 
 template <typename T>
-__global__ void kb_correct(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+__global__ void IBPF_CELL_BOUNDS kb_correct(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                            int nblk, int cur) {
-  for (int b_ = blockIdx.x; b_ < nblk; b_ += gridDim.x) {
+  {   // one block per work unit (the grid is nblk blocks)
+    const int b_ = blockIdx.x;
+    if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     int i, jb, bad = 0;
     tile_base(d, w_.y, i, jb);
     T s_hi = T(0), s_lo = T(0);
+    T o_u[kRowsPerThread], o_v[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
       if (i < d.nx && j < d.ny) {
-        correct_cell(d.a, d.C[1 - cur], d.dp, d.phat, d.U[1 - cur], d.V[1 - cur],
-                     i, j, bad);
+        correct_cell(d.a, d.C[1 - cur], d.dp, d.phat, d.U[1 - cur], d.V[1 - cur], i, j, o_u[q],
+                     o_v[q], bad);
         const size_t c = (size_t)j * d.nx + i;
         const T lo = d.Clo[1 - cur] ? d.Clo[1 - cur][c] : T(0);
         pair_add(s_hi, s_lo, d.C[1 - cur][c], lo);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const int j = jb + q * kTileY;
+      if (i < d.nx && j < d.ny) {
+        d.U[1 - cur][(size_t)j * d.nx + i] = o_u[q];
+        if (j >= 1) d.V[1 - cur][(size_t)j * d.nx + i] = o_v[q];
       }
     }
     if (bad) atomicOr(d.status, 1);
@@ -837,7 +895,38 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     plan.max_nx = in.nx > plan.max_nx ? in.nx : plan.max_nx;
     plan.max_ny = in.ny > plan.max_ny ? in.ny : plan.max_ny;
   }
-  cudaError_t e = cudaMalloc(&plan.d_inst, sizeof(InstDev<T>) * n);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 8) {
+    for (int k = 0; k < n; ++k) {
+      host[k].au = c.inst[k].tab.alpha_u;
+      host[k].av = c.inst[k].tab.alpha_v;
+    }
+  } else {
+    // the FP32 form reads the face fractions in FP32 (rounded once from the FP64 tables)
+    size_t tot = 0;
+    for (int k = 0; k < n; ++k) tot += (size_t)(2 * c.inst[k].ny + 1) * c.inst[k].nx;
+    e = cudaMalloc(&plan.alpha_f, sizeof(float) * tot);
+    if (e != cudaSuccess) return e;
+    float* dst = (float*)plan.alpha_f;
+    std::vector<double> hd;
+    std::vector<float> hf;
+    for (int k = 0; k < n; ++k) {
+      const Instance& in = c.inst[k];
+      const size_t nu = (size_t)in.ny * in.nx, nv = nu + in.nx;
+      hd.resize(nu + nv);
+      e = cudaMemcpy(hd.data(), in.tab.alpha_u, sizeof(double) * nu, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return e;
+      e = cudaMemcpy(hd.data() + nu, in.tab.alpha_v, sizeof(double) * nv, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return e;
+      hf.assign(hd.begin(), hd.end());
+      e = cudaMemcpy(dst, hf.data(), sizeof(float) * (nu + nv), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+      host[k].au = (const T*)dst;
+      host[k].av = (const T*)(dst + nu);
+      dst += nu + nv;
+    }
+  }
+  e = cudaMalloc(&plan.d_inst, sizeof(InstDev<T>) * n);
   if (e != cudaSuccess) return e;
   e = cudaMemcpy(plan.d_inst, host.data(), sizeof(InstDev<T>) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
@@ -876,6 +965,7 @@ cudaError_t batch_setup(Ctx& c, BatchPlan& plan) {
 
 void batch_free(BatchPlan& plan) {
   if (plan.d_inst) cudaFree(plan.d_inst);
+  if (plan.alpha_f) cudaFree(plan.alpha_f);
   for (int f = 0; f < kNumFam; ++f)
     if (plan.d_blk[f]) cudaFree(plan.d_blk[f]);
   plan = BatchPlan();
