@@ -1,0 +1,197 @@
+"""Pins of the 3D CPU oracle against what the paper and the mathematics fix.
+
+* a 3D step with no solid and data invariant along y (or along x) is the 2D step of the
+  remaining plane: the 2D oracle is pinned on its own (test_oracle_pins), so this pins
+  every stencil, both solves, the momentum terms, the projection and the correction of the
+  3D oracle, including the index conventions of each axis;
+* the eigen-solves against a dense brute-force matrix of the 7-point operator;
+* the pre-fill mass invariant of the CH solve and a divergence-free velocity after the
+  projection;
+* geometry: flat-wall fractions exact, sphere fractions against the sphere's volume,
+  intersect points on the sphere, normals radial to O(h), x <-> y symmetry of a centred
+  sphere;
+* the vector slip formula against the 2D one where the normal lies in a plane.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ib_pf2d as O2
+from oracle import ib_pf3d as O3
+from workloads import cases as W
+
+
+def _free3d(nx, ny, nz, rho_ratio=10.0, mu_ratio=10.0):
+    return W.flat_wall_case3d(nx=nx, ny=ny, nz=nz, geom_kind=W.GEOM_NONE, Cn=0.1,
+                              rho_ratio=rho_ratio, mu_ratio=mu_ratio)
+
+
+def _case2d_like(c3, n1, n2, l1):
+    p = c3.params
+    return W.Case2D("plane", n1, n2, l1, n2 * c3.h, W.GEOM_NONE, (0.0,) * 4, (0.0, 0.0), 0.0,
+                    p, 1)
+
+
+def _plane_state(rng, n1, n2):
+    """A smooth random 2D state (C, u, v, H, P at two levels) on an n2 x n1 plane."""
+    def smooth(shape, amp):
+        a = rng.standard_normal(shape)
+        for _ in range(3):
+            a = 0.25 * (np.roll(a, 1, 1) + np.roll(a, -1, 1)) + 0.5 * a
+            a[1:-1] = 0.25 * (a[:-2] + a[2:]) + 0.5 * a[1:-1]
+        return amp * a / np.abs(a).max()
+    st = {"C": 0.8 * smooth((n2, n1), 1.0), "C_old": 0.8 * smooth((n2, n1), 1.0)}
+    for k in ("u", "u_old", "Hu"):
+        st[k] = smooth((n2, n1), 0.1)
+    for k in ("v", "v_old", "Hv"):
+        a = smooth((n2 + 1, n1), 0.1)
+        a[0] = a[-1] = 0.0
+        st[k] = a
+    st["P"] = smooth((n2, n1), 1.0)
+    st["P_old"] = smooth((n2, n1), 1.0)
+    return st
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("axis", ["y", "x"])
+def test_step_reduces_to_2d_plane(axis):
+    rng = np.random.default_rng(17)
+    n1, n2, nrep = 16, 8, 4
+    if axis == "y":      # data varies in (x, z), constant along y
+        c3 = _free3d(n1, nrep, n2)
+    else:                # data varies in (y, z), constant along x
+        c3 = _free3d(nrep, n1, n2)
+        c3 = W.Case3D(c3.name, nrep, n1, n2, nrep * c3.h, n1 * c3.h, n2 * c3.h, c3.geom_kind,
+                      c3.geom_p, c3.drop_c, c3.drop_r, c3.params, 1)
+    c2 = _case2d_like(c3, n1, n2, n1 * c3.h)
+    s2 = _plane_state(rng, n1, n2)
+    zero3 = np.zeros((n2, c3.ny, c3.nx))
+    s3 = {}
+    if axis == "y":
+        ext = lambda a: np.repeat(a[:, None, :], nrep, axis=1)
+        s3 = {"C": ext(s2["C"]), "C_old": ext(s2["C_old"]),
+              "u": ext(s2["u"]), "u_old": ext(s2["u_old"]), "Hu": ext(s2["Hu"]),
+              "v": zero3.copy(), "v_old": zero3.copy(), "Hv": zero3.copy(),
+              "w": ext(s2["v"]), "w_old": ext(s2["v_old"]), "Hw": ext(s2["Hv"]),
+              "P": ext(s2["P"]), "P_old": ext(s2["P_old"])}
+    else:
+        ext = lambda a: np.repeat(a[:, :, None], nrep, axis=2)
+        s3 = {"C": ext(s2["C"]), "C_old": ext(s2["C_old"]),
+              "v": ext(s2["u"]), "v_old": ext(s2["u_old"]), "Hv": ext(s2["Hu"]),
+              "u": zero3.copy(), "u_old": zero3.copy(), "Hu": zero3.copy(),
+              "w": ext(s2["v"]), "w_old": ext(s2["v_old"]), "Hw": ext(s2["Hv"]),
+              "P": ext(s2["P"]), "P_old": ext(s2["P_old"])}
+    g2 = O2.build_geometry(c2)
+    g3 = O3.build_geometry3(c3)
+    assert len(g3.gcell) == 0
+    r2, _ = O2.step(c2, g2, s2)
+    r3, _ = O3.step3(c3, g3, s3)
+    tang = "u" if axis == "y" else "v"
+    other = "v" if axis == "y" else "u"
+    for rep in range(nrep):
+        sl = (slice(None), rep, slice(None)) if axis == "y" else (slice(None), slice(None), rep)
+        assert _rel(r3["C"][sl], r2["C"]) < 1e-12
+        assert _rel(r3[tang][sl], r2["u"]) < 1e-12
+        assert _rel(r3["H" + tang][sl], r2["Hu"]) < 1e-12
+        assert _rel(r3["w"][sl], r2["v"]) < 1e-12
+        assert _rel(r3["Hw"][sl], r2["Hv"]) < 1e-12
+        p3 = r3["P"][sl] - r3["P"][sl].mean()
+        p2 = r2["P"] - r2["P"].mean()
+        assert _rel(p3, p2) < 1e-11
+    assert np.abs(r3[other]).max() < 1e-14
+
+
+def test_solves_against_dense_operator():
+    nx, ny, nz, h = 4, 4, 4, 0.25
+    n = nx * ny * nz
+    L = np.zeros((n, n))
+    for col in range(n):
+        e = np.zeros(n)
+        e[col] = 1.0
+        L[:, col] = O3.laplacian3(e.reshape(nz, ny, nx), h).reshape(-1)
+    case = _free3d(nx, ny, nz)
+    case = W.Case3D(case.name, nx, ny, nz, nx * h, ny * h, nz * h, case.geom_kind, case.geom_p,
+                    case.drop_c, case.drop_r, case.params, 1)
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal((nz, ny, nx))
+    p = case.params
+    eta2 = p.Cn ** 2
+    A = L @ L - (p.S / eta2) * L + 1.5 * p.Pe / (eta2 * p.dt) * np.eye(n)
+    c_dense = np.linalg.solve(A, Q.reshape(-1))
+    assert _rel(O3.ch_solve3(case, Q).reshape(-1), c_dense) < 1e-12
+    rhs = Q - Q.mean()
+    P = O3.poisson_solve3(case, rhs)
+    assert _rel(O3.laplacian3(P, h), rhs) < 1e-11
+    assert abs(P.mean()) < 1e-12
+
+
+def test_mass_invariant_and_divergence_free():
+    case = W.small_sphere_case(16)
+    geo = O3.build_geometry3(case)
+    st = W.random_state3d(case, seed=5)
+    st["C_old"] = st["C"].copy()          # equal levels: sum C_pre = sum C
+    new, info = O3.step3(case, geo, st)
+    assert abs(info["mass_pre"] - st["C"].sum()) <= 1e-11 * np.abs(st["C"]).sum()
+    div = O3.divergence3(new["u"], new["v"], new["w"], case.h)
+    vel = max(np.abs(new["u"]).max(), np.abs(new["v"]).max(), np.abs(new["w"]).max())
+    assert np.abs(div).max() * case.h < 1e-10 * vel
+
+
+def test_flat_wall_fractions_exact():
+    case = W.flat_wall_case3d(nx=8, ny=8, nz=8, wall_z=0.55)   # h = 0.25: wall inside cell 2
+    a = O3.volume_fractions3(case, (0.0, 0.0, 0.0), (8, 8, 8))
+    assert np.all(a[:2] == 0.0) and np.all(a[3:] == 1.0)
+    assert np.allclose(a[2], (0.75 - 0.55) / 0.25 + 0.0, atol=1.0 / O3.NSUB3)
+    # subgrid planes z = 0.5 + (a + 1/2) / 64: plane 2 (0.5390625) is solid, plane 3
+    # (0.5546875) is fluid, so 13 of the 16 planes count as fluid
+    assert np.all(a[2] == 13.0 / 16.0)
+
+
+def test_sphere_fractions_volume_and_symmetry():
+    case = W.small_sphere_case(16)
+    a = O3.volume_fractions3(case, (0.0, 0.0, 0.0), (16, 16, 16))
+    solid_vol = ((1.0 - a).sum()) * case.h ** 3
+    exact = 4.0 / 3.0 * math.pi * 0.25 ** 3
+    assert abs(solid_vol - exact) < 2e-3 * exact
+    assert np.array_equal(a, np.transpose(a, (0, 2, 1)))        # x <-> y
+    assert np.array_equal(a, a[:, :, ::-1]) and np.array_equal(a, a[::-1])
+
+
+def test_sphere_ghost_geometry():
+    case = W.small_sphere_case(16)
+    geo = O3.build_geometry3(case)
+    h = case.h
+    c = np.array([0.5, 0.5, 0.5])
+    k, r = np.divmod(geo.gcell, 16 * 16)
+    j, i = np.divmod(r, 16)
+    G = np.stack([(i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h], axis=1)
+    I = G + geo.dn[:, None] * geo.n
+    assert np.abs(np.linalg.norm(I - c, axis=1) - 0.25).max() < 1e-12
+    radial = (G - c) / np.linalg.norm(G - c, axis=1)[:, None]
+    cosang = np.sum(radial * geo.n, axis=1)
+    assert cosang.min() > math.cos(math.radians(15.0))
+    assert np.all(np.abs(geo.w1.sum(axis=1) - 1.0) < 1e-14)
+    assert np.all(geo.gamma > 0.0) and geo.n_fallback_ap == 0
+    assert np.all(geo.cls.reshape(-1)[geo.ap1[geo.w1 > 0]] == O3.CELL_FLUID)
+
+
+def test_slip_vector_form_matches_2d():
+    rng = np.random.default_rng(9)
+    ng = 50
+    th = rng.uniform(0, 2 * math.pi, ng)
+    n2d = np.stack([np.cos(th), np.sin(th)], axis=1)
+    uM, vM = rng.standard_normal(ng), rng.standard_normal(ng)
+    gamma = rng.uniform(0.5, 3.0, ng)
+    dn = rng.uniform(0.01, 0.02, ng)
+    c2 = W.flat_wall_128x64()
+    c2 = W.with_params(c2, l_s=0.01)
+    u2, v2 = O2.slip_ghost(c2, uM, vM, n2d, gamma, dn)
+    c3 = W.flat_wall_case3d(l_s=0.01)
+    n3 = np.stack([n2d[:, 0], np.zeros(ng), n2d[:, 1]], axis=1)
+    u3, v3, w3 = O3.slip_ghost3(c3, uM, np.zeros(ng), vM, n3, gamma, dn)
+    assert np.abs(u3 - u2).max() < 1e-13 and np.abs(w3 - v2).max() < 1e-13
+    assert np.abs(v3).max() == 0.0

@@ -210,3 +210,178 @@ def random_state(case: Case2D, seed: int = 7, amp_u: float = 0.05) -> dict:
     s["P"] -= s["P"].mean()
     s["P_old"] -= s["P_old"].mean()
     return s
+
+
+# ============================================================================ 3D
+# Layout: cell fields (nz, ny, nx), x fastest; u on x-faces (nz, ny, nx; face i is the left
+# face of cell i), v on y-faces (nz, ny, nx), w on z-faces (nz+1, ny, nx; rows 0 and nz are
+# the domain walls).  Periodic in x and y, walls in z.
+#
+# 3D solid descriptors
+#   GEOM_FLAT     z < p0
+#   GEOM_SPHERE   |x - (p0, p1, p2)| < p3
+#   GEOM_SPHERES  union of the spheres (cx, cy, cz, r) of Case3D.spheres
+#   GEOM_NONE     no solid
+GEOM_SPHERE = 4
+GEOM_SPHERES = 5
+
+
+@dataclass(frozen=True)
+class Case3D:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lz: float
+    geom_kind: int
+    geom_p: tuple
+    drop_c: tuple
+    drop_r: float
+    params: Params
+    steps: int
+    spheres: tuple = ()          # ((cx, cy, cz, r), ...) for GEOM_SPHERES
+
+    @property
+    def h(self) -> float:
+        return self.lx / self.nx
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def _dt_rule(h: float, Re: float) -> float:
+    # viscous rule of Eq. timestep, 0.25 Re h^2 / 6
+    return 0.25 * Re * h * h / 6.0
+
+
+def sphere_case(n: int = 256, steps: int = 1000, name: str | None = None) -> Case3D:
+    """Droplet on a solid sphere: n^3 cells on the unit cube, sphere R_s = 0.25 at the centre,
+    droplet R = 0.2 centred on the sphere's top point (0.5, 0.5, 0.75), theta = 120 deg,
+    Cn = 0.01 (scaled with h below 256), Re = 20, Ca = 0.05, l_s = 0.005, Pe = 1e4."""
+    h = 1.0 / n
+    d1, d2 = _ghost_lengths(h, 3)
+    p = Params(Re=20.0, Ca=0.05, Cn=0.01 * 256 / n, Pe=1.0e4, S=2.0, theta_deg=120.0,
+               l_s=0.005, d1=d1, d2=d2, dt=_dt_rule(h, 20.0))
+    return Case3D(name or f"sphere_{n}", n, n, n, 1.0, 1.0, 1.0, GEOM_SPHERE,
+                  (0.5, 0.5, 0.5, 0.25), (0.5, 0.5, 0.75), 0.2, p, steps)
+
+
+def sphere_packing(seed: int = 350, r_lo: float = 0.03, r_hi: float = 0.06, z_top: float = 0.35,
+                   solid_fraction: float = 0.4, max_fail: int = 1_000_000) -> tuple:
+    """Random sequential addition of non-overlapping spheres, radii ~ U(r_lo, r_hi), centres
+    uniform in [0,1)^2 x [0, z_top), periodic in x and y (overlap tested against the nearest
+    periodic image), until the spheres' volume reaches solid_fraction of the slab
+    [0,1]^2 x [0, z_top] or max_fail placements in a row fail.  Seeded PCG64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    target = solid_fraction * z_top
+    out = []
+    vol = 0.0
+    fails = 0
+    while vol < target and fails < max_fail:
+        r = float(rng.uniform(r_lo, r_hi))
+        c = (float(rng.uniform(0.0, 1.0)), float(rng.uniform(0.0, 1.0)),
+             float(rng.uniform(0.0, z_top)))
+        ok = True
+        for (x, y, z, rr) in out:
+            dx = abs(c[0] - x)
+            dx = min(dx, 1.0 - dx)
+            dy = abs(c[1] - y)
+            dy = min(dy, 1.0 - dy)
+            dz = c[2] - z
+            if dx * dx + dy * dy + dz * dz < (r + rr) * (r + rr):
+                ok = False
+                break
+        if ok:
+            out.append((c[0], c[1], c[2], r))
+            vol += 4.0 / 3.0 * math.pi * r ** 3
+            fails = 0
+        else:
+            fails += 1
+    return tuple(out)
+
+
+def porous_case(n: int = 512, steps: int = 500, seed: int = 350, name: str | None = None,
+                max_fail: int = 1_000_000) -> Case3D:
+    """Droplet R = 0.15 at (0.5, 0.5, 0.5) above a random packing of spheres (sphere_packing)
+    in z < 0.35, n^3 cells on the unit cube, theta = 60 deg, Cn = 0.005 (scaled with h below
+    512), Re = 10, Ca = 0.1, l_s = 0.002, Pe = 1e4."""
+    h = 1.0 / n
+    d1, d2 = _ghost_lengths(h, 3)
+    p = Params(Re=10.0, Ca=0.1, Cn=0.005 * 512 / n, Pe=1.0e4, S=2.0, theta_deg=60.0,
+               l_s=0.002, d1=d1, d2=d2, dt=_dt_rule(h, 10.0))
+    sph = sphere_packing(seed, max_fail=max_fail)
+    return Case3D(name or f"porous_{n}", n, n, n, 1.0, 1.0, 1.0, GEOM_SPHERES, (0.0,) * 4,
+                  (0.5, 0.5, 0.5), 0.15, p, steps, sph)
+
+
+def flat_wall_case3d(nx: int = 32, ny: int = 16, nz: int = 16, wall_z: float = 0.2,
+                     theta_deg: float = 60.0, l_s: float = 0.0, Cn: float | None = None,
+                     drop_r: float = 0.35, rho_ratio: float = 10.0, mu_ratio: float = 10.0,
+                     geom_kind: int | None = None, name: str | None = None) -> Case3D:
+    """Flat immersed wall z < wall_z in [0, nx h] x [0, ny h] x [0, nz h] with h = 2/nx; a
+    droplet centred on the wall at the box centre (small parity cases)."""
+    h = 2.0 / nx
+    d1, d2 = _ghost_lengths(h, 3)
+    p = Params(Re=10.0, Ca=0.1, Cn=Cn if Cn is not None else 2.56 * h, Pe=5.0e3, S=2.0,
+               rho_ratio=rho_ratio, mu_ratio=mu_ratio, theta_deg=theta_deg, l_s=l_s, d1=d1,
+               d2=d2, dt=_dt_rule(h, 10.0))
+    kind = GEOM_FLAT if geom_kind is None else geom_kind
+    return Case3D(name or f"flat3d_{nx}x{ny}x{nz}", nx, ny, nz, 2.0, ny * h, nz * h, kind,
+                  (wall_z, 0.0, 0.0, 0.0), (1.0, 0.5 * ny * h, wall_z), drop_r, p, 1)
+
+
+def small_sphere_case(n: int = 32, theta_deg: float = 120.0, l_s: float = 0.005) -> Case3D:
+    """The sphere workload on an n^3 grid (Cn = 2.56 h) for parity tests."""
+    c = sphere_case(n, steps=1)
+    return replace(c, params=replace(c.params, theta_deg=theta_deg, l_s=l_s))
+
+
+def initial_state3d(case: Case3D) -> dict:
+    """Initial fields (FP64): tanh droplet, zero velocity and pressure, old level = new."""
+    h = case.h
+    xc = (np.arange(case.nx) + 0.5) * h
+    yc = (np.arange(case.ny) + 0.5) * h
+    zc = (np.arange(case.nz) + 0.5) * h
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")
+    r = np.sqrt((X - case.drop_c[0]) ** 2 + (Y - case.drop_c[1]) ** 2 + (Z - case.drop_c[2]) ** 2)
+    C = np.tanh((case.drop_r - r) / (math.sqrt(2.0) * case.params.Cn))
+    zc3 = np.zeros((case.nz, case.ny, case.nx))
+    zw = np.zeros((case.nz + 1, case.ny, case.nx))
+    return {"C": C.copy(), "C_old": C.copy(),
+            "u": zc3.copy(), "u_old": zc3.copy(), "v": zc3.copy(), "v_old": zc3.copy(),
+            "w": zw.copy(), "w_old": zw.copy(),
+            "Hu": zc3.copy(), "Hv": zc3.copy(), "Hw": zw.copy(),
+            "P": zc3.copy(), "P_old": zc3.copy()}
+
+
+def random_state3d(case: Case3D, seed: int = 7, amp_u: float = 0.05) -> dict:
+    """The initial droplet with smooth random perturbations of every field."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s = initial_state3d(case)
+    nz, ny, nx = case.nz, case.ny, case.nx
+
+    def smooth(shape, amp):
+        a = rng.standard_normal(shape)
+        for _ in range(3):
+            a = 0.25 * (np.roll(a, 1, 2) + np.roll(a, -1, 2)) + 0.5 * a
+            a = 0.25 * (np.roll(a, 1, 1) + np.roll(a, -1, 1)) + 0.5 * a
+            a[1:-1] = 0.25 * (a[:-2] + a[2:]) + 0.5 * a[1:-1]
+        return amp * a / max(1e-30, np.abs(a).max())
+
+    s["C_old"] = s["C"] + smooth((nz, ny, nx), 0.02)
+    s["C"] = s["C"] + smooth((nz, ny, nx), 0.02)
+    for key in ("u", "u_old", "Hu", "v", "v_old", "Hv"):
+        s[key] = smooth((nz, ny, nx), 1.0 if key[0] == "H" else amp_u)
+    for key in ("w", "w_old", "Hw"):
+        a = smooth((nz + 1, ny, nx), 1.0 if key == "Hw" else amp_u)
+        a[0] = 0.0
+        a[nz] = 0.0
+        s[key] = a
+    s["P"] = smooth((nz, ny, nx), 1.0)
+    s["P_old"] = s["P"] + smooth((nz, ny, nx), 0.1)
+    s["P"] -= s["P"].mean()
+    s["P_old"] -= s["P_old"].mean()
+    return s
