@@ -104,10 +104,25 @@ def volume_fraction_cv(case: Case3D, x0: float, y0: float, z0: float, sph=None) 
         return n_fluid / float(NSUB3 ** 3)
     sph = _spheres(case) if sph is None else sph
     cand = _candidates(case, sph, x0, y0, z0, h)
-    if len(cand) == 0:
+    # reading R12: a sphere whose nearest point of the volume is at or beyond its radius
+    # holds no subpoint; one holding the 8 corners holds every subpoint (convexity)
+    hh = 0.5 * h
+    band = []
+    for cx, cy, cz, r in cand:
+        ax = abs(float(_wrap(np.float64(x0 + hh - cx), case.lx)))
+        ay = abs(float(_wrap(np.float64(y0 + hh - cy), case.ly)))
+        az = abs(z0 + hh - cz)
+        nx_, ny_, nz_ = max(ax - hh, 0.0), max(ay - hh, 0.0), max(az - hh, 0.0)
+        if (nx_ * nx_ + ny_ * ny_) + nz_ * nz_ >= r * r:
+            continue
+        fx, fy, fz = ax + hh, ay + hh, az + hh
+        if (fx * fx + fy * fy) + fz * fz < r * r:
+            return 0.0
+        band.append((cx, cy, cz, r))
+    if not band:
         return 1.0
     Z, Y, X = np.meshgrid(z0 + off, y0 + off, x0 + off, indexing="ij")
-    n_fluid = np.count_nonzero(~solid3(case, X, Y, Z, cand))
+    n_fluid = np.count_nonzero(~solid3(case, X, Y, Z, np.array(band)))
     return n_fluid / float(NSUB3 ** 3)
 
 
@@ -201,6 +216,34 @@ def _normal3(case: Case3D, alpha_c, cls, i, j, k):
     return m[0] / norm, m[1] / norm, m[2] / norm, False
 
 
+def _normals3(case: Case3D, alpha_c, gi, gj, gk):
+    """Mean of the 8 corner gradients of alpha (reading R13) for arrays of cells, in the
+    order and grouping of _normal3."""
+    h = case.h
+    nz, ny, nx = alpha_c.shape
+
+    def al(i, j, k):
+        return alpha_c[np.clip(k, 0, nz - 1), j % ny, i % nx]
+
+    acc = np.zeros((len(gi), 3))
+    for dk in (-1, 0):
+        for dj in (-1, 0):
+            for di in (-1, 0):
+                ci, cj, ck = gi + di, gj + dj, gk + dk
+                a = [[[al(ci + ei, cj + ej, ck + ek) for ei in (0, 1)] for ej in (0, 1)]
+                     for ek in (0, 1)]
+                mx = ((a[0][0][1] + a[0][1][1]) + (a[1][0][1] + a[1][1][1])
+                      - ((a[0][0][0] + a[0][1][0]) + (a[1][0][0] + a[1][1][0]))) / (4.0 * h)
+                my = ((a[0][1][0] + a[0][1][1]) + (a[1][1][0] + a[1][1][1])
+                      - ((a[0][0][0] + a[0][0][1]) + (a[1][0][0] + a[1][0][1]))) / (4.0 * h)
+                mz = ((a[1][0][0] + a[1][0][1]) + (a[1][1][0] + a[1][1][1])
+                      - ((a[0][0][0] + a[0][0][1]) + (a[0][1][0] + a[0][1][1]))) / (4.0 * h)
+                acc[:, 0] = acc[:, 0] + mx
+                acc[:, 1] = acc[:, 1] + my
+                acc[:, 2] = acc[:, 2] + mz
+    return acc / 8.0
+
+
 def _averaging_points3(case: Case3D, cls, px, py, pz):
     """Reading R6': the cell holding (px, py, pz) and its 6 face neighbours, fluid centres
     only, inverse-squared-distance weights normalised (Eq. weright averaged)."""
@@ -267,50 +310,63 @@ def build_geometry3(case: Case3D) -> Geometry3D:
     gk, gj, gi = np.nonzero(cls == CELL_GHOST)
     ng = len(gi)
     gcell = ((gk * ny + gj) * nx + gi).astype(np.int64)
-    nrm = np.zeros((ng, 3))
-    dn = np.zeros(ng)
-    gamma = np.zeros(ng)
     ap1 = np.zeros((ng, NAP3), dtype=np.int64)
     ap2 = np.zeros((ng, NAP3), dtype=np.int64)
     w1 = np.zeros((ng, NAP3))
     w2 = np.zeros((ng, NAP3))
     nfb_n = nfb_ap = 0
+    # normals (reading R13), every ghost at once; the arithmetic of each ghost is the
+    # scalar sequence of _normal3
+    m = _normals3(case, alpha_c, gi, gj, gk)
+    mag2 = (m[:, 0] * m[:, 0] + m[:, 1] * m[:, 1]) + m[:, 2] * m[:, 2]
+    norm = np.sqrt(mag2 + EPS0)
+    nrm = m / norm[:, None]
+    for g in np.nonzero(np.sqrt(mag2) * h < 1.0e-12)[0]:
+        nb = _first_fluid_neighbour3(cls, int(gi[g]), int(gj[g]), int(gk[g]))
+        if nb is None:
+            raise ValueError("ghost cell without fluid neighbour")
+        nrm[g] = (nb[3], nb[4], nb[5])
+        nfb_n += 1
+    G = np.stack([(gi + 0.5) * h, (gj + 0.5) * h, (gk + 0.5) * h], axis=1)
+    # intersect points: march h/100 along n to the first point outside, then bisect
     ds = h / MARCH_DIV
+    qs = np.zeros(ng, dtype=np.int64)
+    active = np.arange(ng)
+    q = 1
+    while len(active) and q <= MARCH_MAX:
+        t = q * ds
+        out = ~solid3(case, G[active, 0] + t * nrm[active, 0], G[active, 1] + t * nrm[active, 1],
+                      G[active, 2] + t * nrm[active, 2], sph)
+        qs[active[out]] = q
+        active = active[~out]
+        q += 1
+    if len(active):
+        raise ValueError(f"no intersect point found for {len(active)} ghost(s)")
+    lo, hi = (qs - 1) * ds, qs * ds
+    for _ in range(BISECT):
+        mid = 0.5 * (lo + hi)
+        ins = solid3(case, G[:, 0] + mid * nrm[:, 0], G[:, 1] + mid * nrm[:, 1],
+                     G[:, 2] + mid * nrm[:, 2], sph)
+        lo = np.where(ins, mid, lo)
+        hi = np.where(ins, hi, mid)
+    dn = hi
+    gamma = p.d1 / hi
     for g in range(ng):
         i, j, k = int(gi[g]), int(gj[g]), int(gk[g])
-        n1, n2, n3, fb = _normal3(case, alpha_c, cls, i, j, k)
-        nfb_n += int(fb)
-        nrm[g] = (n1, n2, n3)
-        gx, gy, gz = (i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h
-        q = 1
-        while q <= MARCH_MAX:
-            t = q * ds
-            if not solid3(case, gx + t * n1, gy + t * n2, gz + t * n3, sph):
-                break
-            q += 1
-        if q > MARCH_MAX:
-            raise ValueError(f"no intersect point found for ghost ({i},{j},{k})")
-        lo, hi = (q - 1) * ds, q * ds
-        for _ in range(BISECT):
-            mid = 0.5 * (lo + hi)
-            if solid3(case, gx + mid * n1, gy + mid * n2, gz + mid * n3, sph):
-                lo = mid
-            else:
-                hi = mid
-        dn[g] = hi
-        gamma[g] = p.d1 / hi
-        s1 = (hi + p.d1) + p.d2
-        s2 = (hi + p.d1) + 2.0 * p.d2
-        for s, aps, ws in ((s1, ap1, w1), (s2, ap2, w2)):
-            res = _averaging_points3(case, cls, gx + s * n1, gy + s * n2, gz + s * n3)
+        n1, n2, n3 = nrm[g]
+        gx, gy, gz = G[g]
+        s1 = (dn[g] + p.d1) + p.d2
+        s2 = (dn[g] + p.d1) + 2.0 * p.d2
+        for sdist, aps, ws in ((s1, ap1, w1), (s2, ap2, w2)):
+            res = _averaging_points3(case, cls, gx + sdist * n1, gy + sdist * n2, gz + sdist * n3)
             if res is None:
                 nb = _first_fluid_neighbour3(cls, i, j, k)
                 res = ([(nb[2] * ny + nb[1]) * nx + nb[0]], [1.0])
                 nfb_ap += 1
             idx, w = res
-            for a in range(NAP3):
-                aps[g, a] = idx[a] if a < len(idx) else idx[0]
-                ws[g, a] = w[a] if a < len(idx) else 0.0
+            for aa in range(NAP3):
+                aps[g, aa] = idx[aa] if aa < len(idx) else idx[0]
+                ws[g, aa] = w[aa] if aa < len(idx) else 0.0
     isg = cls == CELL_GHOST
     fu = np.flatnonzero(((alpha_u < 1.0) & (isg | np.roll(isg, 1, axis=2))).reshape(-1))
     fv = np.flatnonzero(((alpha_v < 1.0) & (isg | np.roll(isg, 1, axis=1))).reshape(-1))
