@@ -25,6 +25,14 @@
  * are ny x nx with face i the left face of cell i; x2-face fields (v, Hv) are
  * (ny+1) x nx with rows 0 and ny on the domain walls (always zero).
  *
+ * 3D (dim 3).  nx x ny x nz cubic cells, periodic in x and y, solid walls (w = 0) at
+ * z = 0 and z = lz; nx, ny, nz powers of two, 8 <= n <= 1024.  Cell fields and the x-/y-face
+ * fields (u, v, Hu, Hv) are nz x ny x nx (x fastest; u face i is the left face of cell i, v
+ * face j the front face of cell j); z-face fields (w, Hw) are (nz+1) x ny x nx with planes 0
+ * and nz on the domain walls.  The 3D step is the 2D one with the third axis: 7-point
+ * stencils, 7 averaging points per interpolation point, the full stress tensor, the slip
+ * condition in vector form (V_t = u - (u.n) n).
+ *
  * Element type.  The element type of every field buffer passed in or out is the
  * context's arithmetic type: double for IB_PF_FP64, float for IB_PF_FP32.
  *
@@ -46,7 +54,7 @@ typedef struct ib_pf_ctx ib_pf_ctx;   /* opaque; owned by the library */
 typedef enum {
   IB_PF_OK = 0,
   IB_PF_E_ARG = -1,          /* invalid argument (sizes, ids, null pointers, params) */
-  IB_PF_E_UNSUPPORTED = -2,  /* valid but not implemented (e.g. dim 3, dynamic angle) */
+  IB_PF_E_UNSUPPORTED = -2,  /* valid but not implemented (e.g. dynamic angle) */
   IB_PF_E_CUDA = -3,         /* a CUDA runtime call failed; see ib_pf_last_error */
   IB_PF_E_NUMERIC = -4,      /* NaN/Inf seen in C or the velocity by the device check */
   IB_PF_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
@@ -57,19 +65,27 @@ typedef enum {
 typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
 
 /* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points
- * against it).  FLAT: x2 < p[0].  SINUSOID: x2 < p[0] + p[1] sin(2 pi p[2] x1).
- * NONE: no solid. */
-typedef enum { IB_PF_WALL_FLAT = 0, IB_PF_WALL_SINUSOID = 1, IB_PF_WALL_NONE = 3 } ib_pf_wall_kind;
+ * against it).  FLAT: x2 < p[0] (2D), z < p[0] (3D).  SINUSOID (2D): x2 < p[0] + p[1]
+ * sin(2 pi p[2] x1).  SPHERE (3D): |x - (p[0], p[1], p[2])| < p[3].  SPHERES (3D): the union
+ * of the spheres (cx, cy, cz, r) of ib_pf_geometry.spheres.  NONE: no solid.  Sphere
+ * distances take the nearest periodic image in x and y. */
+typedef enum {
+  IB_PF_WALL_FLAT = 0, IB_PF_WALL_SINUSOID = 1, IB_PF_WALL_NONE = 3, IB_PF_WALL_SPHERE = 4,
+  IB_PF_WALL_SPHERES = 5
+} ib_pf_wall_kind;
 
 typedef struct {
-  int dim;        /* 2 (3 returns IB_PF_E_UNSUPPORTED) */
-  int n[3];       /* cells per axis: n[0] = nx, n[1] = ny */
+  int dim;        /* 2 or 3; all instances of a context share it */
+  int n[3];       /* cells per axis: n[0] = nx, n[1] = ny, n[2] = nz (3D) */
   double L[3];    /* domain lengths */
 } ib_pf_grid;
 
 typedef struct {
   int kind;       /* ib_pf_wall_kind */
   double p[8];    /* wall parameters, see above */
+  const double* spheres;   /* SPHERES: host array of n_spheres x (cx, cy, cz, r), copied by
+                              ib_pf_init_geometry (the caller keeps ownership); else NULL */
+  int n_spheres;
 } ib_pf_geometry;
 
 /* Nondimensional parameters as defined in Sec. 5.1 (Re, Ca, Cn) and Sec. 5.3 (Pe);
@@ -104,7 +120,10 @@ typedef enum {
   IB_PF_F_C_LO = 13,    /* FP32 contexts only: low part of the compensated C^n (C^n is held
                            as the unevaluated sum C + C_LO); read/write, for restarts.
                            Writing IB_PF_F_C clears it. */
-  IB_PF_F_C_OLD_LO = 14 /* FP32 contexts only: low part of C^{n-1} */
+  IB_PF_F_C_OLD_LO = 14, /* FP32 contexts only: low part of C^{n-1} */
+  IB_PF_F_W = 15,       /* 3D: w^n (z-faces) read/write */
+  IB_PF_F_W_OLD = 16,   /* 3D: w^{n-1} */
+  IB_PF_F_HW = 17       /* 3D: H_w^{n-1} */
 } ib_pf_field;
 
 /* geometry tables for ib_pf_read_table (element type in brackets) */
@@ -122,8 +141,12 @@ typedef enum {
   IB_PF_T_AP2 = 10,     /* [int]    ng x 5 */
   IB_PF_T_W2 = 11,      /* [double] ng x 5 */
   IB_PF_T_FACE_U = 12,  /* [int]    nfu          re-interpolated x1-faces (j*nx+i) */
-  IB_PF_T_FACE_V = 13   /* [int]    nfv          re-interpolated x2-faces (j*nx+i) */
+  IB_PF_T_FACE_V = 13,  /* [int]    nfv          re-interpolated x2-faces (j*nx+i) */
+  IB_PF_T_ALPHA_W = 14, /* 3D: [double] (nz+1) x ny x nx  z-face volumes */
+  IB_PF_T_FACE_W = 15   /* 3D: [int] nfw  re-interpolated z-faces ((k*ny+j)*nx+i) */
 } ib_pf_table;
+/* In 3D the cell and face tables are nz x ny x nx (alpha_v too), linear indices are
+ * (k*ny + j)*nx + i, normals are ng x 3 and the averaging stencils ng x 7. */
 
 /* quantities for ib_pf_query */
 typedef enum {
@@ -134,7 +157,8 @@ typedef enum {
   IB_PF_Q_STATUS = 4,      /* device status word: 0 ok, 1 non-finite seen */
   IB_PF_Q_STEPS = 5,       /* steps taken since creation */
   IB_PF_Q_N_FALLBACK = 6,  /* normals or averaging stencils that used the fallback */
-  IB_PF_Q_LAUNCHES_PER_STEP = 7  /* kernels one step launches */
+  IB_PF_Q_LAUNCHES_PER_STEP = 7, /* kernels one step launches */
+  IB_PF_Q_N_FACE_W = 8           /* 3D: re-interpolated z-faces */
 } ib_pf_query_id;
 
 /* Create a context for n_instances independent problems (grids[k], geoms[k],

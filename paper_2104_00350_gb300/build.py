@@ -19,8 +19,9 @@ OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libibpf.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # geometry decisions (subgrid counts, march, averaging cells) want unfused products
-PER_FILE = {"geometry.cu": ["-fmad=false"]}
-SOURCES = ["ib_pf_api.cu", "geometry.cu", "spectral.cu", "step2d.cu", "noalloc.cu"]
+PER_FILE = {"geometry.cu": ["-fmad=false"], "geometry3d.cu": ["-fmad=false"]}
+SOURCES = ["ib_pf_api.cu", "geometry.cu", "geometry3d.cu", "spectral.cu", "step2d.cu", "step3d.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:
@@ -43,7 +44,7 @@ def _compile(src: str, build: Path) -> Path:
 
 def build(force: bool = False, verbose: bool = False) -> Path:
     """Build the shared library if any source is newer than it; return its path."""
-    srcs = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + [ROOT / "include" / "ib_pf.h"]
+    srcs = [CSRC / s for s in SOURCES] + list(CSRC.glob("*.h")) + list(CSRC.glob("*.cuh")) + [ROOT / "include" / "ib_pf.h"]
     if LIB.exists() and not force:
         newest = max(p.stat().st_mtime for p in srcs)
         if LIB.stat().st_mtime >= newest:

@@ -34,9 +34,11 @@ int ilog2(int n) {
 ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg);
 
 size_t field_elems(const Instance& in, int id) {
-  const size_t cells = (size_t)in.nx * in.ny;
+  const size_t nxy = (size_t)in.nx * in.ny, cells = nxy * in.nz;
   switch (id) {
-    case IB_PF_F_V: case IB_PF_F_V_OLD: case IB_PF_F_HV: return cells + in.nx;
+    case IB_PF_F_V: case IB_PF_F_V_OLD: case IB_PF_F_HV:
+      return in.dim == 3 ? cells : cells + in.nx;
+    case IB_PF_F_W: case IB_PF_F_W_OLD: case IB_PF_F_HW: return cells + nxy;
     default: return cells;
   }
 }
@@ -59,6 +61,9 @@ void* field_ptr(Ctx& c, Instance& in, int id) {
     case IB_PF_F_RHS_P: return in.rhs;
     case IB_PF_F_C_LO: return in.Clo[n];
     case IB_PF_F_C_OLD_LO: return in.Clo[o];
+    case IB_PF_F_W: return in.W[n];
+    case IB_PF_F_W_OLD: return in.W[o];
+    case IB_PF_F_HW: return in.Hw;
     default: return nullptr;
   }
 }
@@ -69,7 +74,9 @@ void free_instance(Instance& in) {
                   in.lamx, in.lamy, in.lamx_f, in.lamy_f, in.twx, in.twy, in.wdct, in.partial, in.ticket, in.mass,
                   in.status, in.tab.alpha_c, in.tab.alpha_u, in.tab.alpha_v, in.tab.solidc,
                   in.tab.cmap, in.tab.gcell, in.tab.nrm, in.tab.dn, in.tab.gamma, in.tab.ap1,
-                  in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv};
+                  in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv, in.W[0], in.W[1], in.Hw,
+                  in.gw, in.lamz, in.lamz_f, in.twz, in.sph, in.bstart, in.blist,
+                  in.tab.alpha_w, in.tab.fw, in.alpha_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -105,10 +112,55 @@ ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg) {
   return st;
 }
 
+ib_pf_status validate3(const ib_pf_grid& g, const ib_pf_geometry& w, std::string& why) {
+  for (int a = 0; a < 3; ++a) {
+    if (!is_pow2(g.n[a]) || g.n[a] < 8 || g.n[a] > 1024) {
+      why = "3D: nx, ny, nz must be powers of two with 8 <= n <= 1024";
+      return IB_PF_E_ARG;
+    }
+    if (!(g.L[a] > 0)) { why = "domain lengths must be positive"; return IB_PF_E_ARG; }
+  }
+  const double hx = g.L[0] / g.n[0];
+  if (std::fabs(g.L[1] / g.n[1] - hx) > 1e-12 * hx || std::fabs(g.L[2] / g.n[2] - hx) > 1e-12 * hx) {
+    why = "cells must be cubes (lx/nx == ly/ny == lz/nz)";
+    return IB_PF_E_ARG;
+  }
+  if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SPHERE && w.kind != IB_PF_WALL_SPHERES &&
+      w.kind != IB_PF_WALL_NONE) {
+    why = "3D wall kind must be FLAT, SPHERE, SPHERES or NONE";
+    return IB_PF_E_ARG;
+  }
+  if (w.kind == IB_PF_WALL_SPHERE && !(w.p[3] > 0)) { why = "sphere radius must be positive"; return IB_PF_E_ARG; }
+  if (w.kind == IB_PF_WALL_SPHERES) {
+    if (!w.spheres || w.n_spheres < 1) { why = "SPHERES needs a sphere array"; return IB_PF_E_ARG; }
+    for (int q = 0; q < w.n_spheres; ++q)
+      if (!(w.spheres[4 * q + 3] > 0) || !std::isfinite(w.spheres[4 * q]) ||
+          !std::isfinite(w.spheres[4 * q + 1]) || !std::isfinite(w.spheres[4 * q + 2])) {
+        why = "sphere " + std::to_string(q) + ": finite centre and positive radius required";
+        return IB_PF_E_ARG;
+      }
+  }
+  return IB_PF_OK;
+}
+
 ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_params& p,
                       std::string& why) {
-  if (g.dim == 3) { why = "dim 3 is not built"; return IB_PF_E_UNSUPPORTED; }
-  if (g.dim != 2) { why = "dim must be 2"; return IB_PF_E_ARG; }
+  if (g.dim != 2 && g.dim != 3) { why = "dim must be 2 or 3"; return IB_PF_E_ARG; }
+  if (g.dim == 3) {
+    if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
+    if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }
+    const double vals3[] = {p.Re, p.Ca, p.Cn, p.Pe, p.rho_ratio, p.mu_ratio, p.dt, p.d1, p.d2};
+    for (double v : vals3)
+      if (!(v > 0) || !std::isfinite(v)) { why = "Re, Ca, Cn, Pe, ratios, dt, d1, d2 must be positive"; return IB_PF_E_ARG; }
+    if (!(p.S >= 0) || !(p.l_s >= 0) || !std::isfinite(p.theta_deg)) { why = "S, l_s must be >= 0"; return IB_PF_E_ARG; }
+    ib_pf_status st = validate3(g, w, why);
+    if (st != IB_PF_OK) return st;
+    if (!(p.d2 < p.d1) || !(p.d1 > 0.5 * std::sqrt(3.0) * (g.L[0] / g.n[0]))) {
+      why = "need d1 > half the cell diagonal and d2 < d1 (Sec. 4.1.2)";
+      return IB_PF_E_ARG;
+    }
+    return IB_PF_OK;
+  }
   const int nx = g.n[0], ny = g.n[1];
   if (!is_pow2(nx) || !is_pow2(ny) || nx < 8 || ny < 8 || nx > 4096 || ny > 2048) {
     why = "nx, ny must be powers of two with 8 <= nx <= 4096 and 8 <= ny <= 2048";
@@ -146,7 +198,9 @@ ib_pf_status capture_graphs(ib_pf_ctx* ctx) {
       rec.names = &ctx->tnames;
       rec.start(ctx->work);
     }
-    launches = step_batch(*ctx, *(BatchPlan*)ctx->plan, ph, ctx->work, ctx->timing ? &rec : nullptr);
+    launches = ctx->dim == 3
+                   ? step3d(*ctx, ph, ctx->work, ctx->timing ? &rec : nullptr)
+                   : step_batch(*ctx, *(BatchPlan*)ctx->plan, ph, ctx->work, ctx->timing ? &rec : nullptr);
     for (size_t k = 0; k < ctx->inst.size(); ++k) {
       cudaMemcpyAsync(ctx->h_status + k, ctx->inst[k].status, sizeof(int), cudaMemcpyDeviceToHost,
                       ctx->work);
@@ -181,10 +235,13 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     if (st != IB_PF_OK) return fail(nullptr, st, "instance " + std::to_string(k) + ": " + why);
     if (params[k].precision != params[0].precision)
       return fail(nullptr, IB_PF_E_ARG, "all instances must share one precision");
+    if (grids[k].dim != grids[0].dim)
+      return fail(nullptr, IB_PF_E_ARG, "all instances must share one dimension");
   }
   ib_pf_ctx* ctx = new (std::nothrow) ib_pf_ctx();
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "out of host memory");
   ctx->precision = params[0].precision;
+  ctx->dim = grids[0].dim;
   ctx->esz = ctx->precision == IB_PF_FP64 ? 8 : 4;
   ctx->user_stream = (cudaStream_t)cuda_stream;
   auto bail = [&](ib_pf_status st) {
@@ -204,12 +261,18 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
   ctx->inst.resize(n_instances);
   for (int k = 0; k < n_instances; ++k) {
     Instance& in = ctx->inst[k];
+    in.dim = grids[k].dim;
     in.nx = grids[k].n[0];
     in.ny = grids[k].n[1];
     in.lognx = ilog2(in.nx);
     in.logny = ilog2(in.ny);
     in.lx = grids[k].L[0];
     in.ly = grids[k].L[1];
+    if (in.dim == 3) {
+      in.nz = grids[k].n[2];
+      in.lognz = ilog2(in.nz);
+      in.lz = grids[k].L[2];
+    }
     in.h = in.lx / in.nx;
     in.geom = geoms[k];
     in.prm = params[k];
@@ -217,7 +280,8 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     in.wall.p0 = geoms[k].p[0];
     in.wall.p1 = geoms[k].p[1];
     in.wall.w = (2.0 * M_PI) * geoms[k].p[2];
-    const size_t cells = (size_t)in.nx * in.ny, vf = cells + in.nx, es = ctx->esz;
+    const size_t nxy = (size_t)in.nx * in.ny, cells = nxy * in.nz, es = ctx->esz;
+    const size_t vf = in.dim == 3 ? cells : cells + in.nx;
     const size_t nh1 = (size_t)in.nx / 2 + 1;
     void** cell_fields[] = {&in.C[0], &in.C[1], &in.P[0], &in.P[1], &in.U[0], &in.U[1], &in.Hu,
                             &in.Q, &in.phi, &in.rhs, &in.phat, &in.dp};
@@ -236,14 +300,21 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
       if (cudaMalloc(f, vf * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
       cudaMemsetAsync(*f, 0, vf * es, ctx->work);
     }
-    if (cudaMalloc(&in.spec, (size_t)in.ny * nh1 * 2 * es) != cudaSuccess) {
+    if (in.dim == 3) {
+      void** wfields[] = {&in.W[0], &in.W[1], &in.Hw};
+      for (void** f : wfields) {
+        if (cudaMalloc(f, (cells + nxy) * es) != cudaSuccess) { ctx->err = "field allocation failed"; return bail(IB_PF_E_CUDA); }
+        cudaMemsetAsync(*f, 0, (cells + nxy) * es, ctx->work);
+      }
+    }
+    if (cudaMalloc(&in.spec, (size_t)in.ny * in.nz * nh1 * 2 * es) != cudaSuccess) {
       ctx->err = "spectral workspace allocation failed";
       return bail(IB_PF_E_CUDA);
     }
     // partial sums: one per cell tile of the step's reduction, or per 256-cell block of
     // the stand-alone reduction, whichever is more
     const int ntile = ((in.nx + kTileX - 1) / kTileX) * ((in.ny + kTileH - 1) / kTileH);
-    const int nred = (in.nx * in.ny + 255) / 256;
+    const int nred = (int)((cells + 255) / 256);
     const int nblk = ntile > nred ? ntile : nred;
     in.nblk_red = nblk;
     if (cudaMalloc((void**)&in.partial, sizeof(double) * nblk) != cudaSuccess ||
@@ -256,19 +327,23 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     cudaMemsetAsync(in.ticket, 0, sizeof(unsigned), ctx->work);
     cudaMemsetAsync(in.mass, 0, sizeof(double), ctx->work);
     cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work);
-    if (spectral_tables(in, ctx->precision) != cudaSuccess) {
+    if ((in.dim == 3 ? spectral3_tables(in, ctx->precision) : spectral_tables(in, ctx->precision)) !=
+        cudaSuccess) {
       ctx->err = std::string("transform tables: ") + cudaGetErrorString(cudaGetLastError());
       return bail(IB_PF_E_CUDA);
     }
     std::string gerr;
-    if (geometry_init(in, ctx->work, gerr) != cudaSuccess) {
+    const cudaError_t ge = in.dim == 3 ? geometry3_init(in, geoms[k].spheres, geoms[k].n_spheres, ctx->work, gerr)
+                                       : geometry_init(in, ctx->work, gerr);
+    if (ge != cudaSuccess) {
       ctx->err = "geometry: " + gerr;
       return bail(IB_PF_E_CUDA);
     }
     const Tables& t = in.tab;
     if (cudaMalloc(&in.gu, (size_t)(t.ng ? t.ng : 1) * es) != cudaSuccess ||
         cudaMalloc(&in.gv, (size_t)(t.ng ? t.ng : 1) * es) != cudaSuccess ||
-        cudaMalloc(&in.fval, (size_t)(t.nfu + t.nfv + 1) * es) != cudaSuccess) {
+        (in.dim == 3 && cudaMalloc(&in.gw, (size_t)(t.ng ? t.ng : 1) * es) != cudaSuccess) ||
+        cudaMalloc(&in.fval, (size_t)(t.nfu + t.nfv + t.nfw + 1) * es) != cudaSuccess) {
       ctx->err = "ghost scratch allocation failed";
       return bail(IB_PF_E_CUDA);
     }
@@ -277,7 +352,13 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     ctx->err = std::string("init: ") + cudaGetErrorString(cudaGetLastError());
     return bail(IB_PF_E_CUDA);
   }
-  {
+  if (ctx->dim == 3) {
+    cudaError_t e = step3d_setup(*ctx);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("3D setup: ") + cudaGetErrorString(e);
+      return bail(IB_PF_E_CUDA);
+    }
+  } else {
     BatchPlan* plan = new (std::nothrow) BatchPlan();
     if (!plan) { ctx->err = "out of host memory"; return bail(IB_PF_E_ARG); }
     ctx->plan = plan;
@@ -301,7 +382,9 @@ ib_pf_status ib_pf_precompute_weights(ib_pf_ctx* ctx) {
   for (Instance& in : ctx->inst) {
     int nf = 0;
     std::string gerr;
-    if (geometry_weights(in, ctx->work, &nf, gerr) != cudaSuccess)
+    const cudaError_t ge = in.dim == 3 ? geometry3_weights(in, ctx->work, &nf, gerr)
+                                       : geometry_weights(in, ctx->work, &nf, gerr);
+    if (ge != cudaSuccess)
       return fail(ctx, IB_PF_E_CUDA, "weights: " + gerr);
     total_fail += nf;
   }
@@ -356,11 +439,12 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
   if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
   if (!src) return fail(ctx, IB_PF_E_ARG, "null source");
   const bool lo_field = field_id == IB_PF_F_C_LO || field_id == IB_PF_F_C_OLD_LO;
-  if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field)
+  const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
+  if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field && !w_field)
     return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
   Instance& in = ctx->inst[instance];
   void* dst = field_ptr(*ctx, in, field_id);
-  if (!dst) return fail(ctx, IB_PF_E_ARG, "low parts of C exist only in FP32 contexts");
+  if (!dst) return fail(ctx, IB_PF_E_ARG, "low parts of C exist only in FP32 contexts, w only in 3D");
   const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
   if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
   CK(join_in(*ctx));
@@ -370,7 +454,12 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
     void* lo = field_ptr(*ctx, in, field_id == IB_PF_F_C ? IB_PF_F_C_LO : IB_PF_F_C_OLD_LO);
     CK(cudaMemsetAsync(lo, 0, (size_t)nbytes, ctx->work));
   }
-  if (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV) {
+  if (in.dim == 3 && w_field) {   // the wall planes of w are zero
+    const size_t plane = (size_t)in.nx * in.ny * ctx->esz;
+    CK(cudaMemsetAsync(dst, 0, plane, ctx->work));
+    CK(cudaMemsetAsync((char*)dst + (size_t)in.nz * plane, 0, plane, ctx->work));
+  }
+  if (in.dim == 2 && (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV)) {
     const size_t row = (size_t)in.nx * ctx->esz;
     CK(cudaMemsetAsync(dst, 0, row, ctx->work));
     CK(cudaMemsetAsync((char*)dst + (size_t)in.ny * row, 0, row, ctx->work));
@@ -389,24 +478,31 @@ ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* 
   if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
   Instance& in = ctx->inst[instance];
   const Tables& t = in.tab;
-  const size_t cells = (size_t)in.nx * in.ny;
+  const size_t nxy = (size_t)in.nx * in.ny, cells = nxy * in.nz;
   const void* src = nullptr;
   size_t n = 0, es = 8;
+  const size_t nap = (size_t)t.nap;
   switch (table_id) {
     case IB_PF_T_ALPHA_C: src = t.alpha_c; n = cells; break;
     case IB_PF_T_ALPHA_U: src = t.alpha_u; n = cells; break;
-    case IB_PF_T_ALPHA_V: src = t.alpha_v; n = cells + in.nx; break;
+    case IB_PF_T_ALPHA_V: src = t.alpha_v; n = in.dim == 3 ? cells : cells + in.nx; break;
     case IB_PF_T_CLASS: src = t.cmap; n = cells; es = 4; break;
     case IB_PF_T_GHOST_CELL: src = t.gcell; n = t.ng; es = 4; break;
-    case IB_PF_T_NORMAL: src = t.nrm; n = 2 * (size_t)t.ng; break;
+    case IB_PF_T_NORMAL: src = t.nrm; n = (size_t)in.dim * t.ng; break;
     case IB_PF_T_DN: src = t.dn; n = t.ng; break;
     case IB_PF_T_GAMMA: src = t.gamma; n = t.ng; break;
-    case IB_PF_T_AP1: src = t.ap1; n = (size_t)t.ng * kNap; es = 4; break;
-    case IB_PF_T_W1: src = t.w1; n = (size_t)t.ng * kNap; break;
-    case IB_PF_T_AP2: src = t.ap2; n = (size_t)t.ng * kNap; es = 4; break;
-    case IB_PF_T_W2: src = t.w2; n = (size_t)t.ng * kNap; break;
+    case IB_PF_T_AP1: src = t.ap1; n = (size_t)t.ng * nap; es = 4; break;
+    case IB_PF_T_W1: src = t.w1; n = (size_t)t.ng * nap; break;
+    case IB_PF_T_AP2: src = t.ap2; n = (size_t)t.ng * nap; es = 4; break;
+    case IB_PF_T_W2: src = t.w2; n = (size_t)t.ng * nap; break;
     case IB_PF_T_FACE_U: src = t.fu; n = t.nfu; es = 4; break;
     case IB_PF_T_FACE_V: src = t.fv; n = t.nfv; es = 4; break;
+    case IB_PF_T_ALPHA_W:
+      if (in.dim != 3) return fail(ctx, IB_PF_E_ARG, "alpha_w exists only in 3D");
+      src = t.alpha_w; n = cells + nxy; break;
+    case IB_PF_T_FACE_W:
+      if (in.dim != 3) return fail(ctx, IB_PF_E_ARG, "z-faces exist only in 3D");
+      src = t.fw; n = t.nfw; es = 4; break;
     default: return fail(ctx, IB_PF_E_ARG, "bad table id");
   }
   if (table_id >= IB_PF_T_NORMAL && table_id <= IB_PF_T_W2 && !ctx->weights_ready)
@@ -443,6 +539,7 @@ ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out) {
     case IB_PF_Q_N_GHOST: *out = in.tab.ng; return IB_PF_OK;
     case IB_PF_Q_N_FACE_U: *out = in.tab.nfu; return IB_PF_OK;
     case IB_PF_Q_N_FACE_V: *out = in.tab.nfv; return IB_PF_OK;
+    case IB_PF_Q_N_FACE_W: *out = in.tab.nfw; return IB_PF_OK;
     case IB_PF_Q_STATUS: {
       CK(join_in(*ctx));
       int s = 0;

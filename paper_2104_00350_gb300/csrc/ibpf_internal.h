@@ -11,7 +11,9 @@
 namespace ibpf {
 
 constexpr int kNap = 5;            // averaging points per interpolation point (2D)
+constexpr int kNap3 = 7;           // the same in 3D: the cell holding the point + 6 neighbours
 constexpr int kNsub = 100;         // subgrid points per direction for alpha (Sec. 4.1.1)
+constexpr int kNsub3 = 16;         // subgrid points per direction in 3D (16^3 per volume)
 constexpr int kMarchDiv = 100;     // normal-march step h/100 (Sec. 4.1.2)
 constexpr int kMarchMax = 1000;    // march limit: 10 h
 constexpr int kBisect = 60;        // bisection refinements of the intersect point
@@ -21,16 +23,33 @@ constexpr double kEps0 = 1.0e-30;  // epsilon_0 of Eq. NormalVectors_part2
 constexpr int kCellFluid = -1;
 constexpr int kCellSolid = -2;
 
+struct Sph {   // sphere centre and radius
+  double x, y, z, r;
+};
+
+// A union of spheres with a uniform bin grid over the periodic box: bin b lists every
+// sphere whose bounding box, grown by one cell, meets the bin (z bins clamped at the ends).
+struct SphereSet {
+  const Sph* sph = nullptr;
+  const int* bstart = nullptr;    // nb[0] nb[1] nb[2] + 1 offsets into blist
+  const int* blist = nullptr;
+  int nb[3] = {0, 0, 0};
+  double bs[3] = {0, 0, 0};       // bin edge lengths
+};
+
 struct WallDev {       // wall predicate parameters as the device sees them
   int kind;
   double p0, p1, w;    // w = (2 pi) * p[2]
+  double lx = 0, ly = 0, lz = 0;   // 3D: box (periodic images in x and y)
+  SphereSet ss;                    // 3D SPHERE / SPHERES
 };
 
 // geometry tables of one instance (device pointers, FP64 / int)
 struct Tables {
   double* alpha_c = nullptr;   // ny x nx
   double* alpha_u = nullptr;   // ny x nx
-  double* alpha_v = nullptr;   // (ny+1) x nx
+  double* alpha_v = nullptr;   // (ny+1) x nx; 3D: nz x ny x nx (y-faces)
+  double* alpha_w = nullptr;   // 3D: (nz+1) x ny x nx (z-faces)
   int* solidc = nullptr;       // ny x nx, 1 where the cell centre is solid
   int* cmap = nullptr;         // ny x nx, ghost index / kCellFluid / kCellSolid
   int ng = 0;
@@ -42,15 +61,19 @@ struct Tables {
   double* w1 = nullptr;
   int* ap2 = nullptr;
   double* w2 = nullptr;
-  int nfu = 0, nfv = 0;
+  int nap = kNap;              // averaging points per interpolation point (5 2D, 7 3D)
+  int nfu = 0, nfv = 0, nfw = 0;
   int* fu = nullptr;           // nfu linear x1-face indices
   int* fv = nullptr;           // nfv linear x2-face indices
+  int* fw = nullptr;           // 3D: nfw linear z-face indices
   int n_fallback = 0;
 };
 
 struct Instance {
+  int dim = 2;
   int nx = 0, ny = 0, lognx = 0, logny = 0;
-  double lx = 0, ly = 0, h = 0;
+  int nz = 1, lognz = 0;       // 3D
+  double lx = 0, ly = 0, lz = 0, h = 0;
   ib_pf_geometry geom{};
   ib_pf_params prm{};
   WallDev wall{};
@@ -63,6 +86,12 @@ struct Instance {
   void* P[2] = {nullptr, nullptr};
   void* Hu = nullptr;
   void* Hv = nullptr;
+  void* W[2] = {nullptr, nullptr};   // 3D z-face velocity
+  void* Hw = nullptr;
+  float* alpha_f = nullptr;          // 3D FP32 form: alpha_u, alpha_v, alpha_w in FP32
+  Sph* sph = nullptr;                // 3D sphere set (device copies)
+  int* bstart = nullptr;
+  int* blist = nullptr;
   // scratch of one step
   void* Q = nullptr;       // CH right-hand side (cells)
   void* phi = nullptr;     // chemical potential (cells)
@@ -72,7 +101,8 @@ struct Instance {
   void* spec = nullptr;    // ny x (nx/2+1) complex spectrum
   void* gu = nullptr;      // ng ghost-cell velocities
   void* gv = nullptr;
-  void* fval = nullptr;    // nfu + nfv re-interpolated face values
+  void* gw = nullptr;      // 3D
+  void* fval = nullptr;    // nfu + nfv (+ nfw) re-interpolated face values
   // transform tables
   double* lamx = nullptr;  // nx/2+1 eigenvalues of the periodic second difference
   double* lamy = nullptr;  // ny eigenvalues of the Neumann second difference
@@ -80,7 +110,12 @@ struct Instance {
   float* lamy_f = nullptr;
   void* twx = nullptr;     // nx/2 complex exp(-2 pi i k/nx), element type
   void* twy = nullptr;     // ny/2 complex exp(-2 pi i k/ny)
-  void* wdct = nullptr;    // ny complex exp(-i pi m/(2 ny))
+  void* wdct = nullptr;    // ny complex exp(-i pi m/(2 ny)); 3D: nz entries
+  // 3D: lamy holds the ny eigenvalues of the periodic y second difference, twy the ny/2
+  // y-FFT twiddles; the wall-normal z axis has its own tables
+  double* lamz = nullptr;  // nz eigenvalues of the Neumann second difference
+  float* lamz_f = nullptr;
+  void* twz = nullptr;     // nz/2 complex exp(-2 pi i k/nz)
   // reductions
   double* partial = nullptr;   // per-block partial sums
   unsigned* ticket = nullptr;  // last-block counter
@@ -120,6 +155,7 @@ struct Recorder {
 };
 
 struct Ctx {
+  int dim = 2;
   std::vector<Instance> inst;
   int precision = IB_PF_FP64;
   size_t esz = 8;
@@ -172,5 +208,17 @@ void set_global_error(const std::string& msg);
 
 // ---- step2d.cu (batched step: see batch.h)
 int mass_reduce(Instance& in, int precision, const void* C, const void* Clo, cudaStream_t s);
+
+// ---- geometry3d.cu: Sec. 4.1 in 3D (alpha, classes, ghosts, faces; weights)
+cudaError_t geometry3_init(Instance& in, const double* h_spheres, int n_spheres,
+                           cudaStream_t s, std::string& err);
+cudaError_t geometry3_weights(Instance& in, cudaStream_t s, int* n_fail, std::string& err);
+
+// ---- spectral.cu / step3d.cu: the 3D step, one instance after another
+cudaError_t spectral3_tables(Instance& in, int precision);
+int spectral3_solve(const Instance& in, int precision, int mode, int cur, cudaStream_t s,
+                    Recorder* rec);
+int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec);
+cudaError_t step3d_setup(Ctx& c);     // FP32 copies of the face fractions
 
 }  // namespace ibpf

@@ -273,6 +273,11 @@ struct SymbolArgs {
   const double* lamy;
   const float* lamx_f;   // FP32 path: eigenvalues computed in FP64, rounded once
   const float* lamy_f;
+  // 3D: the columns are (y mode, x mode) pairs c = ky * ncx + kx, lamy / lamy_f hold the z
+  // eigenvalues (the transformed axis) and lamyp / lamyp_f the periodic y ones; 0 in 2D
+  int ncx = 0;
+  const double* lamyp = nullptr;
+  const float* lamyp_f = nullptr;
 };
 
 // Divide X_m by the symbol at (k, m).  FP64 path: in FP64.  FP32 path: in FP32 -- the
@@ -283,14 +288,16 @@ template <typename T, typename C2>
 __device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs& sym) {
   if constexpr (sizeof(T) == 8) {
     // one reciprocal per point: the quotient is within 1.5 ulp of X / sigma
-    const double L = sym.lamy[m] + sym.lamx[k];
+    const double L = sym.ncx ? (sym.lamy[m] + sym.lamyp[k / sym.ncx]) + sym.lamx[k % sym.ncx]
+                             : sym.lamy[m] + sym.lamx[k];
     double r;
     if (sym.mode == 0) r = 1.0 / (L * L - sym.s_eta2 * L + sym.c0);
     else r = (L == 0.0) ? 0.0 : 1.0 / L;
     X.x = X.x * r;
     X.y = X.y * r;
   } else {
-    const float L = sym.lamy_f[m] + sym.lamx_f[k];
+    const float L = sym.ncx ? (sym.lamy_f[m] + sym.lamyp_f[k / sym.ncx]) + sym.lamx_f[k % sym.ncx]
+                            : sym.lamy_f[m] + sym.lamx_f[k];
     float r;
     if (sym.mode == 0) r = 1.0f / (L * L - (float)sym.s_eta2 * L + (float)sym.c0);
     else r = (L == 0.0f) ? 0.0f : 1.0f / L;
@@ -535,6 +542,58 @@ __global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restr
 #undef IBPF_CASE
 }
 
+// ------------------------------------------------------------------ 3D: y transforms
+// Complex FFT of length ny = 2^LOGN along y of the KC = 8 THREADS / ny columns
+// kx0 .. kx0 + KC - 1 (columns at or beyond nh1 are skipped) of z-plane `plane` of the
+// spectrum spec[(k ny + j) nh1 + kx].  INV: inverse transform scaled by 1/ny.
+template <typename T, int LOGN, int THREADS, bool INV>
+__device__ void yfft_core(typename C2T<T>::type* __restrict__ spec, int nh1, size_t plane,
+                          const typename C2T<T>::type* __restrict__ tw, int kx0,
+                          typename C2T<T>::type* xs) {
+  using C2 = typename C2T<T>::type;
+  constexpr int N = 1 << LOGN, EB = 8 * THREADS, KC = EB / N;
+  static_assert(KC >= 1, "a block holds 8 points per thread");
+  C2* tws = xs + fft_buf(EB);
+  for (int t = threadIdx.x; t < N / 2; t += THREADS) tws[t] = tw[t];
+  C2* base = spec + plane * (size_t)N * nh1;
+  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+    const int cc = idx % KC, j = idx / KC;
+    const int kx = kx0 + cc;
+    C2 v;
+    v.x = T(0);
+    v.y = T(0);
+    if (kx < nh1) v = base[(size_t)j * nh1 + kx];
+    xs[pad(cc * N + j)] = v;
+  }
+  __syncthreads();
+  stockham<LOGN, 0, INV, THREADS, T>(xs, tws, KC);
+  const T sc = INV ? T(1) / T(N) : T(1);
+  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+    const int cc = idx % KC, j = idx / KC;
+    const int kx = kx0 + cc;
+    C2 v = xs[pad(cc * N + j)];
+    v.x *= sc;
+    v.y *= sc;
+    if (kx < nh1) base[(size_t)j * nh1 + kx] = v;
+  }
+  __syncthreads();
+}
+
+// block b: z-plane b / nbp, columns (b % nbp) * fft_per_block(ny) ..
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kFftSmallThreads) k3_yfft(
+    typename C2T<T>::type* __restrict__ spec, int nh1, int ny, int nbp,
+    const typename C2T<T>::type* __restrict__ tw) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const size_t plane = blockIdx.x / nbp;
+  const int kx0 = (int)(blockIdx.x % nbp) * fft_per_block(ny);
+#define IBPF_CASE(L) case L: yfft_core<T, L, kFftSmallThreads, INV>(spec, nh1, plane, tw, kx0, x); break;
+  switch (31 - __clz(ny)) { IBPF_CASES_128 default: break; }
+#undef IBPF_CASE
+}
+
 template <typename T>
 cudaError_t tables_t(Instance& in) {
   using C2 = typename C2T<T>::type;
@@ -591,6 +650,120 @@ cudaError_t tables_t(Instance& in) {
   cudaFuncSetAttribute(kb_rows_inv<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   cudaFuncSetAttribute(kb_cols<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   return cudaGetLastError();
+}
+
+// 3D tables: lamx (nx/2+1, periodic x), lamy (ny, periodic y), lamz (nz, Neumann z) and the
+// FP32 copies; twiddles of the x, y and z transforms and the z cosine weights
+template <typename T>
+cudaError_t tables3_t(Instance& in) {
+  using C2 = typename C2T<T>::type;
+  const int nx = in.nx, ny = in.ny, nz = in.nz;
+  const double h = in.h;
+  std::vector<double> lx(nx / 2 + 1), ly(ny), lz(nz);
+  for (int k = 0; k <= nx / 2; ++k) {
+    const double sn = std::sin(M_PI * (double)k / (double)nx);
+    lx[k] = -(4.0 / (h * h)) * sn * sn;
+  }
+  for (int j = 0; j < ny; ++j) {
+    const double sn = std::sin(M_PI * (double)j / (double)ny);
+    ly[j] = -(4.0 / (h * h)) * sn * sn;
+  }
+  for (int m = 0; m < nz; ++m) {
+    const double sn = std::sin(M_PI * (double)m / (2.0 * (double)nz));
+    lz[m] = -(4.0 / (h * h)) * sn * sn;
+  }
+  auto twiddles = [](int n) {
+    std::vector<C2> t(n / 2);
+    for (int k = 0; k < n / 2; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)n;
+      t[k].x = (T)std::cos(a);
+      t[k].y = (T)(-std::sin(a));
+    }
+    return t;
+  };
+  std::vector<C2> twx = twiddles(nx), twy = twiddles(ny), twz = twiddles(nz), wd(nz);
+  for (int m = 0; m < nz; ++m) {
+    const double a = M_PI * (double)m / (2.0 * (double)nz);
+    wd[m].x = (T)std::cos(a);
+    wd[m].y = (T)(-std::sin(a));
+  }
+  std::vector<float> lxf(lx.begin(), lx.end()), lyf(ly.begin(), ly.end()), lzf(lz.begin(), lz.end());
+  cudaError_t e = cudaSuccess;
+  auto put = [&](void** dst, const void* src, size_t bytes) {
+    if ((e = cudaMalloc(dst, bytes)) != cudaSuccess) return false;
+    return (e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice)) == cudaSuccess;
+  };
+  if (!put((void**)&in.lamx, lx.data(), sizeof(double) * lx.size()) ||
+      !put((void**)&in.lamy, ly.data(), sizeof(double) * ly.size()) ||
+      !put((void**)&in.lamz, lz.data(), sizeof(double) * lz.size()) ||
+      !put((void**)&in.lamx_f, lxf.data(), sizeof(float) * lxf.size()) ||
+      !put((void**)&in.lamy_f, lyf.data(), sizeof(float) * lyf.size()) ||
+      !put((void**)&in.lamz_f, lzf.data(), sizeof(float) * lzf.size()) ||
+      !put(&in.twx, twx.data(), sizeof(C2) * twx.size()) ||
+      !put(&in.twy, twy.data(), sizeof(C2) * twy.size()) ||
+      !put(&in.twz, twz.data(), sizeof(C2) * twz.size()) ||
+      !put(&in.wdct, wd.data(), sizeof(C2) * wd.size()))
+    return e;
+  return cudaSuccess;
+}
+
+// One 3D solve: x rows, y columns, z cosine transform + symbol + inverse, y inverse, x rows
+// inverse with the epilogue of the batched 2D solve (mode 0: C increment into the C^{n-1}
+// slot, compensated in FP32; mode 1: P^{n+1} = P^ + dP).
+template <typename T>
+int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Recorder* rec) {
+  using C2 = typename C2T<T>::type;
+  constexpr int S = kFftSmallThreads;
+  const int nx = in.nx, ny = in.ny, nz = in.nz, nh1 = nx / 2 + 1;
+  const int rows = ny * nz;
+  const int rp = fft_per_block(nx), yp = fft_per_block(ny), cp = fft_per_block(nz);
+  C2* spec = (C2*)in.spec;
+  // n <= 1024: at most 26 / 26 / 42 KiB of shared memory, below the default limit
+  const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
+  const size_t ysm = sizeof(C2) * (fft_buf(8 * S) + ny / 2);
+  const size_t csm = sizeof(C2) * (fft_buf(8 * S) + nz / 2 + nz);
+  const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
+  k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, (const C2*)in.twx);
+  if (rec) rec->mark("rows_fwd", s);
+  const int nbp = (nh1 + yp - 1) / yp;
+  k3_yfft<T, false><<<nz * nbp, S, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  if (rec) rec->mark("y_fft", s);
+  SymbolArgs sym;
+  sym.mode = mode;
+  sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
+  sym.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
+  sym.lamx = in.lamx;
+  sym.lamy = in.lamz;
+  sym.lamx_f = in.lamx_f;
+  sym.lamy_f = in.lamz_f;
+  sym.ncx = nh1;
+  sym.lamyp = in.lamy;
+  sym.lamyp_f = in.lamy_f;
+  const int ncols = ny * nh1;
+  k_cols<T><<<(ncols + cp - 1) / cp, S, csm, s>>>(spec, ncols, nz, (const C2*)in.twz,
+                                                   (const C2*)in.wdct, sym);
+  if (rec) rec->mark("z_solve", s);
+  k3_yfft<T, true><<<nz * nbp, S, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  if (rec) rec->mark("y_ifft", s);
+  EpiArgs epi;
+  T* out;
+  if (mode == 0) {
+    epi.kind = 1;
+    epi.a = in.C[cur];
+    epi.b = in.C[1 - cur];
+    epi.a_lo = in.Clo[cur];
+    epi.b_lo = in.Clo[1 - cur];
+    epi.out_lo = in.Clo[1 - cur];
+    out = (T*)in.C[1 - cur];
+  } else {
+    epi.kind = 2;
+    epi.a = in.phat;
+    epi.delta = in.dp;
+    out = (T*)in.P[1 - cur];
+  }
+  k_rows_inv<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, rows, (const C2*)in.twx, epi);
+  if (rec) rec->mark("rows_inv", s);
+  return 5;
 }
 
 }  // namespace
@@ -665,6 +838,16 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   EpiArgs plain;
   k_rows_inv<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, ny, twx, plain);
   return 3;
+}
+
+cudaError_t spectral3_tables(Instance& in, int precision) {
+  return precision == IB_PF_FP64 ? tables3_t<double>(in) : tables3_t<float>(in);
+}
+
+int spectral3_solve(const Instance& in, int precision, int mode, int cur, cudaStream_t s,
+                    Recorder* rec) {
+  return precision == IB_PF_FP64 ? spectral3_solve_t<double>(in, mode, cur, s, rec)
+                                 : spectral3_solve_t<float>(in, mode, cur, s, rec);
 }
 
 cudaError_t spectral_tables(Instance& in, int precision) {

@@ -13,21 +13,15 @@
 #include <vector>
 
 #include "batch.h"
+#include "cell_common.cuh"
 #include "ibpf_internal.h"
 
 namespace ibpf {
 namespace {
 
-constexpr double kKappa = 1.0606601717798212;   // 3 / (2 sqrt 2)
 
 __device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : i - 1; }
 
-// C clamped to [-1, 1] for the property laws rho(C), mu(C): keeps rho >= rho0 = min(rho_l,
-// rho_g), the bound the Dodd-Ferrante split of Eq. PressurePoisson rests on
-template <typename T>
-__device__ __forceinline__ T clamp1(T c) {
-  return c > T(1) ? T(1) : (c < T(-1) ? T(-1) : c);
-}
 __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
 
 // ---------------------------------------------------------------- a1: CH right-hand side
@@ -376,70 +370,6 @@ __device__ __forceinline__ void correct_cell(const StepArgs<T>& a, const T* __re
   bad |= !isfinite(C[r + i]);
 }
 
-// (hi, lo) += (b_hi, b_lo) without rounding loss in FP32 (TwoSum, then renormalise); plain
-// addition in FP64.
-template <typename T>
-__device__ __forceinline__ void pair_add(T& hi, T& lo, T b_hi, T b_lo) {
-  if constexpr (sizeof(T) == 8) {
-    hi = hi + (b_hi + b_lo);
-  } else {
-    const T s = hi + b_hi;
-    const T bb = s - hi;
-    const T e = (hi - (s - bb)) + (b_hi - bb);
-    const T l = (lo + b_lo) + e;
-    hi = s + l;
-    lo = l - (hi - s);
-  }
-}
-
-// Block reduction of one tile's sum of C in a fixed tree (FP64, or compensated FP32 pairs
-// in the FP32 form), written as FP64 at the tile's index; the last tile of an instance to
-// finish adds the partials in index order in FP64.
-template <typename T>
-__device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__ partial,
-                          unsigned* __restrict__ ticket, double* __restrict__ mass) {
-  __shared__ T rh[kTileX * kTileY];
-  __shared__ T rl[kTileX * kTileY];
-  __shared__ double red[kTileX * kTileY];
-  __shared__ bool last;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
-  rh[tid] = hi;
-  rl[tid] = lo;
-  __syncthreads();
-  for (int s = nthr / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      T a_hi = rh[tid], a_lo = rl[tid];
-      pair_add(a_hi, a_lo, rh[tid + s], rl[tid + s]);
-      rh[tid] = a_hi;
-      rl[tid] = a_lo;
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    partial[tile] = (double)rh[0] + (double)rl[0];
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    double sacc = 0.0;
-    for (int b = tid; b < ntiles; b += nthr) sacc += ((volatile double*)partial)[b];
-    red[tid] = sacc;
-    __syncthreads();
-    for (int q = nthr / 2; q > 0; q >>= 1) {
-      if (tid < q) red[tid] += red[tid + q];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      *mass = red[0];
-      *ticket = 0u;
-    }
-  }
-  __syncthreads();
-}
-
 // stand-alone FP64 sum of a cell field (same reduction as in k_correct)
 template <typename T>
 __global__ void k_mass(int n, const T* __restrict__ C, const T* __restrict__ Clo,
@@ -768,7 +698,7 @@ __global__ void IBPF_CELL_BOUNDS kb_correct(const InstDev<T>* __restrict__ I, co
     }
     if (bad) atomicOr(d.status, 1);
     const int ntiles = d.gx * ((d.ny + kTileH - 1) / kTileH);
-    tile_mass<T>(s_hi, s_lo, w_.y, ntiles, d.partial, d.ticket, d.mass);
+    tile_mass<T, kTileX * kTileY>(s_hi, s_lo, w_.y, ntiles, d.partial, d.ticket, d.mass);
   }
 }
 
@@ -950,7 +880,7 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
 
 template <typename T>
 int mass_t(Instance& in, const void* C, const void* Clo, cudaStream_t s) {
-  const int n = in.nx * in.ny;
+  const int n = in.nx * in.ny * in.nz;
   int nb = (n + 255) / 256;
   if (nb > in.nblk_red) nb = in.nblk_red;
   k_mass<T><<<nb, 256, 0, s>>>(n, (const T*)C, (const T*)Clo, in.partial, in.ticket, in.mass);

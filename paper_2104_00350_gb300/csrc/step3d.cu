@@ -1,0 +1,577 @@
+// One time step of the hybrid IB / phase-field method on a 3D staggered grid (Sec. 4.2 and
+// Appendix A of arXiv 2104.00350 with the third axis), templated on the field type T.
+//
+// Layout: cells (k, j, i) at (k ny + j) nx + i; u on x-faces (face i = left face of cell i),
+// v on y-faces (face j = front face of cell j), both nz x ny x nx; w on z-faces, (nz+1)
+// planes with planes 0 and nz on the walls.  Periodic in x and y; at the z walls C, phi and
+// P take mirror planes and the tangential velocities u, v the no-slip ghost planes -u, -v.
+// Discrete operators as in 2D: 7-point Laplacian, arithmetic face means, edge viscosities
+// from the mean C of the four cells around the edge, divergence-form convection with the
+// products of face means at the edges.  The solves work on increments exactly as the 2D
+// step does (CH: over the BDF2 predictor B; pressure: over P^ = 2P^n - P^{n-1}).
+#include <cmath>
+#include <vector>
+
+#include "batch.h"
+#include "cell_common.cuh"
+#include "ibpf_internal.h"
+
+namespace ibpf {
+namespace {
+
+template <typename T>
+struct S3 {
+  int nx, ny, nz, lnx, lny;
+  T inv_h, inv_h2, dt, S, inv_eta2, pe_eta2, inv_dt, eta2;
+  T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
+  double k_wet, cos_th, l_s;
+  // fields (level cur is n)
+  const T* C;    // C^n
+  const T* Co;   // C^{n-1}
+  T* C1;         // C^{n+1} (the C^{n-1} slot after the solve)
+  T* C1lo;
+  const T *U, *V, *W, *Uo, *Vo, *Wo;   // u^n, u^{n-1}
+  T *Us, *Vs, *Ws;                     // u** and then u^{n+1} (the n-1 slots)
+  T *Hu, *Hv, *Hw;
+  const T *P, *Po;
+  T *Q, *phi, *rhs, *phat, *dp;
+  T *gu, *gv, *gw, *fval;
+  const T *au, *av, *aw;   // face fractions in the field type
+  Tables tab;
+  double* partial;
+  unsigned* ticket;
+  double* mass;
+  int* status;
+};
+
+constexpr int kT3 = 256;   // threads of the cell kernels (one cell each)
+
+template <typename T>
+__device__ __forceinline__ void cell_ijk(const S3<T>& a, size_t c, int& i, int& j, int& k) {
+  i = (int)(c & (size_t)(a.nx - 1));
+  j = (int)((c >> a.lnx) & (size_t)(a.ny - 1));
+  k = (int)(c >> (a.lnx + a.lny));
+}
+
+// linear index of cell (i, j, k), periodic in x and y (k unchanged)
+template <typename T>
+__device__ __forceinline__ size_t lin(const S3<T>& a, int i, int j, int k) {
+  return ((size_t)k * a.ny + (size_t)((j + a.ny) & (a.ny - 1))) * a.nx + (size_t)((i + a.nx) & (a.nx - 1));
+}
+
+template <typename T>
+__device__ __forceinline__ int kmir(const S3<T>& a, int k) {   // mirror planes at the walls
+  return k < 0 ? 0 : (k >= a.nz ? a.nz - 1 : k);
+}
+
+// 7-point Laplacian of a cell field with mirror planes in z
+template <typename T, typename F>
+__device__ __forceinline__ T lap7(const S3<T>& a, F f, int i, int j, int k) {
+  const T c0 = f(i, j, k);
+  return ((((f(i + 1, j, k) + f(i - 1, j, k)) + (f(i, j + 1, k) + f(i, j - 1, k))) +
+           (f(i, j, kmir(a, k + 1)) + f(i, j, kmir(a, k - 1)))) - T(6) * c0) * a.inv_h2;
+}
+
+// ---------------------------------------------------------------- a1: CH right-hand side
+// h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_ch_h(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const T third = T(1.0 / 3.0);
+  auto B = [&](int ii, int jj, int kk) {
+    const size_t q = lin(a, ii, jj, kk);
+    return a.C[q] + (a.C[q] - a.Co[q]) * third;
+  };
+  const T lapb = lap7(a, B, i, j, k);
+  const T d = a.C[c] - a.Co[c];
+  const T ct = a.C[c] + d;
+  a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+}
+
+// R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
+// through the z walls
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_ch_rhs(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
+  auto ut = [&](size_t q) { return T(2) * a.U[q] - a.Uo[q]; };
+  auto vt = [&](size_t q) { return T(2) * a.V[q] - a.Vo[q]; };
+  auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
+  const size_t nxy = (size_t)a.nx * a.ny;
+  const T c0 = ct(c);
+  const size_t xp = lin(a, i + 1, j, k), xm = lin(a, i - 1, j, k);
+  const size_t yp = lin(a, i, j + 1, k), ym = lin(a, i, j - 1, k);
+  const T fx_w = ut(c) * (T(0.5) * (ct(xm) + c0));
+  const T fx_e = ut(xp) * (T(0.5) * (c0 + ct(xp)));
+  const T fy_s = vt(c) * (T(0.5) * (ct(ym) + c0));
+  const T fy_n = vt(yp) * (T(0.5) * (c0 + ct(yp)));
+  const T fz_b = k > 0 ? wt(c) * (T(0.5) * (ct(c - nxy) + c0)) : T(0);
+  const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + ct(c + nxy))) : T(0);
+  const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+  auto hf = [&](int ii, int jj, int kk) { return a.phi[lin(a, ii, jj, kk)]; };
+  a.Q[c] = lap7(a, hf, i, j, k) - a.pe_eta2 * div;
+}
+
+// ------------------------------------------------------------ a3 / a4: ghost fills, phi
+template <typename T>
+__device__ __forceinline__ T gather7(const T* __restrict__ f, const int* __restrict__ ap,
+                                     const double* __restrict__ w, int g) {
+  T acc = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap3; ++q) acc = acc + (T)w[(size_t)g * kNap3 + q] * f[ap[(size_t)g * kNap3 + q]];
+  return acc;
+}
+
+// static contact angle, the same cut-off rule as the 2D step (see step2d.cu)
+template <typename T>
+__global__ void k3_fill_C(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  const T cm = T(2) * gather7(a.C1, t.ap1, t.w1, g) - gather7(a.C1, t.ap2, t.w2, g);
+  const T gam = (T)t.gamma[g], dn = (T)t.dn[g];
+  const T kk = (T)a.k_wet / (gam * dn);
+  const T qa = T(-0.75) * (T)a.cos_th;
+  const T qc = kk * cm + T(0.75) * (T)a.cos_th;
+  T disc = kk * kk - T(4) * qa * qc;
+  disc = disc > T(0) ? disc : T(0);
+  const T sq = sqrt(disc);
+  T ci = T(2) * qc / (kk + sq);
+  if (!(fabs(ci) <= T(1)) && qa != T(0)) {
+    ci = (kk + sq) / (T(2) * qa);
+    ci = ci > T(1) ? T(1) : (ci < T(-1) ? T(-1) : ci);
+  }
+  if (fabs(cm) >= T(1)) ci = cm;
+  a.C1[t.gcell[g]] = ((gam + T(1)) * ci - cm) / gam;
+  if (a.C1lo) a.C1lo[t.gcell[g]] = T(0);
+}
+
+// phi = psi'(C) - Cn^2 lap C on every cell
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_chem_pot(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  auto cf = [&](int ii, int jj, int kk) { return a.C1[lin(a, ii, jj, kk)]; };
+  const T c0 = a.C1[c];
+  a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7(a, cf, i, j, k);
+}
+
+// zero normal gradient of phi at the wall: phi_G = phi_M
+template <typename T>
+__global__ void k3_fill_phi(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
+}
+
+// ------------------------------------------------- a5: AB2 predictor + penalisation (3D)
+// H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho_f)
+// u* = u^n + dt (3/2 H^n - 1/2 H^{n-1} + (kappa/(Re Ca Cn)) phi_f dC/dn_f / rho_f), u** = alpha_f u*
+// Thread (i, j, k) updates x-face (i, j, k), y-face (i, j, k) and, for k >= 1, z-face (i, j, k).
+// Edges: xy-edge (i-1/2, j-1/2, k), xz-edge (i-1/2, j, k-1/2), yz-edge (i, j-1/2, k-1/2).
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_predict(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const T ih = a.inv_h;
+  auto Cc = [&](int ii, int jj, int kk) { return a.C1[lin(a, ii, jj, kmir(a, kk))]; };
+  auto Fc = [&](int ii, int jj, int kk) { return a.phi[lin(a, ii, jj, kk)]; };
+  // tangential velocities with the no-slip ghost planes beyond the z walls
+  auto Ug = [&](int ii, int jj, int kk) {
+    return kk < 0 ? -a.U[lin(a, ii, jj, 0)] : (kk >= a.nz ? -a.U[lin(a, ii, jj, a.nz - 1)] : a.U[lin(a, ii, jj, kk)]);
+  };
+  auto Vg = [&](int ii, int jj, int kk) {
+    return kk < 0 ? -a.V[lin(a, ii, jj, 0)] : (kk >= a.nz ? -a.V[lin(a, ii, jj, a.nz - 1)] : a.V[lin(a, ii, jj, kk)]);
+  };
+  auto Wf = [&](int ii, int jj, int kk) { return a.W[lin(a, ii, jj, kk)]; };   // kk in 0..nz
+  auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
+  auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
+  auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
+  auto txy = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj - 1/2, kk)
+    const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+    return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
+  };
+  auto txz = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj, kk - 1/2), kk = 0..nz
+    const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+    return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
+  };
+  auto tyz = [&](int ii, int jj, int kk) {   // edge (ii, jj - 1/2, kk - 1/2)
+    const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
+    return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
+  };
+  auto uv = [&](int ii, int jj, int kk) {
+    return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
+  };
+  auto uw = [&](int ii, int jj, int kk) {
+    return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
+  };
+  auto vw = [&](int ii, int jj, int kk) {
+    return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
+  };
+  const T k_st = a.k_st;
+  // ---- x-face (i - 1/2, j, k)
+  {
+    const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
+    const T rho_f = rho(T(0.5) * (cL + cR));
+    const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
+                   (txz(i, j, k + 1) - txz(i, j, k)) * ih;
+    const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
+    const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
+    const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
+                   (uw(i, j, k + 1) - uw(i, j, k)) * ih;
+    const T H = -conv + visc / (a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
+    const T us = a.U[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hu[c]) + st);
+    a.Hu[c] = H;
+    a.Us[c] = a.au[c] * us;
+  }
+  // ---- y-face (i, j - 1/2, k)
+  {
+    const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
+    const T rho_f = rho(T(0.5) * (cB + cA));
+    const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
+                   (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
+    const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
+    const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
+    const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
+                   (vw(i, j, k + 1) - vw(i, j, k)) * ih;
+    const T H = -conv + visc / (a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
+    const T vs = a.V[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hv[c]) + st);
+    a.Hv[c] = H;
+    a.Vs[c] = a.av[c] * vs;
+  }
+  // ---- z-face (i, j, k - 1/2), 1 <= k <= nz - 1
+  if (k >= 1) {
+    const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
+    const T rho_f = rho(T(0.5) * (cB + cA));
+    const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
+                   (tzz(k) - tzz(k - 1)) * ih;
+    const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
+    const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
+    const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
+                   (wcA * wcA - wcB * wcB) * ih;
+    const T H = -conv + visc / (a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
+    const T ws = a.W[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hw[c]) + st);
+    a.Hw[c] = H;
+    a.Ws[c] = a.aw[c] * ws;
+  }
+}
+
+// ------------------------------------------------------------- a6: velocity ghost fill (3D)
+// centred u** at the averaging cells, mirror values by Eq. extrapolation, V_nG = -V_nM/gamma
+// (Eq. NoPenetration), V_tG = V_tM (l_s - dn)/(l_s + gamma dn) (Eq. UpdateVtan, static
+// angle) for the tangential vector V_t = u - V_n n, u_G = V_nG n + V_tG (Eq. UpdateVandW)
+template <typename T>
+__device__ __forceinline__ T ucen3(const S3<T>& a, size_t c) {
+  const int i = (int)(c & (size_t)(a.nx - 1));
+  return T(0.5) * (a.Us[c] + a.Us[c - i + ((i + 1) & (a.nx - 1))]);
+}
+template <typename T>
+__device__ __forceinline__ T vcen3(const S3<T>& a, size_t c) {
+  const int j = (int)((c >> a.lnx) & (size_t)(a.ny - 1));
+  const size_t row0 = c - ((size_t)j << a.lnx);
+  return T(0.5) * (a.Vs[c] + a.Vs[row0 + ((size_t)((j + 1) & (a.ny - 1)) << a.lnx)]);
+}
+template <typename T>
+__device__ __forceinline__ T wcen3(const S3<T>& a, size_t c) {
+  return T(0.5) * (a.Ws[c] + a.Ws[c + ((size_t)a.nx << a.lny)]);
+}
+
+template <typename T>
+__global__ void k3_fill_u(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  T u1 = T(0), v1 = T(0), w1 = T(0), u2 = T(0), v2 = T(0), w2 = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap3; ++q) {
+    const size_t c1 = t.ap1[(size_t)g * kNap3 + q], c2 = t.ap2[(size_t)g * kNap3 + q];
+    const T a1 = (T)t.w1[(size_t)g * kNap3 + q], a2 = (T)t.w2[(size_t)g * kNap3 + q];
+    u1 = u1 + a1 * ucen3(a, c1);
+    v1 = v1 + a1 * vcen3(a, c1);
+    w1 = w1 + a1 * wcen3(a, c1);
+    u2 = u2 + a2 * ucen3(a, c2);
+    v2 = v2 + a2 * vcen3(a, c2);
+    w2 = w2 + a2 * wcen3(a, c2);
+  }
+  const T uM = T(2) * u1 - u2, vM = T(2) * v1 - v2, wM = T(2) * w1 - w2;
+  const T n1 = (T)t.nrm[3 * (size_t)g], n2 = (T)t.nrm[3 * (size_t)g + 1], n3 = (T)t.nrm[3 * (size_t)g + 2];
+  const T gam = (T)t.gamma[g], dn = (T)t.dn[g], ls = (T)a.l_s;
+  const T vnM = (uM * n1 + vM * n2) + wM * n3;
+  const T f = (ls - dn) / (ls + gam * dn);
+  const T vnG = -vnM / gam;
+  a.gu[g] = vnG * n1 + f * (uM - vnM * n1);
+  a.gv[g] = vnG * n2 + f * (vM - vnM * n2);
+  a.gw[g] = vnG * n3 + f * (wM - vnM * n3);
+}
+
+// faces with alpha_f < 1 touching a ghost: mean of the two cell-centred values (ghost value,
+// 0 in a solid non-ghost cell, pre-fix centred u** in a fluid cell), staged in fval
+template <typename T>
+__global__ void k3_face_values(S3<T> a) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  const size_t nxy = (size_t)a.nx * a.ny;
+  if (f < t.nfu) {
+    const size_t c = t.fu[f];
+    const int i = (int)(c & (size_t)(a.nx - 1));
+    const size_t cl = c - i + ((i + a.nx - 1) & (a.nx - 1));
+    auto val = [&](size_t cc) -> T {
+      const int m = t.cmap[cc];
+      return m >= 0 ? a.gu[m] : (m == kCellSolid ? T(0) : ucen3(a, cc));
+    };
+    a.fval[f] = T(0.5) * (val(cl) + val(c));
+  } else if (f < t.nfu + t.nfv) {
+    const size_t c = t.fv[f - t.nfu];
+    const int j = (int)((c >> a.lnx) & (size_t)(a.ny - 1));
+    const size_t cb = c - ((size_t)j << a.lnx) + ((size_t)((j + a.ny - 1) & (a.ny - 1)) << a.lnx);
+    auto val = [&](size_t cc) -> T {
+      const int m = t.cmap[cc];
+      return m >= 0 ? a.gv[m] : (m == kCellSolid ? T(0) : vcen3(a, cc));
+    };
+    a.fval[f] = T(0.5) * (val(cb) + val(c));
+  } else if (f < t.nfu + t.nfv + t.nfw) {
+    const size_t c = t.fw[f - t.nfu - t.nfv];   // z-face k in 1..nz-1: cells k-1 and k
+    auto val = [&](size_t cc) -> T {
+      const int m = t.cmap[cc];
+      return m >= 0 ? a.gw[m] : (m == kCellSolid ? T(0) : wcen3(a, cc));
+    };
+    a.fval[f] = T(0.5) * (val(c - nxy) + val(c));
+  }
+}
+
+template <typename T>
+__global__ void k3_face_scatter(S3<T> a) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (f < t.nfu) a.Us[t.fu[f]] = a.fval[f];
+  else if (f < t.nfu + t.nfv) a.Vs[t.fv[f - t.nfu]] = a.fval[f];
+  else if (f < t.nfu + t.nfv + t.nfw) a.Ws[t.fw[f - t.nfu - t.nfv]] = a.fval[f];
+}
+
+// ------------------------------------------------------------------ a7: Poisson RHS (3D)
+// lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_poisson_rhs(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  auto ph = [&](size_t q) { return T(2) * a.P[q] - a.Po[q]; };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const T* C = a.C1;
+  const T p0 = ph(c);
+  const size_t xp = lin(a, i + 1, j, k), xm = lin(a, i - 1, j, k);
+  const size_t yp = lin(a, i, j + 1, k), ym = lin(a, i, j - 1, k);
+  const T gx_w = (a.rho0 / rho(T(0.5) * (C[xm] + C[c]))) * ((p0 - ph(xm)) * a.inv_h);
+  const T gx_e = (a.rho0 / rho(T(0.5) * (C[c] + C[xp]))) * ((ph(xp) - p0) * a.inv_h);
+  const T gy_s = (a.rho0 / rho(T(0.5) * (C[ym] + C[c]))) * ((p0 - ph(ym)) * a.inv_h);
+  const T gy_n = (a.rho0 / rho(T(0.5) * (C[c] + C[yp]))) * ((ph(yp) - p0) * a.inv_h);
+  T gz_b = T(0), gz_t = T(0);
+  if (k > 0) gz_b = (a.rho0 / rho(T(0.5) * (C[c - nxy] + C[c]))) * ((p0 - ph(c - nxy)) * a.inv_h);
+  if (k < a.nz - 1) gz_t = (a.rho0 / rho(T(0.5) * (C[c] + C[c + nxy]))) * ((ph(c + nxy) - p0) * a.inv_h);
+  const T div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
+  const T div_u = ((a.Us[xp] - a.Us[c]) * a.inv_h + (a.Vs[yp] - a.Vs[c]) * a.inv_h) +
+                  (a.Ws[c + nxy] - a.Ws[c]) * a.inv_h;
+  a.rhs[c] = (a.rho0 * a.inv_dt) * div_u - div_g;
+  a.phat[c] = p0;
+}
+
+// ------------------------------------------------- a8: correction + status and mass (3D)
+// u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces 1..nz-1)
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_correct(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const T* C = a.C1;
+  int bad = 0;
+  auto corr = [&](const T* vel, size_t nb) {
+    const T rho_f = rho(T(0.5) * (C[nb] + C[c]));
+    const T vn = vel[c] - a.dt * (((a.phat[c] - a.phat[nb]) * a.inv_h) / rho_f +
+                                  a.inv_rho0 * ((a.dp[c] - a.dp[nb]) * a.inv_h));
+    bad |= !isfinite(vn);
+    return vn;
+  };
+  const T un = corr(a.Us, lin(a, i - 1, j, k));
+  const T vn = corr(a.Vs, lin(a, i, j - 1, k));
+  T wn = T(0);
+  if (k >= 1) wn = corr(a.Ws, c - nxy);
+  bad |= !isfinite(C[c]);
+  a.Us[c] = un;
+  a.Vs[c] = vn;
+  if (k >= 1) a.Ws[c] = wn;
+  if (bad) atomicOr(a.status, 1);
+  const T lo = a.C1lo ? a.C1lo[c] : T(0);
+  const size_t ntiles = (nxy * a.nz) / kT3;
+  tile_mass<T, kT3>(C[c], lo, (int)blockIdx.x, (int)ntiles, a.partial, a.ticket, a.mass);
+}
+
+template <typename T>
+S3<T> make3(const Instance& in, int cur) {
+  const ib_pf_params& p = in.prm;
+  S3<T> a;
+  a.nx = in.nx;
+  a.ny = in.ny;
+  a.nz = in.nz;
+  a.lnx = in.lognx;
+  a.lny = in.logny;
+  a.inv_h = (T)(1.0 / in.h);
+  a.inv_h2 = (T)(1.0 / (in.h * in.h));
+  a.dt = (T)p.dt;
+  const double eta2 = p.Cn * p.Cn;
+  a.S = (T)p.S;
+  a.inv_eta2 = (T)(1.0 / eta2);
+  a.pe_eta2 = (T)(p.Pe / eta2);
+  a.inv_dt = (T)(1.0 / p.dt);
+  a.eta2 = (T)eta2;
+  const double rho_l = 1.0, rho_g = 1.0 / p.rho_ratio, mu_l = 1.0, mu_g = 1.0 / p.mu_ratio;
+  a.rho_a = (T)(0.5 * (rho_l + rho_g));
+  a.rho_b = (T)(0.5 * (rho_l - rho_g));
+  a.mu_a = (T)(0.5 * (mu_l + mu_g));
+  a.mu_b = (T)(0.5 * (mu_l - mu_g));
+  const double rho0 = rho_l < rho_g ? rho_l : rho_g;
+  a.rho0 = (T)rho0;
+  a.inv_rho0 = (T)(1.0 / rho0);
+  a.Re = (T)p.Re;
+  a.k_st = (T)(kKappa / (p.Re * p.Ca * p.Cn));
+  a.k_wet = kKappa * p.Cn;
+  a.cos_th = std::cos(p.theta_deg * M_PI / 180.0);
+  a.l_s = p.l_s;
+  const int n = cur, o = 1 - cur;
+  a.C = (const T*)in.C[n];
+  a.Co = (const T*)in.C[o];
+  a.C1 = (T*)in.C[o];
+  a.C1lo = (T*)in.Clo[o];
+  a.U = (const T*)in.U[n];
+  a.V = (const T*)in.V[n];
+  a.W = (const T*)in.W[n];
+  a.Uo = (const T*)in.U[o];
+  a.Vo = (const T*)in.V[o];
+  a.Wo = (const T*)in.W[o];
+  a.Us = (T*)in.U[o];
+  a.Vs = (T*)in.V[o];
+  a.Ws = (T*)in.W[o];
+  a.Hu = (T*)in.Hu;
+  a.Hv = (T*)in.Hv;
+  a.Hw = (T*)in.Hw;
+  a.P = (const T*)in.P[n];
+  a.Po = (const T*)in.P[o];
+  a.Q = (T*)in.Q;
+  a.phi = (T*)in.phi;
+  a.rhs = (T*)in.rhs;
+  a.phat = (T*)in.phat;
+  a.dp = (T*)in.dp;
+  a.gu = (T*)in.gu;
+  a.gv = (T*)in.gv;
+  a.gw = (T*)in.gw;
+  a.fval = (T*)in.fval;
+  if constexpr (sizeof(T) == 8) {
+    a.au = (const T*)in.tab.alpha_u;
+    a.av = (const T*)in.tab.alpha_v;
+    a.aw = (const T*)in.tab.alpha_w;
+  } else {
+    const size_t cells = (size_t)in.nx * in.ny * in.nz;
+    a.au = (const T*)in.alpha_f;
+    a.av = (const T*)in.alpha_f + cells;
+    a.aw = (const T*)in.alpha_f + 2 * cells;
+  }
+  a.tab = in.tab;
+  a.partial = in.partial;
+  a.ticket = in.ticket;
+  a.mass = in.mass;
+  a.status = in.status;
+  return a;
+}
+
+template <typename T>
+int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
+  int launches = 0;
+  auto mark = [&](const char* name) {
+    ++launches;
+    if (rec) rec->mark(name, s);
+  };
+  for (const Instance& in : ctx.inst) {
+    const S3<T> a = make3<T>(in, cur);
+    const size_t cells = (size_t)in.nx * in.ny * in.nz;
+    const unsigned nb = (unsigned)(cells / kT3);
+    const int ng = in.tab.ng, nf = in.tab.nfu + in.tab.nfv + in.tab.nfw;
+    k3_ch_h<T><<<nb, kT3, 0, s>>>(a);
+    mark("ch_h");
+    k3_ch_rhs<T><<<nb, kT3, 0, s>>>(a);
+    mark("ch_rhs");
+    launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
+    if (ng > 0) {
+      k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+      mark("fill_C");
+    }
+    k3_chem_pot<T><<<nb, kT3, 0, s>>>(a);
+    mark("chem_pot");
+    if (ng > 0) {
+      k3_fill_phi<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+      mark("fill_phi");
+    }
+    k3_predict<T><<<nb, kT3, 0, s>>>(a);
+    mark("predict");
+    if (ng > 0) {
+      k3_fill_u<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+      mark("fill_u");
+    }
+    if (nf > 0) {
+      k3_face_values<T><<<(nf + 127) / 128, 128, 0, s>>>(a);
+      mark("face_values");
+      k3_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(a);
+      mark("face_scatter");
+    }
+    k3_poisson_rhs<T><<<nb, kT3, 0, s>>>(a);
+    mark("poisson_rhs");
+    launches += spectral3_solve(in, ctx.precision, 1, cur, s, rec);
+    k3_correct<T><<<nb, kT3, 0, s>>>(a);
+    mark("correct");
+  }
+  return launches;
+}
+
+}  // namespace
+
+int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec) {
+  return c.precision == IB_PF_FP64 ? step3d_t<double>(c, cur, s, rec)
+                                   : step3d_t<float>(c, cur, s, rec);
+}
+
+// the FP32 form reads the face fractions in FP32 (rounded once from the FP64 tables)
+cudaError_t step3d_setup(Ctx& c) {
+  if (c.precision == IB_PF_FP64) return cudaSuccess;
+  for (Instance& in : c.inst) {
+    const size_t cells = (size_t)in.nx * in.ny * in.nz, nxy = (size_t)in.nx * in.ny;
+    cudaError_t e = cudaMalloc((void**)&in.alpha_f, sizeof(float) * (3 * cells + nxy));
+    if (e != cudaSuccess) return e;
+    std::vector<double> hd(cells + nxy);
+    std::vector<float> hf(cells + nxy);
+    const double* src[3] = {in.tab.alpha_u, in.tab.alpha_v, in.tab.alpha_w};
+    for (int q = 0; q < 3; ++q) {
+      const size_t n = q == 2 ? cells + nxy : cells;
+      e = cudaMemcpy(hd.data(), src[q], sizeof(double) * n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return e;
+      for (size_t r = 0; r < n; ++r) hf[r] = (float)hd[r];
+      e = cudaMemcpy(in.alpha_f + q * cells, hf.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ibpf

@@ -17,20 +17,24 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libibpf.so"
 # ---- enums (mirror include/ib_pf.h)
 OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
-WALL_FLAT, WALL_SINUSOID, WALL_NONE = 0, 1, 3
+WALL_FLAT, WALL_SINUSOID, WALL_NONE, WALL_SPHERE, WALL_SPHERES = 0, 1, 3, 4, 5
 (F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P,
- F_C_LO, F_C_OLD_LO) = range(15)
+ F_C_LO, F_C_OLD_LO, F_W, F_W_OLD, F_HW) = range(18)
 FIELD_IDS = {"C": F_C, "C_old": F_C_OLD, "u": F_U, "u_old": F_U_OLD, "v": F_V, "v_old": F_V_OLD,
              "Hu": F_HU, "Hv": F_HV, "P": F_P, "P_old": F_P_OLD, "phi": F_PHI, "Q": F_Q,
-             "rhs_p": F_RHS_P, "C_lo": F_C_LO, "C_old_lo": F_C_OLD_LO}
+             "rhs_p": F_RHS_P, "C_lo": F_C_LO, "C_old_lo": F_C_OLD_LO, "w": F_W,
+             "w_old": F_W_OLD, "Hw": F_HW}
 STATE_FIELDS = ("C", "C_old", "u", "u_old", "v", "v_old", "Hu", "Hv", "P", "P_old")
+STATE_FIELDS_3D = STATE_FIELDS + ("w", "w_old", "Hw")
 (T_ALPHA_C, T_ALPHA_U, T_ALPHA_V, T_CLASS, T_GHOST_CELL, T_NORMAL, T_DN, T_GAMMA, T_AP1, T_W1,
- T_AP2, T_W2, T_FACE_U, T_FACE_V) = range(14)
+ T_AP2, T_W2, T_FACE_U, T_FACE_V, T_ALPHA_W, T_FACE_W) = range(16)
 _TABLE_DTYPE = {T_ALPHA_C: np.float64, T_ALPHA_U: np.float64, T_ALPHA_V: np.float64,
                 T_CLASS: np.int32, T_GHOST_CELL: np.int32, T_NORMAL: np.float64,
                 T_DN: np.float64, T_GAMMA: np.float64, T_AP1: np.int32, T_W1: np.float64,
-                T_AP2: np.int32, T_W2: np.float64, T_FACE_U: np.int32, T_FACE_V: np.int32}
-Q_MASS, Q_N_GHOST, Q_N_FACE_U, Q_N_FACE_V, Q_STATUS, Q_STEPS, Q_N_FALLBACK, Q_LAUNCHES = range(8)
+                T_AP2: np.int32, T_W2: np.float64, T_FACE_U: np.int32, T_FACE_V: np.int32,
+                T_ALPHA_W: np.float64, T_FACE_W: np.int32}
+(Q_MASS, Q_N_GHOST, Q_N_FACE_U, Q_N_FACE_V, Q_STATUS, Q_STEPS, Q_N_FALLBACK, Q_LAUNCHES,
+ Q_N_FACE_W) = range(9)
 
 
 class Grid(ct.Structure):
@@ -38,7 +42,8 @@ class Grid(ct.Structure):
 
 
 class Geometry(ct.Structure):
-    _fields_ = [("kind", ct.c_int), ("p", ct.c_double * 8)]
+    _fields_ = [("kind", ct.c_int), ("p", ct.c_double * 8),
+                ("spheres", ct.POINTER(ct.c_double)), ("n_spheres", ct.c_int)]
 
 
 PARAM_NAMES = ("Re", "Ca", "Cn", "Pe", "S", "rho_ratio", "mu_ratio", "theta_deg", "l_s", "mu_f",
@@ -182,11 +187,26 @@ def make_grid(nx: int, ny: int, lx: float, ly: float) -> Grid:
     return g
 
 
-def make_geometry(kind: int, p) -> Geometry:
+def make_grid3(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float) -> Grid:
+    g = Grid()
+    g.dim = 3
+    g.n[0], g.n[1], g.n[2] = nx, ny, nz
+    g.L[0], g.L[1], g.L[2] = lx, ly, lz
+    return g
+
+
+def make_geometry(kind: int, p, spheres=()) -> Geometry:
+    """spheres: (cx, cy, cz, r) rows for WALL_SPHERES; the array stays referenced by the
+    returned object, and ib_pf_init_geometry copies it."""
     w = Geometry()
     w.kind = kind
     for k, x in enumerate(p):
         w.p[k] = float(x)
+    if len(spheres):
+        arr = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+        w._keep = arr
+        w.spheres = arr.ctypes.data_as(ct.POINTER(ct.c_double))
+        w.n_spheres = arr.shape[0]
     return w
 
 
@@ -205,7 +225,9 @@ class Solver:
         self.ctx = ib_pf_init_geometry(grids, geoms, params, stream)
         self.precision = params[0].precision
         self.dtype = np.float64 if self.precision == FP64 else np.float32
-        self.shapes = [(g.n[1], g.n[0]) for g in grids]
+        self.dim = grids[0].dim
+        self.shapes = [(g.n[2], g.n[1], g.n[0]) if g.dim == 3 else (g.n[1], g.n[0]) for g in grids]
+        self.state_fields = STATE_FIELDS_3D if self.dim == 3 else STATE_FIELDS
 
     def close(self):
         if self.ctx:
@@ -219,6 +241,9 @@ class Solver:
             pass
 
     def field_shape(self, name: str, instance: int = 0):
+        if self.dim == 3:
+            nz, ny, nx = self.shapes[instance]
+            return (nz + 1, ny, nx) if name in ("w", "w_old", "Hw") else (nz, ny, nx)
         ny, nx = self.shapes[instance]
         return (ny + 1, nx) if name in ("v", "v_old", "Hv") else (ny, nx)
 
@@ -258,11 +283,11 @@ class Solver:
         return ib_pf_query(self.ctx, instance, what)
 
     def write_state(self, state: dict, instance: int = 0):
-        for name in STATE_FIELDS:
+        for name in self.state_fields:
             self.write(name, state[name], instance)
 
     def read_state(self, instance: int = 0) -> dict:
-        return {name: self.read(name, instance) for name in STATE_FIELDS}
+        return {name: self.read(name, instance) for name in self.state_fields}
 
     def read_checkpoint(self, instance: int = 0) -> dict:
         """Everything needed for a bit-exact restart (state plus, in FP32 contexts, the
@@ -281,10 +306,12 @@ class Solver:
 
 
 def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:
-    """Build a Solver from objects carrying nx, ny, lx, ly, geom_kind, geom_p and a
-    ``params`` object with the ib_pf_params fields (duck-typed; no import of callers)."""
-    grids = [make_grid(c.nx, c.ny, c.lx, c.ly) for c in cases]
-    geoms = [make_geometry(c.geom_kind, c.geom_p) for c in cases]
+    """Build a Solver from objects carrying nx, ny, lx, ly (and nz, lz, spheres in 3D),
+    geom_kind, geom_p and a ``params`` object with the ib_pf_params fields (duck-typed; no
+    import of callers)."""
+    grids = [make_grid3(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz) if hasattr(c, "nz")
+             else make_grid(c.nx, c.ny, c.lx, c.ly) for c in cases]
+    geoms = [make_geometry(c.geom_kind, c.geom_p, getattr(c, "spheres", ())) for c in cases]
     params = [make_params(precision, **{n: getattr(c.params, n) for n in PARAM_NAMES})
               for c in cases]
     return Solver(grids, geoms, params, stream)

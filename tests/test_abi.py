@@ -62,9 +62,39 @@ def test_invalid_arguments_rejected_on_host(lib, bad, status):
     assert lib.ib_pf_last_error(None)
 
 
-def test_dim3_is_reported_unsupported(lib):
-    g, w, p = _args(lib)
-    g[0].dim = 3
+def _args3(lib, n=(32, 32, 32), L=(1.0, 1.0, 1.0), kind=None, p=(0.5, 0.5, 0.5, 0.25),
+            spheres=(), d1=None):
+    from workloads import cases as W
+    c = W.small_sphere_case(32)
+    g = lib.make_grid3(*n, *L)
+    w = lib.make_geometry(lib.WALL_SPHERE if kind is None else kind, p, spheres)
+    kw = {k: getattr(c.params, k) for k in lib.PARAM_NAMES}
+    if d1 is not None:
+        kw["d1"] = d1
+    return [g], [w], [lib.make_params(lib.FP64, **kw)]
+
+
+@pytest.mark.parametrize("bad", [
+    {"n": (32, 32, 12)},                       # not a power of two
+    {"n": (2048, 32, 32)},                     # beyond the 3D limit
+    {"L": (1.0, 2.0, 1.0)},                    # non-cubic cells
+    {"kind": 1},                               # the sinusoidal wall is 2D only
+    {"p": (0.5, 0.5, 0.5, 0.0)},               # zero sphere radius
+    {"kind": 5},                               # SPHERES without spheres
+    {"kind": 5, "spheres": [(0.5, 0.5, 0.2, -0.1)]},
+    {"d1": 0.8 * 0.5 * 3 ** 0.5 / 32},         # d1 below half the 3D cell diagonal
+])
+def test_invalid_3d_arguments_rejected_on_host(lib, bad):
+    g, w, p = _args3(lib, **bad)
     with pytest.raises(lib.IbPfError) as ei:
         lib.ib_pf_init_geometry(g, w, p)
-    assert ei.value.status == lib.E_UNSUPPORTED
+    assert ei.value.status == lib.E_ARG
+    assert lib.ib_pf_last_error(None)
+
+
+def test_mixed_dimensions_rejected(lib):
+    g2, w2, p2 = _args(lib)
+    g3, w3, p3 = _args3(lib)
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g2 + g3, w2 + w3, p2 + p3)
+    assert ei.value.status == lib.E_ARG
