@@ -57,8 +57,25 @@ KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form t
 }
 
 
-def kernel_step_bytes(name: str, esz: int, cells: int) -> float:
-    w32, w64, g = KERNEL_STEP_WORDS.get(name, (0, 0, 0))
+# the same for the 3D step (field words per cell and step, FP32 form / FP64 form / FP64
+# table words of the FP64 form)
+KERNEL_STEP_WORDS_3D = {
+    "ch_h": (3, 3, 0),           # C, Co -> h
+    "ch_rhs": (10, 10, 0),       # C, Co, u, uo, v, vo, w, wo, h -> R
+    "rows_fwd": (4, 4, 0),       # 2 launches: real rows in, half spectrum out
+    "y_fft": (4, 4, 0),          # 2 launches: spectrum in and out
+    "z_solve": (4, 4, 0),
+    "y_ifft": (4, 4, 0),
+    "rows_inv": (11, 8, 0),      # as in 2D
+    "chem_pot": (2, 2, 0),
+    "predict": (17, 14, 3),      # C, phi, u, v, w, H (3) -> H (3), u**, v**, w**; alpha (3)
+    "poisson_rhs": (8, 8, 0),    # C, P, Po, u**, v**, w** -> rhs, P^
+    "correct": (10, 9, 0),       # C (+ lo), dP, P^, u**, v**, w** -> u, v, w
+}
+
+
+def kernel_step_bytes(name: str, esz: int, cells: int, table=None) -> float:
+    w32, w64, g = (KERNEL_STEP_WORDS if table is None else table).get(name, (0, 0, 0))
     return float((w32 * 4 if esz == 4 else w64 * 8 + g * 8) * cells)
 
 
@@ -76,6 +93,8 @@ def parse_args():
     ap.add_argument("--precision", choices=("both", "fp64", "fp32"), default="both",
                     help="both: FP32 form is the headline, plain FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-3d", action="store_true",
+                    help="skip the 3D sphere (256^3) and porous (512^3) workloads")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 64-instance batched-ensemble measurement")
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
@@ -261,21 +280,23 @@ def kernel_flops64(name: str, nx: int, ny: int) -> float:
     return table.get(name, 0.0)
 
 
-def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form):
+def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, words=None):
     """Roofline of the dominant kernel and per-kernel table from an event-timed pass:
-    ktot[name] = total ms over `steps` steps, kcount[name] = launches."""
+    ktot[name] = total ms over `steps` steps, kcount[name] = launches.  FP64 2D lines are
+    reported against the FP64 pipe, every other line against HBM bandwidth."""
+    words = KERNEL_STEP_WORDS if words is None else words
     dom = max(ktot, key=ktot.get)
     per_launch_ms = ktot[dom] / kcount[dom]
     tot = sum(ktot.values())
     table = {}
     for k, v in sorted(ktot.items(), key=lambda x: -x[1]):
         ent = {"us_per_step": round(1e3 * v / steps, 2), "share": round(v / tot, 4)}
-        if esz == 4 and k in KERNEL_STEP_WORDS:
-            gbs = kernel_step_bytes(k, esz, cells) * steps / (v * 1e-3) / 1e9
+        if (esz == 4 or words is not KERNEL_STEP_WORDS) and k in words:
+            gbs = kernel_step_bytes(k, esz, cells, words) * steps / (v * 1e-3) / 1e9
             ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
         table[k] = ent
-    if esz == 4:
-        alg = kernel_step_bytes(dom, esz, cells) * steps / kcount[dom]
+    if esz == 4 or words is not KERNEL_STEP_WORDS:
+        alg = kernel_step_bytes(dom, esz, cells, words) * steps / kcount[dom]
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -289,6 +310,60 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form):
                 "traffic": read_traffic(dom, form), "alg_flops_per_launch": alg}
     roof.update({"per_launch_us": per_launch_ms * 1e3, "kernels": table})
     return roof
+
+
+def run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps):
+    """The 3D workloads: droplet on a sphere, 256^3 (FP32 and FP64 forms), and droplet over a
+    random sphere packing, 512^3 (FP32 form); both larger than L2, so no flush is needed.
+    Each line: throughput over `steps` steps (at most 20) and the per-kernel roofline of a
+    second, event-instrumented pass."""
+    import numpy as np
+    out = {}
+    jobs = [("sphere_256", W.sphere_case(256), ("fp32", "fp64")),
+            ("porous_512", W.porous_case(512), ("fp32",))]
+    for name, case, forms in jobs:
+        for form in forms:
+            prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+            esz = 8 if form == "fp64" else 4
+            t0 = time.time()
+            s = ibpf.solver_from_cases([case], prec, stream=stream.cuda_stream)
+            s.precompute_weights()
+            setup_s = time.time() - t0
+            C0 = W.droplet_C3d(case, np.float64 if esz == 8 else np.float32)
+            s.write("C", C0)
+            s.write("C_old", C0)
+            del C0
+            for _ in range(max(3, args.warmup)):
+                s.step(1)
+            torch.cuda.synchronize()
+            n = max(1, min(args.steps, 20))
+            if dist:
+                dist.barrier()
+            ms, _, _ = timed_steps(s, n)
+            ms = max_over_ranks([ms], dist, "cuda")[0]
+            line = {"value": aggregate_rate(world, case.cells, n, ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms / n, "steps": n, "cells": case.cells, "dtype": "f%d" % (8 * esz),
+                    "grid": f"{case.nx}x{case.ny}x{case.nz}",
+                    "ghosts": int(s.query(ibpf.Q_N_GHOST)),
+                    "gpu_launches": int(s.query(ibpf.Q_LAUNCHES)) * n,
+                    "setup_s": round(setup_s, 2), "l2": "inputs larger than L2"}
+            if case.geom_kind == W.GEOM_SPHERES:
+                line["spheres"] = len(case.spheres)
+            try:
+                ibpf.ib_pf_set_kernel_timing(s.ctx, True)
+                s.step(1)
+                torch.cuda.synchronize()
+                _, ktot, kcount = timed_steps(s, n, collect_kernels=True)
+                ibpf.ib_pf_set_kernel_timing(s.ctx, False)
+                line["roofline"] = roofline(ktot, kcount, n, case.cells, esz, case, peak, peak_kind,
+                                            form, KERNEL_STEP_WORDS_3D)
+            except Exception as exc:
+                line["roofline"] = {"error": str(exc)[:200]}
+            line["status"] = s.query(ibpf.Q_STATUS)
+            s.close()
+            out[f"{name}_{form}"] = line
+            torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -456,6 +531,9 @@ def run_ours(args):
                "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls",
                "roofline": eroof}
         esolver.close()
+    d3 = None
+    if not args.no_3d:
+        d3 = run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps)
     clocks = sampler.stop()
 
     cpu = None
@@ -484,6 +562,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "forms": {f: {k: v for k, v in r.items() if k != "e2e"} for f, r in results.items()},
             "batched_ensemble": ens,
+            "workloads_3d": d3,
         }
         print(json.dumps(line), flush=True)
     if dist:

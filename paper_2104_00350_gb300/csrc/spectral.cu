@@ -579,18 +579,38 @@ __device__ void yfft_core(typename C2T<T>::type* __restrict__ spec, int nh1, siz
   __syncthreads();
 }
 
-// block b: z-plane b / nbp, columns (b % nbp) * fft_per_block(ny) ..
-template <typename T, bool INV>
-__global__ void __launch_bounds__(kFftSmallThreads) k3_yfft(
+// 3D transforms of the y and z axes run in blocks of kT3Fft threads (8 kT3Fft points per
+// block; 512-thread blocks, with 128-byte column segments, measured slower on GB300)
+constexpr int kT3Fft = 128;
+#define IBPF_CASES_ALL IBPF_CASES_128 IBPF_CASE(11) IBPF_CASE(12)
+
+// block b: z-plane b / nbp, columns (b % nbp) * (8 THREADS / ny) ..
+template <typename T, bool INV, int THREADS>
+__global__ void __launch_bounds__(THREADS) k3_yfft(
     typename C2T<T>::type* __restrict__ spec, int nh1, int ny, int nbp,
     const typename C2T<T>::type* __restrict__ tw) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* x = reinterpret_cast<C2*>(smem_raw);
   const size_t plane = blockIdx.x / nbp;
-  const int kx0 = (int)(blockIdx.x % nbp) * fft_per_block(ny);
-#define IBPF_CASE(L) case L: yfft_core<T, L, kFftSmallThreads, INV>(spec, nh1, plane, tw, kx0, x); break;
-  switch (31 - __clz(ny)) { IBPF_CASES_128 default: break; }
+  const int kx0 = (int)(blockIdx.x % nbp) * (8 * THREADS / ny);
+#define IBPF_CASE(L) case L: if constexpr ((8 * THREADS >> L) >= 1) yfft_core<T, L, THREADS, INV>(spec, nh1, plane, tw, kx0, x); break;
+  switch (31 - __clz(ny)) { IBPF_CASES_ALL default: break; }
+#undef IBPF_CASE
+}
+
+// z cosine transform + symbol + inverse of the 8 THREADS / nz columns k0 .. of a 3D spectrum
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k3_cols(
+    typename C2T<T>::type* __restrict__ spec, int ncols, int nz,
+    const typename C2T<T>::type* __restrict__ tw, const typename C2T<T>::type* __restrict__ wd,
+    SymbolArgs sym) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int k0 = blockIdx.x * (8 * THREADS / nz);
+#define IBPF_CASE(L) case L: if constexpr ((8 * THREADS >> L) >= 1) cols_core<T, L, THREADS>(spec, ncols, tw, wd, sym, k0, x); break;
+  switch (31 - __clz(nz)) { IBPF_CASES_ALL default: break; }
 #undef IBPF_CASE
 }
 
@@ -704,7 +724,11 @@ cudaError_t tables3_t(Instance& in) {
       !put(&in.twz, twz.data(), sizeof(C2) * twz.size()) ||
       !put(&in.wdct, wd.data(), sizeof(C2) * wd.size()))
     return e;
-  return cudaSuccess;
+  const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(k3_yfft<T, false, kT3Fft>, att, 200 * 1024);
+  cudaFuncSetAttribute(k3_yfft<T, true, kT3Fft>, att, 200 * 1024);
+  cudaFuncSetAttribute(k3_cols<T, kT3Fft>, att, 200 * 1024);
+  return cudaGetLastError();
 }
 
 // One 3D solve: x rows, y columns, z cosine transform + symbol + inverse, y inverse, x rows
@@ -715,18 +739,20 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   using C2 = typename C2T<T>::type;
   constexpr int S = kFftSmallThreads;
   const int nx = in.nx, ny = in.ny, nz = in.nz, nh1 = nx / 2 + 1;
+  constexpr int L = kT3Fft;
   const int rows = ny * nz;
-  const int rp = fft_per_block(nx), yp = fft_per_block(ny), cp = fft_per_block(nz);
+  const int rp = fft_per_block(nx), yp = 8 * L / ny, cp = 8 * L / nz;
   C2* spec = (C2*)in.spec;
-  // n <= 1024: at most 26 / 26 / 42 KiB of shared memory, below the default limit
+  // the row kernels take at most 26 KiB of shared memory; the y and z kernels up to 110 KiB
+  // (FP64, 1024 points), allowed by the attribute set with the tables
   const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
-  const size_t ysm = sizeof(C2) * (fft_buf(8 * S) + ny / 2);
-  const size_t csm = sizeof(C2) * (fft_buf(8 * S) + nz / 2 + nz);
+  const size_t ysm = sizeof(C2) * (fft_buf(8 * L) + ny / 2);
+  const size_t csm = sizeof(C2) * (fft_buf(8 * L) + nz / 2 + nz);
   const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
   k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, (const C2*)in.twx);
   if (rec) rec->mark("rows_fwd", s);
   const int nbp = (nh1 + yp - 1) / yp;
-  k3_yfft<T, false><<<nz * nbp, S, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  k3_yfft<T, false, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
   if (rec) rec->mark("y_fft", s);
   SymbolArgs sym;
   sym.mode = mode;
@@ -740,10 +766,10 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   sym.lamyp = in.lamy;
   sym.lamyp_f = in.lamy_f;
   const int ncols = ny * nh1;
-  k_cols<T><<<(ncols + cp - 1) / cp, S, csm, s>>>(spec, ncols, nz, (const C2*)in.twz,
-                                                   (const C2*)in.wdct, sym);
+  k3_cols<T, L><<<(ncols + cp - 1) / cp, L, csm, s>>>(spec, ncols, nz, (const C2*)in.twz,
+                                                        (const C2*)in.wdct, sym);
   if (rec) rec->mark("z_solve", s);
-  k3_yfft<T, true><<<nz * nbp, S, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  k3_yfft<T, true, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
   if (rec) rec->mark("y_ifft", s);
   EpiArgs epi;
   T* out;

@@ -53,23 +53,31 @@ __device__ __forceinline__ void cell_ijk(const S3<T>& a, size_t c, int& i, int& 
   k = (int)(c >> (a.lnx + a.lny));
 }
 
-// linear index of cell (i, j, k), periodic in x and y (k unchanged)
+// linear indices of the 6 face neighbours of cell c: periodic in x and y, mirror planes in
+// z (zp / zm are c itself at the walls)
+struct Nbr {
+  size_t c, xp, xm, yp, ym, zp, zm;
+};
 template <typename T>
-__device__ __forceinline__ size_t lin(const S3<T>& a, int i, int j, int k) {
-  return ((size_t)k * a.ny + (size_t)((j + a.ny) & (a.ny - 1))) * a.nx + (size_t)((i + a.nx) & (a.nx - 1));
+__device__ __forceinline__ Nbr nbr(const S3<T>& a, size_t c, int i, int j, int k) {
+  const size_t nx = (size_t)a.nx, nxy = nx * a.ny;
+  Nbr n;
+  n.c = c;
+  n.xp = i == a.nx - 1 ? c - (nx - 1) : c + 1;
+  n.xm = i == 0 ? c + (nx - 1) : c - 1;
+  n.yp = j == a.ny - 1 ? c - (nxy - nx) : c + nx;
+  n.ym = j == 0 ? c + (nxy - nx) : c - nx;
+  n.zp = k == a.nz - 1 ? c : c + nxy;
+  n.zm = k == 0 ? c : c - nxy;
+  return n;
 }
 
-template <typename T>
-__device__ __forceinline__ int kmir(const S3<T>& a, int k) {   // mirror planes at the walls
-  return k < 0 ? 0 : (k >= a.nz ? a.nz - 1 : k);
-}
-
-// 7-point Laplacian of a cell field with mirror planes in z
+// 7-point Laplacian of a cell field (f of a linear index) with mirror planes in z
 template <typename T, typename F>
-__device__ __forceinline__ T lap7(const S3<T>& a, F f, int i, int j, int k) {
-  const T c0 = f(i, j, k);
-  return ((((f(i + 1, j, k) + f(i - 1, j, k)) + (f(i, j + 1, k) + f(i, j - 1, k))) +
-           (f(i, j, kmir(a, k + 1)) + f(i, j, kmir(a, k - 1)))) - T(6) * c0) * a.inv_h2;
+__device__ __forceinline__ T lap7(const S3<T>& a, F f, const Nbr& n) {
+  const T c0 = f(n.c);
+  return ((((f(n.xp) + f(n.xm)) + (f(n.yp) + f(n.ym))) + (f(n.zp) + f(n.zm))) - T(6) * c0) *
+         a.inv_h2;
 }
 
 // ---------------------------------------------------------------- a1: CH right-hand side
@@ -80,11 +88,8 @@ __global__ void __launch_bounds__(kT3) k3_ch_h(S3<T> a) {
   int i, j, k;
   cell_ijk(a, c, i, j, k);
   const T third = T(1.0 / 3.0);
-  auto B = [&](int ii, int jj, int kk) {
-    const size_t q = lin(a, ii, jj, kk);
-    return a.C[q] + (a.C[q] - a.Co[q]) * third;
-  };
-  const T lapb = lap7(a, B, i, j, k);
+  auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
+  const T lapb = lap7(a, B, nbr(a, c, i, j, k));
   const T d = a.C[c] - a.Co[c];
   const T ct = a.C[c] + d;
   a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(kT3) k3_ch_rhs(S3<T> a) {
   auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
   const size_t nxy = (size_t)a.nx * a.ny;
   const T c0 = ct(c);
-  const size_t xp = lin(a, i + 1, j, k), xm = lin(a, i - 1, j, k);
-  const size_t yp = lin(a, i, j + 1, k), ym = lin(a, i, j - 1, k);
+  const Nbr n = nbr(a, c, i, j, k);
+  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
   const T fx_w = ut(c) * (T(0.5) * (ct(xm) + c0));
   const T fx_e = ut(xp) * (T(0.5) * (c0 + ct(xp)));
   const T fy_s = vt(c) * (T(0.5) * (ct(ym) + c0));
@@ -112,8 +117,8 @@ __global__ void __launch_bounds__(kT3) k3_ch_rhs(S3<T> a) {
   const T fz_b = k > 0 ? wt(c) * (T(0.5) * (ct(c - nxy) + c0)) : T(0);
   const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + ct(c + nxy))) : T(0);
   const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
-  auto hf = [&](int ii, int jj, int kk) { return a.phi[lin(a, ii, jj, kk)]; };
-  a.Q[c] = lap7(a, hf, i, j, k) - a.pe_eta2 * div;
+  auto hf = [&](size_t q) { return a.phi[q]; };
+  a.Q[c] = lap7(a, hf, n) - a.pe_eta2 * div;
 }
 
 // ------------------------------------------------------------ a3 / a4: ghost fills, phi
@@ -156,9 +161,9 @@ __global__ void __launch_bounds__(kT3) k3_chem_pot(S3<T> a) {
   const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
   int i, j, k;
   cell_ijk(a, c, i, j, k);
-  auto cf = [&](int ii, int jj, int kk) { return a.C1[lin(a, ii, jj, kk)]; };
+  auto cf = [&](size_t q) { return a.C1[q]; };
   const T c0 = a.C1[c];
-  a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7(a, cf, i, j, k);
+  a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7(a, cf, nbr(a, c, i, j, k));
 }
 
 // zero normal gradient of phi at the wall: phi_G = phi_M
@@ -173,98 +178,162 @@ __global__ void k3_fill_phi(S3<T> a) {
 // ------------------------------------------------- a5: AB2 predictor + penalisation (3D)
 // H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho_f)
 // u* = u^n + dt (3/2 H^n - 1/2 H^{n-1} + (kappa/(Re Ca Cn)) phi_f dC/dn_f / rho_f), u** = alpha_f u*
-// Thread (i, j, k) updates x-face (i, j, k), y-face (i, j, k) and, for k >= 1, z-face (i, j, k).
+// Block: a 32 x 8 column of cells marching up kPz planes in z.  Planes k-1, k, k+1 of C, u,
+// v, w (and k-1, k of phi) sit in shared memory with a one-cell halo in x and y (periodic
+// wrap; mirror planes of C, no-slip ghost planes -u, -v beyond the z walls), so every value
+// is read from global memory once per block.  Thread (i, j) updates x-face (i, j, k),
+// y-face (i, j, k) and, for k >= 1, z-face (i, j, k) of each plane.
 // Edges: xy-edge (i-1/2, j-1/2, k), xz-edge (i-1/2, j, k-1/2), yz-edge (i, j-1/2, k-1/2).
+constexpr int kPx = 32, kPy = 8, kPz = 16;
+constexpr int kPhx = kPx + 2, kPhy = kPy + 2;
+
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_predict(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
+__global__ void __launch_bounds__(kPx * kPy) k3_predict(S3<T> a) {
+  __shared__ T sC[3][kPhy][kPhx], sU[3][kPhy][kPhx], sV[3][kPhy][kPhx], sW[3][kPhy][kPhx];
+  __shared__ T sF[2][kPhy][kPhx];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
+  const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
+  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int k0 = blockIdx.z * kz;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < a.nx && j < a.ny;
+  const size_t nxy = (size_t)a.nx * a.ny;
+  auto sl3 = [](int kk) { return (kk + 3) % 3; };
+  auto sl2 = [](int kk) { return (kk + 2) & 1; };
+  auto halo_off = [&](int idx) {   // staged slot idx -> offset of its column in a plane
+    const int r = idx / kPhx, q = idx % kPhx;
+    const int gi = (i0 - 1 + q + a.nx) & (a.nx - 1), gj = (j0 - 1 + r + a.ny) & (a.ny - 1);
+    return (size_t)gj * a.nx + gi;
+  };
+  auto load_plane = [&](int kk) {   // C, u, v, w of plane kk (kk in -1 .. nz)
+    const int sl = sl3(kk);
+    const int km = kk < 0 ? 0 : (kk >= a.nz ? a.nz - 1 : kk);
+    const T sg = (kk < 0 || kk >= a.nz) ? T(-1) : T(1);
+    for (int idx = tid; idx < kPhx * kPhy; idx += kPx * kPy) {
+      const size_t o = halo_off(idx), q = (size_t)km * nxy + o;
+      const int r = idx / kPhx, cc = idx % kPhx;
+      sC[sl][r][cc] = a.C1[q];
+      sU[sl][r][cc] = sg * a.U[q];
+      sV[sl][r][cc] = sg * a.V[q];
+      sW[sl][r][cc] = (kk >= 0 && kk <= a.nz) ? a.W[(size_t)kk * nxy + o] : T(0);
+    }
+  };
+  auto load_phi = [&](int kk) {
+    if (kk < 0 || kk >= a.nz) return;
+    for (int idx = tid; idx < kPhx * kPhy; idx += kPx * kPy)
+      sF[sl2(kk)][idx / kPhx][idx % kPhx] = a.phi[(size_t)kk * nxy + halo_off(idx)];
+  };
+  int k = k0;
+  // slots of planes k-1, k, k+1, set once per plane; every access names its plane as k plus
+  // a constant, so the selection below folds at compile time
+  int s_m = 0, s_0 = 0, s_p = 0;
+  auto pl = [&](int kk) { return kk == k ? s_0 : (kk > k ? s_p : s_m); };
+  auto Cc = [&](int ii, int jj, int kk) { return sC[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Fc = [&](int ii, int jj, int kk) { return sF[sl2(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Ug = [&](int ii, int jj, int kk) { return sU[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Vg = [&](int ii, int jj, int kk) { return sV[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Wf = [&](int ii, int jj, int kk) { return sW[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
   const T ih = a.inv_h;
-  auto Cc = [&](int ii, int jj, int kk) { return a.C1[lin(a, ii, jj, kmir(a, kk))]; };
-  auto Fc = [&](int ii, int jj, int kk) { return a.phi[lin(a, ii, jj, kk)]; };
-  // tangential velocities with the no-slip ghost planes beyond the z walls
-  auto Ug = [&](int ii, int jj, int kk) {
-    return kk < 0 ? -a.U[lin(a, ii, jj, 0)] : (kk >= a.nz ? -a.U[lin(a, ii, jj, a.nz - 1)] : a.U[lin(a, ii, jj, kk)]);
-  };
-  auto Vg = [&](int ii, int jj, int kk) {
-    return kk < 0 ? -a.V[lin(a, ii, jj, 0)] : (kk >= a.nz ? -a.V[lin(a, ii, jj, a.nz - 1)] : a.V[lin(a, ii, jj, kk)]);
-  };
-  auto Wf = [&](int ii, int jj, int kk) { return a.W[lin(a, ii, jj, kk)]; };   // kk in 0..nz
-  auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
-  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
-  auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
-  auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
-  auto txy = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj - 1/2, kk)
-    const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-    return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
-  };
-  auto txz = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj, kk - 1/2), kk = 0..nz
-    const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-    return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
-  };
-  auto tyz = [&](int ii, int jj, int kk) {   // edge (ii, jj - 1/2, kk - 1/2)
-    const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
-    return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
-  };
-  auto uv = [&](int ii, int jj, int kk) {
-    return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
-  };
-  auto uw = [&](int ii, int jj, int kk) {
-    return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
-  };
-  auto vw = [&](int ii, int jj, int kk) {
-    return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
-  };
-  const T k_st = a.k_st;
-  // ---- x-face (i - 1/2, j, k)
-  {
-    const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
-    const T rho_f = rho(T(0.5) * (cL + cR));
-    const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
-                   (txz(i, j, k + 1) - txz(i, j, k)) * ih;
-    const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
-    const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
-    const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
-                   (uw(i, j, k + 1) - uw(i, j, k)) * ih;
-    const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
-    const T us = a.U[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hu[c]) + st);
-    a.Hu[c] = H;
-    a.Us[c] = a.au[c] * us;
-  }
-  // ---- y-face (i, j - 1/2, k)
-  {
-    const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
-    const T rho_f = rho(T(0.5) * (cB + cA));
-    const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
-                   (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
-    const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
-    const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
-    const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
-                   (vw(i, j, k + 1) - vw(i, j, k)) * ih;
-    const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
-    const T vs = a.V[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hv[c]) + st);
-    a.Hv[c] = H;
-    a.Vs[c] = a.av[c] * vs;
-  }
-  // ---- z-face (i, j, k - 1/2), 1 <= k <= nz - 1
-  if (k >= 1) {
-    const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
-    const T rho_f = rho(T(0.5) * (cB + cA));
-    const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
-                   (tzz(k) - tzz(k - 1)) * ih;
-    const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
-    const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
-    const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
-                   (wcA * wcA - wcB * wcB) * ih;
-    const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
-    const T ws = a.W[c] + a.dt * ((T(1.5) * H - T(0.5) * a.Hw[c]) + st);
-    a.Hw[c] = H;
-    a.Ws[c] = a.aw[c] * ws;
+  load_plane(k0 - 1);
+  load_plane(k0);
+  load_phi(k0 - 1);
+  load_phi(k0);
+  for (; k < k0 + kz; ++k) {
+    load_plane(k + 1);
+    s_m = sl3(k - 1);
+    s_0 = sl3(k);
+    s_p = sl3(k + 1);
+    __syncthreads();
+    if (active) {
+      const size_t c = (size_t)k * nxy + (size_t)j * a.nx + i;
+      auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
+      auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+      auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
+      auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
+      auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
+      auto txy = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj - 1/2, kk)
+        const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
+      };
+      auto txz = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj, kk - 1/2), kk = 0..nz
+        const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
+      };
+      auto tyz = [&](int ii, int jj, int kk) {   // edge (ii, jj - 1/2, kk - 1/2)
+        const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
+      };
+      auto uv = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
+      };
+      auto uw = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
+      };
+      auto vw = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
+      };
+      const T k_st = a.k_st;
+      T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
+      // ---- x-face (i - 1/2, j, k)
+      {
+        const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cL + cR));
+        const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
+                       (txz(i, j, k + 1) - txz(i, j, k)) * ih;
+        const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
+        const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
+        const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
+                       (uw(i, j, k + 1) - uw(i, j, k)) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
+        const T us = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hu[c]) + st);
+        Hx = H;
+        ux = us;
+      }
+      // ---- y-face (i, j - 1/2, k)
+      {
+        const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
+                       (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
+        const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
+        const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
+        const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
+                       (vw(i, j, k + 1) - vw(i, j, k)) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
+        const T vs = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hv[c]) + st);
+        Hy = H;
+        vy = vs;
+      }
+      // ---- z-face (i, j, k - 1/2), 1 <= k <= nz - 1
+      if (k >= 1) {
+        const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
+                       (tzz(k) - tzz(k - 1)) * ih;
+        const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
+        const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
+        const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
+                       (wcA * wcA - wcB * wcB) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
+        const T ws = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hw[c]) + st);
+        Hz = H;
+        wz = ws;
+      }
+      // stores after every shared-memory read of the plane
+      a.Hu[c] = Hx;
+      a.Us[c] = a.au[c] * ux;
+      a.Hv[c] = Hy;
+      a.Vs[c] = a.av[c] * vy;
+      if (k >= 1) {
+        a.Hw[c] = Hz;
+        a.Ws[c] = a.aw[c] * wz;
+      }
+    }
+    __syncthreads();
+    load_phi(k + 1);
   }
 }
 
@@ -372,8 +441,8 @@ __global__ void __launch_bounds__(kT3) k3_poisson_rhs(S3<T> a) {
   auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
   const T* C = a.C1;
   const T p0 = ph(c);
-  const size_t xp = lin(a, i + 1, j, k), xm = lin(a, i - 1, j, k);
-  const size_t yp = lin(a, i, j + 1, k), ym = lin(a, i, j - 1, k);
+  const Nbr n = nbr(a, c, i, j, k);
+  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
   const T gx_w = (a.rho0 / rho(T(0.5) * (C[xm] + C[c]))) * ((p0 - ph(xm)) * a.inv_h);
   const T gx_e = (a.rho0 / rho(T(0.5) * (C[c] + C[xp]))) * ((ph(xp) - p0) * a.inv_h);
   const T gy_s = (a.rho0 / rho(T(0.5) * (C[ym] + C[c]))) * ((p0 - ph(ym)) * a.inv_h);
@@ -406,8 +475,9 @@ __global__ void __launch_bounds__(kT3) k3_correct(S3<T> a) {
     bad |= !isfinite(vn);
     return vn;
   };
-  const T un = corr(a.Us, lin(a, i - 1, j, k));
-  const T vn = corr(a.Vs, lin(a, i, j - 1, k));
+  const Nbr n = nbr(a, c, i, j, k);
+  const T un = corr(a.Us, n.xm);
+  const T vn = corr(a.Vs, n.ym);
   T wn = T(0);
   if (k >= 1) wn = corr(a.Ws, c - nxy);
   bad |= !isfinite(C[c]);
@@ -524,7 +594,9 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       k3_fill_phi<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_phi");
     }
-    k3_predict<T><<<nb, kT3, 0, s>>>(a);
+    const int kzp = in.nz < kPz ? in.nz : kPz;
+    k3_predict<T><<<dim3((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzp),
+                    dim3(kPx, kPy), 0, s>>>(a);
     mark("predict");
     if (ng > 0) {
       k3_fill_u<T><<<(ng + 127) / 128, 128, 0, s>>>(a);

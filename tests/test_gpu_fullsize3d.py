@@ -1,0 +1,133 @@
+"""The 3D workloads at full size: the sphere (256^3) and the porous packing (512^3).
+
+The oracle cannot build these geometries or take a step on them in seconds, so the checks
+are (a) sampled outputs the oracle computes one by one: volume fractions of random control
+volumes of each family, cell classes, and for random ghosts the normal (corner gradients of
+alpha computed from the oracle's own fractions) and the intersect distance; (b) properties
+that hold at any size: after a step the velocity is discretely divergence-free (the
+projection of Eq. PressurePoisson / Eq. correction makes div u^{n+1} vanish up to the
+solve's rounding) and the state stays finite.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ib_pf3d as O3
+from workloads import cases as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def ibpf():
+    from paper_2104_00350_gb300 import build
+    build.build()
+    from paper_2104_00350_gb300 import ibpf as m
+    return m
+
+
+FULL = {"sphere_256": lambda: W.sphere_case(256), "porous_512": lambda: W.porous_case(512)}
+
+
+def _oracle_alpha_c(case, sph, i, j, k):
+    h = case.h
+    k = min(max(k, 0), case.nz - 1)
+    return O3.volume_fraction_cv(case, (i % case.nx) * h, (j % case.ny) * h, k * h, sph)
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_fullsize_geometry_samples(ibpf, name):
+    case = FULL[name]()
+    s = ibpf.solver_from_cases([case], ibpf.FP64)
+    s.precompute_weights()
+    nz, ny, nx, h = case.nz, case.ny, case.nx, case.h
+    sph = O3._spheres(case)
+    rng = np.random.default_rng(11)
+    tables = {"c": (ibpf.T_ALPHA_C, (0.0, 0.0, 0.0), nz), "u": (ibpf.T_ALPHA_U, (-0.5, 0.0, 0.0), nz),
+              "v": (ibpf.T_ALPHA_V, (0.0, -0.5, 0.0), nz), "w": (ibpf.T_ALPHA_W, (0.0, 0.0, -0.5), nz + 1)}
+    cls = s.table(ibpf.T_CLASS).reshape(nz, ny, nx)
+    gcell = s.table(ibpf.T_GHOST_CELL)
+    ng = len(gcell)
+    assert ng > 0
+    for key, (tid, sh, planes) in tables.items():
+        a = s.table(tid).reshape(planes, ny, nx)
+        # half of the samples near the solid surface (where the counting is non-trivial)
+        gk, r = np.divmod(gcell[rng.integers(0, ng, 60)], nx * ny)
+        gj, gi = np.divmod(r, nx)
+        ks = np.concatenate([rng.integers(0, planes, 60), np.minimum(gk + rng.integers(-1, 2, 60), planes - 1)])
+        js = np.concatenate([rng.integers(0, ny, 60), (gj + rng.integers(-1, 2, 60)) % ny])
+        iz = np.concatenate([rng.integers(0, nx, 60), (gi + rng.integers(-1, 2, 60)) % nx])
+        for k, j, i in zip(ks, js, iz):
+            ref = O3.volume_fraction_cv(case, (i + sh[0]) * h, (j + sh[1]) * h, (k + sh[2]) * h, sph)
+            assert a[k, j, i] == ref, (key, k, j, i, a[k, j, i], ref)
+    # classes of random cells from the solid predicate at the centre and its 6 neighbours
+    for _ in range(200):
+        k, j, i = int(rng.integers(0, nz)), int(rng.integers(0, ny)), int(rng.integers(0, nx))
+        cen = lambda ii, jj, kk: O3.solid3(case, (ii + 0.5) * h, (jj + 0.5) * h, (kk + 0.5) * h, sph)
+        sol = bool(cen(i, j, k))
+        if not sol:
+            want = 0
+        else:
+            nb = [(i + 1, j, k), (i - 1, j, k), (i, j + 1, k), (i, j - 1, k), (i, j, k + 1), (i, j, k - 1)]
+            fl = any((0 <= kk < nz) and not bool(cen(ii % nx, jj % ny, kk)) for ii, jj, kk in nb)
+            want = 1 if fl else 2
+        assert cls[k, j, i] == want, (k, j, i)
+    # normals and intersect distances of random ghosts
+    nrm = s.table(ibpf.T_NORMAL).reshape(ng, 3)
+    dn = s.table(ibpf.T_DN)
+    for g in rng.integers(0, ng, 40):
+        k, r = divmod(int(gcell[g]), nx * ny)
+        j, i = divmod(r, nx)
+        acc = np.zeros(3)
+        for dk in (-1, 0):
+            for dj in (-1, 0):
+                for di in (-1, 0):
+                    ci, cj, ck = i + di, j + dj, k + dk
+                    v = [[[_oracle_alpha_c(case, sph, ci + ei, cj + ej, ck + ek) for ei in (0, 1)]
+                          for ej in (0, 1)] for ek in (0, 1)]
+                    mx = ((v[0][0][1] + v[0][1][1]) + (v[1][0][1] + v[1][1][1])
+                          - ((v[0][0][0] + v[0][1][0]) + (v[1][0][0] + v[1][1][0]))) / (4.0 * h)
+                    my = ((v[0][1][0] + v[0][1][1]) + (v[1][1][0] + v[1][1][1])
+                          - ((v[0][0][0] + v[0][0][1]) + (v[1][0][0] + v[1][0][1]))) / (4.0 * h)
+                    mz = ((v[1][0][0] + v[1][0][1]) + (v[1][1][0] + v[1][1][1])
+                          - ((v[0][0][0] + v[0][0][1]) + (v[0][1][0] + v[0][1][1]))) / (4.0 * h)
+                    acc = acc + np.array([mx, my, mz])
+        m = acc / 8.0
+        mag2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2]
+        if math.sqrt(mag2) * h < 1e-12:
+            continue      # fallback normal: checked by the small-grid parity tests
+        n_ref = m / math.sqrt(mag2 + O3.EPS0)
+        assert np.abs(nrm[g] - n_ref).max() <= 1e-13, (g, nrm[g], n_ref)
+        G = np.array([(i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h])
+        # the intersect point lies on the solid surface: the point dn along n is outside and
+        # the point h/2^40 before it inside
+        P_out = G + dn[g] * nrm[g]
+        P_in = G + (dn[g] - h * 2.0 ** -40) * nrm[g]
+        assert not bool(O3.solid3(case, *P_out, sph)) and bool(O3.solid3(case, *P_in, sph))
+        assert 0.0 < dn[g] <= 10.0 * h
+    s.close()
+
+
+@pytest.mark.parametrize("name,prec,tol", [("sphere_256", "fp64", 1e-9), ("sphere_256", "fp32", 2e-4),
+                                           ("porous_512", "fp32", 2e-4)])
+def test_fullsize_step_is_divergence_free(ibpf, name, prec, tol):
+    case = FULL[name]()
+    p = ibpf.FP64 if prec == "fp64" else ibpf.FP32
+    dt = np.float64 if prec == "fp64" else np.float32
+    s = ibpf.solver_from_cases([case], p)
+    s.precompute_weights()
+    C0 = W.droplet_C3d(case, dt)
+    s.write("C", C0)
+    s.write("C_old", C0)
+    del C0
+    s.step(5)
+    assert s.query(ibpf.Q_STATUS) == 0.0
+    u = s.read("u").astype(np.float64)
+    v = s.read("v").astype(np.float64)
+    w = s.read("w").astype(np.float64)
+    s.close()
+    scale = max(np.abs(u).max(), np.abs(v).max(), np.abs(w).max())
+    assert scale > 0.0 and np.isfinite(scale)
+    div = O3.divergence3(u, v, w, case.h)
+    assert np.abs(div).max() * case.h <= tol * scale, (np.abs(div).max() * case.h / scale)

@@ -385,3 +385,20 @@ def random_state3d(case: Case3D, seed: int = 7, amp_u: float = 0.05) -> dict:
     s["P"] -= s["P"].mean()
     s["P_old"] -= s["P_old"].mean()
     return s
+
+
+def droplet_C3d(case: Case3D, dtype=np.float32) -> np.ndarray:
+    """The tanh droplet field of initial_state3d alone, built one z-plane at a time in the
+    requested dtype (for grids whose full FP64 state would not fit comfortably on the host);
+    the other initial fields are zero."""
+    h = case.h
+    xc = (np.arange(case.nx) + 0.5) * h
+    yc = (np.arange(case.ny) + 0.5) * h
+    Y, X = np.meshgrid(yc, xc, indexing="ij")
+    r2xy = (X - case.drop_c[0]) ** 2 + (Y - case.drop_c[1]) ** 2
+    out = np.empty((case.nz, case.ny, case.nx), dtype=dtype)
+    s = math.sqrt(2.0) * case.params.Cn
+    for k in range(case.nz):
+        z = (k + 0.5) * h
+        out[k] = np.tanh((case.drop_r - np.sqrt(r2xy + (z - case.drop_c[2]) ** 2)) / s)
+    return out
