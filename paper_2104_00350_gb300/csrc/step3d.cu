@@ -44,7 +44,6 @@ struct S3 {
   int* status;
 };
 
-constexpr int kT3 = 256;   // threads of the cell kernels (one cell each)
 
 template <typename T>
 __device__ __forceinline__ void cell_ijk(const S3<T>& a, size_t c, int& i, int& j, int& k) {
@@ -70,55 +69,6 @@ __device__ __forceinline__ Nbr nbr(const S3<T>& a, size_t c, int i, int j, int k
   n.zp = k == a.nz - 1 ? c : c + nxy;
   n.zm = k == 0 ? c : c - nxy;
   return n;
-}
-
-// 7-point Laplacian of a cell field (f of a linear index) with mirror planes in z
-template <typename T, typename F>
-__device__ __forceinline__ T lap7(const S3<T>& a, F f, const Nbr& n) {
-  const T c0 = f(n.c);
-  return ((((f(n.xp) + f(n.xm)) + (f(n.yp) + f(n.ym))) + (f(n.zp) + f(n.zm))) - T(6) * c0) *
-         a.inv_h2;
-}
-
-// ---------------------------------------------------------------- a1: CH right-hand side
-// h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_ch_h(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  const T third = T(1.0 / 3.0);
-  auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
-  const T lapb = lap7(a, B, nbr(a, c, i, j, k));
-  const T d = a.C[c] - a.Co[c];
-  const T ct = a.C[c] + d;
-  a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
-}
-
-// R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
-// through the z walls
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_ch_rhs(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
-  auto ut = [&](size_t q) { return T(2) * a.U[q] - a.Uo[q]; };
-  auto vt = [&](size_t q) { return T(2) * a.V[q] - a.Vo[q]; };
-  auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
-  const size_t nxy = (size_t)a.nx * a.ny;
-  const T c0 = ct(c);
-  const Nbr n = nbr(a, c, i, j, k);
-  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
-  const T fx_w = ut(c) * (T(0.5) * (ct(xm) + c0));
-  const T fx_e = ut(xp) * (T(0.5) * (c0 + ct(xp)));
-  const T fy_s = vt(c) * (T(0.5) * (ct(ym) + c0));
-  const T fy_n = vt(yp) * (T(0.5) * (c0 + ct(yp)));
-  const T fz_b = k > 0 ? wt(c) * (T(0.5) * (ct(c - nxy) + c0)) : T(0);
-  const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + ct(c + nxy))) : T(0);
-  const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
-  auto hf = [&](size_t q) { return a.phi[q]; };
-  a.Q[c] = lap7(a, hf, n) - a.pe_eta2 * div;
 }
 
 // ------------------------------------------------------------ a3 / a4: ghost fills, phi
@@ -155,9 +105,74 @@ __global__ void k3_fill_C(S3<T> a) {
   if (a.C1lo) a.C1lo[t.gcell[g]] = T(0);
 }
 
+// zero normal gradient of phi at the wall: phi_G = phi_M
+template <typename T>
+__global__ void k3_fill_phi(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
+}
+
+constexpr int kT3 = 256;   // threads of the one-thread-per-cell kernels
+
+// 7-point Laplacian of a cell field (f of a linear index) with mirror planes in z
+template <typename T, typename F>
+__device__ __forceinline__ T lap7(const S3<T>& a, F f, const Nbr& n) {
+  const T c0 = f(n.c);
+  return ((((f(n.xp) + f(n.xm)) + (f(n.yp) + f(n.ym))) + (f(n.zp) + f(n.zm))) - T(6) * c0) *
+         a.inv_h2;
+}
+
+// ----------------------------------------------- one-thread-per-cell kernels (FP32 form)
+// The FP32 form is memory-latency bound; these kernels, one thread per cell with its
+// neighbours read through L1, measured faster for it than the z-marching ones below
+// (which the FP64 form, bound by the FP64 pipe, uses).  Same arithmetic in both.
+
+// ---------------------------------------------------------------- a1: CH right-hand side
+// h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_ch_h_c(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const T third = T(1.0 / 3.0);
+  auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
+  const T lapb = lap7(a, B, nbr(a, c, i, j, k));
+  const T d = a.C[c] - a.Co[c];
+  const T ct = a.C[c] + d;
+  a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+}
+
+// R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
+// through the z walls
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_ch_rhs_c(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
+  auto ut = [&](size_t q) { return T(2) * a.U[q] - a.Uo[q]; };
+  auto vt = [&](size_t q) { return T(2) * a.V[q] - a.Vo[q]; };
+  auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
+  const size_t nxy = (size_t)a.nx * a.ny;
+  const T c0 = ct(c);
+  const Nbr n = nbr(a, c, i, j, k);
+  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
+  const T fx_w = ut(c) * (T(0.5) * (ct(xm) + c0));
+  const T fx_e = ut(xp) * (T(0.5) * (c0 + ct(xp)));
+  const T fy_s = vt(c) * (T(0.5) * (ct(ym) + c0));
+  const T fy_n = vt(yp) * (T(0.5) * (c0 + ct(yp)));
+  const T fz_b = k > 0 ? wt(c) * (T(0.5) * (ct(c - nxy) + c0)) : T(0);
+  const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + ct(c + nxy))) : T(0);
+  const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+  auto hf = [&](size_t q) { return a.phi[q]; };
+  a.Q[c] = lap7(a, hf, n) - a.pe_eta2 * div;
+}
+
 // phi = psi'(C) - Cn^2 lap C on every cell
 template <typename T>
-__global__ void __launch_bounds__(kT3) k3_chem_pot(S3<T> a) {
+__global__ void __launch_bounds__(kT3) k3_chem_pot_c(S3<T> a) {
   const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
   int i, j, k;
   cell_ijk(a, c, i, j, k);
@@ -166,13 +181,65 @@ __global__ void __launch_bounds__(kT3) k3_chem_pot(S3<T> a) {
   a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7(a, cf, nbr(a, c, i, j, k));
 }
 
-// zero normal gradient of phi at the wall: phi_G = phi_M
+// ------------------------------------------------------------------ a7: Poisson RHS (3D)
+// lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
 template <typename T>
-__global__ void k3_fill_phi(S3<T> a) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  const Tables& t = a.tab;
-  if (g >= t.ng) return;
-  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
+__global__ void __launch_bounds__(kT3) k3_poisson_rhs_c(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  auto ph = [&](size_t q) { return T(2) * a.P[q] - a.Po[q]; };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const T* C = a.C1;
+  const T p0 = ph(c);
+  const Nbr n = nbr(a, c, i, j, k);
+  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
+  const T gx_w = (a.rho0 / rho(T(0.5) * (C[xm] + C[c]))) * ((p0 - ph(xm)) * a.inv_h);
+  const T gx_e = (a.rho0 / rho(T(0.5) * (C[c] + C[xp]))) * ((ph(xp) - p0) * a.inv_h);
+  const T gy_s = (a.rho0 / rho(T(0.5) * (C[ym] + C[c]))) * ((p0 - ph(ym)) * a.inv_h);
+  const T gy_n = (a.rho0 / rho(T(0.5) * (C[c] + C[yp]))) * ((ph(yp) - p0) * a.inv_h);
+  T gz_b = T(0), gz_t = T(0);
+  if (k > 0) gz_b = (a.rho0 / rho(T(0.5) * (C[c - nxy] + C[c]))) * ((p0 - ph(c - nxy)) * a.inv_h);
+  if (k < a.nz - 1) gz_t = (a.rho0 / rho(T(0.5) * (C[c] + C[c + nxy]))) * ((ph(c + nxy) - p0) * a.inv_h);
+  const T div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
+  const T div_u = ((a.Us[xp] - a.Us[c]) * a.inv_h + (a.Vs[yp] - a.Vs[c]) * a.inv_h) +
+                  (a.Ws[c + nxy] - a.Ws[c]) * a.inv_h;
+  a.rhs[c] = (a.rho0 * a.inv_dt) * div_u - div_g;
+  a.phat[c] = p0;
+}
+
+// ------------------------------------------------- a8: correction + status and mass (3D)
+// u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces 1..nz-1)
+template <typename T>
+__global__ void __launch_bounds__(kT3) k3_correct_c(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const T* C = a.C1;
+  int bad = 0;
+  auto corr = [&](const T* vel, size_t nb) {
+    const T rho_f = rho(T(0.5) * (C[nb] + C[c]));
+    const T vn = vel[c] - a.dt * (((a.phat[c] - a.phat[nb]) * a.inv_h) / rho_f +
+                                  a.inv_rho0 * ((a.dp[c] - a.dp[nb]) * a.inv_h));
+    bad |= !isfinite(vn);
+    return vn;
+  };
+  const Nbr n = nbr(a, c, i, j, k);
+  const T un = corr(a.Us, n.xm);
+  const T vn = corr(a.Vs, n.ym);
+  T wn = T(0);
+  if (k >= 1) wn = corr(a.Ws, c - nxy);
+  bad |= !isfinite(C[c]);
+  a.Us[c] = un;
+  a.Vs[c] = vn;
+  if (k >= 1) a.Ws[c] = wn;
+  if (bad) atomicOr(a.status, 1);
+  const T lo = a.C1lo ? a.C1lo[c] : T(0);
+  const size_t ntiles = (nxy * a.nz) / kT3;
+  tile_mass<T, kT3>(C[c], lo, (int)blockIdx.x, (int)ntiles, a.partial, a.ticket, a.mass);
 }
 
 // ------------------------------------------------- a5: AB2 predictor + penalisation (3D)
@@ -337,6 +404,245 @@ __global__ void __launch_bounds__(kPx * kPy) k3_predict(S3<T> a) {
   }
 }
 
+// ------------------------------------------------------------- z-marching cell kernels
+constexpr int kCz = 16;   // planes per block of the cell kernels
+// Same blocks as the predictor: a 32 x 8 column of cells marching up kPz planes.  Fields
+// differentiated in x, y or z are staged plane by plane in a rotating window with a one-cell
+// halo in x and y (periodic wrap) and mirror planes beyond the z walls; each staged value is
+// read from global memory once per block.
+template <typename T, int NP>
+struct Win {
+  T p[NP][kPhy][kPhx];
+};
+
+struct Tile {
+  int tx, ty, tid, i0, j0, i, j, k0, kz;
+  bool active;
+};
+
+template <typename T>
+__device__ __forceinline__ Tile tile3(const S3<T>& a) {
+  Tile t;
+  t.tx = threadIdx.x;
+  t.ty = threadIdx.y;
+  t.tid = t.ty * kPx + t.tx;
+  t.i0 = blockIdx.x * kPx;
+  t.j0 = blockIdx.y * kPy;
+  t.kz = a.nz < kCz ? a.nz : kCz;
+  t.k0 = blockIdx.z * t.kz;
+  t.i = t.i0 + t.tx;
+  t.j = t.j0 + t.ty;
+  t.active = t.i < a.nx && t.j < a.ny;
+  return t;
+}
+
+// stage plane kk (mirrored into 0 .. nz-1) of get(linear index) into window slot sl
+template <typename T, int NP, typename G>
+__device__ __forceinline__ void win_load(Win<T, NP>& w, int sl, const S3<T>& a, const Tile& t,
+                                         int kk, G get) {
+  const int km = kk < 0 ? 0 : (kk >= a.nz ? a.nz - 1 : kk);
+  const size_t base = (size_t)km * a.nx * a.ny;
+  for (int idx = t.tid; idx < kPhx * kPhy; idx += kPx * kPy) {
+    const int r = idx / kPhx, q = idx % kPhx;
+    const int gi = (t.i0 - 1 + q + a.nx) & (a.nx - 1), gj = (t.j0 - 1 + r + a.ny) & (a.ny - 1);
+    w.p[sl][r][q] = get(base + (size_t)gj * a.nx + gi);
+  }
+}
+
+__device__ __forceinline__ int slot3(int kk) { return (kk + 3) % 3; }
+__device__ __forceinline__ int slot2(int kk) { return (kk + 2) & 1; }
+
+// 7-point Laplacian from a window: (((x+ + x-) + (y+ + y-)) + (z+ + z-)) - 6 c, over h^2
+template <typename T>
+__device__ __forceinline__ T lap7w(const Win<T, 3>& w, int sm, int s0, int sp, const Tile& t,
+                                   T inv_h2) {
+  const int x = t.tx + 1, y = t.ty + 1;
+  const T c0 = w.p[s0][y][x];
+  return ((((w.p[s0][y][x + 1] + w.p[s0][y][x - 1]) + (w.p[s0][y + 1][x] + w.p[s0][y - 1][x])) +
+           (w.p[sp][y][x] + w.p[sm][y][x])) - T(6) * c0) * inv_h2;
+}
+
+template <typename T>
+__device__ __forceinline__ size_t cell_at(const S3<T>& a, const Tile& t, int k) {
+  return ((size_t)k * a.ny + t.j) * a.nx + t.i;
+}
+
+// ---------------------------------------------------------------- a1: CH right-hand side
+// h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy) k3_ch_h_z(S3<T> a) {
+  __shared__ Win<T, 3> wb;
+  const Tile t = tile3(a);
+  const T third = T(1.0 / 3.0);
+  auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
+  win_load(wb, slot3(t.k0 - 1), a, t, t.k0 - 1, B);
+  win_load(wb, slot3(t.k0), a, t, t.k0, B);
+  for (int k = t.k0; k < t.k0 + t.kz; ++k) {
+    win_load(wb, slot3(k + 1), a, t, k + 1, B);
+    __syncthreads();
+    if (t.active) {
+      const size_t c = cell_at(a, t, k);
+      const T lapb = lap7w(wb, slot3(k - 1), slot3(k), slot3(k + 1), t, a.inv_h2);
+      const T d = a.C[c] - a.Co[c];
+      const T ct = a.C[c] + d;
+      a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+    }
+    __syncthreads();
+  }
+}
+
+// R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
+// through the z walls
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy) k3_ch_rhs_z(S3<T> a) {
+  __shared__ Win<T, 3> wc, wh;
+  const Tile t = tile3(a);
+  auto CT = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
+  auto HH = [&](size_t q) { return a.phi[q]; };
+  auto ut = [&](size_t q) { return T(2) * a.U[q] - a.Uo[q]; };
+  auto vt = [&](size_t q) { return T(2) * a.V[q] - a.Vo[q]; };
+  auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
+  const size_t nxy = (size_t)a.nx * a.ny;
+  for (int kk = t.k0 - 1; kk <= t.k0; ++kk) {
+    win_load(wc, slot3(kk), a, t, kk, CT);
+    win_load(wh, slot3(kk), a, t, kk, HH);
+  }
+  const int x = t.tx + 1, y = t.ty + 1;
+  for (int k = t.k0; k < t.k0 + t.kz; ++k) {
+    win_load(wc, slot3(k + 1), a, t, k + 1, CT);
+    win_load(wh, slot3(k + 1), a, t, k + 1, HH);
+    __syncthreads();
+    if (t.active) {
+      const int sm = slot3(k - 1), s0 = slot3(k), sp = slot3(k + 1);
+      const size_t c = cell_at(a, t, k);
+      const Nbr n = nbr(a, c, t.i, t.j, k);
+      const T c0 = wc.p[s0][y][x];
+      const T fx_w = ut(c) * (T(0.5) * (wc.p[s0][y][x - 1] + c0));
+      const T fx_e = ut(n.xp) * (T(0.5) * (c0 + wc.p[s0][y][x + 1]));
+      const T fy_s = vt(c) * (T(0.5) * (wc.p[s0][y - 1][x] + c0));
+      const T fy_n = vt(n.yp) * (T(0.5) * (c0 + wc.p[s0][y + 1][x]));
+      const T fz_b = k > 0 ? wt(c) * (T(0.5) * (wc.p[sm][y][x] + c0)) : T(0);
+      const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + wc.p[sp][y][x])) : T(0);
+      const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+      a.Q[c] = lap7w(wh, sm, s0, sp, t, a.inv_h2) - a.pe_eta2 * div;
+    }
+    __syncthreads();
+  }
+}
+
+// phi = psi'(C) - Cn^2 lap C on every cell
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy) k3_chem_pot_z(S3<T> a) {
+  __shared__ Win<T, 3> wc;
+  const Tile t = tile3(a);
+  auto CC = [&](size_t q) { return a.C1[q]; };
+  win_load(wc, slot3(t.k0 - 1), a, t, t.k0 - 1, CC);
+  win_load(wc, slot3(t.k0), a, t, t.k0, CC);
+  for (int k = t.k0; k < t.k0 + t.kz; ++k) {
+    win_load(wc, slot3(k + 1), a, t, k + 1, CC);
+    __syncthreads();
+    if (t.active) {
+      const size_t c = cell_at(a, t, k);
+      const T c0 = wc.p[slot3(k)][t.ty + 1][t.tx + 1];
+      a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7w(wc, slot3(k - 1), slot3(k), slot3(k + 1), t, a.inv_h2);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ a7: Poisson RHS (3D)
+// lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy) k3_poisson_rhs_z(S3<T> a) {
+  __shared__ Win<T, 3> wc, wp;
+  const Tile t = tile3(a);
+  auto CC = [&](size_t q) { return a.C1[q]; };
+  auto PH = [&](size_t q) { return T(2) * a.P[q] - a.Po[q]; };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const size_t nxy = (size_t)a.nx * a.ny;
+  for (int kk = t.k0 - 1; kk <= t.k0; ++kk) {
+    win_load(wc, slot3(kk), a, t, kk, CC);
+    win_load(wp, slot3(kk), a, t, kk, PH);
+  }
+  const int x = t.tx + 1, y = t.ty + 1;
+  for (int k = t.k0; k < t.k0 + t.kz; ++k) {
+    win_load(wc, slot3(k + 1), a, t, k + 1, CC);
+    win_load(wp, slot3(k + 1), a, t, k + 1, PH);
+    __syncthreads();
+    if (t.active) {
+      const int sm = slot3(k - 1), s0 = slot3(k), sp = slot3(k + 1);
+      const size_t c = cell_at(a, t, k);
+      const Nbr n = nbr(a, c, t.i, t.j, k);
+      const T cc0 = wc.p[s0][y][x], p0 = wp.p[s0][y][x];
+      const T gx_w = (a.rho0 / rho(T(0.5) * (wc.p[s0][y][x - 1] + cc0))) * ((p0 - wp.p[s0][y][x - 1]) * a.inv_h);
+      const T gx_e = (a.rho0 / rho(T(0.5) * (cc0 + wc.p[s0][y][x + 1]))) * ((wp.p[s0][y][x + 1] - p0) * a.inv_h);
+      const T gy_s = (a.rho0 / rho(T(0.5) * (wc.p[s0][y - 1][x] + cc0))) * ((p0 - wp.p[s0][y - 1][x]) * a.inv_h);
+      const T gy_n = (a.rho0 / rho(T(0.5) * (cc0 + wc.p[s0][y + 1][x]))) * ((wp.p[s0][y + 1][x] - p0) * a.inv_h);
+      T gz_b = T(0), gz_t = T(0);
+      if (k > 0)
+        gz_b = (a.rho0 / rho(T(0.5) * (wc.p[sm][y][x] + cc0))) * ((p0 - wp.p[sm][y][x]) * a.inv_h);
+      if (k < a.nz - 1)
+        gz_t = (a.rho0 / rho(T(0.5) * (cc0 + wc.p[sp][y][x]))) * ((wp.p[sp][y][x] - p0) * a.inv_h);
+      const T div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
+      const T div_u = ((a.Us[n.xp] - a.Us[c]) * a.inv_h + (a.Vs[n.yp] - a.Vs[c]) * a.inv_h) +
+                      (a.Ws[c + nxy] - a.Ws[c]) * a.inv_h;
+      a.rhs[c] = (a.rho0 * a.inv_dt) * div_u - div_g;
+      a.phat[c] = p0;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------- a8: correction + status and mass (3D)
+// u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces 1..nz-1);
+// planes k-1 and k of C, P^ and dP in two-plane windows
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy) k3_correct_z(S3<T> a) {
+  __shared__ Win<T, 2> wc, wq, wd;
+  const Tile t = tile3(a);
+  auto CC = [&](size_t q) { return a.C1[q]; };
+  auto PQ = [&](size_t q) { return a.phat[q]; };
+  auto DP = [&](size_t q) { return a.dp[q]; };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  win_load(wc, slot2(t.k0 - 1), a, t, t.k0 - 1, CC);
+  win_load(wq, slot2(t.k0 - 1), a, t, t.k0 - 1, PQ);
+  win_load(wd, slot2(t.k0 - 1), a, t, t.k0 - 1, DP);
+  const int x = t.tx + 1, y = t.ty + 1;
+  int bad = 0;
+  T s_hi = T(0), s_lo = T(0);
+  for (int k = t.k0; k < t.k0 + t.kz; ++k) {
+    win_load(wc, slot2(k), a, t, k, CC);
+    win_load(wq, slot2(k), a, t, k, PQ);
+    win_load(wd, slot2(k), a, t, k, DP);
+    __syncthreads();
+    if (t.active) {
+      const int sm = slot2(k - 1), s0 = slot2(k);
+      const size_t c = cell_at(a, t, k);
+      const T cc0 = wc.p[s0][y][x], q0 = wq.p[s0][y][x], d0 = wd.p[s0][y][x];
+      auto corr = [&](T vel, T cnb, T qnb, T dnb) {
+        const T rho_f = rho(T(0.5) * (cnb + cc0));
+        const T vn = vel - a.dt * (((q0 - qnb) * a.inv_h) / rho_f + a.inv_rho0 * ((d0 - dnb) * a.inv_h));
+        bad |= !isfinite(vn);
+        return vn;
+      };
+      const T un = corr(a.Us[c], wc.p[s0][y][x - 1], wq.p[s0][y][x - 1], wd.p[s0][y][x - 1]);
+      const T vn = corr(a.Vs[c], wc.p[s0][y - 1][x], wq.p[s0][y - 1][x], wd.p[s0][y - 1][x]);
+      T wn = T(0);
+      if (k >= 1) wn = corr(a.Ws[c], wc.p[sm][y][x], wq.p[sm][y][x], wd.p[sm][y][x]);
+      bad |= !isfinite(cc0);
+      a.Us[c] = un;
+      a.Vs[c] = vn;
+      if (k >= 1) a.Ws[c] = wn;
+      pair_add(s_hi, s_lo, cc0, a.C1lo ? a.C1lo[c] : T(0));
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(a.status, 1);
+  const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  const int nblk = gridDim.x * gridDim.y * gridDim.z;
+  tile_mass<T, kPx * kPy>(s_hi, s_lo, blk, nblk, a.partial, a.ticket, a.mass);
+}
+
 // ------------------------------------------------------------- a6: velocity ghost fill (3D)
 // centred u** at the averaging cells, mirror values by Eq. extrapolation, V_nG = -V_nM/gamma
 // (Eq. NoPenetration), V_tG = V_tM (l_s - dn)/(l_s + gamma dn) (Eq. UpdateVtan, static
@@ -429,67 +735,6 @@ __global__ void k3_face_scatter(S3<T> a) {
   else if (f < t.nfu + t.nfv + t.nfw) a.Ws[t.fw[f - t.nfu - t.nfv]] = a.fval[f];
 }
 
-// ------------------------------------------------------------------ a7: Poisson RHS (3D)
-// lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_poisson_rhs(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  const size_t nxy = (size_t)a.nx * a.ny;
-  auto ph = [&](size_t q) { return T(2) * a.P[q] - a.Po[q]; };
-  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  const T* C = a.C1;
-  const T p0 = ph(c);
-  const Nbr n = nbr(a, c, i, j, k);
-  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
-  const T gx_w = (a.rho0 / rho(T(0.5) * (C[xm] + C[c]))) * ((p0 - ph(xm)) * a.inv_h);
-  const T gx_e = (a.rho0 / rho(T(0.5) * (C[c] + C[xp]))) * ((ph(xp) - p0) * a.inv_h);
-  const T gy_s = (a.rho0 / rho(T(0.5) * (C[ym] + C[c]))) * ((p0 - ph(ym)) * a.inv_h);
-  const T gy_n = (a.rho0 / rho(T(0.5) * (C[c] + C[yp]))) * ((ph(yp) - p0) * a.inv_h);
-  T gz_b = T(0), gz_t = T(0);
-  if (k > 0) gz_b = (a.rho0 / rho(T(0.5) * (C[c - nxy] + C[c]))) * ((p0 - ph(c - nxy)) * a.inv_h);
-  if (k < a.nz - 1) gz_t = (a.rho0 / rho(T(0.5) * (C[c] + C[c + nxy]))) * ((ph(c + nxy) - p0) * a.inv_h);
-  const T div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
-  const T div_u = ((a.Us[xp] - a.Us[c]) * a.inv_h + (a.Vs[yp] - a.Vs[c]) * a.inv_h) +
-                  (a.Ws[c + nxy] - a.Ws[c]) * a.inv_h;
-  a.rhs[c] = (a.rho0 * a.inv_dt) * div_u - div_g;
-  a.phat[c] = p0;
-}
-
-// ------------------------------------------------- a8: correction + status and mass (3D)
-// u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces 1..nz-1)
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_correct(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  const size_t nxy = (size_t)a.nx * a.ny;
-  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  const T* C = a.C1;
-  int bad = 0;
-  auto corr = [&](const T* vel, size_t nb) {
-    const T rho_f = rho(T(0.5) * (C[nb] + C[c]));
-    const T vn = vel[c] - a.dt * (((a.phat[c] - a.phat[nb]) * a.inv_h) / rho_f +
-                                  a.inv_rho0 * ((a.dp[c] - a.dp[nb]) * a.inv_h));
-    bad |= !isfinite(vn);
-    return vn;
-  };
-  const Nbr n = nbr(a, c, i, j, k);
-  const T un = corr(a.Us, n.xm);
-  const T vn = corr(a.Vs, n.ym);
-  T wn = T(0);
-  if (k >= 1) wn = corr(a.Ws, c - nxy);
-  bad |= !isfinite(C[c]);
-  a.Us[c] = un;
-  a.Vs[c] = vn;
-  if (k >= 1) a.Ws[c] = wn;
-  if (bad) atomicOr(a.status, 1);
-  const T lo = a.C1lo ? a.C1lo[c] : T(0);
-  const size_t ntiles = (nxy * a.nz) / kT3;
-  tile_mass<T, kT3>(C[c], lo, (int)blockIdx.x, (int)ntiles, a.partial, a.ticket, a.mass);
-}
-
 template <typename T>
 S3<T> make3(const Instance& in, int cur) {
   const ib_pf_params& p = in.prm;
@@ -576,27 +821,33 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
   };
   for (const Instance& in : ctx.inst) {
     const S3<T> a = make3<T>(in, cur);
-    const size_t cells = (size_t)in.nx * in.ny * in.nz;
-    const unsigned nb = (unsigned)(cells / kT3);
     const int ng = in.tab.ng, nf = in.tab.nfu + in.tab.nfv + in.tab.nfw;
-    k3_ch_h<T><<<nb, kT3, 0, s>>>(a);
+    const int kzp = in.nz < kPz ? in.nz : kPz, kzc = in.nz < kCz ? in.nz : kCz;
+    const dim3 zb(kPx, kPy);
+    const dim3 zg((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzc);
+    const dim3 zgp((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzp);
+    // FP32: one thread per cell; FP64: z-marching (each the faster form on GB300)
+    const unsigned nb = (unsigned)(((size_t)in.nx * in.ny * in.nz) / kT3);
+    constexpr bool percell = sizeof(T) == 4;
+    if constexpr (percell) k3_ch_h_c<T><<<nb, kT3, 0, s>>>(a);
+    else k3_ch_h_z<T><<<zg, zb, 0, s>>>(a);
     mark("ch_h");
-    k3_ch_rhs<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_ch_rhs_c<T><<<nb, kT3, 0, s>>>(a);
+    else k3_ch_rhs_z<T><<<zg, zb, 0, s>>>(a);
     mark("ch_rhs");
     launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
     if (ng > 0) {
       k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_C");
     }
-    k3_chem_pot<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_chem_pot_c<T><<<nb, kT3, 0, s>>>(a);
+    else k3_chem_pot_z<T><<<zg, zb, 0, s>>>(a);
     mark("chem_pot");
     if (ng > 0) {
       k3_fill_phi<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_phi");
     }
-    const int kzp = in.nz < kPz ? in.nz : kPz;
-    k3_predict<T><<<dim3((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzp),
-                    dim3(kPx, kPy), 0, s>>>(a);
+    k3_predict<T><<<zgp, zb, 0, s>>>(a);
     mark("predict");
     if (ng > 0) {
       k3_fill_u<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
@@ -608,10 +859,12 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       k3_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(a);
       mark("face_scatter");
     }
-    k3_poisson_rhs<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_poisson_rhs_c<T><<<nb, kT3, 0, s>>>(a);
+    else k3_poisson_rhs_z<T><<<zg, zb, 0, s>>>(a);
     mark("poisson_rhs");
     launches += spectral3_solve(in, ctx.precision, 1, cur, s, rec);
-    k3_correct<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_correct_c<T><<<nb, kT3, 0, s>>>(a);
+    else k3_correct_z<T><<<zg, zb, 0, s>>>(a);
     mark("correct");
   }
   return launches;
