@@ -128,3 +128,25 @@ def test_multi_step_sphere_tracks_oracle(ibpf):
     s.close()
     for k in ("C", "u", "v", "w"):
         assert _rel(out[k], st[k]) <= 1e-10, k
+
+
+@pytest.mark.parametrize("name,steps", [("sphere64", 400), ("porous64", 200)])
+def test_fp32_run_bounds_vs_fp64_path_3d(ibpf, name, steps):
+    # the FP32 form against the FP64 path (which tracks the oracle to round-off, see above)
+    # from the initial droplet: C within 1e-5 and the velocity within 1e-4 (max-norm relative),
+    # the bounds of the 2D mixed form
+    case = W.small_sphere_case(64) if name == "sphere64" else W.porous_case(64, steps=1)
+    st = W.initial_state3d(case)
+    out = {}
+    for prec in (ibpf.FP64, ibpf.FP32):
+        s = _solver(ibpf, case, prec)
+        s.write_state(st)
+        s.step(steps)
+        assert s.query(ibpf.Q_STATUS) == 0.0
+        d = {k: v.astype(np.float64) for k, v in s.read_state().items()}
+        if prec == ibpf.FP32:
+            d["C"] = d["C"] + s.read("C_lo").astype(np.float64)
+        out[prec] = d
+        s.close()
+    errs = {k: _rel(out[ibpf.FP32][k], out[ibpf.FP64][k]) for k in ("C", "u", "v", "w")}
+    assert errs["C"] <= 1e-5 and max(errs["u"], errs["v"], errs["w"]) <= 1e-4, errs
