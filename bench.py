@@ -244,10 +244,11 @@ def kernel_sources_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
-    f = ROOT / "profiles" / f"traffic_sinusoid_512x256_{precision}.txt"
+def read_traffic(kernel: str, precision: str, workload: str = "sinusoid_512x256x6"):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
+    profiles/traffic_<workload>_<precision>.txt, if it was taken on the current kernel
+    sources (else None)."""
+    f = ROOT / "profiles" / f"traffic_{workload}_{precision}.txt"
     if not f.exists():
         return None
     sha = kernel_sources_sha()
@@ -280,7 +281,8 @@ def kernel_flops64(name: str, nx: int, ny: int) -> float:
     return table.get(name, 0.0)
 
 
-def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, words=None):
+def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, words=None,
+             workload="sinusoid_512x256x6"):
     """Roofline of the dominant kernel and per-kernel table from an event-timed pass:
     ktot[name] = total ms over `steps` steps, kcount[name] = launches.  FP64 2D lines are
     reported against the FP64 pipe, every other line against HBM bandwidth."""
@@ -300,14 +302,14 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": read_traffic(dom, form), "alg_bytes_per_launch": alg}
+                "traffic": read_traffic(dom, form, workload), "alg_bytes_per_launch": alg}
     else:
         alg = kernel_flops64(dom, case0.nx, case0.ny) * cells
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
                 "peak": FP64_PEAK_GFLOPS, "peak_kind": "derived (FP64 pipe)",
                 "unit": "GFLOP/s (FP64)", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": read_traffic(dom, form), "alg_flops_per_launch": alg}
+                "traffic": read_traffic(dom, form, workload), "alg_flops_per_launch": alg}
     roof.update({"per_launch_us": per_launch_ms * 1e3, "kernels": table})
     return roof
 
@@ -356,7 +358,7 @@ def run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, ti
                 _, ktot, kcount = timed_steps(s, n, collect_kernels=True)
                 ibpf.ib_pf_set_kernel_timing(s.ctx, False)
                 line["roofline"] = roofline(ktot, kcount, n, case.cells, esz, case, peak, peak_kind,
-                                            form, KERNEL_STEP_WORDS_3D)
+                                            form, KERNEL_STEP_WORDS_3D, workload=name)
             except Exception as exc:
                 line["roofline"] = {"error": str(exc)[:200]}
             line["status"] = s.query(ibpf.Q_STATUS)
@@ -521,7 +523,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             _, ktot, kcount = timed_steps(esolver, esteps, collect_kernels=True)
             ibpf.ib_pf_set_kernel_timing(esolver.ctx, False)
-            eroof = roofline(ktot, kcount, esteps, ecells, 4, ecl[0], peak, peak_kind, "fp32")
+            eroof = roofline(ktot, kcount, esteps, ecells, 4, ecl[0], peak, peak_kind, "fp32",
+                             workload="ensemble64")
         except Exception as exc:
             eroof = {"error": str(exc)[:200]}
         ens = {"value": aggregate_rate(world, ecells, esteps, ems * 1e-3), "unit": UNIT,
