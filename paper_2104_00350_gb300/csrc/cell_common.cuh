@@ -32,48 +32,65 @@ __device__ __forceinline__ void pair_add(T& hi, T& lo, T b_hi, T b_lo) {
 }
 
 // Block reduction of one tile's sum of C in a fixed tree (FP64, or compensated FP32 pairs
-// in the FP32 form), written as FP64 at the tile's index; the last tile of an instance to
-// finish adds the partials in index order in FP64.
+// in the FP32 form): a shuffle tree within each warp, then over the warps' results; written
+// as FP64 at the tile's index.  The last tile of an instance to finish adds the partials
+// (each thread a fixed strided subset, then the same two-level tree) in FP64.
+template <typename T>
+__device__ __forceinline__ void warp_pair_sum(T& hi, T& lo) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T oh = __shfl_down_sync(0xffffffffu, hi, off), ol = __shfl_down_sync(0xffffffffu, lo, off);
+    pair_add(hi, lo, oh, ol);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = v + __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
 template <typename T, int NT>
 __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__ partial,
                           unsigned* __restrict__ ticket, double* __restrict__ mass) {
-  __shared__ T rh[NT];
-  __shared__ T rl[NT];
-  __shared__ double red[NT];
+  static_assert(NT % 32 == 0 && NT <= 1024, "whole warps");
+  constexpr int NW = NT / 32;
+  __shared__ T wh[NW];
+  __shared__ T wl[NW];
+  __shared__ double wd[NW];
   __shared__ bool last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
-  rh[tid] = hi;
-  rl[tid] = lo;
-  __syncthreads();
-  for (int s = nthr / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      T a_hi = rh[tid], a_lo = rl[tid];
-      pair_add(a_hi, a_lo, rh[tid + s], rl[tid + s]);
-      rh[tid] = a_hi;
-      rl[tid] = a_lo;
-    }
-    __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  warp_pair_sum(hi, lo);
+  if (lane == 0) {
+    wh[warp] = hi;
+    wl[warp] = lo;
   }
-  if (tid == 0) {
-    partial[tile] = (double)rh[0] + (double)rl[0];
-    __threadfence();
-    last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
+  __syncthreads();
+  if (warp == 0) {
+    hi = lane < NW ? wh[lane] : T(0);
+    lo = lane < NW ? wl[lane] : T(0);
+    warp_pair_sum(hi, lo);
+    if (lane == 0) {
+      partial[tile] = (double)hi + (double)lo;
+      __threadfence();
+      last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
+    }
   }
   __syncthreads();
   if (last) {
     __threadfence();
     double sacc = 0.0;
-    for (int b = tid; b < ntiles; b += nthr) sacc += ((volatile double*)partial)[b];
-    red[tid] = sacc;
+    for (int b = tid; b < ntiles; b += NT) sacc += ((volatile double*)partial)[b];
+    sacc = warp_sum(sacc);
+    if (lane == 0) wd[warp] = sacc;
     __syncthreads();
-    for (int q = nthr / 2; q > 0; q >>= 1) {
-      if (tid < q) red[tid] += red[tid + q];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      *mass = red[0];
-      *ticket = 0u;
+    if (warp == 0) {
+      sacc = warp_sum(lane < NW ? wd[lane] : 0.0);
+      if (lane == 0) {
+        *mass = sacc;
+        *ticket = 0u;
+      }
     }
   }
   __syncthreads();

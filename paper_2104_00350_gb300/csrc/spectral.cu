@@ -278,6 +278,7 @@ struct SymbolArgs {
   int ncx = 0;
   const double* lamyp = nullptr;
   const float* lamyp_f = nullptr;
+  float s_eta2_f = 0.f, c0_f = 0.f;   // FP32 path: s_eta2 and c0 rounded once
 };
 
 // Divide X_m by the symbol at (k, m).  FP64 path: in FP64.  FP32 path: in FP32 -- the
@@ -299,7 +300,7 @@ __device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs
     const float L = sym.ncx ? (sym.lamy_f[m] + sym.lamyp_f[k / sym.ncx]) + sym.lamx_f[k % sym.ncx]
                             : sym.lamy_f[m] + sym.lamx_f[k];
     float r;
-    if (sym.mode == 0) r = 1.0f / (L * L - (float)sym.s_eta2 * L + (float)sym.c0);
+    if (sym.mode == 0) r = 1.0f / (L * L - sym.s_eta2_f * L + sym.c0_f);
     else r = (L == 0.0f) ? 0.0f : 1.0f / L;
     X.x = X.x * r;
     X.y = X.y * r;
@@ -497,6 +498,8 @@ __global__ void __launch_bounds__(THREADS) kb_cols(const InstDev<T>* __restrict_
   sym.mode = mode;
   sym.s_eta2 = d.s_eta2;
   sym.c0 = d.c0;
+  sym.s_eta2_f = (float)d.s_eta2;
+  sym.c0_f = (float)d.c0;
   sym.lamx = d.lamx;
   sym.lamy = d.lamy;
   sym.lamx_f = d.lamx_f;
@@ -758,6 +761,8 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   sym.mode = mode;
   sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
   sym.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
+  sym.s_eta2_f = (float)sym.s_eta2;
+  sym.c0_f = (float)sym.c0;
   sym.lamx = in.lamx;
   sym.lamy = in.lamz;
   sym.lamx_f = in.lamx_f;
