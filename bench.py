@@ -484,13 +484,12 @@ def run_ours(args):
             e2e_steps = max(1, min(args.steps, 50))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            writes = [(name, pinned[k][name], k) for k in range(len(cl)) for name in ibpf.STATE_FIELDS]
+            reads = [("C", outC[k], k) for k in range(len(cl))]
             for _ in range(e2e_steps):
-                for k in range(len(cl)):
-                    for name in ibpf.STATE_FIELDS:
-                        solver.write(name, pinned[k][name], k)
+                solver.write_many(writes)     # one call, one synchronisation
                 solver.step(1)
-                for k in range(len(cl)):
-                    solver.read("C", k, out=outC[k])
+                solver.read_many(reads)
             torch.cuda.synchronize()
             e2e_s = time.perf_counter() - t0
             e2e = {"value": aggregate_rate(world, cells, e2e_steps,

@@ -199,6 +199,19 @@ ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void*
 ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
                                 long long nbytes, int src_on_host);
 
+/* Batched field I/O: entry q of the arrays is one ib_pf_write_fields / ib_pf_read_fields
+ * (instances[q], field_ids[q], bufs[q], nbytes[q]) with the same checks and effects; all
+ * copies are queued on the work stream in order and the call synchronises once at the end
+ * when buffers are host memory (on_host != 0), instead of once per field.  Entries are
+ * validated before anything is queued: one bad entry fails the whole call with
+ * IB_PF_E_ARG and nothing is copied.  n = 0 is a no-op. */
+ib_pf_status ib_pf_write_fields_batch(ib_pf_ctx* ctx, int n, const int* instances,
+                                      const int* field_ids, const void* const* srcs,
+                                      const long long* nbytes, int src_on_host);
+ib_pf_status ib_pf_read_fields_batch(ib_pf_ctx* ctx, int n, const int* instances,
+                                     const int* field_ids, void* const* dsts,
+                                     const long long* nbytes, int dst_on_host);
+
 /* Copy geometry table `table_id` of `instance` to host memory.  If dst is NULL only the
  * element count is returned in *count; otherwise nbytes must match.  Synchronises. */
 ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* dst,

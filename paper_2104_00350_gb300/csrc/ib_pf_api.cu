@@ -415,45 +415,42 @@ ib_pf_status ib_pf_step(ib_pf_ctx* ctx, int nsteps) {
   return IB_PF_OK;
 }
 
-ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void* dst,
-                               long long nbytes, int dst_on_host) {
-  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+}  // extern "C"
+
+namespace {
+
+// checks of one read (write = false) or write entry; returns the field's device pointer
+ib_pf_status check_field(ib_pf_ctx* ctx, int instance, int field_id, const void* buf,
+                         long long nbytes, bool write, void** dev) {
   if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
-  if (!dst) return fail(ctx, IB_PF_E_ARG, "null destination");
+  if (!buf) return fail(ctx, IB_PF_E_ARG, write ? "null source" : "null destination");
+  if (write) {
+    const bool lo_field = field_id == IB_PF_F_C_LO || field_id == IB_PF_F_C_OLD_LO;
+    const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
+    if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field && !w_field)
+      return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
+  }
   Instance& in = ctx->inst[instance];
-  void* src = field_ptr(*ctx, in, field_id);
-  if (!src) return fail(ctx, IB_PF_E_ARG, "bad field id (low parts exist only in FP32 contexts)");
+  void* p = field_ptr(*ctx, in, field_id);
+  if (!p) return fail(ctx, IB_PF_E_ARG, "bad field id (low parts of C exist only in FP32 contexts, w only in 3D)");
   const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
   if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
-  CK(join_in(*ctx));
-  CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                     ctx->work));
-  if (dst_on_host) CK(cudaStreamSynchronize(ctx->work));
-  CK(join_out(*ctx));
+  *dev = p;
   return IB_PF_OK;
 }
 
-ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
-                                long long nbytes, int src_on_host) {
-  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
-  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
-  if (!src) return fail(ctx, IB_PF_E_ARG, "null source");
-  const bool lo_field = field_id == IB_PF_F_C_LO || field_id == IB_PF_F_C_OLD_LO;
-  const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
-  if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field && !w_field)
-    return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
+// queue one write (already checked): the copy, the cleared low part of a written C level,
+// the zero wall rows / planes of v (2D) or w (3D), the cleared status word
+ib_pf_status queue_write(ib_pf_ctx* ctx, int instance, int field_id, void* dst, const void* src,
+                         long long nbytes, int src_on_host) {
   Instance& in = ctx->inst[instance];
-  void* dst = field_ptr(*ctx, in, field_id);
-  if (!dst) return fail(ctx, IB_PF_E_ARG, "low parts of C exist only in FP32 contexts, w only in 3D");
-  const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
-  if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
-  CK(join_in(*ctx));
   CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                      ctx->work));
   if ((field_id == IB_PF_F_C || field_id == IB_PF_F_C_OLD) && ctx->precision == IB_PF_FP32) {
     void* lo = field_ptr(*ctx, in, field_id == IB_PF_F_C ? IB_PF_F_C_LO : IB_PF_F_C_OLD_LO);
     CK(cudaMemsetAsync(lo, 0, (size_t)nbytes, ctx->work));
   }
+  const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
   if (in.dim == 3 && w_field) {   // the wall planes of w are zero
     const size_t plane = (size_t)in.nx * in.ny * ctx->esz;
     CK(cudaMemsetAsync(dst, 0, plane, ctx->work));
@@ -466,8 +463,82 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
   }
   // new state: forget an earlier non-finite flag of this instance
   CK(cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work));
+  return IB_PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void* dst,
+                               long long nbytes, int dst_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  void* src = nullptr;
+  ib_pf_status st = check_field(ctx, instance, field_id, dst, nbytes, false, &src);
+  if (st != IB_PF_OK) return st;
+  CK(join_in(*ctx));
+  CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     ctx->work));
+  if (dst_on_host) CK(cudaStreamSynchronize(ctx->work));
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
+                                long long nbytes, int src_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  void* dst = nullptr;
+  ib_pf_status st = check_field(ctx, instance, field_id, src, nbytes, true, &dst);
+  if (st != IB_PF_OK) return st;
+  CK(join_in(*ctx));
+  st = queue_write(ctx, instance, field_id, dst, src, nbytes, src_on_host);
+  if (st != IB_PF_OK) return st;
   CK(cudaStreamSynchronize(ctx->work));
   ((volatile int*)ctx->h_status)[instance] = 0;
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_write_fields_batch(ib_pf_ctx* ctx, int n, const int* instances,
+                                      const int* field_ids, const void* const* srcs,
+                                      const long long* nbytes, int src_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (n < 0) return fail(ctx, IB_PF_E_ARG, "n < 0");
+  if (n == 0) return IB_PF_OK;
+  if (!instances || !field_ids || !srcs || !nbytes) return fail(ctx, IB_PF_E_ARG, "null array");
+  std::vector<void*> dst(n);
+  for (int q = 0; q < n; ++q) {
+    ib_pf_status st = check_field(ctx, instances[q], field_ids[q], srcs[q], nbytes[q], true, &dst[q]);
+    if (st != IB_PF_OK) return fail(ctx, st, "entry " + std::to_string(q) + ": " + ctx->err);
+  }
+  CK(join_in(*ctx));
+  for (int q = 0; q < n; ++q) {
+    ib_pf_status st = queue_write(ctx, instances[q], field_ids[q], dst[q], srcs[q], nbytes[q], src_on_host);
+    if (st != IB_PF_OK) return st;
+  }
+  CK(cudaStreamSynchronize(ctx->work));
+  for (int q = 0; q < n; ++q) ((volatile int*)ctx->h_status)[instances[q]] = 0;
+  CK(join_out(*ctx));
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_read_fields_batch(ib_pf_ctx* ctx, int n, const int* instances,
+                                     const int* field_ids, void* const* dsts,
+                                     const long long* nbytes, int dst_on_host) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (n < 0) return fail(ctx, IB_PF_E_ARG, "n < 0");
+  if (n == 0) return IB_PF_OK;
+  if (!instances || !field_ids || !dsts || !nbytes) return fail(ctx, IB_PF_E_ARG, "null array");
+  std::vector<void*> src(n);
+  for (int q = 0; q < n; ++q) {
+    ib_pf_status st = check_field(ctx, instances[q], field_ids[q], dsts[q], nbytes[q], false, &src[q]);
+    if (st != IB_PF_OK) return fail(ctx, st, "entry " + std::to_string(q) + ": " + ctx->err);
+  }
+  CK(join_in(*ctx));
+  for (int q = 0; q < n; ++q)
+    CK(cudaMemcpyAsync(dsts[q], src[q], (size_t)nbytes[q],
+                       dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->work));
+  if (dst_on_host) CK(cudaStreamSynchronize(ctx->work));
   CK(join_out(*ctx));
   return IB_PF_OK;
 }

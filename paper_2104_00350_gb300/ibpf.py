@@ -73,6 +73,10 @@ def _load():
         "ib_pf_step": (i, [vp, i]),
         "ib_pf_read_fields": (i, [vp, i, i, vp, ll, i]),
         "ib_pf_write_fields": (i, [vp, i, i, vp, ll, i]),
+        "ib_pf_write_fields_batch": (i, [vp, i, ct.POINTER(i), ct.POINTER(i), ct.POINTER(vp),
+                                         ct.POINTER(ll), i]),
+        "ib_pf_read_fields_batch": (i, [vp, i, ct.POINTER(i), ct.POINTER(i), ct.POINTER(vp),
+                                        ct.POINTER(ll), i]),
         "ib_pf_read_table": (i, [vp, i, i, vp, ll, ct.POINTER(ll)]),
         "ib_pf_query": (i, [vp, i, i, ct.POINTER(ct.c_double)]),
         "ib_pf_set_kernel_timing": (i, [vp, i]),
@@ -140,6 +144,27 @@ def ib_pf_read_fields(ctx, instance: int, field_id: int, dst_ptr: int, nbytes: i
 def ib_pf_write_fields(ctx, instance: int, field_id: int, src_ptr: int, nbytes: int, src_on_host: bool):
     _check(lib().ib_pf_write_fields(ctx, instance, field_id, ct.c_void_p(src_ptr), nbytes,
                                     int(src_on_host)), ctx)
+
+
+def _batch_args(items):
+    n = len(items)
+    inst = (ct.c_int * n)(*[it[0] for it in items])
+    fids = (ct.c_int * n)(*[it[1] for it in items])
+    ptrs = (ct.c_void_p * n)(*[it[2] for it in items])
+    nb = (ct.c_longlong * n)(*[it[3] for it in items])
+    return n, inst, fids, ptrs, nb
+
+
+def ib_pf_write_fields_batch(ctx, items, src_on_host: bool):
+    """items: (instance, field_id, src_ptr, nbytes) tuples."""
+    n, inst, fids, ptrs, nb = _batch_args(items)
+    _check(lib().ib_pf_write_fields_batch(ctx, n, inst, fids, ptrs, nb, int(src_on_host)), ctx)
+
+
+def ib_pf_read_fields_batch(ctx, items, dst_on_host: bool):
+    """items: (instance, field_id, dst_ptr, nbytes) tuples."""
+    n, inst, fids, ptrs, nb = _batch_args(items)
+    _check(lib().ib_pf_read_fields_batch(ctx, n, inst, fids, ptrs, nb, int(dst_on_host)), ctx)
 
 
 def ib_pf_read_table(ctx, instance: int, table_id: int, dst_ptr: int | None, nbytes: int) -> int:
@@ -271,6 +296,42 @@ class Solver:
         a = np.empty(self.field_shape(name, instance), dtype=self.dtype)
         ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
         return a
+
+    def write_many(self, items):
+        """items: (name, array, instance) with numpy host arrays or torch tensors, all on
+        the host or all on the device; one synchronisation for the whole batch."""
+        keep, args, host = [], [], None
+        for name, arr, inst in items:
+            if hasattr(arr, "data_ptr"):
+                assert arr.is_contiguous()
+                on_host = not arr.is_cuda
+                args.append((inst, FIELD_IDS[name], arr.data_ptr(), arr.numel() * arr.element_size()))
+            else:
+                a = np.ascontiguousarray(arr, dtype=self.dtype)
+                keep.append(a)
+                on_host = True
+                args.append((inst, FIELD_IDS[name], a.ctypes.data, a.nbytes))
+            assert host is None or host == on_host, "mixed host and device buffers"
+            host = on_host
+        if args:
+            ib_pf_write_fields_batch(self.ctx, args, host)
+
+    def read_many(self, items):
+        """items: (name, out, instance) with preallocated numpy arrays or torch tensors, all on
+        the host or all on the device; one synchronisation for the whole batch."""
+        args, host = [], None
+        for name, out, inst in items:
+            if hasattr(out, "data_ptr"):
+                on_host = not out.is_cuda
+                args.append((inst, FIELD_IDS[name], out.data_ptr(), out.numel() * out.element_size()))
+            else:
+                assert out.flags["C_CONTIGUOUS"] and out.dtype == self.dtype
+                on_host = True
+                args.append((inst, FIELD_IDS[name], out.ctypes.data, out.nbytes))
+            assert host is None or host == on_host, "mixed host and device buffers"
+            host = on_host
+        if args:
+            ib_pf_read_fields_batch(self.ctx, args, host)
 
     def table(self, table_id: int, instance: int = 0) -> np.ndarray:
         n = ib_pf_read_table(self.ctx, instance, table_id, None, 0)

@@ -241,3 +241,34 @@ def test_batched_uneven_ensemble_matches_oracle(ibpf):
             assert _rel(out[f], ref[f]) <= TOL64, (k, c.name, f)
     assert s.query(ibpf.Q_LAUNCHES) <= 17
     s.close()
+
+
+def test_batched_field_io_matches_single_calls(ibpf):
+    # one batched write of every state field of two instances equals field-by-field writes;
+    # one batched read equals single reads; a bad entry fails the call and copies nothing
+    cl = [cases.flat_wall_128x64(), cases.sinusoid_wall_512x256(theta_deg=90.0, l_s=0.0)]
+    states = [cases.random_state(c, seed=21 + k) for k, c in enumerate(cl)]
+    a = ibpf.solver_from_cases(cl, ibpf.FP32)
+    b = ibpf.solver_from_cases(cl, ibpf.FP32)
+    for s in (a, b):
+        s.precompute_weights()
+    for k in range(2):
+        a.write_state(states[k], k)
+    b.write_many([(n, states[k][n], k) for k in range(2) for n in ibpf.STATE_FIELDS])
+    for k in range(2):
+        for n in ibpf.STATE_FIELDS + ("C_lo", "C_old_lo"):
+            assert np.array_equal(a.read(n, k), b.read(n, k)), (k, n)
+    a.step(3)
+    b.step(3)
+    outs = [(n, np.empty(b.field_shape(n, k), np.float32), k) for k in range(2) for n in ("C", "u", "v", "P")]
+    b.read_many(outs)
+    for n, arr, k in outs:
+        assert np.array_equal(arr, a.read(n, k)), (k, n)
+    before = b.read("C", 0)
+    bad = [("C", np.zeros((64, 128), np.float32), 0), ("u", np.zeros((3, 3), np.float32), 1)]
+    with pytest.raises(ibpf.IbPfError) as ei:
+        b.write_many(bad)
+    assert ei.value.status == ibpf.E_ARG
+    assert np.array_equal(b.read("C", 0), before)
+    a.close()
+    b.close()
