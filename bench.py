@@ -484,12 +484,13 @@ def run_ours(args):
             e2e_steps = max(1, min(args.steps, 50))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            writes = [(name, pinned[k][name], k) for k in range(len(cl)) for name in ibpf.STATE_FIELDS]
-            reads = [("C", outC[k], k) for k in range(len(cl))]
+            writes = solver.prepare_writes([(name, pinned[k][name], k) for k in range(len(cl))
+                                            for name in ibpf.STATE_FIELDS])
+            reads = solver.prepare_reads([("C", outC[k], k) for k in range(len(cl))])
             for _ in range(e2e_steps):
-                solver.write_many(writes)     # one call, one synchronisation
+                writes.run()     # one call, one synchronisation
                 solver.step(1)
-                solver.read_many(reads)
+                reads.run()
             torch.cuda.synchronize()
             e2e_s = time.perf_counter() - t0
             e2e = {"value": aggregate_rate(world, cells, e2e_steps,

@@ -194,17 +194,23 @@ ib_pf_status ib_pf_read_fields(ib_pf_ctx* ctx, int instance, int field_id, void*
 
 /* Copy src into state field `field_id` of `instance` (restart / initial condition).
  * Only the read/write ids above are accepted.  src_on_host as for ib_pf_read_fields.
- * Rows 0 and ny of v fields are forced to zero.  Clears the instance's non-finite status
- * and synchronises the stream. */
+ * Rows 0 and ny of v fields (2D) and planes 0 and nz of w fields (3D) are forced to zero;
+ * writing C or C_old in the FP32 form clears its low part.  Device sources and pinned
+ * (page-locked) host sources are read by one copy kernel on the work stream; other host
+ * memory goes through cudaMemcpyAsync.  Clears the instance's non-finite status and
+ * synchronises the stream; src may be reused when the call returns. */
 ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, const void* src,
                                 long long nbytes, int src_on_host);
 
 /* Batched field I/O: entry q of the arrays is one ib_pf_write_fields / ib_pf_read_fields
- * (instances[q], field_ids[q], bufs[q], nbytes[q]) with the same checks and effects; all
- * copies are queued on the work stream in order and the call synchronises once at the end
- * when buffers are host memory (on_host != 0), instead of once per field.  Entries are
- * validated before anything is queued: one bad entry fails the whole call with
- * IB_PF_E_ARG and nothing is copied.  n = 0 is a no-op. */
+ * (instances[q], field_ids[q], bufs[q], nbytes[q]) with the same checks and effects, as if
+ * the entries ran in order (a later write of the same field wins; C_lo written after C
+ * keeps the written low part).  Copies from or to device or pinned host memory go to one
+ * copy kernel launch per 48 entries (other host memory: cudaMemcpyAsync); the destination
+ * buffers of one read batch must not overlap.  The call synchronises once at the end
+ * (writes always, reads when on_host != 0) instead of once per field.  Entries are validated before
+ * anything is queued: one bad entry fails the whole call with IB_PF_E_ARG and nothing is
+ * copied.  n = 0 is a no-op. */
 ib_pf_status ib_pf_write_fields_batch(ib_pf_ctx* ctx, int n, const int* instances,
                                       const int* field_ids, const void* const* srcs,
                                       const long long* nbytes, int src_on_host);

@@ -1,10 +1,13 @@
 // C ABI of the ib_pf library: context life cycle, field I/O and step replay through CUDA
 // graphs.  Declarations and argument contracts are in include/ib_pf.h.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
+#include <algorithm>
 
 #include "batch.h"
 #include "ibpf_internal.h"
@@ -439,31 +442,149 @@ ib_pf_status check_field(ib_pf_ctx* ctx, int instance, int field_id, const void*
   return IB_PF_OK;
 }
 
-// queue one write (already checked): the copy, the cleared low part of a written C level,
-// the zero wall rows / planes of v (2D) or w (3D), the cleared status word
-ib_pf_status queue_write(ib_pf_ctx* ctx, int instance, int field_id, void* dst, const void* src,
-                         long long nbytes, int src_on_host) {
+// One entry of a batched write, in 32-bit words: dst[i] = src[i] for zhead <= i < words - ztail
+// and 0 elsewhere; src == nullptr zeroes all of dst.  src is device memory or the device
+// address of pinned (page-locked, mapped) host memory, which the kernel reads directly.
+struct CopyEntry {
+  const unsigned int* src;
+  unsigned int* dst;
+  unsigned long long words, zhead, ztail;
+};
+constexpr int kCopyMax = 48;   // 48 entries = 1920 bytes of kernel parameters
+struct CopyList {
+  CopyEntry e[kCopyMax];
+};
+constexpr int kCopyThreads = 256, kCopyUnroll = 4;
+
+__global__ void __launch_bounds__(kCopyThreads) k_copy_entries(CopyList L) {
+  const CopyEntry c = L.e[blockIdx.y];
+  const unsigned long long lo = c.src ? c.zhead : c.words, hi = c.src ? c.words - c.ztail : c.words;
+  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst)) & 15) == 0 &&
+                   (c.words & 3) == 0;
+  if (vec) {
+    // 16-byte words; every vector lies inside [0, words), so a vector that holds any copied
+    // word is read whole and its zero words are masked afterwards
+    const uint4* s = reinterpret_cast<const uint4*>(c.src);
+    uint4* d = reinterpret_cast<uint4*>(c.dst);
+    const unsigned long long nv = c.words >> 2;
+    for (unsigned long long base = t0; base < nv; base += stride * kCopyUnroll) {
+      uint4 v[kCopyUnroll];
+#pragma unroll
+      for (int u = 0; u < kCopyUnroll; ++u) {   // all loads first: several in flight per thread
+        const unsigned long long q = base + u * stride;
+        v[u] = make_uint4(0u, 0u, 0u, 0u);
+        if (q < nv && 4 * q + 4 > lo && 4 * q < hi) v[u] = s[q];
+      }
+#pragma unroll
+      for (int u = 0; u < kCopyUnroll; ++u) {
+        const unsigned long long q = base + u * stride;
+        if (q >= nv) continue;
+        const unsigned long long w0 = 4 * q;
+        if (w0 < lo || w0 + 4 > hi) {
+          if (w0 + 0 < lo || w0 + 0 >= hi) v[u].x = 0u;
+          if (w0 + 1 < lo || w0 + 1 >= hi) v[u].y = 0u;
+          if (w0 + 2 < lo || w0 + 2 >= hi) v[u].z = 0u;
+          if (w0 + 3 < lo || w0 + 3 >= hi) v[u].w = 0u;
+        }
+        d[q] = v[u];
+      }
+    }
+  } else {
+    for (unsigned long long i = t0; i < c.words; i += stride)
+      c.dst[i] = (i >= lo && i < hi) ? c.src[i] : 0u;
+  }
+}
+
+// The effects of a sequence of field writes, gathered so that one launch (per kCopyMax
+// entries) performs them: entries keyed by destination, a later write of the same
+// destination replacing the earlier one.  Sources that are neither device memory nor
+// pinned host memory are copied by cudaMemcpyAsync when added (stream order then puts
+// them before the launch, which carries only their zero rows).
+struct WritePlan {
+  std::vector<CopyEntry> e;
+  std::vector<const void*> key;   // destination field of each entry
+
+  void kill(const void* dst) {
+    for (size_t q = 0; q < e.size(); ++q)
+      if (key[q] == dst) e[q].words = 0;
+  }
+  void add(const void* field, const CopyEntry& c) {
+    e.push_back(c);
+    key.push_back(field);
+  }
+};
+
+// device address of a host or device buffer, or nullptr if a kernel cannot access it
+const void* device_source(const void* src, int src_on_host) {
+  if (!src_on_host) return src;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return src;
+  return nullptr;
+}
+
+// plan one write (already checked): the copy with the zero wall rows / planes of v (2D)
+// or w (3D), and the cleared low part of a written C level (FP32 form)
+ib_pf_status plan_write(ib_pf_ctx* ctx, WritePlan& plan, int instance, int field_id, void* dst,
+                        const void* src, long long nbytes, int src_on_host) {
   Instance& in = ctx->inst[instance];
-  CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                     ctx->work));
+  const unsigned long long words = (unsigned long long)nbytes / 4;
+  unsigned long long zrow = 0;   // words of each zero wall row / plane at both ends
+  const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
+  if (in.dim == 3 && w_field) zrow = (unsigned long long)in.nx * in.ny * ctx->esz / 4;
+  if (in.dim == 2 && (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV))
+    zrow = (unsigned long long)in.nx * ctx->esz / 4;
+  plan.kill(dst);
+  const void* dsrc = device_source(src, src_on_host);
+  if (dsrc) {
+    plan.add(dst, {(const unsigned int*)dsrc, (unsigned int*)dst, words, zrow, zrow});
+  } else {
+    CK(cudaMemcpyAsync(dst, src, (size_t)nbytes, cudaMemcpyDefault, ctx->work));
+    if (zrow) {
+      plan.add(dst, {nullptr, (unsigned int*)dst, zrow, 0, 0});
+      plan.add(dst, {nullptr, (unsigned int*)dst + (words - zrow), zrow, 0, 0});
+    }
+  }
   if ((field_id == IB_PF_F_C || field_id == IB_PF_F_C_OLD) && ctx->precision == IB_PF_FP32) {
     void* lo = field_ptr(*ctx, in, field_id == IB_PF_F_C ? IB_PF_F_C_LO : IB_PF_F_C_OLD_LO);
-    CK(cudaMemsetAsync(lo, 0, (size_t)nbytes, ctx->work));
+    plan.kill(lo);
+    plan.add(lo, {nullptr, (unsigned int*)lo, words, 0, 0});
   }
-  const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
-  if (in.dim == 3 && w_field) {   // the wall planes of w are zero
-    const size_t plane = (size_t)in.nx * in.ny * ctx->esz;
-    CK(cudaMemsetAsync(dst, 0, plane, ctx->work));
-    CK(cudaMemsetAsync((char*)dst + (size_t)in.nz * plane, 0, plane, ctx->work));
-  }
-  if (in.dim == 2 && (field_id == IB_PF_F_V || field_id == IB_PF_F_V_OLD || field_id == IB_PF_F_HV)) {
-    const size_t row = (size_t)in.nx * ctx->esz;
-    CK(cudaMemsetAsync(dst, 0, row, ctx->work));
-    CK(cudaMemsetAsync((char*)dst + (size_t)in.ny * row, 0, row, ctx->work));
-  }
-  // new state: forget an earlier non-finite flag of this instance
-  CK(cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work));
   return IB_PF_OK;
+}
+
+// one k_copy_entries launch per kCopyMax entries on the work stream
+ib_pf_status launch_entries(ib_pf_ctx* ctx, const std::vector<CopyEntry>& live) {
+  for (size_t a = 0; a < live.size(); a += kCopyMax) {
+    CopyList L{};
+    const int m = (int)std::min<size_t>(kCopyMax, live.size() - a);
+    unsigned long long most = 0;
+    for (int q = 0; q < m; ++q) {
+      L.e[q] = live[a + q];
+      most = std::max(most, L.e[q].words);
+    }
+    const unsigned long long per_block = 4ull * kCopyThreads * kCopyUnroll;
+    const int gx = (int)std::min<unsigned long long>(128, std::max<unsigned long long>(1, (most + per_block - 1) / per_block));
+    k_copy_entries<<<dim3(gx, m), kCopyThreads, 0, ctx->work>>>(L);
+    CK(cudaGetLastError());
+  }
+  return IB_PF_OK;
+}
+
+// launch the plan's live entries and clear the status words of the written instances
+ib_pf_status run_plan(ib_pf_ctx* ctx, WritePlan& plan, const std::vector<char>& touched) {
+  for (size_t k = 0; k < touched.size(); ++k)
+    if (touched[k]) plan.add(ctx->inst[k].status, {nullptr, (unsigned int*)ctx->inst[k].status, 1, 0, 0});
+  std::vector<CopyEntry> live;
+  for (const CopyEntry& c : plan.e)
+    if (c.words) live.push_back(c);
+  return launch_entries(ctx, live);
 }
 
 }  // namespace
@@ -491,7 +612,12 @@ ib_pf_status ib_pf_write_fields(ib_pf_ctx* ctx, int instance, int field_id, cons
   ib_pf_status st = check_field(ctx, instance, field_id, src, nbytes, true, &dst);
   if (st != IB_PF_OK) return st;
   CK(join_in(*ctx));
-  st = queue_write(ctx, instance, field_id, dst, src, nbytes, src_on_host);
+  WritePlan plan;
+  st = plan_write(ctx, plan, instance, field_id, dst, src, nbytes, src_on_host);
+  if (st != IB_PF_OK) return st;
+  std::vector<char> touched(ctx->inst.size(), 0);
+  touched[instance] = 1;
+  st = run_plan(ctx, plan, touched);
   if (st != IB_PF_OK) return st;
   CK(cudaStreamSynchronize(ctx->work));
   ((volatile int*)ctx->h_status)[instance] = 0;
@@ -512,10 +638,16 @@ ib_pf_status ib_pf_write_fields_batch(ib_pf_ctx* ctx, int n, const int* instance
     if (st != IB_PF_OK) return fail(ctx, st, "entry " + std::to_string(q) + ": " + ctx->err);
   }
   CK(join_in(*ctx));
+  std::vector<char> touched(ctx->inst.size(), 0);
+  WritePlan plan;
   for (int q = 0; q < n; ++q) {
-    ib_pf_status st = queue_write(ctx, instances[q], field_ids[q], dst[q], srcs[q], nbytes[q], src_on_host);
+    ib_pf_status st = plan_write(ctx, plan, instances[q], field_ids[q], dst[q], srcs[q], nbytes[q],
+                                 src_on_host);
     if (st != IB_PF_OK) return st;
+    touched[instances[q]] = 1;
   }
+  ib_pf_status rs = run_plan(ctx, plan, touched);
+  if (rs != IB_PF_OK) return rs;
   CK(cudaStreamSynchronize(ctx->work));
   for (int q = 0; q < n; ++q) ((volatile int*)ctx->h_status)[instances[q]] = 0;
   CK(join_out(*ctx));
@@ -535,9 +667,17 @@ ib_pf_status ib_pf_read_fields_batch(ib_pf_ctx* ctx, int n, const int* instances
     if (st != IB_PF_OK) return fail(ctx, st, "entry " + std::to_string(q) + ": " + ctx->err);
   }
   CK(join_in(*ctx));
-  for (int q = 0; q < n; ++q)
-    CK(cudaMemcpyAsync(dsts[q], src[q], (size_t)nbytes[q],
-                       dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->work));
+  // device and pinned host destinations: written by the copy kernel; others: cudaMemcpyAsync
+  std::vector<CopyEntry> ent;
+  for (int q = 0; q < n; ++q) {
+    void* d = const_cast<void*>(device_source(dsts[q], dst_on_host));
+    if (d)
+      ent.push_back({(const unsigned int*)src[q], (unsigned int*)d, (unsigned long long)nbytes[q] / 4, 0, 0});
+    else
+      CK(cudaMemcpyAsync(dsts[q], src[q], (size_t)nbytes[q], cudaMemcpyDefault, ctx->work));
+  }
+  ib_pf_status ls = launch_entries(ctx, ent);
+  if (ls != IB_PF_OK) return ls;
   if (dst_on_host) CK(cudaStreamSynchronize(ctx->work));
   CK(join_out(*ctx));
   return IB_PF_OK;

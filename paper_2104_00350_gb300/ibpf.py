@@ -297,41 +297,29 @@ class Solver:
         ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
         return a
 
+    def prepare_writes(self, items) -> "FieldBatch":
+        """A reusable batched write of (name, array, instance) items (torch tensors or
+        contiguous numpy arrays of the context's dtype, all on the host or all on the device):
+        the argument arrays are built once; .run() issues the one C call."""
+        return FieldBatch(self, items, write=True)
+
+    def prepare_reads(self, items) -> "FieldBatch":
+        """The same for batched reads into preallocated (name, out, instance) buffers."""
+        return FieldBatch(self, items, write=False)
+
     def write_many(self, items):
         """items: (name, array, instance) with numpy host arrays or torch tensors, all on
         the host or all on the device; one synchronisation for the whole batch."""
-        keep, args, host = [], [], None
-        for name, arr, inst in items:
-            if hasattr(arr, "data_ptr"):
-                assert arr.is_contiguous()
-                on_host = not arr.is_cuda
-                args.append((inst, FIELD_IDS[name], arr.data_ptr(), arr.numel() * arr.element_size()))
-            else:
-                a = np.ascontiguousarray(arr, dtype=self.dtype)
-                keep.append(a)
-                on_host = True
-                args.append((inst, FIELD_IDS[name], a.ctypes.data, a.nbytes))
-            assert host is None or host == on_host, "mixed host and device buffers"
-            host = on_host
-        if args:
-            ib_pf_write_fields_batch(self.ctx, args, host)
+        items = [(n, a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=self.dtype), k)
+                 for n, a, k in items]
+        if items:
+            FieldBatch(self, items, write=True).run()
 
     def read_many(self, items):
         """items: (name, out, instance) with preallocated numpy arrays or torch tensors, all on
         the host or all on the device; one synchronisation for the whole batch."""
-        args, host = [], None
-        for name, out, inst in items:
-            if hasattr(out, "data_ptr"):
-                on_host = not out.is_cuda
-                args.append((inst, FIELD_IDS[name], out.data_ptr(), out.numel() * out.element_size()))
-            else:
-                assert out.flags["C_CONTIGUOUS"] and out.dtype == self.dtype
-                on_host = True
-                args.append((inst, FIELD_IDS[name], out.ctypes.data, out.nbytes))
-            assert host is None or host == on_host, "mixed host and device buffers"
-            host = on_host
-        if args:
-            ib_pf_read_fields_batch(self.ctx, args, host)
+        if items:
+            FieldBatch(self, list(items), write=False).run()
 
     def table(self, table_id: int, instance: int = 0) -> np.ndarray:
         n = ib_pf_read_table(self.ctx, instance, table_id, None, 0)
@@ -364,6 +352,34 @@ class Solver:
         for name in ("C_lo", "C_old_lo"):
             if name in d:
                 self.write(name, d[name], instance)
+
+
+class FieldBatch:
+    """Prepared arguments of one batched field read or write (see Solver.prepare_writes)."""
+
+    def __init__(self, solver: Solver, items, write: bool):
+        self.solver, self.write = solver, write
+        self._keep = []
+        args, host = [], None
+        for name, arr, inst in items:
+            if hasattr(arr, "data_ptr"):
+                assert arr.is_contiguous()
+                on_host = not arr.is_cuda
+                ptr, nb = arr.data_ptr(), arr.numel() * arr.element_size()
+            else:
+                assert arr.flags["C_CONTIGUOUS"] and arr.dtype == solver.dtype
+                on_host, ptr, nb = True, arr.ctypes.data, arr.nbytes
+            self._keep.append(arr)
+            assert host is None or host == on_host, "mixed host and device buffers"
+            host = on_host
+            args.append((inst, FIELD_IDS[name], ptr, nb))
+        self.on_host = bool(host)
+        self.n, self.inst, self.fids, self.ptrs, self.nb = _batch_args(args)
+
+    def run(self):
+        fn = lib().ib_pf_write_fields_batch if self.write else lib().ib_pf_read_fields_batch
+        _check(fn(self.solver.ctx, self.n, self.inst, self.fids, self.ptrs, self.nb,
+                  int(self.on_host)), self.solver.ctx)
 
 
 def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:

@@ -264,6 +264,15 @@ def test_batched_field_io_matches_single_calls(ibpf):
     b.read_many(outs)
     for n, arr, k in outs:
         assert np.array_equal(arr, a.read(n, k)), (k, n)
+    # a prepared batch runs again with the buffers' current contents
+    src = [(n, np.array(states[k][n], np.float32), k) for k in range(2) for n in ibpf.STATE_FIELDS]
+    prep = b.prepare_writes(src)
+    for rep in range(2):
+        for n, arr, k in src:
+            arr[...] = np.asarray(states[k][n], np.float32) * (1.0 + rep)
+        prep.run()
+        for n, arr, k in src:
+            assert np.array_equal(b.read(n, k), arr), (rep, k, n)
     before = b.read("C", 0)
     bad = [("C", np.zeros((64, 128), np.float32), 0), ("u", np.zeros((3, 3), np.float32), 1)]
     with pytest.raises(ibpf.IbPfError) as ei:
@@ -272,3 +281,79 @@ def test_batched_field_io_matches_single_calls(ibpf):
     assert np.array_equal(b.read("C", 0), before)
     a.close()
     b.close()
+
+
+def test_write_sources_and_ordering(ibpf):
+    # pinned, pageable, unaligned pinned and device sources give the same state; the wall
+    # rows of v are zero whatever the source holds; within a batch a later write of the same
+    # destination wins, and writing C clears its low part unless C_lo is written after it
+    torch = pytest.importorskip("torch")
+    case = cases.flat_wall_128x64()
+    st = cases.random_state(case, seed=31)
+    s = ibpf.solver_from_cases([case], ibpf.FP32)
+    s.precompute_weights()
+    want = {n: np.asarray(st[n], np.float32).copy() for n in ibpf.STATE_FIELDS}
+    for n in ("v", "v_old", "Hv"):
+        want[n][0] = 0.0
+        want[n][-1] = 0.0
+    srcs = {n: np.asarray(st[n], np.float32).copy() for n in ibpf.STATE_FIELDS}
+    for n in ("v", "v_old", "Hv"):
+        srcs[n][0] = 7.0
+        srcs[n][-1] = -3.0
+
+    def pinned(a, offset=0):
+        t = torch.empty(a.size + offset, dtype=torch.float32).pin_memory()
+        t = t[offset:].view(*a.shape)
+        t.copy_(torch.from_numpy(a))
+        return t
+
+    def check():
+        for n in ibpf.STATE_FIELDS:
+            assert np.array_equal(s.read(n), want[n]), n
+        assert not s.read("C_lo").any() and not s.read("C_old_lo").any()
+
+    for kind in ("pinned", "pageable", "unaligned", "device", "mixed"):
+        s.write("C_lo", np.full(case.ny * case.nx, 1e-9, np.float32).reshape(case.ny, case.nx))
+        if kind == "pinned":
+            items = [(n, pinned(a), 0) for n, a in srcs.items()]
+        elif kind == "pageable":
+            items = [(n, a, 0) for n, a in srcs.items()]
+        elif kind == "unaligned":
+            items = [(n, pinned(a, 1), 0) for n, a in srcs.items()]
+            assert all(t.data_ptr() % 16 for _, t, _ in items)
+        elif kind == "device":
+            items = [(n, torch.from_numpy(a).cuda(), 0) for n, a in srcs.items()]
+            torch.cuda.synchronize()
+        else:
+            items = [(n, pinned(a) if k % 2 else a, 0) for k, (n, a) in enumerate(srcs.items())]
+        s.write_many(items)
+        check()
+    # last write wins; C then C_lo keeps the written low part, C_lo then C clears it
+    lo = np.full((case.ny, case.nx), 2.5e-8, np.float32)
+    s.write_many([("C", pinned(srcs["C"] * 0.5), 0), ("C", pinned(srcs["C"]), 0), ("C_lo", pinned(lo), 0)])
+    assert np.array_equal(s.read("C"), want["C"]) and np.array_equal(s.read("C_lo"), lo)
+    s.write_many([("C_lo", lo, 0), ("C", srcs["C"], 0)])
+    assert np.array_equal(s.read("C"), want["C"]) and not s.read("C_lo").any()
+    s.write_many([("C_lo", lo, 0), ("C", pinned(srcs["C"]), 0)])
+    assert not s.read("C_lo").any()
+    s.write_many([("C", pinned(srcs["C"]), 0), ("C_lo", lo, 0)])
+    assert np.array_equal(s.read("C_lo"), lo)
+    # batched reads into pinned, unaligned pinned, pageable and device buffers
+    s.write_many([(n, a, 0) for n, a in srcs.items()])
+    names = list(ibpf.STATE_FIELDS)
+    for kind in ("pinned", "unaligned", "pageable", "mixed", "device"):
+        outs = []
+        for k, n in enumerate(names):
+            z = np.zeros_like(want[n])
+            if kind == "pageable" or (kind == "mixed" and k % 2):
+                outs.append((n, z, 0))
+            elif kind == "device":
+                outs.append((n, torch.zeros(z.shape, dtype=torch.float32, device="cuda"), 0))
+            else:
+                outs.append((n, pinned(z, 1 if kind == "unaligned" else 0), 0))
+        s.read_many(outs)
+        torch.cuda.synchronize()
+        for n, o, _ in outs:
+            got = o.cpu().numpy() if hasattr(o, "data_ptr") else o
+            assert np.array_equal(got, want[n]), (kind, n)
+    s.close()
