@@ -96,4 +96,43 @@ __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__
   __syncthreads();
 }
 
+// ---- runs of four x-consecutive FP32 cells per thread (one 16-byte word per field and row)
+struct V4 {
+  float e[4];
+};
+__device__ __forceinline__ V4 ld4(const float* __restrict__ f, size_t q) {
+  const float4 v = *reinterpret_cast<const float4*>(f + q);
+  return V4{{v.x, v.y, v.z, v.w}};
+}
+__device__ __forceinline__ void st4(float* __restrict__ f, size_t q, const V4& v) {
+  *reinterpret_cast<float4*>(f + q) = make_float4(v.e[0], v.e[1], v.e[2], v.e[3]);
+}
+template <typename F>
+__device__ __forceinline__ V4 map4(F f) {
+  V4 r;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) r.e[e] = f(e);
+  return r;
+}
+
+// x neighbours of a run: l = value left of cell 0, r = value right of cell 3.  The runs of
+// one row segment sit on W consecutive lanes (lane gl of the group); the neighbours come
+// from the adjacent lanes by shuffles, except at the ends of the group or of the row
+// (periodic wrap), where get(linear index) supplies them.  Every lane of the warp must call.
+struct X2 {
+  float l, r;
+};
+template <int W, typename G>
+__device__ __forceinline__ X2 xnb(const V4& v, int gl, bool row_start, bool row_end, size_t xl,
+                                  size_t xr, G get) {
+  X2 x;
+  x.l = __shfl_up_sync(0xffffffffu, v.e[3], 1, W);
+  x.r = __shfl_down_sync(0xffffffffu, v.e[0], 1, W);
+  if (gl == 0 || row_start) x.l = get(xl);
+  if (gl == W - 1 || row_end) x.r = get(xr);
+  return x;
+}
+__device__ __forceinline__ float left(const V4& v, const X2& x, int e) { return e == 0 ? x.l : v.e[e - 1]; }
+__device__ __forceinline__ float right(const V4& v, const X2& x, int e) { return e == 3 ? x.r : v.e[e + 1]; }
+
 }  // namespace ibpf

@@ -702,6 +702,201 @@ __global__ void IBPF_CELL_BOUNDS kb_correct(const InstDev<T>* __restrict__ I, co
   }
 }
 
+// ------------------------------------------- FP32 form: four cells per thread
+// The same 32 x 32 cell tiles and block tables, each thread owning a run of four
+// x1-consecutive cells of one row (8 runs x 32 rows; a warp holds 4 row segments of 8 runs).
+// One 16-byte load per field and row; the x1 neighbours of a run come from the adjacent
+// lanes by shuffles.  The arithmetic of each cell is that of the *_cell functions above, term
+// for term.  Threads of a partial tile (nx or ny below 32) take part in the shuffles with
+// loads of cell 0 and store nothing.
+struct Run2 {
+  size_t q, s, n, xl, xr;   // first cell of the run, the runs below / above (mirror), x wrap
+  int i0, j, gl;
+  bool act;
+};
+__device__ __forceinline__ Run2 run2(const InstDev<float>& d, int lb) {
+  Run2 r;
+  const int tid = threadIdx.y * kTileX + threadIdx.x;
+  r.gl = tid & 7;
+  const int i0 = (lb % d.gx) * kTileX + 4 * r.gl, j = (lb / d.gx) * kTileH + (tid >> 3);
+  const int nx = d.nx, ny = d.ny;
+  r.act = i0 < nx && j < ny;
+  r.i0 = r.act ? i0 : 0;
+  r.j = r.act ? j : 0;
+  r.q = (size_t)r.j * nx + r.i0;
+  r.s = (size_t)(r.j > 0 ? r.j - 1 : 0) * nx + r.i0;
+  r.n = (size_t)(r.j < ny - 1 ? r.j + 1 : ny - 1) * nx + r.i0;
+  r.xl = r.i0 == 0 ? r.q + (nx - 1) : r.q - 1;
+  r.xr = r.i0 + 4 == nx ? r.q + 4 - nx : r.q + 4;
+  return r;
+}
+template <typename G>
+__device__ __forceinline__ X2 xnb2(const V4& v, const Run2& r, int nx, G get) {
+  return xnb<8>(v, r.gl, r.i0 == 0, r.i0 + 4 == nx, r.xl, r.xr, get);
+}
+
+// 5-point Laplacian of cell e of a run (xp + xm first, as the *_cell functions)
+__device__ __forceinline__ float lap5q(const StepArgs<float>& a, const V4& c, const X2& x,
+                                       const V4& n, const V4& s, int e) {
+  return (((right(c, x, e) + left(c, x, e)) + (n.e[e] + s.e[e])) - 4.0f * c.e[e]) * a.inv_h2;
+}
+
+#define IBPF_QUAD_PROLOGUE                 \
+  const int b_ = blockIdx.x;               \
+  if (b_ >= nblk) return;                  \
+  const int2 w_ = blk[b_];                 \
+  const InstDev<float>& d = I[w_.x];       \
+  const StepArgs<float>& a = d.a;          \
+  const Run2 r = run2(d, w_.y);
+
+__global__ void IBPF_CELL_BOUNDS kq_ch_h(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                         int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float* C = d.C[cur];
+  const float* Co = d.C[1 - cur];
+  const float third = float(1.0 / 3.0);
+  auto B4 = [&](size_t q) {
+    const V4 c = ld4(C, q), o = ld4(Co, q);
+    return map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
+  };
+  const V4 c = ld4(C, r.q), o = ld4(Co, r.q);
+  const V4 b = map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
+  const V4 bn = B4(r.n), bs = B4(r.s);
+  const X2 bx = xnb2(b, r, d.nx, [&](size_t q) { return C[q] + (C[q] - Co[q]) * third; });
+  const V4 out = map4([&](int e) {
+    const float dd = c.e[e] - o.e[e];
+    const float ct = c.e[e] + dd;
+    return ((ct * ct * ct - ct) - a.S * (2.0f * third * dd)) * a.inv_eta2 - lap5q(a, b, bx, bn, bs, e);
+  });
+  if (r.act) st4(d.phi, r.q, out);
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_ch_rhs(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                           int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float *C = d.C[cur], *Co = d.C[1 - cur], *u = d.U[cur], *uo = d.U[1 - cur];
+  const float *v = d.V[cur], *vo = d.V[1 - cur], *hf = d.phi;
+  const int nx = d.nx, ny = d.ny;
+  auto two = [&](const float* f, const float* fo, size_t q) {
+    const V4 x = ld4(f, q), y = ld4(fo, q);
+    return map4([&](int e) { return 2.0f * x.e[e] - y.e[e]; });
+  };
+  const V4 c0 = two(C, Co, r.q), cn = two(C, Co, r.n), cs = two(C, Co, r.s);
+  const V4 ut = two(u, uo, r.q), vt = two(v, vo, r.q), vtn = two(v, vo, r.q + nx);
+  const V4 h = ld4(hf, r.q), hn = ld4(hf, r.n), hs = ld4(hf, r.s);
+  const X2 cx = xnb2(c0, r, nx, [&](size_t q) { return 2.0f * C[q] - Co[q]; });
+  const X2 ux = xnb2(ut, r, nx, [&](size_t q) { return 2.0f * u[q] - uo[q]; });
+  const X2 hx = xnb2(h, r, nx, [&](size_t q) { return hf[q]; });
+  const V4 out = map4([&](int e) {
+    const float cc = c0.e[e];
+    const float fx_w = ut.e[e] * (0.5f * (left(c0, cx, e) + cc));
+    const float fx_e = right(ut, ux, e) * (0.5f * (cc + right(c0, cx, e)));
+    float fy_s = 0.0f, fy_n = 0.0f;
+    if (r.j > 0) fy_s = vt.e[e] * (0.5f * (cs.e[e] + cc));
+    if (r.j < ny - 1) fy_n = vtn.e[e] * (0.5f * (cc + cn.e[e]));
+    const float div = (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
+    return lap5q(a, h, hx, hn, hs, e) - a.pe_eta2 * div;
+  });
+  if (r.act) st4(d.Q, r.q, out);
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_chem_pot(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                             int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float* C = d.C[1 - cur];
+  const V4 c = ld4(C, r.q), cn = ld4(C, r.n), cs = ld4(C, r.s);
+  const X2 cx = xnb2(c, r, d.nx, [&](size_t q) { return C[q]; });
+  const V4 out = map4([&](int e) {
+    const float c0 = c.e[e];
+    return (c0 * c0 * c0 - c0) - a.eta2 * lap5q(a, c, cx, cn, cs, e);
+  });
+  if (r.act) st4(d.phi, r.q, out);
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_poisson_rhs(const InstDev<float>* __restrict__ I,
+                                                const int2* __restrict__ blk, int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float *C = d.C[1 - cur], *P = d.P[cur], *Po = d.P[1 - cur];
+  const float *uss = d.U[1 - cur], *vss = d.V[1 - cur];
+  const int nx = d.nx, ny = d.ny;
+  auto rho = [&](float cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  auto ph4 = [&](size_t q) {
+    const V4 p = ld4(P, q), po = ld4(Po, q);
+    return map4([&](int e) { return 2.0f * p.e[e] - po.e[e]; });
+  };
+  const V4 p0 = ph4(r.q), pn = ph4(r.n), ps = ph4(r.s);
+  const V4 c0 = ld4(C, r.q), cn = ld4(C, r.n), cs = ld4(C, r.s);
+  const V4 us = ld4(uss, r.q), vs = ld4(vss, r.q), vsn = ld4(vss, r.q + nx);
+  const X2 px = xnb2(p0, r, nx, [&](size_t q) { return 2.0f * P[q] - Po[q]; });
+  const X2 cx = xnb2(c0, r, nx, [&](size_t q) { return C[q]; });
+  const X2 ux = xnb2(us, r, nx, [&](size_t q) { return uss[q]; });
+  V4 rhs;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float pc = p0.e[e], cc = c0.e[e];
+    const float gx_w = (a.rho0 / rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
+    const float gx_e = (a.rho0 / rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
+    float gy_s = 0.0f, gy_n = 0.0f;
+    if (r.j > 0) gy_s = (a.rho0 / rho(0.5f * (cs.e[e] + cc))) * ((pc - ps.e[e]) * a.inv_h);
+    if (r.j < ny - 1) gy_n = (a.rho0 / rho(0.5f * (cc + cn.e[e]))) * ((pn.e[e] - pc) * a.inv_h);
+    const float div_g = (gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h;
+    const float div_u = (right(us, ux, e) - us.e[e]) * a.inv_h + (vsn.e[e] - vs.e[e]) * a.inv_h;
+    rhs.e[e] = (a.rho0 * a.inv_dt) * div_u - div_g;
+  }
+  if (r.act) {
+    st4(d.rhs, r.q, rhs);
+    st4(d.phat, r.q, p0);
+  }
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_correct(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                            int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float *C = d.C[1 - cur], *dP = d.dp, *phat = d.phat;
+  float *uss = d.U[1 - cur], *vss = d.V[1 - cur];
+  auto rho = [&](float cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const V4 c0 = ld4(C, r.q), cs = ld4(C, r.s);
+  const V4 ph = ld4(phat, r.q), phs = ld4(phat, r.s);
+  const V4 dp = ld4(dP, r.q), dps = ld4(dP, r.s);
+  const V4 us = ld4(uss, r.q), vs = ld4(vss, r.q);
+  const X2 cx = xnb2(c0, r, d.nx, [&](size_t q) { return C[q]; });
+  const X2 phx = xnb2(ph, r, d.nx, [&](size_t q) { return phat[q]; });
+  const X2 dpx = xnb2(dp, r, d.nx, [&](size_t q) { return dP[q]; });
+  const V4 lo = d.Clo[1 - cur] ? ld4(d.Clo[1 - cur], r.q) : V4{{0.0f, 0.0f, 0.0f, 0.0f}};
+  int bad = 0;
+  V4 un, vn;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float cc = c0.e[e];
+    {
+      const float rho_f = rho(0.5f * (left(c0, cx, e) + cc));
+      un.e[e] = us.e[e] - a.dt * (((ph.e[e] - left(ph, phx, e)) * a.inv_h) / rho_f +
+                                  a.inv_rho0 * ((dp.e[e] - left(dp, dpx, e)) * a.inv_h));
+      bad |= !isfinite(un.e[e]);
+    }
+    if (r.j >= 1) {
+      const float rho_f = rho(0.5f * (cs.e[e] + cc));
+      vn.e[e] = vs.e[e] - a.dt * (((ph.e[e] - phs.e[e]) * a.inv_h) / rho_f +
+                                  a.inv_rho0 * ((dp.e[e] - dps.e[e]) * a.inv_h));
+      bad |= !isfinite(vn.e[e]);
+    }
+    bad |= !isfinite(cc);
+  }
+  float s_hi = 0.0f, s_lo = 0.0f;
+  if (r.act) {
+    st4(uss, r.q, un);
+    if (r.j >= 1) st4(vss, r.q, vn);
+    if (bad) atomicOr(d.status, 1);
+    s_hi = c0.e[0];
+    s_lo = lo.e[0];
+#pragma unroll
+    for (int e = 1; e < 4; ++e) pair_add(s_hi, s_lo, c0.e[e], lo.e[e]);
+  }
+  const int ntiles = d.gx * ((d.ny + kTileH - 1) / kTileH);
+  tile_mass<float, kTileX * kTileY>(s_hi, s_lo, w_.y, ntiles, d.partial, d.ticket, d.mass);
+}
+#undef IBPF_QUAD_PROLOGUE
+
 template <typename T>
 int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, Recorder* rec) {
   const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
@@ -716,9 +911,11 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     if (rec) rec->mark(n, s);
   };
   // a1 + a2: CH right-hand side, then the solve; C^{n+1} lands in slot 1 - cur
-  kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  if constexpr (sizeof(T) == 4) kq_ch_h<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  else kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("ch_h");
-  kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  if constexpr (sizeof(T) == 4) kq_ch_rhs<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  else kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("ch_rhs");
   launches += spectral_solve_batch<T>(plan, 0, cur, s, rec);
   // a3: contact-angle ghost fill
@@ -727,7 +924,8 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     mark("fill_C");
   }
   // a4: chemical potential and its ghost fill
-  kb_chem_pot<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  if constexpr (sizeof(T) == 4) kq_chem_pot<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  else kb_chem_pot<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("chem_pot");
   if (ng > 0) {
     kb_fill_phi<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng);
@@ -748,11 +946,13 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     mark("face_scatter");
   }
   // a7: Poisson right-hand side and solve, P^{n+1} into slot 1 - cur
-  kb_poisson_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  if constexpr (sizeof(T) == 4) kq_poisson_rhs<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  else kb_poisson_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("poisson_rhs");
   launches += spectral_solve_batch<T>(plan, 1, cur, s, rec);
   // a8: correction, status, mass
-  kb_correct<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  if constexpr (sizeof(T) == 4) kq_correct<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+  else kb_correct<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("correct");
   (void)c;
   return launches;

@@ -114,132 +114,193 @@ __global__ void k3_fill_phi(S3<T> a) {
   a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
 }
 
-constexpr int kT3 = 256;   // threads of the one-thread-per-cell kernels
+// --------------------------------------- four-cells-per-thread kernels (FP32 form)
+// Thread t owns the x-run of cells 4t .. 4t+3 (one 16-byte word per field and row); the
+// y and z neighbours are the words one row or one plane away, the x neighbours of the run
+// come from the adjacent lanes by shuffles (or a load at a row end or a warp end).  The
+// arithmetic of each cell is that of the z-marching kernels below (the FP64 form), term for
+// term.  For the FP32 form, which is memory-latency bound, these measured faster on GB300
+// than one thread per cell (by 1.5-2.2x) and than the z-marching windows.
+constexpr int kTQ = 128;   // threads per block: 512 cells, the smallest grid has 512 cells
 
-// 7-point Laplacian of a cell field (f of a linear index) with mirror planes in z
-template <typename T, typename F>
-__device__ __forceinline__ T lap7(const S3<T>& a, F f, const Nbr& n) {
-  const T c0 = f(n.c);
-  return ((((f(n.xp) + f(n.xm)) + (f(n.yp) + f(n.ym))) + (f(n.zp) + f(n.zm))) - T(6) * c0) *
-         a.inv_h2;
+// the run of a thread: first cell q (i0 = q mod nx), its row / plane offsets for the y and z
+// neighbours (periodic in y; the run itself at the z walls), and the linear indices of the
+// left neighbour of cell 0 and the right neighbour of cell 3 (periodic in x)
+struct Run {
+  size_t q, ym, yp, zm, zp, xl, xr;
+  int i0, j, k, lane;
+};
+__device__ __forceinline__ Run run4(const S3<float>& a) {
+  Run r;
+  r.q = ((size_t)blockIdx.x * kTQ + threadIdx.x) * 4;
+  cell_ijk(a, r.q, r.i0, r.j, r.k);
+  const size_t nx = (size_t)a.nx, nxy = nx * a.ny;
+  r.lane = threadIdx.x & 31;
+  r.xl = r.i0 == 0 ? r.q + (nx - 1) : r.q - 1;
+  r.xr = r.i0 + 4 == a.nx ? r.q + 4 - nx : r.q + 4;
+  r.yp = r.j == a.ny - 1 ? r.q - (nxy - nx) : r.q + nx;
+  r.ym = r.j == 0 ? r.q + (nxy - nx) : r.q - nx;
+  r.zp = r.k == a.nz - 1 ? r.q : r.q + nxy;
+  r.zm = r.k == 0 ? r.q : r.q - nxy;
+  return r;
 }
 
-// ----------------------------------------------- one-thread-per-cell kernels (FP32 form)
-// The FP32 form is memory-latency bound; these kernels, one thread per cell with its
-// neighbours read through L1, measured faster for it than the z-marching ones below
-// (which the FP64 form, bound by the FP64 pipe, uses).  Same arithmetic in both.
-
-// ---------------------------------------------------------------- a1: CH right-hand side
-// h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_ch_h_c(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  const T third = T(1.0 / 3.0);
-  auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
-  const T lapb = lap7(a, B, nbr(a, c, i, j, k));
-  const T d = a.C[c] - a.Co[c];
-  const T ct = a.C[c] + d;
-  a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+template <typename G>
+__device__ __forceinline__ X2 xnb(const V4& v, const Run& d, int nx, G g) {
+  return xnb<32>(v, d.lane, d.i0 == 0, d.i0 + 4 == nx, d.xl, d.xr, g);
 }
 
-// R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
+// 7-point Laplacian of cell e of the run (xm + xp first, as lap7)
+__device__ __forceinline__ float lap7q(const S3<float>& a, const V4& c, const X2& x, const V4& yp,
+                                       const V4& ym, const V4& zp, const V4& zm, int e) {
+  return ((((right(c, x, e) + left(c, x, e)) + (yp.e[e] + ym.e[e])) + (zp.e[e] + zm.e[e])) -
+          6.0f * c.e[e]) * a.inv_h2;
+}
+
+// a1: h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
+__global__ void __launch_bounds__(kTQ) k3_ch_h_q(S3<float> a) {
+  const Run d = run4(a);
+  const float third = float(1.0 / 3.0);
+  auto Bq = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
+  auto B4 = [&](size_t q) {
+    const V4 c = ld4(a.C, q), o = ld4(a.Co, q);
+    return map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
+  };
+  const V4 c = ld4(a.C, d.q), o = ld4(a.Co, d.q);
+  const V4 b = map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
+  const V4 byp = B4(d.yp), bym = B4(d.ym), bzp = B4(d.zp), bzm = B4(d.zm);
+  const X2 bx = xnb(b, d, a.nx, Bq);
+  st4(a.phi, d.q, map4([&](int e) {
+        const float lapb = lap7q(a, b, bx, byp, bym, bzp, bzm, e);
+        const float dd = c.e[e] - o.e[e];
+        const float ct = c.e[e] + dd;
+        return ((ct * ct * ct - ct) - a.S * (2.0f * third * dd)) * a.inv_eta2 - lapb;
+      }));
+}
+
+// a1: R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
 // through the z walls
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_ch_rhs_c(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
-  auto ut = [&](size_t q) { return T(2) * a.U[q] - a.Uo[q]; };
-  auto vt = [&](size_t q) { return T(2) * a.V[q] - a.Vo[q]; };
-  auto wt = [&](size_t q) { return T(2) * a.W[q] - a.Wo[q]; };
+__global__ void __launch_bounds__(kTQ) k3_ch_rhs_q(S3<float> a) {
+  const Run d = run4(a);
   const size_t nxy = (size_t)a.nx * a.ny;
-  const T c0 = ct(c);
-  const Nbr n = nbr(a, c, i, j, k);
-  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
-  const T fx_w = ut(c) * (T(0.5) * (ct(xm) + c0));
-  const T fx_e = ut(xp) * (T(0.5) * (c0 + ct(xp)));
-  const T fy_s = vt(c) * (T(0.5) * (ct(ym) + c0));
-  const T fy_n = vt(yp) * (T(0.5) * (c0 + ct(yp)));
-  const T fz_b = k > 0 ? wt(c) * (T(0.5) * (ct(c - nxy) + c0)) : T(0);
-  const T fz_t = k < a.nz - 1 ? wt(c + nxy) * (T(0.5) * (c0 + ct(c + nxy))) : T(0);
-  const T div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
-  auto hf = [&](size_t q) { return a.phi[q]; };
-  a.Q[c] = lap7(a, hf, n) - a.pe_eta2 * div;
+  auto two = [&](const float* f, const float* fo, size_t q) {
+    const V4 x = ld4(f, q), y = ld4(fo, q);
+    return map4([&](int e) { return 2.0f * x.e[e] - y.e[e]; });
+  };
+  auto ctq = [&](size_t q) { return 2.0f * a.C[q] - a.Co[q]; };
+  auto utq = [&](size_t q) { return 2.0f * a.U[q] - a.Uo[q]; };
+  const V4 c0 = two(a.C, a.Co, d.q), cyp = two(a.C, a.Co, d.yp), cym = two(a.C, a.Co, d.ym);
+  const V4 czp = two(a.C, a.Co, d.zp), czm = two(a.C, a.Co, d.zm);
+  const V4 ut = two(a.U, a.Uo, d.q), vt = two(a.V, a.Vo, d.q), vtn = two(a.V, a.Vo, d.yp);
+  const V4 wt = two(a.W, a.Wo, d.q), wtt = two(a.W, a.Wo, d.q + nxy);
+  const V4 h = ld4(a.phi, d.q), hyp = ld4(a.phi, d.yp), hym = ld4(a.phi, d.ym);
+  const V4 hzp = ld4(a.phi, d.zp), hzm = ld4(a.phi, d.zm);
+  const X2 cx = xnb(c0, d, a.nx, ctq), ux = xnb(ut, d, a.nx, utq);
+  const X2 hx = xnb(h, d, a.nx, [&](size_t q) { return a.phi[q]; });
+  st4(a.Q, d.q, map4([&](int e) {
+        const float cc = c0.e[e];
+        const float fx_w = ut.e[e] * (0.5f * (left(c0, cx, e) + cc));
+        const float fx_e = right(ut, ux, e) * (0.5f * (cc + right(c0, cx, e)));
+        const float fy_s = vt.e[e] * (0.5f * (cym.e[e] + cc));
+        const float fy_n = vtn.e[e] * (0.5f * (cc + cyp.e[e]));
+        const float fz_b = d.k > 0 ? wt.e[e] * (0.5f * (czm.e[e] + cc)) : 0.0f;
+        const float fz_t = d.k < a.nz - 1 ? wtt.e[e] * (0.5f * (cc + czp.e[e])) : 0.0f;
+        const float div = ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+        return lap7q(a, h, hx, hyp, hym, hzp, hzm, e) - a.pe_eta2 * div;
+      }));
 }
 
-// phi = psi'(C) - Cn^2 lap C on every cell
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_chem_pot_c(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  auto cf = [&](size_t q) { return a.C1[q]; };
-  const T c0 = a.C1[c];
-  a.phi[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7(a, cf, nbr(a, c, i, j, k));
+// a4: phi = psi'(C) - Cn^2 lap C on every cell
+__global__ void __launch_bounds__(kTQ) k3_chem_pot_q(S3<float> a) {
+  const Run d = run4(a);
+  const V4 c = ld4(a.C1, d.q);
+  const V4 cyp = ld4(a.C1, d.yp), cym = ld4(a.C1, d.ym), czp = ld4(a.C1, d.zp), czm = ld4(a.C1, d.zm);
+  const X2 cx = xnb(c, d, a.nx, [&](size_t q) { return a.C1[q]; });
+  st4(a.phi, d.q, map4([&](int e) {
+        const float c0 = c.e[e];
+        return (c0 * c0 * c0 - c0) - a.eta2 * lap7q(a, c, cx, cyp, cym, czp, czm, e);
+      }));
 }
 
-// ------------------------------------------------------------------ a7: Poisson RHS (3D)
-// lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_poisson_rhs_c(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
+// a7: lap dP = (rho0/dt) div u** - div[(rho0/rho_f) grad P^], dP = P^{n+1} - P^; stores P^
+__global__ void __launch_bounds__(kTQ) k3_poisson_rhs_q(S3<float> a) {
+  const Run d = run4(a);
   const size_t nxy = (size_t)a.nx * a.ny;
-  auto ph = [&](size_t q) { return T(2) * a.P[q] - a.Po[q]; };
-  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  const T* C = a.C1;
-  const T p0 = ph(c);
-  const Nbr n = nbr(a, c, i, j, k);
-  const size_t xp = n.xp, xm = n.xm, yp = n.yp, ym = n.ym;
-  const T gx_w = (a.rho0 / rho(T(0.5) * (C[xm] + C[c]))) * ((p0 - ph(xm)) * a.inv_h);
-  const T gx_e = (a.rho0 / rho(T(0.5) * (C[c] + C[xp]))) * ((ph(xp) - p0) * a.inv_h);
-  const T gy_s = (a.rho0 / rho(T(0.5) * (C[ym] + C[c]))) * ((p0 - ph(ym)) * a.inv_h);
-  const T gy_n = (a.rho0 / rho(T(0.5) * (C[c] + C[yp]))) * ((ph(yp) - p0) * a.inv_h);
-  T gz_b = T(0), gz_t = T(0);
-  if (k > 0) gz_b = (a.rho0 / rho(T(0.5) * (C[c - nxy] + C[c]))) * ((p0 - ph(c - nxy)) * a.inv_h);
-  if (k < a.nz - 1) gz_t = (a.rho0 / rho(T(0.5) * (C[c] + C[c + nxy]))) * ((ph(c + nxy) - p0) * a.inv_h);
-  const T div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
-  const T div_u = ((a.Us[xp] - a.Us[c]) * a.inv_h + (a.Vs[yp] - a.Vs[c]) * a.inv_h) +
-                  (a.Ws[c + nxy] - a.Ws[c]) * a.inv_h;
-  a.rhs[c] = (a.rho0 * a.inv_dt) * div_u - div_g;
-  a.phat[c] = p0;
+  auto rho = [&](float cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  auto ph4 = [&](size_t q) {
+    const V4 p = ld4(a.P, q), po = ld4(a.Po, q);
+    return map4([&](int e) { return 2.0f * p.e[e] - po.e[e]; });
+  };
+  const float* C = a.C1;
+  const V4 p0 = ph4(d.q), pyp = ph4(d.yp), pym = ph4(d.ym), pzp = ph4(d.zp), pzm = ph4(d.zm);
+  const V4 c0 = ld4(C, d.q), cyp = ld4(C, d.yp), cym = ld4(C, d.ym), czp = ld4(C, d.zp), czm = ld4(C, d.zm);
+  const V4 us = ld4(a.Us, d.q), vs = ld4(a.Vs, d.q), vsn = ld4(a.Vs, d.yp);
+  const V4 ws = ld4(a.Ws, d.q), wst = ld4(a.Ws, d.q + nxy);
+  const X2 px = xnb(p0, d, a.nx, [&](size_t q) { return 2.0f * a.P[q] - a.Po[q]; });
+  const X2 cx = xnb(c0, d, a.nx, [&](size_t q) { return C[q]; });
+  const X2 ux = xnb(us, d, a.nx, [&](size_t q) { return a.Us[q]; });
+  V4 rhs, phat;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float pc = p0.e[e], cc = c0.e[e];
+    const float gx_w = (a.rho0 / rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
+    const float gx_e = (a.rho0 / rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
+    const float gy_s = (a.rho0 / rho(0.5f * (cym.e[e] + cc))) * ((pc - pym.e[e]) * a.inv_h);
+    const float gy_n = (a.rho0 / rho(0.5f * (cc + cyp.e[e]))) * ((pyp.e[e] - pc) * a.inv_h);
+    float gz_b = 0.0f, gz_t = 0.0f;
+    if (d.k > 0) gz_b = (a.rho0 / rho(0.5f * (czm.e[e] + cc))) * ((pc - pzm.e[e]) * a.inv_h);
+    if (d.k < a.nz - 1) gz_t = (a.rho0 / rho(0.5f * (cc + czp.e[e]))) * ((pzp.e[e] - pc) * a.inv_h);
+    const float div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
+    const float div_u = ((right(us, ux, e) - us.e[e]) * a.inv_h + (vsn.e[e] - vs.e[e]) * a.inv_h) +
+                        (wst.e[e] - ws.e[e]) * a.inv_h;
+    rhs.e[e] = (a.rho0 * a.inv_dt) * div_u - div_g;
+    phat.e[e] = pc;
+  }
+  st4(a.rhs, d.q, rhs);
+  st4(a.phat, d.q, phat);
 }
 
-// ------------------------------------------------- a8: correction + status and mass (3D)
-// u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces 1..nz-1)
-template <typename T>
-__global__ void __launch_bounds__(kT3) k3_correct_c(S3<T> a) {
-  const size_t c = (size_t)blockIdx.x * kT3 + threadIdx.x;
-  int i, j, k;
-  cell_ijk(a, c, i, j, k);
-  const size_t nxy = (size_t)a.nx * a.ny;
-  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  const T* C = a.C1;
+// a8: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces
+// 1..nz-1); non-finite check; the tile's compensated sum of C for the FP64 mass
+__global__ void __launch_bounds__(kTQ) k3_correct_q(S3<float> a) {
+  const Run d = run4(a);
+  auto rho = [&](float cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  const float* C = a.C1;
+  const V4 c0 = ld4(C, d.q), cym = ld4(C, d.ym), czm = ld4(C, d.zm);
+  const V4 ph = ld4(a.phat, d.q), phym = ld4(a.phat, d.ym), phzm = ld4(a.phat, d.zm);
+  const V4 dp = ld4(a.dp, d.q), dpym = ld4(a.dp, d.ym), dpzm = ld4(a.dp, d.zm);
+  const V4 us = ld4(a.Us, d.q), vs = ld4(a.Vs, d.q);
+  const X2 cx = xnb(c0, d, a.nx, [&](size_t q) { return C[q]; });
+  const X2 phx = xnb(ph, d, a.nx, [&](size_t q) { return a.phat[q]; });
+  const X2 dpx = xnb(dp, d, a.nx, [&](size_t q) { return a.dp[q]; });
+  const bool top = d.k >= 1;
+  V4 ws = {{0.0f, 0.0f, 0.0f, 0.0f}};
+  if (top) ws = ld4(a.Ws, d.q);
   int bad = 0;
-  auto corr = [&](const T* vel, size_t nb) {
-    const T rho_f = rho(T(0.5) * (C[nb] + C[c]));
-    const T vn = vel[c] - a.dt * (((a.phat[c] - a.phat[nb]) * a.inv_h) / rho_f +
-                                  a.inv_rho0 * ((a.dp[c] - a.dp[nb]) * a.inv_h));
+  auto corr = [&](float vel, float cn, float cc, float phn, float phc, float dpn, float dpc) {
+    const float rho_f = rho(0.5f * (cn + cc));
+    const float vn = vel - a.dt * (((phc - phn) * a.inv_h) / rho_f + a.inv_rho0 * ((dpc - dpn) * a.inv_h));
     bad |= !isfinite(vn);
     return vn;
   };
-  const Nbr n = nbr(a, c, i, j, k);
-  const T un = corr(a.Us, n.xm);
-  const T vn = corr(a.Vs, n.ym);
-  T wn = T(0);
-  if (k >= 1) wn = corr(a.Ws, c - nxy);
-  bad |= !isfinite(C[c]);
-  a.Us[c] = un;
-  a.Vs[c] = vn;
-  if (k >= 1) a.Ws[c] = wn;
+  V4 un, vn, wn;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float cc = c0.e[e], pc = ph.e[e], dc = dp.e[e];
+    un.e[e] = corr(us.e[e], left(c0, cx, e), cc, left(ph, phx, e), pc, left(dp, dpx, e), dc);
+    vn.e[e] = corr(vs.e[e], cym.e[e], cc, phym.e[e], pc, dpym.e[e], dc);
+    wn.e[e] = top ? corr(ws.e[e], czm.e[e], cc, phzm.e[e], pc, dpzm.e[e], dc) : 0.0f;
+    bad |= !isfinite(cc);
+  }
+  st4(a.Us, d.q, un);
+  st4(a.Vs, d.q, vn);
+  if (top) st4(a.Ws, d.q, wn);
   if (bad) atomicOr(a.status, 1);
-  const T lo = a.C1lo ? a.C1lo[c] : T(0);
-  const size_t ntiles = (nxy * a.nz) / kT3;
-  tile_mass<T, kT3>(C[c], lo, (int)blockIdx.x, (int)ntiles, a.partial, a.ticket, a.mass);
+  const V4 lo = a.C1lo ? ld4(a.C1lo, d.q) : V4{{0.0f, 0.0f, 0.0f, 0.0f}};
+  float hi = c0.e[0], lsum = lo.e[0];
+#pragma unroll
+  for (int e = 1; e < 4; ++e) pair_add(hi, lsum, c0.e[e], lo.e[e]);
+  tile_mass<float, kTQ>(hi, lsum, (int)blockIdx.x, (int)gridDim.x, a.partial, a.ticket, a.mass);
 }
 
 // ------------------------------------------------- a5: AB2 predictor + penalisation (3D)
@@ -402,6 +463,186 @@ __global__ void __launch_bounds__(kPx * kPy) k3_predict(S3<T> a) {
     __syncthreads();
     load_phi(k + 1);
   }
+}
+
+// FP32 form of the predictor: the same blocks, arithmetic and stores, with the staging made
+// asynchronous.  Planes go through a ring of four shared-memory slots filled by cp.async
+// (no registers held in flight): while plane k is computed the copies of plane k+2 are
+// outstanding.  The ghost planes beyond the z walls are staged unsigned (C, u, v of the
+// mirrored plane, w and phi zero-filled) and the no-slip sign of u and v is applied on
+// reading.
+constexpr int kPr = 4;   // ring slots: planes k-1, k, k+1 in use, k+2 arriving
+
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* smem, const T* g, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(g), "n"((int)sizeof(T)),
+               "r"(valid ? (int)sizeof(T) : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
+  __shared__ T sC[kPr][kPhy][kPhx], sU[kPr][kPhy][kPhx], sV[kPr][kPhy][kPhx], sW[kPr][kPhy][kPhx];
+  __shared__ T sF[kPr][kPhy][kPhx];
+  constexpr int kSlots = kPhx * kPhy, kThreads = kPx * kPy;
+  constexpr int NS = (kSlots + kThreads - 1) / kThreads;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
+  const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
+  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int k0 = blockIdx.z * kz;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < a.nx && j < a.ny;
+  const size_t nxy = (size_t)a.nx * a.ny;
+  // this thread's staged slots and the in-plane offsets of their columns (periodic wrap)
+  unsigned off[NS];
+  int sidx[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int idx = tid + q * kThreads;
+    sidx[q] = idx < kSlots ? idx : -1;
+    const int r = idx / kPhx, cc = idx % kPhx;
+    const int gi = (i0 - 1 + cc + a.nx) & (a.nx - 1), gj = (j0 - 1 + r + a.ny) & (a.ny - 1);
+    off[q] = (unsigned)gj * (unsigned)a.nx + (unsigned)gi;
+  }
+  auto issue = [&](int kk) {   // plane kk (-1 .. nz+1) into slot kk mod 4
+    const int sl = (kk + kPr) & (kPr - 1);
+    const int km = kk < 0 ? 0 : (kk >= a.nz ? a.nz - 1 : kk);
+    const bool win = kk >= 0 && kk <= a.nz, fin = kk >= 0 && kk < a.nz;
+    const size_t base = (size_t)km * nxy, wbase = (size_t)(win ? kk : 0) * nxy;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      if (sidx[q] < 0) continue;
+      const int e = sl * kSlots + sidx[q];
+      cp_async_el(&sC[0][0][0] + e, a.C1 + base + off[q], true);
+      cp_async_el(&sU[0][0][0] + e, a.U + base + off[q], true);
+      cp_async_el(&sV[0][0][0] + e, a.V + base + off[q], true);
+      cp_async_el(&sW[0][0][0] + e, a.W + wbase + off[q], win);
+      cp_async_el(&sF[0][0][0] + e, a.phi + base + off[q], fin);
+    }
+    cp_async_commit();
+  };
+  int k = k0;
+  int s_m = 0, s_0 = 0, s_p = 0;
+  T g_m = T(1), g_p = T(1);   // no-slip sign of the staged u, v of planes k-1 and k+1
+  auto pl = [&](int kk) { return kk == k ? s_0 : (kk > k ? s_p : s_m); };
+  auto sg = [&](int kk) { return kk == k ? T(1) : (kk > k ? g_p : g_m); };
+  auto Cc = [&](int ii, int jj, int kk) { return sC[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Fc = [&](int ii, int jj, int kk) { return sF[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Ug = [&](int ii, int jj, int kk) { return sg(kk) * sU[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Vg = [&](int ii, int jj, int kk) { return sg(kk) * sV[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  auto Wf = [&](int ii, int jj, int kk) { return sW[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+  const T ih = a.inv_h;
+  issue(k0 - 1);
+  issue(k0);
+  issue(k0 + 1);
+  for (; k < k0 + kz; ++k) {
+    issue(k + 2);
+    const size_t c = (size_t)k * nxy + (size_t)j * a.nx + i;
+    // per-face operands of plane k, requested before the wait so their latency overlaps it
+    T hu = T(0), hv = T(0), hw = T(0), fu = T(0), fv = T(0), fw = T(0);
+    if (active) {
+      hu = a.Hu[c];
+      hv = a.Hv[c];
+      fu = a.au[c];
+      fv = a.av[c];
+      if (k >= 1) {
+        hw = a.Hw[c];
+        fw = a.aw[c];
+      }
+    }
+    cp_async_wait1();   // every plane but k+2 has arrived (this thread's copies)
+    __syncthreads();    // ... and every thread's
+    s_m = (k + kPr - 1) & (kPr - 1);
+    s_0 = k & (kPr - 1);
+    s_p = (k + 1) & (kPr - 1);
+    g_m = k - 1 < 0 ? T(-1) : T(1);
+    g_p = k + 1 >= a.nz ? T(-1) : T(1);
+    if (active) {
+      auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
+      auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+      auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
+      auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
+      auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
+      auto txy = [&](int ii, int jj, int kk) {
+        const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
+      };
+      auto txz = [&](int ii, int jj, int kk) {
+        const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
+      };
+      auto tyz = [&](int ii, int jj, int kk) {
+        const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
+        return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
+      };
+      auto uv = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
+      };
+      auto uw = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
+      };
+      auto vw = [&](int ii, int jj, int kk) {
+        return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
+      };
+      const T k_st = a.k_st;
+      T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
+      {
+        const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cL + cR));
+        const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
+                       (txz(i, j, k + 1) - txz(i, j, k)) * ih;
+        const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
+        const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
+        const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
+                       (uw(i, j, k + 1) - uw(i, j, k)) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
+        Hx = H;
+        ux = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
+      }
+      {
+        const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
+                       (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
+        const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
+        const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
+        const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
+                       (vw(i, j, k + 1) - vw(i, j, k)) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
+        Hy = H;
+        vy = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
+      }
+      if (k >= 1) {
+        const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
+                       (tzz(k) - tzz(k - 1)) * ih;
+        const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
+        const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
+        const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
+                       (wcA * wcA - wcB * wcB) * ih;
+        const T H = -conv + visc / (a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
+        Hz = H;
+        wz = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
+      }
+      a.Hu[c] = Hx;
+      a.Us[c] = fu * ux;
+      a.Hv[c] = Hy;
+      a.Vs[c] = fv * vy;
+      if (k >= 1) {
+        a.Hw[c] = Hz;
+        a.Ws[c] = fw * wz;
+      }
+    }
+    __syncthreads();   // the slot of plane k-1 takes plane k+3 next
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy outlives the block
 }
 
 // ------------------------------------------------------------- z-marching cell kernels
@@ -826,13 +1067,13 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
     const dim3 zb(kPx, kPy);
     const dim3 zg((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzc);
     const dim3 zgp((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzp);
-    // FP32: one thread per cell; FP64: z-marching (each the faster form on GB300)
-    const unsigned nb = (unsigned)(((size_t)in.nx * in.ny * in.nz) / kT3);
+    // FP32: four cells per thread; FP64: z-marching (each the faster form on GB300)
+    const unsigned nb = (unsigned)(((size_t)in.nx * in.ny * in.nz) / (4 * kTQ));
     constexpr bool percell = sizeof(T) == 4;
-    if constexpr (percell) k3_ch_h_c<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_ch_h_q<<<nb, kTQ, 0, s>>>(a);
     else k3_ch_h_z<T><<<zg, zb, 0, s>>>(a);
     mark("ch_h");
-    if constexpr (percell) k3_ch_rhs_c<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_ch_rhs_q<<<nb, kTQ, 0, s>>>(a);
     else k3_ch_rhs_z<T><<<zg, zb, 0, s>>>(a);
     mark("ch_rhs");
     launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
@@ -840,14 +1081,15 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_C");
     }
-    if constexpr (percell) k3_chem_pot_c<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_chem_pot_q<<<nb, kTQ, 0, s>>>(a);
     else k3_chem_pot_z<T><<<zg, zb, 0, s>>>(a);
     mark("chem_pot");
     if (ng > 0) {
       k3_fill_phi<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_phi");
     }
-    k3_predict<T><<<zgp, zb, 0, s>>>(a);
+    if constexpr (sizeof(T) == 4) k3_predict_a<T><<<zgp, zb, 0, s>>>(a);
+    else k3_predict<T><<<zgp, zb, 0, s>>>(a);
     mark("predict");
     if (ng > 0) {
       k3_fill_u<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
@@ -859,11 +1101,11 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       k3_face_scatter<T><<<(nf + 127) / 128, 128, 0, s>>>(a);
       mark("face_scatter");
     }
-    if constexpr (percell) k3_poisson_rhs_c<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_poisson_rhs_q<<<nb, kTQ, 0, s>>>(a);
     else k3_poisson_rhs_z<T><<<zg, zb, 0, s>>>(a);
     mark("poisson_rhs");
     launches += spectral3_solve(in, ctx.precision, 1, cur, s, rec);
-    if constexpr (percell) k3_correct_c<T><<<nb, kT3, 0, s>>>(a);
+    if constexpr (percell) k3_correct_q<<<nb, kTQ, 0, s>>>(a);
     else k3_correct_z<T><<<zg, zb, 0, s>>>(a);
     mark("correct");
   }
