@@ -96,6 +96,15 @@ __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__
   __syncthreads();
 }
 
+// Quotient by a density-type factor (rho_f, Re rho_f; both O(1) and positive).  FP32 form:
+// __fdividef, within 2 ulp, a fraction of the cost of the IEEE quotient; the FP32 error
+// budget is set by FP32 storage.  FP64: the IEEE quotient.
+template <typename T>
+__device__ __forceinline__ T qdiv(T a, T b) {
+  if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+  else return a / b;
+}
+
 // ---- runs of four x-consecutive FP32 cells per thread (one 16-byte word per field and row)
 struct V4 {
   float e[4];

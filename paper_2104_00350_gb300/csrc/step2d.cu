@@ -212,8 +212,8 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T ucR = T(0.5) * (Us(0, 0) + Us(1, 0));
     const T ucL = T(0.5) * (Us(-1, 0) + Us(0, 0));
     const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(0, 1) - uv(0, 0)) * a.inv_h;
-    const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * ((cR - cL) * a.inv_h) / rho_f;
+    const T H = -conv + qdiv(visc, a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * qdiv((cR - cL) * a.inv_h, rho_f);
     const T ustar = Us(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hu_old) + st);
     Hu[r + i] = H;
     uss[r + i] = au * ustar;
@@ -228,8 +228,8 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
     const T vcA = T(0.5) * (Vs(0, 0) + Vs(0, 1));
     const T vcB = T(0.5) * (Vs(0, -1) + Vs(0, 0));
     const T conv = (uv(1, 0) - uv(0, 0)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
-    const T H = -conv + visc / (a.Re * rho_f);
-    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * ((cA - cB) * a.inv_h) / rho_f;
+    const T H = -conv + qdiv(visc, a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * qdiv((cA - cB) * a.inv_h, rho_f);
     const T vstar = Vs(0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hv_old) + st);
     Hv[r + i] = H;
     vss[r + i] = av * vstar;
@@ -834,11 +834,11 @@ __global__ void IBPF_CELL_BOUNDS kq_poisson_rhs(const InstDev<float>* __restrict
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const float pc = p0.e[e], cc = c0.e[e];
-    const float gx_w = (a.rho0 / rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
-    const float gx_e = (a.rho0 / rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
+    const float gx_w = qdiv(a.rho0, rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
+    const float gx_e = qdiv(a.rho0, rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
     float gy_s = 0.0f, gy_n = 0.0f;
-    if (r.j > 0) gy_s = (a.rho0 / rho(0.5f * (cs.e[e] + cc))) * ((pc - ps.e[e]) * a.inv_h);
-    if (r.j < ny - 1) gy_n = (a.rho0 / rho(0.5f * (cc + cn.e[e]))) * ((pn.e[e] - pc) * a.inv_h);
+    if (r.j > 0) gy_s = qdiv(a.rho0, rho(0.5f * (cs.e[e] + cc))) * ((pc - ps.e[e]) * a.inv_h);
+    if (r.j < ny - 1) gy_n = qdiv(a.rho0, rho(0.5f * (cc + cn.e[e]))) * ((pn.e[e] - pc) * a.inv_h);
     const float div_g = (gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h;
     const float div_u = (right(us, ux, e) - us.e[e]) * a.inv_h + (vsn.e[e] - vs.e[e]) * a.inv_h;
     rhs.e[e] = (a.rho0 * a.inv_dt) * div_u - div_g;
@@ -870,13 +870,13 @@ __global__ void IBPF_CELL_BOUNDS kq_correct(const InstDev<float>* __restrict__ I
     const float cc = c0.e[e];
     {
       const float rho_f = rho(0.5f * (left(c0, cx, e) + cc));
-      un.e[e] = us.e[e] - a.dt * (((ph.e[e] - left(ph, phx, e)) * a.inv_h) / rho_f +
+      un.e[e] = us.e[e] - a.dt * (qdiv((ph.e[e] - left(ph, phx, e)) * a.inv_h, rho_f) +
                                   a.inv_rho0 * ((dp.e[e] - left(dp, dpx, e)) * a.inv_h));
       bad |= !isfinite(un.e[e]);
     }
     if (r.j >= 1) {
       const float rho_f = rho(0.5f * (cs.e[e] + cc));
-      vn.e[e] = vs.e[e] - a.dt * (((ph.e[e] - phs.e[e]) * a.inv_h) / rho_f +
+      vn.e[e] = vs.e[e] - a.dt * (qdiv((ph.e[e] - phs.e[e]) * a.inv_h, rho_f) +
                                   a.inv_rho0 * ((dp.e[e] - dps.e[e]) * a.inv_h));
       bad |= !isfinite(vn.e[e]);
     }

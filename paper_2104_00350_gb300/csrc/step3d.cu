@@ -243,13 +243,13 @@ __global__ void __launch_bounds__(kTQ) k3_poisson_rhs_q(S3<float> a) {
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const float pc = p0.e[e], cc = c0.e[e];
-    const float gx_w = (a.rho0 / rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
-    const float gx_e = (a.rho0 / rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
-    const float gy_s = (a.rho0 / rho(0.5f * (cym.e[e] + cc))) * ((pc - pym.e[e]) * a.inv_h);
-    const float gy_n = (a.rho0 / rho(0.5f * (cc + cyp.e[e]))) * ((pyp.e[e] - pc) * a.inv_h);
+    const float gx_w = qdiv(a.rho0, rho(0.5f * (left(c0, cx, e) + cc))) * ((pc - left(p0, px, e)) * a.inv_h);
+    const float gx_e = qdiv(a.rho0, rho(0.5f * (cc + right(c0, cx, e)))) * ((right(p0, px, e) - pc) * a.inv_h);
+    const float gy_s = qdiv(a.rho0, rho(0.5f * (cym.e[e] + cc))) * ((pc - pym.e[e]) * a.inv_h);
+    const float gy_n = qdiv(a.rho0, rho(0.5f * (cc + cyp.e[e]))) * ((pyp.e[e] - pc) * a.inv_h);
     float gz_b = 0.0f, gz_t = 0.0f;
-    if (d.k > 0) gz_b = (a.rho0 / rho(0.5f * (czm.e[e] + cc))) * ((pc - pzm.e[e]) * a.inv_h);
-    if (d.k < a.nz - 1) gz_t = (a.rho0 / rho(0.5f * (cc + czp.e[e]))) * ((pzp.e[e] - pc) * a.inv_h);
+    if (d.k > 0) gz_b = qdiv(a.rho0, rho(0.5f * (czm.e[e] + cc))) * ((pc - pzm.e[e]) * a.inv_h);
+    if (d.k < a.nz - 1) gz_t = qdiv(a.rho0, rho(0.5f * (cc + czp.e[e]))) * ((pzp.e[e] - pc) * a.inv_h);
     const float div_g = ((gx_e - gx_w) * a.inv_h + (gy_n - gy_s) * a.inv_h) + (gz_t - gz_b) * a.inv_h;
     const float div_u = ((right(us, ux, e) - us.e[e]) * a.inv_h + (vsn.e[e] - vs.e[e]) * a.inv_h) +
                         (wst.e[e] - ws.e[e]) * a.inv_h;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kTQ) k3_correct_q(S3<float> a) {
   int bad = 0;
   auto corr = [&](float vel, float cn, float cc, float phn, float phc, float dpn, float dpc) {
     const float rho_f = rho(0.5f * (cn + cc));
-    const float vn = vel - a.dt * (((phc - phn) * a.inv_h) / rho_f + a.inv_rho0 * ((dpc - dpn) * a.inv_h));
+    const float vn = vel - a.dt * (qdiv((phc - phn) * a.inv_h, rho_f) + a.inv_rho0 * ((dpc - dpn) * a.inv_h));
     bad |= !isfinite(vn);
     return vn;
   };
@@ -598,8 +598,8 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
         const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
         const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
                        (uw(i, j, k + 1) - uw(i, j, k)) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * qdiv((cR - cL) * ih, rho_f);
         Hx = H;
         ux = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
       }
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
         const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
         const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
                        (vw(i, j, k + 1) - vw(i, j, k)) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * qdiv((cA - cB) * ih, rho_f);
         Hy = H;
         vy = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
       }
@@ -626,8 +626,8 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
         const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
         const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
                        (wcA * wcA - wcB * wcB) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * qdiv((cA - cB) * ih, rho_f);
         Hz = H;
         wz = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
       }
