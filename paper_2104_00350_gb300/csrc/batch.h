@@ -38,6 +38,15 @@ __host__ __device__ constexpr int fft_threads(int n) {
 __host__ __device__ constexpr int fft_per_block(int n) { return 8 * fft_threads(n) / n; }
 // shared-memory slots of a transform buffer of e points: one pad slot per 16 points
 __host__ __device__ constexpr int fft_buf(int e) { return e + (e >> 4); }
+// dynamic shared memory of a column-transform block of eb points for columns of n points:
+// points, twiddles and cosine weights (complex) and two eigenvalue parts per column.  nmin:
+// the shortest column length the block may get (most columns per block) when one size
+// serves several lengths up to n.
+template <typename T>
+constexpr size_t cols_smem_bytes(int n, int eb, int nmin = 0) {
+  return sizeof(typename C2T<T>::type) * (size_t)(fft_buf(eb) + n / 2 + n) +
+         sizeof(T) * (size_t)(2 * (eb / (nmin ? nmin : n)));
+}
 constexpr int kGhostChunk = 128;
 
 template <typename T>

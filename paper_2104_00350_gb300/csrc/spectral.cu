@@ -281,24 +281,21 @@ struct SymbolArgs {
   float s_eta2_f = 0.f, c0_f = 0.f;   // FP32 path: s_eta2 and c0 rounded once
 };
 
-// Divide X_m by the symbol at (k, m).  FP64 path: in FP64.  FP32 path: in FP32 -- the
-// three terms of L^2 - (S/Cn^2) L + c0 (L <= 0) and the two of L are all of one sign, so
-// the FP32 evaluation has no cancellation and keeps FP32 relative accuracy (FP64 here
-// would occupy GB300's narrow FP64 pipe for most of the kernel).
+// Divide X_m by the symbol at eigenvalue L = lm + lc (2D: lm = lamy[m], lc = lamx[k]; 3D:
+// (lamz[m] + lamy[ky]) + lamx[kx], summed in that order by the caller).  FP64 path: in FP64.
+// FP32 path: in FP32 -- the three terms of L^2 - (S/Cn^2) L + c0 (L <= 0) and the two of L
+// are all of one sign, so the FP32 evaluation has no cancellation and keeps FP32 relative
+// accuracy (FP64 here would occupy GB300's narrow FP64 pipe for most of the kernel).
 template <typename T, typename C2>
-__device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs& sym) {
+__device__ __forceinline__ C2 divide_symbol(C2 X, T L, const SymbolArgs& sym) {
   if constexpr (sizeof(T) == 8) {
     // one reciprocal per point: the quotient is within 1.5 ulp of X / sigma
-    const double L = sym.ncx ? (sym.lamy[m] + sym.lamyp[k / sym.ncx]) + sym.lamx[k % sym.ncx]
-                             : sym.lamy[m] + sym.lamx[k];
     double r;
     if (sym.mode == 0) r = 1.0 / (L * L - sym.s_eta2 * L + sym.c0);
     else r = (L == 0.0) ? 0.0 : 1.0 / L;
     X.x = X.x * r;
     X.y = X.y * r;
   } else {
-    const float L = sym.ncx ? (sym.lamy_f[m] + sym.lamyp_f[k / sym.ncx]) + sym.lamx_f[k % sym.ncx]
-                            : sym.lamy_f[m] + sym.lamx_f[k];
     float r;
     if (sym.mode == 0) r = 1.0f / (L * L - sym.s_eta2_f * L + sym.c0_f);
     else r = (L == 0.0f) ? 0.0f : 1.0f / L;
@@ -317,6 +314,8 @@ __device__ __forceinline__ C2 divide_symbol(C2 X, int k, int m, const SymbolArgs
 //   divide   X_m /= sigma(k, m);
 //   inverse  Z_m = conj(w_m) (X_m - i X_{N-m}) (X_N = 0), z = IFFT(Z)/N,
 //            x_{2n} = z_n, x_{2n+1} = z_{N-1-n}.
+// Dynamic shared memory: cols_smem_bytes<T>(N, EB) (points, twiddles, cosine weights and the
+// per-column eigenvalue parts).
 template <typename T, int LOGN, int THREADS>
 __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
                           const typename C2T<T>::type* __restrict__ tw,
@@ -328,8 +327,24 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
   static_assert(KC >= 1, "a block holds 8 points per thread");
   C2* tws = xs + fft_buf(EB);   // FFT twiddles, staged once per block
   C2* wds = tws + half;         // cosine-transform weights
+  // per column c: lcs[c] = lamx[kx], lcs[KC + c] = lamy[ky] (3D: columns k = ky ncx + kx;
+  // 2D: kx = k, no y part), computed once per block; lms[m]: the transformed axis
+  T* lcs = reinterpret_cast<T*>(wds + N);
+  const T* lms = sizeof(T) == 8 ? (const T*)sym.lamy : (const T*)sym.lamy_f;
+  const T* lam_x = sizeof(T) == 8 ? (const T*)sym.lamx : (const T*)sym.lamx_f;
+  const T* lam_y = sizeof(T) == 8 ? (const T*)sym.lamyp : (const T*)sym.lamyp_f;
   for (int t = threadIdx.x; t < half; t += THREADS) tws[t] = tw[t];
   for (int t = threadIdx.x; t < N; t += THREADS) wds[t] = wd[t];
+  for (int c = threadIdx.x; c < KC; c += THREADS) {
+    const int k = min(k0 + c, nh1 - 1);
+    lcs[c] = sym.ncx ? lam_x[k % sym.ncx] : lam_x[k];
+    lcs[KC + c] = sym.ncx ? lam_y[k / sym.ncx] : T(0);
+  }
+  // L at (column c, mode m), in the order (lamz[m] + lamy[ky]) + lamx[kx] (3D) or
+  // lamy[m] + lamx[k] (2D)
+  auto eig = [&](int c, int m) -> T {
+    return sym.ncx ? (lms[m] + lcs[KC + c]) + lcs[c] : lms[m] + lcs[c];
+  };
   // load: consecutive threads take consecutive columns of one row
   for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
     const int cc = idx % KC, r = idx / KC;
@@ -346,7 +361,6 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
   // pair tasks (m, N - m), m = 0..N/2, of every column
   for (int t = threadIdx.x; t < KC * (half + 1); t += THREADS) {
     const int c = t / (half + 1), m = t - c * (half + 1);
-    const int k = min(k0 + c, nh1 - 1);
     const int mm = (N - m) & (N - 1);
     const int im = pad(c * N + m), imm = pad(c * N + mm);
     const C2 Vm = xs[im], Vmm = xs[imm];
@@ -369,8 +383,8 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
       Xmm.x = w.x * vr.x - w.y * vr.y;
       Xmm.y = w.x * vi.x - w.y * vi.y;
     }
-    Xm = divide_symbol<T>(Xm, k, m, sym);
-    Xmm = divide_symbol<T>(Xmm, k, mm, sym);
+    Xm = divide_symbol<T>(Xm, eig(c, m), sym);
+    Xmm = divide_symbol<T>(Xmm, eig(c, mm), sym);
     // inverse pre-processing: Z_m = conj(w_m) (X_m - i X_{N-m})
     C2 Zm, Zmm;
     {
@@ -750,7 +764,7 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   // (FP64, 1024 points), allowed by the attribute set with the tables
   const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
   const size_t ysm = sizeof(C2) * (fft_buf(8 * L) + ny / 2);
-  const size_t csm = sizeof(C2) * (fft_buf(8 * L) + nz / 2 + nz);
+  const size_t csm = cols_smem_bytes<T>(nz, 8 * L);
   const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
   k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, (const C2*)in.twx);
   if (rec) rec->mark("rows_fwd", s);
@@ -857,7 +871,7 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   // nx, ny <= 1024 here: the row buffers take at most 26 KiB and the column buffers 42 KiB
   // of shared memory, below the default limit, so this path sets no function attributes
   const size_t rsm = sizeof(double2) * (fft_buf(8 * S) + nx / 2);
-  const size_t csm = sizeof(double2) * (fft_buf(8 * S) + ny / 2 + ny);
+  const size_t csm = cols_smem_bytes<double>(ny, 8 * S);
   k_rows_fwd<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(rhs, spec, nx, ny, twx);
   SymbolArgs sym;
   sym.mode = mode;

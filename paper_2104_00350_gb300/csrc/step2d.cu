@@ -1073,7 +1073,7 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
   for (int c = 0; c < 2; ++c) {
     const int eb = 8 * (c ? kFftLargeThreads : kFftSmallThreads);
     plan.rows_smem[c] = sizeof(C2) * (fft_buf(eb) + rmax[c] / 2);
-    plan.cols_smem[c] = sizeof(C2) * (fft_buf(eb) + cmax[c] / 2 + cmax[c]);
+    plan.cols_smem[c] = cols_smem_bytes<T>(cmax[c], eb, 8);
   }
   return cudaSuccess;
 }
