@@ -64,6 +64,15 @@ typedef enum {
 
 typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
 
+/* time integration of the Cahn-Hilliard equation (rows a1 + a2): SEMI_IMPLICIT, the
+ * stabilised split of Appendix A.1 solved in one eigenbasis; EXPLICIT, the Adams-Bashforth
+ * update of Eq. ExpCH, C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}) with
+ * F = -div(u C) + (1/Pe) lap(phi), F^{n-1} taken from the level n-1 fields (C^{n-1},
+ * u^{n-1}, v^{n-1} and phi(C^{n-1}) with its ghost fill); no transform.  EXPLICIT: 2D only
+ * (IB_PF_E_UNSUPPORTED in 3D); its time step is limited by dt <~ Pe h^4 / (8 Cn^2) and
+ * dt <~ Pe h^2 / 8, which the library does not check. */
+typedef enum { IB_PF_CH_SEMI_IMPLICIT = 0, IB_PF_CH_EXPLICIT = 1 } ib_pf_ch_scheme;
+
 /* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points
  * against it).  FLAT: x2 < p[0] (2D), z < p[0] (3D).  SINUSOID (2D): x2 < p[0] + p[1]
  * sin(2 pi p[2] x1).  SPHERE (3D): |x - (p[0], p[1], p[2])| < p[3].  SPHERES (3D): the union
@@ -97,6 +106,7 @@ typedef struct {
 typedef struct {
   double Re, Ca, Cn, Pe, S, rho_ratio, mu_ratio, theta_deg, l_s, mu_f, d1, d2, dt;
   int precision;  /* ib_pf_precision */
+  int ch_scheme;  /* ib_pf_ch_scheme; all instances of a context share it */
 } ib_pf_params;
 
 /* field ids for read / write */

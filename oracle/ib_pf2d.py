@@ -11,6 +11,7 @@ What it computes (Shahmardi, Rosti, Tammisola & Brandt, arXiv 2104.00350):
   * per step, in the order of the block diagram of Sec. 4.2 / Appendix A:
       a1  RHS of the semi-implicit Cahn-Hilliard split (Eq. Helmholtz1, Appendix A.1)
       a2  the two Helmholtz solves (Eqs. Helmholtz1, Helmholtz2) in one eigenbasis
+          (or, with params.ch_scheme = 1, a1+a2 as the explicit AB2 update of Eq. ExpCH)
       a3  contact-angle ghost fill of C (Eqs. interpolationAtWall, ProjectingToNT, UpdateC,
           static form of Eq. WallBCS)
       a4  chemical potential (Eq. Chemical-Potential) and its zero-gradient ghost fill
@@ -60,6 +61,15 @@ restatement, with the CUDA path):
       Eq. PressurePoisson rests on rho >= rho0 = min(rho_l, rho_g), which an unclamped
       linear law breaks wherever C overshoots -1 (observed inside the solid, where it ended
       runs after ~1e4 steps).
+  R15 Explicit CH (Eq. ExpCH) in the form of R1 and R8: the update is
+      C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),  F = -div(u C_f) + (1/Pe) lap(phi),
+      the convective term in divergence form (the paper writes u . grad C; equal for a
+      divergence-free u) and the mobility term with the paper's 3/(2 sqrt 2) M absorbed into
+      1/Pe.  F^{n-1} is evaluated from the level n-1 fields (C^{n-1}, u^{n-1}, v^{n-1}, and
+      phi^{n-1} = phi(C^{n-1}) with its zero-gradient ghost fill), so the first step of a
+      run started with C^{n-1} = C^n, u^{n-1} = u^n is a forward Euler step.  As in the
+      semi-implicit variant every cell is updated (also inside the solid) before the a3
+      ghost fill.
 """
 from __future__ import annotations
 
@@ -446,6 +456,38 @@ def ch_rhs(case: Case2D, st: dict) -> np.ndarray:
     return (p.Pe / eta2) * (Cc / p.dt - div) + laplacian(g, h)
 
 
+def chemical_potential(case: Case2D, geo: "Geometry2D", C: np.ndarray) -> np.ndarray:
+    """a4 (Eq. Chemical-Potential, reading R1): phi = psi'(C) - Cn^2 lap(C) on every cell, then
+    the zero normal gradient at the wall, phi_G = phi_M (Sec. 4.2.2, last lines)."""
+    eta = case.params.Cn
+    phi = (C * C * C - C) - (eta * eta) * laplacian(C, case.h)
+    phi_f = phi.reshape(-1)
+    phi_f[geo.gcell] = mirror_value(phi_f.copy(), geo)
+    return phi
+
+
+def ch_flux_div(case: Case2D, C: np.ndarray, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """div(u C_f) with face means of C, no flux through the x2 walls (reading R8)."""
+    h, ny = case.h, case.ny
+    Fx = u * (0.5 * (_xm(C) + C))
+    Fy = np.zeros((ny + 1, case.nx))
+    Fy[1:ny] = v[1:ny] * (0.5 * (C[:-1] + C[1:]))
+    return (_xp(Fx) - Fx) / h + (Fy[1:] - Fy[:-1]) / h
+
+
+def ch_explicit(case: Case2D, geo: "Geometry2D", st: dict) -> np.ndarray:
+    """a1 + a2, explicit variant (Eq. ExpCH, reading R15): the updated C on every cell,
+    before the ghost fill."""
+    p = case.params
+
+    def F(C, u, v):
+        return -ch_flux_div(case, C, u, v) + laplacian(chemical_potential(case, geo, C), case.h) / p.Pe
+
+    Fn = F(st["C"], st["u"], st["v"])
+    Fo = F(st["C_old"], st["u_old"], st["v_old"])
+    return st["C"] + p.dt * (1.5 * Fn - 0.5 * Fo)
+
+
 def _gather(field_flat, ap, w):
     """Omega_IP = sum_a W(a) Omega(AP_a) (Eq. weright averaged), per ghost."""
     acc = np.zeros(ap.shape[0])
@@ -545,10 +587,13 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     rho, mu, rho0 = _props(case)
     info = {}
 
-    # a1 + a2: semi-implicit CH (Appendix A.1)
-    Q = ch_rhs(case, st)
-    C_pre = ch_solve(case, Q)
-    info["Q"] = Q
+    # a1 + a2: semi-implicit CH (Appendix A.1), or the explicit variant (Eq. ExpCH)
+    if getattr(p, "ch_scheme", 0) == 1:
+        C_pre = ch_explicit(case, geo, st)
+    else:
+        Q = ch_rhs(case, st)
+        C_pre = ch_solve(case, Q)
+        info["Q"] = Q
     info["C_pre"] = C_pre
     info["mass_pre"] = float(C_pre.sum())
 
@@ -564,9 +609,7 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     info["mass"] = float(C1.sum())
 
     # a4: chemical potential, zero normal gradient at the wall (Sec. 4.2.2, last lines)
-    phi = (C1 * C1 * C1 - C1) - (eta * eta) * laplacian(C1, h)
-    phi_f = phi.reshape(-1)
-    phi_f[geo.gcell] = mirror_value(phi_f.copy(), geo)
+    phi = chemical_potential(case, geo, C1)
     info["phi"] = phi
 
     # a5: explicit AB2 predictor + penalisation (Eq. PredictionExp, Eq. Penalization2)

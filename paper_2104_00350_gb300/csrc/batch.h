@@ -55,6 +55,7 @@ struct StepArgs {
   T inv_h, inv_h2, dt;
   // Cahn-Hilliard
   T S, inv_eta2, pe_eta2, inv_dt, eta2;
+  T inv_pe;   // 1/Pe (explicit variant)
   // fluid properties: rho(C) = rho_a + rho_b C, mu(C) = mu_a + mu_b C
   T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
   // contact angle / slip

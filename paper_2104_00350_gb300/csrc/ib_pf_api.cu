@@ -149,6 +149,14 @@ ib_pf_status validate3(const ib_pf_grid& g, const ib_pf_geometry& w, std::string
 ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_params& p,
                       std::string& why) {
   if (g.dim != 2 && g.dim != 3) { why = "dim must be 2 or 3"; return IB_PF_E_ARG; }
+  if (p.ch_scheme != IB_PF_CH_SEMI_IMPLICIT && p.ch_scheme != IB_PF_CH_EXPLICIT) {
+    why = "unknown ch_scheme";
+    return IB_PF_E_ARG;
+  }
+  if (g.dim == 3 && p.ch_scheme == IB_PF_CH_EXPLICIT) {
+    why = "the explicit Cahn-Hilliard variant is built for 2D only";
+    return IB_PF_E_UNSUPPORTED;
+  }
   if (g.dim == 3) {
     if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
     if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }
@@ -240,11 +248,14 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
       return fail(nullptr, IB_PF_E_ARG, "all instances must share one precision");
     if (grids[k].dim != grids[0].dim)
       return fail(nullptr, IB_PF_E_ARG, "all instances must share one dimension");
+    if (params[k].ch_scheme != params[0].ch_scheme)
+      return fail(nullptr, IB_PF_E_ARG, "all instances must share one ch_scheme");
   }
   ib_pf_ctx* ctx = new (std::nothrow) ib_pf_ctx();
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "out of host memory");
   ctx->precision = params[0].precision;
   ctx->dim = grids[0].dim;
+  ctx->ch_scheme = params[0].ch_scheme;
   ctx->esz = ctx->precision == IB_PF_FP64 ? 8 : 4;
   ctx->user_stream = (cudaStream_t)cuda_stream;
   auto bail = [&](ib_pf_status st) {

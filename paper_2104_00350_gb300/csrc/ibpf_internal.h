@@ -156,6 +156,7 @@ struct Recorder {
 
 struct Ctx {
   int dim = 2;
+  int ch_scheme = IB_PF_CH_SEMI_IMPLICIT;
   std::vector<Instance> inst;
   int precision = IB_PF_FP64;
   size_t esz = 8;

@@ -423,6 +423,7 @@ StepArgs<T> make_args(const Instance& in) {
   a.S = (T)p.S;
   a.inv_eta2 = (T)(1.0 / eta2);
   a.pe_eta2 = (T)(p.Pe / eta2);
+  a.inv_pe = (T)(1.0 / p.Pe);
   a.inv_dt = (T)(1.0 / p.dt);
   a.eta2 = (T)eta2;
   const double rho_l = 1.0, rho_g = 1.0 / p.rho_ratio, mu_l = 1.0, mu_g = 1.0 / p.mu_ratio;
@@ -897,6 +898,119 @@ __global__ void IBPF_CELL_BOUNDS kq_correct(const InstDev<float>* __restrict__ I
 }
 #undef IBPF_QUAD_PROLOGUE
 
+// ------------------------------------------- a1 + a2, explicit variant (Eq. ExpCH)
+// C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),  F = -div(u C_f) + (1/Pe) lap(phi), F^{n-1}
+// from the level n-1 fields; phi^n = phi(C^n) and phi^{n-1} = phi(C^{n-1}) with their
+// zero-gradient ghost fills.  Three launches:
+//   kx_phi2      phi^n -> phi, phi^{n-1} -> rhs, A^{n-1} = -div(u^{n-1} C^{n-1}_f) -> Q
+//   kx_fill_phi2 ghost values of phi and rhs (phi_G = phi_M)
+//   kx_update    C^{n+1} into the C^{n-1} slot (compensated in FP32); reads C^{n-1} only
+//                through Q and rhs, so writing the slot in place is safe
+// div(u C_f) with face means of C and no flux through the x2 walls, as in ch_rhs_cell.
+template <typename T>
+__device__ __forceinline__ T flux_div_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                           const T* __restrict__ u, const T* __restrict__ v,
+                                           int i, int j) {
+  const int nx = a.nx, ny = a.ny;
+  const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
+  const size_t r = (size_t)j * nx;
+  const T c0 = C[r + i];
+  const T fx_w = u[r + i] * (T(0.5) * (C[r + im] + c0));
+  const T fx_e = u[r + ip] * (T(0.5) * (c0 + C[r + ip]));
+  T fy_s = T(0), fy_n = T(0);
+  if (j > 0) fy_s = v[r + i] * (T(0.5) * (C[r - nx + i] + c0));
+  if (j < ny - 1) fy_n = v[r + nx + i] * (T(0.5) * (c0 + C[r + nx + i]));
+  return (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
+}
+
+template <typename T>
+__device__ __forceinline__ T lap5_cell(const StepArgs<T>& a, const T* __restrict__ f, int i, int j) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t r = (size_t)j * nx;
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  return (((f[r + wrap_p(i, nx)] + f[r + wrap_m(i, nx)]) + (f[(size_t)jn * nx + i] + f[(size_t)js * nx + i])) -
+          T(4) * f[r + i]) * a.inv_h2;
+}
+
+template <typename T>
+__global__ void IBPF_CELL_BOUNDS kx_phi2(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                                         int nblk, int cur) {
+  const int b_ = blockIdx.x;
+  if (b_ >= nblk) return;
+  const int2 w_ = blk[b_];
+  const InstDev<T>& d = I[w_.x];
+  int i, jb;
+  tile_base(d, w_.y, i, jb);
+  T o_pn[kRowsPerThread], o_po[kRowsPerThread], o_a[kRowsPerThread];
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int j = jb + q * kTileY;
+    if (i < d.nx && j < d.ny) {
+      o_pn[q] = chem_pot_cell(d.a, d.C[cur], i, j);
+      o_po[q] = chem_pot_cell(d.a, d.C[1 - cur], i, j);
+      o_a[q] = -flux_div_cell(d.a, d.C[1 - cur], d.U[1 - cur], d.V[1 - cur], i, j);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int j = jb + q * kTileY;
+    if (i < d.nx && j < d.ny) {
+      const size_t c = (size_t)j * d.nx + i;
+      d.phi[c] = o_pn[q];
+      d.rhs[c] = o_po[q];
+      d.Q[c] = o_a[q];
+    }
+  }
+}
+
+template <typename T>
+__global__ void kx_fill_phi2(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk) {
+  const int b_ = blockIdx.x;
+  if (b_ >= nblk) return;
+  const int2 w_ = blk[b_];
+  const InstDev<T>& d = I[w_.x];
+  const int g = w_.y * kGhostChunk + threadIdx.x;
+  if (g < d.tab.ng) {
+    fill_phi_ghost(d.tab, d.phi, g);
+    fill_phi_ghost(d.tab, d.rhs, g);
+  }
+}
+
+template <typename T>
+__global__ void IBPF_CELL_BOUNDS kx_update(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
+                                           int nblk, int cur) {
+  const int b_ = blockIdx.x;
+  if (b_ >= nblk) return;
+  const int2 w_ = blk[b_];
+  const InstDev<T>& d = I[w_.x];
+  int i, jb;
+  tile_base(d, w_.y, i, jb);
+  T o_d[kRowsPerThread];
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int j = jb + q * kTileY;
+    if (i < d.nx && j < d.ny) {
+      const size_t c = (size_t)j * d.nx + i;
+      const T Fn = -flux_div_cell(d.a, d.C[cur], d.U[cur], d.V[cur], i, j) +
+                   lap5_cell(d.a, d.phi, i, j) * d.a.inv_pe;
+      const T Fo = d.Q[c] + lap5_cell(d.a, d.rhs, i, j) * d.a.inv_pe;
+      o_d[q] = d.a.dt * (T(1.5) * Fn - T(0.5) * Fo);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRowsPerThread; ++q) {
+    const int j = jb + q * kTileY;
+    if (i < d.nx && j < d.ny) {
+      const size_t c = (size_t)j * d.nx + i;
+      T hi = d.C[cur][c];
+      T lo = d.Clo[cur] ? d.Clo[cur][c] : T(0);
+      pair_add(hi, lo, o_d[q], T(0));   // FP64: plain addition
+      d.C[1 - cur][c] = hi;
+      if (d.Clo[1 - cur]) d.Clo[1 - cur][c] = lo;
+    }
+  }
+}
+
 template <typename T>
 int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, Recorder* rec) {
   const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
@@ -910,14 +1024,26 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     ++launches;
     if (rec) rec->mark(n, s);
   };
-  // a1 + a2: CH right-hand side, then the solve; C^{n+1} lands in slot 1 - cur
-  if constexpr (sizeof(T) == 4) kq_ch_h<<<nc, tile, 0, s>>>(I, bc, nc, cur);
-  else kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
-  mark("ch_h");
-  if constexpr (sizeof(T) == 4) kq_ch_rhs<<<nc, tile, 0, s>>>(I, bc, nc, cur);
-  else kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
-  mark("ch_rhs");
-  launches += spectral_solve_batch<T>(plan, 0, cur, s, rec);
+  // a1 + a2: CH right-hand side, then the solve (or the explicit update); C^{n+1} lands in
+  // slot 1 - cur
+  if (c.ch_scheme == IB_PF_CH_EXPLICIT) {
+    kx_phi2<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("ch_phi2");
+    if (ng > 0) {
+      kx_fill_phi2<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng);
+      mark("ch_fill2");
+    }
+    kx_update<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("ch_explicit");
+  } else {
+    if constexpr (sizeof(T) == 4) kq_ch_h<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    else kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("ch_h");
+    if constexpr (sizeof(T) == 4) kq_ch_rhs<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    else kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("ch_rhs");
+    launches += spectral_solve_batch<T>(plan, 0, cur, s, rec);
+  }
   // a3: contact-angle ghost fill
   if (ng > 0) {
     kb_fill_C<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
@@ -954,7 +1080,6 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
   if constexpr (sizeof(T) == 4) kq_correct<<<nc, tile, 0, s>>>(I, bc, nc, cur);
   else kb_correct<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
   mark("correct");
-  (void)c;
   return launches;
 }
 

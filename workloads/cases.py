@@ -55,6 +55,7 @@ class Params:
     d1: float = 0.0
     d2: float = 0.0
     dt: float = 1.0e-4
+    ch_scheme: int = 0   # 0: semi-implicit CH (Appendix A.1); 1: explicit AB2 (Eq. ExpCH)
 
 
 @dataclass(frozen=True)
