@@ -11,6 +11,9 @@ together, so one bench step is one full time step (a1..a8) of all six instances.
   e2e       the same metric through the C ABI with host buffers: every step writes the
             whole state from pinned host memory, steps, and reads C back to the host.
   roofline  dominant kernel of a second, event-instrumented pass over the same steps.
+  batched_ensemble / workloads_3d / explicit_ch: the 64-instance FP32 ensemble, the 3D
+            sphere (256^3) and packing (512^3) workloads, and the headline workload with the
+            explicit Cahn-Hilliard variant (Eq. ExpCH), each with its per-kernel roofline.
   cpu_baseline / --impl reference: the FP64 CPU oracle (test infrastructure) timed on
             the host cores.
 
@@ -41,7 +44,6 @@ L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic traffic per cell and per step, summed over the launches of each kernel name:
 # field words read once and written once (FP32 form, FP64 form) plus FP64 geometry words.
-# See the design doc for the derivation.
 KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form table words)
     "ch_h": (3, 3, 0),           # C, Co -> h
     "ch_rhs": (8, 8, 0),         # C, Co, u, uo, v, vo, h -> R
@@ -54,6 +56,9 @@ KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form t
                                  # (FP32 copies in the FP32 form, FP64 tables otherwise)
     "poisson_rhs": (7, 7, 0),    # C, P, Po, u**, v** -> rhs, P^
     "correct": (8, 7, 0),        # C (+ lo for the mass), dP, P^, u**, v** -> u, v
+    # explicit Cahn-Hilliard variant (replaces ch_h, ch_rhs and the CH solve)
+    "ch_phi2": (7, 7, 0),        # C, Co, uo, vo -> phi^n, phi^{n-1}, A^{n-1}
+    "ch_explicit": (9, 7, 0),    # C (+ lo), u, v, phi^n, phi^{n-1}, A^{n-1} -> C (+ lo)
 }
 
 
@@ -97,6 +102,8 @@ def parse_args():
                     help="skip the 3D sphere (256^3) and porous (512^3) workloads")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 64-instance batched-ensemble measurement")
+    ap.add_argument("--no-explicit", action="store_true",
+                    help="skip the explicit Cahn-Hilliard variant of the headline workload")
     ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="busy GPU time before the timed region so clocks settle")
@@ -267,7 +274,7 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flops x GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM (ncu peak_sustained) x flops x GHz
 
 
 def kernel_flops64(name: str, nx: int, ny: int) -> float:
@@ -275,7 +282,7 @@ def kernel_flops64(name: str, nx: int, ny: int) -> float:
     each shared corner / cell quantity once; a division counts as one flop)."""
     import math
     table = {"predict": 99.0, "ch_h": 25.0, "ch_rhs": 30.0, "chem_pot": 9.0,
-             "poisson_rhs": 40.0, "correct": 30.0,
+             "poisson_rhs": 40.0, "correct": 30.0, "ch_phi2": 30.0, "ch_explicit": 34.0,
              "rows_fwd": 2.5 * math.log2(nx) + 4.0, "rows_inv": 2.5 * math.log2(nx) + 4.0,
              "cols_solve": 5.0 * math.log2(ny) + 16.0}
     return table.get(name, 0.0)
@@ -400,7 +407,7 @@ def run_ours(args):
 
     def restart(solver):
         # every timed pass starts from t = 0 (one of the six runs becomes non-finite near
-        # step 4600; see DESIGN.md)
+        # step 4600)
         for k in range(len(cl)):
             solver.write_state(init[k], k)
         torch.cuda.synchronize()
@@ -534,6 +541,42 @@ def run_ours(args):
                "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls",
                "roofline": eroof}
         esolver.close()
+    # explicit Cahn-Hilliard variant (Eq. ExpCH) of the headline workload, both forms
+    expl = None
+    if not args.no_explicit:
+        import dataclasses
+        expl = {}
+        xcl = [dataclasses.replace(c, params=dataclasses.replace(c.params, ch_scheme=1)) for c in cl]
+        for form in forms:
+            prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+            esz = 8 if prec == ibpf.FP64 else 4
+            xs = ibpf.solver_from_cases(xcl, prec, stream=stream.cuda_stream)
+            xs.precompute_weights()
+            restart(xs)
+            for _ in range(max(3, args.warmup // 4)):
+                flush.zero_()
+                xs.step(1)
+            torch.cuda.synchronize()
+            xsteps = max(1, min(args.steps, 100))
+            xms, _, _ = timed_steps(xs, xsteps)
+            xms = max_over_ranks([xms], dist, "cuda")[0]
+            try:
+                restart(xs)
+                ibpf.ib_pf_set_kernel_timing(xs.ctx, True)
+                xs.step(1)
+                torch.cuda.synchronize()
+                _, ktot, kcount = timed_steps(xs, xsteps, collect_kernels=True)
+                ibpf.ib_pf_set_kernel_timing(xs.ctx, False)
+                xroof = roofline(ktot, kcount, xsteps, cells, esz, xcl[0], peak, peak_kind, form,
+                                 workload="sinusoid_512x256x6_explicit")
+            except Exception as exc:
+                xroof = {"error": str(exc)[:200]}
+            expl[form] = {"value": aggregate_rate(world, cells, xsteps, xms * 1e-3), "unit": UNIT,
+                          "ms_per_step": xms / xsteps, "steps": xsteps,
+                          "dtype": "f64" if esz == 8 else "f32",
+                          "gpu_launches": int(xs.query(ibpf.Q_LAUNCHES)) * xsteps,
+                          "l2": "flushed before every timed step", "roofline": xroof}
+            xs.close()
     d3 = None
     if not args.no_3d:
         d3 = run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps)
@@ -565,6 +608,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "forms": {f: {k: v for k, v in r.items() if k != "e2e"} for f, r in results.items()},
             "batched_ensemble": ens,
+            "explicit_ch": expl,
             "workloads_3d": d3,
         }
         print(json.dumps(line), flush=True)

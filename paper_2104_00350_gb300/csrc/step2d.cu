@@ -896,6 +896,78 @@ __global__ void IBPF_CELL_BOUNDS kq_correct(const InstDev<float>* __restrict__ I
   const int ntiles = d.gx * ((d.ny + kTileH - 1) / kTileH);
   tile_mass<float, kTileX * kTileY>(s_hi, s_lo, w_.y, ntiles, d.partial, d.ticket, d.mass);
 }
+// explicit Cahn-Hilliard variant: kx_phi2 and kx_update on runs of four cells
+__device__ __forceinline__ float flux_div_q(const StepArgs<float>& a, const Run2& r, int ny,
+                                            const V4& c, const X2& cx, const V4& cn, const V4& cs,
+                                            const V4& u, const X2& ux, const V4& v, const V4& vn,
+                                            int e) {
+  const float c0 = c.e[e];
+  const float fx_w = u.e[e] * (0.5f * (left(c, cx, e) + c0));
+  const float fx_e = right(u, ux, e) * (0.5f * (c0 + right(c, cx, e)));
+  float fy_s = 0.0f, fy_n = 0.0f;
+  if (r.j > 0) fy_s = v.e[e] * (0.5f * (cs.e[e] + c0));
+  if (r.j < ny - 1) fy_n = vn.e[e] * (0.5f * (c0 + cn.e[e]));
+  return (fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h;
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_phi2(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                         int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float *C = d.C[cur], *Co = d.C[1 - cur], *uo = d.U[1 - cur], *vo = d.V[1 - cur];
+  const int nx = d.nx;
+  const V4 c = ld4(C, r.q), cn = ld4(C, r.n), cs = ld4(C, r.s);
+  const V4 o = ld4(Co, r.q), on = ld4(Co, r.n), os = ld4(Co, r.s);
+  const V4 u = ld4(uo, r.q), v = ld4(vo, r.q), vn = ld4(vo, r.q + nx);
+  const X2 cx = xnb2(c, r, nx, [&](size_t q) { return C[q]; });
+  const X2 ox = xnb2(o, r, nx, [&](size_t q) { return Co[q]; });
+  const X2 ux = xnb2(u, r, nx, [&](size_t q) { return uo[q]; });
+  const V4 pn = map4([&](int e) {
+    const float c0 = c.e[e];
+    return (c0 * c0 * c0 - c0) - a.eta2 * lap5q(a, c, cx, cn, cs, e);
+  });
+  const V4 po = map4([&](int e) {
+    const float c0 = o.e[e];
+    return (c0 * c0 * c0 - c0) - a.eta2 * lap5q(a, o, ox, on, os, e);
+  });
+  const V4 ao = map4([&](int e) { return -flux_div_q(a, r, d.ny, o, ox, on, os, u, ux, v, vn, e); });
+  if (r.act) {
+    st4(d.phi, r.q, pn);
+    st4(d.rhs, r.q, po);
+    st4(d.Q, r.q, ao);
+  }
+}
+
+__global__ void IBPF_CELL_BOUNDS kq_update(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
+                                           int nblk, int cur) {
+  IBPF_QUAD_PROLOGUE
+  const float *C = d.C[cur], *u = d.U[cur], *v = d.V[cur], *ph = d.phi, *po = d.rhs;
+  const int nx = d.nx;
+  const V4 c = ld4(C, r.q), cn = ld4(C, r.n), cs = ld4(C, r.s);
+  const V4 uu = ld4(u, r.q), vv = ld4(v, r.q), vn = ld4(v, r.q + nx);
+  const V4 f = ld4(ph, r.q), fn = ld4(ph, r.n), fs = ld4(ph, r.s);
+  const V4 g = ld4(po, r.q), gn = ld4(po, r.n), gs = ld4(po, r.s);
+  const V4 ao = ld4(d.Q, r.q);
+  const V4 lo = d.Clo[cur] ? ld4(d.Clo[cur], r.q) : V4{{0.0f, 0.0f, 0.0f, 0.0f}};
+  const X2 cx = xnb2(c, r, nx, [&](size_t q) { return C[q]; });
+  const X2 ux = xnb2(uu, r, nx, [&](size_t q) { return u[q]; });
+  const X2 fx = xnb2(f, r, nx, [&](size_t q) { return ph[q]; });
+  const X2 gx = xnb2(g, r, nx, [&](size_t q) { return po[q]; });
+  V4 hi, nlo;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float Fn = -flux_div_q(a, r, d.ny, c, cx, cn, cs, uu, ux, vv, vn, e) +
+                     lap5q(a, f, fx, fn, fs, e) * a.inv_pe;
+    const float Fo = ao.e[e] + lap5q(a, g, gx, gn, gs, e) * a.inv_pe;
+    float h = c.e[e], l = lo.e[e];
+    pair_add(h, l, a.dt * (1.5f * Fn - 0.5f * Fo), 0.0f);
+    hi.e[e] = h;
+    nlo.e[e] = l;
+  }
+  if (r.act) {
+    st4(d.C[1 - cur], r.q, hi);
+    if (d.Clo[1 - cur]) st4(d.Clo[1 - cur], r.q, nlo);
+  }
+}
 #undef IBPF_QUAD_PROLOGUE
 
 // ------------------------------------------- a1 + a2, explicit variant (Eq. ExpCH)
@@ -1027,13 +1099,15 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
   // a1 + a2: CH right-hand side, then the solve (or the explicit update); C^{n+1} lands in
   // slot 1 - cur
   if (c.ch_scheme == IB_PF_CH_EXPLICIT) {
-    kx_phi2<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    if constexpr (sizeof(T) == 4) kq_phi2<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    else kx_phi2<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
     mark("ch_phi2");
     if (ng > 0) {
       kx_fill_phi2<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng);
       mark("ch_fill2");
     }
-    kx_update<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    if constexpr (sizeof(T) == 4) kq_update<<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    else kx_update<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
     mark("ch_explicit");
   } else {
     if constexpr (sizeof(T) == 4) kq_ch_h<<<nc, tile, 0, s>>>(I, bc, nc, cur);
