@@ -68,9 +68,9 @@ typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
  * stabilised split of Appendix A.1 solved in one eigenbasis; EXPLICIT, the Adams-Bashforth
  * update of Eq. ExpCH, C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}) with
  * F = -div(u C) + (1/Pe) lap(phi), F^{n-1} taken from the level n-1 fields (C^{n-1},
- * u^{n-1}, v^{n-1} and phi(C^{n-1}) with its ghost fill); no transform.  EXPLICIT: 2D only
- * (IB_PF_E_UNSUPPORTED in 3D); its time step is limited by dt <~ Pe h^4 / (8 Cn^2) and
- * dt <~ Pe h^2 / 8, which the library does not check. */
+ * u^{n-1}, v^{n-1} (w^{n-1}) and phi(C^{n-1}) with its ghost fill); no transform.  The
+ * explicit time step is limited by about dt < Pe h^4 / (4 D Cn^2) and dt < Pe h^2 / (4 D)
+ * (D = 2 or 3), which the library does not check. */
 typedef enum { IB_PF_CH_SEMI_IMPLICIT = 0, IB_PF_CH_EXPLICIT = 1 } ib_pf_ch_scheme;
 
 /* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points

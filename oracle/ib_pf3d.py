@@ -25,6 +25,8 @@ with rows 0 and nz on the domain walls.  Readings R1-R11 of ib_pf2d hold unchang
       order +z, -z, +x, -x, +y, -y.
   R14 Periodic images: the sphere test takes the nearest image in x and y
       (dx = x - cx, shifted by -L if dx > L/2 or +L if dx < -L/2).
+  With params.ch_scheme = 1, a1 + a2 is the explicit AB2 update of Eq. ExpCH as in the 2D
+  oracle (its reading R15), with the third axis.
 Library primitives used as steps: numpy elementwise arithmetic and scipy's FFT / DCT-II.
 """
 from __future__ import annotations
@@ -483,6 +485,38 @@ def ch_rhs3(case: Case3D, st: dict) -> np.ndarray:
     return (p.Pe / eta2) * (Cc / p.dt - div) + laplacian3(g, h)
 
 
+def chemical_potential3(case: Case3D, geo: "Geometry3D", C: np.ndarray) -> np.ndarray:
+    """a4 in 3D: phi = psi'(C) - Cn^2 lap(C) on every cell, then phi_G = phi_M."""
+    eta = case.params.Cn
+    phi = (C * C * C - C) - (eta * eta) * laplacian3(C, case.h)
+    pf = phi.reshape(-1)
+    pf[geo.gcell] = mirror_value3(pf.copy(), geo)
+    return phi
+
+
+def ch_flux_div3(case: Case3D, C, u, v, w) -> np.ndarray:
+    """div(u C_f) with face means of C, no flux through the z walls."""
+    h, nz = case.h, case.nz
+    Fx = u * (0.5 * (_xm(C) + C))
+    Fy = v * (0.5 * (_ym(C) + C))
+    Fz = np.zeros((nz + 1,) + C.shape[1:])
+    Fz[1:nz] = w[1:nz] * (0.5 * (C[:-1] + C[1:]))
+    return ((_xp(Fx) - Fx) / h + (_yp(Fy) - Fy) / h) + (Fz[1:] - Fz[:-1]) / h
+
+
+def ch_explicit3(case: Case3D, geo: "Geometry3D", st: dict) -> np.ndarray:
+    """a1 + a2, explicit variant in 3D (Eq. ExpCH, reading R15 of the 2D oracle):
+    C^n + dt (3/2 F^n - 1/2 F^{n-1}), F = -div(u C_f) + (1/Pe) lap(phi)."""
+    p = case.params
+
+    def F(C, u, v, w):
+        return -ch_flux_div3(case, C, u, v, w) + laplacian3(chemical_potential3(case, geo, C), case.h) / p.Pe
+
+    Fn = F(st["C"], st["u"], st["v"], st["w"])
+    Fo = F(st["C_old"], st["u_old"], st["v_old"], st["w_old"])
+    return st["C"] + p.dt * (1.5 * Fn - 0.5 * Fo)
+
+
 def _gather(field_flat, ap, w):
     acc = np.zeros(ap.shape[0])
     for a in range(ap.shape[1]):
@@ -558,10 +592,14 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     rho, mu, rho0 = _props(case)
     info = {}
 
-    # a1 + a2
-    Q = ch_rhs3(case, st)
-    C_pre = ch_solve3(case, Q)
-    info["Q"], info["C_pre"], info["mass_pre"] = Q, C_pre, float(C_pre.sum())
+    # a1 + a2 (semi-implicit, or the explicit variant with params.ch_scheme = 1)
+    if getattr(p, "ch_scheme", 0) == 1:
+        C_pre = ch_explicit3(case, geo, st)
+    else:
+        Q = ch_rhs3(case, st)
+        C_pre = ch_solve3(case, Q)
+        info["Q"] = Q
+    info["C_pre"], info["mass_pre"] = C_pre, float(C_pre.sum())
 
     # a3
     C1 = C_pre.copy()
@@ -573,9 +611,7 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     info["mass"] = float(C1.sum())
 
     # a4
-    phi = (C1 * C1 * C1 - C1) - (eta * eta) * laplacian3(C1, h)
-    pf = phi.reshape(-1)
-    pf[geo.gcell] = mirror_value3(pf.copy(), geo)
+    phi = chemical_potential3(case, geo, C1)
     info["phi"] = phi
 
     # a5

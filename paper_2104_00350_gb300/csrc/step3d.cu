@@ -24,12 +24,14 @@ struct S3 {
   int nx, ny, nz, lnx, lny;
   T inv_h, inv_h2, dt, S, inv_eta2, pe_eta2, inv_dt, eta2;
   T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
+  T inv_pe;   // 1/Pe (explicit Cahn-Hilliard variant)
   double k_wet, cos_th, l_s;
   // fields (level cur is n)
   const T* C;    // C^n
   const T* Co;   // C^{n-1}
   T* C1;         // C^{n+1} (the C^{n-1} slot after the solve)
   T* C1lo;
+  const T* Clo;  // low part of C^n (FP32 form)
   const T *U, *V, *W, *Uo, *Vo, *Wo;   // u^n, u^{n-1}
   T *Us, *Vs, *Ws;                     // u** and then u^{n+1} (the n-1 slots)
   T *Hu, *Hv, *Hw;
@@ -301,6 +303,142 @@ __global__ void __launch_bounds__(kTQ) k3_correct_q(S3<float> a) {
 #pragma unroll
   for (int e = 1; e < 4; ++e) pair_add(hi, lsum, c0.e[e], lo.e[e]);
   tile_mass<float, kTQ>(hi, lsum, (int)blockIdx.x, (int)gridDim.x, a.partial, a.ticket, a.mass);
+}
+
+// ------------------------------------- a1 + a2, explicit variant (Eq. ExpCH), 3D
+// The 2D variant with the third axis: C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),
+// F = -div(u C_f) + (1/Pe) lap(phi), F^{n-1} from the level n-1 fields, phi at both levels
+// with their ghost fills.  k3x_phi2 writes phi^n -> phi, phi^{n-1} -> rhs and
+// A^{n-1} = -div(u^{n-1} C^{n-1}_f) -> Q; k3x_fill2 fills the ghosts of phi and rhs;
+// k3x_update writes C^{n+1} into the C^{n-1} slot (compensated in FP32), reading C^{n-1}
+// only through Q and rhs.  FP64: one thread per cell; FP32: runs of four cells.
+constexpr int kTX = 256;
+
+template <typename T>
+__device__ __forceinline__ T lap7x(const S3<T>& a, const T* __restrict__ f, const Nbr& n) {
+  return ((((f[n.xp] + f[n.xm]) + (f[n.yp] + f[n.ym])) + (f[n.zp] + f[n.zm])) - T(6) * f[n.c]) *
+         a.inv_h2;
+}
+
+template <typename T>
+__device__ __forceinline__ T flux_div3(const S3<T>& a, const T* __restrict__ C, const T* __restrict__ u,
+                                       const T* __restrict__ v, const T* __restrict__ w,
+                                       const Nbr& n, int k) {
+  const size_t c = n.c, nxy = (size_t)a.nx * a.ny;
+  const T c0 = C[c];
+  const T fx_w = u[c] * (T(0.5) * (C[n.xm] + c0));
+  const T fx_e = u[n.xp] * (T(0.5) * (c0 + C[n.xp]));
+  const T fy_s = v[c] * (T(0.5) * (C[n.ym] + c0));
+  const T fy_n = v[n.yp] * (T(0.5) * (c0 + C[n.yp]));
+  const T fz_b = k > 0 ? w[c] * (T(0.5) * (C[c - nxy] + c0)) : T(0);
+  const T fz_t = k < a.nz - 1 ? w[c + nxy] * (T(0.5) * (c0 + C[c + nxy])) : T(0);
+  return ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTX) k3x_phi2(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kTX + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const Nbr n = nbr(a, c, i, j, k);
+  const T cn = a.C[c], co = a.Co[c];
+  const T pn = (cn * cn * cn - cn) - a.eta2 * lap7x(a, a.C, n);
+  const T po = (co * co * co - co) - a.eta2 * lap7x(a, a.Co, n);
+  const T ao = -flux_div3(a, a.Co, a.Uo, a.Vo, a.Wo, n, k);
+  a.phi[c] = pn;
+  a.rhs[c] = po;
+  a.Q[c] = ao;
+}
+
+template <typename T>
+__global__ void k3x_fill2(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
+  a.rhs[t.gcell[g]] = T(2) * gather7(a.rhs, t.ap1, t.w1, g) - gather7(a.rhs, t.ap2, t.w2, g);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTX) k3x_update(S3<T> a) {
+  const size_t c = (size_t)blockIdx.x * kTX + threadIdx.x;
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const Nbr n = nbr(a, c, i, j, k);
+  const T Fn = -flux_div3(a, a.C, a.U, a.V, a.W, n, k) + lap7x(a, a.phi, n) * a.inv_pe;
+  const T Fo = a.Q[c] + lap7x(a, a.rhs, n) * a.inv_pe;
+  T hi = a.C[c], lo = a.Clo ? a.Clo[c] : T(0);
+  pair_add(hi, lo, a.dt * (T(1.5) * Fn - T(0.5) * Fo), T(0));
+  a.C1[c] = hi;
+  if (a.C1lo) a.C1lo[c] = lo;
+}
+
+// FP32: runs of four cells
+__device__ __forceinline__ float flux_div3q(const S3<float>& a, const Run& d, const V4& c, const X2& cx,
+                                            const V4& cyp, const V4& cym, const V4& czp, const V4& czm,
+                                            const V4& u, const X2& ux, const V4& v, const V4& vn,
+                                            const V4& w, const V4& wt, int e) {
+  const float c0 = c.e[e];
+  const float fx_w = u.e[e] * (0.5f * (left(c, cx, e) + c0));
+  const float fx_e = right(u, ux, e) * (0.5f * (c0 + right(c, cx, e)));
+  const float fy_s = v.e[e] * (0.5f * (cym.e[e] + c0));
+  const float fy_n = vn.e[e] * (0.5f * (c0 + cyp.e[e]));
+  const float fz_b = d.k > 0 ? w.e[e] * (0.5f * (czm.e[e] + c0)) : 0.0f;
+  const float fz_t = d.k < a.nz - 1 ? wt.e[e] * (0.5f * (c0 + czp.e[e])) : 0.0f;
+  return ((fx_e - fx_w) * a.inv_h + (fy_n - fy_s) * a.inv_h) + (fz_t - fz_b) * a.inv_h;
+}
+
+__global__ void __launch_bounds__(kTQ) k3x_phi2_q(S3<float> a) {
+  const Run d = run4(a);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  const V4 c = ld4(a.C, d.q), cyp = ld4(a.C, d.yp), cym = ld4(a.C, d.ym), czp = ld4(a.C, d.zp), czm = ld4(a.C, d.zm);
+  const V4 o = ld4(a.Co, d.q), oyp = ld4(a.Co, d.yp), oym = ld4(a.Co, d.ym), ozp = ld4(a.Co, d.zp), ozm = ld4(a.Co, d.zm);
+  const V4 u = ld4(a.Uo, d.q), v = ld4(a.Vo, d.q), vn = ld4(a.Vo, d.yp);
+  const V4 w = ld4(a.Wo, d.q), wt = ld4(a.Wo, d.q + nxy);
+  const X2 cx = xnb(c, d, a.nx, [&](size_t q) { return a.C[q]; });
+  const X2 ox = xnb(o, d, a.nx, [&](size_t q) { return a.Co[q]; });
+  const X2 ux = xnb(u, d, a.nx, [&](size_t q) { return a.Uo[q]; });
+  const V4 pn = map4([&](int e) {
+    const float c0 = c.e[e];
+    return (c0 * c0 * c0 - c0) - a.eta2 * lap7q(a, c, cx, cyp, cym, czp, czm, e);
+  });
+  const V4 po = map4([&](int e) {
+    const float c0 = o.e[e];
+    return (c0 * c0 * c0 - c0) - a.eta2 * lap7q(a, o, ox, oyp, oym, ozp, ozm, e);
+  });
+  const V4 ao = map4([&](int e) { return -flux_div3q(a, d, o, ox, oyp, oym, ozp, ozm, u, ux, v, vn, w, wt, e); });
+  st4(a.phi, d.q, pn);
+  st4(a.rhs, d.q, po);
+  st4(a.Q, d.q, ao);
+}
+
+__global__ void __launch_bounds__(kTQ) k3x_update_q(S3<float> a) {
+  const Run d = run4(a);
+  const size_t nxy = (size_t)a.nx * a.ny;
+  const V4 c = ld4(a.C, d.q), cyp = ld4(a.C, d.yp), cym = ld4(a.C, d.ym), czp = ld4(a.C, d.zp), czm = ld4(a.C, d.zm);
+  const V4 u = ld4(a.U, d.q), v = ld4(a.V, d.q), vn = ld4(a.V, d.yp);
+  const V4 w = ld4(a.W, d.q), wt = ld4(a.W, d.q + nxy);
+  const V4 f = ld4(a.phi, d.q), fyp = ld4(a.phi, d.yp), fym = ld4(a.phi, d.ym), fzp = ld4(a.phi, d.zp), fzm = ld4(a.phi, d.zm);
+  const V4 g = ld4(a.rhs, d.q), gyp = ld4(a.rhs, d.yp), gym = ld4(a.rhs, d.ym), gzp = ld4(a.rhs, d.zp), gzm = ld4(a.rhs, d.zm);
+  const V4 ao = ld4(a.Q, d.q);
+  const V4 lo = a.Clo ? ld4(a.Clo, d.q) : V4{{0.0f, 0.0f, 0.0f, 0.0f}};
+  const X2 cx = xnb(c, d, a.nx, [&](size_t q) { return a.C[q]; });
+  const X2 ux = xnb(u, d, a.nx, [&](size_t q) { return a.U[q]; });
+  const X2 fx = xnb(f, d, a.nx, [&](size_t q) { return a.phi[q]; });
+  const X2 gx = xnb(g, d, a.nx, [&](size_t q) { return a.rhs[q]; });
+  V4 hi, nlo;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float Fn = -flux_div3q(a, d, c, cx, cyp, cym, czp, czm, u, ux, v, vn, w, wt, e) +
+                     lap7q(a, f, fx, fyp, fym, fzp, fzm, e) * a.inv_pe;
+    const float Fo = ao.e[e] + lap7q(a, g, gx, gyp, gym, gzp, gzm, e) * a.inv_pe;
+    float h = c.e[e], l = lo.e[e];
+    pair_add(h, l, a.dt * (1.5f * Fn - 0.5f * Fo), 0.0f);
+    hi.e[e] = h;
+    nlo.e[e] = l;
+  }
+  st4(a.C1, d.q, hi);
+  if (a.C1lo) st4(a.C1lo, d.q, nlo);
 }
 
 // ------------------------------------------------- a5: AB2 predictor + penalisation (3D)
@@ -992,6 +1130,7 @@ S3<T> make3(const Instance& in, int cur) {
   a.S = (T)p.S;
   a.inv_eta2 = (T)(1.0 / eta2);
   a.pe_eta2 = (T)(p.Pe / eta2);
+  a.inv_pe = (T)(1.0 / p.Pe);
   a.inv_dt = (T)(1.0 / p.dt);
   a.eta2 = (T)eta2;
   const double rho_l = 1.0, rho_g = 1.0 / p.rho_ratio, mu_l = 1.0, mu_g = 1.0 / p.mu_ratio;
@@ -1012,6 +1151,7 @@ S3<T> make3(const Instance& in, int cur) {
   a.Co = (const T*)in.C[o];
   a.C1 = (T*)in.C[o];
   a.C1lo = (T*)in.Clo[o];
+  a.Clo = (const T*)in.Clo[n];
   a.U = (const T*)in.U[n];
   a.V = (const T*)in.V[n];
   a.W = (const T*)in.W[n];
@@ -1070,13 +1210,27 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
     // FP32: four cells per thread; FP64: z-marching (each the faster form on GB300)
     const unsigned nb = (unsigned)(((size_t)in.nx * in.ny * in.nz) / (4 * kTQ));
     constexpr bool percell = sizeof(T) == 4;
-    if constexpr (percell) k3_ch_h_q<<<nb, kTQ, 0, s>>>(a);
-    else k3_ch_h_z<T><<<zg, zb, 0, s>>>(a);
-    mark("ch_h");
-    if constexpr (percell) k3_ch_rhs_q<<<nb, kTQ, 0, s>>>(a);
-    else k3_ch_rhs_z<T><<<zg, zb, 0, s>>>(a);
-    mark("ch_rhs");
-    launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
+    if (ctx.ch_scheme == IB_PF_CH_EXPLICIT) {
+      const unsigned nbx = (unsigned)(((size_t)in.nx * in.ny * in.nz) / kTX);
+      if constexpr (percell) k3x_phi2_q<<<nb, kTQ, 0, s>>>(a);
+      else k3x_phi2<T><<<nbx, kTX, 0, s>>>(a);
+      mark("ch_phi2");
+      if (ng > 0) {
+        k3x_fill2<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+        mark("ch_fill2");
+      }
+      if constexpr (percell) k3x_update_q<<<nb, kTQ, 0, s>>>(a);
+      else k3x_update<T><<<nbx, kTX, 0, s>>>(a);
+      mark("ch_explicit");
+    } else {
+      if constexpr (percell) k3_ch_h_q<<<nb, kTQ, 0, s>>>(a);
+      else k3_ch_h_z<T><<<zg, zb, 0, s>>>(a);
+      mark("ch_h");
+      if constexpr (percell) k3_ch_rhs_q<<<nb, kTQ, 0, s>>>(a);
+      else k3_ch_rhs_z<T><<<zg, zb, 0, s>>>(a);
+      mark("ch_rhs");
+      launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
+    }
     if (ng > 0) {
       k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
       mark("fill_C");

@@ -106,11 +106,6 @@ def test_ch_scheme_checked_on_host(lib):
     with pytest.raises(lib.IbPfError) as ei:
         lib.ib_pf_init_geometry(g, w, p)
     assert ei.value.status == lib.E_ARG
-    g3, w3, p3 = _args3(lib)
-    p3[0].ch_scheme = lib.CH_EXPLICIT                    # explicit variant: 2D only
-    with pytest.raises(lib.IbPfError) as ei:
-        lib.ib_pf_init_geometry(g3, w3, p3)
-    assert ei.value.status == -2
     ga, wa, pa = _args(lib)
     gb, wb, pb = _args(lib)
     pb[0].ch_scheme = lib.CH_EXPLICIT                    # one scheme per context

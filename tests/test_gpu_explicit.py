@@ -114,3 +114,54 @@ def test_explicit_fp32_run_bounds_vs_fp64_path(ibpf):
         s.close()
     errs = {k: _rel(out[ibpf.FP32][k], out[ibpf.FP64][k]) for k in ("C", "u", "v")}
     assert errs["C"] <= 1e-5 and max(errs["u"], errs["v"]) <= 1e-4, errs
+
+
+# ---------------------------------------------------------------------------- 3D
+CASES3 = {
+    "sphere32": lambda: _explicit(W.small_sphere_case(32)),
+    "flat3d": lambda: _explicit(W.flat_wall_case3d(nx=32, ny=16, nz=16, wall_z=0.37, l_s=0.01)),
+}
+FIELDS3 = ("C", "u", "v", "w", "P", "Hu", "Hv", "Hw", "C_old", "w_old")
+
+
+@pytest.mark.parametrize("name", list(CASES3))
+def test_explicit_step_parity_3d_fp64(ibpf, name):
+    from oracle import ib_pf3d as O3
+    case = CASES3[name]()
+    geo = O3.build_geometry3(case)
+    st = W.random_state3d(case, seed=23)
+    ref, _ = O3.step3(case, geo, st)
+    s = ibpf.solver_from_cases([case], ibpf.FP64)
+    s.precompute_weights()
+    s.write_state(st)
+    s.step(1)
+    out = s.read_state()
+    s.close()
+    bad = {}
+    for k in FIELDS3:
+        a, b = out[k], ref[k]
+        if k == "P":
+            a, b = a - a.mean(), b - b.mean()
+        e = _rel(a, b)
+        if not e <= TOL64:
+            bad[k] = e
+    assert not bad, bad
+
+
+def test_explicit_3d_fp32_run_bounds_vs_fp64_path(ibpf):
+    case = _explicit(W.small_sphere_case(64))
+    st = W.initial_state3d(case)
+    out = {}
+    for prec in (ibpf.FP64, ibpf.FP32):
+        s = ibpf.solver_from_cases([case], prec)
+        s.precompute_weights()
+        s.write_state(st)
+        s.step(400)
+        assert s.query(ibpf.Q_STATUS) == 0.0
+        d = {k: v.astype(np.float64) for k, v in s.read_state().items()}
+        if prec == ibpf.FP32:
+            d["C"] = d["C"] + s.read("C_lo").astype(np.float64)
+        out[prec] = d
+        s.close()
+    errs = {k: _rel(out[ibpf.FP32][k], out[ibpf.FP64][k]) for k in ("C", "u", "v", "w")}
+    assert errs["C"] <= 1e-5 and max(errs["u"], errs["v"], errs["w"]) <= 1e-4, errs

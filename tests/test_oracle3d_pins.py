@@ -1,9 +1,10 @@
 """Pins of the 3D CPU oracle against what the paper and the mathematics fix.
 
 * a 3D step with no solid and data invariant along y (or along x) is the 2D step of the
-  remaining plane: the 2D oracle is pinned on its own (test_oracle_pins), so this pins
-  every stencil, both solves, the momentum terms, the projection and the correction of the
-  3D oracle, including the index conventions of each axis;
+  remaining plane: the 2D oracle is pinned on its own (test_oracle_pins,
+  test_oracle_explicit_pins), so this pins every stencil, both solves (or the explicit
+  Cahn-Hilliard update), the momentum terms, the projection and the correction of the 3D
+  oracle, including the index conventions of each axis;
 * the eigen-solves against a dense brute-force matrix of the 7-point operator;
 * the pre-fill mass invariant of the CH solve and a divergence-free velocity after the
   projection;
@@ -57,8 +58,9 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("axis", ["y", "x"])
-def test_step_reduces_to_2d_plane(axis):
+@pytest.mark.parametrize("axis,scheme", [("y", 0), ("x", 0), ("y", 1), ("x", 1)])
+def test_step_reduces_to_2d_plane(axis, scheme):
+    import dataclasses
     rng = np.random.default_rng(17)
     n1, n2, nrep = 16, 8, 4
     if axis == "y":      # data varies in (x, z), constant along y
@@ -67,6 +69,7 @@ def test_step_reduces_to_2d_plane(axis):
         c3 = _free3d(nrep, n1, n2)
         c3 = W.Case3D(c3.name, nrep, n1, n2, nrep * c3.h, n1 * c3.h, n2 * c3.h, c3.geom_kind,
                       c3.geom_p, c3.drop_c, c3.drop_r, c3.params, 1)
+    c3 = dataclasses.replace(c3, params=dataclasses.replace(c3.params, ch_scheme=scheme))
     c2 = _case2d_like(c3, n1, n2, n1 * c3.h)
     s2 = _plane_state(rng, n1, n2)
     zero3 = np.zeros((n2, c3.ny, c3.nx))
@@ -195,3 +198,14 @@ def test_slip_vector_form_matches_2d():
     u3, v3, w3 = O3.slip_ghost3(c3, uM, np.zeros(ng), vM, n3, gamma, dn)
     assert np.abs(u3 - u2).max() < 1e-13 and np.abs(w3 - v2).max() < 1e-13
     assert np.abs(v3).max() == 0.0
+
+
+def test_explicit_update_conserves_sum_before_fill_3d():
+    import dataclasses
+    case = W.small_sphere_case(16)
+    case = dataclasses.replace(case, params=dataclasses.replace(case.params, ch_scheme=1))
+    geo = O3.build_geometry3(case)
+    assert len(geo.gcell) > 0
+    st = W.random_state3d(case, seed=9)
+    C_pre = O3.ch_explicit3(case, geo, st)
+    assert abs(C_pre.sum() - st["C"].sum()) <= 1e-13 * np.abs(st["C"]).sum()
