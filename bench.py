@@ -76,6 +76,8 @@ KERNEL_STEP_WORDS_3D = {
     "predict": (17, 14, 3),      # C, phi, u, v, w, H (3) -> H (3), u**, v**, w**; alpha (3)
     "poisson_rhs": (8, 8, 0),    # C, P, Po, u**, v**, w** -> rhs, P^
     "correct": (10, 9, 0),       # C (+ lo), dP, P^, u**, v**, w** -> u, v, w
+    "ch_phi2": (9, 9, 0),        # C, Co, uo, vo, wo -> phi^n, phi^{n-1}, A^{n-1}
+    "ch_explicit": (11, 9, 0),   # C (+ lo), u, v, w, phi^n, phi^{n-1}, A^{n-1} -> C (+ lo)
 }
 
 
@@ -322,13 +324,18 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
 
 
 def run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps):
-    """The 3D workloads: droplet on a sphere, 256^3 (FP32 and FP64 forms), and droplet over a
-    random sphere packing, 512^3 (FP32 form); both larger than L2, so no flush is needed.
-    Each line: throughput over `steps` steps (at most 20) and the per-kernel roofline of a
-    second, event-instrumented pass."""
+    """The 3D workloads: droplet on a sphere, 256^3 (FP32 and FP64 forms; also with the
+    explicit Cahn-Hilliard variant, FP32), and droplet over a random sphere packing, 512^3
+    (FP32 form); all larger than L2, so no flush is needed.  Each line: throughput over
+    `steps` steps (at most 20) and the per-kernel roofline of a second, event-instrumented
+    pass."""
+    import dataclasses
     import numpy as np
     out = {}
-    jobs = [("sphere_256", W.sphere_case(256), ("fp32", "fp64")),
+    sph = W.sphere_case(256)
+    sph_x = dataclasses.replace(sph, params=dataclasses.replace(sph.params, ch_scheme=1))
+    jobs = [("sphere_256", sph, ("fp32", "fp64")),
+            ("sphere_256_explicit", sph_x, ("fp32",)),
             ("porous_512", W.porous_case(512), ("fp32",))]
     for name, case, forms in jobs:
         for form in forms:

@@ -1,11 +1,12 @@
 """Run one of the synthetic workloads for a number of steps (a driver for profilers).
 
-    python -m paper_2104_00350_gb300.run --case sphere --n 128 --steps 2 --precision fp32
+    python -m paper_2104_00350_gb300.run --case sphere --n 128 --steps 2 --precision fp32 [--explicit]
 
 Cases: ``sphere`` (droplet on a sphere, n^3), ``porous`` (droplet over a sphere packing,
 n^3), ``sinusoid`` (the six 512 x 256 sinusoidal-wall runs), ``ensemble`` (the 64-instance
-2D ensemble).  The initial droplet is written, the step runs ``--steps`` times, and the
-status word and the launch count are printed.
+2D ensemble).  ``--explicit`` selects the explicit Cahn-Hilliard variant (Eq. ExpCH).
+The initial droplet is written, the step runs ``--steps`` times, and the status word and
+the launch count are printed.
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128, help="cells per axis (3D cases)")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--explicit", action="store_true", help="explicit Cahn-Hilliard variant")
     args = ap.parse_args(argv)
     from paper_2104_00350_gb300 import build
     build.build()
@@ -41,6 +43,9 @@ def main(argv=None):
         cl = [W.sinusoid_wall_512x256(t, l) for t in (45.0, 90.0, 135.0) for l in (0.0, 0.01)]
     else:
         cl = W.ensemble_2d(64)
+    if args.explicit:
+        import dataclasses
+        cl = [dataclasses.replace(c, params=dataclasses.replace(c.params, ch_scheme=1)) for c in cl]
     s = ibpf.solver_from_cases(cl, prec)
     s.precompute_weights()
     for k, c in enumerate(cl):
