@@ -81,6 +81,17 @@ KERNEL_STEP_WORDS_3D = {
 }
 
 
+def explicit_words(table: dict, axes: tuple) -> dict:
+    """The words table of a step with the explicit Cahn-Hilliard variant: the transforms run
+    once (Poisson only), so half of their two-launch words, and rows_inv keeps only its
+    Poisson part (spectrum, P^ -> dP, P)."""
+    w = dict(table)
+    for k in axes:
+        w[k] = tuple(x // 2 for x in table[k])
+    w["rows_inv"] = (4, 4, 0)
+    return w
+
+
 def kernel_step_bytes(name: str, esz: int, cells: int, table=None) -> float:
     w32, w64, g = (KERNEL_STEP_WORDS if table is None else table).get(name, (0, 0, 0))
     return float((w32 * 4 if esz == 4 else w64 * 8 + g * 8) * cells)
@@ -295,6 +306,7 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
     """Roofline of the dominant kernel and per-kernel table from an event-timed pass:
     ktot[name] = total ms over `steps` steps, kcount[name] = launches.  FP64 2D lines are
     reported against the FP64 pipe, every other line against HBM bandwidth."""
+    alu = esz == 8 and (words is None or words.get("cols_solve") is not None)
     words = KERNEL_STEP_WORDS if words is None else words
     dom = max(ktot, key=ktot.get)
     per_launch_ms = ktot[dom] / kcount[dom]
@@ -302,11 +314,11 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
     table = {}
     for k, v in sorted(ktot.items(), key=lambda x: -x[1]):
         ent = {"us_per_step": round(1e3 * v / steps, 2), "share": round(v / tot, 4)}
-        if (esz == 4 or words is not KERNEL_STEP_WORDS) and k in words:
+        if not alu and k in words:
             gbs = kernel_step_bytes(k, esz, cells, words) * steps / (v * 1e-3) / 1e9
             ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
         table[k] = ent
-    if esz == 4 or words is not KERNEL_STEP_WORDS:
+    if not alu:
         alg = kernel_step_bytes(dom, esz, cells, words) * steps / kcount[dom]
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -371,8 +383,11 @@ def run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, ti
                 torch.cuda.synchronize()
                 _, ktot, kcount = timed_steps(s, n, collect_kernels=True)
                 ibpf.ib_pf_set_kernel_timing(s.ctx, False)
+                words = KERNEL_STEP_WORDS_3D
+                if getattr(case.params, "ch_scheme", 0) == 1:
+                    words = explicit_words(words, ("rows_fwd", "y_fft", "z_solve", "y_ifft"))
                 line["roofline"] = roofline(ktot, kcount, n, case.cells, esz, case, peak, peak_kind,
-                                            form, KERNEL_STEP_WORDS_3D, workload=name)
+                                            form, words, workload=name)
             except Exception as exc:
                 line["roofline"] = {"error": str(exc)[:200]}
             line["status"] = s.query(ibpf.Q_STATUS)
@@ -575,6 +590,7 @@ def run_ours(args):
                 _, ktot, kcount = timed_steps(xs, xsteps, collect_kernels=True)
                 ibpf.ib_pf_set_kernel_timing(xs.ctx, False)
                 xroof = roofline(ktot, kcount, xsteps, cells, esz, xcl[0], peak, peak_kind, form,
+                                 explicit_words(KERNEL_STEP_WORDS, ("rows_fwd", "cols_solve")),
                                  workload="sinusoid_512x256x6_explicit")
             except Exception as exc:
                 xroof = {"error": str(exc)[:200]}
