@@ -165,3 +165,27 @@ def test_explicit_3d_fp32_run_bounds_vs_fp64_path(ibpf):
         s.close()
     errs = {k: _rel(out[ibpf.FP32][k], out[ibpf.FP64][k]) for k in ("C", "u", "v", "w")}
     assert errs["C"] <= 1e-5 and max(errs["u"], errs["v"], errs["w"]) <= 1e-4, errs
+
+
+def test_explicit_batched_ensemble_fp32_bounds_vs_fp64(ibpf):
+    # the FP32 form of the explicit variant on an uneven batch, 200 steps from the droplet
+    ens = [_explicit(c) for c in W.ensemble_2d(64)[:8]]
+    out = {}
+    for prec in (ibpf.FP64, ibpf.FP32):
+        s = ibpf.solver_from_cases(ens, prec)
+        s.precompute_weights()
+        for k, c in enumerate(ens):
+            s.write_state(W.initial_state(c), k)
+        s.step(200)
+        out[prec] = []
+        for k in range(len(ens)):
+            assert s.query(ibpf.Q_STATUS, k) == 0.0
+            d = {f: v.astype(np.float64) for f, v in s.read_state(k).items()}
+            if prec == ibpf.FP32:
+                d["C"] = d["C"] + s.read("C_lo", k).astype(np.float64)
+            out[prec].append(d)
+        s.close()
+    for k in range(len(ens)):
+        a, b = out[ibpf.FP32][k], out[ibpf.FP64][k]
+        assert _rel(a["C"], b["C"]) <= 1e-5, k
+        assert max(_rel(a["u"], b["u"]), _rel(a["v"], b["v"])) <= 1e-4, k
