@@ -4,9 +4,11 @@
  * (Shahmardi, Rosti, Tammisola & Brandt, arXiv 2104.00350).
  *
  * One call of ib_pf_step advances every instance of a context by one or more time
- * steps of the semi-implicit scheme (Sec. 4.2 and Appendix A):
+ * steps of the scheme of Sec. 4.2 and Appendix A:
  *   a1 Cahn-Hilliard right-hand side            (Appendix A.1, Eq. Helmholtz1)
  *   a2 the two Helmholtz solves, one eigenbasis (Eqs. Helmholtz1, Helmholtz2)
+ *      (a1 + a2 are the explicit AB2 update of Eq. ExpCH instead when
+ *       ib_pf_params.ch_scheme = IB_PF_CH_EXPLICIT)
  *   a3 contact-angle ghost fill of C            (Eqs. interpolationAtWall, ProjectingToNT,
  *                                                UpdateC, static form of Eq. WallBCS)
  *   a4 chemical potential + ghost fill          (Eq. Chemical-Potential, Sec. 4.2.2)
