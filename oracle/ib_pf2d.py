@@ -61,6 +61,21 @@ restatement, with the CUDA path):
       Eq. PressurePoisson rests on rho >= rho0 = min(rho_l, rho_g), which an unclamped
       linear law breaks wherever C overshoots -1 (observed inside the solid, where it ended
       runs after ~1e4 steps).
+  R16 No flux through the immersed wall in the semi-implicit CH step.  The wall condition
+      d(phi)/dn = 0 (Eq. AllBCs, second line; imposed by phi_G = phi_M, Sec. 4.2.2) enters
+      the explicit part of the Appendix A.1 split: its right-hand side holds lap(phi~)/Cn^2
+      with phi~ = psi'(C~) - Cn^2 lap(C~) ghost-filled, and only the stabilisation of the
+      increment C^{n+1} - C~ stays implicit across the wall.  Appendix A.1 solves on the
+      whole box with Neumann conditions at the box walls only; without this term C
+      diffuses through the ghost layer into and out of the solid and a droplet settled 7 deg
+      off the prescribed angle (52.9 deg for 60).
+  R17 Averaging weights (Eq. weright averaged): the normalised 1/h_i^2 weights w_i are made
+      linear-exact by moving least squares with a linear basis and the same weight
+      function: xb = sum w_i d_i, S = sum w_i (d_i - xb)(d_i - xb)^T, W_i = w_i (1 + (d_i - xb)
+      . S^{-1}(-xb)) (d_i: offset from the IP in cells), when the kept averaging points are
+      not all on one line (else the plain weights).  Plain Shepard weights reproduce
+      constants only; their first-order error moved the settled angle by 2-3 deg at
+      Cn/h = 1.28.  params.weights = 1 selects the plain weights of the paper.
   R15 Explicit CH (Eq. ExpCH) in the form of R1 and R8: the update is
       C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),  F = -div(u C_f) + (1/Pe) lap(phi),
       the convective term in divergence form (the paper writes u . grad C; equal for a
@@ -211,15 +226,40 @@ def _first_fluid_neighbour(cls, i, j):
     return None
 
 
+def spans_plane(offsets) -> bool:
+    """True when the integer stencil offsets (di, dj) of the kept averaging points are not
+    all on one line (affinely independent in 2D); decided in integers."""
+    o = [(a - offsets[0][0], b - offsets[0][1]) for a, b in offsets]
+    return any(o[p][0] * o[q][1] - o[p][1] * o[q][0] != 0
+               for p in range(len(o)) for q in range(p + 1, len(o)))
+
+
+def linear_exact_weights(w, d):
+    """Reading R17: moving-least-squares weights with a linear basis and the weight function
+    w of Eq. weright averaged (normalised, sum 1), for points at offsets d (k x D, in cells)
+    from the interpolation point.  With xb = sum w_i d_i and S = sum w_i (d_i - xb)(d_i - xb)^T
+    the weights are W_i = w_i (1 + (d_i - xb) . S^{-1} (0 - xb)); sum W_i = 1 and
+    sum W_i d_i = 0, i.e. constants and linear fields are reproduced exactly.  Shepard's
+    weights of the paper are the same construction with a constant basis (W = w)."""
+    w = np.asarray(w, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    xb = w @ d
+    e = d - xb
+    S = (e * w[:, None]).T @ e
+    v = np.linalg.solve(S, -xb)
+    return list(w * (1.0 + e @ v))
+
+
 def _averaging_points(case: Case2D, cls, px, py):
     """Cell holding (px, py) plus its 4 face neighbours; solid centres and cells outside
     the x2 range dropped; inverse-squared-distance weights, normalised (Eq. weright
-    averaged); a coincident point takes the whole weight."""
+    averaged); a coincident point takes the whole weight.  With params.weights = 0 the
+    weights are made linear-exact (reading R17) when the kept points span the plane."""
     h = case.h
     ny, nx = cls.shape
     i0 = math.floor(px / h)
     j0 = math.floor(py / h)
-    idx, d2s = [], []
+    idx, d2s, offs, rel = [], [], [], []
     for di, dj in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
         ic, jc = i0 + di, j0 + dj
         if jc < 0 or jc >= ny:
@@ -232,6 +272,8 @@ def _averaging_points(case: Case2D, cls, px, py):
         dy = cy - py
         idx.append(jc * nx + (ic % nx))
         d2s.append(dx * dx + dy * dy)
+        offs.append((di, dj))
+        rel.append((dx / h, dy / h))
     if not idx:
         return None
     tiny = (1.0e-12 * h) * (1.0e-12 * h)
@@ -244,7 +286,10 @@ def _averaging_points(case: Case2D, cls, px, py):
     q = 0.0
     for x in wr:
         q += x
-    return idx, [x / q for x in wr]
+    w = [x / q for x in wr]
+    if getattr(case.params, "weights", 0) == 0 and len(idx) >= 3 and spans_plane(offs):
+        w = linear_exact_weights(w, rel)
+    return idx, w
 
 
 def build_geometry(case: Case2D) -> Geometry2D:
@@ -434,11 +479,18 @@ def _props(case: Case2D):
     return rho, mu, min(rho_l, rho_g)
 
 
-def ch_rhs(case: Case2D, st: dict) -> np.ndarray:
+def ch_rhs(case: Case2D, geo: "Geometry2D", st: dict) -> np.ndarray:
     """a1: right-hand side Q of the combined CH solve (Appendix A.1, Eq. Helmholtz1 times
     Pe/Cn^2 in the nondimensional form of reading R1):
-    Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2],
-    C~ = 2C^n - C^{n-1}, C_check = 2C^n - C^{n-1}/2, u~ = 2u^n - u^{n-1}."""
+    Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2]
+        + lap[(phi~_wall - phi~)/Cn^2],
+    C~ = 2C^n - C^{n-1}, C_check = 2C^n - C^{n-1}/2, u~ = 2u^n - u^{n-1}.
+    The last term is reading R16: phi~ = psi'(C~) - Cn^2 lap(C~) is the chemical potential
+    of C~ on every cell and phi~_wall the same field with the wall's no-flux condition
+    d(phi)/dn = 0 (Eq. AllBCs) imposed by the ghost fill phi_G = phi_M of Sec. 4.2.2; the
+    two differ only at the ghost cells.  With it the explicit part of the split is
+    lap(phi~_wall)/Cn^2 and only the stabilisation of the increment C^{n+1} - C~ stays
+    implicit across the wall."""
     p = case.params
     h = case.h
     ny = case.ny
@@ -453,7 +505,9 @@ def ch_rhs(case: Case2D, st: dict) -> np.ndarray:
     Fy[1:ny] = vt[1:ny] * (0.5 * (Ct[:-1] + Ct[1:]))
     div = (_xp(Fx) - Fx) / h + (Fy[1:] - Fy[:-1]) / h
     g = ((Ct * Ct * Ct - Ct) - p.S * Ct) / eta2
-    return (p.Pe / eta2) * (Cc / p.dt - div) + laplacian(g, h)
+    phi_t = (Ct * Ct * Ct - Ct) - eta2 * laplacian(Ct, h)
+    phi_t_wall = chemical_potential(case, geo, Ct)
+    return (p.Pe / eta2) * (Cc / p.dt - div) + laplacian(g, h) + laplacian((phi_t_wall - phi_t) / eta2, h)
 
 
 def chemical_potential(case: Case2D, geo: "Geometry2D", C: np.ndarray) -> np.ndarray:
@@ -547,6 +601,29 @@ def slip_ghost(case: Case2D, uM, vM, n, gamma, dn):
     return VnG * n1 + VtG * n2, VnG * n2 - VtG * n1
 
 
+def face_fix(case: Case2D, geo: "Geometry2D", uss, vss, ucen, vcen, uG, vG):
+    """a6, last step (reading R10): the velocity on the faces of the face lists (alpha_f < 1,
+    touching a ghost cell) becomes the mean of its two cells' centred values, where a ghost
+    cell holds its filled value (uG, vG), a solid non-ghost cell 0 and a fluid cell its
+    centred u** (ucen, vcen) from before the fill (the last sentence of Sec. 4.3).  x1-face
+    (j, i) lies between cells (j, i-1) and (j, i); x2-face (j, i) between (j-1, i) and (j, i)."""
+    nx = case.nx
+    ucell = ucen.copy().reshape(-1)
+    vcell = vcen.copy().reshape(-1)
+    solid_flat = (geo.cls == CELL_SOLID).reshape(-1)
+    ucell[solid_flat] = 0.0
+    vcell[solid_flat] = 0.0
+    ucell[geo.gcell] = uG
+    vcell[geo.gcell] = vG
+    uss_f = uss.copy()
+    vss_f = vss.copy()
+    fu_j, fu_i = np.divmod(geo.fu, nx)
+    uss_f[fu_j, fu_i] = 0.5 * (ucell[fu_j * nx + (fu_i - 1) % nx] + ucell[fu_j * nx + fu_i])
+    fv_j, fv_i = np.divmod(geo.fv, nx)
+    vss_f[fv_j, fv_i] = 0.5 * (vcell[(fv_j - 1) * nx + fv_i] + vcell[fv_j * nx + fv_i])
+    return uss_f, vss_f
+
+
 def momentum_rhs(case: Case2D, C1: np.ndarray, u: np.ndarray, v: np.ndarray):
     """H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho) on the x1-faces (ny, nx) and the
     x2-faces (ny+1, nx; wall rows zero), with rho and mu from C1 (Eq. PredictionExp, the
@@ -591,7 +668,7 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     if getattr(p, "ch_scheme", 0) == 1:
         C_pre = ch_explicit(case, geo, st)
     else:
-        Q = ch_rhs(case, st)
+        Q = ch_rhs(case, geo, st)
         C_pre = ch_solve(case, Q)
         info["Q"] = Q
     info["C_pre"] = C_pre
@@ -636,19 +713,7 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     uM = mirror_value(ucen.reshape(-1), geo)
     vM = mirror_value(vcen.reshape(-1), geo)
     uG, vG = slip_ghost(case, uM, vM, geo.n, geo.gamma, geo.dn)
-    ucell = ucen.copy().reshape(-1)
-    vcell = vcen.copy().reshape(-1)
-    solid_flat = (geo.cls == CELL_SOLID).reshape(-1)
-    ucell[solid_flat] = 0.0
-    vcell[solid_flat] = 0.0
-    ucell[geo.gcell] = uG
-    vcell[geo.gcell] = vG
-    uss_f = uss.copy()
-    vss_f = vss.copy()
-    fu_j, fu_i = np.divmod(geo.fu, nx)
-    uss_f[fu_j, fu_i] = 0.5 * (ucell[fu_j * nx + (fu_i - 1) % nx] + ucell[fu_j * nx + fu_i])
-    fv_j, fv_i = np.divmod(geo.fv, nx)
-    vss_f[fv_j, fv_i] = 0.5 * (vcell[(fv_j - 1) * nx + fv_i] + vcell[fv_j * nx + fv_i])
+    uss_f, vss_f = face_fix(case, geo, uss, vss, ucen, vcen, uG, vG)
     info["uG"], info["vG"] = uG, vG
     info["u_ss"], info["v_ss"] = uss_f, vss_f
 

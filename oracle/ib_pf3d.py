@@ -39,7 +39,7 @@ import scipy.fft as sfft
 
 from oracle.ib_pf2d import KAPPA, GAMMA0, MARCH_DIV, MARCH_MAX, BISECT, EPS0
 from oracle.ib_pf2d import CELL_FLUID, CELL_GHOST, CELL_SOLID
-from oracle.ib_pf2d import contact_angle_ghost
+from oracle.ib_pf2d import contact_angle_ghost, linear_exact_weights
 from workloads.cases import GEOM_FLAT, GEOM_NONE, GEOM_SPHERE, GEOM_SPHERES, Case3D
 
 NSUB3 = 16     # subgrid points per direction in 3D (reading R12)
@@ -252,7 +252,7 @@ def _averaging_points3(case: Case3D, cls, px, py, pz):
     h = case.h
     nz, ny, nx = cls.shape
     i0, j0, k0 = math.floor(px / h), math.floor(py / h), math.floor(pz / h)
-    idx, d2s = [], []
+    idx, d2s, offs, rel = [], [], [], []
     for di, dj, dk in ((0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1),
                        (0, 0, -1)):
         ic, jc, kc = i0 + di, j0 + dj, k0 + dk
@@ -265,6 +265,8 @@ def _averaging_points3(case: Case3D, cls, px, py, pz):
         dz = (kc + 0.5) * h - pz
         idx.append((kc * ny + jc % ny) * nx + ic % nx)
         d2s.append((dx * dx + dy * dy) + dz * dz)
+        offs.append((di, dj, dk))
+        rel.append((dx / h, dy / h, dz / h))
     if not idx:
         return None
     tiny = (1.0e-12 * h) * (1.0e-12 * h)
@@ -277,7 +279,26 @@ def _averaging_points3(case: Case3D, cls, px, py, pz):
     s = 0.0
     for x in wr:
         s += x
-    return idx, [x / s for x in wr]
+    w = [x / s for x in wr]
+    if getattr(case.params, "weights", 0) == 0 and len(idx) >= 4 and spans_space(offs):
+        w = linear_exact_weights(w, rel)
+    return idx, w
+
+
+def spans_space(offsets) -> bool:
+    """True when the integer stencil offsets of the kept averaging points are not all in
+    one plane (affinely independent in 3D); decided in integers."""
+    o = [tuple(a - b for a, b in zip(p, offsets[0])) for p in offsets]
+    n = len(o)
+    for p in range(n):
+        for q in range(p + 1, n):
+            for r in range(q + 1, n):
+                a, b, c = o[p], o[q], o[r]
+                det = (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+                       + a[2] * (b[0] * c[1] - b[1] * c[0]))
+                if det != 0:
+                    return True
+    return False
 
 
 def classify3(case: Case3D):
@@ -465,8 +486,10 @@ def _props(case: Case3D):
     return rho, mu, min(rho_l, rho_g)
 
 
-def ch_rhs3(case: Case3D, st: dict) -> np.ndarray:
-    """a1 in 3D: Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2]."""
+def ch_rhs3(case: Case3D, geo: "Geometry3D", st: dict) -> np.ndarray:
+    """a1 in 3D: Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2]
+    + lap[(phi~_wall - phi~)/Cn^2], the last term the wall's no-flux condition on the
+    chemical potential of C~ (reading R16 of the 2D oracle)."""
     p = case.params
     h, nz = case.h, case.nz
     eta2 = p.Cn * p.Cn
@@ -482,7 +505,10 @@ def ch_rhs3(case: Case3D, st: dict) -> np.ndarray:
     Fz[1:nz] = wt[1:nz] * (0.5 * (Ct[:-1] + Ct[1:]))
     div = ((_xp(Fx) - Fx) / h + (_yp(Fy) - Fy) / h) + (Fz[1:] - Fz[:-1]) / h
     g = ((Ct * Ct * Ct - Ct) - p.S * Ct) / eta2
-    return (p.Pe / eta2) * (Cc / p.dt - div) + laplacian3(g, h)
+    phi_t = (Ct * Ct * Ct - Ct) - eta2 * laplacian3(Ct, h)
+    phi_t_wall = chemical_potential3(case, geo, Ct)
+    return ((p.Pe / eta2) * (Cc / p.dt - div) + laplacian3(g, h)
+            + laplacian3((phi_t_wall - phi_t) / eta2, h))
 
 
 def chemical_potential3(case: Case3D, geo: "Geometry3D", C: np.ndarray) -> np.ndarray:
@@ -596,7 +622,7 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     if getattr(p, "ch_scheme", 0) == 1:
         C_pre = ch_explicit3(case, geo, st)
     else:
-        Q = ch_rhs3(case, st)
+        Q = ch_rhs3(case, geo, st)
         C_pre = ch_solve3(case, Q)
         info["Q"] = Q
     info["C_pre"], info["mass_pre"] = C_pre, float(C_pre.sum())

@@ -177,9 +177,41 @@ def test_sphere_ghost_geometry():
     radial = (G - c) / np.linalg.norm(G - c, axis=1)[:, None]
     cosang = np.sum(radial * geo.n, axis=1)
     assert cosang.min() > math.cos(math.radians(15.0))
-    assert np.all(np.abs(geo.w1.sum(axis=1) - 1.0) < 1e-14)
+    assert np.all(np.abs(geo.w1.sum(axis=1) - 1.0) < 1e-13)
     assert np.all(geo.gamma > 0.0) and geo.n_fallback_ap == 0
-    assert np.all(geo.cls.reshape(-1)[geo.ap1[geo.w1 > 0]] == O3.CELL_FLUID)
+    assert np.all(geo.cls.reshape(-1)[geo.ap1[geo.w1 != 0]] == O3.CELL_FLUID)
+
+
+@pytest.mark.parametrize("weights", [0, 1])
+def test_averaging_weights_on_linear_fields_3d(weights):
+    # Default weights (reading R17): every linear field is reproduced exactly at IP1 and IP2
+    # around the sphere.  Plain inverse-distance weights (Eq. weright averaged): constants
+    # exact, linear fields with a first-order error below h |grad f|.
+    import dataclasses
+    case = W.small_sphere_case(16)
+    case = dataclasses.replace(case, params=dataclasses.replace(case.params, weights=weights))
+    geo = O3.build_geometry3(case)
+    h, n = case.h, case.nx
+    k, r = np.divmod(geo.gcell, n * n)
+    j, i = np.divmod(r, n)
+    G = np.stack([(i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h], axis=1)
+    grad = np.array([0.7, -1.1, 1.9])
+    worst = 0.0
+    for s_, ap, w in ((1, geo.ap1, geo.w1), (2, geo.ap2, geo.w2)):
+        ip = G + (geo.dn + case.params.d1 + s_ * case.params.d2)[:, None] * geo.n
+        ak, ar = np.divmod(ap, n * n)
+        aj, ai = np.divmod(ar, n)
+        A = np.stack([(ai + 0.5) * h, (aj + 0.5) * h, (ak + 0.5) * h], axis=-1)
+        # periodic x and y: each averaging point on the side of the box nearest its IP
+        A[..., :2] -= case.lx * np.round((A[..., :2] - ip[:, None, :2]) / case.lx)
+        f = 2.0 + A @ grad
+        got = (w * f).sum(axis=1)
+        assert np.allclose(w.sum(axis=1), 1.0, atol=1e-13)
+        worst = max(worst, float(np.abs(got - (2.0 + ip @ grad)).max()))
+    if weights == 0:
+        assert worst < 1e-12, worst
+    else:
+        assert 1e-3 * h < worst < h * np.linalg.norm(grad), worst
 
 
 def test_slip_vector_form_matches_2d():

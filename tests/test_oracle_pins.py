@@ -192,15 +192,41 @@ def test_geometry_flat_wall_matches_hand_derivation():
     assert set(ap2_rows) == {g["ip2_row"] - 1, g["ip2_row"], g["ip2_row"] + 1}
 
 
+def _ip_positions(case, geo, s):
+    """IP_s = G + (dn + d1 + s d2) n (Sec. 4.1.2), from the ghost centres and the tables."""
+    h, nx = case.h, case.nx
+    gx = (geo.gcell % nx + 0.5) * h
+    gy = (geo.gcell // nx + 0.5) * h
+    d = geo.dn + case.params.d1 + s * case.params.d2
+    return gx + d * geo.n[:, 0], gy + d * geo.n[:, 1]
+
+
+def _linear_gather_error(case, geo, a=3.0, b=0.7, c=1.3):
+    """max |gathered - exact| of f = a + b x + c y at IP1 and IP2, with the x1 coordinate of
+    each averaging point unwrapped to the side of the periodic box nearest the IP."""
+    h, nx = case.h, case.nx
+    err = 0.0
+    for s, ap, w in ((1, geo.ap1, geo.w1), (2, geo.ap2, geo.w2)):
+        px, py = _ip_positions(case, geo, s)
+        ax = (ap % nx + 0.5) * h
+        ax = ax - case.lx * np.round((ax - px[:, None]) / case.lx)
+        ay = (ap // nx + 0.5) * h
+        got = (w * (a + b * ax + c * ay)).sum(axis=1)
+        err = max(err, float(np.abs(got - (a + b * px + c * py)).max()))
+    return err
+
+
 def test_idw_weights_constants_and_symmetric_linear_fields():
-    # Eq. weright averaged: sum W = 1 (constants exact) on a curved wall; on the flat wall
-    # the stencil is symmetric in x1 about the IP, so fields linear in x1 are exact.
+    # Eq. weright averaged (plain inverse-distance weights, params.weights = 1): sum W = 1
+    # (constants exact) and W >= 0 on a curved wall; on the flat wall the stencil is
+    # symmetric in x1 about the IP, so fields linear in x1 are exact.
     case, _ = _random_case_state()
+    case = cases.with_params(case, weights=1)
     geo = O.build_geometry(case)
     assert np.allclose(geo.w1.sum(axis=1), 1.0, atol=1e-14)
     assert np.allclose(geo.w2.sum(axis=1), 1.0, atol=1e-14)
     assert (geo.w1 >= 0).all() and (geo.w2 >= 0).all()
-    flat = cases.flat_wall_case(nx=64, ny=32)
+    flat = cases.with_params(cases.flat_wall_case(nx=64, ny=32), weights=1)
     gf = O.build_geometry(flat)
     h = flat.h
     x = (np.arange(flat.nx) + 0.5) * h
@@ -209,6 +235,31 @@ def test_idw_weights_constants_and_symmetric_linear_fields():
     gx = (gf.gcell % flat.nx + 0.5) * h
     interior = (gf.gcell % flat.nx > 0) & (gf.gcell % flat.nx < flat.nx - 1)
     assert np.allclose(ip[interior], (3.0 + 0.7 * gx)[interior], rtol=0, atol=1e-13)
+
+
+def test_idw_weights_first_order_on_general_linear_fields():
+    # The plain inverse-distance average is not exact for a general linear field on the
+    # sinusoidal wall (asymmetric stencils): its error is first order, bounded by a fraction
+    # of h |grad f| and about halved when h is halved.
+    errs = []
+    for nx in (256, 512):
+        case = cases.with_params(cases.sinusoid_wall_512x256(nx=nx, ny=nx // 2), weights=1)
+        e = _linear_gather_error(case, O.build_geometry(case))
+        errs.append(e / (case.h * math.hypot(0.7, 1.3)))
+    assert 0.05 < errs[0] < 0.5 and 0.05 < errs[1] < 0.5, errs
+    assert abs(errs[0] / errs[1] - 1.0) < 0.25, errs     # error / h constant: first order
+
+
+@pytest.mark.parametrize("nx", [64, 256])
+def test_linear_exact_weights_reproduce_linear_fields(nx):
+    # Reading R17 (default weights): W1/W2 reproduce constants and every linear field
+    # exactly at IP1 and IP2, on the curved wall and the flat one.
+    for case in (cases.sinusoid_wall_512x256(nx=nx, ny=nx // 2), cases.flat_wall_case(nx=nx, ny=nx // 2)):
+        geo = O.build_geometry(case)
+        assert np.allclose(geo.w1.sum(axis=1), 1.0, atol=1e-13)
+        assert np.allclose(geo.w2.sum(axis=1), 1.0, atol=1e-13)
+        assert _linear_gather_error(case, geo) < 1e-12
+        assert _linear_gather_error(case, geo, a=-1.0, b=-5.0, c=2.5) < 1e-12
 
 
 def _lagrange_slope_at_I(CG, CI, CM, dn, gamma):
@@ -369,31 +420,48 @@ def test_laplace_pressure_jump():
     assert errs[1] < 0.02 and errs[0] > 2.0 * errs[1], errs
 
 
-def _fit_contact_angle(case, C, yw):
-    """Contact angle (deg, through the liquid) of the circle fitted to the C = 0 level set
-    above the wall."""
-    h = case.h
-    pts = []
-    for j in range(case.ny):
-        row = C[j]
-        y = (j + 0.5) * h
-        if y < yw + 3 * case.params.Cn:
-            continue
-        for i in range(case.nx):
-            a, b = row[i], row[(i + 1) % case.nx]
-            if a * b < 0:
-                pts.append(((i + 0.5 + a / (a - b)) * h, y))
-    for i in range(case.nx):
-        col = C[:, i]
-        x = (i + 0.5) * h
-        for j in range(case.ny - 1):
-            a, b = col[j], col[j + 1]
-            ya = (j + 0.5) * h
-            if a * b < 0 and ya > yw + 3 * case.params.Cn:
-                pts.append((x, ya + h * a / (a - b)))
-    P = np.array(pts)
-    A = np.c_[2 * P[:, 0], 2 * P[:, 1], np.ones(len(P))]
-    bvec = (P ** 2).sum(axis=1)
-    xc, yc, c = np.linalg.lstsq(A, bvec, rcond=None)[0]
-    r = math.sqrt(c + xc * xc + yc * yc)
-    return math.degrees(math.acos((yw - yc) / r))
+def test_face_fix_on_flat_wall_in_closed_form():
+    # Reading R10 on a 32 x 16 grid with the wall at x2 = 0.1 (h = 1/16): row 1 holds the
+    # ghosts, row 0 solid cells, rows >= 2 fluid.  Listed faces, derived by hand: every
+    # x1-face of row 1 (alpha_u = 0.4), and the x2-faces of rows 1 (alpha_v = 0) and 2
+    # (alpha_v = 0.9).  With distinct ghost values per column the re-interpolated faces are
+    # u(1, i) = (uG(i-1) + uG(i))/2 (periodic), v(1, i) = (0 + vG(i))/2 and
+    # v(2, i) = (vG(i) + vcen(2, i))/2; no other face changes.
+    case = cases.flat_wall_case(nx=32, ny=16)
+    geo = O.build_geometry(case)
+    nx, ny = 32, 16
+    assert np.array_equal(geo.gcell, np.arange(nx) + nx)
+    assert np.array_equal(np.sort(geo.fu), np.arange(nx) + nx)
+    assert np.array_equal(np.sort(geo.fv), np.r_[np.arange(nx) + nx, np.arange(nx) + 2 * nx])
+    rng = np.random.default_rng(5)
+    uss = rng.standard_normal((ny, nx))
+    vss = rng.standard_normal((ny + 1, nx))
+    ucen = rng.standard_normal((ny, nx))
+    vcen = rng.standard_normal((ny, nx))
+    uG = rng.standard_normal(nx)
+    vG = rng.standard_normal(nx)
+    u2, v2 = O.face_fix(case, geo, uss, vss, ucen, vcen, uG, vG)
+    i = np.arange(nx)
+    assert np.array_equal(u2[1], 0.5 * (uG[(i - 1) % nx] + uG))
+    assert np.array_equal(v2[1], 0.5 * (0.0 + vG))
+    assert np.array_equal(v2[2], 0.5 * (vG + vcen[2]))
+    keep_u = np.ones((ny, nx), bool)
+    keep_u[1] = False
+    keep_v = np.ones((ny + 1, nx), bool)
+    keep_v[1:3] = False
+    assert np.array_equal(u2[keep_u], uss[keep_u]) and np.array_equal(v2[keep_v], vss[keep_v])
+
+
+def test_penalisation_zeroes_solid_faces_and_keeps_fluid_faces():
+    # Eq. Penalization2, u** = alpha u*: on the flat wall of the 128 x 64 case the x1-faces of
+    # rows 0..4 are wholly solid (alpha_u = 0, not re-interpolated) and those of rows >= 7
+    # wholly fluid (alpha_u = 1): u** = 0 there and u** = u* respectively.
+    case = cases.flat_wall_128x64()
+    geo = O.build_geometry(case)
+    st = cases.random_state(case, seed=21)
+    _, info = O.step(case, geo, st)
+    assert np.all(geo.alpha_u[:5] == 0.0) and np.all(geo.alpha_u[7:] == 1.0)
+    assert np.all(info["u_ss"][:5] == 0.0)
+    assert np.array_equal(info["u_ss"][7:], info["u_star"][7:])
+    assert np.all(info["v_ss"][:5] == 0.0)
+    assert np.array_equal(info["v_ss"][8:], info["v_star"][8:])

@@ -56,6 +56,7 @@ class Params:
     d2: float = 0.0
     dt: float = 1.0e-4
     ch_scheme: int = 0   # 0: semi-implicit CH (Appendix A.1); 1: explicit AB2 (Eq. ExpCH)
+    weights: int = 0     # averaging weights: 0 linear-exact (default), 1 plain inverse-distance
 
 
 @dataclass(frozen=True)
