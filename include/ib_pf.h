@@ -75,6 +75,16 @@ typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
  * (D = 2 or 3), which the library does not check. */
 typedef enum { IB_PF_CH_SEMI_IMPLICIT = 0, IB_PF_CH_EXPLICIT = 1 } ib_pf_ch_scheme;
 
+/* averaging weights W1/W2 of the ghost-cell gathers (Sec. 4.1.4).  IDW: the normalised
+ * inverse-squared-distance weights of Eq. weright averaged (Shepard's average: constants are
+ * reproduced, linear fields only on stencils symmetric about the interpolation point).
+ * LINEAR: the same weight function with a linear basis (moving least squares,
+ * W_i = w_i (1 + (d_i - xb) . S^{-1} (-xb)), xb = sum w_i d_i, S = sum w_i (d_i - xb)(d_i - xb)^T,
+ * d_i the offset of averaging point i from the interpolation point), which reproduces
+ * linear fields exactly; where the kept averaging points are all on one line (2D) or in one
+ * plane (3D) the IDW weights are used.  LINEAR is the default (0). */
+typedef enum { IB_PF_W_LINEAR = 0, IB_PF_W_IDW = 1 } ib_pf_weights;
+
 /* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points
  * against it).  FLAT: x2 < p[0] (2D), z < p[0] (3D).  SINUSOID (2D): x2 < p[0] + p[1]
  * sin(2 pi p[2] x1).  SPHERE (3D): |x - (p[0], p[1], p[2])| < p[3].  SPHERES (3D): the union
@@ -109,6 +119,7 @@ typedef struct {
   double Re, Ca, Cn, Pe, S, rho_ratio, mu_ratio, theta_deg, l_s, mu_f, d1, d2, dt;
   int precision;  /* ib_pf_precision */
   int ch_scheme;  /* ib_pf_ch_scheme; all instances of a context share it */
+  int weights;    /* ib_pf_weights (per instance) */
 } ib_pf_params;
 
 /* field ids for read / write */

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "ibpf_internal.h"
+#include "weights.cuh"
 
 namespace ibpf {
 namespace {
@@ -160,6 +161,7 @@ struct GhostArgs {
   double* w2;
   int* n_fallback;
   int* n_fail;
+  int weights;     // ib_pf_weights
 };
 
 __device__ __forceinline__ double alpha_at(const GhostArgs& A, int i, int j) {
@@ -205,6 +207,8 @@ __device__ int averaging_points(const GhostArgs& A, double px, double py, int* i
   int i0 = (int)floor(px / A.h), j0 = (int)floor(py / A.h);
   int n = 0;
   double d2s[kNap];
+  int off[kNap][3];
+  double rel[kNap][3];
   for (int k = 0; k < kNap; ++k) {
     int ic = i0 + di[k], jc = j0 + dj[k];
     if (jc < 0 || jc >= A.ny) continue;
@@ -214,6 +218,12 @@ __device__ int averaging_points(const GhostArgs& A, double px, double py, int* i
     double dy = ((double)jc + 0.5) * A.h - py;
     idx[n] = jc * A.nx + icw;
     d2s[n] = dx * dx + dy * dy;
+    off[n][0] = di[k];
+    off[n][1] = dj[k];
+    off[n][2] = 0;
+    rel[n][0] = dx / A.h;
+    rel[n][1] = dy / A.h;
+    rel[n][2] = 0.0;
     ++n;
   }
   if (n == 0) return 0;
@@ -230,6 +240,8 @@ __device__ int averaging_points(const GhostArgs& A, double px, double py, int* i
     q += wt[k];
   }
   for (int k = 0; k < n; ++k) wt[k] = wt[k] / q;
+  if (A.weights == IB_PF_W_LINEAR && n >= 3 && stencil_spans<2>(off, n))
+    linear_exact_weights<2>(wt, rel, n);
   return n;
 }
 
@@ -408,6 +420,7 @@ cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::str
   A.w2 = t.w2;
   A.n_fallback = counters;
   A.n_fail = counters + 1;
+  A.weights = in.prm.weights;
   k_ghost_weights<<<(t.ng + 127) / 128, 128, 0, s>>>(A, t.ng);
   IBPF_TRY(cudaGetLastError());
   int h[2] = {0, 0};

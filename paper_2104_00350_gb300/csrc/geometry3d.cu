@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ibpf_internal.h"
+#include "weights.cuh"
 
 namespace ibpf {
 namespace {
@@ -234,6 +235,7 @@ struct Ghost3Args {
   double* w2;
   int* n_fail;     // ghosts without an intersect point within 10 h
   int* n_fallback;
+  int weights;     // ib_pf_weights
 };
 
 __device__ __forceinline__ double alpha_at3(const Ghost3Args& a, int i, int j, int k) {
@@ -272,6 +274,8 @@ __device__ int averaging3(const Ghost3Args& a, double px, double py, double pz, 
   const int i0 = (int)floor(px / h), j0 = (int)floor(py / h), k0 = (int)floor(pz / h);
   const int off[7][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
   double d2s[kNap3];
+  int koff[kNap3][3];
+  double rel[kNap3][3];
   int n = 0;
   for (int q = 0; q < kNap3; ++q) {
     const int ic = i0 + off[q][0], jc = j0 + off[q][1], kc = k0 + off[q][2];
@@ -282,6 +286,10 @@ __device__ int averaging3(const Ghost3Args& a, double px, double py, double pz, 
     const int im = ((ic % a.nx) + a.nx) % a.nx, jm = ((jc % a.ny) + a.ny) % a.ny;
     ap[n] = (kc * a.ny + jm) * a.nx + im;
     d2s[n] = (dx * dx + dy * dy) + dz * dz;
+    for (int k = 0; k < 3; ++k) koff[n][k] = off[q][k];
+    rel[n][0] = dx / h;
+    rel[n][1] = dy / h;
+    rel[n][2] = dz / h;
     ++n;
   }
   if (n == 0) return 0;
@@ -298,6 +306,8 @@ __device__ int averaging3(const Ghost3Args& a, double px, double py, double pz, 
     s = s + wt[q];
   }
   for (int q = 0; q < n; ++q) wt[q] = wt[q] / s;
+  if (a.weights == IB_PF_W_LINEAR && n >= 4 && stencil_spans<3>(koff, n))
+    linear_exact_weights<3>(wt, rel, n);
   return n;
 }
 
@@ -581,6 +591,7 @@ cudaError_t geometry3_weights(Instance& in, cudaStream_t s, int* n_fail, std::st
   A.h = in.h;
   A.d1 = in.prm.d1;
   A.d2 = in.prm.d2;
+  A.weights = in.prm.weights;
   A.gcell = t.gcell;
   A.cmap = t.cmap;
   A.alpha_c = t.alpha_c;

@@ -153,6 +153,10 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
     why = "unknown ch_scheme";
     return IB_PF_E_ARG;
   }
+  if (p.weights != IB_PF_W_LINEAR && p.weights != IB_PF_W_IDW) {
+    why = "unknown weights";
+    return IB_PF_E_ARG;
+  }
   if (g.dim == 3) {
     if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
     if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }

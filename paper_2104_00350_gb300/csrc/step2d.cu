@@ -136,6 +136,41 @@ __device__ __forceinline__ void fill_phi_ghost(const Tables& t, T* __restrict__ 
   phi[t.gcell[g]] = T(2) * gather(phi, t.ap1, t.w1, g) - gather(phi, t.ap2, t.w2, g);
 }
 
+// ------------------------------------------- a1, wall term: no flux of C through the wall
+// The explicit part of the split is lap(phi~)/Cn^2 with phi~ = psi'(C~) - Cn^2 lap(C~) the
+// chemical potential of C~ = 2C^n - C^{n-1}, and the wall condition d(phi)/dn = 0 of Eq.
+// AllBCs is imposed on it by the ghost fill of Sec. 4.2.2, phi~_G = phi~_M: h at a ghost cell
+// gains (phi~_M - phi~_G)/Cn^2, phi~ evaluated at the averaging points and at G from C~.
+// Only ghost entries of h change and the averaging points are fluid cells, so ghosts do not
+// read one another's results.
+template <typename T>
+__device__ __forceinline__ T phit_cell(const StepArgs<T>& a, const T* __restrict__ C,
+                                       const T* __restrict__ Co, int c) {
+  const int nx = a.nx, ny = a.ny;
+  const int i = c % nx, j = c / nx;
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  const size_t r = (size_t)j * nx;
+  auto ct = [&](size_t idx) { return T(2) * C[idx] - Co[idx]; };
+  const T c0 = ct(r + i);
+  const T lap = (((ct(r + wrap_p(i, nx)) + ct(r + wrap_m(i, nx))) +
+                  (ct((size_t)jn * nx + i) + ct((size_t)js * nx + i))) - T(4) * c0) * a.inv_h2;
+  return (c0 * c0 * c0 - c0) - a.eta2 * lap;
+}
+
+template <typename T>
+__device__ __forceinline__ void ch_wall_ghost(const StepArgs<T>& a, const Tables& t,
+                                              const T* __restrict__ C, const T* __restrict__ Co,
+                                              T* __restrict__ hf, int g) {
+  T m1 = T(0), m2 = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap; ++q) {
+    m1 = m1 + (T)t.w1[(size_t)g * kNap + q] * phit_cell(a, C, Co, t.ap1[(size_t)g * kNap + q]);
+    m2 = m2 + (T)t.w2[(size_t)g * kNap + q] * phit_cell(a, C, Co, t.ap2[(size_t)g * kNap + q]);
+  }
+  const int c = t.gcell[g];
+  hf[c] = hf[c] + ((T(2) * m1 - m2) - phit_cell(a, C, Co, c)) * a.inv_eta2;
+}
+
 // ----------------------------------------------------- a5: AB2 predictor + penalisation
 // H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho_f)
 // u* = u^n + dt (3/2 H^n - 1/2 H^{n-1} + (kappa/(Re Ca Cn)) phi_f dC/dx / rho_f)
@@ -506,6 +541,17 @@ __global__ void IBPF_CELL_BOUNDS kb_ch_rhs(const InstDev<T>* __restrict__ I, con
       if (i < d.nx && j < d.ny) d.Q[(size_t)j * d.nx + i] = out[q];
     }
   }
+}
+
+template <typename T>
+__global__ void kb_ch_wall(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
+                           int cur) {
+  const int b_ = blockIdx.x;
+  if (b_ >= nblk) return;
+  const int2 w_ = blk[b_];
+  const InstDev<T>& d = I[w_.x];
+  const int g = w_.y * kGhostChunk + threadIdx.x;
+  if (g < d.tab.ng) ch_wall_ghost(d.a, d.tab, d.C[cur], d.C[1 - cur], d.phi, g);
 }
 
 // C^{n+1} sits in slot 1 - cur after the CH solve
@@ -1113,6 +1159,10 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     if constexpr (sizeof(T) == 4) kq_ch_h<<<nc, tile, 0, s>>>(I, bc, nc, cur);
     else kb_ch_h<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
     mark("ch_h");
+    if (ng > 0) {
+      kb_ch_wall<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
+      mark("ch_wall");
+    }
     if constexpr (sizeof(T) == 4) kq_ch_rhs<<<nc, tile, 0, s>>>(I, bc, nc, cur);
     else kb_ch_rhs<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
     mark("ch_rhs");

@@ -107,6 +107,37 @@ __global__ void k3_fill_C(S3<T> a) {
   if (a.C1lo) a.C1lo[t.gcell[g]] = T(0);
 }
 
+// a1, wall term: the wall's no-flux condition d(phi)/dn = 0 (Eq. AllBCs) on the chemical
+// potential phi~ = psi'(C~) - Cn^2 lap(C~) of C~ = 2C^n - C^{n-1}, imposed by the ghost fill
+// phi~_G = phi~_M of Sec. 4.2.2: h_G += (phi~_M - phi~_G)/Cn^2 (as the 2D step; only ghost
+// entries of h change, the averaging points are fluid cells)
+template <typename T>
+__device__ __forceinline__ T phit3(const S3<T>& a, size_t c) {
+  int i, j, k;
+  cell_ijk(a, c, i, j, k);
+  const Nbr n = nbr(a, c, i, j, k);
+  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
+  const T c0 = ct(c);
+  const T lap = ((((ct(n.xp) + ct(n.xm)) + (ct(n.yp) + ct(n.ym))) + (ct(n.zp) + ct(n.zm))) -
+                 T(6) * c0) * a.inv_h2;
+  return (c0 * c0 * c0 - c0) - a.eta2 * lap;
+}
+
+template <typename T>
+__global__ void k3_ch_wall(S3<T> a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  if (g >= t.ng) return;
+  T m1 = T(0), m2 = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap3; ++q) {
+    m1 = m1 + (T)t.w1[(size_t)g * kNap3 + q] * phit3(a, (size_t)t.ap1[(size_t)g * kNap3 + q]);
+    m2 = m2 + (T)t.w2[(size_t)g * kNap3 + q] * phit3(a, (size_t)t.ap2[(size_t)g * kNap3 + q]);
+  }
+  const size_t c = (size_t)t.gcell[g];
+  a.phi[c] = a.phi[c] + ((T(2) * m1 - m2) - phit3(a, c)) * a.inv_eta2;
+}
+
 // zero normal gradient of phi at the wall: phi_G = phi_M
 template <typename T>
 __global__ void k3_fill_phi(S3<T> a) {
@@ -1226,6 +1257,10 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       if constexpr (percell) k3_ch_h_q<<<nb, kTQ, 0, s>>>(a);
       else k3_ch_h_z<T><<<zg, zb, 0, s>>>(a);
       mark("ch_h");
+      if (ng > 0) {
+        k3_ch_wall<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+        mark("ch_wall");
+      }
       if constexpr (percell) k3_ch_rhs_q<<<nb, kTQ, 0, s>>>(a);
       else k3_ch_rhs_z<T><<<zg, zb, 0, s>>>(a);
       mark("ch_rhs");

@@ -18,6 +18,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libibpf.so"
 OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0, -1, -2, -3, -4, -5, -6, -7
 FP64, FP32 = 0, 1
 CH_SEMI_IMPLICIT, CH_EXPLICIT = 0, 1
+W_LINEAR, W_IDW = 0, 1            # ib_pf_weights
 WALL_FLAT, WALL_SINUSOID, WALL_NONE, WALL_SPHERE, WALL_SPHERES = 0, 1, 3, 4, 5
 (F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P,
  F_C_LO, F_C_OLD_LO, F_W, F_W_OLD, F_HW) = range(18)
@@ -52,7 +53,8 @@ PARAM_NAMES = ("Re", "Ca", "Cn", "Pe", "S", "rho_ratio", "mu_ratio", "theta_deg"
 
 
 class Params(ct.Structure):
-    _fields_ = [(n, ct.c_double) for n in PARAM_NAMES] + [("precision", ct.c_int), ("ch_scheme", ct.c_int)]
+    _fields_ = [(n, ct.c_double) for n in PARAM_NAMES] + [("precision", ct.c_int), ("ch_scheme", ct.c_int),
+                                                         ("weights", ct.c_int)]
 
 
 class IbPfError(RuntimeError):
@@ -236,12 +238,14 @@ def make_geometry(kind: int, p, spheres=()) -> Geometry:
     return w
 
 
-def make_params(precision: int = FP64, ch_scheme: int = CH_SEMI_IMPLICIT, **kw) -> Params:
+def make_params(precision: int = FP64, ch_scheme: int = CH_SEMI_IMPLICIT, weights: int = 0,
+                **kw) -> Params:
     p = Params()
     for n in PARAM_NAMES:
         setattr(p, n, float(kw[n]))
     p.precision = precision
     p.ch_scheme = int(ch_scheme)
+    p.weights = int(weights)
     return p
 
 
@@ -392,5 +396,6 @@ def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:
              else make_grid(c.nx, c.ny, c.lx, c.ly) for c in cases]
     geoms = [make_geometry(c.geom_kind, c.geom_p, getattr(c, "spheres", ())) for c in cases]
     params = [make_params(precision, getattr(c.params, "ch_scheme", CH_SEMI_IMPLICIT),
+                          getattr(c.params, "weights", W_LINEAR),
                           **{n: getattr(c.params, n) for n in PARAM_NAMES}) for c in cases]
     return Solver(grids, geoms, params, stream)

@@ -17,6 +17,8 @@ import pytest
 from oracle import ib_pf2d as O
 from workloads import cases
 
+import wetting
+
 pytestmark = pytest.mark.gpu
 
 
@@ -53,49 +55,9 @@ def _errs(got, ref):
 
 
 def contact_angle(case, C):
-    """Apparent contact angles (deg, through the liquid) at the left and right contact
-    points: circle fitted to the C = 0 level set at least 3 Cn above the wall, angle between
-    the circle's outward normal and the wall normal where the circle meets the wall."""
-    h, nx, ny = case.h, case.nx, case.ny
-    cn = case.params.Cn
-    pts = []
-    for j in range(ny):
-        y = (j + 0.5) * h
-        row = C[j]
-        for i in range(nx):
-            a, b = row[i], row[(i + 1) % nx]
-            if a * b < 0:
-                x = (i + 0.5 + a / (a - b)) * h
-                if y > O.wall_height(case, np.array([x]))[0] + 3 * cn:
-                    pts.append((x, y))
-    for i in range(nx):
-        x = (i + 0.5) * h
-        col = C[:, i]
-        yw = O.wall_height(case, np.array([x]))[0]
-        for j in range(ny - 1):
-            a, b = col[j], col[j + 1]
-            if a * b < 0:
-                y = (j + 0.5 + a / (a - b)) * h
-                if y > yw + 3 * cn:
-                    pts.append((x, y))
-    P = np.array(pts)
-    A = np.c_[2 * P[:, 0], 2 * P[:, 1], np.ones(len(P))]
-    xc, yc, c = np.linalg.lstsq(A, (P ** 2).sum(axis=1), rcond=None)[0]
-    r = math.sqrt(c + xc * xc + yc * yc)
-    xs = np.linspace(xc - r - 0.2, xc + r + 0.2, 40001)
-    f = (xs - xc) ** 2 + (O.wall_height(case, xs) - yc) ** 2 - r * r
-    roots = np.nonzero(np.sign(f[:-1]) != np.sign(f[1:]))[0]
-    angles = []
-    for k in roots:
-        x0 = xs[k] - f[k] * (xs[k + 1] - xs[k]) / (f[k + 1] - f[k])
-        y0 = O.wall_height(case, np.array([x0]))[0]
-        dx = 1e-6
-        slope = (O.wall_height(case, np.array([x0 + dx]))[0] -
-                 O.wall_height(case, np.array([x0 - dx]))[0]) / (2 * dx)
-        nw = np.array([-slope, 1.0]) / math.hypot(slope, 1.0)
-        nc = np.array([x0 - xc, y0 - yc]) / r
-        angles.append(math.degrees(math.acos(np.clip(nc @ nw, -1.0, 1.0))))
-    return np.array(angles)
+    """Apparent contact angles (deg) at the two contact points of the circle fitted to the
+    C = 0 level set (tests/wetting.py)."""
+    return wetting.contact_angles(case, C, lambda x: float(O.wall_height(case, np.array([x]))[0]))
 
 
 def test_fp32_one_step_vs_oracle(ibpf):
@@ -148,26 +110,6 @@ def test_fp32_run_bounds_vs_fp64_path(ibpf, theta, l_s):
     assert e["C"] <= 1e-5 and e["u"] <= 1e-4 and e["v"] <= 1e-4, e
     da = np.abs(contact_angle(case, out[ibpf.FP32]["C"]) - contact_angle(case, out[ibpf.FP64]["C"]))
     assert da.shape == (2,) and da.max() < 0.1, da
-
-
-def test_droplet_relaxes_towards_the_static_angle(ibpf):
-    # A droplet started as a semicircle (90 deg) on the flat immersed wall (128 x 64,
-    # Cn = 0.02) and run to t = 5 (50000 steps, FP64 path) moves towards the prescribed
-    # static angle and stays there; at this interface resolution (Cn = 1.28 h) the apparent
-    # angle of the fitted circle settles a few degrees from theta (about 53 deg for 60 and
-    # 123.5 deg for 120), which bounds the check below.
-    for theta in (60.0, 120.0):
-        case = cases.flat_wall_case(theta_deg=theta)
-        s = _solver(ibpf, case, ibpf.FP64)
-        s.write_state(cases.initial_state(case))
-        s.step(10000)
-        a1 = contact_angle(case, s.read("C"))
-        s.step(40000)
-        a5 = contact_angle(case, s.read("C"))
-        assert s.query(ibpf.Q_STATUS) == 0.0
-        s.close()
-        assert np.all(np.abs(a1 - theta) < 3.0), (theta, a1)
-        assert np.all(np.abs(a5 - theta) < 10.0) and np.all(np.sign(a5 - 90.0) == np.sign(theta - 90.0)), (theta, a5)
 
 
 def test_fp32_flat_wall_tracks_oracle(ibpf):
