@@ -76,6 +76,22 @@ restatement, with the CUDA path):
       not all on one line (else the plain weights).  Plain Shepard weights reproduce
       constants only; their first-order error moved the settled angle by 2-3 deg at
       Cn/h = 1.28.  params.weights = 1 selects the plain weights of the paper.
+  R18 Dynamic contact angle (mu_f > 0): Eq. WallBCS_recast, nondimensional as
+      dC_I/dt = -v_t (dC/dx_t)_I + (1/(mu_f Cn)) [kappa Cn dC/dn + cos(theta) g'(C_I)]
+      (the paper's mu_f eps over sigma eps, with eps -> Cn and sigma -> 1), integrated by one
+      backward-Euler step per time step for a per-ghost state C_I (the normal derivative,
+      R4's slope (C_M - C_I)/(gamma dn), and g'(C_I) at the new level, solved as R4's
+      quadratic with modified coefficients; an explicit g' is unstable for small mu_f), the
+      advection explicit; v_t and dC/dx_t at I
+      are gamma-weighted means of the ghost's and the mirror point's values (Eq.
+      interpolationAtWall) of the level-n cell-centred velocity and of central differences
+      of C^{n+1} before the fill.  An unset C_I (NaN) starts as (gamma C^n_G + C^n_M)/(gamma+1).
+      The bracket B = kappa Cn dC/dn + cos(theta) g'(C_I) at the new level enters the slip
+      condition (Eq. UpdateVtan) as -(1/Ca) B (dC/dx_t)_I l_s (gamma+1) dn / (mu_I (l_s +
+      gamma dn)), mu_I = mu(C_I): the stress balance of Eq. SlipVelocity multiplied by Re,
+      with the surface-tension scale 1/(Re Ca) of R1 (the paper's Eq. UpdateVtan drops kappa
+      and eps).  mu_f -> 0 recovers R4's static root; mu_f -> infinity freezes C_I but for
+      advection along the wall.
   R15 Explicit CH (Eq. ExpCH) in the form of R1 and R8: the update is
       C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),  F = -div(u C_f) + (1/Pe) lap(phi),
       the convective term in divergence form (the paper writes u . grad C; equal for a
@@ -589,15 +605,87 @@ def contact_angle_ghost(case: Case2D, C_M, gamma, dn):
     return C_G, C_I, clamped
 
 
-def slip_ghost(case: Case2D, uM, vM, n, gamma, dn):
-    """a6 core: Eq. NoPenetration for the normal component, Eq. UpdateVtan (static angle,
-    reading R4) for the tangential one, Eq. UpdateVandW back to x1/x2 (reading R5)."""
+def g_prime(C):
+    """g'(C) = 3/4 (1 - C^2) of the wall-energy switch g(C) = (2 + 3C - C^3)/4 of Eq. WallBCS,
+    zero beyond the pure phases (g constant there; reading R4)."""
+    C = np.asarray(C, dtype=np.float64)
+    return np.where(np.abs(C) < 1.0, 0.75 * (1.0 - C * C), 0.0)
+
+
+def dynamic_contact_ghost(case: Case2D, C_M, gamma, dn, CI_n, adv):
+    """a3 core, dynamic angle (mu_f > 0), reading R18.  Eq. WallBCS_recast integrated over
+    one step for the per-ghost wall value C_I, implicitly in C_I:
+      (C_I^{n+1} - C_I^n)/dt = -adv + (1/(mu_f Cn)) [kappa Cn dC/dn + cos(theta) g'(C_I^{n+1})],
+    adv = v_t (dC/dx_t) at I (level-n velocity, gradient of C^{n+1} before the fill), the
+    normal derivative the slope (C_M - C_I^{n+1})/(gamma dn) of reading R4.  With
+    a = dt/(mu_f Cn), k = kappa Cn/(gamma dn) and R = C_I^n - dt adv + a k C_M this is
+      F(C) = (1 + a k) C - a cos(theta) g'(C) - R = 0,
+    linear where g' = 0 (|C| >= 1) and the quadratic (3/4) a cos C^2 + (1 + a k) C - (R + (3/4) a
+    cos) = 0 on [-1, 1].  As in the static case (reading R4): if the linear solution
+    R/(1 + a k) lies outside (-1, 1) it is taken; otherwise F(-1) < 0 < F(1) and the one root
+    of the quadratic in [-1, 1] is taken (r2 = 2c/(b + sqrt(D)) when it qualifies, else
+    r1 = -(b + sqrt(D))/(2a')).  As mu_f -> 0 this is R4's static quadratic (C_M for R/(1+ak));
+    as mu_f -> infinity C_I^{n+1} = C_I^n - dt adv.  Then C_G by Eq. UpdateC and the wetting
+    bracket B = kappa Cn dC/dn + cos(theta) g'(C_I) at the new level.
+    Returns (C_G, C_I, B)."""
+    p = case.params
+    ct = math.cos(math.radians(p.theta_deg))
+    k = KAPPA * p.Cn / (gamma * dn)
+    a = p.dt / (p.mu_f * p.Cn)
+    R = CI_n - p.dt * adv + a * k * C_M
+    qb = 1.0 + a * k
+    lin = R / qb
+    qa = 0.75 * a * ct
+    qc = R + 0.75 * a * ct
+    sq = np.sqrt(np.maximum(qb * qb + 4.0 * qa * qc, 0.0))
+    r2 = 2.0 * qc / (qb + sq)
+    if qa != 0.0:
+        r1 = -(qb + sq) / (2.0 * qa)
+        root = np.where(np.abs(r2) <= 1.0, r2, np.clip(r1, -1.0, 1.0))
+    else:
+        root = r2
+    C_I = np.where(np.abs(lin) >= 1.0, lin, root)
+    C_G = ((gamma + 1.0) * C_I - C_M) / gamma
+    B = k * (C_M - C_I) + ct * g_prime(C_I)
+    return C_G, C_I, B
+
+
+def cell_gradient(case: Case2D, C):
+    """Central differences of a cell field at the cell centres (periodic x1; zero-gradient
+    mirror rows at the x2 walls, reading R8)."""
+    h = case.h
+    return (_xp(C) - _xm(C)) / (2.0 * h), (_yp_mirror(C) - _ym_mirror(C)) / (2.0 * h)
+
+
+def wall_advection(case: Case2D, geo: "Geometry2D", u, v, C_pre):
+    """v_t (dC/dx_t) at the intersect points and (dC/dx_t)_I (Eq. ProjectingToNT, t = (n2, -n1)):
+    the level-n cell-centred velocity and the central-difference gradient of C^{n+1} (before
+    the fill), each at I as the gamma-weighted mean of the ghost's value and the mirror value
+    (Eq. interpolationAtWall)."""
+    g, gam = geo.gcell, geo.gamma
+    at_I = lambda fld: (gam * fld.reshape(-1)[g] + mirror_value(fld.reshape(-1), geo)) / (gam + 1.0)
+    uI = at_I(0.5 * (u + _xp(u)))
+    vI = at_I(0.5 * (v[:-1] + v[1:]))
+    gx, gy = cell_gradient(case, C_pre)
+    gxI, gyI = at_I(gx), at_I(gy)
+    n1, n2 = geo.n[:, 0], geo.n[:, 1]
+    gt = gxI * n2 - gyI * n1
+    return (uI * n2 - vI * n1) * gt, gt
+
+
+def slip_ghost(case: Case2D, uM, vM, n, gamma, dn, B=None, gt=None, mu_I=None):
+    """a6 core: Eq. NoPenetration for the normal component, Eq. UpdateVtan for the tangential
+    one, Eq. UpdateVandW back to x1/x2 (reading R5).  With a dynamic angle the wetting bracket
+    B and the tangential derivative gt = (dC/dx_t)_I enter through the term
+    -(1/Ca) B gt l_s (gamma + 1) dn / (mu_I (l_s + gamma dn)) (reading R18); static: B = 0."""
     p = case.params
     n1, n2 = n[:, 0], n[:, 1]
     VnM = uM * n1 + vM * n2
     VtM = uM * n2 - vM * n1
     VnG = -VnM / gamma
     VtG = VtM * (p.l_s - dn) / (p.l_s + gamma * dn)
+    if B is not None:
+        VtG = VtG - (B * gt / p.Ca) * (p.l_s * (gamma + 1.0) * dn) / (mu_I * (p.l_s + gamma * dn))
     return VnG * n1 + VtG * n2, VnG * n2 - VtG * n1
 
 
@@ -678,10 +766,27 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     C1 = C_pre.copy()
     f = C1.reshape(-1)
     C_M = mirror_value(C_pre.reshape(-1), geo)
-    C_G, C_I, clamped = contact_angle_ghost(case, C_M, geo.gamma, geo.dn)
+    B = gt = None
+    if p.mu_f > 0.0:
+        # dynamic angle (reading R18): the wall value C_I is state; unset (NaN) it starts as
+        # the wall value of the level-n field, (gamma C^n_G + C^n_M)/(gamma + 1) (Eq.
+        # interpolationAtWall at level n)
+        g = geo.gcell
+        gam = geo.gamma
+        Cn_flat = st["C"].reshape(-1)
+        CI_n = st.get("C_I")
+        CI_n = np.full(len(g), np.nan) if CI_n is None else CI_n
+        CI_n = np.where(np.isfinite(CI_n), CI_n,
+                        (gam * Cn_flat[g] + mirror_value(Cn_flat, geo)) / (gam + 1.0))
+        adv, gt = wall_advection(case, geo, st["u"], st["v"], C_pre)
+        C_G, C_I, B = dynamic_contact_ghost(case, C_M, gam, geo.dn, CI_n, adv)
+        clamped = 0
+    else:
+        C_G, C_I, clamped = contact_angle_ghost(case, C_M, geo.gamma, geo.dn)
     f[geo.gcell] = C_G
     info["C"] = C1
     info["C_I"] = C_I
+    info["B"] = B
     info["disc_clamped"] = clamped
     info["mass"] = float(C1.sum())
 
@@ -712,7 +817,8 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     vcen = 0.5 * (vss[:-1] + vss[1:])
     uM = mirror_value(ucen.reshape(-1), geo)
     vM = mirror_value(vcen.reshape(-1), geo)
-    uG, vG = slip_ghost(case, uM, vM, geo.n, geo.gamma, geo.dn)
+    mu_I = mu(C_I) if B is not None else None
+    uG, vG = slip_ghost(case, uM, vM, geo.n, geo.gamma, geo.dn, B, gt, mu_I)
     uss_f, vss_f = face_fix(case, geo, uss, vss, ucen, vcen, uG, vG)
     info["uG"], info["vG"] = uG, vG
     info["u_ss"], info["v_ss"] = uss_f, vss_f
@@ -740,6 +846,8 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     new = {"C": C1, "C_old": st["C"].copy(), "u": u1, "u_old": st["u"].copy(),
            "v": v1, "v_old": st["v"].copy(), "Hu": Hu, "Hv": Hv,
            "P": P1, "P_old": st["P"].copy()}
+    if p.mu_f > 0.0:
+        new["C_I"] = C_I.copy()
     return new, info
 
 

@@ -39,7 +39,7 @@ import scipy.fft as sfft
 
 from oracle.ib_pf2d import KAPPA, GAMMA0, MARCH_DIV, MARCH_MAX, BISECT, EPS0
 from oracle.ib_pf2d import CELL_FLUID, CELL_GHOST, CELL_SOLID
-from oracle.ib_pf2d import contact_angle_ghost, linear_exact_weights
+from oracle.ib_pf2d import contact_angle_ghost, dynamic_contact_ghost, linear_exact_weights
 from workloads.cases import GEOM_FLAT, GEOM_NONE, GEOM_SPHERE, GEOM_SPHERES, Case3D
 
 NSUB3 = 16     # subgrid points per direction in 3D (reading R12)
@@ -555,9 +555,11 @@ def mirror_value3(field_flat, geo: Geometry3D):
     return 2.0 * _gather(field_flat, geo.ap1, geo.w1) - _gather(field_flat, geo.ap2, geo.w2)
 
 
-def slip_ghost3(case: Case3D, uM, vM, wM, n, gamma, dn):
-    """a6 core, reading R5': Eq. NoPenetration for V_n, Eq. UpdateVtan (static angle) for
-    the tangential vector, Eq. UpdateVandW back to the axes."""
+def slip_ghost3(case: Case3D, uM, vM, wM, n, gamma, dn, B=None, gt=None, mu_I=None):
+    """a6 core in 3D (reading R5'): Eq. NoPenetration for V_n = u.n, Eq. UpdateVtan for the
+    tangential vector, Eq. UpdateVandW back to the axes.  Dynamic angle (reading R18 of the
+    2D oracle): the tangential vector gains -(1/Ca) B gt l_s (gamma + 1) dn / (mu_I (l_s +
+    gamma dn)), gt (ng x 3) the tangential gradient of C at I."""
     p = case.params
     n1, n2, n3 = n[:, 0], n[:, 1], n[:, 2]
     VnM = (uM * n1 + vM * n2) + wM * n3
@@ -566,6 +568,9 @@ def slip_ghost3(case: Case3D, uM, vM, wM, n, gamma, dn):
     uG = VnG * n1 + f * (uM - VnM * n1)
     vG = VnG * n2 + f * (vM - VnM * n2)
     wG = VnG * n3 + f * (wM - VnM * n3)
+    if B is not None:
+        c = (B / p.Ca) * (p.l_s * (gamma + 1.0) * dn) / (mu_I * (p.l_s + gamma * dn))
+        uG, vG, wG = uG - c * gt[:, 0], vG - c * gt[:, 1], wG - c * gt[:, 2]
     return uG, vG, wG
 
 
@@ -631,9 +636,32 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     C1 = C_pre.copy()
     f = C1.reshape(-1)
     C_M = mirror_value3(C_pre.reshape(-1), geo)
-    C_G, C_I, clamped = contact_angle_ghost(case, C_M, geo.gamma, geo.dn)
+    B = gt = None
+    if p.mu_f > 0.0:
+        # dynamic angle (reading R18 of the 2D oracle), vector form: v_t (dC/dx_t) = V_t . grad C
+        g = geo.gcell
+        gam = geo.gamma
+        Cn_flat = st["C"].reshape(-1)
+        CI_n = st.get("C_I")
+        CI_n = np.full(len(g), np.nan) if CI_n is None else CI_n
+        CI_n = np.where(np.isfinite(CI_n), CI_n,
+                        (gam * Cn_flat[g] + mirror_value3(Cn_flat, geo)) / (gam + 1.0))
+        at_I = lambda fld: (gam * fld.reshape(-1)[g] + mirror_value3(fld.reshape(-1), geo)) / (gam + 1.0)
+        UI = np.stack([at_I(0.5 * (st["u"] + _xp(st["u"]))), at_I(0.5 * (st["v"] + _yp(st["v"]))),
+                       at_I(0.5 * (st["w"][:-1] + st["w"][1:]))], axis=1)
+        GI = np.stack([at_I((_xp(C_pre) - _xm(C_pre)) / (2.0 * h)),
+                       at_I((_yp(C_pre) - _ym(C_pre)) / (2.0 * h)),
+                       at_I((_zp_mirror(C_pre) - _zm_mirror(C_pre)) / (2.0 * h))], axis=1)
+        nn = geo.n
+        Vt = UI - (UI * nn).sum(axis=1)[:, None] * nn
+        gt = GI - (GI * nn).sum(axis=1)[:, None] * nn
+        adv = (Vt * GI).sum(axis=1)
+        C_G, C_I, B = dynamic_contact_ghost(case, C_M, gam, geo.dn, CI_n, adv)
+        clamped = 0
+    else:
+        C_G, C_I, clamped = contact_angle_ghost(case, C_M, geo.gamma, geo.dn)
     f[geo.gcell] = C_G
-    info["C"], info["C_I"], info["disc_clamped"] = C1, C_I, clamped
+    info["C"], info["C_I"], info["disc_clamped"], info["B"] = C1, C_I, clamped, B
     info["mass"] = float(C1.sum())
 
     # a4
@@ -666,7 +694,8 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     uM = mirror_value3(ucen.reshape(-1), geo)
     vM = mirror_value3(vcen.reshape(-1), geo)
     wM = mirror_value3(wcen.reshape(-1), geo)
-    uG, vG, wG = slip_ghost3(case, uM, vM, wM, geo.n, geo.gamma, geo.dn)
+    mu_I = mu(C_I) if B is not None else None
+    uG, vG, wG = slip_ghost3(case, uM, vM, wM, geo.n, geo.gamma, geo.dn, B, gt, mu_I)
     solid_flat = (geo.cls == CELL_SOLID).reshape(-1)
     cells = []
     for cen, g in ((ucen, uG), (vcen, vG), (wcen, wG)):
@@ -710,6 +739,8 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     new = {"C": C1, "C_old": st["C"].copy(), "u": u1, "u_old": u.copy(), "v": v1,
            "v_old": v.copy(), "w": w1, "w_old": w.copy(), "Hu": Hu, "Hv": Hv, "Hw": Hw,
            "P": P1, "P_old": st["P"].copy()}
+    if p.mu_f > 0.0:
+        new["C_I"] = C_I.copy()
     return new, info
 
 
