@@ -92,6 +92,17 @@ restatement, with the CUDA path):
       with the surface-tension scale 1/(Re Ca) of R1 (the paper's Eq. UpdateVtan drops kappa
       and eps).  mu_f -> 0 recovers R4's static root; mu_f -> infinity freezes C_I but for
       advection along the wall.
+  R19 Semi-implicit momentum predictor (params.ns_scheme = 1; Appendix A.2, Eq.
+      predictionSemi): u* = u^n + d with (1 - (dt nu0/2) L) d = dt [3/2 N^n - 1/2 N^{n-1} + ST
+      + V^n + MF], N = -div(u u) (the history field holds N only), V^n = div(mu^{n+1}(grad u^n +
+      grad u^n^T))/(Re rho^{n+1}) at level n, ST the surface tension of R9, nu0 =
+      (mu_l/rho_l + mu_g/rho_g)/(2 Re), L the 5-point Laplacian of each component with its
+      own x2 boundary rows (no-slip ghost rows for u: DST-II; v = 0 on the walls: DST-I),
+      solved on the whole box like the CH split.  MF = (rho'/(rho_f Pe)) (grad phi . grad) u,
+      rho' = (rho_l - rho_g)/2: the mass-flux consistency term, derived from the momentum
+      equation with the diffusive mass flux rho' J, J = -(1/Pe) grad phi (the paper prints
+      (rho_1 - rho_2)/2 M (grad phi . grad) u without the 1/rho); the discrete form is in
+      mass_flux_term.
   R15 Explicit CH (Eq. ExpCH) in the form of R1 and R8: the update is
       C^{n+1} = C^n + dt (3/2 F^n - 1/2 F^{n-1}),  F = -div(u C_f) + (1/Pe) lap(phi),
       the convective term in divergence form (the paper writes u . grad C; equal for a
@@ -716,6 +727,13 @@ def momentum_rhs(case: Case2D, C1: np.ndarray, u: np.ndarray, v: np.ndarray):
     """H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho) on the x1-faces (ny, nx) and the
     x2-faces (ny+1, nx; wall rows zero), with rho and mu from C1 (Eq. PredictionExp, the
     convective and viscous brackets; reading R8 for the discrete operators)."""
+    Nu, Nv, Vu, Vv = momentum_terms(case, C1, u, v)
+    return Nu + Vu, Nv + Vv
+
+
+def momentum_terms(case: Case2D, C1: np.ndarray, u: np.ndarray, v: np.ndarray):
+    """The two brackets of momentum_rhs separately: N = -div(u u) and
+    V = div(mu (grad u + grad u^T)) / (Re rho) (x2-face wall rows zero)."""
     p = case.params
     nx, ny, h = case.nx, case.ny, case.h
     rho, mu, _ = _props(case)
@@ -738,10 +756,66 @@ def momentum_rhs(case: Case2D, C1: np.ndarray, u: np.ndarray, v: np.ndarray):
     uv = (0.5 * (upad[1:] + upad[:-1])) * (0.5 * (v + _xm(v)))
     conv_u = (uc * uc - _xm(uc * uc)) / h + (uv[1:] - uv[:-1]) / h
     conv_v = (_xp(uv) - uv)[1:ny] / h + (vc[1:] * vc[1:] - vc[:-1] * vc[:-1]) / h
-    Hu = -conv_u + visc_u / (p.Re * rho(Cf_u))
-    Hv = np.zeros((ny + 1, nx))
-    Hv[1:ny] = -conv_v + visc_v / (p.Re * rho(Cf_v))
-    return Hu, Hv
+    Nv = np.zeros((ny + 1, nx))
+    Vv = np.zeros((ny + 1, nx))
+    Nv[1:ny] = -conv_v
+    Vv[1:ny] = visc_v / (p.Re * rho(Cf_v))
+    return -conv_u, Nv, visc_u / (p.Re * rho(Cf_u)), Vv
+
+
+def mass_flux_term(case: Case2D, C1, phi, u, v):
+    """(rho'/(rho_f Pe)) (grad phi . grad) u on the x1- and x2-faces (the last term of Eq.
+    predictionSemi, reading R19): rho' = (rho_l - rho_g)/2, the chemical potential's gradient
+    by the face difference across the face and the mean of the two cells' central differences
+    along it, the velocity's by central differences of its own faces (no-slip ghost rows -u
+    at the x2 walls; v on the interior x2-faces, zero on the walls)."""
+    p = case.params
+    h, ny, nx = case.h, case.ny, case.nx
+    rho, _, _ = _props(case)
+    rp = 0.5 * (1.0 - 1.0 / p.rho_ratio)
+    upad = np.vstack([-u[:1], u, -u[-1:]])
+    phy_c = (_yp_mirror(phi) - _ym_mirror(phi)) / (2.0 * h)
+    phx_c = (_xp(phi) - _xm(phi)) / (2.0 * h)
+    mfu = (rp / (rho(0.5 * (_xm(C1) + C1)) * p.Pe)) * (
+        ((phi - _xm(phi)) / h) * ((_xp(u) - _xm(u)) / (2.0 * h))
+        + (0.5 * (phy_c + _xm(phy_c))) * ((upad[2:] - upad[:-2]) / (2.0 * h)))
+    mfv = np.zeros((ny + 1, nx))
+    vi = v[1:ny]
+    mfv[1:ny] = (rp / (rho(0.5 * (C1[:-1] + C1[1:])) * p.Pe)) * (
+        (0.5 * (phx_c[1:] + phx_c[:-1])) * ((_xp(vi) - _xm(vi)) / (2.0 * h))
+        + ((phi[1:] - phi[:-1]) / h) * ((v[2:] - v[:-2]) / (2.0 * h)))
+    return mfu, mfv
+
+
+def velocity_eigenvalues(case: Case2D):
+    """Eigenvalues of the 5-point Laplacian of the two velocity components with their x2
+    boundary rows (periodic x1): x1-faces (no-slip ghost rows -u) in the real-Fourier x DST-II
+    basis, modes m = 1..ny; x2-faces (interior faces, v = 0 on the walls) in the real-Fourier x
+    DST-I basis, modes m = 1..ny-1; both -(4/h^2)(sin^2(pi k/nx) + sin^2(pi m/(2 ny)))."""
+    nx, ny, h = case.nx, case.ny, case.h
+    lx = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(nx // 2 + 1) / nx) ** 2
+    lu = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(1, ny + 1) / (2.0 * ny)) ** 2
+    lv = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(1, ny) / (2.0 * ny)) ** 2
+    return lu[:, None] + lx[None, :], lv[:, None] + lx[None, :]
+
+
+def velocity_helmholtz(case: Case2D, ru, rv, a):
+    """(1 - a L) d = r for both velocity components (Appendix A.2, Eq. predictionSemi, the
+    implicit half of nu0 lap u), by the transforms of velocity_eigenvalues."""
+    nx, ny = case.nx, case.ny
+    lu, lv = velocity_eigenvalues(case)
+
+    def solve(r, typ, lam):
+        s = sfft.rfft(r, axis=1)
+        t = sfft.dst(s.real, type=typ, axis=0) + 1j * sfft.dst(s.imag, type=typ, axis=0)
+        t = t / (1.0 - a * lam)
+        t = sfft.idst(t.real, type=typ, axis=0) + 1j * sfft.idst(t.imag, type=typ, axis=0)
+        return sfft.irfft(t, n=nx, axis=1)
+
+    du = solve(ru, 2, lu)
+    dv = np.zeros((ny + 1, nx))
+    dv[1:ny] = solve(rv[1:ny], 1, lv)
+    return du, dv
 
 
 def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
@@ -794,9 +868,9 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     phi = chemical_potential(case, geo, C1)
     info["phi"] = phi
 
-    # a5: explicit AB2 predictor + penalisation (Eq. PredictionExp, Eq. Penalization2)
+    # a5: AB2 predictor + penalisation (Eq. PredictionExp, Eq. Penalization2), or the
+    # semi-implicit predictor of Appendix A.2 (Eq. predictionSemi, reading R19)
     u, v = st["u"], st["v"]
-    Hu, Hv = momentum_rhs(case, C1, u, v)
     Cf_u = 0.5 * (_xm(C1) + C1)
     Cf_v = 0.5 * (C1[:-1] + C1[1:])                  # x2-faces j = 1..ny-1
     rho_u = rho(Cf_u)
@@ -804,9 +878,21 @@ def step(case: Case2D, geo: Geometry2D, st: dict) -> tuple[dict, dict]:
     k_st = KAPPA / (p.Re * p.Ca * eta)
     st_u = k_st * (0.5 * (phi + _xm(phi))) * ((C1 - _xm(C1)) / h) / rho_u
     st_v = k_st * (0.5 * (phi[1:] + phi[:-1])) * ((C1[1:] - C1[:-1]) / h) / rho_v
-    u_star = u + p.dt * ((1.5 * Hu - 0.5 * st["Hu"]) + st_u)
     v_star = np.zeros((ny + 1, nx))
-    v_star[1:ny] = v[1:ny] + p.dt * ((1.5 * Hv[1:ny] - 0.5 * st["Hv"][1:ny]) + st_v)
+    if getattr(p, "ns_scheme", 0) == 1:
+        Hu, Hv, Vu, Vv = momentum_terms(case, C1, u, v)     # history: the convective bracket
+        mfu, mfv = mass_flux_term(case, C1, phi, u, v)
+        Fu = (((1.5 * Hu - 0.5 * st["Hu"]) + st_u) + Vu) + mfu
+        Fv = np.zeros((ny + 1, nx))
+        Fv[1:ny] = (((1.5 * Hv[1:ny] - 0.5 * st["Hv"][1:ny]) + st_v) + Vv[1:ny]) + mfv[1:ny]
+        nu0 = 0.5 * (1.0 + (1.0 / p.mu_ratio) / (1.0 / p.rho_ratio)) / p.Re
+        du, dv = velocity_helmholtz(case, p.dt * Fu, p.dt * Fv, 0.5 * p.dt * nu0)
+        u_star = u + du
+        v_star[1:ny] = v[1:ny] + dv[1:ny]
+    else:
+        Hu, Hv = momentum_rhs(case, C1, u, v)
+        u_star = u + p.dt * ((1.5 * Hu - 0.5 * st["Hu"]) + st_u)
+        v_star[1:ny] = v[1:ny] + p.dt * ((1.5 * Hv[1:ny] - 0.5 * st["Hv"][1:ny]) + st_v)
     uss = geo.alpha_u * u_star
     vss = geo.alpha_v * v_star
     info["Hu"], info["Hv"] = Hu, Hv

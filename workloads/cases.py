@@ -57,6 +57,8 @@ class Params:
     dt: float = 1.0e-4
     ch_scheme: int = 0   # 0: semi-implicit CH (Appendix A.1); 1: explicit AB2 (Eq. ExpCH)
     weights: int = 0     # averaging weights: 0 linear-exact (default), 1 plain inverse-distance
+    ns_scheme: int = 0   # momentum predictor: 0 explicit AB2 (Eq. PredictionExp); 1 semi-implicit
+                         # (Eq. predictionSemi, Appendix A.2)
 
 
 @dataclass(frozen=True)
