@@ -36,7 +36,8 @@
  * condition in vector form (V_t = u - (u.n) n).
  *
  * Element type.  The element type of every field buffer passed in or out is the
- * context's arithmetic type: double for IB_PF_FP64, float for IB_PF_FP32.
+ * context's arithmetic type (double for IB_PF_FP64, float for IB_PF_FP32), except the
+ * wall values IB_PF_F_C_I, which are double in both.
  *
  * Errors.  Every call returns an ib_pf_status; nothing aborts, traps the device or exits.
  * The last error message of a context is kept (ib_pf_last_error).  Device-detected
@@ -85,6 +86,15 @@ typedef enum { IB_PF_CH_SEMI_IMPLICIT = 0, IB_PF_CH_EXPLICIT = 1 } ib_pf_ch_sche
  * plane (3D) the IDW weights are used.  LINEAR is the default (0). */
 typedef enum { IB_PF_W_LINEAR = 0, IB_PF_W_IDW = 1 } ib_pf_weights;
 
+/* momentum predictor (row a5): EXPLICIT, the Adams-Bashforth step of Eq. PredictionExp;
+ * SEMI_IMPLICIT, Eq. predictionSemi of Appendix A.2: u* = u^n + d with
+ * (1 - (dt nu0/2) L) d = dt [3/2 N^n - 1/2 N^{n-1} + ST + V^n + MF], N = -div(u u) (the history
+ * fields H then hold N only), V^n the viscous term at level n, nu0 = (mu_l/rho_l +
+ * mu_g/rho_g)/(2 Re), MF = ((rho_l - rho_g)/(2 rho Pe)) (grad phi . grad) u the mass-flux
+ * consistency term, solved per component with Fourier x cosine-type transforms (DST-II
+ * for u, DST-I for v); 2D contexts only.  All instances of a context share it. */
+typedef enum { IB_PF_NS_EXPLICIT = 0, IB_PF_NS_SEMI_IMPLICIT = 1 } ib_pf_ns_scheme;
+
 /* wall kinds: the solid is where the predicate holds (Sec. 4.1.1 counts subgrid points
  * against it).  FLAT: x2 < p[0] (2D), z < p[0] (3D).  SINUSOID (2D): x2 < p[0] + p[1]
  * sin(2 pi p[2] x1).  SPHERE (3D): |x - (p[0], p[1], p[2])| < p[3].  SPHERES (3D): the union
@@ -113,13 +123,18 @@ typedef struct {
  * S is the stabilisation of Appendix A.1; rho_ratio and mu_ratio are liquid/gas with the
  * liquid (C = +1) at rho = mu = 1; theta_deg the static contact angle measured through
  * the liquid; l_s the slip length of Eq. SlipVelocity; mu_f the wall friction of
- * Eq. WallBCS (must be 0: static angle); d1, d2 the ghost-cell lengths of Sec. 4.1.2
- * (d1 > half a cell diagonal, 0 < d2 < d1); dt the time step. */
+ * Eq. WallBCS, nondimensional as in (dC/dt + v_t dC/dx_t)_I = (1/(mu_f Cn)) [kappa Cn dC/dn +
+ * cos(theta) g'(C_I)] (Eq. WallBCS_recast): 0 = static angle (the wetting condition holds
+ * at every step), > 0 = dynamic angle with the wall values C_I as per-ghost state advanced
+ * implicitly by one step per time step, and the wetting bracket in the slip condition (Eq.
+ * UpdateVtan); d1, d2 the ghost-cell lengths of Sec. 4.1.2 (d1 > half a cell diagonal,
+ * 0 < d2 < d1); dt the time step. */
 typedef struct {
   double Re, Ca, Cn, Pe, S, rho_ratio, mu_ratio, theta_deg, l_s, mu_f, d1, d2, dt;
   int precision;  /* ib_pf_precision */
   int ch_scheme;  /* ib_pf_ch_scheme; all instances of a context share it */
   int weights;    /* ib_pf_weights (per instance) */
+  int ns_scheme;  /* ib_pf_ns_scheme; all instances of a context share it */
 } ib_pf_params;
 
 /* field ids for read / write */
@@ -146,7 +161,12 @@ typedef enum {
   IB_PF_F_C_OLD_LO = 14, /* FP32 contexts only: low part of C^{n-1} */
   IB_PF_F_W = 15,       /* 3D: w^n (z-faces) read/write */
   IB_PF_F_W_OLD = 16,   /* 3D: w^{n-1} */
-  IB_PF_F_HW = 17       /* 3D: H_w^{n-1} */
+  IB_PF_F_HW = 17,      /* 3D: H_w^{n-1} */
+  IB_PF_F_C_I = 18      /* dynamic angle (mu_f > 0): the wall values C_I at the intersect points,
+                           one per ghost in ghost order (IB_PF_T_GHOST_CELL), double in both
+                           forms; read/write for restarts.  NaN = unset: a write of IB_PF_F_C
+                           unsets them and the next step starts them from the field,
+                           (gamma C_G + C_M)/(gamma + 1) */
 } ib_pf_field;
 
 /* geometry tables for ib_pf_read_table (element type in brackets) */
@@ -186,7 +206,8 @@ typedef enum {
 
 /* Create a context for n_instances independent problems (grids[k], geoms[k],
  * params[k]) and run the first part of the precompute of Sec. 4.1: volume fractions of
- * the cell and face control volumes by counting 100 x 100 subgrid points (Sec. 4.1.1),
+ * the cell and face control volumes by counting 100 x 100 subgrid points per volume in 2D,
+ * 16 x 16 x 16 in 3D (Sec. 4.1.1),
  * ghost classification (cell centre in the solid with a fluid face neighbour, Sec.
  * 4.1.2) and compaction, and the list of faces re-interpolated after the velocity ghost
  * fill.  Fields start at zero.  `cuda_stream` is a cudaStream_t (NULL = default stream);
@@ -273,11 +294,35 @@ ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char*
  * return IB_PF_E_ARG with a message in ib_pf_last_error(NULL).
  * Scratch: one fixed file-scope device array of about 4.3 MB that every GPU loading the
  * library holds until the process exits.  The first call on each device looks up the
- * array's device address; make that first call before any stream capture.  All calls
- * share the array, so calls that may overlap on the GPU (different streams, or threads)
- * race and must be serialised by the caller. */
+ * array's device address and keeps it for the life of the process; make that first call
+ * before any stream capture, and restart the process after a cudaDeviceReset before
+ * calling again.  All calls share the array, so calls that may overlap on the GPU
+ * (different streams, or threads) race and must be serialised by the caller.  A CUDA error
+ * already pending on the calling thread makes the call return IB_PF_E_CUDA without
+ * queueing work (the error is left in place). */
 ib_pf_status ib_pf_poisson_solve_noalloc(const double* rhs, double* out, int nx, int ny,
                                          double h, void* cuda_stream);
+
+/* Bind caller-owned device memory (e.g. a torch CUDA tensor) as the storage of a state
+ * field of `instance`, in place of the buffer the library allocated (which is freed).
+ * The state of the scheme is what the step reads and writes (Sec. 4.2 and Appendix A: C,
+ * u, v (w), P at levels n and n-1 and the Adams-Bashforth history H); the library keeps
+ * the two buffers of a two-level field and swaps their roles every step.
+ *   field_id  IB_PF_F_C, IB_PF_F_U, IB_PF_F_V, IB_PF_F_P, IB_PF_F_W (3D) and, in FP32
+ *             contexts, IB_PF_F_C_LO: time_level 0 binds the buffer that holds level n at
+ *             the time of the call, 1 the one that holds level n-1 (after a step the two
+ *             have swapped roles: read the levels through ib_pf_read_fields or keep the
+ *             step parity);  IB_PF_F_HU, IB_PF_F_HV, IB_PF_F_HW (3D): time_level 0.
+ *   device_ptr device (or managed) memory of the context's element type, 16-byte aligned,
+ *             nbytes = the field size (layout as above); it must not alias another bound
+ *             field.  Its current content becomes the field's value (nothing is copied),
+ *             except that the wall rows of v (planes of w) are set to zero.
+ * The caller keeps ownership: ib_pf_destroy does not free bound buffers, and they must
+ * stay valid until the context is destroyed or the field is bound again.  The call
+ * synchronises the context stream and rebuilds the step graphs (not for hot loops).
+ * Errors: IB_PF_E_ARG (ids, size, alignment, not device memory), IB_PF_E_CUDA. */
+ib_pf_status ib_pf_bind_fields(ib_pf_ctx* ctx, int instance, int field_id, int time_level,
+                               void* device_ptr, long long nbytes);
 
 /* Last error message of ctx (or of the last failed creation when ctx is NULL). */
 const char* ib_pf_last_error(const ib_pf_ctx* ctx);

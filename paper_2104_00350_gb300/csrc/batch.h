@@ -22,7 +22,9 @@ enum Family {
   kFamFace = 4,    // chunks of kGhostChunk re-interpolated faces
   kFamRowsL = 5,   // as kFamRows for rows of 2048 or 4096 points
   kFamColsL = 6,   // as kFamCols for columns of 2048 points
-  kNumFam = 7
+  kFamD1 = 7,      // semi-implicit predictor: groups of DST-I columns (2 ny-point FFTs)
+  kFamD1L = 8,     // the same for 2 ny of 2048 or 4096 points
+  kNumFam = 9
 };
 constexpr int kTileX = 32, kTileY = 8;       // threads of a cell-family block
 constexpr int kRowsPerThread = 4;            // cells per thread along x2
@@ -62,6 +64,10 @@ struct StepArgs {
   double k_wet;   // kappa Cn
   double cos_th;
   double l_s;
+  // dynamic angle (mu_f > 0): a_dyn = dt / (mu_f Cn), 0 for the static angle
+  double a_dyn;
+  double inv_ca;  // 1 / Ca
+  double mf_coef; // semi-implicit predictor: (rho_l - rho_g) / (2 Pe)
 };
 
 template <typename T>
@@ -85,6 +91,8 @@ struct InstDev {
   T* gu;
   T* gv;
   T* fval;
+  double* ci;  // dynamic angle: per-ghost wall value C_I (state, FP64 in both forms)
+  T* gq;       // dynamic angle: per-ghost scratch C_G, B, (dC/dx_t)_I
   Tables tab;
   const T* au;                // face fractions alpha_u, alpha_v in the field type
   const T* av;
@@ -96,6 +104,12 @@ struct InstDev {
   const C2* twy;
   const C2* wd;
   double s_eta2, c0;          // CH symbol: L^2 - s_eta2 L + c0
+  double a_visc;              // semi-implicit predictor: (1 - a_visc L), a_visc = dt nu0 / 2
+  const double* lam_s2;       // its wall-normal eigenvalues (DST-II, cosine order; DST-I)
+  const double* lam_d1;
+  const float* lam_s2_f;
+  const float* lam_d1_f;
+  const C2* tw2;              // twiddles of the 2 ny-point FFTs
   double* partial;
   unsigned* ticket;
   double* mass;
@@ -109,6 +123,7 @@ struct BatchPlan {
   int2* d_blk[kNumFam] = {};           // (instance, local block) per launched block
   int nblk[kNumFam] = {};
   size_t rows_smem[2] = {}, cols_smem[2] = {};   // small / large transform class
+  size_t d1_smem[2] = {};                          // DST-I blocks
   int max_nx = 0, max_ny = 0;
 };
 

@@ -42,6 +42,7 @@ size_t field_elems(const Instance& in, int id) {
     case IB_PF_F_V: case IB_PF_F_V_OLD: case IB_PF_F_HV:
       return in.dim == 3 ? cells : cells + in.nx;
     case IB_PF_F_W: case IB_PF_F_W_OLD: case IB_PF_F_HW: return cells + nxy;
+    case IB_PF_F_C_I: return (size_t)in.tab.ng;
     default: return cells;
   }
 }
@@ -67,6 +68,7 @@ void* field_ptr(Ctx& c, Instance& in, int id) {
     case IB_PF_F_W: return in.W[n];
     case IB_PF_F_W_OLD: return in.W[o];
     case IB_PF_F_HW: return in.Hw;
+    case IB_PF_F_C_I: return in.ci;
     default: return nullptr;
   }
 }
@@ -79,9 +81,14 @@ void free_instance(Instance& in) {
                   in.tab.cmap, in.tab.gcell, in.tab.nrm, in.tab.dn, in.tab.gamma, in.tab.ap1,
                   in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv, in.W[0], in.W[1], in.Hw,
                   in.gw, in.lamz, in.lamz_f, in.twz, in.sph, in.bstart, in.blist,
-                  in.tab.alpha_w, in.tab.fw, in.alpha_f};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+                  in.tab.alpha_w, in.tab.fw, in.alpha_f, in.ci, in.gq, in.lam_s2, in.lam_d1,
+                  in.lam_s2_f, in.lam_d1_f, in.tw2};
+  for (void* p : ptrs) {
+    if (!p) continue;
+    bool caller_owned = false;
+    for (void* b : in.bound) caller_owned = caller_owned || b == p;
+    if (!caller_owned) cudaFree(p);
+  }
 }
 
 // order the work stream after everything already queued on the caller's stream
@@ -157,9 +164,17 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
     why = "unknown weights";
     return IB_PF_E_ARG;
   }
+  if (p.ns_scheme != IB_PF_NS_EXPLICIT && p.ns_scheme != IB_PF_NS_SEMI_IMPLICIT) {
+    why = "unknown ns_scheme";
+    return IB_PF_E_ARG;
+  }
+  if (p.ns_scheme == IB_PF_NS_SEMI_IMPLICIT && g.dim == 3) {
+    why = "the semi-implicit momentum predictor is built for 2D contexts";
+    return IB_PF_E_UNSUPPORTED;
+  }
   if (g.dim == 3) {
     if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
-    if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }
+    if (!(p.mu_f >= 0.0) || !std::isfinite(p.mu_f)) { why = "mu_f must be finite and >= 0"; return IB_PF_E_ARG; }
     const double vals3[] = {p.Re, p.Ca, p.Cn, p.Pe, p.rho_ratio, p.mu_ratio, p.dt, p.d1, p.d2};
     for (double v : vals3)
       if (!(v > 0) || !std::isfinite(v)) { why = "Re, Ca, Cn, Pe, ratios, dt, d1, d2 must be positive"; return IB_PF_E_ARG; }
@@ -185,7 +200,7 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
     return IB_PF_E_ARG;
   }
   if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
-  if (p.mu_f != 0.0) { why = "dynamic contact angle (mu_f > 0) is not built"; return IB_PF_E_UNSUPPORTED; }
+  if (!(p.mu_f >= 0.0) || !std::isfinite(p.mu_f)) { why = "mu_f must be finite and >= 0"; return IB_PF_E_ARG; }
   const double vals[] = {p.Re, p.Ca, p.Cn, p.Pe, p.rho_ratio, p.mu_ratio, p.dt, p.d1, p.d2};
   for (double v : vals)
     if (!(v > 0) || !std::isfinite(v)) { why = "Re, Ca, Cn, Pe, ratios, dt, d1, d2 must be positive"; return IB_PF_E_ARG; }
@@ -250,12 +265,15 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
       return fail(nullptr, IB_PF_E_ARG, "all instances must share one dimension");
     if (params[k].ch_scheme != params[0].ch_scheme)
       return fail(nullptr, IB_PF_E_ARG, "all instances must share one ch_scheme");
+    if (params[k].ns_scheme != params[0].ns_scheme)
+      return fail(nullptr, IB_PF_E_ARG, "all instances must share one ns_scheme");
   }
   ib_pf_ctx* ctx = new (std::nothrow) ib_pf_ctx();
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "out of host memory");
   ctx->precision = params[0].precision;
   ctx->dim = grids[0].dim;
   ctx->ch_scheme = params[0].ch_scheme;
+  ctx->ns_scheme = params[0].ns_scheme;
   ctx->esz = ctx->precision == IB_PF_FP64 ? 8 : 4;
   ctx->user_stream = (cudaStream_t)cuda_stream;
   auto bail = [&](ib_pf_status st) {
@@ -290,6 +308,7 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     in.h = in.lx / in.nx;
     in.geom = geoms[k];
     in.prm = params[k];
+    in.prm_ns_semi = params[k].ns_scheme == IB_PF_NS_SEMI_IMPLICIT;
     in.wall.kind = geoms[k].kind;
     in.wall.p0 = geoms[k].p[0];
     in.wall.p1 = geoms[k].p[1];
@@ -360,6 +379,17 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
         cudaMalloc(&in.fval, (size_t)(t.nfu + t.nfv + t.nfw + 1) * es) != cudaSuccess) {
       ctx->err = "ghost scratch allocation failed";
       return bail(IB_PF_E_CUDA);
+    }
+    if (in.prm.mu_f > 0.0) {
+      // dynamic angle: wall values C_I (state, unset = NaN) and per-ghost scratch
+      const size_t ng1 = (size_t)(t.ng ? t.ng : 1);
+      if (cudaMalloc(&in.ci, ng1 * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&in.gq, ng1 * (2 + in.dim) * es) != cudaSuccess) {
+        ctx->err = "dynamic-angle scratch allocation failed";
+        return bail(IB_PF_E_CUDA);
+      }
+      cudaMemsetAsync(in.ci, 0xff, ng1 * sizeof(double), ctx->work);
+      ctx->dynamic = true;
     }
   }
   if (cudaStreamSynchronize(ctx->work) != cudaSuccess) {
@@ -441,13 +471,16 @@ ib_pf_status check_field(ib_pf_ctx* ctx, int instance, int field_id, const void*
   if (write) {
     const bool lo_field = field_id == IB_PF_F_C_LO || field_id == IB_PF_F_C_OLD_LO;
     const bool w_field = field_id >= IB_PF_F_W && field_id <= IB_PF_F_HW;
-    if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field && !w_field)
+    if ((field_id < IB_PF_F_C || field_id > IB_PF_F_P_OLD) && !lo_field && !w_field &&
+        field_id != IB_PF_F_C_I)
       return fail(ctx, IB_PF_E_ARG, "field is read-only or unknown");
   }
   Instance& in = ctx->inst[instance];
   void* p = field_ptr(*ctx, in, field_id);
-  if (!p) return fail(ctx, IB_PF_E_ARG, "bad field id (low parts of C exist only in FP32 contexts, w only in 3D)");
-  const long long want = (long long)(field_elems(in, field_id) * ctx->esz);
+  if (!p) return fail(ctx, IB_PF_E_ARG, "bad field id (low parts of C exist only in FP32 contexts, w only in 3D, "
+                          "C_I only with a dynamic contact angle)");
+  const size_t es = field_id == IB_PF_F_C_I ? sizeof(double) : ctx->esz;   // C_I is FP64 in both forms
+  const long long want = (long long)(field_elems(in, field_id) * es);
   if (nbytes != want) return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != " + std::to_string(want));
   *dev = p;
   return IB_PF_OK;
@@ -460,6 +493,7 @@ struct CopyEntry {
   const unsigned int* src;
   unsigned int* dst;
   unsigned long long words, zhead, ztail;
+  unsigned int fill;   // word written where nothing is copied (0, or all ones: NaN in FP32/FP64)
 };
 constexpr int kCopyMax = 48;   // 48 entries = 1920 bytes of kernel parameters
 struct CopyList {
@@ -485,7 +519,7 @@ __global__ void __launch_bounds__(kCopyThreads) k_copy_entries(CopyList L) {
 #pragma unroll
       for (int u = 0; u < kCopyUnroll; ++u) {   // all loads first: several in flight per thread
         const unsigned long long q = base + u * stride;
-        v[u] = make_uint4(0u, 0u, 0u, 0u);
+        v[u] = make_uint4(c.fill, c.fill, c.fill, c.fill);
         if (q < nv && 4 * q + 4 > lo && 4 * q < hi) v[u] = s[q];
       }
 #pragma unroll
@@ -494,17 +528,17 @@ __global__ void __launch_bounds__(kCopyThreads) k_copy_entries(CopyList L) {
         if (q >= nv) continue;
         const unsigned long long w0 = 4 * q;
         if (w0 < lo || w0 + 4 > hi) {
-          if (w0 + 0 < lo || w0 + 0 >= hi) v[u].x = 0u;
-          if (w0 + 1 < lo || w0 + 1 >= hi) v[u].y = 0u;
-          if (w0 + 2 < lo || w0 + 2 >= hi) v[u].z = 0u;
-          if (w0 + 3 < lo || w0 + 3 >= hi) v[u].w = 0u;
+          if (w0 + 0 < lo || w0 + 0 >= hi) v[u].x = c.fill;
+          if (w0 + 1 < lo || w0 + 1 >= hi) v[u].y = c.fill;
+          if (w0 + 2 < lo || w0 + 2 >= hi) v[u].z = c.fill;
+          if (w0 + 3 < lo || w0 + 3 >= hi) v[u].w = c.fill;
         }
         d[q] = v[u];
       }
     }
   } else {
     for (unsigned long long i = t0; i < c.words; i += stride)
-      c.dst[i] = (i >= lo && i < hi) ? c.src[i] : 0u;
+      c.dst[i] = (i >= lo && i < hi) ? c.src[i] : c.fill;
   }
 }
 
@@ -566,6 +600,13 @@ ib_pf_status plan_write(ib_pf_ctx* ctx, WritePlan& plan, int instance, int field
     void* lo = field_ptr(*ctx, in, field_id == IB_PF_F_C ? IB_PF_F_C_LO : IB_PF_F_C_OLD_LO);
     plan.kill(lo);
     plan.add(lo, {nullptr, (unsigned int*)lo, words, 0, 0});
+  }
+  if (field_id == IB_PF_F_C && in.ci && in.tab.ng > 0) {
+    // a written C^n unsets the wall values C_I of the dynamic angle (all-ones words: NaN);
+    // the next step starts them from the new field
+    plan.kill(in.ci);
+    plan.add(in.ci, {nullptr, (unsigned int*)in.ci, (unsigned long long)in.tab.ng * 2, 0, 0,
+                     0xffffffffu});
   }
   return IB_PF_OK;
 }
@@ -808,6 +849,75 @@ ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char*
     if (ms) ms[k] = (double)t;
     if (names) names[k] = ctx->tnames[k];
   }
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_bind_fields(ib_pf_ctx* ctx, int instance, int field_id, int time_level,
+                               void* device_ptr, long long nbytes) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "bad instance");
+  Instance& in = ctx->inst[instance];
+  void** slot = nullptr;
+  const int lv = time_level == 0 ? ctx->cur : 1 - ctx->cur;
+  const bool two = time_level == 0 || time_level == 1;
+  switch (field_id) {
+    case IB_PF_F_C: slot = two ? &in.C[lv] : nullptr; break;
+    case IB_PF_F_U: slot = two ? &in.U[lv] : nullptr; break;
+    case IB_PF_F_V: slot = two ? &in.V[lv] : nullptr; break;
+    case IB_PF_F_P: slot = two ? &in.P[lv] : nullptr; break;
+    case IB_PF_F_W: slot = (two && in.dim == 3) ? &in.W[lv] : nullptr; break;
+    case IB_PF_F_C_LO: slot = (two && ctx->precision == IB_PF_FP32) ? &in.Clo[lv] : nullptr; break;
+    case IB_PF_F_HU: slot = time_level == 0 ? &in.Hu : nullptr; break;
+    case IB_PF_F_HV: slot = time_level == 0 ? &in.Hv : nullptr; break;
+    case IB_PF_F_HW: slot = (time_level == 0 && in.dim == 3) ? &in.Hw : nullptr; break;
+    default: break;
+  }
+  if (!slot) return fail(ctx, IB_PF_E_ARG, "field id / time level cannot be bound");
+  if (!device_ptr) return fail(ctx, IB_PF_E_ARG, "null device pointer");
+  if (((uintptr_t)device_ptr & 15u) != 0) return fail(ctx, IB_PF_E_ARG, "device pointer not 16-byte aligned");
+  const size_t want = field_elems(in, field_id) * ctx->esz;
+  if (nbytes != (long long)want)
+    return fail(ctx, IB_PF_E_ARG, "nbytes " + std::to_string(nbytes) + " != field size " + std::to_string(want));
+  cudaPointerAttributes pa;
+  CK(cudaPointerGetAttributes(&pa, device_ptr));
+  if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+    return fail(ctx, IB_PF_E_ARG, "not device memory");
+  for (Instance& other : ctx->inst)
+    for (void** q : {&other.C[0], &other.C[1], &other.U[0], &other.U[1], &other.V[0], &other.V[1],
+                     &other.P[0], &other.P[1], &other.W[0], &other.W[1], &other.Clo[0], &other.Clo[1],
+                     &other.Hu, &other.Hv, &other.Hw})
+      if (q != slot && *q == device_ptr) return fail(ctx, IB_PF_E_ARG, "buffer already bound to another field");
+  CK(cudaStreamSynchronize(ctx->work));
+  void* old = *slot;
+  bool old_bound = false;
+  for (void* b : in.bound) old_bound = old_bound || b == old;
+  if (old && !old_bound) CK(cudaFree(old));
+  if (old_bound)
+    for (void*& b : in.bound)
+      if (b == old) b = nullptr;
+  *slot = device_ptr;
+  in.bound.push_back(device_ptr);
+  // the wall rows (planes) of v (w) stay zero
+  const size_t nxy = (size_t)in.nx * in.ny;
+  if (field_id == IB_PF_F_V && in.dim == 2) {
+    CK(cudaMemsetAsync(device_ptr, 0, (size_t)in.nx * ctx->esz, ctx->work));
+    CK(cudaMemsetAsync((char*)device_ptr + (size_t)in.ny * in.nx * ctx->esz, 0, (size_t)in.nx * ctx->esz, ctx->work));
+  }
+  if (field_id == IB_PF_F_W) {
+    CK(cudaMemsetAsync(device_ptr, 0, nxy * ctx->esz, ctx->work));
+    CK(cudaMemsetAsync((char*)device_ptr + (size_t)in.nz * nxy * ctx->esz, 0, nxy * ctx->esz, ctx->work));
+  }
+  // the step graphs (and, in 2D, the device descriptors of the batched launches) hold the
+  // field pointers: rebuild them
+  for (int ph = 0; ph < 2; ++ph) {
+    if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
+    ctx->graph[ph] = nullptr;
+  }
+  if (ctx->plan) {
+    batch_free(*(BatchPlan*)ctx->plan);
+    CK(batch_setup(*ctx, *(BatchPlan*)ctx->plan));
+  }
+  CK(cudaStreamSynchronize(ctx->work));
   return IB_PF_OK;
 }
 

@@ -76,6 +76,7 @@ struct Instance {
   double lx = 0, ly = 0, lz = 0, h = 0;
   ib_pf_geometry geom{};
   ib_pf_params prm{};
+  bool prm_ns_semi = false;    // semi-implicit momentum predictor (ns_scheme 1)
   WallDev wall{};
   Tables tab;
   // state, element type of the context; index cur of each pair is level n
@@ -103,6 +104,8 @@ struct Instance {
   void* gv = nullptr;
   void* gw = nullptr;      // 3D
   void* fval = nullptr;    // nfu + nfv (+ nfw) re-interpolated face values
+  void* ci = nullptr;      // dynamic angle (mu_f > 0): ng wall values C_I (state)
+  void* gq = nullptr;      // dynamic angle: ng x (2 + dim) scratch (C_G, B, dC/dx_t)
   // transform tables
   double* lamx = nullptr;  // nx/2+1 eigenvalues of the periodic second difference
   double* lamy = nullptr;  // ny eigenvalues of the Neumann second difference
@@ -113,6 +116,13 @@ struct Instance {
   void* wdct = nullptr;    // ny complex exp(-i pi m/(2 ny)); 3D: nz entries
   // 3D: lamy holds the ny eigenvalues of the periodic y second difference, twy the ny/2
   // y-FFT twiddles; the wall-normal z axis has its own tables
+  // semi-implicit momentum predictor (ns_scheme 1): the wall-normal eigenvalues of the
+  // velocity components (FP64 and FP32 copies) and the twiddles of the doubled length
+  double* lam_s2 = nullptr;  // DST-II (no-slip ghost rows), in the cosine order k: -(4/h^2) cos^2(pi k/(2n))
+  double* lam_d1 = nullptr;  // DST-I (zero wall faces), modes 0..n: -(4/h^2) sin^2(pi m/(2n))
+  float* lam_s2_f = nullptr;
+  float* lam_d1_f = nullptr;
+  void* tw2 = nullptr;       // n complex exp(-2 pi i k/(2n))
   double* lamz = nullptr;  // nz eigenvalues of the Neumann second difference
   float* lamz_f = nullptr;
   void* twz = nullptr;     // nz/2 complex exp(-2 pi i k/nz)
@@ -122,6 +132,7 @@ struct Instance {
   double* mass = nullptr;      // sum of C after the last step
   int* status = nullptr;       // 1 once a non-finite value was seen
   int nblk_red = 0;
+  std::vector<void*> bound;    // caller-owned field buffers (ib_pf_bind_fields): never freed
 };
 
 // Optional event recorder: mark(name) is called after every kernel launch of a step.
@@ -157,6 +168,8 @@ struct Recorder {
 struct Ctx {
   int dim = 2;
   int ch_scheme = IB_PF_CH_SEMI_IMPLICIT;
+  bool dynamic = false;    // some instance has a dynamic contact angle (mu_f > 0)
+  int ns_scheme = IB_PF_NS_EXPLICIT;   // momentum predictor, shared by all instances
   std::vector<Instance> inst;
   int precision = IB_PF_FP64;
   size_t esz = 8;
@@ -185,6 +198,8 @@ cudaError_t geometry_weights(Instance& in, cudaStream_t s, int* n_fail, std::str
 // predictor (2a - b/2)/1.5, 2 store the increment in delta and add a.
 // With a_lo/b_lo/out_lo set (FP32 path), kind 1 updates the compensated pair (hi, lo)
 // of C exactly: C^{n+1} = (a + a_lo) + ((a + a_lo - b - b_lo)/3 + z) with TwoSum.
+// kind 3 (semi-implicit momentum predictor): out = alpha (a + z), the penalised u** from
+// u^n = a and the increment z (Eq. Penalization2).
 struct EpiArgs {
   int kind = 0;
   const void* a = nullptr;
@@ -193,6 +208,7 @@ struct EpiArgs {
   const void* a_lo = nullptr;
   const void* b_lo = nullptr;
   void* out_lo = nullptr;
+  const void* alpha = nullptr;
 };
 
 // ---- spectral.cu: solve in the real-Fourier (x1) x cosine (x2) basis.

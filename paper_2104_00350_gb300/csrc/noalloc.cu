@@ -71,8 +71,14 @@ extern "C" ib_pf_status ib_pf_poisson_solve_noalloc(const double* rhs, double* o
     return reject("poisson_solve_noalloc: grid " + std::to_string(nx) + "x" + std::to_string(ny) +
                       " exceeds the fixed scratch (nx, ny <= 1024 and nx*ny <= 524288)",
                   IB_PF_E_ARG);
+  // an error left by earlier, unrelated work on this thread is reported as such and not
+  // blamed on (or cleared by) this call
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return reject(std::string("poisson_solve_noalloc: a CUDA error is pending from earlier work: ") +
+                      cudaGetErrorString(e), IB_PF_E_CUDA);
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return reject(std::string("poisson_solve_noalloc: no usable device: ") + cudaGetErrorString(e),
                   IB_PF_E_CUDA);

@@ -48,6 +48,20 @@ __device__ __forceinline__ C2 cconj(C2 a) { a.y = -a.y; return a; }
 // m < N/2, the other half by W^{m + N/2} = -W^m.
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 
+// Slot of point i of transform f.  P = 8 (8 points per thread): transforms back to back,
+// pad(f N + i).  P > 8 (more points per thread): transform f starts at f (N + N/16 + 1),
+// one slot more than its padded length, so that a phase in which consecutive threads take
+// the same point of consecutive transforms hits distinct banks.
+template <int N, int P>
+__device__ __forceinline__ int xslot(int f, int i) {
+  if constexpr (P > 8) return f * (N + (N >> 4) + 1) + pad(i);
+  else return pad(f * N + i);
+}
+// complex slots of a block's transform buffer for e points of length-n transforms
+__host__ __device__ constexpr int xbuf(int e, int n, int p) {
+  return p > 8 ? (e / n) * (n + (n >> 4) + 1) : fft_buf(e);
+}
+
 template <bool INV, typename C2>
 __device__ __forceinline__ C2 mul_mi(C2 a) {   // a times -i (forward) or +i (inverse)
   C2 r;
@@ -90,11 +104,11 @@ __device__ __forceinline__ void dft_reg(C2* v) {
   }
 }
 
-template <int LOGN, int R, int NS, bool INV, int THREADS, typename T, typename C2>
+template <int LOGN, int R, int NS, bool INV, int THREADS, typename T, int P, typename C2>
 __device__ __forceinline__ void stockham_pass(C2* x, const C2* __restrict__ tw, int cnt) {
   constexpr int N = 1 << LOGN, NR = N / R, HALF = N / 2;
-  static_assert(N <= 8 * THREADS, "a block holds 8 points per thread");
-  constexpr int Q = 8 / R;                    // groups per thread
+  static_assert(N <= P * THREADS, "a block holds P points per thread");
+  constexpr int Q = P / R;                    // groups per thread
   constexpr int TSTEP = N / (NS * R);         // twiddle index step
   const int ng = cnt * NR;
   C2 v[Q][R];
@@ -104,7 +118,7 @@ __device__ __forceinline__ void stockham_pass(C2* x, const C2* __restrict__ tw, 
     if (g < ng) {
       const int f = g / NR, j = g % NR;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = x[pad(f * N + j + r * NR)];
+      for (int r = 0; r < R; ++r) v[q][r] = x[xslot<N, P>(f, j + r * NR)];
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -125,20 +139,21 @@ __device__ __forceinline__ void stockham_pass(C2* x, const C2* __restrict__ tw, 
     const int g = threadIdx.x + q * THREADS;
     if (g < ng) {
       const int f = g / NR, j = g % NR, k = j % NS;
-      const int d = f * N + (j - k) * R + k;
+      const int d = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) x[pad(d + r * NS)] = v[q][r];
+      for (int r = 0; r < R; ++r) x[xslot<N, P>(f, d + r * NS)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-template <int LOGN, int DONE, bool INV, int THREADS, typename T, typename C2>
+// P: points per thread (8 by default)
+template <int LOGN, int DONE, bool INV, int THREADS, typename T, int P = 8, typename C2>
 __device__ __forceinline__ void stockham(C2* x, const C2* __restrict__ tw, int cnt) {
   if constexpr (DONE < LOGN) {
     constexpr int LR = (LOGN - DONE) >= 3 ? 3 : (LOGN - DONE);
-    stockham_pass<LOGN, (1 << LR), (1 << DONE), INV, THREADS, T>(x, tw, cnt);
-    stockham<LOGN, DONE + LR, INV, THREADS, T>(x, tw, cnt);
+    stockham_pass<LOGN, (1 << LR), (1 << DONE), INV, THREADS, T, P>(x, tw, cnt);
+    stockham<LOGN, DONE + LR, INV, THREADS, T, P>(x, tw, cnt);
   }
 }
 
@@ -258,6 +273,10 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
       ed[ib] = vb;
       va = va + ea[ia];
       vb = vb + ea[ib];
+    } else if (epi.kind == 3) {
+      const T* al = reinterpret_cast<const T*>(epi.alpha);
+      va = al[ia] * (ea[ia] + va);
+      vb = al[ib] * (ea[ib] + vb);
     }
     out[ia] = va;
     out[ib] = vb;
@@ -266,7 +285,7 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
 }
 
 struct SymbolArgs {
-  int mode;          // 0: Cahn-Hilliard quartic, 1: Poisson
+  int mode;          // 0: Cahn-Hilliard quartic, 1: Poisson, 2: Helmholtz 1 - c0 L
   double s_eta2;     // S / Cn^2
   double c0;         // 1.5 Pe / (Cn^2 dt)
   const double* lamx;
@@ -292,12 +311,14 @@ __device__ __forceinline__ C2 divide_symbol(C2 X, T L, const SymbolArgs& sym) {
     // one reciprocal per point: the quotient is within 1.5 ulp of X / sigma
     double r;
     if (sym.mode == 0) r = 1.0 / (L * L - sym.s_eta2 * L + sym.c0);
+    else if (sym.mode == 2) r = 1.0 / (1.0 - sym.c0 * L);     // (1 - a L), a = c0
     else r = (L == 0.0) ? 0.0 : 1.0 / L;
     X.x = X.x * r;
     X.y = X.y * r;
   } else {
     float r;
     if (sym.mode == 0) r = 1.0f / (L * L - sym.s_eta2_f * L + sym.c0_f);
+    else if (sym.mode == 2) r = 1.0f / (1.0f - sym.c0_f * L);
     else r = (L == 0.0f) ? 0.0f : 1.0f / L;
     X.x = X.x * r;
     X.y = X.y * r;
@@ -316,17 +337,20 @@ __device__ __forceinline__ C2 divide_symbol(C2 X, T L, const SymbolArgs& sym) {
 //            x_{2n} = z_n, x_{2n+1} = z_{N-1-n}.
 // Dynamic shared memory: cols_smem_bytes<T>(N, EB) (points, twiddles, cosine weights and the
 // per-column eigenvalue parts).
-template <typename T, int LOGN, int THREADS>
+// FLIP: the sine transform DST-II (velocity components with no-slip ghost rows) by the same
+// pipeline: DST-II(x)_{N-k} = DCT-II((-1)^j x_j)_k, so the column is multiplied by (-1)^j on
+// load and on store and the eigenvalue table is given in the cosine order k.
+template <typename T, int LOGN, int THREADS, int P = 8, bool FLIP = false>
 __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
                           const typename C2T<T>::type* __restrict__ tw,
                           const typename C2T<T>::type* __restrict__ wd, const SymbolArgs& sym,
                           int k0, typename C2T<T>::type* xs) {
   using C2 = typename C2T<T>::type;
   constexpr int N = 1 << LOGN, half = N >> 1;
-  constexpr int EB = 8 * THREADS, KC = EB / N;
-  static_assert(KC >= 1, "a block holds 8 points per thread");
-  C2* tws = xs + fft_buf(EB);   // FFT twiddles, staged once per block
-  C2* wds = tws + half;         // cosine-transform weights
+  constexpr int EB = P * THREADS, KC = EB / N;
+  static_assert(KC >= 1, "a block holds P points per thread");
+  C2* tws = xs + xbuf(EB, N, P);   // FFT twiddles, staged once per block
+  C2* wds = tws + half;            // cosine-transform weights
   // per column c: lcs[c] = lamx[kx], lcs[KC + c] = lamy[ky] (3D: columns k = ky ncx + kx;
   // 2D: kx = k, no y part), computed once per block; lms[m]: the transformed axis
   T* lcs = reinterpret_cast<T*>(wds + N);
@@ -340,29 +364,46 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
     lcs[c] = sym.ncx ? lam_x[k % sym.ncx] : lam_x[k];
     lcs[KC + c] = sym.ncx ? lam_y[k / sym.ncx] : T(0);
   }
+  // load: consecutive threads take consecutive columns of one row (KC columns: rows of KC
+  // contiguous points); the loads of a chunk of up to 16 points per thread are all issued
+  // before their shared-memory stores
+  constexpr int LC = P < 16 ? P : 16;
+#pragma unroll
+  for (int q0 = 0; q0 < P; q0 += LC) {
+    C2 ld[LC];
+#pragma unroll
+    for (int q = 0; q < LC; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * THREADS;
+      const int cc = idx % KC, r = idx / KC;
+      const int k = k0 + cc;
+      ld[q].x = T(0);
+      ld[q].y = T(0);
+      if (k < nh1) ld[q] = spec[(size_t)r * nh1 + k];
+      if (FLIP && (r & 1)) {
+        ld[q].x = -ld[q].x;
+        ld[q].y = -ld[q].y;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LC; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * THREADS;
+      const int cc = idx % KC, r = idx / KC;
+      const int pos = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
+      xs[xslot<N, P>(cc, pos)] = ld[q];
+    }
+  }
   // L at (column c, mode m), in the order (lamz[m] + lamy[ky]) + lamx[kx] (3D) or
   // lamy[m] + lamx[k] (2D)
   auto eig = [&](int c, int m) -> T {
     return sym.ncx ? (lms[m] + lcs[KC + c]) + lcs[c] : lms[m] + lcs[c];
   };
-  // load: consecutive threads take consecutive columns of one row
-  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
-    const int cc = idx % KC, r = idx / KC;
-    const int k = k0 + cc;
-    C2 val;
-    val.x = T(0);
-    val.y = T(0);
-    if (k < nh1) val = spec[(size_t)r * nh1 + k];
-    const int pos = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
-    xs[pad(cc * N + pos)] = val;
-  }
   __syncthreads();
-  stockham<LOGN, 0, false, THREADS, T>(xs, tws, KC);
+  stockham<LOGN, 0, false, THREADS, T, P>(xs, tws, KC);
   // pair tasks (m, N - m), m = 0..N/2, of every column
   for (int t = threadIdx.x; t < KC * (half + 1); t += THREADS) {
     const int c = t / (half + 1), m = t - c * (half + 1);
     const int mm = (N - m) & (N - 1);
-    const int im = pad(c * N + m), imm = pad(c * N + mm);
+    const int im = xslot<N, P>(c, m), imm = xslot<N, P>(c, mm);
     const C2 Vm = xs[im], Vmm = xs[imm];
     C2 Xm, Xmm;
     {
@@ -405,16 +446,85 @@ __device__ void cols_core(typename C2T<T>::type* __restrict__ spec, int nh1,
     if (mm != m) xs[imm] = Zmm;
   }
   __syncthreads();
-  stockham<LOGN, 0, true, THREADS, T>(xs, tws, KC);
+  stockham<LOGN, 0, true, THREADS, T, P>(xs, tws, KC);
   const T inv = T(1) / T(N);
-  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int idx = threadIdx.x + q * THREADS;
     const int cc = idx % KC, r = idx / KC;
     const int kk = k0 + cc;
     const int n = (r & 1) ? (N - 1 - (r >> 1)) : (r >> 1);
-    C2 z = xs[pad(cc * N + n)];
+    C2 z = xs[xslot<N, P>(cc, n)];
+    const T sc = (FLIP && (r & 1)) ? -inv : inv;
+    z.x *= sc;
+    z.y *= sc;
+    if (kk < nh1) spec[(size_t)r * nh1 + kk] = z;
+  }
+  __syncthreads();
+}
+
+// Sine transform DST-I of the interior rows 1 .. N-1 of the KC = 8 THREADS / (2N) spectral
+// columns k0 .. (velocity components that vanish on the wall rows), divided by the symbol
+// and transformed back: each column is extended oddly to length 2N (e_0 = e_N = 0,
+// e_{2N-j} = -e_j), transformed by a complex FFT of length 2N, divided mode by mode by the
+// symbol at the folded index min(m, 2N - m) (lam_d1, N + 1 entries; the m = 0 and m = N
+// modes vanish), transformed back and scaled by 1/(2N); row 0 is stored as zero.
+template <typename T, int LOGN2, int THREADS>
+__device__ void dst1_core(typename C2T<T>::type* __restrict__ spec, int nh1,
+                          const typename C2T<T>::type* __restrict__ tw2, const SymbolArgs& sym,
+                          const T* __restrict__ lam_d1, int k0, typename C2T<T>::type* xs) {
+  using C2 = typename C2T<T>::type;
+  constexpr int M = 1 << LOGN2, N = M >> 1;
+  constexpr int EB = 8 * THREADS, KC = EB / M;
+  static_assert(KC >= 1, "a block holds 8 points per thread");
+  C2* tws = xs + fft_buf(EB);
+  T* lcs = reinterpret_cast<T*>(tws + N);   // lamx of each column
+  const T* lam_x = sizeof(T) == 8 ? (const T*)sym.lamx : (const T*)sym.lamx_f;
+  for (int t = threadIdx.x; t < N; t += THREADS) tws[t] = tw2[t];
+  for (int c = threadIdx.x; c < KC; c += THREADS) lcs[c] = lam_x[min(k0 + c, nh1 - 1)];
+  // consecutive threads take consecutive columns of one row
+  for (int idx = threadIdx.x; idx < KC * N; idx += THREADS) {
+    const int cc = idx % KC, j = idx / KC;
+    const int k = k0 + cc;
+    C2 v;
+    v.x = T(0);
+    v.y = T(0);
+    if (j > 0 && k < nh1) v = spec[(size_t)j * nh1 + k];
+    xs[pad(cc * M + j)] = v;
+    C2 w;
+    w.x = -v.x;
+    w.y = -v.y;
+    if (j == 0) w = v;   // e_N = 0 (v is zero here)
+    xs[pad(cc * M + (j == 0 ? N : M - j))] = w;
+  }
+  __syncthreads();
+  stockham<LOGN2, 0, false, THREADS, T>(xs, tws, KC);
+  for (int t = threadIdx.x; t < KC * M; t += THREADS) {
+    const int c = t / M, m = t - c * M;
+    const int mm = m <= N ? m : M - m;
+    C2 X = xs[pad(c * M + m)];
+    if (mm == 0 || mm == N) {
+      X.x = T(0);
+      X.y = T(0);
+    } else {
+      X = divide_symbol<T>(X, lam_d1[mm] + lcs[c], sym);
+    }
+    xs[pad(c * M + m)] = X;
+  }
+  __syncthreads();
+  stockham<LOGN2, 0, true, THREADS, T>(xs, tws, KC);
+  const T inv = T(1) / T(M);
+  for (int idx = threadIdx.x; idx < KC * N; idx += THREADS) {
+    const int cc = idx % KC, j = idx / KC;
+    const int k = k0 + cc;
+    C2 z = xs[pad(cc * M + j)];
     z.x *= inv;
     z.y *= inv;
-    if (kk < nh1) spec[(size_t)r * nh1 + kk] = z;
+    if (j == 0) {
+      z.x = T(0);
+      z.y = T(0);
+    }
+    if (k < nh1) spec[(size_t)j * nh1 + k] = z;
   }
   __syncthreads();
 }
@@ -480,9 +590,11 @@ __global__ void __launch_bounds__(kFftSmallThreads) k_cols(
 
 // ------------------------------------------------------------------ batched launches
 // One block per work unit (the grid is nblk blocks); THREADS selects the transform class.
+// src: 0 the CH right-hand side Q, 1 the Poisson right-hand side, 2 / 3 the velocity
+// predictor right-hand sides held in the u / v slot 1 - cur
 template <typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS) kb_rows_fwd(const InstDev<T>* __restrict__ I,
-    const int2* __restrict__ blk, int nblk, int src) {
+    const int2* __restrict__ blk, int nblk, int src, int cur) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
@@ -491,7 +603,7 @@ __global__ void __launch_bounds__(THREADS) kb_rows_fwd(const InstDev<T>* __restr
   const InstDev<T>& d = I[w.x];
   const int rp = fft_per_block(d.nx);
   const int cnt = min(rp, d.ny / 2 - w.y * rp);
-  const T* in = src == 0 ? d.Q : d.rhs;
+  const T* in = src == 0 ? d.Q : (src == 1 ? d.rhs : (src == 2 ? d.U[1 - cur] : d.V[1 - cur]));
   C2* x = reinterpret_cast<C2*>(smem_raw);
   const size_t ra = 2 * (size_t)w.y * rp;
 #define IBPF_CASE(L) case L: rows_fwd_core<T, L, THREADS>(in, d.spec, d.twx, ra, cnt, x); break;
@@ -525,7 +637,58 @@ __global__ void __launch_bounds__(THREADS) kb_cols(const InstDev<T>* __restrict_
 #undef IBPF_CASE
 }
 
-// kind 1: C^{n+1} into the C^{n-1} slot (compensated in FP32); kind 2: P^{n+1} = P^ + dP
+// the velocity Helmholtz solves of the semi-implicit predictor: (1 - a L) with the DST-II
+// (u, no-slip ghost rows) and DST-I (v, zero wall faces) wall-normal bases
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) kb_cols_s2(const InstDev<T>* __restrict__ I,
+    const int2* __restrict__ blk, int nblk) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int2 w = blk[b];
+  const InstDev<T>& d = I[w.x];
+  SymbolArgs sym;
+  sym.mode = 2;
+  sym.c0 = d.a_visc;
+  sym.c0_f = (float)d.a_visc;
+  sym.lamx = d.lamx;
+  sym.lamy = d.lam_s2;
+  sym.lamx_f = d.lamx_f;
+  sym.lamy_f = d.lam_s2_f;
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const int nh1 = d.nx / 2 + 1, k0 = w.y * fft_per_block(d.ny);
+#define IBPF_CASE(L) case L: cols_core<T, L, THREADS, 8, true>(d.spec, nh1, d.twy, d.wd, sym, k0, x); break;
+  IBPF_DISPATCH(THREADS, d.logny)
+#undef IBPF_CASE
+}
+
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) kb_dst1(const InstDev<T>* __restrict__ I,
+    const int2* __restrict__ blk, int nblk) {
+  using C2 = typename C2T<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  if (b >= nblk) return;
+  const int2 w = blk[b];
+  const InstDev<T>& d = I[w.x];
+  SymbolArgs sym;
+  sym.mode = 2;
+  sym.c0 = d.a_visc;
+  sym.c0_f = (float)d.a_visc;
+  sym.lamx = d.lamx;
+  sym.lamx_f = d.lamx_f;
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  const T* ld1 = sizeof(T) == 8 ? (const T*)d.lam_d1 : (const T*)d.lam_d1_f;
+  const int nh1 = d.nx / 2 + 1, k0 = w.y * fft_per_block(2 * d.ny);
+#define IBPF_CASE(L) case L: dst1_core<T, L, THREADS>(d.spec, nh1, d.tw2, sym, ld1, k0, x); break;
+  IBPF_DISPATCH(THREADS, d.logny + 1)
+#undef IBPF_CASE
+}
+
+// kind 1: C^{n+1} into the C^{n-1} slot (compensated in FP32); kind 2: P^{n+1} = P^ + dP;
+// kind 3 / 4: the predicted velocity u** = alpha_u (u^n + du) / v** = alpha_v (v^n + dv)
+// into the u / v slot 1 - cur (rows 0 .. ny-1)
 template <typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restrict__ I,
     const int2* __restrict__ blk, int nblk, int kind, int cur) {
@@ -545,10 +708,15 @@ __global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restr
     epi.b_lo = d.Clo[1 - cur];
     epi.out_lo = d.Clo[1 - cur];
     out = d.C[1 - cur];
-  } else {
+  } else if (kind == 2) {
     epi.a = d.phat;
     epi.delta = d.dp;
     out = d.P[1 - cur];
+  } else {
+    epi.kind = 3;
+    epi.a = kind == 3 ? d.U[cur] : d.V[cur];
+    epi.alpha = kind == 3 ? d.au : d.av;
+    out = kind == 3 ? d.U[1 - cur] : d.V[1 - cur];
   }
   const int rp = fft_per_block(d.nx);
   const int cnt = min(rp, d.ny / 2 - w.y * rp);
@@ -563,32 +731,44 @@ __global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restr
 // Complex FFT of length ny = 2^LOGN along y of the KC = 8 THREADS / ny columns
 // kx0 .. kx0 + KC - 1 (columns at or beyond nh1 are skipped) of z-plane `plane` of the
 // spectrum spec[(k ny + j) nh1 + kx].  INV: inverse transform scaled by 1/ny.
-template <typename T, int LOGN, int THREADS, bool INV>
+template <typename T, int LOGN, int THREADS, bool INV, int P = 8>
 __device__ void yfft_core(typename C2T<T>::type* __restrict__ spec, int nh1, size_t plane,
                           const typename C2T<T>::type* __restrict__ tw, int kx0,
                           typename C2T<T>::type* xs) {
   using C2 = typename C2T<T>::type;
-  constexpr int N = 1 << LOGN, EB = 8 * THREADS, KC = EB / N;
-  static_assert(KC >= 1, "a block holds 8 points per thread");
-  C2* tws = xs + fft_buf(EB);
-  for (int t = threadIdx.x; t < N / 2; t += THREADS) tws[t] = tw[t];
+  constexpr int N = 1 << LOGN, EB = P * THREADS, KC = EB / N;
+  static_assert(KC >= 1, "a block holds P points per thread");
+  C2* tws = xs + xbuf(EB, N, P);
   C2* base = spec + plane * (size_t)N * nh1;
-  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
-    const int cc = idx % KC, j = idx / KC;
-    const int kx = kx0 + cc;
-    C2 v;
-    v.x = T(0);
-    v.y = T(0);
-    if (kx < nh1) v = base[(size_t)j * nh1 + kx];
-    xs[pad(cc * N + j)] = v;
+  for (int t = threadIdx.x; t < N / 2; t += THREADS) tws[t] = tw[t];
+  constexpr int LC = P < 16 ? P : 16;   // loads issued together, as in cols_core
+#pragma unroll
+  for (int q0 = 0; q0 < P; q0 += LC) {
+    C2 ld[LC];
+#pragma unroll
+    for (int q = 0; q < LC; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * THREADS;
+      const int cc = idx % KC, j = idx / KC;
+      const int kx = kx0 + cc;
+      ld[q].x = T(0);
+      ld[q].y = T(0);
+      if (kx < nh1) ld[q] = base[(size_t)j * nh1 + kx];
+    }
+#pragma unroll
+    for (int q = 0; q < LC; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * THREADS;
+      xs[xslot<N, P>(idx % KC, idx / KC)] = ld[q];
+    }
   }
   __syncthreads();
-  stockham<LOGN, 0, INV, THREADS, T>(xs, tws, KC);
+  stockham<LOGN, 0, INV, THREADS, T, P>(xs, tws, KC);
   const T sc = INV ? T(1) / T(N) : T(1);
-  for (int idx = threadIdx.x; idx < EB; idx += THREADS) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int idx = threadIdx.x + q * THREADS;
     const int cc = idx % KC, j = idx / KC;
     const int kx = kx0 + cc;
-    C2 v = xs[pad(cc * N + j)];
+    C2 v = xs[xslot<N, P>(cc, j)];
     v.x *= sc;
     v.y *= sc;
     if (kx < nh1) base[(size_t)j * nh1 + kx] = v;
@@ -678,6 +858,37 @@ cudaError_t tables_t(Instance& in) {
   cudaMemcpy(in.twy, twy.data(), sizeof(C2) * twy.size(), cudaMemcpyHostToDevice);
   e = cudaMemcpy(in.wdct, wd.data(), sizeof(C2) * wd.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
+  if (in.prm_ns_semi) {
+    // semi-implicit predictor: DST-II eigenvalues in the cosine order k (mode m = ny - k),
+    // DST-I eigenvalues of the modes 0 .. ny, twiddles of the 2 ny-point FFTs
+    std::vector<double> ls2(ny), ld1(ny + 1);
+    for (int k = 0; k < ny; ++k) {
+      const double cs = std::cos(M_PI * (double)k / (2.0 * (double)ny));
+      ls2[k] = -(4.0 / (h * h)) * cs * cs;
+    }
+    for (int m = 0; m <= ny; ++m) {
+      const double sn = std::sin(M_PI * (double)m / (2.0 * (double)ny));
+      ld1[m] = -(4.0 / (h * h)) * sn * sn;
+    }
+    std::vector<C2> tw2(ny);
+    for (int k = 0; k < ny; ++k) {
+      const double a = M_PI * (double)k / (double)ny;
+      tw2[k].x = (T)std::cos(a);
+      tw2[k].y = (T)(-std::sin(a));
+    }
+    std::vector<float> ls2f(ls2.begin(), ls2.end()), ld1f(ld1.begin(), ld1.end());
+    if ((e = cudaMalloc((void**)&in.lam_s2, sizeof(double) * ls2.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&in.lam_d1, sizeof(double) * ld1.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&in.lam_s2_f, sizeof(float) * ls2f.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&in.lam_d1_f, sizeof(float) * ld1f.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&in.tw2, sizeof(C2) * tw2.size())) != cudaSuccess) return e;
+    cudaMemcpy(in.lam_s2, ls2.data(), sizeof(double) * ls2.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(in.lam_d1, ld1.data(), sizeof(double) * ld1.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(in.lam_s2_f, ls2f.data(), sizeof(float) * ls2f.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(in.lam_d1_f, ld1f.data(), sizeof(float) * ld1f.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(in.tw2, tw2.data(), sizeof(C2) * tw2.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
   // the 4096-point class needs up to 120 KiB of shared memory (FP64)
   const int att = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaFuncSetAttribute(kb_rows_fwd<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
@@ -686,6 +897,10 @@ cudaError_t tables_t(Instance& in) {
   cudaFuncSetAttribute(kb_rows_fwd<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   cudaFuncSetAttribute(kb_rows_inv<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   cudaFuncSetAttribute(kb_cols<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_cols_s2<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_cols_s2<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_dst1<T, kFftSmallThreads>, (cudaFuncAttribute)att, 200 * 1024);
+  cudaFuncSetAttribute(kb_dst1<T, kFftLargeThreads>, (cudaFuncAttribute)att, 200 * 1024);
   return cudaGetLastError();
 }
 
@@ -745,6 +960,7 @@ cudaError_t tables3_t(Instance& in) {
   cudaFuncSetAttribute(k3_yfft<T, false, kT3Fft>, att, 200 * 1024);
   cudaFuncSetAttribute(k3_yfft<T, true, kT3Fft>, att, 200 * 1024);
   cudaFuncSetAttribute(k3_cols<T, kT3Fft>, att, 200 * 1024);
+
   return cudaGetLastError();
 }
 
@@ -769,7 +985,11 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, (const C2*)in.twx);
   if (rec) rec->mark("rows_fwd", s);
   const int nbp = (nh1 + yp - 1) / yp;
-  k3_yfft<T, false, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  auto yfft = [&](bool inv) {
+    if (inv) k3_yfft<T, true, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+    else k3_yfft<T, false, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  };
+  yfft(false);
   if (rec) rec->mark("y_fft", s);
   SymbolArgs sym;
   sym.mode = mode;
@@ -788,7 +1008,7 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   k3_cols<T, L><<<(ncols + cp - 1) / cp, L, csm, s>>>(spec, ncols, nz, (const C2*)in.twz,
                                                         (const C2*)in.wdct, sym);
   if (rec) rec->mark("z_solve", s);
-  k3_yfft<T, true, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
+  yfft(true);
   if (rec) rec->mark("y_ifft", s);
   EpiArgs epi;
   T* out;
@@ -816,44 +1036,61 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
 template <typename T>
 int spectral_solve_batch(const BatchPlan& plan, int mode, int cur, cudaStream_t s,
                          Recorder* rec) {
+  // mode 0: Cahn-Hilliard (Q -> C^{n+1}), 1: Poisson (rhs -> P^{n+1}), 2 / 3: the semi-implicit
+  // predictor's u / v Helmholtz solves (dt F in the u** slot -> u** = alpha (u^n + d))
   const InstDev<T>* I = reinterpret_cast<const InstDev<T>*>(plan.d_inst);
   constexpr int S = kFftSmallThreads, L = kFftLargeThreads;
-  const int kind = mode == 0 ? 1 : 2;
+  const int kind = mode == 0 ? 1 : (mode == 1 ? 2 : (mode == 2 ? 3 : 4));
+  const char* cname = mode == 2 ? "vel_cols_u" : (mode == 3 ? "vel_cols_v" : "cols_solve");
+  const char* fname = mode >= 2 ? "vel_rows_fwd" : "rows_fwd";
+  const char* iname = mode >= 2 ? "vel_rows_inv" : "rows_inv";
   int n = 0;
   if (plan.nblk[kFamRows]) {
     kb_rows_fwd<T, S><<<plan.nblk[kFamRows], S, plan.rows_smem[0], s>>>(
-        I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode);
-    if (rec) rec->mark("rows_fwd", s);
+        I, plan.d_blk[kFamRows], plan.nblk[kFamRows], mode, cur);
+    if (rec) rec->mark(fname, s);
     ++n;
   }
   if (plan.nblk[kFamRowsL]) {
     kb_rows_fwd<T, L><<<plan.nblk[kFamRowsL], L, plan.rows_smem[1], s>>>(
-        I, plan.d_blk[kFamRowsL], plan.nblk[kFamRowsL], mode);
-    if (rec) rec->mark("rows_fwd", s);
+        I, plan.d_blk[kFamRowsL], plan.nblk[kFamRowsL], mode, cur);
+    if (rec) rec->mark(fname, s);
     ++n;
   }
-  if (plan.nblk[kFamCols]) {
-    kb_cols<T, S><<<plan.nblk[kFamCols], S, plan.cols_smem[0], s>>>(
-        I, plan.d_blk[kFamCols], plan.nblk[kFamCols], mode);
-    if (rec) rec->mark("cols_solve", s);
-    ++n;
-  }
-  if (plan.nblk[kFamColsL]) {
-    kb_cols<T, L><<<plan.nblk[kFamColsL], L, plan.cols_smem[1], s>>>(
-        I, plan.d_blk[kFamColsL], plan.nblk[kFamColsL], mode);
-    if (rec) rec->mark("cols_solve", s);
-    ++n;
+  if (mode <= 2) {
+    for (int c = 0; c < 2; ++c) {
+      const int f = c ? kFamColsL : kFamCols;
+      if (!plan.nblk[f]) continue;
+      if (mode == 2) {
+        if (c) kb_cols_s2<T, L><<<plan.nblk[f], L, plan.cols_smem[1], s>>>(I, plan.d_blk[f], plan.nblk[f]);
+        else kb_cols_s2<T, S><<<plan.nblk[f], S, plan.cols_smem[0], s>>>(I, plan.d_blk[f], plan.nblk[f]);
+      } else {
+        if (c) kb_cols<T, L><<<plan.nblk[f], L, plan.cols_smem[1], s>>>(I, plan.d_blk[f], plan.nblk[f], mode);
+        else kb_cols<T, S><<<plan.nblk[f], S, plan.cols_smem[0], s>>>(I, plan.d_blk[f], plan.nblk[f], mode);
+      }
+      if (rec) rec->mark(cname, s);
+      ++n;
+    }
+  } else {
+    for (int c = 0; c < 2; ++c) {
+      const int f = c ? kFamD1L : kFamD1;
+      if (!plan.nblk[f]) continue;
+      if (c) kb_dst1<T, L><<<plan.nblk[f], L, plan.d1_smem[1], s>>>(I, plan.d_blk[f], plan.nblk[f]);
+      else kb_dst1<T, S><<<plan.nblk[f], S, plan.d1_smem[0], s>>>(I, plan.d_blk[f], plan.nblk[f]);
+      if (rec) rec->mark(cname, s);
+      ++n;
+    }
   }
   if (plan.nblk[kFamRows]) {
     kb_rows_inv<T, S><<<plan.nblk[kFamRows], S, plan.rows_smem[0], s>>>(
         I, plan.d_blk[kFamRows], plan.nblk[kFamRows], kind, cur);
-    if (rec) rec->mark("rows_inv", s);
+    if (rec) rec->mark(iname, s);
     ++n;
   }
   if (plan.nblk[kFamRowsL]) {
     kb_rows_inv<T, L><<<plan.nblk[kFamRowsL], L, plan.rows_smem[1], s>>>(
         I, plan.d_blk[kFamRowsL], plan.nblk[kFamRowsL], kind, cur);
-    if (rec) rec->mark("rows_inv", s);
+    if (rec) rec->mark(iname, s);
     ++n;
   }
   return n;

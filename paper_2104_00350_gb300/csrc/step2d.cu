@@ -24,6 +24,17 @@ __device__ __forceinline__ int wrap_m(int i, int nx) { return i == 0 ? nx - 1 : 
 
 __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : i + 1; }
 
+// cell-centred velocity components at cell c (mean of the two faces)
+template <typename T>
+__device__ __forceinline__ T ucen(const T* __restrict__ u, int nx, int c) {
+  const int i = c % nx;
+  return T(0.5) * (u[c] + u[c - i + wrap_p(i, nx)]);
+}
+template <typename T>
+__device__ __forceinline__ T vcen(const T* __restrict__ v, int nx, int c) {
+  return T(0.5) * (v[c] + v[c + nx]);
+}
+
 // ---------------------------------------------------------------- a1: CH right-hand side
 // The combined solve (L^2 - (S/Cn^2) L + c0) C^{n+1} = Q of Appendix A.1, with
 //   Q = (Pe/Cn^2)(C_check/dt - div(u~ C~)) + lap[(psi'(C~) - S C~)/Cn^2],  c0 = 1.5 Pe/(Cn^2 dt),
@@ -34,9 +45,11 @@ __device__ __forceinline__ int wrap_p(int i, int nx) { return i == nx - 1 ? 0 : 
 //   h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B),
 // which is small, so the solve's rounding stays relative to the change of C in one step.
 // k_ch_h writes h; k_ch_rhs writes R.
+// Also returns phi~ = psi'(C~) - Cn^2 lap(C~), the chemical potential of C~ that the wall term
+// below fills at the ghosts (written to the rhs scratch, which the CH phase does not use).
 template <typename T>
 __device__ __forceinline__ T ch_h_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                       const T* __restrict__ Co, int i, int j) {
+                                       const T* __restrict__ Co, int i, int j, T& phit) {
   const int nx = a.nx, ny = a.ny;
   const int im = wrap_m(i, nx), ip = wrap_p(i, nx);
   const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
@@ -45,11 +58,15 @@ __device__ __forceinline__ T ch_h_cell(const StepArgs<T>& a, const T* __restrict
   // only the small difference meets a rounded constant, so B carries no rounding bias
   const T third = T(1.0 / 3.0);
   auto bdf = [&](size_t idx) { return C[idx] + (C[idx] - Co[idx]) * third; };
+  auto ctl = [&](size_t idx) { return T(2) * C[idx] - Co[idx]; };
   const T b0 = bdf(r + i);
-  const T lapb = (((bdf(r + ip) + bdf(r + im)) + (bdf((size_t)jn * nx + i) + bdf((size_t)js * nx + i))) -
-                  T(4) * b0) * a.inv_h2;
+  const size_t qn = (size_t)jn * nx + i, qs = (size_t)js * nx + i;
+  const T lapb = (((bdf(r + ip) + bdf(r + im)) + (bdf(qn) + bdf(qs))) - T(4) * b0) * a.inv_h2;
   const T d = C[r + i] - Co[r + i];
   const T ct = C[r + i] + d;
+  const T c0 = ctl(r + i);
+  const T lapc = (((ctl(r + ip) + ctl(r + im)) + (ctl(qn) + ctl(qs))) - T(4) * c0) * a.inv_h2;
+  phit = (c0 * c0 * c0 - c0) - a.eta2 * lapc;
   return ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
 }
 
@@ -116,6 +133,98 @@ __device__ __forceinline__ void fill_C_ghost(const StepArgs<T>& a, const Tables&
   if (Clo) Clo[t.gcell[g]] = T(0);   // a ghost value is exact as stored
 }
 
+// ---------------------------------------------- a3, dynamic angle (mu_f > 0)
+// Eq. WallBCS_recast for the per-ghost state C_I, one backward-Euler step in C_I:
+//   F(C) = (1 + a k) C - a cos(theta) g'(C) - R = 0,  a = dt/(mu_f Cn), k = kappa Cn/(gamma dn),
+//   R = C_I^n - dt v_t (dC/dx_t)_I + a k C_M,
+// linear where g' = 0 (|C| >= 1): C = R/(1 + a k) if that is outside (-1, 1); otherwise the one
+// root in [-1, 1] of (3/4) a cos C^2 + (1 + a k) C - (R + (3/4) a cos) = 0 (r2 = 2c/(b + sqrt D)
+// if it qualifies, else r1 = -(b + sqrt D)/(2 a')).  v_t and dC/dx_t at I: gamma-weighted means
+// of the ghost's value and the mirror value (Eq. interpolationAtWall) of the level-n centred
+// velocity and of central differences of C^{n+1} before the fill; t = (n2, -n1).  An unset
+// C_I (NaN) starts as the level-n wall value (gamma C^n_G + C^n_M)/(gamma + 1).  The results
+// go to scratch (C_G, B = kappa Cn dC/dn + cos g'(C_I), dC/dx_t): no cell is written while
+// other ghosts still read their neighbours.
+template <typename T>
+__device__ __forceinline__ void cgrad(const StepArgs<T>& a, const T* __restrict__ C, int c, T& gx,
+                                      T& gy) {
+  const int nx = a.nx, ny = a.ny;
+  const int i = c % nx, j = c / nx;
+  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
+  const size_t r = (size_t)j * nx;
+  const T half_inv_h = T(0.5) * a.inv_h;
+  gx = (C[r + wrap_p(i, nx)] - C[r + wrap_m(i, nx)]) * half_inv_h;
+  gy = (C[(size_t)jn * nx + i] - C[(size_t)js * nx + i]) * half_inv_h;
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_C_dynamic(const StepArgs<T>& a, const Tables& t,
+                                               const T* __restrict__ C1, const T* __restrict__ Cn,
+                                               const T* __restrict__ u, const T* __restrict__ v,
+                                               double* __restrict__ ci, T* __restrict__ gq, int g) {
+  const int nx = a.nx, ng = t.ng;
+  T m1 = T(0), m2 = T(0), n1c = T(0), n2c = T(0);
+  T u1 = T(0), v1 = T(0), u2 = T(0), v2 = T(0), gx1 = T(0), gy1 = T(0), gx2 = T(0), gy2 = T(0);
+#pragma unroll
+  for (int q = 0; q < kNap; ++q) {
+    const int c1 = t.ap1[(size_t)g * kNap + q], c2 = t.ap2[(size_t)g * kNap + q];
+    const T w1 = (T)t.w1[(size_t)g * kNap + q], w2 = (T)t.w2[(size_t)g * kNap + q];
+    m1 = m1 + w1 * C1[c1];
+    m2 = m2 + w2 * C1[c2];
+    n1c = n1c + w1 * Cn[c1];
+    n2c = n2c + w2 * Cn[c2];
+    u1 = u1 + w1 * ucen(u, nx, c1);
+    v1 = v1 + w1 * vcen(v, nx, c1);
+    u2 = u2 + w2 * ucen(u, nx, c2);
+    v2 = v2 + w2 * vcen(v, nx, c2);
+    T gx, gy;
+    cgrad(a, C1, c1, gx, gy);
+    gx1 = gx1 + w1 * gx;
+    gy1 = gy1 + w1 * gy;
+    cgrad(a, C1, c2, gx, gy);
+    gx2 = gx2 + w2 * gx;
+    gy2 = gy2 + w2 * gy;
+  }
+  // the wall value is state that changes by a small increment every step: it is held and
+  // updated in FP64 in both forms (in FP32 its rounding would accumulate like that of C)
+  const int cg = t.gcell[g];
+  const double gam = t.gamma[g], dn = t.dn[g];
+  const double gp1 = gam + 1.0;
+  const double cm = 2.0 * (double)m1 - (double)m2;
+  double ci_n = ci[g];
+  if (!isfinite(ci_n)) ci_n = (gam * (double)Cn[cg] + (2.0 * (double)n1c - (double)n2c)) / gp1;
+  T gxg, gyg;
+  cgrad(a, C1, cg, gxg, gyg);
+  const T tg = (T)gam, tp1 = (T)gp1;
+  const T uI = (tg * ucen(u, nx, cg) + (T(2) * u1 - u2)) / tp1;
+  const T vI = (tg * vcen(v, nx, cg) + (T(2) * v1 - v2)) / tp1;
+  const T gxI = (tg * gxg + (T(2) * gx1 - gx2)) / tp1;
+  const T gyI = (tg * gyg + (T(2) * gy1 - gy2)) / tp1;
+  const T n1 = (T)t.nrm[2 * g], n2 = (T)t.nrm[2 * g + 1];
+  const T gt = gxI * n2 - gyI * n1;
+  const double adv = (double)((uI * n2 - vI * n1) * gt);
+  const double ct = a.cos_th, aa = a.a_dyn;
+  const double k = a.k_wet / (gam * dn);
+  const double R = (ci_n - (double)a.dt * adv) + aa * k * cm;
+  const double qb = 1.0 + aa * k;
+  const double lin = R / qb;
+  const double qa = 0.75 * aa * ct;
+  const double qc = R + 0.75 * aa * ct;
+  double disc = qb * qb + 4.0 * qa * qc;
+  disc = disc > 0.0 ? disc : 0.0;
+  const double sq = sqrt(disc);
+  double cI = 2.0 * qc / (qb + sq);
+  if (!(fabs(cI) <= 1.0) && qa != 0.0) {
+    cI = -(qb + sq) / (2.0 * qa);
+    cI = cI > 1.0 ? 1.0 : (cI < -1.0 ? -1.0 : cI);
+  }
+  if (fabs(lin) >= 1.0) cI = lin;
+  ci[g] = cI;
+  gq[g] = (T)((gp1 * cI - cm) / gam);                                  // C_G (Eq. UpdateC)
+  gq[ng + g] = (T)(k * (cm - cI) + ct * (fabs(cI) < 1.0 ? 0.75 * (1.0 - cI * cI) : 0.0));   // B
+  gq[2 * ng + g] = gt;                                                 // (dC/dx_t)_I
+}
+
 // ------------------------------------------------------------- a4: chemical potential
 // phi = psi'(C) - Cn^2 lap C on every cell (Eq. Chemical-Potential, nondimensional)
 template <typename T>
@@ -138,37 +247,16 @@ __device__ __forceinline__ void fill_phi_ghost(const Tables& t, T* __restrict__ 
 
 // ------------------------------------------- a1, wall term: no flux of C through the wall
 // The explicit part of the split is lap(phi~)/Cn^2 with phi~ = psi'(C~) - Cn^2 lap(C~) the
-// chemical potential of C~ = 2C^n - C^{n-1}, and the wall condition d(phi)/dn = 0 of Eq.
-// AllBCs is imposed on it by the ghost fill of Sec. 4.2.2, phi~_G = phi~_M: h at a ghost cell
-// gains (phi~_M - phi~_G)/Cn^2, phi~ evaluated at the averaging points and at G from C~.
-// Only ghost entries of h change and the averaging points are fluid cells, so ghosts do not
-// read one another's results.
-template <typename T>
-__device__ __forceinline__ T phit_cell(const StepArgs<T>& a, const T* __restrict__ C,
-                                       const T* __restrict__ Co, int c) {
-  const int nx = a.nx, ny = a.ny;
-  const int i = c % nx, j = c / nx;
-  const int js = j > 0 ? j - 1 : 0, jn = j < ny - 1 ? j + 1 : ny - 1;
-  const size_t r = (size_t)j * nx;
-  auto ct = [&](size_t idx) { return T(2) * C[idx] - Co[idx]; };
-  const T c0 = ct(r + i);
-  const T lap = (((ct(r + wrap_p(i, nx)) + ct(r + wrap_m(i, nx))) +
-                  (ct((size_t)jn * nx + i) + ct((size_t)js * nx + i))) - T(4) * c0) * a.inv_h2;
-  return (c0 * c0 * c0 - c0) - a.eta2 * lap;
-}
-
+// chemical potential of C~ = 2C^n - C^{n-1} (written by ch_h), and the wall condition
+// d(phi)/dn = 0 of Eq. AllBCs is imposed on it by the ghost fill of Sec. 4.2.2,
+// phi~_G = phi~_M: h at a ghost cell gains (phi~_M - phi~_G)/Cn^2.  Only ghost entries of h
+// change and phi~ is read, never written, so ghosts do not read one another's results.
 template <typename T>
 __device__ __forceinline__ void ch_wall_ghost(const StepArgs<T>& a, const Tables& t,
-                                              const T* __restrict__ C, const T* __restrict__ Co,
-                                              T* __restrict__ hf, int g) {
-  T m1 = T(0), m2 = T(0);
-#pragma unroll
-  for (int q = 0; q < kNap; ++q) {
-    m1 = m1 + (T)t.w1[(size_t)g * kNap + q] * phit_cell(a, C, Co, t.ap1[(size_t)g * kNap + q]);
-    m2 = m2 + (T)t.w2[(size_t)g * kNap + q] * phit_cell(a, C, Co, t.ap2[(size_t)g * kNap + q]);
-  }
+                                              const T* __restrict__ phit, T* __restrict__ hf, int g) {
+  const T pm = T(2) * gather(phit, t.ap1, t.w1, g) - gather(phit, t.ap2, t.w2, g);
   const int c = t.gcell[g];
-  hf[c] = hf[c] + ((T(2) * m1 - m2) - phit_cell(a, C, Co, c)) * a.inv_eta2;
+  hf[c] = hf[c] + (pm - phit[c]) * a.inv_eta2;
 }
 
 // ----------------------------------------------------- a5: AB2 predictor + penalisation
@@ -271,24 +359,94 @@ __device__ __forceinline__ void predict_point(const StepArgs<T>& a, const Predic
   }
 }
 
+// -------------------------------------- a5, semi-implicit predictor (Appendix A.2)
+// Eq. predictionSemi: u* = u^n + d, (1 - (dt nu0/2) L) d = dt F with
+//   F = (3/2 N^n - 1/2 N^{n-1}) + ST + V^n + MF,  N = -div(u u),  V = div(mu (grad u + grad u^T))/(Re rho_f)
+// (the history field holds N only), ST the surface tension as in predict_point, and the
+// mass-flux term MF = (rho'/(rho_f Pe)) (grad phi . grad) u, rho' = (rho_l - rho_g)/2: the
+// chemical potential's gradient by the difference across the face and the mean of the two
+// cells' central differences along it, the velocity's by central differences of its own
+// faces.  This kernel writes dt F into the u** slot (the solves and the penalisation follow
+// in the row / column transforms) and N into the history.
+template <typename T>
+__device__ __forceinline__ void predict_point_semi(const StepArgs<T>& a, const PredictSmem<T>& sm,
+                                                   int i, int j, int lx, int ly, T hu_old, T hv_old,
+                                                   T* __restrict__ Hu, T* __restrict__ Hv,
+                                                   T* __restrict__ fu, T* __restrict__ fv) {
+  const int nx = a.nx;
+  const int tx = lx + 1, ty = ly + 1;
+  const size_t r = (size_t)j * nx;
+  auto Cs = [&](int di, int dj) { return sm.C[ty + dj][tx + di]; };
+  auto Us = [&](int di, int dj) { return sm.U[ty + dj][tx + di]; };
+  auto Vs = [&](int di, int dj) { return sm.V[ty + dj][tx + di]; };
+  auto Fs = [&](int di, int dj) { return sm.F[ty + dj][tx + di]; };
+  auto mu = [&](T c) { return a.mu_a + a.mu_b * clamp1(c); };
+  auto rho = [&](T c) { return a.rho_a + a.rho_b * clamp1(c); };
+  auto tau_xy = [&](int di, int dj) -> T {
+    const T ce = T(0.25) * (((Cs(di - 1, dj - 1) + Cs(di, dj - 1)) + Cs(di - 1, dj)) + Cs(di, dj));
+    const T dudy = (Us(di, dj) - Us(di, dj - 1)) * a.inv_h;
+    const T dvdx = (Vs(di, dj) - Vs(di - 1, dj)) * a.inv_h;
+    return mu(ce) * (dudy + dvdx);
+  };
+  auto uv = [&](int di, int dj) -> T {
+    return (T(0.5) * (Us(di, dj) + Us(di, dj - 1))) * (T(0.5) * (Vs(di, dj) + Vs(di - 1, dj)));
+  };
+  const T k_st = a.k_st, half_ih = T(0.5) * a.inv_h, mfc = (T)a.mf_coef;
+  // ---- x1-face (i, j)
+  {
+    const T cL = Cs(-1, 0), cR = Cs(0, 0);
+    const T rho_f = rho(T(0.5) * (cL + cR));
+    const T txx_R = T(2) * mu(cR) * ((Us(1, 0) - Us(0, 0)) * a.inv_h);
+    const T txx_L = T(2) * mu(cL) * ((Us(0, 0) - Us(-1, 0)) * a.inv_h);
+    const T visc = (txx_R - txx_L) * a.inv_h + (tau_xy(0, 1) - tau_xy(0, 0)) * a.inv_h;
+    const T ucR = T(0.5) * (Us(0, 0) + Us(1, 0));
+    const T ucL = T(0.5) * (Us(-1, 0) + Us(0, 0));
+    const T conv = (ucR * ucR - ucL * ucL) * a.inv_h + (uv(0, 1) - uv(0, 0)) * a.inv_h;
+    const T N = -conv;
+    const T V = qdiv(visc, a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(-1, 0))) * qdiv((cR - cL) * a.inv_h, rho_f);
+    const T phx = (Fs(0, 0) - Fs(-1, 0)) * a.inv_h;
+    const T phy = T(0.5) * ((Fs(0, 1) - Fs(0, -1)) * half_ih + (Fs(-1, 1) - Fs(-1, -1)) * half_ih);
+    const T ux = (Us(1, 0) - Us(-1, 0)) * half_ih, uy = (Us(0, 1) - Us(0, -1)) * half_ih;
+    const T mf = qdiv(mfc, rho_f) * (phx * ux + phy * uy);
+    Hu[r + i] = N;
+    fu[r + i] = a.dt * ((((T(1.5) * N - T(0.5) * hu_old) + st) + V) + mf);
+  }
+  // ---- x2-face (i, j), 1 <= j <= ny-1; the wall faces get 0
+  if (j >= 1) {
+    const T cB = Cs(0, -1), cA = Cs(0, 0);
+    const T rho_f = rho(T(0.5) * (cB + cA));
+    const T tyy_A = T(2) * mu(cA) * ((Vs(0, 1) - Vs(0, 0)) * a.inv_h);
+    const T tyy_B = T(2) * mu(cB) * ((Vs(0, 0) - Vs(0, -1)) * a.inv_h);
+    const T visc = (tau_xy(1, 0) - tau_xy(0, 0)) * a.inv_h + (tyy_A - tyy_B) * a.inv_h;
+    const T vcA = T(0.5) * (Vs(0, 0) + Vs(0, 1));
+    const T vcB = T(0.5) * (Vs(0, -1) + Vs(0, 0));
+    const T conv = (uv(1, 0) - uv(0, 0)) * a.inv_h + (vcA * vcA - vcB * vcB) * a.inv_h;
+    const T N = -conv;
+    const T V = qdiv(visc, a.Re * rho_f);
+    const T st = k_st * (T(0.5) * (Fs(0, 0) + Fs(0, -1))) * qdiv((cA - cB) * a.inv_h, rho_f);
+    const T phx = T(0.5) * ((Fs(1, 0) - Fs(-1, 0)) * half_ih + (Fs(1, -1) - Fs(-1, -1)) * half_ih);
+    const T phy = (Fs(0, 0) - Fs(0, -1)) * a.inv_h;
+    const T vx = (Vs(1, 0) - Vs(-1, 0)) * half_ih, vy = (Vs(0, 1) - Vs(0, -1)) * half_ih;
+    const T mf = qdiv(mfc, rho_f) * (phx * vx + phy * vy);
+    Hv[r + i] = N;
+    fv[r + i] = a.dt * ((((T(1.5) * N - T(0.5) * hv_old) + st) + V) + mf);
+  } else {
+    fv[r + i] = T(0);
+  }
+}
+
 // ------------------------------------------------------------- a6: velocity ghost fill
 // centred u** at the averaging points, mirror value by Eq. extrapolation, then
 // V_nG = -V_nM / gamma (Eq. NoPenetration), V_tG = V_tM (l_s - dn)/(l_s + gamma dn)
 // (Eq. UpdateVtan with the static-angle bracket zero), t = (n2, -n1), Eq. UpdateVandW.
-template <typename T>
-__device__ __forceinline__ T ucen(const T* __restrict__ u, int nx, int c) {
-  const int i = c % nx;
-  return T(0.5) * (u[c] + u[c - i + wrap_p(i, nx)]);
-}
-template <typename T>
-__device__ __forceinline__ T vcen(const T* __restrict__ v, int nx, int c) {
-  return T(0.5) * (v[c] + v[c + nx]);
-}
 
 template <typename T>
 __device__ __forceinline__ void fill_u_ghost(const StepArgs<T>& a, const Tables& t,
                                              const T* __restrict__ uss, const T* __restrict__ vss,
-                                             T* __restrict__ gu, T* __restrict__ gv, int g) {
+                                             T* __restrict__ gu, T* __restrict__ gv,
+                                             const double* __restrict__ ci, const T* __restrict__ gq,
+                                             int g) {
   const int nx = a.nx;
   T u1 = T(0), v1 = T(0), u2 = T(0), v2 = T(0);
 #pragma unroll
@@ -306,7 +464,14 @@ __device__ __forceinline__ void fill_u_ghost(const StepArgs<T>& a, const Tables&
   const T vnM = uM * n1 + vM * n2;
   const T vtM = uM * n2 - vM * n1;
   const T vnG = -vnM / gam;
-  const T vtG = vtM * (ls - dn) / (ls + gam * dn);
+  T vtG = vtM * (ls - dn) / (ls + gam * dn);
+  if (a.a_dyn > 0.0) {
+    // dynamic angle: -(1/Ca) B (dC/dx_t)_I l_s (gamma + 1) dn / (mu_I (l_s + gamma dn))
+    const int ng = t.ng;
+    const T mu_I = a.mu_a + a.mu_b * clamp1((T)ci[g]);
+    vtG = vtG - (gq[ng + g] * gq[2 * ng + g] * (T)a.inv_ca) * (ls * (gam + T(1)) * dn) /
+                    (mu_I * (ls + gam * dn));
+  }
   gu[g] = vnG * n1 + vtG * n2;
   gv[g] = vnG * n2 - vtG * n1;
 }
@@ -474,6 +639,9 @@ StepArgs<T> make_args(const Instance& in) {
   a.k_wet = kKappa * p.Cn;
   a.cos_th = std::cos(p.theta_deg * M_PI / 180.0);
   a.l_s = p.l_s;
+  a.a_dyn = p.mu_f > 0.0 ? p.dt / (p.mu_f * p.Cn) : 0.0;
+  a.inv_ca = 1.0 / p.Ca;
+  a.mf_coef = 0.5 * (rho_l - rho_g) / p.Pe;
   return a;
 }
 
@@ -503,16 +671,19 @@ __global__ void IBPF_CELL_BOUNDS kb_ch_h(const InstDev<T>* __restrict__ I, const
     tile_base(d, w_.y, i, jb);
     // all rows are computed before any is stored, so that the loads of every row are in
     // flight together (a store could alias a later row's loads as far as the compiler knows)
-    T out[kRowsPerThread];
+    T out[kRowsPerThread], pt[kRowsPerThread];
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
-      if (i < d.nx && j < d.ny) out[q] = ch_h_cell(d.a, d.C[cur], d.C[1 - cur], i, j);
+      if (i < d.nx && j < d.ny) out[q] = ch_h_cell(d.a, d.C[cur], d.C[1 - cur], i, j, pt[q]);
     }
 #pragma unroll
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int j = jb + q * kTileY;
-      if (i < d.nx && j < d.ny) d.phi[(size_t)j * d.nx + i] = out[q];
+      if (i < d.nx && j < d.ny) {
+        d.phi[(size_t)j * d.nx + i] = out[q];
+        if (d.tab.ng > 0) d.rhs[(size_t)j * d.nx + i] = pt[q];
+      }
     }
   }
 }
@@ -551,20 +722,31 @@ __global__ void kb_ch_wall(const InstDev<T>* __restrict__ I, const int2* __restr
   const int2 w_ = blk[b_];
   const InstDev<T>& d = I[w_.x];
   const int g = w_.y * kGhostChunk + threadIdx.x;
-  if (g < d.tab.ng) ch_wall_ghost(d.a, d.tab, d.C[cur], d.C[1 - cur], d.phi, g);
+  if (g < d.tab.ng) ch_wall_ghost(d.a, d.tab, d.rhs, d.phi, g);
 }
 
-// C^{n+1} sits in slot 1 - cur after the CH solve
+// C^{n+1} sits in slot 1 - cur after the CH solve.  Static angle: one pass.  Dynamic angle
+// (instances with mu_f > 0): pass 0 computes into scratch, pass 1 writes the ghost cells.
 template <typename T>
 __global__ void kb_fill_C(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk, int nblk,
-                          int cur) {
+                          int cur, int pass) {
   {   // one block per work unit (the grid is nblk blocks)
     const int b_ = blockIdx.x;
     if (b_ >= nblk) return;
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int g = w_.y * kGhostChunk + threadIdx.x;
-    if (g < d.tab.ng) fill_C_ghost(d.a, d.tab, d.C[1 - cur], d.Clo[1 - cur], g);
+    if (g >= d.tab.ng) return;
+    if (d.a.a_dyn > 0.0) {
+      if (pass == 0) {
+        fill_C_dynamic(d.a, d.tab, d.C[1 - cur], d.C[cur], d.U[cur], d.V[cur], d.ci, d.gq, g);
+      } else {
+        d.C[1 - cur][d.tab.gcell[g]] = d.gq[g];
+        if (d.Clo[1 - cur]) d.Clo[1 - cur][d.tab.gcell[g]] = T(0);
+      }
+    } else if (pass == 0) {
+      fill_C_ghost(d.a, d.tab, d.C[1 - cur], d.Clo[1 - cur], g);
+    }
   }
 }
 
@@ -605,8 +787,8 @@ __global__ void kb_fill_phi(const InstDev<T>* __restrict__ I, const int2* __rest
   }
 }
 
-// u** goes into the u^{n-1} slot (1 - cur)
-template <typename T>
+// u** goes into the u^{n-1} slot (1 - cur); SEMI: dt F of the semi-implicit predictor
+template <typename T, bool SEMI>
 __global__ void IBPF_CELL_BOUNDS kb_predict(const InstDev<T>* __restrict__ I, const int2* __restrict__ blk,
                            int nblk, int cur) {
   __shared__ PredictSmem<T> sm;
@@ -636,9 +818,14 @@ __global__ void IBPF_CELL_BOUNDS kb_predict(const InstDev<T>* __restrict__ I, co
     for (int q = 0; q < kRowsPerThread; ++q) {
       const int ly = threadIdx.y + q * kTileY;
       const int j = j0 + ly;
-      if (i < d.nx && j < d.ny)
-        predict_point(d.a, sm, i, j, threadIdx.x, ly, huo[q], hvo[q], au[q], av[q], d.Hu, d.Hv,
-                      d.U[1 - cur], d.V[1 - cur]);
+      if (i < d.nx && j < d.ny) {
+        if constexpr (SEMI)
+          predict_point_semi(d.a, sm, i, j, threadIdx.x, ly, huo[q], hvo[q], d.Hu, d.Hv,
+                             d.U[1 - cur], d.V[1 - cur]);
+        else
+          predict_point(d.a, sm, i, j, threadIdx.x, ly, huo[q], hvo[q], au[q], av[q], d.Hu, d.Hv,
+                        d.U[1 - cur], d.V[1 - cur]);
+      }
     }
     __syncthreads();
   }
@@ -653,7 +840,7 @@ __global__ void kb_fill_u(const InstDev<T>* __restrict__ I, const int2* __restri
     const int2 w_ = blk[b_];
     const InstDev<T>& d = I[w_.x];
     const int g = w_.y * kGhostChunk + threadIdx.x;
-    if (g < d.tab.ng) fill_u_ghost(d.a, d.tab, d.U[1 - cur], d.V[1 - cur], d.gu, d.gv, g);
+    if (g < d.tab.ng) fill_u_ghost(d.a, d.tab, d.U[1 - cur], d.V[1 - cur], d.gu, d.gv, d.ci, d.gq, g);
   }
 }
 
@@ -816,6 +1003,21 @@ __global__ void IBPF_CELL_BOUNDS kq_ch_h(const InstDev<float>* __restrict__ I, c
     return ((ct * ct * ct - ct) - a.S * (2.0f * third * dd)) * a.inv_eta2 - lap5q(a, b, bx, bn, bs, e);
   });
   if (r.act) st4(d.phi, r.q, out);
+  if (d.tab.ng > 0) {
+    // phi~ = psi'(C~) - Cn^2 lap(C~) for the wall term (ch_wall), into the rhs scratch
+    auto T4 = [&](size_t q) {
+      const V4 x = ld4(C, q), y = ld4(Co, q);
+      return map4([&](int e) { return 2.0f * x.e[e] - y.e[e]; });
+    };
+    const V4 ct = map4([&](int e) { return 2.0f * c.e[e] - o.e[e]; });
+    const V4 tn = T4(r.n), ts = T4(r.s);
+    const X2 tx = xnb2(ct, r, d.nx, [&](size_t q) { return 2.0f * C[q] - Co[q]; });
+    const V4 pt = map4([&](int e) {
+      const float x = ct.e[e];
+      return (x * x * x - x) - a.eta2 * lap5q(a, ct, tx, tn, ts, e);
+    });
+    if (r.act) st4(d.rhs, r.q, pt);
+  }
 }
 
 __global__ void IBPF_CELL_BOUNDS kq_ch_rhs(const InstDev<float>* __restrict__ I, const int2* __restrict__ blk,
@@ -1170,8 +1372,12 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
   }
   // a3: contact-angle ghost fill
   if (ng > 0) {
-    kb_fill_C<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
+    kb_fill_C<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur, 0);
     mark("fill_C");
+    if (c.dynamic) {
+      kb_fill_C<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur, 1);
+      mark("fill_C");
+    }
   }
   // a4: chemical potential and its ghost fill
   if constexpr (sizeof(T) == 4) kq_chem_pot<<<nc, tile, 0, s>>>(I, bc, nc, cur);
@@ -1181,9 +1387,17 @@ int step_batch_t(const Ctx& c, const BatchPlan& plan, int cur, cudaStream_t s, R
     kb_fill_phi<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng);
     mark("fill_phi");
   }
-  // a5: predictor + penalisation, u** into slot 1 - cur
-  kb_predict<T><<<nc, tile, 0, s>>>(I, bc, nc, cur);
-  mark("predict");
+  // a5: predictor + penalisation, u** into slot 1 - cur (semi-implicit: the right-hand sides,
+  // then the two velocity Helmholtz solves, whose inverse row transforms penalise)
+  if (c.ns_scheme == IB_PF_NS_SEMI_IMPLICIT) {
+    kb_predict<T, true><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("predict");
+    launches += spectral_solve_batch<T>(plan, 2, cur, s, rec);
+    launches += spectral_solve_batch<T>(plan, 3, cur, s, rec);
+  } else {
+    kb_predict<T, false><<<nc, tile, 0, s>>>(I, bc, nc, cur);
+    mark("predict");
+  }
   // a6: velocity ghost fill and face re-interpolation
   if (ng > 0) {
     kb_fill_u<T><<<ng, kGhostChunk, 0, s>>>(I, bg, ng, cur);
@@ -1214,6 +1428,7 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
   std::vector<InstDev<T>> host(n);
   std::vector<int2> fam[kNumFam];
   int rmax[2] = {0, 0}, cmax[2] = {0, 0};   // longest row / column per transform class
+  int dmax[2] = {0, 0};                     // longest doubled column (DST-I) per class
   plan.max_nx = plan.max_ny = 0;
   for (int k = 0; k < n; ++k) {
     Instance& in = c.inst[k];
@@ -1242,6 +1457,8 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.gu = (T*)in.gu;
     d.gv = (T*)in.gv;
     d.fval = (T*)in.fval;
+    d.ci = (double*)in.ci;
+    d.gq = (T*)in.gq;
     d.tab = in.tab;
     d.lamx = in.lamx;
     d.lamy = in.lamy;
@@ -1251,6 +1468,13 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     d.twy = (const C2*)in.twy;
     d.wd = (const C2*)in.wdct;
     d.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
+    // semi-implicit predictor: a = dt nu0 / 2, nu0 = (mu_l/rho_l + mu_g/rho_g) / (2 Re)
+    d.a_visc = 0.5 * in.prm.dt * 0.5 * (1.0 + (1.0 / in.prm.mu_ratio) / (1.0 / in.prm.rho_ratio)) / in.prm.Re;
+    d.lam_s2 = in.lam_s2;
+    d.lam_d1 = in.lam_d1;
+    d.lam_s2_f = in.lam_s2_f;
+    d.lam_d1_f = in.lam_d1_f;
+    d.tw2 = (const C2*)in.tw2;
     d.c0 = 1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt);
     d.partial = in.partial;
     d.ticket = in.ticket;
@@ -1262,10 +1486,17 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     const int rl = fft_threads(in.nx) == kFftLargeThreads, cl = fft_threads(in.ny) == kFftLargeThreads;
     for (int b = 0; b < (in.ny / 2 + rp - 1) / rp; ++b)
       fam[rl ? kFamRowsL : kFamRows].push_back(make_int2(k, b));
+    rmax[rl] = in.nx > rmax[rl] ? in.nx : rmax[rl];
     const int ncg = (in.nx / 2 + 1 + cp - 1) / cp;
     for (int b = 0; b < ncg; ++b) fam[cl ? kFamColsL : kFamCols].push_back(make_int2(k, b));
-    rmax[rl] = in.nx > rmax[rl] ? in.nx : rmax[rl];
     cmax[cl] = in.ny > cmax[cl] ? in.ny : cmax[cl];
+    if (c.ns_scheme == IB_PF_NS_SEMI_IMPLICIT) {
+      // DST-I columns: complex FFTs of 2 ny points
+      const int dp = fft_per_block(2 * in.ny), dl = fft_threads(2 * in.ny) == kFftLargeThreads;
+      for (int b = 0; b < (in.nx / 2 + 1 + dp - 1) / dp; ++b)
+        fam[dl ? kFamD1L : kFamD1].push_back(make_int2(k, b));
+      dmax[dl] = 2 * in.ny > dmax[dl] ? 2 * in.ny : dmax[dl];
+    }
     for (int b = 0; b < (in.tab.ng + kGhostChunk - 1) / kGhostChunk; ++b)
       fam[kFamGhost].push_back(make_int2(k, b));
     const int nf = in.tab.nfu + in.tab.nfv;
@@ -1323,6 +1554,8 @@ cudaError_t batch_setup_t(Ctx& c, BatchPlan& plan) {
     const int eb = 8 * (c ? kFftLargeThreads : kFftSmallThreads);
     plan.rows_smem[c] = sizeof(C2) * (fft_buf(eb) + rmax[c] / 2);
     plan.cols_smem[c] = cols_smem_bytes<T>(cmax[c], eb, 8);
+    // DST-I blocks: points, twiddles of the doubled length, one eigenvalue part per column
+    plan.d1_smem[c] = sizeof(C2) * (size_t)(fft_buf(eb) + dmax[c] / 2) + sizeof(T) * (size_t)(eb / 16);
   }
   return cudaSuccess;
 }

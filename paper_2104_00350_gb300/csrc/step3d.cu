@@ -26,6 +26,7 @@ struct S3 {
   T rho_a, rho_b, mu_a, mu_b, rho0, inv_rho0, Re, k_st;
   T inv_pe;   // 1/Pe (explicit Cahn-Hilliard variant)
   double k_wet, cos_th, l_s;
+  double a_dyn, inv_ca;    // dynamic angle: dt / (mu_f Cn) (0: static), 1 / Ca
   // fields (level cur is n)
   const T* C;    // C^n
   const T* Co;   // C^{n-1}
@@ -38,6 +39,8 @@ struct S3 {
   const T *P, *Po;
   T *Q, *phi, *rhs, *phat, *dp;
   T *gu, *gv, *gw, *fval;
+  double* ci;    // dynamic angle: wall values C_I (state, FP64 in both forms)
+  T* gq;         // dynamic angle: scratch C_G, B, (dC/dx_t)_I (3)
   const T *au, *av, *aw;   // face fractions in the field type
   Tables tab;
   double* partial;
@@ -107,35 +110,133 @@ __global__ void k3_fill_C(S3<T> a) {
   if (a.C1lo) a.C1lo[t.gcell[g]] = T(0);
 }
 
-// a1, wall term: the wall's no-flux condition d(phi)/dn = 0 (Eq. AllBCs) on the chemical
-// potential phi~ = psi'(C~) - Cn^2 lap(C~) of C~ = 2C^n - C^{n-1}, imposed by the ghost fill
-// phi~_G = phi~_M of Sec. 4.2.2: h_G += (phi~_M - phi~_G)/Cn^2 (as the 2D step; only ghost
-// entries of h change, the averaging points are fluid cells)
+// dynamic angle (mu_f > 0): Eq. WallBCS_recast for the per-ghost state C_I, as the 2D step
+// (step2d.cu, fill_C_dynamic) with the vector forms v_t (dC/dx_t) = V_t . grad C and
+// (dC/dx_t)_I = grad C - (grad C . n) n; pass 0 computes into scratch, pass 1 writes the ghosts
 template <typename T>
-__device__ __forceinline__ T phit3(const S3<T>& a, size_t c) {
+__device__ __forceinline__ T cen3(const S3<T>& a, const T* __restrict__ f, size_t c, int axis) {
+  if (axis == 0) {
+    const int i = (int)(c & (size_t)(a.nx - 1));
+    return T(0.5) * (f[c] + f[c - i + ((i + 1) & (a.nx - 1))]);
+  }
+  if (axis == 1) {
+    const int j = (int)((c >> a.lnx) & (size_t)(a.ny - 1));
+    const size_t row0 = c - ((size_t)j << a.lnx);
+    return T(0.5) * (f[c] + f[row0 + ((size_t)((j + 1) & (a.ny - 1)) << a.lnx)]);
+  }
+  return T(0.5) * (f[c] + f[c + ((size_t)a.nx << a.lny)]);
+}
+
+template <typename T>
+__device__ __forceinline__ void cgrad3(const S3<T>& a, const T* __restrict__ C, size_t c, T* g) {
   int i, j, k;
   cell_ijk(a, c, i, j, k);
   const Nbr n = nbr(a, c, i, j, k);
-  auto ct = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
-  const T c0 = ct(c);
-  const T lap = ((((ct(n.xp) + ct(n.xm)) + (ct(n.yp) + ct(n.ym))) + (ct(n.zp) + ct(n.zm))) -
-                 T(6) * c0) * a.inv_h2;
-  return (c0 * c0 * c0 - c0) - a.eta2 * lap;
+  const T hh = T(0.5) * a.inv_h;
+  g[0] = (C[n.xp] - C[n.xm]) * hh;
+  g[1] = (C[n.yp] - C[n.ym]) * hh;
+  g[2] = (C[n.zp] - C[n.zm]) * hh;
 }
 
+template <typename T>
+__global__ void k3_fill_Cd(S3<T> a, int pass) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const Tables& t = a.tab;
+  const int ng = t.ng;
+  if (g >= ng) return;
+  if (pass == 1) {
+    a.C1[t.gcell[g]] = a.gq[g];
+    if (a.C1lo) a.C1lo[t.gcell[g]] = T(0);
+    return;
+  }
+  T m1 = T(0), m2 = T(0), n1c = T(0), n2c = T(0);
+  T U1[3] = {T(0), T(0), T(0)}, U2[3] = {T(0), T(0), T(0)};
+  T G1[3] = {T(0), T(0), T(0)}, G2[3] = {T(0), T(0), T(0)};
+  const T* uf[3] = {a.U, a.V, a.W};
+#pragma unroll
+  for (int q = 0; q < kNap3; ++q) {
+    const size_t c1 = t.ap1[(size_t)g * kNap3 + q], c2 = t.ap2[(size_t)g * kNap3 + q];
+    const T w1 = (T)t.w1[(size_t)g * kNap3 + q], w2 = (T)t.w2[(size_t)g * kNap3 + q];
+    m1 = m1 + w1 * a.C1[c1];
+    m2 = m2 + w2 * a.C1[c2];
+    n1c = n1c + w1 * a.C[c1];
+    n2c = n2c + w2 * a.C[c2];
+    T g1[3], g2[3];
+    cgrad3(a, (const T*)a.C1, c1, g1);
+    cgrad3(a, (const T*)a.C1, c2, g2);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      U1[d] = U1[d] + w1 * cen3(a, uf[d], c1, d);
+      U2[d] = U2[d] + w2 * cen3(a, uf[d], c2, d);
+      G1[d] = G1[d] + w1 * g1[d];
+      G2[d] = G2[d] + w2 * g2[d];
+    }
+  }
+  const size_t cg = (size_t)t.gcell[g];
+  // the wall value is state: held and updated in FP64 in both forms (see step2d.cu)
+  const double gam = t.gamma[g], dn = t.dn[g];
+  const double gp1 = gam + 1.0;
+  const double cm = 2.0 * (double)m1 - (double)m2;
+  double ci_n = a.ci[g];
+  if (!isfinite(ci_n)) ci_n = (gam * (double)a.C[cg] + (2.0 * (double)n1c - (double)n2c)) / gp1;
+  T gG[3];
+  cgrad3(a, (const T*)a.C1, cg, gG);
+  const T nn[3] = {(T)t.nrm[3 * (size_t)g], (T)t.nrm[3 * (size_t)g + 1], (T)t.nrm[3 * (size_t)g + 2]};
+  const T tg = (T)gam, tp1 = (T)gp1;
+  T UI[3], GI[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    UI[d] = (tg * cen3(a, uf[d], cg, d) + (T(2) * U1[d] - U2[d])) / tp1;
+    GI[d] = (tg * gG[d] + (T(2) * G1[d] - G2[d])) / tp1;
+  }
+  const T un = (UI[0] * nn[0] + UI[1] * nn[1]) + UI[2] * nn[2];
+  const T gn = (GI[0] * nn[0] + GI[1] * nn[1]) + GI[2] * nn[2];
+  T gt[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) gt[d] = GI[d] - gn * nn[d];
+  T advT;
+  {
+    const T vt0 = UI[0] - un * nn[0], vt1 = UI[1] - un * nn[1], vt2 = UI[2] - un * nn[2];
+    advT = (vt0 * GI[0] + vt1 * GI[1]) + vt2 * GI[2];
+  }
+  const double adv = (double)advT;
+  const double ct = a.cos_th, aa = a.a_dyn;
+  const double k = a.k_wet / (gam * dn);
+  const double R = (ci_n - (double)a.dt * adv) + aa * k * cm;
+  const double qb = 1.0 + aa * k;
+  const double lin = R / qb;
+  const double qa = 0.75 * aa * ct;
+  const double qc = R + 0.75 * aa * ct;
+  double disc = qb * qb + 4.0 * qa * qc;
+  disc = disc > 0.0 ? disc : 0.0;
+  const double sq = sqrt(disc);
+  double cI = 2.0 * qc / (qb + sq);
+  if (!(fabs(cI) <= 1.0) && qa != 0.0) {
+    cI = -(qb + sq) / (2.0 * qa);
+    cI = cI > 1.0 ? 1.0 : (cI < -1.0 ? -1.0 : cI);
+  }
+  if (fabs(lin) >= 1.0) cI = lin;
+  const double gpr = fabs(cI) < 1.0 ? 0.75 * (1.0 - cI * cI) : 0.0;
+  a.ci[g] = cI;
+  a.gq[g] = (T)((gp1 * cI - cm) / gam);
+  a.gq[ng + g] = (T)(k * (cm - cI) + ct * gpr);
+  a.gq[2 * ng + g] = gt[0];
+  a.gq[3 * ng + g] = gt[1];
+  a.gq[4 * ng + g] = gt[2];
+}
+
+// a1, wall term: the wall's no-flux condition d(phi)/dn = 0 (Eq. AllBCs) on the chemical
+// potential phi~ = psi'(C~) - Cn^2 lap(C~) of C~ = 2C^n - C^{n-1} (written by ch_h into the
+// rhs scratch), imposed by the ghost fill phi~_G = phi~_M of Sec. 4.2.2: h_G += (phi~_M -
+// phi~_G)/Cn^2 (as the 2D step; only ghost entries of h change, phi~ is only read)
 template <typename T>
 __global__ void k3_ch_wall(S3<T> a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const Tables& t = a.tab;
   if (g >= t.ng) return;
-  T m1 = T(0), m2 = T(0);
-#pragma unroll
-  for (int q = 0; q < kNap3; ++q) {
-    m1 = m1 + (T)t.w1[(size_t)g * kNap3 + q] * phit3(a, (size_t)t.ap1[(size_t)g * kNap3 + q]);
-    m2 = m2 + (T)t.w2[(size_t)g * kNap3 + q] * phit3(a, (size_t)t.ap2[(size_t)g * kNap3 + q]);
-  }
+  const T pm = T(2) * gather7((const T*)a.rhs, t.ap1, t.w1, g) - gather7((const T*)a.rhs, t.ap2, t.w2, g);
   const size_t c = (size_t)t.gcell[g];
-  a.phi[c] = a.phi[c] + ((T(2) * m1 - m2) - phit3(a, c)) * a.inv_eta2;
+  a.phi[c] = a.phi[c] + (pm - a.rhs[c]) * a.inv_eta2;
 }
 
 // zero normal gradient of phi at the wall: phi_G = phi_M
@@ -209,6 +310,20 @@ __global__ void __launch_bounds__(kTQ) k3_ch_h_q(S3<float> a) {
         const float ct = c.e[e] + dd;
         return ((ct * ct * ct - ct) - a.S * (2.0f * third * dd)) * a.inv_eta2 - lapb;
       }));
+  if (a.tab.ng > 0) {
+    // phi~ = psi'(C~) - Cn^2 lap(C~) for the wall term (k3_ch_wall), into the rhs scratch
+    auto T4 = [&](size_t q) {
+      const V4 x = ld4(a.C, q), y = ld4(a.Co, q);
+      return map4([&](int e) { return 2.0f * x.e[e] - y.e[e]; });
+    };
+    const V4 ct = map4([&](int e) { return 2.0f * c.e[e] - o.e[e]; });
+    const V4 typ = T4(d.yp), tym = T4(d.ym), tzp = T4(d.zp), tzm = T4(d.zm);
+    const X2 tx = xnb(ct, d, a.nx, [&](size_t q) { return 2.0f * a.C[q] - a.Co[q]; });
+    st4(a.rhs, d.q, map4([&](int e) {
+          const float x = ct.e[e];
+          return (x * x * x - x) - a.eta2 * lap7q(a, ct, tx, typ, tym, tzp, tzm, e);
+        }));
+  }
 }
 
 // a1: R = lap(h) - (Pe/Cn^2) div(u~ C~), u~ = 2u^n - u^{n-1}, C~ = 2C^n - C^{n-1}; no flux
@@ -881,14 +996,21 @@ __device__ __forceinline__ size_t cell_at(const S3<T>& a, const Tile& t, int k) 
 // h = (psi'(C~) - S (C~ - B))/Cn^2 - lap(B), B = C^n + (C^n - C^{n-1})/3, C~ - B = 2 d/3
 template <typename T>
 __global__ void __launch_bounds__(kPx * kPy) k3_ch_h_z(S3<T> a) {
-  __shared__ Win<T, 3> wb;
+  __shared__ Win<T, 3> wb, wt;
   const Tile t = tile3(a);
   const T third = T(1.0 / 3.0);
+  const bool wall = a.tab.ng > 0;
   auto B = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
+  auto CT = [&](size_t q) { return T(2) * a.C[q] - a.Co[q]; };
   win_load(wb, slot3(t.k0 - 1), a, t, t.k0 - 1, B);
   win_load(wb, slot3(t.k0), a, t, t.k0, B);
+  if (wall) {
+    win_load(wt, slot3(t.k0 - 1), a, t, t.k0 - 1, CT);
+    win_load(wt, slot3(t.k0), a, t, t.k0, CT);
+  }
   for (int k = t.k0; k < t.k0 + t.kz; ++k) {
     win_load(wb, slot3(k + 1), a, t, k + 1, B);
+    if (wall) win_load(wt, slot3(k + 1), a, t, k + 1, CT);
     __syncthreads();
     if (t.active) {
       const size_t c = cell_at(a, t, k);
@@ -896,6 +1018,10 @@ __global__ void __launch_bounds__(kPx * kPy) k3_ch_h_z(S3<T> a) {
       const T d = a.C[c] - a.Co[c];
       const T ct = a.C[c] + d;
       a.phi[c] = ((ct * ct * ct - ct) - a.S * (T(2) * third * d)) * a.inv_eta2 - lapb;
+      if (wall) {
+        const T c0 = T(2) * a.C[c] - a.Co[c];
+        a.rhs[c] = (c0 * c0 * c0 - c0) - a.eta2 * lap7w(wt, slot3(k - 1), slot3(k), slot3(k + 1), t, a.inv_h2);
+      }
     }
     __syncthreads();
   }
@@ -1096,9 +1222,21 @@ __global__ void k3_fill_u(S3<T> a) {
   const T vnM = (uM * n1 + vM * n2) + wM * n3;
   const T f = (ls - dn) / (ls + gam * dn);
   const T vnG = -vnM / gam;
-  a.gu[g] = vnG * n1 + f * (uM - vnM * n1);
-  a.gv[g] = vnG * n2 + f * (vM - vnM * n2);
-  a.gw[g] = vnG * n3 + f * (wM - vnM * n3);
+  T gu = vnG * n1 + f * (uM - vnM * n1);
+  T gv = vnG * n2 + f * (vM - vnM * n2);
+  T gw = vnG * n3 + f * (wM - vnM * n3);
+  if (a.a_dyn > 0.0) {
+    // dynamic angle: -(1/Ca) B (dC/dx_t)_I l_s (gamma + 1) dn / (mu_I (l_s + gamma dn))
+    const int ng = t.ng;
+    const T mu_I = a.mu_a + a.mu_b * clamp1((T)a.ci[g]);
+    const T c = (a.gq[ng + g] * (T)a.inv_ca) * (ls * (gam + T(1)) * dn) / (mu_I * (ls + gam * dn));
+    gu = gu - c * a.gq[2 * ng + g];
+    gv = gv - c * a.gq[3 * ng + g];
+    gw = gw - c * a.gq[4 * ng + g];
+  }
+  a.gu[g] = gu;
+  a.gv[g] = gv;
+  a.gw[g] = gw;
 }
 
 // faces with alpha_f < 1 touching a ghost: mean of the two cell-centred values (ghost value,
@@ -1177,6 +1315,10 @@ S3<T> make3(const Instance& in, int cur) {
   a.k_wet = kKappa * p.Cn;
   a.cos_th = std::cos(p.theta_deg * M_PI / 180.0);
   a.l_s = p.l_s;
+  a.a_dyn = p.mu_f > 0.0 ? p.dt / (p.mu_f * p.Cn) : 0.0;
+  a.inv_ca = 1.0 / p.Ca;
+  a.ci = (double*)in.ci;
+  a.gq = (T*)in.gq;
   const int n = cur, o = 1 - cur;
   a.C = (const T*)in.C[n];
   a.Co = (const T*)in.C[o];
@@ -1267,8 +1409,15 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       launches += spectral3_solve(in, ctx.precision, 0, cur, s, rec);
     }
     if (ng > 0) {
-      k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
-      mark("fill_C");
+      if (in.prm.mu_f > 0.0) {
+        k3_fill_Cd<T><<<(ng + 127) / 128, 128, 0, s>>>(a, 0);
+        mark("fill_C");
+        k3_fill_Cd<T><<<(ng + 127) / 128, 128, 0, s>>>(a, 1);
+        mark("fill_C");
+      } else {
+        k3_fill_C<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
+        mark("fill_C");
+      }
     }
     if constexpr (percell) k3_chem_pot_q<<<nb, kTQ, 0, s>>>(a);
     else k3_chem_pot_z<T><<<zg, zb, 0, s>>>(a);

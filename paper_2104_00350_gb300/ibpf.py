@@ -19,13 +19,14 @@ OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0,
 FP64, FP32 = 0, 1
 CH_SEMI_IMPLICIT, CH_EXPLICIT = 0, 1
 W_LINEAR, W_IDW = 0, 1            # ib_pf_weights
+NS_EXPLICIT, NS_SEMI_IMPLICIT = 0, 1   # ib_pf_ns_scheme
 WALL_FLAT, WALL_SINUSOID, WALL_NONE, WALL_SPHERE, WALL_SPHERES = 0, 1, 3, 4, 5
 (F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P,
- F_C_LO, F_C_OLD_LO, F_W, F_W_OLD, F_HW) = range(18)
+ F_C_LO, F_C_OLD_LO, F_W, F_W_OLD, F_HW, F_C_I) = range(19)
 FIELD_IDS = {"C": F_C, "C_old": F_C_OLD, "u": F_U, "u_old": F_U_OLD, "v": F_V, "v_old": F_V_OLD,
              "Hu": F_HU, "Hv": F_HV, "P": F_P, "P_old": F_P_OLD, "phi": F_PHI, "Q": F_Q,
              "rhs_p": F_RHS_P, "C_lo": F_C_LO, "C_old_lo": F_C_OLD_LO, "w": F_W,
-             "w_old": F_W_OLD, "Hw": F_HW}
+             "w_old": F_W_OLD, "Hw": F_HW, "C_I": F_C_I}
 STATE_FIELDS = ("C", "C_old", "u", "u_old", "v", "v_old", "Hu", "Hv", "P", "P_old")
 STATE_FIELDS_3D = STATE_FIELDS + ("w", "w_old", "Hw")
 (T_ALPHA_C, T_ALPHA_U, T_ALPHA_V, T_CLASS, T_GHOST_CELL, T_NORMAL, T_DN, T_GAMMA, T_AP1, T_W1,
@@ -54,7 +55,7 @@ PARAM_NAMES = ("Re", "Ca", "Cn", "Pe", "S", "rho_ratio", "mu_ratio", "theta_deg"
 
 class Params(ct.Structure):
     _fields_ = [(n, ct.c_double) for n in PARAM_NAMES] + [("precision", ct.c_int), ("ch_scheme", ct.c_int),
-                                                         ("weights", ct.c_int)]
+                                                         ("weights", ct.c_int), ("ns_scheme", ct.c_int)]
 
 
 class IbPfError(RuntimeError):
@@ -86,6 +87,7 @@ def _load():
         "ib_pf_kernel_times": (i, [vp, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_char_p),
                                    ct.POINTER(i)]),
         "ib_pf_poisson_solve_noalloc": (i, [vp, vp, i, i, ct.c_double, vp]),
+        "ib_pf_bind_fields": (i, [vp, i, i, i, vp, ct.c_longlong]),
         "ib_pf_last_error": (ct.c_char_p, [vp]),
         "ib_pf_destroy": (None, [vp]),
     }
@@ -196,6 +198,12 @@ def ib_pf_kernel_times(ctx, cap: int = 4096):
     return [names[i].decode() for i in range(k)], [ms[i] for i in range(k)]
 
 
+def ib_pf_bind_fields(ctx, instance: int, field_id: int, time_level: int, device_ptr: int,
+                      nbytes: int):
+    _check(lib().ib_pf_bind_fields(ctx, instance, field_id, time_level, ct.c_void_p(device_ptr),
+                                   nbytes), ctx)
+
+
 def ib_pf_poisson_solve_noalloc(rhs_ptr: int, out_ptr: int, nx: int, ny: int, h: float,
                                 stream: int = 0):
     _check(lib().ib_pf_poisson_solve_noalloc(ct.c_void_p(rhs_ptr), ct.c_void_p(out_ptr), nx, ny,
@@ -239,13 +247,14 @@ def make_geometry(kind: int, p, spheres=()) -> Geometry:
 
 
 def make_params(precision: int = FP64, ch_scheme: int = CH_SEMI_IMPLICIT, weights: int = 0,
-                **kw) -> Params:
+                ns_scheme: int = 0, **kw) -> Params:
     p = Params()
     for n in PARAM_NAMES:
         setattr(p, n, float(kw[n]))
     p.precision = precision
     p.ch_scheme = int(ch_scheme)
     p.weights = int(weights)
+    p.ns_scheme = int(ns_scheme)
     return p
 
 
@@ -259,6 +268,7 @@ class Solver:
         self.dim = grids[0].dim
         self.shapes = [(g.n[2], g.n[1], g.n[0]) if g.dim == 3 else (g.n[1], g.n[0]) for g in grids]
         self.state_fields = STATE_FIELDS_3D if self.dim == 3 else STATE_FIELDS
+        self.dynamic = any(p.mu_f > 0.0 for p in params)
 
     def close(self):
         if self.ctx:
@@ -271,12 +281,26 @@ class Solver:
         except Exception:
             pass
 
+    def field_dtype(self, name: str):
+        """Element type of a field: the context's, except the FP64 wall values C_I."""
+        return np.float64 if name == "C_I" else self.dtype
+
     def field_shape(self, name: str, instance: int = 0):
+        if name == "C_I":
+            return (int(self.query(Q_N_GHOST, instance)),)
         if self.dim == 3:
             nz, ny, nx = self.shapes[instance]
             return (nz + 1, ny, nx) if name in ("w", "w_old", "Hw") else (nz, ny, nx)
         ny, nx = self.shapes[instance]
         return (ny + 1, nx) if name in ("v", "v_old", "Hv") else (ny, nx)
+
+    def bind(self, name: str, tensor, time_level: int = 0, instance: int = 0):
+        """Make a contiguous torch CUDA tensor the storage of a state field (ib_pf_bind_fields);
+        the tensor must outlive the context (a reference is kept here)."""
+        assert tensor.is_cuda and tensor.is_contiguous()
+        ib_pf_bind_fields(self.ctx, instance, FIELD_IDS[name], time_level, tensor.data_ptr(),
+                          tensor.numel() * tensor.element_size())
+        self._bound = getattr(self, "_bound", []) + [tensor]
 
     def precompute_weights(self):
         ib_pf_precompute_weights(self.ctx)
@@ -290,7 +314,7 @@ class Solver:
             ib_pf_write_fields(self.ctx, instance, FIELD_IDS[name], arr.data_ptr(),
                                arr.numel() * arr.element_size(), not arr.is_cuda)
             return
-        a = np.ascontiguousarray(arr, dtype=self.dtype)
+        a = np.ascontiguousarray(arr, dtype=self.field_dtype(name))
         assert a.shape == self.field_shape(name, instance), (name, a.shape)
         ib_pf_write_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
 
@@ -299,7 +323,7 @@ class Solver:
             ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], out.data_ptr(),
                               out.numel() * out.element_size(), not out.is_cuda)
             return out
-        a = np.empty(self.field_shape(name, instance), dtype=self.dtype)
+        a = np.empty(self.field_shape(name, instance), dtype=self.field_dtype(name))
         ib_pf_read_fields(self.ctx, instance, FIELD_IDS[name], a.ctypes.data, a.nbytes, True)
         return a
 
@@ -351,11 +375,13 @@ class Solver:
         if self.precision == FP32:
             d["C_lo"] = self.read("C_lo", instance)
             d["C_old_lo"] = self.read("C_old_lo", instance)
+        if self.dynamic:
+            d["C_I"] = self.read("C_I", instance)
         return d
 
     def write_checkpoint(self, d: dict, instance: int = 0):
         self.write_state(d, instance)
-        for name in ("C_lo", "C_old_lo"):
+        for name in ("C_lo", "C_old_lo", "C_I"):
             if name in d:
                 self.write(name, d[name], instance)
 
@@ -397,5 +423,6 @@ def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:
     geoms = [make_geometry(c.geom_kind, c.geom_p, getattr(c, "spheres", ())) for c in cases]
     params = [make_params(precision, getattr(c.params, "ch_scheme", CH_SEMI_IMPLICIT),
                           getattr(c.params, "weights", W_LINEAR),
+                          getattr(c.params, "ns_scheme", NS_EXPLICIT),
                           **{n: getattr(c.params, n) for n in PARAM_NAMES}) for c in cases]
     return Solver(grids, geoms, params, stream)

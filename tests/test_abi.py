@@ -51,6 +51,7 @@ def _args(lib, nx=128, ny=64, **over):
     (dict(Cn=-1.0), -1),                # negative parameter
     (dict(mu_f=-0.5), -1),              # negative wall friction
     (dict(weights=7), -1),              # unknown averaging weights
+    (dict(ns_scheme=5), -1),            # unknown momentum predictor
     (dict(d1=0.001), -1),               # d1 not beyond half a cell diagonal
 ])
 def test_invalid_arguments_rejected_on_host(lib, bad, status):

@@ -39,7 +39,19 @@ CASES = {
     "porous32": lambda: W.porous_case(32, steps=1),
     "flat3d": lambda: W.flat_wall_case3d(nx=32, ny=16, nz=16, wall_z=0.37, l_s=0.01),
     "free3d": lambda: W.flat_wall_case3d(nx=16, ny=16, nz=8, geom_kind=W.GEOM_NONE),
+    # one long axis of 512 points each: the row transforms, the y transforms and the z
+    # solve at the transform lengths of the 512^3 workload (and, in z, 32 windows of the
+    # FP64 z-marching kernels; in the FP32 form, the wide y and z blocks)
+    "xlong": lambda: _long(512, 16, 16),
+    "ylong": lambda: _long(16, 512, 16),
+    "zlong": lambda: _long(16, 16, 512),
 }
+
+
+def _long(nx, ny, nz):
+    h = 2.0 / nx
+    return W.flat_wall_case3d(nx=nx, ny=ny, nz=nz, wall_z=0.37 * min(nz, 16) * h, l_s=0.01)
+
 
 _GEO = {}
 
@@ -108,7 +120,7 @@ def test_step_parity_3d_fp64(ibpf, name):
     assert abs(mass - ref["C"].sum()) <= 1e-12 * np.abs(ref["C"]).sum()
 
 
-@pytest.mark.parametrize("name", ["sphere32", "porous32"])
+@pytest.mark.parametrize("name", ["sphere32", "porous32", "xlong", "ylong", "zlong"])
 def test_step_parity_3d_fp32(ibpf, name):
     errs, _, _ = _step_parity(ibpf, name, seed=3, prec=ibpf.FP32)
     assert errs["C"] <= 5e-6, errs
