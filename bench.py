@@ -1,21 +1,26 @@
 #!/usr/bin/env python
 """Throughput of the hybrid IB / phase-field step on GB300 (one JSON line on rank 0).
 
-Workload: the sinusoidal-wall droplet, 512 x 256 cells on [0,2] x [0,1], wall
-y = 0.2 + 0.05 sin(4 pi x), R = 0.3, Cn = 0.01, Re = 10, Ca = 0.1, Pe = 1e4, dt from the
-viscous rule; its six runs (theta in {45, 90, 135} deg x l_s in {0, 0.01}) advance
-together, so one bench step is one full time step (a1..a8) of all six instances.
+Headline workload: the droplet over a random sphere packing, 512^3 cells on the unit cube
+(532 non-overlapping spheres r ~ U(0.03, 0.06) in z < 0.35, porosity 0.6, PCG64 seed 350),
+droplet R = 0.15 at the centre, theta = 60 deg, Cn = 0.005, Re = 10, Ca = 0.1, l_s = 0.002,
+Pe = 1e4, FP32 form.  One bench step is one full time step (a1..a8) of the 134M cells.
 
-  value     Mcell-steps/s = instances x cells x timed steps / device time of ib_pf_step,
-            inputs resident in HBM, L2 flushed (256 MiB write) before every timed step.
+  value     Mcell-steps/s = cells x timed steps / device time of ib_pf_step (CUDA events on
+            the work stream), inputs resident in HBM; the working set (about 15 GB) is far
+            larger than L2, so no flush is needed.
   e2e       the same metric through the C ABI with host buffers: every step writes the
-            whole state from pinned host memory, steps, and reads C back to the host.
-  roofline  dominant kernel of a second, event-instrumented pass over the same steps.
-  batched_ensemble / workloads_3d / explicit_ch: the 64-instance FP32 ensemble, the 3D
-            sphere (256^3) and packing (512^3) workloads, and the headline workload with the
-            explicit Cahn-Hilliard variant (Eq. ExpCH), each with its per-kernel roofline.
-  cpu_baseline / --impl reference: the FP64 CPU oracle (test infrastructure) timed on
-            the host cores.
+            whole state (13 FP32 fields) from pinned host memory, steps, and reads C back.
+  roofline  dominant kernel of a second, event-instrumented pass over the same steps, with
+            the per-kernel table (stencil kernels: algorithmic bytes per cell; ghost-cell
+            gathers and face kernels: algorithmic bytes per ghost / face).
+  workloads_3d / workloads_2d: the 256^3 droplet on a sphere (FP32, FP64, explicit
+            Cahn-Hilliard variant), the six 512 x 256 sinusoidal-wall runs (FP32, FP64,
+            explicit variant) and the 64-instance batched FP32 ensemble, each with its
+            per-kernel roofline table.
+  cpu_baseline / --impl reference: the FP64 CPU oracle (test infrastructure) on a bounded
+            sample of the headline workload: the same packing and parameters on a 32^3 grid,
+            one oracle process per host core, each advancing its own copy.
 
 Multi-GPU (torchrun): every rank runs its own copy of the workload (independent problems,
 no data-path collective); value = all ranks' cell-steps / max-over-ranks time.
@@ -38,6 +43,7 @@ if str(ROOT) not in sys.path:
 
 METRIC = "Mcell-steps/s per full CH+NS step (plain FP64 vs FP32/split, batched) at stated error"
 UNIT = "Mcell-steps/s"
+HEADLINE = "porous_512"
 THETAS = (45.0, 90.0, 135.0)
 SLIPS = (0.0, 0.01)
 L2_FLUSH_BYTES = 256 << 20
@@ -45,7 +51,7 @@ L2_FLUSH_BYTES = 256 << 20
 # Algorithmic traffic per cell and per step, summed over the launches of each kernel name:
 # field words read once and written once (FP32 form, FP64 form) plus FP64 geometry words.
 KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form table words)
-    "ch_h": (3, 3, 0),           # C, Co -> h
+    "ch_h": (4, 4, 0),           # C, Co -> h, phi~ (phi~ for the wall term)
     "ch_rhs": (8, 8, 0),         # C, Co, u, uo, v, vo, h -> R
     "rows_fwd": (4, 4, 0),       # 2 launches: real rows in, half spectrum out
     "cols_solve": (4, 4, 0),     # 2 launches: half spectrum in and out
@@ -65,7 +71,7 @@ KERNEL_STEP_WORDS = {     # name: (FP32-form words, FP64-form words, FP64-form t
 # the same for the 3D step (field words per cell and step, FP32 form / FP64 form / FP64
 # table words of the FP64 form)
 KERNEL_STEP_WORDS_3D = {
-    "ch_h": (3, 3, 0),           # C, Co -> h
+    "ch_h": (4, 4, 0),           # C, Co -> h, phi~ (phi~ for the wall term)
     "ch_rhs": (10, 10, 0),       # C, Co, u, uo, v, vo, w, wo, h -> R
     "rows_fwd": (4, 4, 0),       # 2 launches: real rows in, half spectrum out
     "y_fft": (4, 4, 0),          # 2 launches: spectrum in and out
@@ -97,6 +103,29 @@ def kernel_step_bytes(name: str, esz: int, cells: int, table=None) -> float:
     return float((w32 * 4 if esz == 4 else w64 * 8 + g * 8) * cells)
 
 
+def sparse_unit_bytes(name: str, esz: int, dim: int):
+    """Algorithmic bytes per unit (ghost or face) of the sparse kernels, and the unit.
+    Tables: averaging cells (int32) and weights (FP64), 2 nap of each per ghost (nap = 5 in
+    2D, 7 in 3D), the ghost's cell index, gamma and dn, the normal (dim FP64); field words
+    once per gathered value; one write per output word."""
+    nap = 5 if dim == 2 else 7
+    tab = 2 * nap * (4 + 8)
+    if name == "fill_C":      # C at the 2 nap cells -> C_G (+ low part zeroed in FP32)
+        return tab + 4 + 16 + 2 * nap * esz + (2 if esz == 4 else 1) * esz, "ghost"
+    if name in ("fill_phi", "ch_fill2"):   # phi (and phi^{n-1}) at the 2 nap cells -> phi_G
+        k = 2 if name == "ch_fill2" else 1
+        return tab + 4 + k * (2 * nap + 1) * esz, "ghost"
+    if name == "ch_wall":     # phi~ at the 2 nap cells and G; h_G read and written
+        return tab + 4 + (2 * nap + 1) * esz + 2 * esz, "ghost"
+    if name == "fill_u":      # 2 face words per component at the 2 nap cells -> dim words
+        return tab + 16 + 8 * dim + 2 * nap * 2 * dim * esz + dim * esz, "ghost"
+    if name == "face_values":  # face index, 2 cell classes, 2 centred values (2 words), write
+        return 4 + 8 + 4 * esz + esz, "face"
+    if name == "face_scatter":  # face index, staged value -> face
+        return 4 + 2 * esz, "face"
+    return None, None
+
+
 def workload_cases():
     from workloads import cases
     return [cases.sinusoid_wall_512x256(theta_deg=t, l_s=s) for t in THETAS for s in SLIPS]
@@ -105,19 +134,20 @@ def workload_cases():
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("both", "fp64", "fp32"), default="both",
                     help="both: FP32 form is the headline, plain FP64 reported beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-3d", action="store_true",
-                    help="skip the 3D sphere (256^3) and porous (512^3) workloads")
+                    help="skip the 3D sphere (256^3) workloads (the 512^3 headline always runs)")
     ap.add_argument("--no-ensemble", action="store_true",
                     help="skip the 64-instance batched-ensemble measurement")
     ap.add_argument("--no-explicit", action="store_true",
-                    help="skip the explicit Cahn-Hilliard variant of the headline workload")
-    ap.add_argument("--cpu-sample-seconds", type=float, default=12.0)
+                    help="skip the explicit Cahn-Hilliard variant of the 2D workload")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D workloads")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="busy GPU time before the timed region so clocks settle")
     return ap.parse_args()
@@ -144,66 +174,73 @@ def aggregate_rate(world: int, cells_per_rank: int, steps: int, max_seconds: flo
 
 
 # ----------------------------------------------------------------- CPU oracle timings
-def oracle_rate(case_list, seconds: float, full_steps: int | None = None):
-    """Mcell-steps/s of the FP64 CPU oracle: either `full_steps` steps of every case, or as
-    many steps of the first case as fit in about `seconds`.  Returns (rate, steps, secs)."""
-    from oracle import ib_pf2d as O
+ORACLE_SAMPLE_N = 32      # grid of the oracle's sample of the headline workload
+
+
+def _oracle3d_worker(job):
+    """One host core: advance a copy of the sample with the FP64 3D oracle; `warmup` steps,
+    then wait for every worker, then time `steps` steps.  Returns (cell-steps, t0, t1)."""
+    case, geo, st, warmup, steps, barrier = job
+    from oracle import ib_pf3d as O3
+    for _ in range(warmup):
+        st, _ = O3.step3(case, geo, st)
+    barrier.wait()
+    t0 = time.time()
+    for _ in range(steps):
+        st, _ = O3.step3(case, geo, st)
+    return case.cells * steps, t0, time.time()
+
+
+def oracle_parallel(steps: int | None, warmup: int, seconds: float | None = None):
+    """Mcell-steps/s of the FP64 CPU oracle on the sample of the headline workload (the
+    packing and parameters of the 512^3 case on a 32^3 grid, Cn scaled with h), one spawned
+    process per host core, all started together after their warm-up steps: total cell-steps
+    over the span from the first start to the last finish.  With `seconds`, the step count is
+    chosen so that each process works about that long.  Returns (rate, steps, cores, secs,
+    sample description)."""
+    import multiprocessing as mp
+    from oracle import ib_pf3d as O3
     from workloads import cases as W
-    if full_steps is not None:
-        geos = [O.build_geometry(c) for c in case_list]
-        states = [W.initial_state(c) for c in case_list]
+    case = W.porous_case(ORACLE_SAMPLE_N)
+    geo = O3.build_geometry3(case)
+    st = W.initial_state3d(case)
+    if steps is None:
         t0 = time.perf_counter()
-        for _ in range(full_steps):
-            for k, c in enumerate(case_list):
-                states[k], _ = O.step(c, geos[k], states[k])
-        dt = time.perf_counter() - t0
-        cells = sum(c.cells for c in case_list) * full_steps
-        return cells / dt / 1e6, full_steps, dt
-    c = case_list[0]
-    geo = O.build_geometry(c)
-    st = W.initial_state(c)
-    st, _ = O.step(c, geo, st)                 # first step outside the sample
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        st, _ = O.step(c, geo, st)
-        n += 1
-    dt = time.perf_counter() - t0
-    return c.cells * n / dt / 1e6, n, dt
+        O3.step3(case, geo, st)
+        one = time.perf_counter() - t0
+        steps = max(2, int(seconds / max(one, 1e-3)))
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle3d_worker, [(case, geo, st, warmup, steps, barrier)] * cores,
+                           chunksize=1)
+    cells = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    desc = (f"{cores} processes (one per host core), each {steps} FP64 oracle steps of the "
+            f"packing workload on a {ORACLE_SAMPLE_N}^3 grid ({case.cells} cells, same spheres "
+            f"and parameters, Cn scaled with h) after {warmup} warm-up steps")
+    return cells / span / 1e6, steps, cores, span, desc
 
 
 def run_reference(args):
-    """The FP64 CPU oracle on the same workload and metric.  One reference step is one
-    oracle time step of one of the six instances, cycling through them (a bounded sample of
-    the bench step, so that the run stays within minutes)."""
+    """The FP64 CPU oracle on the headline workload's metric: one reference step is one
+    oracle step of every host core's copy of the 32^3 sample of the 512^3 packing workload (a
+    bounded sample, so that the run stays within minutes)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cl = workload_cases()
-    from oracle import ib_pf2d as O
-    from workloads import cases as W
-    geos = [O.build_geometry(c) for c in cl]
-    states = [W.initial_state(c) for c in cl]
-    for i in range(args.warmup):
-        k = i % len(cl)
-        states[k], _ = O.step(cl[k], geos[k], states[k])
-    cells = 0
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        k = i % len(cl)
-        states[k], _ = O.step(cl[k], geos[k], states[k])
-        cells += cl[k].cells
-    dt = time.perf_counter() - t0
-    value = cells / dt / 1e6
+    value, steps, cores, span, desc = oracle_parallel(args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "sinusoid_wall_512x256_x6", "grid": "512x256", "instances": 6,
-                   "precision": "fp64", "engine": "FP64 CPU oracle (numpy/scipy)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle steps, one 512x256 instance each, "
-                                   "cycling through the six"},
+        "config": {"workload": HEADLINE, "grid": "512x512x512 (sampled on 32^3)",
+                   "precision": "fp64", "engine": "FP64 CPU oracle (numpy/scipy), one process per core"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -302,12 +339,15 @@ def kernel_flops64(name: str, nx: int, ny: int) -> float:
 
 
 def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, words=None,
-             workload="sinusoid_512x256x6"):
+             workload="sinusoid_512x256x6", units=None, dim=2):
     """Roofline of the dominant kernel and per-kernel table from an event-timed pass:
-    ktot[name] = total ms over `steps` steps, kcount[name] = launches.  FP64 2D lines are
-    reported against the FP64 pipe, every other line against HBM bandwidth."""
+    ktot[name] = total ms over `steps` steps, kcount[name] = launches.  Stencil kernels are
+    rated by algorithmic bytes per cell, the ghost and face kernels by algorithmic bytes per
+    ghost / face (units = {"ghost": n, "face": n}).  FP64 2D lines are reported against the
+    FP64 pipe, every other line against HBM bandwidth."""
     alu = esz == 8 and (words is None or words.get("cols_solve") is not None)
     words = KERNEL_STEP_WORDS if words is None else words
+    units = units or {}
     dom = max(ktot, key=ktot.get)
     per_launch_ms = ktot[dom] / kcount[dom]
     tot = sum(ktot.values())
@@ -317,6 +357,12 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
         if not alu and k in words:
             gbs = kernel_step_bytes(k, esz, cells, words) * steps / (v * 1e-3) / 1e9
             ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
+        elif not alu:
+            ub, unit = sparse_unit_bytes(k, esz, dim)
+            if ub is not None and units.get(unit):
+                gbs = ub * units[unit] * kcount[k] / (v * 1e-3) / 1e9
+                ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+                            f"bytes_per_{unit}": ub, f"{unit}s": units[unit]})
         table[k] = ent
     if not alu:
         alg = kernel_step_bytes(dom, esz, cells, words) * steps / kcount[dom]
@@ -335,70 +381,286 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
     return roof
 
 
-def run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps):
-    """The 3D workloads: droplet on a sphere, 256^3 (FP32 and FP64 forms; also with the
-    explicit Cahn-Hilliard variant, FP32), and droplet over a random sphere packing, 512^3
-    (FP32 form); all larger than L2, so no flush is needed.  Each line: throughput over
-    `steps` steps (at most 20) and the per-kernel roofline of a second, event-instrumented
-    pass."""
+def sparse_units(s, ibpf, instances=1):
+    """Ghosts and re-interpolated faces of a context (summed over its instances)."""
+    ng = nf = 0
+    for k in range(instances):
+        ng += int(s.query(ibpf.Q_N_GHOST, k))
+        nf += int(s.query(ibpf.Q_N_FACE_U, k)) + int(s.query(ibpf.Q_N_FACE_V, k))
+        if s.dim == 3:
+            nf += int(s.query(ibpf.Q_N_FACE_W, k))
+    return {"ghost": ng, "face": nf}
+
+
+class Timer:
+    """Device time of solver steps with CUDA events on the work stream (optionally with an
+    L2 flush before each step), and per-kernel times from the event-instrumented graphs."""
+
+    def __init__(self, torch, ibpf, stream, flush=None):
+        self.torch, self.ibpf, self.stream, self.flush = torch, ibpf, stream, flush
+
+    def steps(self, solver, n, collect_kernels=False, flush=False):
+        torch = self.torch
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n)]
+        ktot, kcount = {}, {}
+        for i in range(n):
+            if flush:
+                self.flush.zero_()
+            evs[i][0].record(self.stream)
+            solver.step(1)
+            evs[i][1].record(self.stream)
+            if collect_kernels:
+                names, ms = self.ibpf.ib_pf_kernel_times(solver.ctx)
+                for nm, t in zip(names, ms):
+                    ktot[nm] = ktot.get(nm, 0.0) + t
+                    kcount[nm] = kcount.get(nm, 0) + 1
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), ktot, kcount
+
+    def kernels(self, solver, n, flush=False, before=None):
+        """(ktot, kcount) of n event-instrumented steps."""
+        if before:
+            before()
+        self.ibpf.ib_pf_set_kernel_timing(solver.ctx, True)
+        solver.step(1)
+        self.torch.cuda.synchronize()
+        _, ktot, kcount = self.steps(solver, n, collect_kernels=True, flush=flush)
+        self.ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
+        return ktot, kcount
+
+
+def words_for(case):
+    w = KERNEL_STEP_WORDS_3D
+    if getattr(case.params, "ch_scheme", 0) == 1:
+        w = explicit_words(w, ("rows_fwd", "y_fft", "z_solve", "y_ifft"))
+    return w
+
+
+def run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world, name, case, form,
+                e2e=False):
+    """One 3D workload in one form: throughput over `steps` steps (at most 20), the
+    per-kernel roofline of a second, event-instrumented pass, and (e2e) the same metric
+    through the C ABI with the whole state written from pinned host memory and C read back
+    every step."""
+    import numpy as np
+    prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+    esz = 8 if form == "fp64" else 4
+    t0 = time.time()
+    s = ibpf.solver_from_cases([case], prec, stream=stream.cuda_stream)
+    s.precompute_weights()
+    setup_s = time.time() - t0
+    dt_np = np.float64 if esz == 8 else np.float32
+    C0 = W.droplet_C3d(case, dt_np)
+
+    def restart():
+        s.write("C", C0)
+        s.write("C_old", C0)
+        torch.cuda.synchronize()
+
+    # every other state field starts at zero (fresh context)
+    restart()
+    for _ in range(max(3, args.warmup)):
+        s.step(1)
+    torch.cuda.synchronize()
+    n = max(1, min(args.steps, 20))
+    if dist:
+        dist.barrier()
+    ms, _, _ = tm.steps(s, n)
+    ms = max_over_ranks([ms], dist, "cuda")[0]
+    line = {"value": aggregate_rate(world, case.cells, n, ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / n, "steps": n, "cells": case.cells, "dtype": "f%d" % (8 * esz),
+            "grid": f"{case.nx}x{case.ny}x{case.nz}",
+            "ghosts": int(s.query(ibpf.Q_N_GHOST)),
+            "gpu_launches": int(s.query(ibpf.Q_LAUNCHES)) * n,
+            "setup_s": round(setup_s, 2), "l2": "inputs larger than L2"}
+    if case.geom_kind == W.GEOM_SPHERES:
+        line["spheres"] = len(case.spheres)
+    try:
+        ktot, kcount = tm.kernels(s, n)
+        line["roofline"] = roofline(ktot, kcount, n, case.cells, esz, case, peak, peak_kind,
+                                    form, words_for(case), workload=name,
+                                    units=sparse_units(s, ibpf), dim=3)
+    except Exception as exc:
+        line["roofline"] = {"error": str(exc)[:200]}
+    if e2e:
+        restart()
+        shape_c = (case.nz, case.ny, case.nx)
+        shape_w = (case.nz + 1, case.ny, case.nx)
+        dt_t = torch.float64 if esz == 8 else torch.float32
+        pinned, h2d = {}, 0
+        for fname in ibpf.STATE_FIELDS_3D:
+            shp = shape_w if fname in ("w", "w_old", "Hw") else shape_c
+            if fname in ("C", "C_old"):
+                t = torch.from_numpy(C0).pin_memory()
+            else:
+                t = torch.zeros(shp, dtype=dt_t, pin_memory=True)
+            pinned[fname] = t
+            h2d += t.numel() * esz
+        outC = torch.empty(shape_c, dtype=dt_t, pin_memory=True)
+        d2h = outC.numel() * esz
+        writes = s.prepare_writes([(fname, pinned[fname], 0) for fname in ibpf.STATE_FIELDS_3D])
+        reads = s.prepare_reads([("C", outC, 0)])
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            writes.run()     # one call, one synchronisation
+            s.step(1)
+            reads.run()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": aggregate_rate(world, case.cells, e2e_steps,
+                                               max_over_ranks([e2e_s], dist, "cuda")[0]),
+                       "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "steps": e2e_steps}
+        del pinned, outC, writes, reads
+    line["status"] = s.query(ibpf.Q_STATUS)
+    s.close()
+    del C0
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_2d(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world):
+    """The 2D workloads: the six 512 x 256 sinusoidal-wall runs in one context (both forms,
+    L2 flushed before every timed step; e2e with the whole state written from pinned host
+    memory), the same with the explicit Cahn-Hilliard variant, and the 64-instance FP32
+    ensemble."""
     import dataclasses
     import numpy as np
+    cl = workload_cases()
+    init = [W.initial_state(c) for c in cl]
+    cells = sum(c.cells for c in cl)
+    forms = ("fp32", "fp64") if args.precision == "both" else (args.precision,)
+    units = None
+
+    def restart(solver):
+        # every timed pass starts from t = 0
+        for k in range(len(cl)):
+            solver.write_state(init[k], k)
+        torch.cuda.synchronize()
+
     out = {}
-    sph = W.sphere_case(256)
-    sph_x = dataclasses.replace(sph, params=dataclasses.replace(sph.params, ch_scheme=1))
-    jobs = [("sphere_256", sph, ("fp32", "fp64")),
-            ("sphere_256_explicit", sph_x, ("fp32",)),
-            ("porous_512", W.porous_case(512), ("fp32",))]
-    for name, case, forms in jobs:
+    for form in forms:
+        prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+        esz = 8 if prec == ibpf.FP64 else 4
+        solver = ibpf.solver_from_cases(cl, prec, stream=stream.cuda_stream)
+        solver.precompute_weights()
+        units = sparse_units(solver, ibpf, len(cl))
+        restart(solver)
+        for _ in range(args.warmup):
+            tm.flush.zero_()
+            solver.step(1)
+        torch.cuda.synchronize()
+        n = max(1, min(args.steps, 100))
+        total_ms, _, _ = tm.steps(solver, n, flush=True)
+        total_ms = max_over_ranks([total_ms], dist, "cuda")[0]
+        try:
+            ktot, kcount = tm.kernels(solver, n, flush=True, before=lambda: restart(solver))
+            roof = roofline(ktot, kcount, n, cells, esz, cl[0], peak, peak_kind, form,
+                            units=units, dim=2)
+        except Exception as exc:
+            roof = {"error": str(exc)[:200]}
+        ent = {"value": aggregate_rate(world, cells, n, total_ms * 1e-3), "unit": UNIT,
+               "ms_per_step": total_ms / n, "steps": n, "dtype": "f64" if esz == 8 else "f32",
+               "gpu_launches": int(solver.query(ibpf.Q_LAUNCHES)) * n,
+               "l2": "flushed before every timed step (256 MiB write)", "roofline": roof}
+        if form == forms[0]:
+            restart(solver)
+            dt_np = np.float64 if esz == 8 else np.float32
+            dt_t = torch.float64 if esz == 8 else torch.float32
+            pinned, h2d = [], 0
+            for k in range(len(cl)):
+                d = {}
+                for name in ibpf.STATE_FIELDS:
+                    d[name] = torch.from_numpy(np.ascontiguousarray(init[k][name], dtype=dt_np)).pin_memory()
+                    h2d += d[name].numel() * esz
+                pinned.append(d)
+            outC = [torch.empty(c.ny, c.nx, dtype=dt_t).pin_memory() for c in cl]
+            d2h = sum(o.numel() * esz for o in outC)
+            e2e_steps = max(1, min(args.steps, 50))
+            writes = solver.prepare_writes([(name, pinned[k][name], k) for k in range(len(cl))
+                                            for name in ibpf.STATE_FIELDS])
+            reads = solver.prepare_reads([("C", outC[k], k) for k in range(len(cl))])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                writes.run()
+                solver.step(1)
+                reads.run()
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            ent["e2e"] = {"value": aggregate_rate(world, cells, e2e_steps,
+                                                  max_over_ranks([e2e_s], dist, "cuda")[0]),
+                          "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                          "steps": e2e_steps}
+        out[f"sinusoid_512x256x6_{form}"] = ent
+        solver.close()
+    if not args.no_explicit:
+        xcl = [dataclasses.replace(c, params=dataclasses.replace(c.params, ch_scheme=1)) for c in cl]
         for form in forms:
             prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
-            esz = 8 if form == "fp64" else 4
-            t0 = time.time()
-            s = ibpf.solver_from_cases([case], prec, stream=stream.cuda_stream)
-            s.precompute_weights()
-            setup_s = time.time() - t0
-            C0 = W.droplet_C3d(case, np.float64 if esz == 8 else np.float32)
-            s.write("C", C0)
-            s.write("C_old", C0)
-            del C0
-            for _ in range(max(3, args.warmup)):
-                s.step(1)
+            esz = 8 if prec == ibpf.FP64 else 4
+            xs = ibpf.solver_from_cases(xcl, prec, stream=stream.cuda_stream)
+            xs.precompute_weights()
+            restart(xs)
+            for _ in range(max(3, args.warmup // 4)):
+                tm.flush.zero_()
+                xs.step(1)
             torch.cuda.synchronize()
-            n = max(1, min(args.steps, 20))
-            if dist:
-                dist.barrier()
-            ms, _, _ = timed_steps(s, n)
-            ms = max_over_ranks([ms], dist, "cuda")[0]
-            line = {"value": aggregate_rate(world, case.cells, n, ms * 1e-3), "unit": UNIT,
-                    "ms_per_step": ms / n, "steps": n, "cells": case.cells, "dtype": "f%d" % (8 * esz),
-                    "grid": f"{case.nx}x{case.ny}x{case.nz}",
-                    "ghosts": int(s.query(ibpf.Q_N_GHOST)),
-                    "gpu_launches": int(s.query(ibpf.Q_LAUNCHES)) * n,
-                    "setup_s": round(setup_s, 2), "l2": "inputs larger than L2"}
-            if case.geom_kind == W.GEOM_SPHERES:
-                line["spheres"] = len(case.spheres)
+            xsteps = max(1, min(args.steps, 100))
+            xms, _, _ = tm.steps(xs, xsteps, flush=True)
+            xms = max_over_ranks([xms], dist, "cuda")[0]
             try:
-                ibpf.ib_pf_set_kernel_timing(s.ctx, True)
-                s.step(1)
-                torch.cuda.synchronize()
-                _, ktot, kcount = timed_steps(s, n, collect_kernels=True)
-                ibpf.ib_pf_set_kernel_timing(s.ctx, False)
-                words = KERNEL_STEP_WORDS_3D
-                if getattr(case.params, "ch_scheme", 0) == 1:
-                    words = explicit_words(words, ("rows_fwd", "y_fft", "z_solve", "y_ifft"))
-                line["roofline"] = roofline(ktot, kcount, n, case.cells, esz, case, peak, peak_kind,
-                                            form, words, workload=name)
+                ktot, kcount = tm.kernels(xs, xsteps, flush=True, before=lambda: restart(xs))
+                xroof = roofline(ktot, kcount, xsteps, cells, esz, xcl[0], peak, peak_kind, form,
+                                 explicit_words(KERNEL_STEP_WORDS, ("rows_fwd", "cols_solve")),
+                                 workload="sinusoid_512x256x6_explicit", units=units, dim=2)
             except Exception as exc:
-                line["roofline"] = {"error": str(exc)[:200]}
-            line["status"] = s.query(ibpf.Q_STATUS)
-            s.close()
-            out[f"{name}_{form}"] = line
-            torch.cuda.empty_cache()
+                xroof = {"error": str(exc)[:200]}
+            out[f"sinusoid_512x256x6_explicit_{form}"] = {
+                "value": aggregate_rate(world, cells, xsteps, xms * 1e-3), "unit": UNIT,
+                "ms_per_step": xms / xsteps, "steps": xsteps,
+                "dtype": "f64" if esz == 8 else "f32",
+                "gpu_launches": int(xs.query(ibpf.Q_LAUNCHES)) * xsteps,
+                "l2": "flushed before every timed step", "roofline": xroof}
+            xs.close()
+    if not args.no_ensemble:
+        # batched form at scale: the 64-instance uneven ensemble (grids 256x128 .. 1024x512,
+        # ~14.5M cells, larger than L2) in one context, one launch per sub-step
+        ecl = W.ensemble_2d(64)
+        ecells = sum(c.cells for c in ecl)
+        es = ibpf.solver_from_cases(ecl, ibpf.FP32, stream=stream.cuda_stream)
+        es.precompute_weights()
+        for k, c in enumerate(ecl):
+            es.write_state(W.initial_state(c), k)
+        for _ in range(max(1, args.warmup // 4)):
+            es.step(1)
+        torch.cuda.synchronize()
+        esteps = max(1, min(args.steps, 50))
+        ems, _, _ = tm.steps(es, esteps)
+        ems = max_over_ranks([ems], dist, "cuda")[0]
+        try:
+            ktot, kcount = tm.kernels(es, esteps)
+            eroof = roofline(ktot, kcount, esteps, ecells, 4, ecl[0], peak, peak_kind, "fp32",
+                             workload="ensemble64", units=sparse_units(es, ibpf, len(ecl)), dim=2)
+        except Exception as exc:
+            eroof = {"error": str(exc)[:200]}
+        out["ensemble64_fp32"] = {
+            "value": aggregate_rate(world, ecells, esteps, ems * 1e-3), "unit": UNIT,
+            "ms_per_step": ems / esteps, "steps": esteps, "instances": len(ecl),
+            "cells": ecells, "dtype": "f32",
+            "gpu_launches": int(es.query(ibpf.Q_LAUNCHES)) * esteps,
+            "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls", "roofline": eroof}
+        es.close()
     return out
 
 
 def run_ours(args):
-    import numpy as np
+    import dataclasses
     import torch
 
     rank, world, local = dist_env()
@@ -415,224 +677,63 @@ def run_ours(args):
     from paper_2104_00350_gb300 import ibpf
     from workloads import cases as W
 
-    cl = workload_cases()
-    init = [W.initial_state(c) for c in cl]
-    cells = sum(c.cells for c in cl)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    tm = Timer(torch, ibpf, stream, flush)
     peak, peak_kind = measured_peak()
-    forms = ("fp32", "fp64") if args.precision == "both" else (args.precision,)
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     gpu_idx = int(vis.split(",")[local]) if vis and vis.split(",")[local].isdigit() else local
     sampler = ClockSampler(gpu_idx)
     sampler.start()
-
-    def restart(solver):
-        # every timed pass starts from t = 0 (one of the six runs becomes non-finite near
-        # step 4600)
-        for k in range(len(cl)):
-            solver.write_state(init[k], k)
-        torch.cuda.synchronize()
-
-    def timed_steps(solver, n, collect_kernels=False):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n)]
-        ktot, kcount = {}, {}
-        for i in range(n):
+    # keep the GPU busy for a moment so that clocks settle before the timed regions
+    t_soak = time.time()
+    while time.time() - t_soak < args.soak_seconds:
+        for _ in range(50):
             flush.zero_()
-            evs[i][0].record(stream)
-            solver.step(1)
-            evs[i][1].record(stream)
-            if collect_kernels:
-                names, ms = ibpf.ib_pf_kernel_times(solver.ctx)
-                for nm, t in zip(names, ms):
-                    ktot[nm] = ktot.get(nm, 0.0) + t
-                    kcount[nm] = kcount.get(nm, 0) + 1
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs), ktot, kcount
 
-    results = {}
-    for form in forms:
-        prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
-        esz = 8 if prec == ibpf.FP64 else 4
-        solver = ibpf.solver_from_cases(cl, prec, stream=stream.cuda_stream)
-        solver.precompute_weights()
-        restart(solver)
-        for _ in range(args.warmup):
-            flush.zero_()
-            solver.step(1)
-        # keep the GPU busy so that clocks settle, in chunks that stay far from step 4600
-        t_soak = time.time()
-        while time.time() - t_soak < args.soak_seconds:
-            restart(solver)
-            for _ in range(10):
-                solver.step(100)
-            torch.cuda.synchronize()
-        restart(solver)
-        for _ in range(args.warmup):
-            flush.zero_()
-            solver.step(1)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        total_ms, _, _ = timed_steps(solver, args.steps)
-        if dist:
-            dist.barrier()
-        launches = int(solver.query(ibpf.Q_LAUNCHES))
-        max_ms = max_over_ranks([total_ms], dist, "cuda")[0]
-        value = aggregate_rate(world, cells, args.steps, max_ms * 1e-3)
-
-        # kernel-timing pass over the same number of steps (event-instrumented graphs)
-        try:
-            restart(solver)
-            ibpf.ib_pf_set_kernel_timing(solver.ctx, True)
-            solver.step(1)
-            torch.cuda.synchronize()
-            _, ktot, kcount = timed_steps(solver, args.steps, collect_kernels=True)
-            ibpf.ib_pf_set_kernel_timing(solver.ctx, False)
-            roof = roofline(ktot, kcount, args.steps, cells, esz, cl[0], peak, peak_kind, form)
-        except Exception as exc:   # keep the headline line even if the timing pass fails
-            roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
-                    "frac": None, "traffic": None, "error": str(exc)[:200]}
-
-        e2e = None
-        if form == forms[0]:
-            # end to end through the C ABI with host buffers: whole state in, C out
-            restart(solver)
-            dt_np = np.float64 if esz == 8 else np.float32
-            dt_t = torch.float64 if esz == 8 else torch.float32
-            pinned, h2d = [], 0
-            for k in range(len(cl)):
-                d = {}
-                for name in ibpf.STATE_FIELDS:
-                    d[name] = torch.from_numpy(np.ascontiguousarray(init[k][name], dtype=dt_np)).pin_memory()
-                    h2d += d[name].numel() * esz
-                pinned.append(d)
-            outC = [torch.empty(c.ny, c.nx, dtype=dt_t).pin_memory() for c in cl]
-            d2h = sum(o.numel() * esz for o in outC)
-            e2e_steps = max(1, min(args.steps, 50))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            writes = solver.prepare_writes([(name, pinned[k][name], k) for k in range(len(cl))
-                                            for name in ibpf.STATE_FIELDS])
-            reads = solver.prepare_reads([("C", outC[k], k) for k in range(len(cl))])
-            for _ in range(e2e_steps):
-                writes.run()     # one call, one synchronisation
-                solver.step(1)
-                reads.run()
-            torch.cuda.synchronize()
-            e2e_s = time.perf_counter() - t0
-            e2e = {"value": aggregate_rate(world, cells, e2e_steps,
-                                           max_over_ranks([e2e_s], dist, "cuda")[0]),
-                   "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "steps": e2e_steps}
-        results[form] = {"value": value, "ms_per_step": max_ms / args.steps,
-                         "gpu_launches": launches * args.steps, "roofline": roof, "e2e": e2e,
-                         "dtype": "f64" if esz == 8 else "f32"}
-        solver.close()
-    # batched form at scale: the 64-instance uneven ensemble (grids 256x128 .. 1024x512,
-    # ~14.5M cells, larger than L2) in one context, one launch per sub-step
-    ens = None
-    if not args.no_ensemble:
-        ecl = W.ensemble_2d(64)
-        ecells = sum(c.cells for c in ecl)
-        esolver = ibpf.solver_from_cases(ecl, ibpf.FP32, stream=stream.cuda_stream)
-        esolver.precompute_weights()
-        for k, c in enumerate(ecl):
-            esolver.write_state(W.initial_state(c), k)
-        for _ in range(max(1, args.warmup // 4)):
-            esolver.step(1)
-        torch.cuda.synchronize()
-        esteps = max(1, min(args.steps, 50))
-        ems, _, _ = timed_steps(esolver, esteps)
-        ems = max_over_ranks([ems], dist, "cuda")[0]
-        try:
-            ibpf.ib_pf_set_kernel_timing(esolver.ctx, True)
-            esolver.step(1)
-            torch.cuda.synchronize()
-            _, ktot, kcount = timed_steps(esolver, esteps, collect_kernels=True)
-            ibpf.ib_pf_set_kernel_timing(esolver.ctx, False)
-            eroof = roofline(ktot, kcount, esteps, ecells, 4, ecl[0], peak, peak_kind, "fp32",
-                             workload="ensemble64")
-        except Exception as exc:
-            eroof = {"error": str(exc)[:200]}
-        ens = {"value": aggregate_rate(world, ecells, esteps, ems * 1e-3), "unit": UNIT,
-               "ms_per_step": ems / esteps, "steps": esteps, "instances": len(ecl),
-               "cells": ecells, "dtype": "f32",
-               "gpu_launches": int(esolver.query(ibpf.Q_LAUNCHES)) * esteps,
-               "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls",
-               "roofline": eroof}
-        esolver.close()
-    # explicit Cahn-Hilliard variant (Eq. ExpCH) of the headline workload, both forms
-    expl = None
-    if not args.no_explicit:
-        import dataclasses
-        expl = {}
-        xcl = [dataclasses.replace(c, params=dataclasses.replace(c.params, ch_scheme=1)) for c in cl]
-        for form in forms:
-            prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
-            esz = 8 if prec == ibpf.FP64 else 4
-            xs = ibpf.solver_from_cases(xcl, prec, stream=stream.cuda_stream)
-            xs.precompute_weights()
-            restart(xs)
-            for _ in range(max(3, args.warmup // 4)):
-                flush.zero_()
-                xs.step(1)
-            torch.cuda.synchronize()
-            xsteps = max(1, min(args.steps, 100))
-            xms, _, _ = timed_steps(xs, xsteps)
-            xms = max_over_ranks([xms], dist, "cuda")[0]
-            try:
-                restart(xs)
-                ibpf.ib_pf_set_kernel_timing(xs.ctx, True)
-                xs.step(1)
-                torch.cuda.synchronize()
-                _, ktot, kcount = timed_steps(xs, xsteps, collect_kernels=True)
-                ibpf.ib_pf_set_kernel_timing(xs.ctx, False)
-                xroof = roofline(ktot, kcount, xsteps, cells, esz, xcl[0], peak, peak_kind, form,
-                                 explicit_words(KERNEL_STEP_WORDS, ("rows_fwd", "cols_solve")),
-                                 workload="sinusoid_512x256x6_explicit")
-            except Exception as exc:
-                xroof = {"error": str(exc)[:200]}
-            expl[form] = {"value": aggregate_rate(world, cells, xsteps, xms * 1e-3), "unit": UNIT,
-                          "ms_per_step": xms / xsteps, "steps": xsteps,
-                          "dtype": "f64" if esz == 8 else "f32",
-                          "gpu_launches": int(xs.query(ibpf.Q_LAUNCHES)) * xsteps,
-                          "l2": "flushed before every timed step", "roofline": xroof}
-            xs.close()
-    d3 = None
+    # headline: the 512^3 packing workload, FP32 form
+    head = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world,
+                       HEADLINE, W.porous_case(512), "fp32", e2e=True)
+    d3 = {}
     if not args.no_3d:
-        d3 = run_3d(args, ibpf, W, torch, stream, flush, peak, peak_kind, dist, world, timed_steps)
+        sph = W.sphere_case(256)
+        sph_x = dataclasses.replace(sph, params=dataclasses.replace(sph.params, ch_scheme=1))
+        for name, case, form in (("sphere_256", sph, "fp32"), ("sphere_256", sph, "fp64"),
+                                 ("sphere_256_explicit", sph_x, "fp32")):
+            if form == "fp64" and args.precision == "fp32":
+                continue
+            d3[f"{name}_{form}"] = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind,
+                                               dist, world, name, case, form)
+    d2 = None if args.no_2d else run_2d(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist,
+                                        world)
     clocks = sampler.stop()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, secs = oracle_rate(cl, args.cpu_sample_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} steps of one 512x256 instance (theta 45, l_s 0) in {secs:.1f} s"}
+        rate, n, cores, secs, desc = oracle_parallel(None, 1, args.cpu_sample_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
-        head = results[forms[0]]
+        case = W.porous_case(512)
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "steps": head["steps"], "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": head["dtype"], "data": "synthetic",
-            "config": {"workload": "sinusoid_wall_512x256_x6", "grid": "512x256",
-                       "instances": 6, "thetas_deg": list(THETAS), "slip_lengths": list(SLIPS),
-                       "form": {"fp32": "FP32 fields and transforms, compensated C, FP64 "
-                                        "geometry/weights/mass (meets C<=1e-5, u<=1e-4, 0.1 deg)",
-                                "fp64": "plain FP64"}[forms[0]],
-                       "l2": "flushed before every timed step (256 MiB write)",
+            "config": {"workload": HEADLINE, "grid": "512x512x512", "cells": case.cells,
+                       "spheres": len(case.spheres), "ghosts": head["ghosts"],
+                       "theta_deg": case.params.theta_deg, "Cn": case.params.Cn,
+                       "form": "FP32 fields and transforms, compensated C, FP64 geometry/weights/mass",
+                       "l2": "inputs larger than L2 (about 15 GB resident)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clocks,
-            "e2e": head["e2e"],
+            "e2e": head.get("e2e"),
             "gpu_launches": head["gpu_launches"],
             "roofline": head["roofline"],
             "cpu_baseline": cpu,
-            "forms": {f: {k: v for k, v in r.items() if k != "e2e"} for f, r in results.items()},
-            "batched_ensemble": ens,
-            "explicit_ch": expl,
+            "headline_status": head["status"],
             "workloads_3d": d3,
+            "workloads_2d": d2,
         }
         print(json.dumps(line), flush=True)
     if dist:
