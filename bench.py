@@ -150,7 +150,35 @@ def parse_args():
     ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="busy GPU time before the timed region so clocks settle")
+    ap.add_argument("--only", default=None, metavar="WORKLOAD",
+                    help="time one 3D workload alone (porous_N, porous_NXxNYxNZ, sphere_N) in "
+                         "the form --precision names (fp32 for 'both') and print its line; "
+                         "the size for profiling runs")
     return ap.parse_args()
+
+
+def only_case(W, name: str):
+    """The 3D workload `name`: porous_N (the packing workload on N^3 cells), porous_NXxNYxNZ
+    (the packing's spheres that fit a box NY/NX deep and NZ/NX high, cell size h = 1/NX, the
+    droplet moved into it), sphere_N."""
+    import dataclasses
+    kind, _, size = name.partition("_")
+    dims = [int(v) for v in size.split("x")]
+    if kind == "sphere" and len(dims) == 1:
+        return W.sphere_case(dims[0])
+    if kind == "porous" and len(dims) == 1:
+        return W.porous_case(dims[0])
+    if kind == "porous" and len(dims) == 3:
+        nx, ny, nz = dims
+        base = W.porous_case(nx)
+        lz = nz / nx
+        zc = min(base.drop_c[2], lz - base.drop_r - 2.0 / nx)
+        ly = ny / nx
+        # the spheres of the unit-cube packing that lie inside the shorter box
+        sph = tuple(q for q in base.spheres if q[1] - q[3] >= 0.0 and q[1] + q[3] <= ly)
+        return dataclasses.replace(base, name=name, ny=ny, nz=nz, ly=ly, lz=lz,
+                                   drop_c=(base.drop_c[0], base.drop_c[1] * ly, zc), spheres=sph)
+    raise SystemExit(f"--only: unknown workload {name!r}")
 
 
 def dist_env():
@@ -691,6 +719,19 @@ def run_ours(args):
         for _ in range(50):
             flush.zero_()
         torch.cuda.synchronize()
+
+    if args.only:
+        form = "fp64" if args.precision == "fp64" else "fp32"
+        line = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world,
+                           args.only, only_case(W, args.only), form)
+        line["workload"] = args.only
+        line["clocks"] = sampler.stop()
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
 
     # headline: the 512^3 packing workload, FP32 form
     head = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world,

@@ -42,7 +42,9 @@
  * Errors.  Every call returns an ib_pf_status; nothing aborts, traps the device or exits.
  * The last error message of a context is kept (ib_pf_last_error).  Device-detected
  * non-finite values set a status word that the next synchronising call returns as
- * IB_PF_E_NUMERIC.  A context is not thread-safe; separate contexts are independent.
+ * IB_PF_E_NUMERIC; a 3D transform tile whose copies fail their alignment check (an internal
+ * error: no layout of the library produces one) is skipped and sets another bit, returned
+ * as IB_PF_E_CUDA.  A context is not thread-safe; separate contexts are independent.
  * All device work is issued on the stream given at creation (0 = legacy default).
  */
 #ifndef IB_PF_H
@@ -60,7 +62,7 @@ typedef enum {
   IB_PF_E_UNSUPPORTED = -2,  /* valid but not implemented (e.g. dynamic angle) */
   IB_PF_E_CUDA = -3,         /* a CUDA runtime call failed; see ib_pf_last_error */
   IB_PF_E_NUMERIC = -4,      /* NaN/Inf seen in C or the velocity by the device check */
-  IB_PF_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up */
+  IB_PF_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up (no kernel waits) */
   IB_PF_E_STATE = -6,        /* call out of order (e.g. step before precompute) */
   IB_PF_E_GEOMETRY = -7      /* precompute failed (no intersect point within 10 h) */
 } ib_pf_status;
@@ -197,7 +199,8 @@ typedef enum {
   IB_PF_Q_N_GHOST = 1,
   IB_PF_Q_N_FACE_U = 2,
   IB_PF_Q_N_FACE_V = 3,
-  IB_PF_Q_STATUS = 4,      /* device status word: 0 ok, 1 non-finite seen */
+  IB_PF_Q_STATUS = 4,      /* device status word: 0 ok, bit 1 non-finite seen, bit 2 a 3D
+                              transform tile failed its alignment check */
   IB_PF_Q_STEPS = 5,       /* steps taken since creation */
   IB_PF_Q_N_FALLBACK = 6,  /* normals or averaging stencils that used the fallback */
   IB_PF_Q_LAUNCHES_PER_STEP = 7, /* kernels one step launches */

@@ -40,6 +40,8 @@ __host__ __device__ constexpr int fft_threads(int n) {
 __host__ __device__ constexpr int fft_per_block(int n) { return 8 * fft_threads(n) / n; }
 // shared-memory slots of a transform buffer of e points: one pad slot per 16 points
 __host__ __device__ constexpr int fft_buf(int e) { return e + (e >> 4); }
+// row pitch of the 3D half spectrum: nx/2 + 1 rounded up to even (16-byte aligned rows)
+__host__ __device__ constexpr int spec3_pitch(int nx) { return (nx / 2 + 2) & ~1; }
 // dynamic shared memory of a column-transform block of eb points for columns of n points:
 // points, twiddles and cosine weights (complex) and two eigenvalue parts per column.  nmin:
 // the shortest column length the block may get (most columns per block) when one size

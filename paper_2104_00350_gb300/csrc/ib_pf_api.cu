@@ -340,10 +340,14 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
         cudaMemsetAsync(*f, 0, (cells + nxy) * es, ctx->work);
       }
     }
-    if (cudaMalloc(&in.spec, (size_t)in.ny * in.nz * nh1 * 2 * es) != cudaSuccess) {
+    // 3D: rows of spec3_pitch(nx) points, the pad column zero for good
+    const size_t spec_bytes =
+        (size_t)in.ny * in.nz * (in.dim == 3 ? spec3_pitch(in.nx) : nh1) * 2 * es;
+    if (cudaMalloc(&in.spec, spec_bytes) != cudaSuccess) {
       ctx->err = "spectral workspace allocation failed";
       return bail(IB_PF_E_CUDA);
     }
+    cudaMemsetAsync(in.spec, 0, spec_bytes, ctx->work);
     // partial sums: one per cell tile of the step's reduction, or per 256-cell block of
     // the stand-alone reduction, whichever is more
     const int ntile = ((in.nx + kTileX - 1) / kTileX) * ((in.ny + kTileH - 1) / kTileH);
@@ -443,9 +447,13 @@ ib_pf_status ib_pf_step(ib_pf_ctx* ctx, int nsteps) {
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
   if (nsteps < 0) return fail(ctx, IB_PF_E_ARG, "nsteps < 0");
   if (!ctx->weights_ready) return fail(ctx, IB_PF_E_STATE, "ib_pf_precompute_weights has not succeeded");
-  for (size_t k = 0; k < ctx->inst.size(); ++k)
-    if (((volatile int*)ctx->h_status)[k] != 0)
+  for (size_t k = 0; k < ctx->inst.size(); ++k) {
+    const int st = ((volatile int*)ctx->h_status)[k];
+    if (st & 2)
+      return fail(ctx, IB_PF_E_CUDA, "a 3D transform tile failed its alignment check in instance " + std::to_string(k));
+    if (st != 0)
       return fail(ctx, IB_PF_E_NUMERIC, "non-finite value seen in instance " + std::to_string(k));
+  }
   if (nsteps == 0) return IB_PF_OK;
   ib_pf_status st = capture_graphs(ctx);
   if (st != IB_PF_OK) return st;

@@ -158,12 +158,12 @@ __device__ __forceinline__ void stockham(C2* x, const C2* __restrict__ tw, int c
 }
 
 // Forward real FFT of the cnt row pairs (ra + 2f, ra + 2f + 1), f < cnt, of in (ny x nx)
-// into spec (ny x (nx/2+1)).  Per pair z = row_a + i row_b;
+// into spec (ny rows of sp >= nx/2+1 points).  Per pair z = row_a + i row_b;
 // A_k = (Z_k + conj Z_{N-k})/2,  B_k = (Z_k - conj Z_{N-k})/(2i).
 template <typename T, int LOGN, int THREADS>
 __device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* __restrict__ spec,
                               const typename C2T<T>::type* __restrict__ tw, size_t ra, int cnt,
-                              typename C2T<T>::type* x) {
+                              int sp, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
   constexpr int nx = 1 << LOGN, nh = nx >> 1;
   constexpr int EB = 8 * THREADS;
@@ -188,8 +188,8 @@ __device__ void rows_fwd_core(const T* __restrict__ in, typename C2T<T>::type* _
     A.y = T(0.5) * (z.y - zc.y);
     B.x = T(0.5) * (z.y + zc.y);
     B.y = T(-0.5) * (z.x - zc.x);
-    spec[r * (nh + 1) + k] = A;
-    spec[(r + 1) * (nh + 1) + k] = B;
+    spec[r * sp + k] = A;
+    spec[(r + 1) * sp + k] = B;
   }
   __syncthreads();   // the shared buffer may be reused by the caller
 }
@@ -217,7 +217,7 @@ __device__ __forceinline__ void two_sum_into(T hi, T inc, T lo, T& out_hi, T& ou
 template <typename T, int LOGN, int THREADS>
 __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T* out,
                               const typename C2T<T>::type* __restrict__ tw, const EpiArgs& epi,
-                              size_t ra, int cnt, typename C2T<T>::type* x) {
+                              size_t ra, int cnt, int sp, typename C2T<T>::type* x) {
   using C2 = typename C2T<T>::type;
   constexpr int nx = 1 << LOGN, nh = nx >> 1;
   constexpr int EB = 8 * THREADS;
@@ -225,7 +225,7 @@ __device__ void rows_inv_core(const typename C2T<T>::type* __restrict__ spec, T*
     const int f = t >> LOGN, k = t & (nx - 1);
     const size_t r = ra + 2 * f;
     int kk = k <= nh ? k : nx - k;
-    C2 A = spec[r * (nh + 1) + kk], B = spec[(r + 1) * (nh + 1) + kk];
+    C2 A = spec[r * sp + kk], B = spec[(r + 1) * sp + kk];
     if (kk == 0 || kk == nh) {
       A.y = T(0);
       B.y = T(0);
@@ -308,18 +308,19 @@ struct SymbolArgs {
 template <typename T, typename C2>
 __device__ __forceinline__ C2 divide_symbol(C2 X, T L, const SymbolArgs& sym) {
   if constexpr (sizeof(T) == 8) {
-    // one reciprocal per point: the quotient is within 1.5 ulp of X / sigma
+    // one correctly rounded reciprocal per point (__drcp_rn / __frcp_rn, the value of 1/x):
+    // the quotient is within 1.5 ulp of X / sigma
     double r;
-    if (sym.mode == 0) r = 1.0 / (L * L - sym.s_eta2 * L + sym.c0);
-    else if (sym.mode == 2) r = 1.0 / (1.0 - sym.c0 * L);     // (1 - a L), a = c0
-    else r = (L == 0.0) ? 0.0 : 1.0 / L;
+    if (sym.mode == 0) r = __drcp_rn(L * L - sym.s_eta2 * L + sym.c0);
+    else if (sym.mode == 2) r = __drcp_rn(1.0 - sym.c0 * L);     // (1 - a L), a = c0
+    else r = (L == 0.0) ? 0.0 : __drcp_rn(L);
     X.x = X.x * r;
     X.y = X.y * r;
   } else {
     float r;
-    if (sym.mode == 0) r = 1.0f / (L * L - sym.s_eta2_f * L + sym.c0_f);
-    else if (sym.mode == 2) r = 1.0f / (1.0f - sym.c0_f * L);
-    else r = (L == 0.0f) ? 0.0f : 1.0f / L;
+    if (sym.mode == 0) r = __frcp_rn(L * L - sym.s_eta2_f * L + sym.c0_f);
+    else if (sym.mode == 2) r = __frcp_rn(1.0f - sym.c0_f * L);
+    else r = (L == 0.0f) ? 0.0f : __frcp_rn(L);
     X.x = X.x * r;
     X.y = X.y * r;
   }
@@ -546,7 +547,7 @@ __device__ void dst1_core(typename C2T<T>::type* __restrict__ spec, int nh1,
 // columns b * fft_per_block(n) ..
 template <typename T>
 __global__ void __launch_bounds__(kFftSmallThreads) k_rows_fwd(const T* __restrict__ in,
-    typename C2T<T>::type* __restrict__ spec, int nx, int ny,
+    typename C2T<T>::type* __restrict__ spec, int nx, int ny, int sp,
     const typename C2T<T>::type* __restrict__ tw) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -554,14 +555,14 @@ __global__ void __launch_bounds__(kFftSmallThreads) k_rows_fwd(const T* __restri
   const int rp = fft_per_block(nx);
   const int cnt = min(rp, ny / 2 - (int)blockIdx.x * rp);
   const size_t ra = 2 * (size_t)blockIdx.x * rp;
-#define IBPF_CASE(L) case L: rows_fwd_core<T, L, kFftSmallThreads>(in, spec, tw, ra, cnt, x); break;
+#define IBPF_CASE(L) case L: rows_fwd_core<T, L, kFftSmallThreads>(in, spec, tw, ra, cnt, sp, x); break;
   switch (31 - __clz(nx)) { IBPF_CASES_128 default: break; }
 #undef IBPF_CASE
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kFftSmallThreads) k_rows_inv(
-    const typename C2T<T>::type* __restrict__ spec, T* out, int nx, int ny,
+    const typename C2T<T>::type* __restrict__ spec, T* out, int nx, int ny, int sp,
     const typename C2T<T>::type* __restrict__ tw, EpiArgs epi) {
   using C2 = typename C2T<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(kFftSmallThreads) k_rows_inv(
   const int rp = fft_per_block(nx);
   const int cnt = min(rp, ny / 2 - (int)blockIdx.x * rp);
   const size_t ra = 2 * (size_t)blockIdx.x * rp;
-#define IBPF_CASE(L) case L: rows_inv_core<T, L, kFftSmallThreads>(spec, out, tw, epi, ra, cnt, x); break;
+#define IBPF_CASE(L) case L: rows_inv_core<T, L, kFftSmallThreads>(spec, out, tw, epi, ra, cnt, sp, x); break;
   switch (31 - __clz(nx)) { IBPF_CASES_128 default: break; }
 #undef IBPF_CASE
 }
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(THREADS) kb_rows_fwd(const InstDev<T>* __restr
   const T* in = src == 0 ? d.Q : (src == 1 ? d.rhs : (src == 2 ? d.U[1 - cur] : d.V[1 - cur]));
   C2* x = reinterpret_cast<C2*>(smem_raw);
   const size_t ra = 2 * (size_t)w.y * rp;
-#define IBPF_CASE(L) case L: rows_fwd_core<T, L, THREADS>(in, d.spec, d.twx, ra, cnt, x); break;
+#define IBPF_CASE(L) case L: rows_fwd_core<T, L, THREADS>(in, d.spec, d.twx, ra, cnt, d.nx / 2 + 1, x); break;
   IBPF_DISPATCH(THREADS, d.lognx)
 #undef IBPF_CASE
 }
@@ -722,93 +723,384 @@ __global__ void __launch_bounds__(THREADS) kb_rows_inv(const InstDev<T>* __restr
   const int cnt = min(rp, d.ny / 2 - w.y * rp);
   C2* x = reinterpret_cast<C2*>(smem_raw);
   const size_t ra = 2 * (size_t)w.y * rp;
-#define IBPF_CASE(L) case L: rows_inv_core<T, L, THREADS>(d.spec, out, d.twx, epi, ra, cnt, x); break;
+#define IBPF_CASE(L) case L: rows_inv_core<T, L, THREADS>(d.spec, out, d.twx, epi, ra, cnt, d.nx / 2 + 1, x); break;
   IBPF_DISPATCH(THREADS, d.lognx)
 #undef IBPF_CASE
 }
 
-// ------------------------------------------------------------------ 3D: y transforms
-// Complex FFT of length ny = 2^LOGN along y of the KC = 8 THREADS / ny columns
-// kx0 .. kx0 + KC - 1 (columns at or beyond nh1 are skipped) of z-plane `plane` of the
-// spectrum spec[(k ny + j) nh1 + kx].  INV: inverse transform scaled by 1/ny.
-template <typename T, int LOGN, int THREADS, bool INV, int P = 8>
-__device__ void yfft_core(typename C2T<T>::type* __restrict__ spec, int nh1, size_t plane,
-                          const typename C2T<T>::type* __restrict__ tw, int kx0,
-                          typename C2T<T>::type* xs) {
-  using C2 = typename C2T<T>::type;
-  constexpr int N = 1 << LOGN, EB = P * THREADS, KC = EB / N;
-  static_assert(KC >= 1, "a block holds P points per thread");
-  C2* tws = xs + xbuf(EB, N, P);
-  C2* base = spec + plane * (size_t)N * nh1;
-  for (int t = threadIdx.x; t < N / 2; t += THREADS) tws[t] = tw[t];
-  constexpr int LC = P < 16 ? P : 16;   // loads issued together, as in cols_core
+// ------------------------------------------------------------------ 3D: strided axes
+// The transforms along the strided axes of the 3D half spectrum spec[(z ny + y) sp + kx]
+// (row pitch sp = nx/2 + 1 rounded up to even, so that every row starts on a 16-byte
+// boundary; the pad column is zero from allocation on and stays zero) run on tiles of PW
+// consecutive columns (one 128-byte segment per row: 16 FP32 or 8 FP64 complex values;
+// 64 bytes for 1024-point transforms) times the whole transform length N.  One block per
+// tile:
+//   load   16-byte cp.async copies, consecutive threads on consecutive chunks of a row, all
+//          issued before one wait: the whole tile is in flight at once and holds no
+//          registers;
+//   FFT    in place, radix 8 with one radix-2 or radix-4 pass for the rest of the length:
+//          decimation in frequency forward, which leaves mode k at row fft_pos(k), and
+//          decimation in time inverse, which takes that order back to natural order, so no
+//          pass permutes;
+//   store  the last pass writes its outputs from registers straight to global memory.
+// A thread takes CP = 16 / sizeof(complex) adjacent columns of a butterfly (two in FP32,
+// sharing its twiddles) with 16-byte shared-memory accesses; consecutive threads take
+// consecutive column groups of a row, so no phase has bank conflicts.
+// y axis: the forward transform leaves its rows in the order fft_pos (row p holds mode
+// fft_rev(p)); the z solve takes the y eigenvalue of row p from a table in that order and
+// the inverse y transform starts from it.
+
+// mode held by row p after the forward passes of a 2^logn-point transform (radix-8 passes
+// first): p's digits, most significant first, are the radix digits of the mode, least first
+__host__ __device__ constexpr int fft_rev(int p, int logn) {
+  int k = 0, lw = logn, lo = 0;
+  while (lw > 0) {
+    const int lr = lw >= 3 ? 3 : lw;
+    lw -= lr;
+    k |= ((p >> lw) & ((1 << lr) - 1)) << lo;
+    lo += lr;
+  }
+  return k;
+}
+// row of mode k (the inverse of fft_rev)
+__host__ __device__ constexpr int fft_pos(int k, int logn) {
+  int p = 0, lw = logn, lo = 0;
+  while (lw > 0) {
+    const int lr = lw >= 3 ? 3 : lw;
+    lw -= lr;
+    p |= ((k >> lo) & ((1 << lr) - 1)) << lw;
+    lo += lr;
+  }
+  return p;
+}
+
+constexpr int kTileThreads = 256;
+
+// columns per tile for 2^LOGN-point transforms of T
+template <typename T, int LOGN>
+__host__ __device__ constexpr int tile_cols() {
+  return (LOGN >= 10 ? 64 : 128) / (int)sizeof(typename C2T<T>::type);
+}
+
+// shared memory of a tile block: the tile, the twiddles, the cosine weights and the
+// per-column eigenvalue parts (z solve)
+template <typename T>
+__host__ __device__ constexpr size_t tile_smem_bytes(int n, int pw, bool zsolve) {
+  return sizeof(typename C2T<T>::type) * ((size_t)n * pw + n / 2 + (zsolve ? n : 0)) +
+         sizeof(T) * 2 * pw;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+
+// Rows rows(r) of the tile come from src + r * pitch (nc columns), in 16-byte chunks; the
+// caller waits (cp.async.wait_all) and synchronises before reading them.  The copies need
+// 16-byte aligned addresses and sizes: a tile whose source, pitch or width breaks that (no
+// layout of this file does) is not loaded and false is returned to every thread.
+template <typename C2, typename RowMap>
+__device__ __forceinline__ bool tile_load(C2* x, int pw, int n, const C2* src, size_t pitch,
+                                          int nc, RowMap rows) {
+  const size_t bad = (reinterpret_cast<size_t>(src) | (pitch * sizeof(C2)) | (nc * sizeof(C2))) & 15;
+  if (bad != 0 || nc <= 0 || nc > pw) return false;
+  const int cpr = (int)(nc * sizeof(C2) / 16);   // chunks per row
+  const int total = n * cpr;
+  for (int c = threadIdx.x; c < total; c += kTileThreads) {
+    const int r = c / cpr, q = c - r * cpr;
+    cp_async16(reinterpret_cast<char*>(x + (size_t)rows(r) * pw) + 16 * q,
+               reinterpret_cast<const char*>(src + r * pitch) + 16 * q);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return true;
+}
+__device__ __forceinline__ void tile_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+// twiddle exp(-2 pi i t / N), 0 <= t < N, from the half table tw[m] = exp(-2 pi i m / N)
+template <int N, typename C2>
+__device__ __forceinline__ C2 twiddle(const C2* tw, int t) {
+  C2 w = tw[t & (N / 2 - 1)];
+  if (t & (N / 2)) {
+    w.x = -w.x;
+    w.y = -w.y;
+  }
+  return w;
+}
+
+// CP adjacent complex values of a tile row as one 16-byte shared-memory access
+template <typename C2, int CP>
+__device__ __forceinline__ void ld_cols(const C2* p, C2* v) {
+  if constexpr (CP == 2) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0].x = q.x; v[0].y = q.y; v[1].x = q.z; v[1].y = q.w;
+  } else {
+    v[0] = *p;
+  }
+}
+template <typename C2, int CP>
+__device__ __forceinline__ void st_cols(C2* p, const C2* v) {
+  if constexpr (CP == 2) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  } else {
+    *p = v[0];
+  }
+}
+
+// Pass S of the in-place transform of length N = 2^LOGN on the tile x (N rows of PW points):
+// span L = N / 8^S, radix R = min(8, L), stride L/R.  Forward (decimation in frequency):
+// v_r = x[b + j + r L/R], R-point DFT, output q times W_L^{j q}, back at b + j + q L/R.
+// Inverse (decimation in time): the inverse of that step without its 1/R, input q times
+// conj(W_L^{j q}), then the inverse R-point DFT.  A thread takes CP adjacent columns of a
+// butterfly; put(row, column, values) takes every output (CP values from that column on).
+template <int LOGN, int S, bool INV, int PW, typename T, typename C2, typename Put>
+__device__ __forceinline__ void ip_pass(C2* x, const C2* __restrict__ tw, Put put) {
+  constexpr int N = 1 << LOGN, LWB = LOGN - 3 * S;
+  constexpr int LR = LWB >= 3 ? 3 : LWB, R = 1 << LR, L = 1 << LWB, STR = L / R;
+  constexpr int CP = 16 / (int)sizeof(C2), NG = PW / CP;
+  constexpr int NB = (N / R) * NG, TS = N / L;
+#pragma unroll 2
+  for (int u = threadIdx.x; u < NB; u += kTileThreads) {
+    const int f = (u % NG) * CP, bf = u / NG;
+    const int j = bf % STR, row0 = (bf / STR) * L + j;
+    C2 v[CP][R];
 #pragma unroll
-  for (int q0 = 0; q0 < P; q0 += LC) {
-    C2 ld[LC];
+    for (int r = 0; r < R; ++r) {
+      C2 t[CP];
+      ld_cols<C2, CP>(x + (row0 + r * STR) * PW + f, t);
 #pragma unroll
-    for (int q = 0; q < LC; ++q) {
-      const int idx = threadIdx.x + (q0 + q) * THREADS;
-      const int cc = idx % KC, j = idx / KC;
-      const int kx = kx0 + cc;
-      ld[q].x = T(0);
-      ld[q].y = T(0);
-      if (kx < nh1) ld[q] = base[(size_t)j * nh1 + kx];
+      for (int c = 0; c < CP; ++c) v[c][r] = t[c];
+    }
+    if constexpr (INV) {
+      if constexpr (STR > 1) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          const C2 w = cconj(twiddle<N>(tw, j * q * TS));
+#pragma unroll
+          for (int c = 0; c < CP; ++c) v[c][q] = cmul(v[c][q], w);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c) dft_reg<R, true, T>(v[c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CP; ++c) dft_reg<R, false, T>(v[c]);
+      if constexpr (STR > 1) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+          const C2 w = twiddle<N>(tw, j * q * TS);
+#pragma unroll
+          for (int c = 0; c < CP; ++c) v[c][q] = cmul(v[c][q], w);
+        }
+      }
     }
 #pragma unroll
-    for (int q = 0; q < LC; ++q) {
-      const int idx = threadIdx.x + (q0 + q) * THREADS;
-      xs[xslot<N, P>(idx % KC, idx / KC)] = ld[q];
+    for (int r = 0; r < R; ++r) {
+      C2 t[CP];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) t[c] = v[c][r];
+      put(row0 + r * STR, f, t);
     }
   }
-  __syncthreads();
-  stockham<LOGN, 0, INV, THREADS, T, P>(xs, tws, KC);
+}
+
+// The whole in-place transform from pass K on: forward passes S = 0, 1, ..; inverse passes
+// in the reverse order.  The last pass hands its outputs to `last`; the others store them
+// back into the tile, with a barrier between passes.
+template <int LOGN, int K, bool INV, int PW, typename T, typename C2, typename Put>
+__device__ __forceinline__ void ip_fft(C2* x, const C2* __restrict__ tw, Put last) {
+  constexpr int NP = (LOGN + 2) / 3;
+  constexpr int S = INV ? NP - 1 - K : K;
+  constexpr int CP = 16 / (int)sizeof(C2);
+  if constexpr (K == NP - 1) {
+    ip_pass<LOGN, S, INV, PW, T>(x, tw, last);
+  } else {
+    ip_pass<LOGN, S, INV, PW, T>(x, tw, [x](int row, int f, const C2* v) {
+      st_cols<C2, CP>(x + row * PW + f, v);
+    });
+    __syncthreads();
+    ip_fft<LOGN, K + 1, INV, PW, T>(x, tw, last);
+  }
+}
+
+// CP values (columns f.. of a tile row) to global memory at p, scaled by sc, the columns at
+// or beyond nc skipped (nc and f are multiples of CP)
+template <typename C2, int CP, typename T>
+__device__ __forceinline__ void st_global(C2* p, const C2* v, int f, int nc, T sc) {
+  if (f >= nc) return;
+  C2 o[CP];
+#pragma unroll
+  for (int c = 0; c < CP; ++c) {
+    o[c].x = v[c].x * sc;
+    o[c].y = v[c].y * sc;
+  }
+  st_cols<C2, CP>(p, o);
+}
+
+// y transform of one tile: z-plane blockIdx.x / nbt, columns kx0 = (blockIdx.x % nbt) PW ..
+// (nc = min(PW, sp - kx0) of them).  Forward: rows in natural order in, in the order fft_pos
+// out.  Inverse: back, scaled by 1/N.
+template <typename T, int LOGN, bool INV>
+__global__ void __launch_bounds__(kTileThreads) k3_ytile(typename C2T<T>::type* __restrict__ spec,
+    int sp, int nbt, const typename C2T<T>::type* __restrict__ tw, int* status) {
+  using C2 = typename C2T<T>::type;
+  constexpr int N = 1 << LOGN, PW = tile_cols<T, LOGN>(), CP = 16 / (int)sizeof(C2);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  C2* tws = x + N * PW;
+  const int z = blockIdx.x / nbt, kx0 = (int)(blockIdx.x % nbt) * PW;
+  const int nc = min(PW, sp - kx0);
+  C2* g = spec + (size_t)z * N * sp + kx0;
+  if (!tile_load(x, PW, N, g, (size_t)sp, nc, [](int r) { return r; })) {
+    if (threadIdx.x == 0) atomicOr(status, 2);
+    return;
+  }
+  for (int t = threadIdx.x; t < N / 2; t += kTileThreads) tws[t] = tw[t];
+  tile_wait();
   const T sc = INV ? T(1) / T(N) : T(1);
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    const int idx = threadIdx.x + q * THREADS;
-    const int cc = idx % KC, j = idx / KC;
-    const int kx = kx0 + cc;
-    C2 v = xs[xslot<N, P>(cc, j)];
-    v.x *= sc;
-    v.y *= sc;
-    if (kx < nh1) base[(size_t)j * nh1 + kx] = v;
+  ip_fft<LOGN, 0, INV, PW, T>(x, tws, [&](int row, int f, const C2* v) {
+    st_global<C2, CP>(g + (size_t)row * sp + f, v, f, nc, sc);
+  });
+}
+
+// z solve of one tile: columns k0 = blockIdx.x PW .. of the ny sp columns k = p sp + kx (p a y
+// row in the order fft_pos).  Cosine transform along z by Makhoul's reordering (folded into
+// the row copies: row r goes to r/2 if even, N - 1 - (r-1)/2 if odd) and an N-point FFT,
+// division by the symbol at L = (lamz[m] + lamy[fft_rev(p)]) + lamx[kx], inverse transform
+// and the inverse reordering on the way out (the pair formulas of cols_core).
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(kTileThreads) k3_ztile(typename C2T<T>::type* __restrict__ spec,
+    int ncols, int sp, int nh1, const typename C2T<T>::type* __restrict__ tw,
+    const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym, int* status) {
+  using C2 = typename C2T<T>::type;
+  constexpr int N = 1 << LOGN, PW = tile_cols<T, LOGN>(), half = N / 2;
+  constexpr int CP = 16 / (int)sizeof(C2);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C2* x = reinterpret_cast<C2*>(smem_raw);
+  C2* tws = x + N * PW;
+  C2* wds = tws + half;
+  T* lcx = reinterpret_cast<T*>(wds + N);   // lamx[kx] of each column
+  T* lcy = lcx + PW;                        // the y eigenvalue of each column's row
+  const int k0 = blockIdx.x * PW;
+  const int nc = min(PW, ncols - k0);
+  const size_t pitch = (size_t)ncols;
+  C2* g = spec + k0;
+  if (!tile_load(x, PW, N, g, pitch, nc,
+                 [](int r) { return (r & 1) ? N - 1 - (r >> 1) : (r >> 1); })) {
+    if (threadIdx.x == 0) atomicOr(status, 2);
+    return;
+  }
+  const T* lamz = sizeof(T) == 8 ? (const T*)sym.lamy : (const T*)sym.lamy_f;
+  const T* lam_x = sizeof(T) == 8 ? (const T*)sym.lamx : (const T*)sym.lamx_f;
+  const T* lam_y = sizeof(T) == 8 ? (const T*)sym.lamyp : (const T*)sym.lamyp_f;
+  for (int t = threadIdx.x; t < half; t += kTileThreads) tws[t] = tw[t];
+  for (int t = threadIdx.x; t < N; t += kTileThreads) wds[t] = wd[t];
+  for (int c = threadIdx.x; c < PW; c += kTileThreads) {
+    const int k = min(k0 + c, ncols - 1);
+    lcx[c] = lam_x[min(k % sp, nh1 - 1)];   // the pad column (zero) takes the last mode's
+    lcy[c] = lam_y[k / sp];
+  }
+  tile_wait();
+  ip_fft<LOGN, 0, false, PW, T>(x, tws, [x](int row, int f, const C2* v) {
+    st_cols<C2, CP>(x + row * PW + f, v);
+  });
+  __syncthreads();
+  // pair tasks (m, N - m), m = 0..N/2, of every column; mode m sits at row fft_pos(m)
+  for (int t = threadIdx.x; t < PW * (half + 1); t += kTileThreads) {
+    const int c = t % PW, m = t / PW;
+    const int mm = (N - m) & (N - 1);
+    const int im = fft_pos(m, LOGN) * PW + c, imm = fft_pos(mm, LOGN) * PW + c;
+    const C2 Vm = x[im], Vmm = x[imm];
+    C2 Xm, Xmm;
+    {
+      C2 vr, vi, w = wds[m];
+      vr.x = T(0.5) * (Vm.x + Vmm.x);
+      vr.y = T(0.5) * (Vm.y - Vmm.y);
+      vi.x = T(0.5) * (Vm.y + Vmm.y);
+      vi.y = T(-0.5) * (Vm.x - Vmm.x);
+      Xm.x = w.x * vr.x - w.y * vr.y;
+      Xm.y = w.x * vi.x - w.y * vi.y;
+    }
+    {
+      C2 vr, vi, w = wds[mm];
+      vr.x = T(0.5) * (Vmm.x + Vm.x);
+      vr.y = T(0.5) * (Vmm.y - Vm.y);
+      vi.x = T(0.5) * (Vmm.y + Vm.y);
+      vi.y = T(-0.5) * (Vmm.x - Vm.x);
+      Xmm.x = w.x * vr.x - w.y * vr.y;
+      Xmm.y = w.x * vi.x - w.y * vi.y;
+    }
+    Xm = divide_symbol<T>(Xm, (lamz[m] + lcy[c]) + lcx[c], sym);
+    Xmm = divide_symbol<T>(Xmm, (lamz[mm] + lcy[c]) + lcx[c], sym);
+    C2 Zm, Zmm;
+    {
+      C2 y;   // X_m - i X_{N-m}; X_N = 0 for m = 0
+      const C2 xo = (m == 0) ? C2{T(0), T(0)} : Xmm;
+      y.x = Xm.x + xo.y;
+      y.y = Xm.y - xo.x;
+      Zm = cmul(cconj(wds[m]), y);
+    }
+    {
+      C2 y;
+      const C2 xo = (mm == 0) ? C2{T(0), T(0)} : Xm;
+      y.x = Xmm.x + xo.y;
+      y.y = Xmm.y - xo.x;
+      Zmm = cmul(cconj(wds[mm]), y);
+    }
+    x[im] = Zm;
+    if (mm != m) x[imm] = Zmm;
   }
   __syncthreads();
+  const T inv = T(1) / T(N);
+  ip_fft<LOGN, 0, true, PW, T>(x, tws, [&](int n, int f, const C2* v) {
+    const int r = n < half ? 2 * n : 2 * (N - 1 - n) + 1;
+    st_global<C2, CP>(g + (size_t)r * pitch + f, v, f, nc, inv);
+  });
 }
 
-// 3D transforms of the y and z axes run in blocks of kT3Fft threads (8 kT3Fft points per
-// block; 512-thread blocks, with 128-byte column segments, measured slower on GB300)
-constexpr int kT3Fft = 128;
-#define IBPF_CASES_ALL IBPF_CASES_128 IBPF_CASE(11) IBPF_CASE(12)
-
-// block b: z-plane b / nbp, columns (b % nbp) * (8 THREADS / ny) ..
-template <typename T, bool INV, int THREADS>
-__global__ void __launch_bounds__(THREADS) k3_yfft(
-    typename C2T<T>::type* __restrict__ spec, int nh1, int ny, int nbp,
-    const typename C2T<T>::type* __restrict__ tw) {
-  using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  const size_t plane = blockIdx.x / nbp;
-  const int kx0 = (int)(blockIdx.x % nbp) * (8 * THREADS / ny);
-#define IBPF_CASE(L) case L: if constexpr ((8 * THREADS >> L) >= 1) yfft_core<T, L, THREADS, INV>(spec, nh1, plane, tw, kx0, x); break;
-  switch (31 - __clz(ny)) { IBPF_CASES_ALL default: break; }
-#undef IBPF_CASE
+// maximum dynamic shared memory of the tile kernels for lengths 2^L .. 2^10
+template <typename T, int L>
+void tile_attributes() {
+  const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  constexpr int PW = tile_cols<T, L>();
+  cudaFuncSetAttribute(k3_ytile<T, L, false>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
+  cudaFuncSetAttribute(k3_ytile<T, L, true>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
+  cudaFuncSetAttribute(k3_ztile<T, L>, att, (int)tile_smem_bytes<T>(1 << L, PW, true));
+  if constexpr (L < 10) tile_attributes<T, L + 1>();
 }
 
-// z cosine transform + symbol + inverse of the 8 THREADS / nz columns k0 .. of a 3D spectrum
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS) k3_cols(
-    typename C2T<T>::type* __restrict__ spec, int ncols, int nz,
-    const typename C2T<T>::type* __restrict__ tw, const typename C2T<T>::type* __restrict__ wd,
-    SymbolArgs sym) {
-  using C2 = typename C2T<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2* x = reinterpret_cast<C2*>(smem_raw);
-  const int k0 = blockIdx.x * (8 * THREADS / nz);
-#define IBPF_CASE(L) case L: if constexpr ((8 * THREADS >> L) >= 1) cols_core<T, L, THREADS>(spec, ncols, tw, wd, sym, k0, x); break;
-  switch (31 - __clz(nz)) { IBPF_CASES_ALL default: break; }
-#undef IBPF_CASE
+template <typename T>
+int tile_cols_of(int logn) {
+  return (logn >= 10 ? 64 : 128) / (int)sizeof(typename C2T<T>::type);
+}
+
+#define IBPF_TILE_CASES IBPF_T(3) IBPF_T(4) IBPF_T(5) IBPF_T(6) IBPF_T(7) IBPF_T(8) IBPF_T(9) IBPF_T(10)
+
+template <typename T, bool INV>
+void launch_ytile(int logn, int blocks, size_t smem, cudaStream_t s,
+                  typename C2T<T>::type* spec, int sp, int nbt,
+                  const typename C2T<T>::type* tw, int* status) {
+  switch (logn) {
+#define IBPF_T(L) case L: k3_ytile<T, L, INV><<<blocks, kTileThreads, smem, s>>>(spec, sp, nbt, tw, status); break;
+    IBPF_TILE_CASES
+#undef IBPF_T
+    default: break;
+  }
+}
+
+template <typename T>
+void launch_ztile(int logn, int blocks, size_t smem, cudaStream_t s,
+                  typename C2T<T>::type* spec, int ncols, int sp, int nh1,
+                  const typename C2T<T>::type* tw, const typename C2T<T>::type* wd,
+                  const SymbolArgs& sym, int* status) {
+  switch (logn) {
+#define IBPF_T(L) case L: k3_ztile<T, L><<<blocks, kTileThreads, smem, s>>>(spec, ncols, sp, nh1, tw, wd, sym, status); break;
+    IBPF_TILE_CASES
+#undef IBPF_T
+    default: break;
+  }
 }
 
 template <typename T>
@@ -916,9 +1208,13 @@ cudaError_t tables3_t(Instance& in) {
     const double sn = std::sin(M_PI * (double)k / (double)nx);
     lx[k] = -(4.0 / (h * h)) * sn * sn;
   }
-  for (int j = 0; j < ny; ++j) {
-    const double sn = std::sin(M_PI * (double)j / (double)ny);
-    ly[j] = -(4.0 / (h * h)) * sn * sn;
+  // y eigenvalues in the row order of the y-transformed spectrum: row p holds mode
+  // fft_rev(p) (the in-place forward transform leaves its modes in that order)
+  int logny = 0;
+  while ((1 << logny) < ny) ++logny;
+  for (int p = 0; p < ny; ++p) {
+    const double sn = std::sin(M_PI * (double)fft_rev(p, logny) / (double)ny);
+    ly[p] = -(4.0 / (h * h)) * sn * sn;
   }
   for (int m = 0; m < nz; ++m) {
     const double sn = std::sin(M_PI * (double)m / (2.0 * (double)nz));
@@ -957,9 +1253,8 @@ cudaError_t tables3_t(Instance& in) {
       !put(&in.wdct, wd.data(), sizeof(C2) * wd.size()))
     return e;
   const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaFuncSetAttribute(k3_yfft<T, false, kT3Fft>, att, 200 * 1024);
-  cudaFuncSetAttribute(k3_yfft<T, true, kT3Fft>, att, 200 * 1024);
-  cudaFuncSetAttribute(k3_cols<T, kT3Fft>, att, 200 * 1024);
+  (void)att;
+  tile_attributes<T, 3>();
 
   return cudaGetLastError();
 }
@@ -971,25 +1266,23 @@ template <typename T>
 int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Recorder* rec) {
   using C2 = typename C2T<T>::type;
   constexpr int S = kFftSmallThreads;
-  const int nx = in.nx, ny = in.ny, nz = in.nz, nh1 = nx / 2 + 1;
-  constexpr int L = kT3Fft;
+  const int nx = in.nx, ny = in.ny, nz = in.nz, nh1 = nx / 2 + 1, sp = spec3_pitch(nx);
   const int rows = ny * nz;
-  const int rp = fft_per_block(nx), yp = 8 * L / ny, cp = 8 * L / nz;
+  const int rp = fft_per_block(nx);
   C2* spec = (C2*)in.spec;
-  // the row kernels take at most 26 KiB of shared memory; the y and z kernels up to 110 KiB
-  // (FP64, 1024 points), allowed by the attribute set with the tables
+  // the row kernels take at most 26 KiB of shared memory; the tile kernels up to 88 KiB,
+  // allowed by the attributes set with the tables
   const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
-  const size_t ysm = sizeof(C2) * (fft_buf(8 * L) + ny / 2);
-  const size_t csm = cols_smem_bytes<T>(nz, 8 * L);
   const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
-  k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, (const C2*)in.twx);
+  k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, sp, (const C2*)in.twx);
   if (rec) rec->mark("rows_fwd", s);
-  const int nbp = (nh1 + yp - 1) / yp;
-  auto yfft = [&](bool inv) {
-    if (inv) k3_yfft<T, true, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
-    else k3_yfft<T, false, L><<<nz * nbp, L, ysm, s>>>(spec, nh1, ny, nbp, (const C2*)in.twy);
-  };
-  yfft(false);
+  int logny = 0, lognz = 0;
+  while ((1 << logny) < ny) ++logny;
+  while ((1 << lognz) < nz) ++lognz;
+  const int pwy = tile_cols_of<T>(logny), pwz = tile_cols_of<T>(lognz);
+  const int nbt = (sp + pwy - 1) / pwy;
+  const size_t ysm = tile_smem_bytes<T>(ny, pwy, false);
+  launch_ytile<T, false>(logny, nz * nbt, ysm, s, spec, sp, nbt, (const C2*)in.twy, in.status);
   if (rec) rec->mark("y_fft", s);
   SymbolArgs sym;
   sym.mode = mode;
@@ -1004,11 +1297,11 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   sym.ncx = nh1;
   sym.lamyp = in.lamy;
   sym.lamyp_f = in.lamy_f;
-  const int ncols = ny * nh1;
-  k3_cols<T, L><<<(ncols + cp - 1) / cp, L, csm, s>>>(spec, ncols, nz, (const C2*)in.twz,
-                                                        (const C2*)in.wdct, sym);
+  const int ncols = ny * sp;
+  launch_ztile<T>(lognz, (ncols + pwz - 1) / pwz, tile_smem_bytes<T>(nz, pwz, true), s, spec,
+                  ncols, sp, nh1, (const C2*)in.twz, (const C2*)in.wdct, sym, in.status);
   if (rec) rec->mark("z_solve", s);
-  yfft(true);
+  launch_ytile<T, true>(logny, nz * nbt, ysm, s, spec, sp, nbt, (const C2*)in.twy, in.status);
   if (rec) rec->mark("y_ifft", s);
   EpiArgs epi;
   T* out;
@@ -1026,7 +1319,7 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
     epi.delta = in.dp;
     out = (T*)in.P[1 - cur];
   }
-  k_rows_inv<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, rows, (const C2*)in.twx, epi);
+  k_rows_inv<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, rows, sp, (const C2*)in.twx, epi);
   if (rec) rec->mark("rows_inv", s);
   return 5;
 }
@@ -1109,7 +1402,7 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   // of shared memory, below the default limit, so this path sets no function attributes
   const size_t rsm = sizeof(double2) * (fft_buf(8 * S) + nx / 2);
   const size_t csm = cols_smem_bytes<double>(ny, 8 * S);
-  k_rows_fwd<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(rhs, spec, nx, ny, twx);
+  k_rows_fwd<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(rhs, spec, nx, ny, nh1, twx);
   SymbolArgs sym;
   sym.mode = mode;
   sym.s_eta2 = s_eta2;
@@ -1118,7 +1411,7 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
   sym.lamy = lamy;
   k_cols<double><<<(nh1 + cp - 1) / cp, S, csm, s>>>(spec, nh1, ny, twy, wd, sym);
   EpiArgs plain;
-  k_rows_inv<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, ny, twx, plain);
+  k_rows_inv<double><<<(ny / 2 + rp - 1) / rp, S, rsm, s>>>(spec, out, nx, ny, nh1, twx, plain);
   return 3;
 }
 

@@ -929,6 +929,222 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
   asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy outlives the block
 }
 
+// The FP64 form of the predictor, with the edge work shared: planes k-1, k, k+1 of C, u, v,
+// w and phi staged in a four-slot ring (dynamic shared memory, k3_pred_smem bytes) filled by
+// cp.async (plane k+2 in flight while plane k is computed).  Each
+// thread owns the faces of cell (i, j, k) and evaluates every edge stress and product it
+// needs with the same expressions and operation order as the plain form, but shares them:
+// x-neighbour values (txx(i-1), txy(i+1), txz(i+1), uv(i+1), uw(i+1)) come from the adjacent
+// lane by a warp shuffle (a warp is one row of 32 cells; the end lanes evaluate theirs), and
+// the z-edge values of plane k+1 (txz, tyz, uw, vw at k+1 and tzz(k)) are carried in
+// registers to the next plane, where they are the k-level values.  Results are those of
+// the plain evaluation (k3_predict), bit for bit; the FP64 pipe does about half the work.
+// (In the FP32 form, which is bound by its issue rate and memory, this sharing measured
+// 3.5 % slower than k3_predict_a, so that form evaluates every value per face.)
+template <typename T>
+__global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
+  static_assert(kPx == 32, "one warp per tile row");
+  constexpr int kSlots = kPhx * kPhy, kThreads = kPx * kPy;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const sC = reinterpret_cast<T*>(smem_raw);
+  T* const sU = sC + kPr * kSlots;
+  T* const sV = sU + kPr * kSlots;
+  T* const sW = sV + kPr * kSlots;
+  T* const sF = sW + kPr * kSlots;
+  constexpr int NS = (kSlots + kThreads - 1) / kThreads;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
+  const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
+  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int k0 = blockIdx.z * kz;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < a.nx && j < a.ny;
+  const size_t nxy = (size_t)a.nx * a.ny;
+  const unsigned FULL = 0xffffffffu;
+  const bool first_lane = tx == 0, last_lane = tx == kPx - 1;
+  // this thread's staged slots and the in-plane offsets of their columns (periodic wrap)
+  unsigned off[NS];
+  int sidx[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int idx = tid + q * kThreads;
+    sidx[q] = idx < kSlots ? idx : -1;
+    const int r = idx / kPhx, cc = idx % kPhx;
+    const int gi = (i0 - 1 + cc + a.nx) & (a.nx - 1), gj = (j0 - 1 + r + a.ny) & (a.ny - 1);
+    off[q] = (unsigned)gj * (unsigned)a.nx + (unsigned)gi;
+  }
+  auto issue = [&](int kk) {   // plane kk (-1 .. nz+1) into slot kk mod 4
+    const int sl = (kk + kPr) & (kPr - 1);
+    const int km = kk < 0 ? 0 : (kk >= a.nz ? a.nz - 1 : kk);
+    const bool win = kk >= 0 && kk <= a.nz, fin = kk >= 0 && kk < a.nz;
+    const size_t base = (size_t)km * nxy, wbase = (size_t)(win ? kk : 0) * nxy;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      if (sidx[q] < 0) continue;
+      const int e = sl * kSlots + sidx[q];
+      cp_async_el(sC + e, a.C1 + base + off[q], true);
+      cp_async_el(sU + e, a.U + base + off[q], true);
+      cp_async_el(sV + e, a.V + base + off[q], true);
+      cp_async_el(sW + e, a.W + wbase + off[q], win);
+      cp_async_el(sF + e, a.phi + base + off[q], fin);
+    }
+    cp_async_commit();
+  };
+  // planes are addressed by their offset from the current plane: dk = -1, 0, +1
+  int sl3[3] = {0, 0, 0};
+  T sg3[3] = {T(1), T(1), T(1)};   // no-slip sign of the staged u, v (-1 beyond the z walls)
+  auto at = [&](int di, int dj, int dk) { return sl3[dk + 1] * kSlots + (ty + 1 + dj) * kPhx + (tx + 1 + di); };
+  auto Cc = [&](int di, int dj, int dk) { return sC[at(di, dj, dk)]; };
+  auto Fc = [&](int di, int dj, int dk) { return sF[at(di, dj, dk)]; };
+  auto Ug = [&](int di, int dj, int dk) { return sg3[dk + 1] * sU[at(di, dj, dk)]; };
+  auto Vg = [&](int di, int dj, int dk) { return sg3[dk + 1] * sV[at(di, dj, dk)]; };
+  auto Wf = [&](int di, int dj, int dk) { return sW[at(di, dj, dk)]; };
+  const T ih = a.inv_h;
+  auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
+  auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+  // the stresses and products of the plain form, at offsets from cell (i, j, k)
+  auto txx = [&](int di) { return T(2) * mu(Cc(di, 0, 0)) * ((Ug(di + 1, 0, 0) - Ug(di, 0, 0)) * ih); };
+  auto tyy = [&](int dj) { return T(2) * mu(Cc(0, dj, 0)) * ((Vg(0, dj + 1, 0) - Vg(0, dj, 0)) * ih); };
+  auto tzz = [&](int dk) { return T(2) * mu(Cc(0, 0, dk)) * ((Wf(0, 0, dk + 1) - Wf(0, 0, dk)) * ih); };
+  auto txy = [&](int di, int dj, int dk) {
+    const T ce = T(0.25) * (((Cc(di - 1, dj - 1, dk) + Cc(di, dj - 1, dk)) + Cc(di - 1, dj, dk)) + Cc(di, dj, dk));
+    return mu(ce) * ((Ug(di, dj, dk) - Ug(di, dj - 1, dk)) * ih + (Vg(di, dj, dk) - Vg(di - 1, dj, dk)) * ih);
+  };
+  auto txz = [&](int di, int dj, int dk) {
+    const T ce = T(0.25) * (((Cc(di - 1, dj, dk - 1) + Cc(di, dj, dk - 1)) + Cc(di - 1, dj, dk)) + Cc(di, dj, dk));
+    return mu(ce) * ((Ug(di, dj, dk) - Ug(di, dj, dk - 1)) * ih + (Wf(di, dj, dk) - Wf(di - 1, dj, dk)) * ih);
+  };
+  auto tyz = [&](int di, int dj, int dk) {
+    const T ce = T(0.25) * (((Cc(di, dj - 1, dk - 1) + Cc(di, dj, dk - 1)) + Cc(di, dj - 1, dk)) + Cc(di, dj, dk));
+    return mu(ce) * ((Vg(di, dj, dk) - Vg(di, dj, dk - 1)) * ih + (Wf(di, dj, dk) - Wf(di, dj - 1, dk)) * ih);
+  };
+  auto uv = [&](int di, int dj, int dk) {
+    return (T(0.5) * (Ug(di, dj, dk) + Ug(di, dj - 1, dk))) * (T(0.5) * (Vg(di, dj, dk) + Vg(di - 1, dj, dk)));
+  };
+  auto uw = [&](int di, int dj, int dk) {
+    return (T(0.5) * (Ug(di, dj, dk) + Ug(di, dj, dk - 1))) * (T(0.5) * (Wf(di, dj, dk) + Wf(di - 1, dj, dk)));
+  };
+  auto vw = [&](int di, int dj, int dk) {
+    return (T(0.5) * (Vg(di, dj, dk) + Vg(di, dj, dk - 1))) * (T(0.5) * (Wf(di, dj, dk) + Wf(di, dj - 1, dk)));
+  };
+  // z-edge values carried from the previous plane (at offsets (0,0,0) and (0,1,0) of the
+  // current plane), valid after the first iteration
+  T c_txz = T(0), c_tyz = T(0), c_tyzn = T(0), c_uw = T(0), c_vw = T(0), c_vwn = T(0), c_tzz = T(0);
+  issue(k0 - 1);
+  issue(k0);
+  issue(k0 + 1);
+  for (int k = k0; k < k0 + kz; ++k) {
+    issue(k + 2);
+    const size_t c = (size_t)k * nxy + (size_t)j * a.nx + i;
+    // per-face operands of plane k, requested before the wait so their latency overlaps it
+    T hu = T(0), hv = T(0), hw = T(0), fu = T(0), fv = T(0), fw = T(0);
+    if (active) {
+      hu = a.Hu[c];
+      hv = a.Hv[c];
+      fu = a.au[c];
+      fv = a.av[c];
+      if (k >= 1) {
+        hw = a.Hw[c];
+        fw = a.aw[c];
+      }
+    }
+    cp_async_wait1();   // every plane but k+2 has arrived (this thread's copies)
+    __syncthreads();    // ... and every thread's
+    sl3[0] = (k + kPr - 1) & (kPr - 1);
+    sl3[1] = k & (kPr - 1);
+    sl3[2] = (k + 1) & (kPr - 1);
+    sg3[0] = k - 1 < 0 ? T(-1) : T(1);
+    sg3[2] = k + 1 >= a.nz ? T(-1) : T(1);
+    if (k == k0) {   // first plane of the block: the k-level z-edge values directly
+      c_txz = txz(0, 0, 0);
+      c_tyz = tyz(0, 0, 0);
+      c_tyzn = tyz(0, 1, 0);
+      c_uw = uw(0, 0, 0);
+      c_vw = vw(0, 0, 0);
+      c_vwn = vw(0, 1, 0);
+      c_tzz = tzz(-1);
+    }
+    // in-plane values with x-neighbours from the adjacent lane (every lane takes part)
+    const T txx0 = txx(0);
+    T txxm = __shfl_up_sync(FULL, txx0, 1);
+    if (first_lane) txxm = txx(-1);
+    const T txy0 = txy(0, 0, 0);
+    T txyx = __shfl_down_sync(FULL, txy0, 1);
+    if (last_lane) txyx = txy(1, 0, 0);
+    const T uv0 = uv(0, 0, 0);
+    T uvx = __shfl_down_sync(FULL, uv0, 1);
+    if (last_lane) uvx = uv(1, 0, 0);
+    T txzx = __shfl_down_sync(FULL, c_txz, 1);
+    if (last_lane) txzx = txz(1, 0, 0);
+    T uwx = __shfl_down_sync(FULL, c_uw, 1);
+    if (last_lane) uwx = uw(1, 0, 0);
+    // the z-edge values of plane k+1 (carried to the next iteration)
+    const T n_txz = txz(0, 0, 1), n_tyz = tyz(0, 0, 1), n_tyzn = tyz(0, 1, 1);
+    const T n_uw = uw(0, 0, 1), n_vw = vw(0, 0, 1), n_vwn = vw(0, 1, 1);
+    const T n_tzz = tzz(0);
+    if (active) {
+      const T k_st = a.k_st;
+      T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
+      {
+        const T cL = Cc(-1, 0, 0), cR = Cc(0, 0, 0);
+        const T rho_f = rho(T(0.5) * (cL + cR));
+        const T visc = ((txx0 - txxm) * ih + (txy(0, 1, 0) - txy0) * ih) + (n_txz - c_txz) * ih;
+        const T ucR = T(0.5) * (Ug(0, 0, 0) + Ug(1, 0, 0));
+        const T ucL = T(0.5) * (Ug(-1, 0, 0) + Ug(0, 0, 0));
+        const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(0, 1, 0) - uv0) * ih) + (n_uw - c_uw) * ih;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(-1, 0, 0))) * qdiv((cR - cL) * ih, rho_f);
+        Hx = H;
+        ux = Ug(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
+      }
+      {
+        const T cB = Cc(0, -1, 0), cA = Cc(0, 0, 0);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txyx - txy0) * ih + (tyy(0) - tyy(-1)) * ih) + (n_tyz - c_tyz) * ih;
+        const T vcA = T(0.5) * (Vg(0, 0, 0) + Vg(0, 1, 0));
+        const T vcB = T(0.5) * (Vg(0, -1, 0) + Vg(0, 0, 0));
+        const T conv = ((uvx - uv0) * ih + (vcA * vcA - vcB * vcB) * ih) + (n_vw - c_vw) * ih;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, -1, 0))) * qdiv((cA - cB) * ih, rho_f);
+        Hy = H;
+        vy = Vg(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
+      }
+      if (k >= 1) {
+        const T cB = Cc(0, 0, -1), cA = Cc(0, 0, 0);
+        const T rho_f = rho(T(0.5) * (cB + cA));
+        const T visc = ((txzx - c_txz) * ih + (c_tyzn - c_tyz) * ih) + (n_tzz - c_tzz) * ih;
+        const T wcA = T(0.5) * (Wf(0, 0, 0) + Wf(0, 0, 1));
+        const T wcB = T(0.5) * (Wf(0, 0, -1) + Wf(0, 0, 0));
+        const T conv = ((uwx - c_uw) * ih + (c_vwn - c_vw) * ih) + (wcA * wcA - wcB * wcB) * ih;
+        const T H = -conv + qdiv(visc, a.Re * rho_f);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, 0, -1))) * qdiv((cA - cB) * ih, rho_f);
+        Hz = H;
+        wz = Wf(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
+      }
+      a.Hu[c] = Hx;
+      a.Us[c] = fu * ux;
+      a.Hv[c] = Hy;
+      a.Vs[c] = fv * vy;
+      if (k >= 1) {
+        a.Hw[c] = Hz;
+        a.Ws[c] = fw * wz;
+      }
+    }
+    c_txz = n_txz;
+    c_tyz = n_tyz;
+    c_tyzn = n_tyzn;
+    c_uw = n_uw;
+    c_vw = n_vw;
+    c_vwn = n_vwn;
+    c_tzz = n_tzz;
+    __syncthreads();   // the slot of plane k-1 takes plane k+3 next
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy outlives the block
+}
+
+// dynamic shared memory of k3_predict_s: five fields, four planes, the haloed tile
+template <typename T>
+constexpr size_t k3_pred_smem() { return sizeof(T) * 5 * kPr * kPhx * kPhy; }
+
 // ------------------------------------------------------------- z-marching cell kernels
 constexpr int kCz = 16;   // planes per block of the cell kernels
 // Same blocks as the predictor: a 32 x 8 column of cells marching up kPz planes.  Fields
@@ -1427,7 +1643,7 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
       mark("fill_phi");
     }
     if constexpr (sizeof(T) == 4) k3_predict_a<T><<<zgp, zb, 0, s>>>(a);
-    else k3_predict<T><<<zgp, zb, 0, s>>>(a);
+    else k3_predict_s<T><<<zgp, zb, k3_pred_smem<T>(), s>>>(a);
     mark("predict");
     if (ng > 0) {
       k3_fill_u<T><<<(ng + 127) / 128, 128, 0, s>>>(a);
@@ -1459,7 +1675,9 @@ int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec) {
 
 // the FP32 form reads the face fractions in FP32 (rounded once from the FP64 tables)
 cudaError_t step3d_setup(Ctx& c) {
-  if (c.precision == IB_PF_FP64) return cudaSuccess;
+  if (c.precision == IB_PF_FP64)
+    return cudaFuncSetAttribute(k3_predict_s<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)k3_pred_smem<double>());
   for (Instance& in : c.inst) {
     const size_t cells = (size_t)in.nx * in.ny * in.nz, nxy = (size_t)in.nx * in.ny;
     cudaError_t e = cudaMalloc((void**)&in.alpha_f, sizeof(float) * (3 * cells + nxy));
