@@ -782,12 +782,12 @@ __host__ __device__ constexpr int tile_cols() {
   return (LOGN >= 10 ? 64 : 128) / (int)sizeof(typename C2T<T>::type);
 }
 
-// shared memory of a tile block: the tile, the twiddles, the cosine weights and the
-// per-column eigenvalue parts (z solve)
+// shared memory of a tile block: the tile, the twiddles (n), the cosine weights (n), the
+// z eigenvalues (n) and the per-column eigenvalue parts (2 pw) (the last three: z solve)
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int n, int pw, bool zsolve) {
-  return sizeof(typename C2T<T>::type) * ((size_t)n * pw + n / 2 + (zsolve ? n : 0)) +
-         sizeof(T) * 2 * pw;
+  return sizeof(typename C2T<T>::type) * ((size_t)n * pw + n + (zsolve ? n : 0)) +
+         (zsolve ? sizeof(T) * (n + 2 * pw) : 0);
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -799,17 +799,22 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 // caller waits (cp.async.wait_all) and synchronises before reading them.  The copies need
 // 16-byte aligned addresses and sizes: a tile whose source, pitch or width breaks that (no
 // layout of this file does) is not loaded and false is returned to every thread.
-template <typename C2, typename RowMap>
-__device__ __forceinline__ bool tile_load(C2* x, int pw, int n, const C2* src, size_t pitch,
-                                          int nc, RowMap rows) {
+template <int PW, int N, typename C2, typename RowMap>
+__device__ __forceinline__ bool tile_load(C2* x, const C2* src, size_t pitch, int nc,
+                                          RowMap rows) {
   const size_t bad = (reinterpret_cast<size_t>(src) | (pitch * sizeof(C2)) | (nc * sizeof(C2))) & 15;
-  if (bad != 0 || nc <= 0 || nc > pw) return false;
-  const int cpr = (int)(nc * sizeof(C2) / 16);   // chunks per row
-  const int total = n * cpr;
-  for (int c = threadIdx.x; c < total; c += kTileThreads) {
-    const int r = c / cpr, q = c - r * cpr;
-    cp_async16(reinterpret_cast<char*>(x + (size_t)rows(r) * pw) + 16 * q,
+  if (bad != 0 || nc <= 0 || nc > PW) return false;
+  auto copy = [&](int r, int q) {
+    cp_async16(reinterpret_cast<char*>(x + (size_t)rows(r) * PW) + 16 * q,
                reinterpret_cast<const char*>(src + r * pitch) + 16 * q);
+  };
+  constexpr int CPR = PW * (int)sizeof(C2) / 16;   // chunks of a full row
+  if (nc == PW) {
+#pragma unroll 4
+    for (int c = threadIdx.x; c < N * CPR; c += kTileThreads) copy(c / CPR, c % CPR);
+  } else {
+    const int cpr = (int)(nc * sizeof(C2) / 16);
+    for (int c = threadIdx.x; c < N * cpr; c += kTileThreads) copy(c / cpr, c % cpr);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   return true;
@@ -819,15 +824,15 @@ __device__ __forceinline__ void tile_wait() {
   __syncthreads();
 }
 
-// twiddle exp(-2 pi i t / N), 0 <= t < N, from the half table tw[m] = exp(-2 pi i m / N)
+// the full twiddle table exp(-2 pi i t / N), t < N, in shared memory from the half table
+// tw[m] = exp(-2 pi i m / N), m < N/2 (the other half is its negative)
 template <int N, typename C2>
-__device__ __forceinline__ C2 twiddle(const C2* tw, int t) {
-  C2 w = tw[t & (N / 2 - 1)];
-  if (t & (N / 2)) {
-    w.x = -w.x;
-    w.y = -w.y;
+__device__ __forceinline__ void stage_twiddles(C2* tws, const C2* __restrict__ tw) {
+  for (int t = threadIdx.x; t < N / 2; t += kTileThreads) {
+    const C2 w = tw[t];
+    tws[t] = w;
+    tws[t + N / 2] = C2{-w.x, -w.y};
   }
-  return w;
 }
 
 // CP adjacent complex values of a tile row as one 16-byte shared-memory access
@@ -877,7 +882,7 @@ __device__ __forceinline__ void ip_pass(C2* x, const C2* __restrict__ tw, Put pu
       if constexpr (STR > 1) {
 #pragma unroll
         for (int q = 1; q < R; ++q) {
-          const C2 w = cconj(twiddle<N>(tw, j * q * TS));
+          const C2 w = cconj(tw[j * q * TS]);
 #pragma unroll
           for (int c = 0; c < CP; ++c) v[c][q] = cmul(v[c][q], w);
         }
@@ -890,7 +895,7 @@ __device__ __forceinline__ void ip_pass(C2* x, const C2* __restrict__ tw, Put pu
       if constexpr (STR > 1) {
 #pragma unroll
         for (int q = 1; q < R; ++q) {
-          const C2 w = twiddle<N>(tw, j * q * TS);
+          const C2 w = tw[j * q * TS];
 #pragma unroll
           for (int c = 0; c < CP; ++c) v[c][q] = cmul(v[c][q], w);
         }
@@ -953,11 +958,11 @@ __global__ void __launch_bounds__(kTileThreads) k3_ytile(typename C2T<T>::type* 
   const int z = blockIdx.x / nbt, kx0 = (int)(blockIdx.x % nbt) * PW;
   const int nc = min(PW, sp - kx0);
   C2* g = spec + (size_t)z * N * sp + kx0;
-  if (!tile_load(x, PW, N, g, (size_t)sp, nc, [](int r) { return r; })) {
+  if (!tile_load<PW, N>(x, g, (size_t)sp, nc, [](int r) { return r; })) {
     if (threadIdx.x == 0) atomicOr(status, 2);
     return;
   }
-  for (int t = threadIdx.x; t < N / 2; t += kTileThreads) tws[t] = tw[t];
+  stage_twiddles<N>(tws, tw);
   tile_wait();
   const T sc = INV ? T(1) / T(N) : T(1);
   ip_fft<LOGN, 0, INV, PW, T>(x, tws, [&](int row, int f, const C2* v) {
@@ -980,23 +985,27 @@ __global__ void __launch_bounds__(kTileThreads) k3_ztile(typename C2T<T>::type* 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C2* x = reinterpret_cast<C2*>(smem_raw);
   C2* tws = x + N * PW;
-  C2* wds = tws + half;
-  T* lcx = reinterpret_cast<T*>(wds + N);   // lamx[kx] of each column
+  C2* wds = tws + N;
+  T* lzs = reinterpret_cast<T*>(wds + N);   // lamz[m]
+  T* lcx = lzs + N;                         // lamx[kx] of each column
   T* lcy = lcx + PW;                        // the y eigenvalue of each column's row
   const int k0 = blockIdx.x * PW;
   const int nc = min(PW, ncols - k0);
   const size_t pitch = (size_t)ncols;
   C2* g = spec + k0;
-  if (!tile_load(x, PW, N, g, pitch, nc,
-                 [](int r) { return (r & 1) ? N - 1 - (r >> 1) : (r >> 1); })) {
+  if (!tile_load<PW, N>(x, g, pitch, nc,
+                        [](int r) { return (r & 1) ? N - 1 - (r >> 1) : (r >> 1); })) {
     if (threadIdx.x == 0) atomicOr(status, 2);
     return;
   }
   const T* lamz = sizeof(T) == 8 ? (const T*)sym.lamy : (const T*)sym.lamy_f;
   const T* lam_x = sizeof(T) == 8 ? (const T*)sym.lamx : (const T*)sym.lamx_f;
   const T* lam_y = sizeof(T) == 8 ? (const T*)sym.lamyp : (const T*)sym.lamyp_f;
-  for (int t = threadIdx.x; t < half; t += kTileThreads) tws[t] = tw[t];
-  for (int t = threadIdx.x; t < N; t += kTileThreads) wds[t] = wd[t];
+  stage_twiddles<N>(tws, tw);
+  for (int t = threadIdx.x; t < N; t += kTileThreads) {
+    wds[t] = wd[t];
+    lzs[t] = lamz[t];
+  }
   for (int c = threadIdx.x; c < PW; c += kTileThreads) {
     const int k = min(k0 + c, ncols - 1);
     lcx[c] = lam_x[min(k % sp, nh1 - 1)];   // the pad column (zero) takes the last mode's
@@ -1007,50 +1016,59 @@ __global__ void __launch_bounds__(kTileThreads) k3_ztile(typename C2T<T>::type* 
     st_cols<C2, CP>(x + row * PW + f, v);
   });
   __syncthreads();
-  // pair tasks (m, N - m), m = 0..N/2, of every column; mode m sits at row fft_pos(m)
-  for (int t = threadIdx.x; t < PW * (half + 1); t += kTileThreads) {
-    const int c = t % PW, m = t / PW;
+  // pair tasks (m, N - m), m = 0..N/2, of CP adjacent columns; mode m sits at row fft_pos(m)
+  constexpr int NG = PW / CP;
+  for (int t = threadIdx.x; t < NG * (half + 1); t += kTileThreads) {
+    const int c0 = (t % NG) * CP, m = t / NG;
     const int mm = (N - m) & (N - 1);
-    const int im = fft_pos(m, LOGN) * PW + c, imm = fft_pos(mm, LOGN) * PW + c;
-    const C2 Vm = x[im], Vmm = x[imm];
-    C2 Xm, Xmm;
-    {
-      C2 vr, vi, w = wds[m];
-      vr.x = T(0.5) * (Vm.x + Vmm.x);
-      vr.y = T(0.5) * (Vm.y - Vmm.y);
-      vi.x = T(0.5) * (Vm.y + Vmm.y);
-      vi.y = T(-0.5) * (Vm.x - Vmm.x);
-      Xm.x = w.x * vr.x - w.y * vr.y;
-      Xm.y = w.x * vi.x - w.y * vi.y;
+    C2* pm = x + fft_pos(m, LOGN) * PW + c0;
+    C2* pmm = x + fft_pos(mm, LOGN) * PW + c0;
+    C2 Vm[CP], Vmm[CP], Zm[CP], Zmm[CP];
+    ld_cols<C2, CP>(pm, Vm);
+    ld_cols<C2, CP>(pmm, Vmm);
+    const C2 wm = wds[m], wmm = wds[mm];
+    const T lzm = lzs[m], lzmm = lzs[mm];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) {
+      C2 Xm, Xmm;
+      {
+        C2 vr, vi;
+        vr.x = T(0.5) * (Vm[c].x + Vmm[c].x);
+        vr.y = T(0.5) * (Vm[c].y - Vmm[c].y);
+        vi.x = T(0.5) * (Vm[c].y + Vmm[c].y);
+        vi.y = T(-0.5) * (Vm[c].x - Vmm[c].x);
+        Xm.x = wm.x * vr.x - wm.y * vr.y;
+        Xm.y = wm.x * vi.x - wm.y * vi.y;
+      }
+      {
+        C2 vr, vi;
+        vr.x = T(0.5) * (Vmm[c].x + Vm[c].x);
+        vr.y = T(0.5) * (Vmm[c].y - Vm[c].y);
+        vi.x = T(0.5) * (Vmm[c].y + Vm[c].y);
+        vi.y = T(-0.5) * (Vmm[c].x - Vm[c].x);
+        Xmm.x = wmm.x * vr.x - wmm.y * vr.y;
+        Xmm.y = wmm.x * vi.x - wmm.y * vi.y;
+      }
+      const T lc = lcy[c0 + c], lx = lcx[c0 + c];
+      Xm = divide_symbol<T>(Xm, (lzm + lc) + lx, sym);
+      Xmm = divide_symbol<T>(Xmm, (lzmm + lc) + lx, sym);
+      {
+        C2 y;   // X_m - i X_{N-m}; X_N = 0 for m = 0
+        const C2 xo = (m == 0) ? C2{T(0), T(0)} : Xmm;
+        y.x = Xm.x + xo.y;
+        y.y = Xm.y - xo.x;
+        Zm[c] = cmul(cconj(wm), y);
+      }
+      {
+        C2 y;
+        const C2 xo = (mm == 0) ? C2{T(0), T(0)} : Xm;
+        y.x = Xmm.x + xo.y;
+        y.y = Xmm.y - xo.x;
+        Zmm[c] = cmul(cconj(wmm), y);
+      }
     }
-    {
-      C2 vr, vi, w = wds[mm];
-      vr.x = T(0.5) * (Vmm.x + Vm.x);
-      vr.y = T(0.5) * (Vmm.y - Vm.y);
-      vi.x = T(0.5) * (Vmm.y + Vm.y);
-      vi.y = T(-0.5) * (Vmm.x - Vm.x);
-      Xmm.x = w.x * vr.x - w.y * vr.y;
-      Xmm.y = w.x * vi.x - w.y * vi.y;
-    }
-    Xm = divide_symbol<T>(Xm, (lamz[m] + lcy[c]) + lcx[c], sym);
-    Xmm = divide_symbol<T>(Xmm, (lamz[mm] + lcy[c]) + lcx[c], sym);
-    C2 Zm, Zmm;
-    {
-      C2 y;   // X_m - i X_{N-m}; X_N = 0 for m = 0
-      const C2 xo = (m == 0) ? C2{T(0), T(0)} : Xmm;
-      y.x = Xm.x + xo.y;
-      y.y = Xm.y - xo.x;
-      Zm = cmul(cconj(wds[m]), y);
-    }
-    {
-      C2 y;
-      const C2 xo = (mm == 0) ? C2{T(0), T(0)} : Xm;
-      y.x = Xmm.x + xo.y;
-      y.y = Xmm.y - xo.x;
-      Zmm = cmul(cconj(wds[mm]), y);
-    }
-    x[im] = Zm;
-    if (mm != m) x[imm] = Zmm;
+    st_cols<C2, CP>(pm, Zm);
+    if (mm != m) st_cols<C2, CP>(pmm, Zmm);
   }
   __syncthreads();
   const T inv = T(1) / T(N);

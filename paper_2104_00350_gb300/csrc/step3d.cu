@@ -10,6 +10,7 @@
 // products of face means at the edges.  The solves work on increments exactly as the 2D
 // step does (CH: over the BDF2 predictor B; pressure: over P^ = 2P^n - P^{n-1}).
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "batch.h"
@@ -812,13 +813,117 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
   int s_m = 0, s_0 = 0, s_p = 0;
   T g_m = T(1), g_p = T(1);   // no-slip sign of the staged u, v of planes k-1 and k+1
   auto pl = [&](int kk) { return kk == k ? s_0 : (kk > k ? s_p : s_m); };
-  auto sg = [&](int kk) { return kk == k ? T(1) : (kk > k ? g_p : g_m); };
-  auto Cc = [&](int ii, int jj, int kk) { return sC[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Fc = [&](int ii, int jj, int kk) { return sF[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Ug = [&](int ii, int jj, int kk) { return sg(kk) * sU[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Vg = [&](int ii, int jj, int kk) { return sg(kk) * sV[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Wf = [&](int ii, int jj, int kk) { return sW[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
   const T ih = a.inv_h;
+  // z-edge values of plane k at this thread's column, carried from the previous plane's
+  // k+1 evaluation (the same expressions and operands, so the same values)
+  T c_txz = T(0), c_tyz = T(0), c_uw = T(0), c_vw = T(0), c_tzz = T(0);
+  // the faces of cell (i, j, k); SG: planes k-1 or k+1 are ghost planes beyond a z wall,
+  // whose staged u, v take the no-slip sign on reading (without SG every sign is +1)
+  auto plane = [&](auto sg_tag, size_t c, T hu, T hv, T hw, T fu, T fv, T fw) {
+    constexpr bool SG = decltype(sg_tag)::value;
+    auto sg = [&](int kk) -> T {
+      if constexpr (SG) return kk == k ? T(1) : (kk > k ? g_p : g_m);
+      else return T(1);
+    };
+    auto Cc = [&](int ii, int jj, int kk) { return sC[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+    auto Fc = [&](int ii, int jj, int kk) { return sF[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+    auto Ug = [&](int ii, int jj, int kk) {
+      const T v = sU[pl(kk)][jj - j0 + 1][ii - i0 + 1];
+      if constexpr (SG) return sg(kk) * v; else return v;
+    };
+    auto Vg = [&](int ii, int jj, int kk) {
+      const T v = sV[pl(kk)][jj - j0 + 1][ii - i0 + 1];
+      if constexpr (SG) return sg(kk) * v; else return v;
+    };
+    auto Wf = [&](int ii, int jj, int kk) { return sW[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
+    auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
+    auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
+    auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
+    auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
+    auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
+    auto txy = [&](int ii, int jj, int kk) {
+      const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+      return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
+    };
+    auto txz = [&](int ii, int jj, int kk) {
+      const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
+      return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
+    };
+    auto tyz = [&](int ii, int jj, int kk) {
+      const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
+      return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
+    };
+    auto uv = [&](int ii, int jj, int kk) {
+      return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
+    };
+    auto uw = [&](int ii, int jj, int kk) {
+      return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
+    };
+    auto vw = [&](int ii, int jj, int kk) {
+      return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
+    };
+    if (k == k0) {   // first plane of the block: the k-level z-edge values directly
+      c_txz = txz(i, j, k);
+      c_tyz = tyz(i, j, k);
+      c_uw = uw(i, j, k);
+      c_vw = vw(i, j, k);
+      c_tzz = tzz(k - 1);
+    }
+    const T n_txz = txz(i, j, k + 1), n_tyz = tyz(i, j, k + 1);
+    const T n_uw = uw(i, j, k + 1), n_vw = vw(i, j, k + 1), n_tzz = tzz(k);
+    const T k_st = a.k_st;
+    T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
+    {
+      const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
+      const T rho_f = rho(T(0.5) * (cL + cR));
+      const T txy0 = txy(i, j, k);
+      const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy0) * ih) + (n_txz - c_txz) * ih;
+      const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
+      const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
+      const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) + (n_uw - c_uw) * ih;
+      const T H = -conv + qdiv(visc, a.Re * rho_f);
+      const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * qdiv((cR - cL) * ih, rho_f);
+      Hx = H;
+      ux = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
+    }
+    {
+      const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
+      const T rho_f = rho(T(0.5) * (cB + cA));
+      const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) + (n_tyz - c_tyz) * ih;
+      const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
+      const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
+      const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) + (n_vw - c_vw) * ih;
+      const T H = -conv + qdiv(visc, a.Re * rho_f);
+      const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * qdiv((cA - cB) * ih, rho_f);
+      Hy = H;
+      vy = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
+    }
+    if (k >= 1) {
+      const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
+      const T rho_f = rho(T(0.5) * (cB + cA));
+      const T visc = ((txz(i + 1, j, k) - c_txz) * ih + (tyz(i, j + 1, k) - c_tyz) * ih) + (n_tzz - c_tzz) * ih;
+      const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
+      const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
+      const T conv = ((uw(i + 1, j, k) - c_uw) * ih + (vw(i, j + 1, k) - c_vw) * ih) + (wcA * wcA - wcB * wcB) * ih;
+      const T H = -conv + qdiv(visc, a.Re * rho_f);
+      const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * qdiv((cA - cB) * ih, rho_f);
+      Hz = H;
+      wz = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
+    }
+    a.Hu[c] = Hx;
+    a.Us[c] = fu * ux;
+    a.Hv[c] = Hy;
+    a.Vs[c] = fv * vy;
+    if (k >= 1) {
+      a.Hw[c] = Hz;
+      a.Ws[c] = fw * wz;
+    }
+    c_txz = n_txz;
+    c_tyz = n_tyz;
+    c_uw = n_uw;
+    c_vw = n_vw;
+    c_tzz = n_tzz;
+  };
   issue(k0 - 1);
   issue(k0);
   issue(k0 + 1);
@@ -845,84 +950,8 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
     g_m = k - 1 < 0 ? T(-1) : T(1);
     g_p = k + 1 >= a.nz ? T(-1) : T(1);
     if (active) {
-      auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
-      auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-      auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
-      auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
-      auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
-      auto txy = [&](int ii, int jj, int kk) {
-        const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
-      };
-      auto txz = [&](int ii, int jj, int kk) {
-        const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
-      };
-      auto tyz = [&](int ii, int jj, int kk) {
-        const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
-      };
-      auto uv = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
-      };
-      auto uw = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
-      };
-      auto vw = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
-      };
-      const T k_st = a.k_st;
-      T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
-      {
-        const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cL + cR));
-        const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
-                       (txz(i, j, k + 1) - txz(i, j, k)) * ih;
-        const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
-        const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
-        const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
-                       (uw(i, j, k + 1) - uw(i, j, k)) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * qdiv((cR - cL) * ih, rho_f);
-        Hx = H;
-        ux = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
-      }
-      {
-        const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cB + cA));
-        const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
-                       (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
-        const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
-        const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
-        const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
-                       (vw(i, j, k + 1) - vw(i, j, k)) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * qdiv((cA - cB) * ih, rho_f);
-        Hy = H;
-        vy = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
-      }
-      if (k >= 1) {
-        const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cB + cA));
-        const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
-                       (tzz(k) - tzz(k - 1)) * ih;
-        const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
-        const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
-        const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
-                       (wcA * wcA - wcB * wcB) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * qdiv((cA - cB) * ih, rho_f);
-        Hz = H;
-        wz = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
-      }
-      a.Hu[c] = Hx;
-      a.Us[c] = fu * ux;
-      a.Hv[c] = Hy;
-      a.Vs[c] = fv * vy;
-      if (k >= 1) {
-        a.Hw[c] = Hz;
-        a.Ws[c] = fw * wz;
-      }
+      if (k >= 1 && k + 1 < a.nz) plane(std::false_type{}, c, hu, hv, hw, fu, fv, fw);
+      else plane(std::true_type{}, c, hu, hv, hw, fu, fv, fw);
     }
     __syncthreads();   // the slot of plane k-1 takes plane k+3 next
   }
