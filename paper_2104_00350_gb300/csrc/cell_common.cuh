@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "ibpf_internal.h"
+
 namespace ibpf {
 
 constexpr double kKappa = 1.0606601717798212;   // 3 / (2 sqrt 2)
@@ -33,8 +35,9 @@ __device__ __forceinline__ void pair_add(T& hi, T& lo, T b_hi, T b_lo) {
 
 // Block reduction of one tile's sum of C in a fixed tree (FP64, or compensated FP32 pairs
 // in the FP32 form): a shuffle tree within each warp, then over the warps' results; written
-// as FP64 at the tile's index.  The last tile of an instance to finish adds the partials
-// (each thread a fixed strided subset, then the same two-level tree) in FP64.
+// as FP64 at the tile's index.  The partials are then added in FP64 in two levels (groups of
+// kMassGroup tiles, then the groups), each by the last block of its level to finish, each
+// in a fixed order.
 template <typename T>
 __device__ __forceinline__ void warp_pair_sum(T& hi, T& lo) {
 #pragma unroll
@@ -50,6 +53,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// The two-level final sum of tile_mass (kMassGroup tiles per group, ibpf_internal.h): the
+// last tile of a group to finish adds the group's partials, the last group to finish adds
+// the group sums, so no block adds more than max(kMassGroup, groups) values.  partial holds
+// ntiles + groups doubles, ticket 1 + groups counters (all zero between steps).
+
+// FP64 sum of v over the NT threads of a block in a fixed tree (every thread gets it)
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* wd) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  v = warp_sum(v);
+  if (lane == 0) wd[warp] = v;
+  __syncthreads();
+  v = warp_sum(lane < NW ? wd[lane] : 0.0);
+  return v;
+}
+
 template <typename T, int NT>
 __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__ partial,
                           unsigned* __restrict__ ticket, double* __restrict__ mass) {
@@ -61,6 +82,9 @@ __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__
   __shared__ bool last;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  const int grp = tile / kMassGroup, ngrp = (ntiles + kMassGroup - 1) / kMassGroup;
+  const int b0 = grp * kMassGroup;
+  const int gsz = ntiles - b0 < kMassGroup ? ntiles - b0 : kMassGroup;
   warp_pair_sum(hi, lo);
   if (lane == 0) {
     wh[warp] = hi;
@@ -74,26 +98,34 @@ __device__ void tile_mass(T hi, T lo, int tile, int ntiles, double* __restrict__
     if (lane == 0) {
       partial[tile] = (double)hi + (double)lo;
       __threadfence();
-      last = (atomicAdd(ticket, 1u) == (unsigned)ntiles - 1u);
+      last = (atomicAdd(ticket + 1 + grp, 1u) == (unsigned)gsz - 1u);
     }
   }
   __syncthreads();
-  if (last) {
+  if (!last) return;   // the same for every thread of the block
+  // the last tile of group grp: the group's sum
+  __threadfence();
+  double sacc = 0.0;
+  for (int b = tid; b < gsz; b += NT) sacc += ((volatile double*)partial)[b0 + b];
+  sacc = block_sum<NT>(sacc, wd);
+  if (tid == 0) {
+    partial[ntiles + grp] = sacc;
+    ticket[1 + grp] = 0u;
     __threadfence();
-    double sacc = 0.0;
-    for (int b = tid; b < ntiles; b += NT) sacc += ((volatile double*)partial)[b];
-    sacc = warp_sum(sacc);
-    if (lane == 0) wd[warp] = sacc;
-    __syncthreads();
-    if (warp == 0) {
-      sacc = warp_sum(lane < NW ? wd[lane] : 0.0);
-      if (lane == 0) {
-        *mass = sacc;
-        *ticket = 0u;
-      }
-    }
+    last = (atomicAdd(ticket, 1u) == (unsigned)ngrp - 1u);
   }
   __syncthreads();
+  if (!last) return;
+  // the last group: the sum of the group sums
+  __threadfence();
+  sacc = 0.0;
+  for (int b = tid; b < ngrp; b += NT) sacc += ((volatile double*)partial)[ntiles + b];
+  __syncthreads();   // wd is reused
+  sacc = block_sum<NT>(sacc, wd);
+  if (tid == 0) {
+    *mass = sacc;
+    *ticket = 0u;
+  }
 }
 
 // Quotient by a density-type factor (rho_f, Re rho_f; both O(1) and positive).  FP32 form:

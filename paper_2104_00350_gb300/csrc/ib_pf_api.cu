@@ -354,14 +354,16 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     const int nred = (int)((cells + 255) / 256);
     const int nblk = ntile > nred ? ntile : nred;
     in.nblk_red = nblk;
-    if (cudaMalloc((void**)&in.partial, sizeof(double) * nblk) != cudaSuccess ||
-        cudaMalloc((void**)&in.ticket, sizeof(unsigned)) != cudaSuccess ||
+    // group sums and group counters of the two-level final sum (tile_mass)
+    const int ngrp = (nblk + kMassGroup - 1) / kMassGroup;
+    if (cudaMalloc((void**)&in.partial, sizeof(double) * (nblk + ngrp)) != cudaSuccess ||
+        cudaMalloc((void**)&in.ticket, sizeof(unsigned) * (1 + ngrp)) != cudaSuccess ||
         cudaMalloc((void**)&in.mass, sizeof(double)) != cudaSuccess ||
         cudaMalloc((void**)&in.status, sizeof(int)) != cudaSuccess) {
       ctx->err = "reduction buffers allocation failed";
       return bail(IB_PF_E_CUDA);
     }
-    cudaMemsetAsync(in.ticket, 0, sizeof(unsigned), ctx->work);
+    cudaMemsetAsync(in.ticket, 0, sizeof(unsigned) * (1 + ngrp), ctx->work);
     cudaMemsetAsync(in.mass, 0, sizeof(double), ctx->work);
     cudaMemsetAsync(in.status, 0, sizeof(int), ctx->work);
     if ((in.dim == 3 ? spectral3_tables(in, ctx->precision) : spectral_tables(in, ctx->precision)) !=

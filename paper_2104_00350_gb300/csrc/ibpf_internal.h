@@ -45,6 +45,9 @@ struct WallDev {       // wall predicate parameters as the device sees them
 };
 
 // geometry tables of one instance (device pointers, FP64 / int)
+// tiles per group of the two-level FP64 mass sum (tile_mass in cell_common.cuh)
+constexpr int kMassGroup = 256;
+
 struct Tables {
   double* alpha_c = nullptr;   // ny x nx
   double* alpha_u = nullptr;   // ny x nx
@@ -131,7 +134,7 @@ struct Instance {
   unsigned* ticket = nullptr;  // last-block counter
   double* mass = nullptr;      // sum of C after the last step
   int* status = nullptr;       // 1 once a non-finite value was seen
-  int nblk_red = 0;
+  int nblk_red = 0;            // partial sums of the mass reduction (plus their groups)
   std::vector<void*> bound;    // caller-owned field buffers (ib_pf_bind_fields): never freed
 };
 

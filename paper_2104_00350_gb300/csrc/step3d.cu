@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kTQ, 6) k3_poisson_rhs_q(S3<float> a) {
 
 // a8: u^{n+1} = u** - dt [ (1/rho_f) grad P^ + (1/rho0) grad dP ] on every face (z-faces
 // 1..nz-1); non-finite check; the tile's compensated sum of C for the FP64 mass
-__global__ void __launch_bounds__(kTQ) k3_correct_q(S3<float> a) {
+__global__ void __launch_bounds__(kTQ, 10) k3_correct_q(S3<float> a) {
   const Run d = run4(a);
   auto rho = [&](float cc) { return a.rho_a + a.rho_b * clamp1(cc); };
   const float* C = a.C1;
