@@ -478,6 +478,9 @@ def run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world, 
     s = ibpf.solver_from_cases([case], prec, stream=stream.cuda_stream)
     s.precompute_weights()
     setup_s = time.time() - t0
+    # the schedule (transform tile widths, predictor planes) picked by the library's tuner;
+    # it times its candidates on the fresh context and leaves the state as it was
+    tuned = s.autotune(0, reps=3)
     dt_np = np.float64 if esz == 8 else np.float32
     C0 = W.droplet_C3d(case, dt_np)
 
@@ -501,7 +504,9 @@ def run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world, 
             "grid": f"{case.nx}x{case.ny}x{case.nz}",
             "ghosts": int(s.query(ibpf.Q_N_GHOST)),
             "gpu_launches": int(s.query(ibpf.Q_LAUNCHES)) * n,
-            "setup_s": round(setup_s, 2), "l2": "inputs larger than L2"}
+            "setup_s": round(setup_s, 2), "l2": "inputs larger than L2",
+            "tuning": {"choice": tuned["choice"],
+                       "candidate_ms": {k: round(v, 4) for k, v in tuned["ms"].items()}}}
     if case.geom_kind == W.GEOM_SPHERES:
         line["spheres"] = len(case.spheres)
     try:

@@ -273,6 +273,38 @@ ib_pf_status ib_pf_read_table(ib_pf_ctx* ctx, int instance, int table_id, void* 
 /* Scalar diagnostics (ib_pf_query_id) of `instance`.  Synchronises the stream. */
 ib_pf_status ib_pf_query(ib_pf_ctx* ctx, int instance, int what, double* out);
 
+/* Schedule choices of a 3D instance (0 = the built-in default).
+ *   y_tile_bytes, z_tile_bytes  row bytes of the column tiles of the y transforms and of the
+ *                               z solve: 128 (transform lengths <= 512) or 64 (lengths >= 256;
+ *                               the default from 1024 points on, 128 below)
+ *   predict_planes              planes each predictor block marches through: 8, 16 (default)
+ *                               or 32 (capped at nz)
+ * The choices change the schedule only; results are the same bit for bit (each kernel's
+ * arithmetic per point is fixed). */
+typedef struct {
+  int y_tile_bytes;
+  int z_tile_bytes;
+  int predict_planes;
+} ib_pf_tuning;
+
+/* Sets the schedule of 3D instance `instance` (IB_PF_E_ARG for a value not listed above or
+ * not built for the instance's lengths; IB_PF_E_UNSUPPORTED for a 2D context, whose batched
+ * kernels have fixed tiles).  The step graphs are recaptured at the next step. */
+ib_pf_status ib_pf_set_tuning(ib_pf_ctx* ctx, int instance, const ib_pf_tuning* t);
+ib_pf_status ib_pf_get_tuning(ib_pf_ctx* ctx, int instance, ib_pf_tuning* t);
+
+/* Autotuner (3D): times every built candidate of each choice on instance `instance` -- the
+ * y transforms and the z solve on the instance's spectral scratch, the predictor on its own
+ * state with the AB2 history (Hu, Hv, Hw) saved before and restored after -- `reps` launches
+ * each after one warm-up, and sets the fastest.  The state after the call equals the state
+ * before.  chosen (may be NULL) receives the choice; times_ms (may be NULL) the mean ms per
+ * launch of the candidates in the order y 128, y 64, z 128, z 64, planes 8, 16, 32 (-1 for a
+ * candidate not built for the lengths), 7 values.  Synchronises the stream; allocates a
+ * scratch copy of the history for the duration of the call.  The caller may cache the choice
+ * (the Python binding keeps a JSON file keyed by grid shape, precision and GPU name). */
+ib_pf_status ib_pf_autotune(ib_pf_ctx* ctx, int instance, int reps, ib_pf_tuning* chosen,
+                            double* times_ms);
+
 /* Per-kernel timing.  enable != 0 recaptures the step graphs with a CUDA event recorded
  * on the work stream before the first kernel of a step and after every kernel; enable = 0
  * restores the plain graphs.  Timing adds the event records to the step, nothing else. */

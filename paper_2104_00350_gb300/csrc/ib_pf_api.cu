@@ -846,6 +846,81 @@ ib_pf_status ib_pf_set_kernel_timing(ib_pf_ctx* ctx, int enable) {
   return IB_PF_OK;
 }
 
+namespace {
+// the tile row widths built for a transform of 2^logn points
+bool tile_rb_built(int logn, int rb) { return (rb == 128 && logn <= 9) || (rb == 64 && logn >= 8); }
+
+void drop_graphs(ib_pf_ctx* ctx) {
+  for (int ph = 0; ph < 2; ++ph) {
+    if (ctx->graph[ph]) cudaGraphExecDestroy(ctx->graph[ph]);
+    ctx->graph[ph] = nullptr;
+  }
+}
+}  // namespace
+
+ib_pf_status ib_pf_set_tuning(ib_pf_ctx* ctx, int instance, const ib_pf_tuning* t) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (!t) return fail(ctx, IB_PF_E_ARG, "null tuning");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "instance out of range");
+  Instance& in = ctx->inst[instance];
+  if (in.dim != 3) return fail(ctx, IB_PF_E_UNSUPPORTED, "tuning applies to 3D instances");
+  if (t->y_tile_bytes != 0 && !tile_rb_built(in.logny, t->y_tile_bytes))
+    return fail(ctx, IB_PF_E_ARG, "y_tile_bytes not built for ny");
+  if (t->z_tile_bytes != 0 && !tile_rb_built(in.lognz, t->z_tile_bytes))
+    return fail(ctx, IB_PF_E_ARG, "z_tile_bytes not built for nz");
+  const int pp = t->predict_planes;
+  if (pp != 0 && pp != 8 && pp != 16 && pp != 32) return fail(ctx, IB_PF_E_ARG, "predict_planes must be 0, 8, 16 or 32");
+  CK(cudaStreamSynchronize(ctx->work));
+  in.tune_y_rb = t->y_tile_bytes;
+  in.tune_z_rb = t->z_tile_bytes;
+  in.tune_pred_planes = pp;
+  drop_graphs(ctx);
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_get_tuning(ib_pf_ctx* ctx, int instance, ib_pf_tuning* t) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (!t) return fail(ctx, IB_PF_E_ARG, "null tuning");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "instance out of range");
+  const Instance& in = ctx->inst[instance];
+  t->y_tile_bytes = in.tune_y_rb;
+  t->z_tile_bytes = in.tune_z_rb;
+  t->predict_planes = in.tune_pred_planes;
+  return IB_PF_OK;
+}
+
+ib_pf_status ib_pf_autotune(ib_pf_ctx* ctx, int instance, int reps, ib_pf_tuning* chosen,
+                            double* times_ms) {
+  if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
+  if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, IB_PF_E_ARG, "instance out of range");
+  if (reps < 1) return fail(ctx, IB_PF_E_ARG, "reps < 1");
+  Instance& in = ctx->inst[instance];
+  if (in.dim != 3) return fail(ctx, IB_PF_E_UNSUPPORTED, "tuning applies to 3D instances");
+  if (!ctx->weights_ready) return fail(ctx, IB_PF_E_STATE, "ib_pf_precompute_weights has not succeeded");
+  CK(cudaStreamSynchronize(ctx->work));
+  float t[7];
+  const int rbs[2] = {128, 64}, planes[3] = {8, 16, 32};
+  for (int q = 0; q < 2; ++q) t[q] = spectral3_time_tiles(in, ctx->precision, 1, rbs[q], reps, ctx->work);
+  for (int q = 0; q < 2; ++q) t[2 + q] = spectral3_time_tiles(in, ctx->precision, 2, rbs[q], reps, ctx->work);
+  for (int q = 0; q < 3; ++q)
+    t[4 + q] = planes[q] <= in.nz || q == 0 ? step3d_time_predict(*ctx, in, planes[q], reps, ctx->work) : -1.0f;
+  CK(cudaGetLastError());
+  auto best = [&](int first, int n, const int* vals) {
+    int b = -1;
+    for (int q = 0; q < n; ++q)
+      if (t[first + q] >= 0.0f && (b < 0 || t[first + q] < t[first + b])) b = q;
+    return b < 0 ? 0 : vals[b];
+  };
+  ib_pf_tuning tu;
+  tu.y_tile_bytes = best(0, 2, rbs);
+  tu.z_tile_bytes = best(2, 2, rbs);
+  tu.predict_planes = best(4, 3, planes);
+  if (times_ms)
+    for (int q = 0; q < 7; ++q) times_ms[q] = (double)t[q];
+  if (chosen) *chosen = tu;
+  return ib_pf_set_tuning(ctx, instance, &tu);
+}
+
 ib_pf_status ib_pf_kernel_times(ib_pf_ctx* ctx, int cap, double* ms, const char** names, int* n) {
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "null context");
   if (!ctx->timing || ctx->steps == 0 || ctx->tev.size() < 2)

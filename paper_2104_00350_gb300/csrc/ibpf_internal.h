@@ -135,6 +135,9 @@ struct Instance {
   double* mass = nullptr;      // sum of C after the last step
   int* status = nullptr;       // 1 once a non-finite value was seen
   int nblk_red = 0;            // partial sums of the mass reduction (plus their groups)
+  // 3D schedule choices (0: the built-in default), set by ib_pf_set_tuning / ib_pf_autotune:
+  // row bytes of the y and z transform tiles (64 or 128), planes per predictor block
+  int tune_y_rb = 0, tune_z_rb = 0, tune_pred_planes = 0;
   std::vector<void*> bound;    // caller-owned field buffers (ib_pf_bind_fields): never freed
 };
 
@@ -236,6 +239,13 @@ cudaError_t geometry3_weights(Instance& in, cudaStream_t s, int* n_fail, std::st
 
 // ---- spectral.cu / step3d.cu: the 3D step, one instance after another
 cudaError_t spectral3_tables(Instance& in, int precision);
+// mean ms per launch of the 3D predictor with `planes` planes per block (AB2 history saved
+// and restored); -1 on a CUDA error
+float step3d_time_predict(const Ctx& c, Instance& in, int planes, int reps, cudaStream_t s);
+// mean ms per launch of the 3D y transforms (axis 1) or z solve (axis 2) with rb-byte tile
+// rows, timed on the instance's spectral scratch; -1 when rb is not built for that length
+float spectral3_time_tiles(const Instance& in, int precision, int axis, int rb, int reps,
+                           cudaStream_t s);
 int spectral3_solve(const Instance& in, int precision, int mode, int cur, cudaStream_t s,
                     Recorder* rec);
 int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec);

@@ -776,10 +776,11 @@ __host__ __device__ constexpr int fft_pos(int k, int logn) {
 
 constexpr int kTileThreads = 256;
 
-// columns per tile for 2^LOGN-point transforms of T
-template <typename T, int LOGN>
+// columns per tile of RB-byte rows (RB = 128: up to 512 points; RB = 64: from 256 points
+// on, the only width for 1024 points, whose 128-byte tiles would leave one block per SM)
+template <typename T, int RB>
 __host__ __device__ constexpr int tile_cols() {
-  return (LOGN >= 10 ? 64 : 128) / (int)sizeof(typename C2T<T>::type);
+  return RB / (int)sizeof(typename C2T<T>::type);
 }
 
 // shared memory of a tile block: the tile, the twiddles (n), the cosine weights (n), the
@@ -947,11 +948,11 @@ __device__ __forceinline__ void st_global(C2* p, const C2* v, int f, int nc, T s
 // y transform of one tile: z-plane blockIdx.x / nbt, columns kx0 = (blockIdx.x % nbt) PW ..
 // (nc = min(PW, sp - kx0) of them).  Forward: rows in natural order in, in the order fft_pos
 // out.  Inverse: back, scaled by 1/N.
-template <typename T, int LOGN, bool INV>
+template <typename T, int LOGN, bool INV, int RB>
 __global__ void __launch_bounds__(kTileThreads) k3_ytile(typename C2T<T>::type* __restrict__ spec,
     int sp, int nbt, const typename C2T<T>::type* __restrict__ tw, int* status) {
   using C2 = typename C2T<T>::type;
-  constexpr int N = 1 << LOGN, PW = tile_cols<T, LOGN>(), CP = 16 / (int)sizeof(C2);
+  constexpr int N = 1 << LOGN, PW = tile_cols<T, RB>(), CP = 16 / (int)sizeof(C2);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C2* x = reinterpret_cast<C2*>(smem_raw);
   C2* tws = x + N * PW;
@@ -975,12 +976,12 @@ __global__ void __launch_bounds__(kTileThreads) k3_ytile(typename C2T<T>::type* 
 // the row copies: row r goes to r/2 if even, N - 1 - (r-1)/2 if odd) and an N-point FFT,
 // division by the symbol at L = (lamz[m] + lamy[fft_rev(p)]) + lamx[kx], inverse transform
 // and the inverse reordering on the way out (the pair formulas of cols_core).
-template <typename T, int LOGN>
+template <typename T, int LOGN, int RB>
 __global__ void __launch_bounds__(kTileThreads) k3_ztile(typename C2T<T>::type* __restrict__ spec,
     int ncols, int sp, int nh1, const typename C2T<T>::type* __restrict__ tw,
     const typename C2T<T>::type* __restrict__ wd, SymbolArgs sym, int* status) {
   using C2 = typename C2T<T>::type;
-  constexpr int N = 1 << LOGN, PW = tile_cols<T, LOGN>(), half = N / 2;
+  constexpr int N = 1 << LOGN, PW = tile_cols<T, RB>(), half = N / 2;
   constexpr int CP = 16 / (int)sizeof(C2);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C2* x = reinterpret_cast<C2*>(smem_raw);
@@ -1078,47 +1079,51 @@ __global__ void __launch_bounds__(kTileThreads) k3_ztile(typename C2T<T>::type* 
   });
 }
 
+// the row widths a tile transform of 2^logn points is built for
+inline bool tile_rb_ok(int logn, int rb) {
+  return (rb == 128 && logn <= 9) || (rb == 64 && logn >= 8);
+}
+// the default row width: 128 bytes up to 512 points, 64 bytes for 1024
+inline int tile_rb_default(int logn) { return logn >= 10 ? 64 : 128; }
+
+template <typename T, int L, int RB>
+void tile_attributes_one() {
+  const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  constexpr int PW = tile_cols<T, RB>();
+  cudaFuncSetAttribute(k3_ytile<T, L, false, RB>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
+  cudaFuncSetAttribute(k3_ytile<T, L, true, RB>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
+  cudaFuncSetAttribute(k3_ztile<T, L, RB>, att, (int)tile_smem_bytes<T>(1 << L, PW, true));
+}
 // maximum dynamic shared memory of the tile kernels for lengths 2^L .. 2^10
 template <typename T, int L>
 void tile_attributes() {
-  const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  constexpr int PW = tile_cols<T, L>();
-  cudaFuncSetAttribute(k3_ytile<T, L, false>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
-  cudaFuncSetAttribute(k3_ytile<T, L, true>, att, (int)tile_smem_bytes<T>(1 << L, PW, false));
-  cudaFuncSetAttribute(k3_ztile<T, L>, att, (int)tile_smem_bytes<T>(1 << L, PW, true));
+  if constexpr (L <= 9) tile_attributes_one<T, L, 128>();
+  if constexpr (L >= 8) tile_attributes_one<T, L, 64>();
   if constexpr (L < 10) tile_attributes<T, L + 1>();
 }
 
-template <typename T>
-int tile_cols_of(int logn) {
-  return (logn >= 10 ? 64 : 128) / (int)sizeof(typename C2T<T>::type);
-}
-
-#define IBPF_TILE_CASES IBPF_T(3) IBPF_T(4) IBPF_T(5) IBPF_T(6) IBPF_T(7) IBPF_T(8) IBPF_T(9) IBPF_T(10)
+#define IBPF_TILE_CASES IBPF_T(3, 128) IBPF_T(4, 128) IBPF_T(5, 128) IBPF_T(6, 128) IBPF_T(7, 128) \
+  IBPF_T(8, 128) IBPF_T(9, 128) IBPF_T(8, 64) IBPF_T(9, 64) IBPF_T(10, 64)
 
 template <typename T, bool INV>
-void launch_ytile(int logn, int blocks, size_t smem, cudaStream_t s,
+void launch_ytile(int logn, int rb, int blocks, size_t smem, cudaStream_t s,
                   typename C2T<T>::type* spec, int sp, int nbt,
                   const typename C2T<T>::type* tw, int* status) {
-  switch (logn) {
-#define IBPF_T(L) case L: k3_ytile<T, L, INV><<<blocks, kTileThreads, smem, s>>>(spec, sp, nbt, tw, status); break;
-    IBPF_TILE_CASES
+#define IBPF_T(L, RB) \
+  if (logn == L && rb == RB) k3_ytile<T, L, INV, RB><<<blocks, kTileThreads, smem, s>>>(spec, sp, nbt, tw, status);
+  IBPF_TILE_CASES
 #undef IBPF_T
-    default: break;
-  }
 }
 
 template <typename T>
-void launch_ztile(int logn, int blocks, size_t smem, cudaStream_t s,
+void launch_ztile(int logn, int rb, int blocks, size_t smem, cudaStream_t s,
                   typename C2T<T>::type* spec, int ncols, int sp, int nh1,
                   const typename C2T<T>::type* tw, const typename C2T<T>::type* wd,
                   const SymbolArgs& sym, int* status) {
-  switch (logn) {
-#define IBPF_T(L) case L: k3_ztile<T, L><<<blocks, kTileThreads, smem, s>>>(spec, ncols, sp, nh1, tw, wd, sym, status); break;
-    IBPF_TILE_CASES
+#define IBPF_T(L, RB) \
+  if (logn == L && rb == RB) k3_ztile<T, L, RB><<<blocks, kTileThreads, smem, s>>>(spec, ncols, sp, nh1, tw, wd, sym, status);
+  IBPF_TILE_CASES
 #undef IBPF_T
-    default: break;
-  }
 }
 
 template <typename T>
@@ -1277,31 +1282,26 @@ cudaError_t tables3_t(Instance& in) {
   return cudaGetLastError();
 }
 
-// One 3D solve: x rows, y columns, z cosine transform + symbol + inverse, y inverse, x rows
-// inverse with the epilogue of the batched 2D solve (mode 0: C increment into the C^{n-1}
-// slot, compensated in FP32; mode 1: P^{n+1} = P^ + dP).
+// row width of the instance's y / z tiles: the tuned one if set, else the default
+inline int y_rb(const Instance& in) { return in.tune_y_rb ? in.tune_y_rb : tile_rb_default(in.logny); }
+inline int z_rb(const Instance& in) { return in.tune_z_rb ? in.tune_z_rb : tile_rb_default(in.lognz); }
+
+// the y transforms of a 3D spectrum (forward or inverse) with rb-byte tile rows
 template <typename T>
-int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Recorder* rec) {
+void ytile3(const Instance& in, bool inv, int rb, cudaStream_t s) {
   using C2 = typename C2T<T>::type;
-  constexpr int S = kFftSmallThreads;
-  const int nx = in.nx, ny = in.ny, nz = in.nz, nh1 = nx / 2 + 1, sp = spec3_pitch(nx);
-  const int rows = ny * nz;
-  const int rp = fft_per_block(nx);
-  C2* spec = (C2*)in.spec;
-  // the row kernels take at most 26 KiB of shared memory; the tile kernels up to 88 KiB,
-  // allowed by the attributes set with the tables
-  const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
-  const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
-  k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, sp, (const C2*)in.twx);
-  if (rec) rec->mark("rows_fwd", s);
-  int logny = 0, lognz = 0;
-  while ((1 << logny) < ny) ++logny;
-  while ((1 << lognz) < nz) ++lognz;
-  const int pwy = tile_cols_of<T>(logny), pwz = tile_cols_of<T>(lognz);
-  const int nbt = (sp + pwy - 1) / pwy;
-  const size_t ysm = tile_smem_bytes<T>(ny, pwy, false);
-  launch_ytile<T, false>(logny, nz * nbt, ysm, s, spec, sp, nbt, (const C2*)in.twy, in.status);
-  if (rec) rec->mark("y_fft", s);
+  const int sp = spec3_pitch(in.nx);
+  const int pw = rb / (int)sizeof(C2), nbt = (sp + pw - 1) / pw;
+  const size_t sm = tile_smem_bytes<T>(in.ny, pw, false);
+  if (inv) launch_ytile<T, true>(in.logny, rb, in.nz * nbt, sm, s, (C2*)in.spec, sp, nbt, (const C2*)in.twy, in.status);
+  else launch_ytile<T, false>(in.logny, rb, in.nz * nbt, sm, s, (C2*)in.spec, sp, nbt, (const C2*)in.twy, in.status);
+}
+
+// the z solve of a 3D spectrum (mode 0: CH symbol, 1: Poisson) with rb-byte tile rows
+template <typename T>
+void ztile3(const Instance& in, int mode, int rb, cudaStream_t s) {
+  using C2 = typename C2T<T>::type;
+  const int nh1 = in.nx / 2 + 1, sp = spec3_pitch(in.nx);
   SymbolArgs sym;
   sym.mode = mode;
   sym.s_eta2 = in.prm.S / (in.prm.Cn * in.prm.Cn);
@@ -1315,11 +1315,33 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   sym.ncx = nh1;
   sym.lamyp = in.lamy;
   sym.lamyp_f = in.lamy_f;
-  const int ncols = ny * sp;
-  launch_ztile<T>(lognz, (ncols + pwz - 1) / pwz, tile_smem_bytes<T>(nz, pwz, true), s, spec,
-                  ncols, sp, nh1, (const C2*)in.twz, (const C2*)in.wdct, sym, in.status);
+  const int ncols = in.ny * sp, pw = rb / (int)sizeof(C2);
+  launch_ztile<T>(in.lognz, rb, (ncols + pw - 1) / pw, tile_smem_bytes<T>(in.nz, pw, true), s,
+                  (C2*)in.spec, ncols, sp, nh1, (const C2*)in.twz, (const C2*)in.wdct, sym, in.status);
+}
+
+// One 3D solve: x rows, y columns, z cosine transform + symbol + inverse, y inverse, x rows
+// inverse with the epilogue of the batched 2D solve (mode 0: C increment into the C^{n-1}
+// slot, compensated in FP32; mode 1: P^{n+1} = P^ + dP).
+template <typename T>
+int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Recorder* rec) {
+  using C2 = typename C2T<T>::type;
+  constexpr int S = kFftSmallThreads;
+  const int nx = in.nx, ny = in.ny, nz = in.nz, sp = spec3_pitch(nx);
+  const int rows = ny * nz;
+  const int rp = fft_per_block(nx);
+  C2* spec = (C2*)in.spec;
+  // the row kernels take at most 26 KiB of shared memory; the tile kernels up to 88 KiB,
+  // allowed by the attributes set with the tables
+  const size_t rsm = sizeof(C2) * (fft_buf(8 * S) + nx / 2);
+  const T* src = (const T*)(mode == 0 ? in.Q : in.rhs);
+  k_rows_fwd<T><<<(rows / 2 + rp - 1) / rp, S, rsm, s>>>(src, spec, nx, rows, sp, (const C2*)in.twx);
+  if (rec) rec->mark("rows_fwd", s);
+  ytile3<T>(in, false, y_rb(in), s);
+  if (rec) rec->mark("y_fft", s);
+  ztile3<T>(in, mode, z_rb(in), s);
   if (rec) rec->mark("z_solve", s);
-  launch_ytile<T, true>(logny, nz * nbt, ysm, s, spec, sp, nbt, (const C2*)in.twy, in.status);
+  ytile3<T>(in, true, y_rb(in), s);
   if (rec) rec->mark("y_ifft", s);
   EpiArgs epi;
   T* out;
@@ -1435,6 +1457,38 @@ int spectral_solve_ptrs(int nx, int ny, const double* rhs, double* out, int mode
 
 cudaError_t spectral3_tables(Instance& in, int precision) {
   return precision == IB_PF_FP64 ? tables3_t<double>(in) : tables3_t<float>(in);
+}
+
+// Tuner: the mean time (ms) of `reps` launches of the y transforms (axis 1: forward and
+// inverse, halved) or of the z solve (axis 2, Poisson symbol) with rb-byte tile rows, run on
+// the instance's spectral scratch (whose content every solve overwrites).  -1: rb is not
+// built for that length.
+float spectral3_time_tiles(const Instance& in, int precision, int axis, int rb, int reps,
+                           cudaStream_t s) {
+  const int logn = axis == 1 ? in.logny : in.lognz;
+  if (!tile_rb_ok(logn, rb)) return -1.0f;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto once = [&]() {
+    if (precision == IB_PF_FP64) {
+      if (axis == 1) { ytile3<double>(in, false, rb, s); ytile3<double>(in, true, rb, s); }
+      else ztile3<double>(in, 1, rb, s);
+    } else {
+      if (axis == 1) { ytile3<float>(in, false, rb, s); ytile3<float>(in, true, rb, s); }
+      else ztile3<float>(in, 1, rb, s);
+    }
+  };
+  once();   // warm-up
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) once();
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / (float)reps / (axis == 1 ? 2.0f : 1.0f);
 }
 
 int spectral3_solve(const Instance& in, int precision, int mode, int cur, cudaStream_t s,

@@ -48,6 +48,7 @@ struct S3 {
   unsigned* ticket;
   double* mass;
   int* status;
+  int pred_kz;   // planes per predictor block (a power of two, at most nz)
 };
 
 
@@ -646,7 +647,7 @@ __global__ void __launch_bounds__(kPx * kPy) k3_predict(S3<T> a) {
   __shared__ T sF[2][kPhy][kPhx];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
   const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
-  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int kz = a.pred_kz;
   const int k0 = blockIdx.z * kz;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < a.nx && j < a.ny;
@@ -816,7 +817,7 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
   constexpr int NS = (kSlots + kThreads - 1) / kThreads;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
   const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
-  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int kz = a.pred_kz;
   const int k0 = blockIdx.z * kz;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < a.nx && j < a.ny;
@@ -1038,7 +1039,7 @@ __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
   constexpr int NS = (kSlots + kThreads - 1) / kThreads;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
   const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
-  const int kz = a.nz < kPz ? a.nz : kPz;
+  const int kz = a.pred_kz;
   const int k0 = blockIdx.z * kz;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < a.nx && j < a.ny;
@@ -1585,6 +1586,10 @@ S3<T> make3(const Instance& in, int cur) {
   a.nx = in.nx;
   a.ny = in.ny;
   a.nz = in.nz;
+  {
+    const int planes = in.tune_pred_planes ? in.tune_pred_planes : kPz;
+    a.pred_kz = in.nz < planes ? in.nz : planes;
+  }
   a.lnx = in.lognx;
   a.lny = in.logny;
   a.inv_h = (T)(1.0 / in.h);
@@ -1672,7 +1677,7 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
     const S3<T> a = make3<T>(in, cur);
     const int ng = in.tab.ng, nf = in.tab.nfu + in.tab.nfv + in.tab.nfw;
     const unsigned gblk = (unsigned)(((size_t)ng * kGhostLanes + kGhostBlock - 1) / kGhostBlock);
-    const int kzp = in.nz < kPz ? in.nz : kPz, kzc = in.nz < kCz ? in.nz : kCz;
+    const int kzp = a.pred_kz, kzc = in.nz < kCz ? in.nz : kCz;
     const dim3 zb(kPx, kPy);
     const dim3 zg((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzc);
     const dim3 zgp((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / kzp);
@@ -1746,7 +1751,63 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
   return launches;
 }
 
+// one launch of the 3D predictor of instance `in` with the state slot cur, writing the
+// predicted velocities to us, vs, ws
+template <typename T>
+void predict3(const Instance& in, int cur, cudaStream_t s, void* us, void* vs, void* ws) {
+  S3<T> a = make3<T>(in, cur);
+  a.Us = (T*)us;
+  a.Vs = (T*)vs;
+  a.Ws = (T*)ws;
+  const dim3 zb(kPx, kPy);
+  const dim3 zgp((in.nx + kPx - 1) / kPx, (in.ny + kPy - 1) / kPy, in.nz / a.pred_kz);
+  if constexpr (sizeof(T) == 4) k3_predict_a<T><<<zgp, zb, 0, s>>>(a);
+  else k3_predict_s<T><<<zgp, zb, k3_pred_smem<T>(), s>>>(a);
+}
+
 }  // namespace
+
+// Tuner: the mean time (ms) of `reps` launches of the 3D predictor of instance `in` with
+// `planes` planes per block (the instance's choice is restored afterwards).  The predictor
+// overwrites the AB2 history Hu, Hv, Hw, which is copied aside before and back after; its
+// predicted velocities go to scratch (in a step they take the level n-1 slots, which hold
+// state between steps).  -1 on a CUDA error (nothing changed).
+float step3d_time_predict(const Ctx& c, Instance& in, int planes, int reps, cudaStream_t s) {
+  const size_t es = c.precision == IB_PF_FP64 ? 8 : 4;
+  const size_t cells = (size_t)in.nx * in.ny * in.nz, nxy = (size_t)in.nx * in.ny;
+  const size_t bu = cells * es, bw = (cells + nxy) * es;
+  void* save = nullptr;
+  if (cudaMalloc(&save, 2 * (2 * bu + bw)) != cudaSuccess) return -1.0f;
+  char* sv = (char*)save;
+  cudaMemcpyAsync(sv, in.Hu, bu, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(sv + bu, in.Hv, bu, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(sv + 2 * bu, in.Hw, bw, cudaMemcpyDeviceToDevice, s);
+  const int keep = in.tune_pred_planes;
+  in.tune_pred_planes = planes;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto once = [&]() {
+    char* out = sv + (2 * bu + bw);
+    if (c.precision == IB_PF_FP64) predict3<double>(in, c.cur, s, out, out + bu, out + 2 * bu);
+    else predict3<float>(in, c.cur, s, out, out + bu, out + 2 * bu);
+  };
+  once();   // warm-up
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) once();
+  cudaEventRecord(e1, s);
+  cudaMemcpyAsync(in.Hu, sv, bu, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(in.Hv, sv + bu, bu, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(in.Hw, sv + 2 * bu, bw, cudaMemcpyDeviceToDevice, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(save);
+  in.tune_pred_planes = keep;
+  return e == cudaSuccess ? ms / (float)reps : -1.0f;
+}
 
 int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec) {
   return c.precision == IB_PF_FP64 ? step3d_t<double>(c, cur, s, rec)

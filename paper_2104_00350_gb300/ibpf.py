@@ -58,6 +58,16 @@ class Params(ct.Structure):
                                                          ("weights", ct.c_int), ("ns_scheme", ct.c_int)]
 
 
+class Tuning(ct.Structure):
+    _fields_ = [("y_tile_bytes", ct.c_int), ("z_tile_bytes", ct.c_int), ("predict_planes", ct.c_int)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+TUNING_CANDIDATES = ("y128", "y64", "z128", "z64", "planes8", "planes16", "planes32")
+
+
 class IbPfError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"ib_pf status {status}: {msg}")
@@ -88,6 +98,9 @@ def _load():
                                    ct.POINTER(i)]),
         "ib_pf_poisson_solve_noalloc": (i, [vp, vp, i, i, ct.c_double, vp]),
         "ib_pf_bind_fields": (i, [vp, i, i, i, vp, ct.c_longlong]),
+        "ib_pf_set_tuning": (i, [vp, i, ct.POINTER(Tuning)]),
+        "ib_pf_get_tuning": (i, [vp, i, ct.POINTER(Tuning)]),
+        "ib_pf_autotune": (i, [vp, i, i, ct.POINTER(Tuning), ct.POINTER(ct.c_double)]),
         "ib_pf_last_error": (ct.c_char_p, [vp]),
         "ib_pf_destroy": (None, [vp]),
     }
@@ -204,6 +217,23 @@ def ib_pf_bind_fields(ctx, instance: int, field_id: int, time_level: int, device
                                    nbytes), ctx)
 
 
+def ib_pf_set_tuning(ctx, instance: int, tuning: Tuning):
+    _check(lib().ib_pf_set_tuning(ctx, instance, ct.byref(tuning)), ctx)
+
+
+def ib_pf_get_tuning(ctx, instance: int) -> Tuning:
+    t = Tuning()
+    _check(lib().ib_pf_get_tuning(ctx, instance, ct.byref(t)), ctx)
+    return t
+
+
+def ib_pf_autotune(ctx, instance: int, reps: int):
+    t = Tuning()
+    ms = (ct.c_double * len(TUNING_CANDIDATES))()
+    _check(lib().ib_pf_autotune(ctx, instance, reps, ct.byref(t), ms), ctx)
+    return t, dict(zip(TUNING_CANDIDATES, list(ms)))
+
+
 def ib_pf_poisson_solve_noalloc(rhs_ptr: int, out_ptr: int, nx: int, ny: int, h: float,
                                 stream: int = 0):
     _check(lib().ib_pf_poisson_solve_noalloc(ct.c_void_p(rhs_ptr), ct.c_void_p(out_ptr), nx, ny,
@@ -304,6 +334,41 @@ class Solver:
 
     def precompute_weights(self):
         ib_pf_precompute_weights(self.ctx)
+
+    def tuning(self, instance: int = 0) -> dict:
+        return ib_pf_get_tuning(self.ctx, instance).as_dict()
+
+    def set_tuning(self, instance: int = 0, **choice):
+        t = Tuning(**{k: int(choice.get(k, 0)) for k, _ in Tuning._fields_})
+        ib_pf_set_tuning(self.ctx, instance, t)
+
+    def autotune(self, instance: int = 0, reps: int = 3, cache: str | Path | None = None,
+                 gpu_name: str | None = None) -> dict:
+        """The 3D schedule of `instance`: taken from the JSON file `cache` when it holds an
+        entry for this grid shape, precision and GPU, else timed by ib_pf_autotune (state
+        unchanged) and written there.  Returns the choice, plus the candidates' times when
+        they were measured."""
+        import json
+        n = self.shapes[instance]
+        if gpu_name is None:
+            try:
+                import torch
+                gpu_name = torch.cuda.get_device_name()
+            except Exception:   # no torch / no device name: key without it
+                gpu_name = "unknown"
+        key = "x".join(str(v) for v in n[::-1]) + f":{'fp64' if self.precision == FP64 else 'fp32'}:{gpu_name}"
+        table = {}
+        if cache is not None and Path(cache).exists():
+            table = json.loads(Path(cache).read_text())
+        if key in table:
+            self.set_tuning(instance, **table[key]["choice"])
+            return {"key": key, "choice": table[key]["choice"], "cached": True}
+        t, ms = ib_pf_autotune(self.ctx, instance, reps)
+        entry = {"choice": t.as_dict(), "ms": ms}
+        if cache is not None:
+            table[key] = entry
+            Path(cache).write_text(json.dumps(table, indent=1, sort_keys=True))
+        return {"key": key, "cached": False, **entry}
 
     def step(self, nsteps: int = 1):
         ib_pf_step(self.ctx, nsteps)

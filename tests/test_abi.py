@@ -114,3 +114,11 @@ def test_ch_scheme_checked_on_host(lib):
     with pytest.raises(lib.IbPfError) as ei:
         lib.ib_pf_init_geometry(ga + gb, wa + wb, pa + pb)
     assert ei.value.status == lib.E_ARG
+
+
+def test_tuning_calls_reject_a_null_context(lib):
+    so = lib.lib()
+    t = lib.Tuning()
+    assert so.ib_pf_set_tuning(None, 0, ct.byref(t)) == lib.E_ARG
+    assert so.ib_pf_get_tuning(None, 0, ct.byref(t)) == lib.E_ARG
+    assert so.ib_pf_autotune(None, 0, 1, ct.byref(t), None) == lib.E_ARG
