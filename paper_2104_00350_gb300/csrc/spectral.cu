@@ -121,13 +121,27 @@ __device__ __forceinline__ void stockham_pass(C2* x, const C2* __restrict__ tw, 
       for (int r = 0; r < R; ++r) v[q][r] = x[xslot<N, P>(f, j + r * NR)];
       if constexpr (NS > 1) {
         const int k = j % NS;
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const int m = r * k * TSTEP;
+        auto tw_at = [&](int m) {   // W^m, m < N
           C2 w = tw[m & (HALF - 1)];
           if (m >= HALF) { w.x = -w.x; w.y = -w.y; }
           if (INV) w.y = -w.y;
-          v[q][r] = cmul(v[q][r], w);
+          return w;
+        };
+        if constexpr (R == 8) {
+          // W^k, W^2k, W^4k from the table, the other four by products (at most two
+          // roundings deep): a third of the table reads of a radix-8 butterfly
+          const C2 w1 = tw_at(k * TSTEP), w2 = tw_at(2 * k * TSTEP), w4 = tw_at(4 * k * TSTEP);
+          const C2 w3 = cmul(w1, w2);
+          v[q][1] = cmul(v[q][1], w1);
+          v[q][2] = cmul(v[q][2], w2);
+          v[q][3] = cmul(v[q][3], w3);
+          v[q][4] = cmul(v[q][4], w4);
+          v[q][5] = cmul(v[q][5], cmul(w1, w4));
+          v[q][6] = cmul(v[q][6], cmul(w2, w4));
+          v[q][7] = cmul(v[q][7], cmul(w3, w4));
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[q][r] = cmul(v[q][r], tw_at(r * k * TSTEP));
         }
       }
       dft_reg<R, INV, T>(v[q]);
