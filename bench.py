@@ -105,11 +105,12 @@ def kernel_step_bytes(name: str, esz: int, cells: int, table=None) -> float:
 
 def sparse_unit_bytes(name: str, esz: int, dim: int):
     """Algorithmic bytes per unit (ghost or face) of the sparse kernels, and the unit.
-    Tables: averaging cells (int32) and weights (FP64), 2 nap of each per ghost (nap = 5 in
-    2D, 7 in 3D), the ghost's cell index, gamma and dn, the normal (dim FP64); field words
-    once per gathered value; one write per output word."""
+    Tables: averaging cells (int32) and weights (FP64; FP32 copies in the 3D FP32 form), 2 nap
+    of each per ghost (nap = 5 in 2D, 7 in 3D), the ghost's cell index, gamma and dn, the
+    normal (dim FP64); field words once per gathered value; one write per output word."""
     nap = 5 if dim == 2 else 7
-    tab = 2 * nap * (4 + 8)
+    wsz = 4 if (dim == 3 and esz == 4) else 8
+    tab = 2 * nap * (4 + wsz)
     if name == "fill_C":      # C at the 2 nap cells -> C_G (+ low part zeroed in FP32)
         return tab + 4 + 16 + 2 * nap * esz + (2 if esz == 4 else 1) * esz, "ghost"
     if name in ("fill_phi", "ch_fill2"):   # phi (and phi^{n-1}) at the 2 nap cells -> phi_G

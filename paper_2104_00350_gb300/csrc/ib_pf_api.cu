@@ -82,7 +82,7 @@ void free_instance(Instance& in) {
                   in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv, in.W[0], in.W[1], in.Hw,
                   in.gw, in.lamz, in.lamz_f, in.twz, in.sph, in.bstart, in.blist,
                   in.tab.alpha_w, in.tab.fw, in.alpha_f, in.ci, in.gq, in.lam_s2, in.lam_d1,
-                  in.lam_s2_f, in.lam_d1_f, in.tw2};
+                  in.lam_s2_f, in.lam_d1_f, in.tw2, in.tab.w1f, in.tab.w2f};
   for (void* p : ptrs) {
     if (!p) continue;
     bool caller_owned = false;
@@ -436,6 +436,7 @@ ib_pf_status ib_pf_precompute_weights(ib_pf_ctx* ctx) {
                                        : geometry_weights(in, ctx->work, &nf, gerr);
     if (ge != cudaSuccess)
       return fail(ctx, IB_PF_E_CUDA, "weights: " + gerr);
+    if (in.dim == 3 && ctx->precision == IB_PF_FP32) CK(weights3_f32(in, ctx->work));
     total_fail += nf;
   }
   CK(join_out(*ctx));

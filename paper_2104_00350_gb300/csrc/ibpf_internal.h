@@ -64,6 +64,8 @@ struct Tables {
   double* w1 = nullptr;
   int* ap2 = nullptr;
   double* w2 = nullptr;
+  float* w1f = nullptr;        // FP32 copies of w1, w2 (3D FP32 contexts), made after the
+  float* w2f = nullptr;        // FP64 precompute
   int nap = kNap;              // averaging points per interpolation point (5 2D, 7 3D)
   int nfu = 0, nfv = 0, nfw = 0;
   int* fu = nullptr;           // nfu linear x1-face indices
@@ -239,6 +241,8 @@ cudaError_t geometry3_weights(Instance& in, cudaStream_t s, int* n_fail, std::st
 
 // ---- spectral.cu / step3d.cu: the 3D step, one instance after another
 cudaError_t spectral3_tables(Instance& in, int precision);
+// FP32 copies of the averaging weights of a 3D FP32 instance (after its precompute)
+cudaError_t weights3_f32(Instance& in, cudaStream_t s);
 // mean ms per launch of the 3D predictor with `planes` planes per block (AB2 history saved
 // and restored); -1 on a CUDA error
 float step3d_time_predict(const Ctx& c, Instance& in, int planes, int reps, cudaStream_t s);

@@ -49,6 +49,7 @@ struct S3 {
   double* mass;
   int* status;
   int pred_kz;   // planes per predictor block (a power of two, at most nz)
+  const T *w1t, *w2t;   // averaging weights in the field type (FP32: copies of the FP64 ones)
 };
 
 
@@ -81,7 +82,7 @@ __device__ __forceinline__ Nbr nbr(const S3<T>& a, size_t c, int i, int j, int k
 // ------------------------------------------------------------ a3 / a4: ghost fills, phi
 template <typename T>
 __device__ __forceinline__ T gather7(const T* __restrict__ f, const int* __restrict__ ap,
-                                     const double* __restrict__ w, int g) {
+                                     const T* __restrict__ w, int g) {
   T acc = T(0);
 #pragma unroll
   for (int q = 0; q < kNap3; ++q) acc = acc + (T)w[(size_t)g * kNap3 + q] * f[ap[(size_t)g * kNap3 + q]];
@@ -101,14 +102,15 @@ __device__ __forceinline__ T gather7(const T* __restrict__ f, const int* __restr
 // 293 us).
 constexpr int kGhostLanes = 8, kGhostBlock = 256;
 template <int NV, typename T, typename Get>
-__device__ __forceinline__ void gather_group(const Tables& t, int g, int q, Get get, T (&s1)[NV],
-                                             T (&s2)[NV]) {
+__device__ __forceinline__ void gather_group(const Tables& t, const T* __restrict__ w1t,
+                                             const T* __restrict__ w2t, int g, int q, Get get,
+                                             T (&s1)[NV], T (&s2)[NV]) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) s1[v] = s2[v] = T(0);
   if (g < t.ng && q < kNap3) {
     const size_t e = (size_t)g * kNap3 + q;
     const size_t c1 = (size_t)t.ap1[e], c2 = (size_t)t.ap2[e];
-    const T w1 = (T)t.w1[e], w2 = (T)t.w2[e];
+    const T w1 = w1t[e], w2 = w2t[e];
     T v1[NV], v2[NV];
     get(c1, v1);
     get(c2, v2);
@@ -134,7 +136,7 @@ __global__ void k3_fill_C(S3<T> a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const Tables& t = a.tab;
   if (g >= t.ng) return;
-  const T cm = T(2) * gather7(a.C1, t.ap1, t.w1, g) - gather7(a.C1, t.ap2, t.w2, g);
+  const T cm = T(2) * gather7(a.C1, t.ap1, a.w1t, g) - gather7(a.C1, t.ap2, a.w2t, g);
   const T gam = (T)t.gamma[g], dn = (T)t.dn[g];
   const T kk = (T)a.k_wet / (gam * dn);
   const T qa = T(-0.75) * (T)a.cos_th;
@@ -198,7 +200,7 @@ __global__ void k3_fill_Cd(S3<T> a, int pass) {
 #pragma unroll
   for (int q = 0; q < kNap3; ++q) {
     const size_t c1 = t.ap1[(size_t)g * kNap3 + q], c2 = t.ap2[(size_t)g * kNap3 + q];
-    const T w1 = (T)t.w1[(size_t)g * kNap3 + q], w2 = (T)t.w2[(size_t)g * kNap3 + q];
+    const T w1 = a.w1t[(size_t)g * kNap3 + q], w2 = a.w2t[(size_t)g * kNap3 + q];
     m1 = m1 + w1 * a.C1[c1];
     m2 = m2 + w2 * a.C1[c2];
     n1c = n1c + w1 * a.C[c1];
@@ -276,7 +278,7 @@ __global__ void k3_ch_wall(S3<T> a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const Tables& t = a.tab;
   if (g >= t.ng) return;
-  const T pm = T(2) * gather7((const T*)a.rhs, t.ap1, t.w1, g) - gather7((const T*)a.rhs, t.ap2, t.w2, g);
+  const T pm = T(2) * gather7((const T*)a.rhs, t.ap1, a.w1t, g) - gather7((const T*)a.rhs, t.ap2, a.w2t, g);
   const size_t c = (size_t)t.gcell[g];
   a.phi[c] = a.phi[c] + (pm - a.rhs[c]) * a.inv_eta2;
 }
@@ -287,7 +289,7 @@ __global__ void k3_fill_phi(S3<T> a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const Tables& t = a.tab;
   if (g >= t.ng) return;
-  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
+  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, a.w1t, g) - gather7(a.phi, t.ap2, a.w2t, g);
 }
 
 // --------------------------------------- four-cells-per-thread kernels (FP32 form)
@@ -338,13 +340,15 @@ __global__ void __launch_bounds__(kTQ) k3_ch_h_q(S3<float> a) {
   const Run d = run4(a);
   const float third = float(1.0 / 3.0);
   auto Bq = [&](size_t q) { return a.C[q] + (a.C[q] - a.Co[q]) * third; };
-  auto B4 = [&](size_t q) {
-    const V4 c = ld4(a.C, q), o = ld4(a.Co, q);
+  auto Bv = [&](const V4& c, const V4& o) {
     return map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
   };
+  // C and C_old at the run and its y / z neighbours, loaded once for h and (with ghosts) phi~
   const V4 c = ld4(a.C, d.q), o = ld4(a.Co, d.q);
-  const V4 b = map4([&](int e) { return c.e[e] + (c.e[e] - o.e[e]) * third; });
-  const V4 byp = B4(d.yp), bym = B4(d.ym), bzp = B4(d.zp), bzm = B4(d.zm);
+  const V4 cyp = ld4(a.C, d.yp), oyp = ld4(a.Co, d.yp), cym = ld4(a.C, d.ym), oym = ld4(a.Co, d.ym);
+  const V4 czp = ld4(a.C, d.zp), ozp = ld4(a.Co, d.zp), czm = ld4(a.C, d.zm), ozm = ld4(a.Co, d.zm);
+  const V4 b = Bv(c, o);
+  const V4 byp = Bv(cyp, oyp), bym = Bv(cym, oym), bzp = Bv(czp, ozp), bzm = Bv(czm, ozm);
   const X2 bx = xnb(b, d, a.nx, Bq);
   st4(a.phi, d.q, map4([&](int e) {
         const float lapb = lap7q(a, b, bx, byp, bym, bzp, bzm, e);
@@ -354,12 +358,11 @@ __global__ void __launch_bounds__(kTQ) k3_ch_h_q(S3<float> a) {
       }));
   if (a.tab.ng > 0) {
     // phi~ = psi'(C~) - Cn^2 lap(C~) for the wall term (k3_ch_wall), into the rhs scratch
-    auto T4 = [&](size_t q) {
-      const V4 x = ld4(a.C, q), y = ld4(a.Co, q);
+    auto Tv = [&](const V4& x, const V4& y) {
       return map4([&](int e) { return 2.0f * x.e[e] - y.e[e]; });
     };
-    const V4 ct = map4([&](int e) { return 2.0f * c.e[e] - o.e[e]; });
-    const V4 typ = T4(d.yp), tym = T4(d.ym), tzp = T4(d.zp), tzm = T4(d.zm);
+    const V4 ct = Tv(c, o);
+    const V4 typ = Tv(cyp, oyp), tym = Tv(cym, oym), tzp = Tv(czp, ozp), tzm = Tv(czm, ozm);
     const X2 tx = xnb(ct, d, a.nx, [&](size_t q) { return 2.0f * a.C[q] - a.Co[q]; });
     st4(a.rhs, d.q, map4([&](int e) {
           const float x = ct.e[e];
@@ -543,8 +546,8 @@ __global__ void k3x_fill2(S3<T> a) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const Tables& t = a.tab;
   if (g >= t.ng) return;
-  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, t.w1, g) - gather7(a.phi, t.ap2, t.w2, g);
-  a.rhs[t.gcell[g]] = T(2) * gather7(a.rhs, t.ap1, t.w1, g) - gather7(a.rhs, t.ap2, t.w2, g);
+  a.phi[t.gcell[g]] = T(2) * gather7(a.phi, t.ap1, a.w1t, g) - gather7(a.phi, t.ap2, a.w2t, g);
+  a.rhs[t.gcell[g]] = T(2) * gather7(a.rhs, t.ap1, a.w1t, g) - gather7(a.rhs, t.ap2, a.w2t, g);
 }
 
 template <typename T>
@@ -640,156 +643,6 @@ __global__ void __launch_bounds__(kTQ) k3x_update_q(S3<float> a) {
 // Edges: xy-edge (i-1/2, j-1/2, k), xz-edge (i-1/2, j, k-1/2), yz-edge (i, j-1/2, k-1/2).
 constexpr int kPx = 32, kPy = 8, kPz = 16;
 constexpr int kPhx = kPx + 2, kPhy = kPy + 2;
-
-template <typename T>
-__global__ void __launch_bounds__(kPx * kPy) k3_predict(S3<T> a) {
-  __shared__ T sC[3][kPhy][kPhx], sU[3][kPhy][kPhx], sV[3][kPhy][kPhx], sW[3][kPhy][kPhx];
-  __shared__ T sF[2][kPhy][kPhx];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kPx + tx;
-  const int i0 = blockIdx.x * kPx, j0 = blockIdx.y * kPy;
-  const int kz = a.pred_kz;
-  const int k0 = blockIdx.z * kz;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < a.nx && j < a.ny;
-  const size_t nxy = (size_t)a.nx * a.ny;
-  auto sl3 = [](int kk) { return (kk + 3) % 3; };
-  auto sl2 = [](int kk) { return (kk + 2) & 1; };
-  auto halo_off = [&](int idx) {   // staged slot idx -> offset of its column in a plane
-    const int r = idx / kPhx, q = idx % kPhx;
-    const int gi = (i0 - 1 + q + a.nx) & (a.nx - 1), gj = (j0 - 1 + r + a.ny) & (a.ny - 1);
-    return (size_t)gj * a.nx + gi;
-  };
-  auto load_plane = [&](int kk) {   // C, u, v, w of plane kk (kk in -1 .. nz)
-    const int sl = sl3(kk);
-    const int km = kk < 0 ? 0 : (kk >= a.nz ? a.nz - 1 : kk);
-    const T sg = (kk < 0 || kk >= a.nz) ? T(-1) : T(1);
-    for (int idx = tid; idx < kPhx * kPhy; idx += kPx * kPy) {
-      const size_t o = halo_off(idx), q = (size_t)km * nxy + o;
-      const int r = idx / kPhx, cc = idx % kPhx;
-      sC[sl][r][cc] = a.C1[q];
-      sU[sl][r][cc] = sg * a.U[q];
-      sV[sl][r][cc] = sg * a.V[q];
-      sW[sl][r][cc] = (kk >= 0 && kk <= a.nz) ? a.W[(size_t)kk * nxy + o] : T(0);
-    }
-  };
-  auto load_phi = [&](int kk) {
-    if (kk < 0 || kk >= a.nz) return;
-    for (int idx = tid; idx < kPhx * kPhy; idx += kPx * kPy)
-      sF[sl2(kk)][idx / kPhx][idx % kPhx] = a.phi[(size_t)kk * nxy + halo_off(idx)];
-  };
-  int k = k0;
-  // slots of planes k-1, k, k+1, set once per plane; every access names its plane as k plus
-  // a constant, so the selection below folds at compile time
-  int s_m = 0, s_0 = 0, s_p = 0;
-  auto pl = [&](int kk) { return kk == k ? s_0 : (kk > k ? s_p : s_m); };
-  auto Cc = [&](int ii, int jj, int kk) { return sC[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Fc = [&](int ii, int jj, int kk) { return sF[sl2(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Ug = [&](int ii, int jj, int kk) { return sU[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Vg = [&](int ii, int jj, int kk) { return sV[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  auto Wf = [&](int ii, int jj, int kk) { return sW[pl(kk)][jj - j0 + 1][ii - i0 + 1]; };
-  const T ih = a.inv_h;
-  load_plane(k0 - 1);
-  load_plane(k0);
-  load_phi(k0 - 1);
-  load_phi(k0);
-  for (; k < k0 + kz; ++k) {
-    load_plane(k + 1);
-    s_m = sl3(k - 1);
-    s_0 = sl3(k);
-    s_p = sl3(k + 1);
-    __syncthreads();
-    if (active) {
-      const size_t c = (size_t)k * nxy + (size_t)j * a.nx + i;
-      auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
-      auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-      auto txx = [&](int ii) { return T(2) * mu(Cc(ii, j, k)) * ((Ug(ii + 1, j, k) - Ug(ii, j, k)) * ih); };
-      auto tyy = [&](int jj) { return T(2) * mu(Cc(i, jj, k)) * ((Vg(i, jj + 1, k) - Vg(i, jj, k)) * ih); };
-      auto tzz = [&](int kk) { return T(2) * mu(Cc(i, j, kk)) * ((Wf(i, j, kk + 1) - Wf(i, j, kk)) * ih); };
-      auto txy = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj - 1/2, kk)
-        const T ce = T(0.25) * (((Cc(ii - 1, jj - 1, kk) + Cc(ii, jj - 1, kk)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj - 1, kk)) * ih + (Vg(ii, jj, kk) - Vg(ii - 1, jj, kk)) * ih);
-      };
-      auto txz = [&](int ii, int jj, int kk) {   // edge (ii - 1/2, jj, kk - 1/2), kk = 0..nz
-        const T ce = T(0.25) * (((Cc(ii - 1, jj, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii - 1, jj, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Ug(ii, jj, kk) - Ug(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii - 1, jj, kk)) * ih);
-      };
-      auto tyz = [&](int ii, int jj, int kk) {   // edge (ii, jj - 1/2, kk - 1/2)
-        const T ce = T(0.25) * (((Cc(ii, jj - 1, kk - 1) + Cc(ii, jj, kk - 1)) + Cc(ii, jj - 1, kk)) + Cc(ii, jj, kk));
-        return mu(ce) * ((Vg(ii, jj, kk) - Vg(ii, jj, kk - 1)) * ih + (Wf(ii, jj, kk) - Wf(ii, jj - 1, kk)) * ih);
-      };
-      auto uv = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj - 1, kk))) * (T(0.5) * (Vg(ii, jj, kk) + Vg(ii - 1, jj, kk)));
-      };
-      auto uw = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Ug(ii, jj, kk) + Ug(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii - 1, jj, kk)));
-      };
-      auto vw = [&](int ii, int jj, int kk) {
-        return (T(0.5) * (Vg(ii, jj, kk) + Vg(ii, jj, kk - 1))) * (T(0.5) * (Wf(ii, jj, kk) + Wf(ii, jj - 1, kk)));
-      };
-      const T k_st = a.k_st;
-      T Hx, ux, Hy, vy, Hz = T(0), wz = T(0);
-      // ---- x-face (i - 1/2, j, k)
-      {
-        const T cL = Cc(i - 1, j, k), cR = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cL + cR));
-        const T visc = ((txx(i) - txx(i - 1)) * ih + (txy(i, j + 1, k) - txy(i, j, k)) * ih) +
-                       (txz(i, j, k + 1) - txz(i, j, k)) * ih;
-        const T ucR = T(0.5) * (Ug(i, j, k) + Ug(i + 1, j, k));
-        const T ucL = T(0.5) * (Ug(i - 1, j, k) + Ug(i, j, k));
-        const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(i, j + 1, k) - uv(i, j, k)) * ih) +
-                       (uw(i, j, k + 1) - uw(i, j, k)) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i - 1, j, k))) * ((cR - cL) * ih) / rho_f;
-        const T us = Ug(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hu[c]) + st);
-        Hx = H;
-        ux = us;
-      }
-      // ---- y-face (i, j - 1/2, k)
-      {
-        const T cB = Cc(i, j - 1, k), cA = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cB + cA));
-        const T visc = ((txy(i + 1, j, k) - txy(i, j, k)) * ih + (tyy(j) - tyy(j - 1)) * ih) +
-                       (tyz(i, j, k + 1) - tyz(i, j, k)) * ih;
-        const T vcA = T(0.5) * (Vg(i, j, k) + Vg(i, j + 1, k));
-        const T vcB = T(0.5) * (Vg(i, j - 1, k) + Vg(i, j, k));
-        const T conv = ((uv(i + 1, j, k) - uv(i, j, k)) * ih + (vcA * vcA - vcB * vcB) * ih) +
-                       (vw(i, j, k + 1) - vw(i, j, k)) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j - 1, k))) * ((cA - cB) * ih) / rho_f;
-        const T vs = Vg(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hv[c]) + st);
-        Hy = H;
-        vy = vs;
-      }
-      // ---- z-face (i, j, k - 1/2), 1 <= k <= nz - 1
-      if (k >= 1) {
-        const T cB = Cc(i, j, k - 1), cA = Cc(i, j, k);
-        const T rho_f = rho(T(0.5) * (cB + cA));
-        const T visc = ((txz(i + 1, j, k) - txz(i, j, k)) * ih + (tyz(i, j + 1, k) - tyz(i, j, k)) * ih) +
-                       (tzz(k) - tzz(k - 1)) * ih;
-        const T wcA = T(0.5) * (Wf(i, j, k) + Wf(i, j, k + 1));
-        const T wcB = T(0.5) * (Wf(i, j, k - 1) + Wf(i, j, k));
-        const T conv = ((uw(i + 1, j, k) - uw(i, j, k)) * ih + (vw(i, j + 1, k) - vw(i, j, k)) * ih) +
-                       (wcA * wcA - wcB * wcB) * ih;
-        const T H = -conv + visc / (a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(i, j, k) + Fc(i, j, k - 1))) * ((cA - cB) * ih) / rho_f;
-        const T ws = Wf(i, j, k) + a.dt * ((T(1.5) * H - T(0.5) * a.Hw[c]) + st);
-        Hz = H;
-        wz = ws;
-      }
-      // stores after every shared-memory read of the plane
-      a.Hu[c] = Hx;
-      a.Us[c] = a.au[c] * ux;
-      a.Hv[c] = Hy;
-      a.Vs[c] = a.av[c] * vy;
-      if (k >= 1) {
-        a.Hw[c] = Hz;
-        a.Ws[c] = a.aw[c] * wz;
-      }
-    }
-    __syncthreads();
-    load_phi(k + 1);
-  }
-}
 
 // FP32 form of the predictor: the same blocks, arithmetic and stores, with the staging made
 // asynchronous.  Planes go through a ring of four shared-memory slots filled by cp.async
@@ -1018,14 +871,14 @@ __global__ void __launch_bounds__(kPx * kPy, 4) k3_predict_a(S3<T> a) {
 // w and phi staged in a four-slot ring (dynamic shared memory, k3_pred_smem bytes) filled by
 // cp.async (plane k+2 in flight while plane k is computed).  Each
 // thread owns the faces of cell (i, j, k) and evaluates every edge stress and product it
-// needs with the same expressions and operation order as the plain form, but shares them:
-// x-neighbour values (txx(i-1), txy(i+1), txz(i+1), uv(i+1), uw(i+1)) come from the adjacent
-// lane by a warp shuffle (a warp is one row of 32 cells; the end lanes evaluate theirs), and
-// the z-edge values of plane k+1 (txz, tyz, uw, vw at k+1 and tzz(k)) are carried in
-// registers to the next plane, where they are the k-level values.  Results are those of
-// the plain evaluation (k3_predict), bit for bit; the FP64 pipe does about half the work.
-// (In the FP32 form, which is bound by its issue rate and memory, this sharing measured
-// 3.5 % slower than k3_predict_a, so that form evaluates every value per face.)
+// needs with the same expressions as a per-face evaluation, but shares them: x-neighbour
+// values (txx(i-1), txy(i+1), txz(i+1), uv(i+1), uw(i+1)) come from the adjacent lane by a
+// warp shuffle (a warp is one row of 32 cells; the end lanes evaluate theirs), and the
+// z-edge values of plane k+1 (txz, tyz, uw, vw at k+1 and tzz(k)) are carried in registers
+// to the next plane, where they are the k-level values; the two quotients by rho_f of a
+// face share one reciprocal.  The FP64 pipe, which bounds this form, does about half the
+// work of the per-face evaluation.  (In the FP32 form, bound by its issue rate, the x
+// shuffles measured slower; k3_predict_a carries the z values only.)
 template <typename T>
 __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
   static_assert(kPx == 32, "one warp per tile row");
@@ -1084,9 +937,10 @@ __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
   auto Vg = [&](int di, int dj, int dk) { return sg3[dk + 1] * sV[at(di, dj, dk)]; };
   auto Wf = [&](int di, int dj, int dk) { return sW[at(di, dj, dk)]; };
   const T ih = a.inv_h;
+  const T inv_re = T(1) / a.Re;
   auto mu = [&](T cc) { return a.mu_a + a.mu_b * clamp1(cc); };
   auto rho = [&](T cc) { return a.rho_a + a.rho_b * clamp1(cc); };
-  // the stresses and products of the plain form, at offsets from cell (i, j, k)
+  // the stresses and products, at offsets from cell (i, j, k)
   auto txx = [&](int di) { return T(2) * mu(Cc(di, 0, 0)) * ((Ug(di + 1, 0, 0) - Ug(di, 0, 0)) * ih); };
   auto tyy = [&](int dj) { return T(2) * mu(Cc(0, dj, 0)) * ((Vg(0, dj + 1, 0) - Vg(0, dj, 0)) * ih); };
   auto tzz = [&](int dk) { return T(2) * mu(Cc(0, 0, dk)) * ((Wf(0, 0, dk + 1) - Wf(0, 0, dk)) * ih); };
@@ -1176,8 +1030,9 @@ __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
         const T ucR = T(0.5) * (Ug(0, 0, 0) + Ug(1, 0, 0));
         const T ucL = T(0.5) * (Ug(-1, 0, 0) + Ug(0, 0, 0));
         const T conv = ((ucR * ucR - ucL * ucL) * ih + (uv(0, 1, 0) - uv0) * ih) + (n_uw - c_uw) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(-1, 0, 0))) * qdiv((cR - cL) * ih, rho_f);
+        const T irho = T(1) / rho_f;   // one FP64 quotient per face
+        const T H = -conv + visc * (irho * inv_re);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(-1, 0, 0))) * (((cR - cL) * ih) * irho);
         Hx = H;
         ux = Ug(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hu) + st);
       }
@@ -1188,8 +1043,9 @@ __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
         const T vcA = T(0.5) * (Vg(0, 0, 0) + Vg(0, 1, 0));
         const T vcB = T(0.5) * (Vg(0, -1, 0) + Vg(0, 0, 0));
         const T conv = ((uvx - uv0) * ih + (vcA * vcA - vcB * vcB) * ih) + (n_vw - c_vw) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, -1, 0))) * qdiv((cA - cB) * ih, rho_f);
+        const T irho = T(1) / rho_f;   // one FP64 quotient per face
+        const T H = -conv + visc * (irho * inv_re);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, -1, 0))) * (((cA - cB) * ih) * irho);
         Hy = H;
         vy = Vg(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hv) + st);
       }
@@ -1200,8 +1056,9 @@ __global__ void __launch_bounds__(kPx * kPy, 2) k3_predict_s(S3<T> a) {
         const T wcA = T(0.5) * (Wf(0, 0, 0) + Wf(0, 0, 1));
         const T wcB = T(0.5) * (Wf(0, 0, -1) + Wf(0, 0, 0));
         const T conv = ((uwx - c_uw) * ih + (c_vwn - c_vw) * ih) + (wcA * wcA - wcB * wcB) * ih;
-        const T H = -conv + qdiv(visc, a.Re * rho_f);
-        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, 0, -1))) * qdiv((cA - cB) * ih, rho_f);
+        const T irho = T(1) / rho_f;   // one FP64 quotient per face
+        const T H = -conv + visc * (irho * inv_re);
+        const T st = k_st * (T(0.5) * (Fc(0, 0, 0) + Fc(0, 0, -1))) * (((cA - cB) * ih) * irho);
         Hz = H;
         wz = Wf(0, 0, 0) + a.dt * ((T(1.5) * H - T(0.5) * hw) + st);
       }
@@ -1506,7 +1363,7 @@ __global__ void __launch_bounds__(kGhostBlock) k3_fill_u(S3<T> a) {
   const int g = gt / kGhostLanes, q = gt % kGhostLanes;
   const Tables& t = a.tab;
   T s1[3], s2[3];
-  gather_group<3>(t, g, q, [&](size_t c, T* v) {
+  gather_group<3>(t, a.w1t, a.w2t, g, q, [&](size_t c, T* v) {
     v[0] = ucen3(a, c);
     v[1] = vcen3(a, c);
     v[2] = wcen3(a, c);
@@ -1590,6 +1447,8 @@ S3<T> make3(const Instance& in, int cur) {
     const int planes = in.tune_pred_planes ? in.tune_pred_planes : kPz;
     a.pred_kz = in.nz < planes ? in.nz : planes;
   }
+  a.w1t = sizeof(T) == 8 ? (const T*)in.tab.w1 : (const T*)in.tab.w1f;
+  a.w2t = sizeof(T) == 8 ? (const T*)in.tab.w2 : (const T*)in.tab.w2f;
   a.lnx = in.lognx;
   a.lny = in.logny;
   a.inv_h = (T)(1.0 / in.h);
@@ -1766,6 +1625,33 @@ void predict3(const Instance& in, int cur, cudaStream_t s, void* us, void* vs, v
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_weights_f32(const double* __restrict__ w1, const double* __restrict__ w2,
+                              float* __restrict__ f1, float* __restrict__ f2, size_t n) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) {
+    f1[e] = (float)w1[e];
+    f2[e] = (float)w2[e];
+  }
+}
+}  // namespace
+
+// The FP32 form's ghost fills read the averaging weights in FP32: copies of the FP64 weights
+// of the precompute, each rounded once (relative error 2^-24 on weights of O(1)), half the
+// table bytes of every gather.
+cudaError_t weights3_f32(Instance& in, cudaStream_t s) {
+  const size_t n = (size_t)in.tab.ng * kNap3;
+  if (in.tab.w1f) cudaFree(in.tab.w1f);
+  if (in.tab.w2f) cudaFree(in.tab.w2f);
+  in.tab.w1f = in.tab.w2f = nullptr;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&in.tab.w1f, sizeof(float) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&in.tab.w2f, sizeof(float) * n);
+  if (e != cudaSuccess) return e;
+  k_weights_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in.tab.w1, in.tab.w2, in.tab.w1f, in.tab.w2f, n);
+  return cudaGetLastError();
+}
 
 // Tuner: the mean time (ms) of `reps` launches of the 3D predictor of instance `in` with
 // `planes` planes per block (the instance's choice is restored afterwards).  The predictor
