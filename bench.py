@@ -729,7 +729,7 @@ def run_ours(args):
     if args.only:
         form = "fp64" if args.precision == "fp64" else "fp32"
         line = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world,
-                           args.only, only_case(W, args.only), form)
+                           args.only, only_case(W, args.only), form, e2e=True)
         line["workload"] = args.only
         line["clocks"] = sampler.stop()
         if rank == 0:

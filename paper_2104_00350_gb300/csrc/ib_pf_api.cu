@@ -351,7 +351,8 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     // partial sums: one per cell tile of the step's reduction, or per 256-cell block of
     // the stand-alone reduction, whichever is more
     const int ntile = ((in.nx + kTileX - 1) / kTileX) * ((in.ny + kTileH - 1) / kTileH);
-    const int nred = (int)((cells + 255) / 256);
+    // (3D FP32: one partial per warp of the correction kernel, 128 cells)
+    const int nred = (int)((cells + (in.dim == 3 ? 127 : 255)) / (in.dim == 3 ? 128 : 256));
     const int nblk = ntile > nred ? ntile : nred;
     in.nblk_red = nblk;
     // group sums and group counters of the two-level final sum (tile_mass)

@@ -493,7 +493,33 @@ __global__ void __launch_bounds__(kTQ, 10) k3_correct_q(S3<float> a) {
   float hi = c0.e[0], lsum = lo.e[0];
 #pragma unroll
   for (int e = 1; e < 4; ++e) pair_add(hi, lsum, c0.e[e], lo.e[e]);
-  tile_mass<float, kTQ>(hi, lsum, (int)blockIdx.x, (int)gridDim.x, a.partial, a.ticket, a.mass);
+  // one FP64 partial per warp (no block barrier); k3_mass_groups / k3_mass_total add them
+  warp_pair_sum(hi, lsum);
+  if ((threadIdx.x & 31) == 0)
+    a.partial[(size_t)blockIdx.x * (kTQ / 32) + (threadIdx.x >> 5)] = (double)hi + (double)lsum;
+}
+
+// The FP64 mass of the FP32 3D step from the correction kernel's warp partials: kMassSpan
+// partials per block in a fixed tree, then the block sums by one block, in a fixed order.
+constexpr int kMassSpan = 1024, kMassThreads = 256;
+__global__ void __launch_bounds__(kMassThreads) k3_mass_groups(const double* __restrict__ partial,
+                                                               int n, double* __restrict__ gsum) {
+  __shared__ double wd[kMassThreads / 32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < kMassSpan; i += kMassThreads) {
+    const size_t e = (size_t)blockIdx.x * kMassSpan + i;
+    if (e < (size_t)n) v += partial[e];
+  }
+  v = block_sum<kMassThreads>(v, wd);
+  if (threadIdx.x == 0) gsum[blockIdx.x] = v;
+}
+__global__ void __launch_bounds__(kMassThreads) k3_mass_total(const double* __restrict__ gsum, int n,
+                                                              double* __restrict__ mass) {
+  __shared__ double wd[kMassThreads / 32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += kMassThreads) v += gsum[i];
+  v = block_sum<kMassThreads>(v, wd);
+  if (threadIdx.x == 0) *mass = v;
 }
 
 // ------------------------------------- a1 + a2, explicit variant (Eq. ExpCH), 3D
@@ -1603,9 +1629,18 @@ int step3d_t(const Ctx& ctx, int cur, cudaStream_t s, Recorder* rec) {
     else k3_poisson_rhs_z<T><<<zg, zb, 0, s>>>(a);
     mark("poisson_rhs");
     launches += spectral3_solve(in, ctx.precision, 1, cur, s, rec);
-    if constexpr (percell) k3_correct_q<<<nb, kTQ, 0, s>>>(a);
-    else k3_correct_z<T><<<zg, zb, 0, s>>>(a);
-    mark("correct");
+    if constexpr (percell) {
+      k3_correct_q<<<nb, kTQ, 0, s>>>(a);
+      mark("correct");
+      const int nw = (int)nb * (kTQ / 32), ngs = (nw + kMassSpan - 1) / kMassSpan;
+      k3_mass_groups<<<ngs, kMassThreads, 0, s>>>(in.partial, nw, in.partial + nw);
+      k3_mass_total<<<1, kMassThreads, 0, s>>>(in.partial + nw, ngs, in.mass);
+      mark("mass");   // one mark for the two launches
+      ++launches;
+    } else {
+      k3_correct_z<T><<<zg, zb, 0, s>>>(a);
+      mark("correct");
+    }
   }
   return launches;
 }

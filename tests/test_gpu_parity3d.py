@@ -122,9 +122,12 @@ def test_step_parity_3d_fp64(ibpf, name):
 
 @pytest.mark.parametrize("name", ["sphere32", "porous32", "xlong", "ylong", "zlong"])
 def test_step_parity_3d_fp32(ibpf, name):
-    errs, _, _ = _step_parity(ibpf, name, seed=3, prec=ibpf.FP32)
+    errs, mass, ref = _step_parity(ibpf, name, seed=3, prec=ibpf.FP32)
     assert errs["C"] <= 5e-6, errs
     assert max(errs["u"], errs["v"], errs["w"], errs["P"]) <= 1e-5, errs
+    # the FP64 mass of the compensated FP32 C: within the per-cell bound summed over cells
+    c = ref["C"]
+    assert abs(mass - c.sum()) <= 5e-6 * np.abs(c).max() * c.size
 
 
 def test_multi_step_sphere_tracks_oracle(ibpf):
