@@ -76,6 +76,7 @@ KERNEL_STEP_WORDS_3D = {
     "rows_fwd": (4, 4, 0),       # 2 launches: real rows in, half spectrum out
     "y_fft": (4, 4, 0),          # 2 launches: spectrum in and out
     "z_solve": (4, 4, 0),
+    "z_solve_tc": (4, 4, 0),     # the same solve on the tensor cores (FP32_3XBF16 form)
     "y_ifft": (4, 4, 0),
     "rows_inv": (11, 8, 0),      # as in 2D
     "chem_pot": (2, 2, 0),
@@ -353,6 +354,26 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor rate (TFLOP/s): the sustained loop, for a kernel timed inside a
+    long step, else the burst figure, else the fallback."""
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        d = json.loads(f.read_text())
+        if "bf16_tflops_sustained" in d:
+            return float(d["bf16_tflops_sustained"]), "measured (sustained)"
+        return float(d["bf16_tflops"]), "measured (burst)"
+    return 1900.0, "fallback"
+
+
+def tc_zsolve_flops(nx: int, ny: int, nz: int) -> float:
+    """Tensor flops of one z solve on the tensor cores: every real spectrum column (2 ny
+    (nx/2 + 1 rounded up to even)) takes, forward and inverse, nz/128 products of a 128 x 128
+    matrix in three BF16 parts."""
+    cols = 2 * ny * 2 * ((nx // 2 + 2) // 2)
+    return cols * 2 * (nz // 128) * 3 * 2.0 * 128 * 128
+
+
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM (ncu peak_sustained) x flops x GHz
 
 
@@ -392,6 +413,11 @@ def roofline(ktot, kcount, steps, cells, esz, case0, peak, peak_kind, form, word
                 gbs = ub * units[unit] * kcount[k] / (v * 1e-3) / 1e9
                 ent.update({"alg_GBs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
                             f"bytes_per_{unit}": ub, f"{unit}s": units[unit]})
+        if k == "z_solve_tc" and dim == 3:
+            tp, tk = measured_bf16_peak()
+            tf = tc_zsolve_flops(case0.nx, case0.ny, case0.nz) * kcount[k] / (v * 1e-3) / 1e12
+            ent.update({"tensor_TFLOPs": round(tf, 1), "tensor_frac": round(tf / tp, 4),
+                        "tensor_peak": tp, "tensor_peak_kind": tk})
         table[k] = ent
     if not alu:
         alg = kernel_step_bytes(dom, esz, cells, words) * steps / kcount[dom]
@@ -473,7 +499,7 @@ def run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world, 
     through the C ABI with the whole state written from pinned host memory and C read back
     every step."""
     import numpy as np
-    prec = ibpf.FP64 if form == "fp64" else ibpf.FP32
+    prec = {"fp64": ibpf.FP64, "fp32": ibpf.FP32, "fp32_3xbf16": ibpf.FP32_3XBF16}[form]
     esz = 8 if form == "fp64" else 4
     t0 = time.time()
     s = ibpf.solver_from_cases([case], prec, stream=stream.cuda_stream)
@@ -746,8 +772,8 @@ def run_ours(args):
     if not args.no_3d:
         sph = W.sphere_case(256)
         sph_x = dataclasses.replace(sph, params=dataclasses.replace(sph.params, ch_scheme=1))
-        for name, case, form in (("sphere_256", sph, "fp32"), ("sphere_256", sph, "fp64"),
-                                 ("sphere_256_explicit", sph_x, "fp32")):
+        for name, case, form in (("sphere_256", sph, "fp32"), ("sphere_256", sph, "fp32_3xbf16"),
+                                 ("sphere_256", sph, "fp64"), ("sphere_256_explicit", sph_x, "fp32")):
             if form == "fp64" and args.precision == "fp32":
                 continue
             d3[f"{name}_{form}"] = run_3d_case(args, ibpf, W, torch, stream, tm, peak, peak_kind,

@@ -62,12 +62,21 @@ typedef enum {
   IB_PF_E_UNSUPPORTED = -2,  /* valid but not implemented (e.g. dynamic angle) */
   IB_PF_E_CUDA = -3,         /* a CUDA runtime call failed; see ib_pf_last_error */
   IB_PF_E_NUMERIC = -4,      /* NaN/Inf seen in C or the velocity by the device check */
-  IB_PF_E_TIMEOUT = -5,      /* reserved: a bounded device wait gave up (no kernel waits) */
+  IB_PF_E_TIMEOUT = -5,      /* a bounded device wait gave up (the tensor-core z solve of
+                                FP32_3XBF16 contexts waits on its MMAs for at most 2 s) */
   IB_PF_E_STATE = -6,        /* call out of order (e.g. step before precompute) */
   IB_PF_E_GEOMETRY = -7      /* precompute failed (no intersect point within 10 h) */
 } ib_pf_status;
 
-typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1 } ib_pf_precision;
+/* arithmetic of a context: FP64 throughout; FP32 fields and transforms (geometry, weights and
+ * the mass of C in FP64, C held as a compensated pair); FP32_3XBF16: the FP32 form with the
+ * wall-normal (z) solve of the 3D Cahn-Hilliard and Poisson problems (Appendix A.1,
+ * Eq. PressurePoisson) done as dense cosine-transform products on the tensor cores, every
+ * operand split into two BF16 parts and three products accumulated in FP32 (about 16
+ * significant bits per transform instead of FP32's 24); 3D contexts with nz = 128 or 256
+ * only (other grids and 2D contexts return IB_PF_E_UNSUPPORTED).  Field buffers, tables and
+ * I/O of an FP32_3XBF16 context are those of an FP32 one. */
+typedef enum { IB_PF_FP64 = 0, IB_PF_FP32 = 1, IB_PF_FP32_3XBF16 = 2 } ib_pf_precision;
 
 /* time integration of the Cahn-Hilliard equation (rows a1 + a2): SEMI_IMPLICIT, the
  * stabilised split of Appendix A.1 solved in one eigenbasis; EXPLICIT, the Adams-Bashforth

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # geometry decisions (subgrid counts, march, averaging cells) want unfused products
 PER_FILE = {"geometry.cu": ["-fmad=false"], "geometry3d.cu": ["-fmad=false"]}
 SOURCES = ["ib_pf_api.cu", "geometry.cu", "geometry3d.cu", "spectral.cu", "step2d.cu", "step3d.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "tc_zsolve.cu"]
 
 
 def nvcc() -> str:

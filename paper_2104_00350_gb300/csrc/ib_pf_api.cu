@@ -82,7 +82,7 @@ void free_instance(Instance& in) {
                   in.tab.w1, in.tab.ap2, in.tab.w2, in.tab.fu, in.tab.fv, in.W[0], in.W[1], in.Hw,
                   in.gw, in.lamz, in.lamz_f, in.twz, in.sph, in.bstart, in.blist,
                   in.tab.alpha_w, in.tab.fw, in.alpha_f, in.ci, in.gq, in.lam_s2, in.lam_d1,
-                  in.lam_s2_f, in.lam_d1_f, in.tw2, in.tab.w1f, in.tab.w2f};
+                  in.lam_s2_f, in.lam_d1_f, in.tw2, in.tab.w1f, in.tab.w2f, in.dmat_z};
   for (void* p : ptrs) {
     if (!p) continue;
     bool caller_owned = false;
@@ -173,7 +173,14 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
     return IB_PF_E_UNSUPPORTED;
   }
   if (g.dim == 3) {
-    if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
+    if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32 && p.precision != IB_PF_FP32_3XBF16) {
+      why = "unknown precision";
+      return IB_PF_E_ARG;
+    }
+    if (p.precision == IB_PF_FP32_3XBF16 && !zsolve_tc_supported(g.n[2])) {
+      why = "the tensor-core z solve (FP32_3XBF16) is built for nz = 128 and 256";
+      return IB_PF_E_UNSUPPORTED;
+    }
     if (!(p.mu_f >= 0.0) || !std::isfinite(p.mu_f)) { why = "mu_f must be finite and >= 0"; return IB_PF_E_ARG; }
     const double vals3[] = {p.Re, p.Ca, p.Cn, p.Pe, p.rho_ratio, p.mu_ratio, p.dt, p.d1, p.d2};
     for (double v : vals3)
@@ -198,6 +205,10 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
   if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SINUSOID && w.kind != IB_PF_WALL_NONE) {
     why = "unknown wall kind";
     return IB_PF_E_ARG;
+  }
+  if (p.precision == IB_PF_FP32_3XBF16) {
+    why = "FP32_3XBF16 (tensor-core z solve) is built for 3D contexts";
+    return IB_PF_E_UNSUPPORTED;
   }
   if (p.precision != IB_PF_FP64 && p.precision != IB_PF_FP32) { why = "unknown precision"; return IB_PF_E_ARG; }
   if (!(p.mu_f >= 0.0) || !std::isfinite(p.mu_f)) { why = "mu_f must be finite and >= 0"; return IB_PF_E_ARG; }
@@ -270,7 +281,8 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
   }
   ib_pf_ctx* ctx = new (std::nothrow) ib_pf_ctx();
   if (!ctx) return fail(nullptr, IB_PF_E_ARG, "out of host memory");
-  ctx->precision = params[0].precision;
+  // the split-BF16 form is the FP32 form with the tensor-core z solve (Instance::tc_z)
+  ctx->precision = params[0].precision == IB_PF_FP32_3XBF16 ? IB_PF_FP32 : params[0].precision;
   ctx->dim = grids[0].dim;
   ctx->ch_scheme = params[0].ch_scheme;
   ctx->ns_scheme = params[0].ns_scheme;
@@ -308,6 +320,8 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     in.h = in.lx / in.nx;
     in.geom = geoms[k];
     in.prm = params[k];
+    in.tc_z = params[k].precision == IB_PF_FP32_3XBF16;
+    in.prm.precision = ctx->precision;
     in.prm_ns_semi = params[k].ns_scheme == IB_PF_NS_SEMI_IMPLICIT;
     in.wall.kind = geoms[k].kind;
     in.wall.p0 = geoms[k].p[0];
@@ -455,6 +469,8 @@ ib_pf_status ib_pf_step(ib_pf_ctx* ctx, int nsteps) {
     const int st = ((volatile int*)ctx->h_status)[k];
     if (st & 2)
       return fail(ctx, IB_PF_E_CUDA, "a 3D transform tile failed its alignment check in instance " + std::to_string(k));
+    if (st & 4)
+      return fail(ctx, IB_PF_E_TIMEOUT, "a tensor-core wait of the z solve gave up in instance " + std::to_string(k));
     if (st != 0)
       return fail(ctx, IB_PF_E_NUMERIC, "non-finite value seen in instance " + std::to_string(k));
   }

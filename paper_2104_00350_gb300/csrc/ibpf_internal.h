@@ -140,6 +140,9 @@ struct Instance {
   // 3D schedule choices (0: the built-in default), set by ib_pf_set_tuning / ib_pf_autotune:
   // row bytes of the y and z transform tiles (64 or 128), planes per predictor block
   int tune_y_rb = 0, tune_z_rb = 0, tune_pred_planes = 0;
+  // FP32_3XBF16: the z solve runs on the tensor cores from the split DCT matrices dmat_z
+  bool tc_z = false;
+  void* dmat_z = nullptr;
   std::vector<void*> bound;    // caller-owned field buffers (ib_pf_bind_fields): never freed
 };
 
@@ -250,6 +253,12 @@ float step3d_time_predict(const Ctx& c, Instance& in, int planes, int reps, cuda
 // rows, timed on the instance's spectral scratch; -1 when rb is not built for that length
 float spectral3_time_tiles(const Instance& in, int precision, int axis, int rb, int reps,
                            cudaStream_t s);
+// tensor-core z solve of the FP32_3XBF16 form (tc_zsolve.cu)
+bool zsolve_tc_supported(int nz);
+cudaError_t zsolve_tc_tables(int nz, void** out);
+void zsolve_tc_launch(float* spec, int nz, long long ncols, int sp, int nh1, const float* lamz,
+                      const float* lamx, const float* lamyp, const void* dmat, int mode, float s_eta2,
+                      float c0, int* status, cudaStream_t s);
 int spectral3_solve(const Instance& in, int precision, int mode, int cur, cudaStream_t s,
                     Recorder* rec);
 int step3d(const Ctx& c, int cur, cudaStream_t s, Recorder* rec);

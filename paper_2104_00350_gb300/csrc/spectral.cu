@@ -1292,6 +1292,7 @@ cudaError_t tables3_t(Instance& in) {
   const cudaFuncAttribute att = cudaFuncAttributeMaxDynamicSharedMemorySize;
   (void)att;
   tile_attributes<T, 3>();
+  if (in.tc_z && (e = zsolve_tc_tables(nz, &in.dmat_z)) != cudaSuccess) return e;
 
   return cudaGetLastError();
 }
@@ -1353,8 +1354,15 @@ int spectral3_solve_t(const Instance& in, int mode, int cur, cudaStream_t s, Rec
   if (rec) rec->mark("rows_fwd", s);
   ytile3<T>(in, false, y_rb(in), s);
   if (rec) rec->mark("y_fft", s);
-  ztile3<T>(in, mode, z_rb(in), s);
-  if (rec) rec->mark("z_solve", s);
+  if (in.tc_z && sizeof(T) == 4) {
+    zsolve_tc_launch((float*)in.spec, nz, (long long)ny * sp, sp, nx / 2 + 1, in.lamz_f, in.lamx_f,
+                     in.lamy_f, in.dmat_z, mode, (float)(in.prm.S / (in.prm.Cn * in.prm.Cn)),
+                     (float)(1.5 * in.prm.Pe / (in.prm.Cn * in.prm.Cn * in.prm.dt)), in.status, s);
+    if (rec) rec->mark("z_solve_tc", s);
+  } else {
+    ztile3<T>(in, mode, z_rb(in), s);
+    if (rec) rec->mark("z_solve", s);
+  }
   ytile3<T>(in, true, y_rb(in), s);
   if (rec) rec->mark("y_ifft", s);
   EpiArgs epi;

@@ -16,7 +16,7 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libibpf.so"
 
 # ---- enums (mirror include/ib_pf.h)
 OK, E_ARG, E_UNSUPPORTED, E_CUDA, E_NUMERIC, E_TIMEOUT, E_STATE, E_GEOMETRY = 0, -1, -2, -3, -4, -5, -6, -7
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_3XBF16 = 0, 1, 2   # ib_pf_precision
 CH_SEMI_IMPLICIT, CH_EXPLICIT = 0, 1
 W_LINEAR, W_IDW = 0, 1            # ib_pf_weights
 NS_EXPLICIT, NS_SEMI_IMPLICIT = 0, 1   # ib_pf_ns_scheme
@@ -356,7 +356,8 @@ class Solver:
                 gpu_name = torch.cuda.get_device_name()
             except Exception:   # no torch / no device name: key without it
                 gpu_name = "unknown"
-        key = "x".join(str(v) for v in n[::-1]) + f":{'fp64' if self.precision == FP64 else 'fp32'}:{gpu_name}"
+        form = {FP64: 'fp64', FP32: 'fp32', FP32_3XBF16: 'fp32_3xbf16'}[self.precision]
+        key = "x".join(str(v) for v in n[::-1]) + f":{form}:{gpu_name}"
         table = {}
         if cache is not None and Path(cache).exists():
             table = json.loads(Path(cache).read_text())
@@ -437,7 +438,7 @@ class Solver:
         """Everything needed for a bit-exact restart (state plus, in FP32 contexts, the
         low parts of the compensated C)."""
         d = self.read_state(instance)
-        if self.precision == FP32:
+        if self.precision != FP64:
             d["C_lo"] = self.read("C_lo", instance)
             d["C_old_lo"] = self.read("C_old_lo", instance)
         if self.dynamic:

@@ -122,3 +122,22 @@ def test_tuning_calls_reject_a_null_context(lib):
     assert so.ib_pf_set_tuning(None, 0, ct.byref(t)) == lib.E_ARG
     assert so.ib_pf_get_tuning(None, 0, ct.byref(t)) == lib.E_ARG
     assert so.ib_pf_autotune(None, 0, 1, ct.byref(t), None) == lib.E_ARG
+
+
+def test_split_bf16_form_limits_checked_on_host(lib):
+    # the tensor-core z solve (FP32_3XBF16) is built for 3D grids with nz = 128 or 256
+    g, w, p = _args(lib)
+    p[0].precision = lib.FP32_3XBF16                     # 2D context
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_UNSUPPORTED
+    g, w, p = _args3(lib, n=(32, 32, 64), L=(1.0, 1.0, 2.0))
+    p[0].precision = lib.FP32_3XBF16                     # nz = 64
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_UNSUPPORTED
+    g, w, p = _args3(lib)
+    p[0].precision = 3                                   # unknown precision
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_ARG

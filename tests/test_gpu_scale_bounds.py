@@ -5,8 +5,8 @@ FP64 GPU path (which tracks the oracle to round-off per step, test_gpu_parity*):
   bit-identical to each run advanced alone (FP64 and FP32);
 * the 64-instance FP32 ensemble over 200 steps: C within 1e-5, velocity within 1e-4
   (max-norm relative, per instance);
-* the 256^3 droplet on a sphere, FP32 over 1000 steps: C within 1e-5, velocity within 1e-4,
-  apparent contact angle within 0.1 deg;
+* the 256^3 droplet on a sphere over 1000 steps, FP32 and the split-BF16 tensor-core form:
+  C within 1e-5, velocity within 1e-4, apparent contact angle within 0.1 deg;
 * the 512^3 packing, FP32 over 500 steps: C within 1e-5, velocity within 1e-4.
 """
 import math
@@ -61,7 +61,7 @@ def _dev_fields(ibpf, s, torch, names, k=0):
                         device="cuda")
         s.read(n, k, out=t)
         out[n] = t.double()
-    if s.precision == ibpf.FP32:
+    if s.precision != ibpf.FP64:
         lo = torch.empty(s.field_shape("C", k), dtype=torch.float32, device="cuda")
         s.read("C_lo", k, out=lo)
         out["C"] = out["C"] + lo.double()
@@ -125,7 +125,8 @@ def test_fp32_sphere_256_bounds_and_angle(ibpf):
     import torch
     case = W.sphere_case(256)
     res, ang = {}, {}
-    for p in (ibpf.FP64, ibpf.FP32):
+    # FP32 and the split-BF16 tensor-core form (the workload's stated transforms)
+    for p in (ibpf.FP64, ibpf.FP32, ibpf.FP32_3XBF16):
         s = ibpf.solver_from_cases([case], p)
         s.precompute_weights()
         C0 = W.droplet_C3d(case, np.float64 if p == ibpf.FP64 else np.float32)
@@ -137,9 +138,10 @@ def test_fp32_sphere_256_bounds_and_angle(ibpf):
         ang[p] = _sphere_angle(case, res[p]["C"].cpu().numpy())
         s.close()
         torch.cuda.empty_cache()
-    e = {f: _rel(res[ibpf.FP32][f], res[ibpf.FP64][f]) for f in ("C", "u", "v", "w")}
-    assert e["C"] <= 1e-5 and max(e["u"], e["v"], e["w"]) <= 1e-4, e
-    assert abs(ang[ibpf.FP32] - ang[ibpf.FP64]) < 0.1, ang
+    for q in (ibpf.FP32, ibpf.FP32_3XBF16):
+        e = {f: _rel(res[q][f], res[ibpf.FP64][f]) for f in ("C", "u", "v", "w")}
+        assert e["C"] <= 1e-5 and max(e["u"], e["v"], e["w"]) <= 1e-4, (q, e)
+        assert abs(ang[q] - ang[ibpf.FP64]) < 0.1, (q, ang)
 
 
 def test_fp32_porous_512_bounds(ibpf):
