@@ -14,22 +14,26 @@
 // Ce[p][j] = D[2p][j] and Co[p][j] = D[2p+1][j]; the inverse is a = Ce^T Y_even,
 // b = Co^T Y_odd, x_j = a_j + b_j, x_{N-1-j} = a_j - b_j (D[2p][N-1-j] = D[2p][j],
 // D[2p+1][N-1-j] = -D[2p+1][j]).  N = 128 uses D itself.  Every product is then
-// 128 x 128 (one MMA tile height), H = N / 128 of them per transform.
+// 128 x 128, H = N / 128 of them per transform.
 //
 // Split precision: every FP32 operand value x is held as hi + lo with hi = bf16(x),
 // lo = bf16(x - hi) (16 significant bits); a product is accumulated in FP32 tensor memory as
-// Ahi Bhi + Ahi Blo + Alo Bhi (the Alo Blo term, ~2^-16 relative, is dropped).  The matrices
+// Ahi Bhi + Alo Bhi + Ahi Blo (the Alo Blo term, ~2^-16 relative, is dropped).  The matrices
 // are rounded once from FP64 on the host.
 //
-// Kernel layout: persistent, one block of 256 threads per SM.  The H x {hi, lo} matrices
-// (H x 64 KiB) arrive once per block by bulk copies and stay in shared memory; the same
-// bytes serve the forward product (K-major A) and the inverse one (the transpose, read as an
-// MN-major A).  A tile is 64 real columns (32 complex spectrum columns) of all N rows: loaded
-// from global memory with the even/odd step applied, split, stored as the MN-major B operand;
-// one thread issues the forward MMAs into tensor memory (H x 64 FP32 columns); the epilogue
-// reads the accumulators, divides by the symbol, splits the result into the B operand of the
-// inverse products; the inverse MMAs reuse the same tensor-memory columns; the last epilogue
-// undoes the even/odd step and stores the columns.
+// Kernel layout: persistent, one block of 512 threads per SM.  The H x {hi, lo} matrices
+// (H x 64 KiB) arrive once per block by bulk copies and stay in shared memory as the B
+// operands: K-major for the forward products, the same bytes read MN-major for the inverse.
+// A tile is 128 real spectrum columns (64 complex) of all N rows, with the columns on the
+// tensor-memory lanes (MMA M = 128, N = 128):
+//   forward  D1[n][m] = sum_j X[n][j] Mat[m][j], X the tile after the even/odd step, split
+//            and written to tensor memory as the A operand;
+//   symbol   Z[n][m] = D1[n][m] / sigma, split, written over X as the next A operand;
+//   inverse  D2[n][j] = sum_m Z[n][m] Mat[m][j], the even/odd step undone on the way out.
+// Each thread owns one column (its lane) and a quarter of the rows, so a warp's loads and
+// stores touch 32 consecutive floats of a spectrum row.  The next tile's loads are issued
+// under the forward and the inverse products.
+
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -42,34 +46,19 @@
 namespace ibpf {
 namespace {
 
-constexpr int kTcThreads = 256;
-constexpr int kTcNG = 64;                      // real columns per tile (MMA N)
 constexpr int kTcMat = 128 * 128 * 2;          // bytes of one 128 x 128 BF16 matrix
-constexpr int kTcOpB = 128 * kTcNG * 2;        // bytes of one 128 x NG BF16 B operand
 
-// descriptor strides (bytes) of the two layouts, see tc_ptx.cuh
-//   matrices (A): K-major, element (m, k) at ((m/8) 16 + k/8) 128 + (m%8) 16 + (k%8) 2
-//   tiles (B):    MN-major, element (k, n) at ((k/8) (NG/8) + n/8) 128 + (k%8) 16 + (n%8) 2
-constexpr uint32_t kA_LBO_K = 128, kA_SBO_K = 2048;     // forward: K-major
-constexpr uint32_t kA_LBO_MN = 2048, kA_SBO_MN = 128;   // inverse: the transpose, MN-major
-constexpr uint32_t kB_LBO = kTcNG * 16, kB_SBO = 128;   // MN-major
+// Matrix layout in shared memory: element (m, j) (row m of Ce, Co or D, column j) at
+// ((m/8) 16 + j/8) 128 + (m%8) 16 + (j%8) 2, core matrices of 8 rows of 16 bytes.  As the B
+// operand of the forward products (K = j, N = m) that is K-major: K-adjacent core matrices
+// 128 bytes apart (LBO), N-adjacent 2048 (SBO); of the inverse ones (K = m, N = j) MN-major:
+// K-adjacent 2048 (LBO), N-adjacent 128 (SBO).
+constexpr uint32_t kA_LBO_K = 128, kA_SBO_K = 2048;
+constexpr uint32_t kA_LBO_MN = 2048, kA_SBO_MN = 128;
 
 __host__ __device__ constexpr int a_off(int m, int k) {
   return (((m >> 3) * 16 + (k >> 3)) << 7) + ((m & 7) << 4) + ((k & 7) << 1);
 }
-__host__ __device__ constexpr int b_off(int k, int n) {
-  return (((k >> 3) * (kTcNG / 8) + (n >> 3)) << 7) + ((k & 7) << 4) + ((n & 7) << 1);
-}
-
-template <int H>
-struct TcSmem {
-  static constexpr int A = 0;                                   // H x {hi, lo} matrices
-  static constexpr int B = A + 2 * H * kTcMat;                   // H x {hi, lo} tiles
-  static constexpr int LZ = B + 2 * H * kTcOpB;                  // lamz (N floats)
-  static constexpr int LC = LZ + 4 * 128 * H;                    // lamy + lamx of the tile's
-  static constexpr int BAR = LC + 4 * (kTcNG / 2);               //   complex columns; barriers
-  static constexpr int BYTES = BAR + 64;
-};
 
 struct TcZArgs {
   float* spec;           // nz rows of 2 ncols floats (complex spectrum, interleaved re/im)
@@ -92,160 +81,106 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
-// 8 values -> 16 bytes of hi parts and 16 bytes of lo parts
-__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
-  split2(x[0], x[1], hi.x, lo.x);
-  split2(x[2], x[3], hi.y, lo.y);
-  split2(x[4], x[5], hi.z, lo.z);
-  split2(x[6], x[7], hi.w, lo.w);
-}
+constexpr int kTtThreads = 512;
+constexpr int kTtCols = 128;          // real columns per tile
+constexpr uint32_t kTtXA = 0;         // tensor-memory columns of the A operands: (2h + part) 64
+constexpr uint32_t kTtD = 256;        // accumulators: h 128
 
-// forward (FWD) or inverse products of one tile: for each of the H matrices, 8 K-steps of
-// 3 split MMAs into the tensor-memory columns tmem + h NG .. + NG - 1
-template <int H, bool FWD>
-__device__ __forceinline__ void issue_products(uint32_t sa, uint32_t sb, uint32_t tmem) {
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, kTcNG, !FWD, true);
-#pragma unroll
-  for (int h = 0; h < H; ++h) {
-    const uint32_t a_hi = sa + (2 * h) * kTcMat, a_lo = a_hi + kTcMat;
-    const uint32_t b_hi = sb + (2 * h) * kTcOpB, b_lo = b_hi + kTcOpB;
-    const uint32_t d = tmem + h * kTcNG;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-      const uint32_t ao = FWD ? s * 256 : s * 4096;   // K-step of 16: two core matrices
-      const uint32_t lbo = FWD ? kA_LBO_K : kA_LBO_MN, sbo = FWD ? kA_SBO_K : kA_SBO_MN;
-      const uint32_t bo = s * 2 * kB_LBO;
-      const uint64_t ah = tc::sdesc(a_hi + ao, lbo, sbo), al = tc::sdesc(a_lo + ao, lbo, sbo);
-      const uint64_t bh = tc::sdesc(b_hi + bo, kB_LBO, kB_SBO), bl = tc::sdesc(b_lo + bo, kB_LBO, kB_SBO);
-      tc::mma_bf16(d, ah, bl, idesc, s > 0 ? 1u : 0u);
-      tc::mma_bf16(d, al, bh, idesc, 1u);
-      tc::mma_bf16(d, ah, bh, idesc, 1u);
-    }
-  }
-}
-
-// This thread's share of a tile: rows j = 8 ((warp >> 1) + 4 i) + (lane & 7), i < 4, and (for
-// H = 2) N - 1 - j; real columns 8 g .. 8 g + 7, g = (lane >> 3) + 4 (warp & 1).
 template <int H>
-struct TileRegs {
-  float4 x[4][2];
-  float4 y[4][2];   // rows N - 1 - j (H = 2)
-  float lc;         // threads 0..NG/2-1: lamy + lamx of complex column tid of the tile
+struct TtSmem {
+  static constexpr int A = 0;                      // H x {hi, lo} matrices
+  static constexpr int LZ = A + 2 * H * kTcMat;    // lamz (N floats)
+  static constexpr int BAR = LZ + 4 * 128 * H;     // 3 mbarriers, tensor-memory base, flag
+  static constexpr int BYTES = BAR + 64;
 };
 
+// one thread's share of a tile: column n, rows j = 32 sub + i (i < 32) and N - 1 - j
 template <int H>
-__device__ __forceinline__ void load_tile(TileRegs<H>& r, const TcZArgs& a, size_t pitch, long long c0,
-                                          int ncr, int warp, int lane) {
+struct TtRegs {
+  float x[32];
+  float y[32];
+  float lc;      // lamy + lamx of the column's complex mode
+};
+
+// rows i in [I0, I0 + 16) of this thread's share (the lc term with the first half)
+template <int H, int I0>
+__device__ __forceinline__ void tt_load(TtRegs<H>& r, const TcZArgs& a, size_t pitch, long long c0, int ncr,
+                                        int n, int sub) {
   constexpr int N = 128 * H;
-  const float* spec = a.spec;
-  if (threadIdx.x < kTcNG / 2) {
-    const long long kc = min(c0 / 2 + threadIdx.x, a.ncols - 1);
+  const bool in = n < ncr;
+  if constexpr (I0 == 0) {
+    const long long kc = min((c0 + n) / 2, a.ncols - 1);
     r.lc = a.lamyp[kc / a.sp] + a.lamx[min((int)(kc % a.sp), a.nh1 - 1)];
   }
-  const int col = 8 * ((lane >> 3) + 4 * (warp & 1));
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* col = a.spec + c0 + n;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int j = 8 * ((warp >> 1) + 4 * i) + (lane & 7);
-    const float* r0 = spec + (size_t)j * pitch + c0 + col;
-    r.x[i][0] = col < ncr ? *reinterpret_cast<const float4*>(r0) : z4;
-    r.x[i][1] = col + 4 < ncr ? *reinterpret_cast<const float4*>(r0 + 4) : z4;
-    if constexpr (H == 2) {
-      const float* r1 = spec + (size_t)(N - 1 - j) * pitch + c0 + col;
-      r.y[i][0] = col < ncr ? *reinterpret_cast<const float4*>(r1) : z4;
-      r.y[i][1] = col + 4 < ncr ? *reinterpret_cast<const float4*>(r1 + 4) : z4;
+  for (int i = I0; i < I0 + 16; ++i) {
+    const int j = 32 * sub + i;
+    r.x[i] = in ? col[(size_t)j * pitch] : 0.f;
+    if constexpr (H == 2) r.y[i] = in ? col[(size_t)(N - 1 - j) * pitch] : 0.f;
+  }
+}
+
+// the even/odd step (H = 2) and the split of the forward A operands into tensor memory
+template <int H>
+__device__ __forceinline__ void tt_store_x(const TtRegs<H>& r, uint32_t t_lane, int sub) {
+  uint32_t hi[16], lo[16];
+  if constexpr (H == 2) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) split2(r.x[2 * i] + r.y[2 * i], r.x[2 * i + 1] + r.y[2 * i + 1], hi[i], lo[i]);
+    tc::tmem_st16(t_lane + kTtXA + 0 * 64 + 16 * sub, hi);
+    tc::tmem_st16(t_lane + kTtXA + 1 * 64 + 16 * sub, lo);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) split2(r.x[2 * i] - r.y[2 * i], r.x[2 * i + 1] - r.y[2 * i + 1], hi[i], lo[i]);
+    tc::tmem_st16(t_lane + kTtXA + 2 * 64 + 16 * sub, hi);
+    tc::tmem_st16(t_lane + kTtXA + 3 * 64 + 16 * sub, lo);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) split2(r.x[2 * i], r.x[2 * i + 1], hi[i], lo[i]);
+    tc::tmem_st16(t_lane + kTtXA + 0 * 64 + 16 * sub, hi);
+    tc::tmem_st16(t_lane + kTtXA + 1 * 64 + 16 * sub, lo);
+  }
+}
+
+template <int H, bool FWD>
+__device__ __forceinline__ void tt_products(uint32_t sa, uint32_t tmem) {
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128, false, !FWD);
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const uint32_t m_hi = sa + (2 * h) * kTcMat, m_lo = m_hi + kTcMat;
+    const uint32_t a_hi = tmem + kTtXA + (2 * h) * 64, a_lo = a_hi + 64;
+    const uint32_t d = tmem + kTtD + h * 128;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const uint32_t bo = FWD ? s * 256 : s * 4096;
+      const uint32_t lbo = FWD ? kA_LBO_K : kA_LBO_MN, sbo = FWD ? kA_SBO_K : kA_SBO_MN;
+      const uint64_t bh = tc::sdesc(m_hi + bo, lbo, sbo), bl = tc::sdesc(m_lo + bo, lbo, sbo);
+      tc::mma_bf16_ts(d, a_hi + 8 * s, bl, idesc, s > 0 ? 1u : 0u);
+      tc::mma_bf16_ts(d, a_lo + 8 * s, bh, idesc, 1u);
+      tc::mma_bf16_ts(d, a_hi + 8 * s, bh, idesc, 1u);
     }
   }
 }
 
-// the even/odd step (H = 2), the split, and the stores of the forward B operands
 template <int H>
-__device__ __forceinline__ void store_tile(const TileRegs<H>& r, unsigned char* bt, int warp, int lane) {
-  const int col = 8 * ((lane >> 3) + 4 * (warp & 1));
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int j = 8 * ((warp >> 1) + 4 * i) + (lane & 7);
-    const float x0[8] = {r.x[i][0].x, r.x[i][0].y, r.x[i][0].z, r.x[i][0].w,
-                         r.x[i][1].x, r.x[i][1].y, r.x[i][1].z, r.x[i][1].w};
-    const int o = b_off(j, col);
-    uint4 hi, lo;
-    if constexpr (H == 2) {
-      const float x1[8] = {r.y[i][0].x, r.y[i][0].y, r.y[i][0].z, r.y[i][0].w,
-                           r.y[i][1].x, r.y[i][1].y, r.y[i][1].z, r.y[i][1].w};
-      float u[8], v[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        u[e] = x0[e] + x1[e];
-        v[e] = x0[e] - x1[e];
-      }
-      split8(u, hi, lo);
-      *reinterpret_cast<uint4*>(bt + o) = hi;
-      *reinterpret_cast<uint4*>(bt + kTcOpB + o) = lo;
-      split8(v, hi, lo);
-      *reinterpret_cast<uint4*>(bt + 2 * kTcOpB + o) = hi;
-      *reinterpret_cast<uint4*>(bt + 3 * kTcOpB + o) = lo;
-    } else {
-      split8(x0, hi, lo);
-      *reinterpret_cast<uint4*>(bt + o) = hi;
-      *reinterpret_cast<uint4*>(bt + kTcOpB + o) = lo;
-    }
-  }
-}
-
-// the inverse products' results of a tile (tensor-memory columns tcol): undo the even/odd
-// step and store this thread's 32 columns of row j (and N - 1 - j)
-template <int H>
-__device__ __forceinline__ void store_result(float* spec, size_t pitch, long long c0, int ncr,
-                                             uint32_t t_row, int lq, int ch, int lane) {
-  constexpr int N = 128 * H, NG = kTcNG;
-  const int j = 32 * lq + lane, n0 = 32 * ch;
-  float ya[32], yb[32];
-  tc::tmem_ld32(t_row, ya);
-  if constexpr (H == 2) tc::tmem_ld32(t_row + NG, yb);
-  if (n0 >= ncr) return;
-  float* o0 = spec + (size_t)j * pitch + c0 + n0;
-  float* o1 = spec + (size_t)(N - 1 - j) * pitch + c0 + n0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (n0 + 4 * q < ncr) {
-      if constexpr (H == 2) {
-        *reinterpret_cast<float4*>(o0 + 4 * q) =
-            make_float4(ya[4 * q] + yb[4 * q], ya[4 * q + 1] + yb[4 * q + 1], ya[4 * q + 2] + yb[4 * q + 2],
-                        ya[4 * q + 3] + yb[4 * q + 3]);
-        *reinterpret_cast<float4*>(o1 + 4 * q) =
-            make_float4(ya[4 * q] - yb[4 * q], ya[4 * q + 1] - yb[4 * q + 1], ya[4 * q + 2] - yb[4 * q + 2],
-                        ya[4 * q + 3] - yb[4 * q + 3]);
-      } else {
-        *reinterpret_cast<float4*>(o0 + 4 * q) = make_float4(ya[4 * q], ya[4 * q + 1], ya[4 * q + 2], ya[4 * q + 3]);
-      }
-    }
-  }
-}
-
-// Software pipeline over the block's tiles t_0, t_1, ... (tensor memory holds two sets of
-// accumulators, k & 1 for tile t_k):  store t_k's operands (loaded into registers during the
-// previous tile) | forward MMAs of t_k, meanwhile the stores of t_{k-1} and the loads of
-// t_{k+1} | symbol division | inverse MMAs of t_k.
-template <int H>
-__global__ void __launch_bounds__(kTcThreads, 1) k3_zsolve_tc(TcZArgs a) {
-  using L = TcSmem<H>;
-  constexpr int N = 128 * H, NG = kTcNG, NGC = NG / 2;
+__global__ void __launch_bounds__(kTtThreads, 1) k3_zsolve_tt(TcZArgs a) {
+  using L = TtSmem<H>;
+  constexpr int N = 128 * H, NT = kTtCols;
   extern __shared__ __align__(1024) unsigned char sm[];
   float* s_lz = reinterpret_cast<float*>(sm + L::LZ);
-  float* s_lc = reinterpret_cast<float*>(sm + L::LC);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);   // matrices, forward, inverse
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + L::BAR + 24);
   int* s_abort = reinterpret_cast<int*>(sm + L::BAR + 28);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t sa = tc::smem_u32(sm + L::A), sb = tc::smem_u32(sm + L::B);
-  unsigned char* const bt = sm + L::B;
+  const int q = warp & 3, sub = warp >> 2, n = 32 * q + lane;
+  const uint32_t sa = tc::smem_u32(sm + L::A);
 
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) tc::mbar_init(&bar[i], 1);
     tc::mbar_init_fence();
     *s_abort = 0;
   }
-  for (int m = tid; m < N; m += kTcThreads) s_lz[m] = a.lamz[m];
+  for (int m = tid; m < N; m += kTtThreads) s_lz[m] = a.lamz[m];
   __syncthreads();
   if (tid == 0) {
     constexpr uint32_t bytes = 2u * H * kTcMat;
@@ -254,107 +189,119 @@ __global__ void __launch_bounds__(kTcThreads, 1) k3_zsolve_tc(TcZArgs a) {
       tc::bulk_g2s(sm + L::A + off, static_cast<const unsigned char*>(a.dmat) + off, 16384, &bar[0]);
   }
   __syncwarp();
-  if (warp == 0) tc::tmem_alloc(s_tmem, 2 * H * NG);
+  if (warp == 0) tc::tmem_alloc(s_tmem, 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *s_tmem;
+  const uint32_t t_lane = tmem + ((uint32_t)(32 * q) << 16);
   if (tid == 0 && !tc::mbar_wait(&bar[0], 0)) {
     *s_abort = 1;
     atomicOr(a.status, 4);
   }
-  const long long ncr_all = 2 * a.ncols;      // real columns
-  const size_t pitch = (size_t)ncr_all;       // floats per z row
-  const long long ntiles = (ncr_all + NG - 1) / NG;
-  const int lq = warp & 3, ch = warp >> 2;    // tensor-memory lane quarter, 32-column half
-  const uint32_t t_lane = tmem + ((uint32_t)(32 * lq) << 16) + 32 * ch;
-  auto tile_cols = [&](long long t) { return (int)min((long long)NG, ncr_all - t * NG); };
+  const long long ncr_all = 2 * a.ncols;
+  const size_t pitch = (size_t)ncr_all;
+  const long long ntiles = (ncr_all + NT - 1) / NT;
+  auto tile_cols = [&](long long t) { return (int)min((long long)NT, ncr_all - t * NT); };
 
-  TileRegs<H> regs;
+  TtRegs<H> r;
   long long t = blockIdx.x;
-  if (t < ntiles) load_tile<H>(regs, a, pitch, t * NG, tile_cols(t), warp, lane);
-  long long t_prev = -1;
-  for (int k = 0; t < ntiles; ++k, t_prev = t, t += gridDim.x) {
-    const uint32_t buf = (uint32_t)(k & 1) * (H * NG);
-    // (a) operands of tile t, per-column eigenvalue parts
-    store_tile<H>(regs, bt, warp, lane);
-    if (tid < NGC) s_lc[tid] = regs.lc;
-    tc::fence_async_smem();
+  if (t < ntiles) {
+    tt_load<H, 0>(r, a, pitch, t * NT, tile_cols(t), n, sub);
+    tt_load<H, 16>(r, a, pitch, t * NT, tile_cols(t), n, sub);
+  }
+  for (int k = 0; t < ntiles; ++k, t += gridDim.x) {
+    const long long c0 = t * NT;
+    const int ncr = tile_cols(t);
+    const float lc = r.lc;
+    tt_store_x<H>(r, t_lane, sub);
+    tc::tmem_st_wait();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (*s_abort) break;
-    // (b) forward products of tile t
     if (tid == 0) {
-      issue_products<H, true>(sa, sb, tmem + buf);
+      tt_products<H, true>(sa, tmem);
       tc::mma_commit(&bar[1]);
     }
     __syncwarp();
-    // (c) results of the previous tile, (d) loads of the next one
-    if (t_prev >= 0)
-      store_result<H>(a.spec, pitch, t_prev * NG, tile_cols(t_prev), t_lane + (buf ^ (H * NG)), lq, ch, lane);
-    const long long t_next = t + gridDim.x;
-    if (t_next < ntiles) load_tile<H>(regs, a, pitch, t_next * NG, tile_cols(t_next), warp, lane);
-    // (e) wait for the forward products, (f) divide by the symbol into the inverse operands
+    // the next tile's loads, half now (under the forward products), half under the inverse
+    const long long tn = t + gridDim.x;
+    if (tn < ntiles) tt_load<H, 0>(r, a, pitch, tn * NT, tile_cols(tn), n, sub);
     if (!tc::mbar_wait(&bar[1], k & 1)) {
       *s_abort = 1;
       atomicOr(a.status, 4);
     }
     tc::fence_after_sync();
-    {
-      const int p = 32 * lq + lane;
+    // divide by the symbol: the quotients become the inverse A operands (over the forward ones)
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        float v[32];
-        tc::tmem_ld32(t_lane + buf + h * NG, v);
-        const float lz = s_lz[H == 2 ? 2 * p + h : p];
+    for (int h = 0; h < H; ++h) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float zq[8];
+      for (int c = 0; c < 2; ++c) {
+        float v[16];
+        tc::tmem_ld16(t_lane + kTtD + h * 128 + 32 * sub + 16 * c, v);
+        uint32_t hi[8], lo[8];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {   // complex column 16 ch + 4 q + e: (re, im)
-            const float Lv = lz + s_lc[16 * ch + 4 * q + e];
-            float r;
-            if (a.mode == 0) r = __fdividef(1.0f, (Lv - a.s_eta2) * Lv + a.c0);
-            else r = (Lv == 0.0f) ? 0.0f : __fdividef(1.0f, Lv);
-            zq[2 * e] = v[8 * q + 2 * e] * r;
-            zq[2 * e + 1] = v[8 * q + 2 * e + 1] * r;
+        for (int i = 0; i < 8; ++i) {
+          float z[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int m = 32 * sub + 16 * c + 2 * i + e;
+            const float Lv = s_lz[H == 2 ? 2 * m + h : m] + lc;
+            float rr;
+            if (a.mode == 0) rr = __fdividef(1.0f, (Lv - a.s_eta2) * Lv + a.c0);
+            else rr = (Lv == 0.0f) ? 0.0f : __fdividef(1.0f, Lv);
+            z[e] = v[2 * i + e] * rr;
           }
-          uint4 hi, lo;
-          split8(zq, hi, lo);
-          const int o = b_off(p, 32 * ch + 8 * q);
-          *reinterpret_cast<uint4*>(bt + 2 * h * kTcOpB + o) = hi;
-          *reinterpret_cast<uint4*>(bt + (2 * h + 1) * kTcOpB + o) = lo;
+          split2(z[0], z[1], hi[i], lo[i]);
         }
+        tc::tmem_st8(t_lane + kTtXA + (2 * h) * 64 + 16 * sub + 8 * c, hi);
+        tc::tmem_st8(t_lane + kTtXA + (2 * h + 1) * 64 + 16 * sub + 8 * c, lo);
       }
     }
-    tc::fence_async_smem();
+    tc::tmem_st_wait();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (*s_abort) break;
-    // (g) inverse products of tile t (same accumulators), (h) wait for them
     if (tid == 0) {
-      issue_products<H, false>(sa, sb, tmem + buf);
+      tt_products<H, false>(sa, tmem);
       tc::mma_commit(&bar[2]);
     }
     __syncwarp();
+    if (tn < ntiles) tt_load<H, 16>(r, a, pitch, tn * NT, tile_cols(tn), n, sub);
     if (!tc::mbar_wait(&bar[2], k & 1)) {
       *s_abort = 1;
       atomicOr(a.status, 4);
     }
     tc::fence_after_sync();
-  }
-  // results of the last tile
-  if (!*s_abort && t_prev >= 0) {
-    const int kl = (int)((t_prev - blockIdx.x) / gridDim.x);
-    const uint32_t buf = (uint32_t)(kl & 1) * (H * NG);
-    store_result<H>(a.spec, pitch, t_prev * NG, tile_cols(t_prev), t_lane + buf, lq, ch, lane);
+    // undo the even/odd step; a warp stores 32 consecutive floats of a row
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float ya[16], yb[16];
+      tc::tmem_ld16(t_lane + kTtD + 32 * sub + 16 * c, ya);
+      if constexpr (H == 2) tc::tmem_ld16(t_lane + kTtD + 128 + 32 * sub + 16 * c, yb);
+      if (n < ncr) {
+        float* col = a.spec + c0 + n;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int j = 32 * sub + 16 * c + i;
+          if constexpr (H == 2) {
+            col[(size_t)j * pitch] = ya[i] + yb[i];
+            col[(size_t)(N - 1 - j) * pitch] = ya[i] - yb[i];
+          } else {
+            col[(size_t)j * pitch] = ya[i];
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 2 * H * NG);
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
+
 
 uint16_t bf16_bits(float f) {   // round to nearest even (finite inputs)
   uint32_t u;
@@ -406,9 +353,9 @@ cudaError_t zsolve_tc_tables(int nz, void** out) {
   if (e != cudaSuccess) return e;
   e = cudaMemcpy(*out, buf.data(), buf.size() * 2, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k3_zsolve_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<1>::BYTES);
+  e = cudaFuncSetAttribute(k3_zsolve_tt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtSmem<1>::BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k3_zsolve_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSmem<2>::BYTES);
+  return cudaFuncSetAttribute(k3_zsolve_tt<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtSmem<2>::BYTES);
 }
 
 // the z solve of a 3D FP32 spectrum: spec holds nz rows of ncols complex values
@@ -428,10 +375,10 @@ void zsolve_tc_launch(float* spec, int nz, long long ncols, int sp, int nh1, con
   a.s_eta2 = s_eta2;
   a.c0 = c0;
   a.status = status;
-  const long long tiles = (2 * ncols + kTcNG - 1) / kTcNG;
+  const long long tiles = (2 * ncols + kTtCols - 1) / kTtCols;
   const int grid = (int)std::min<long long>(tiles, sm_count());
-  if (nz == 256) k3_zsolve_tc<2><<<grid, kTcThreads, TcSmem<2>::BYTES, s>>>(a);
-  else k3_zsolve_tc<1><<<grid, kTcThreads, TcSmem<1>::BYTES, s>>>(a);
+  if (nz == 256) k3_zsolve_tt<2><<<grid, kTtThreads, TtSmem<2>::BYTES, s>>>(a);
+  else k3_zsolve_tt<1><<<grid, kTtThreads, TtSmem<1>::BYTES, s>>>(a);
 }
 
 }  // namespace ibpf
