@@ -121,7 +121,7 @@ from dataclasses import dataclass
 import numpy as np
 import scipy.fft as sfft
 
-from workloads.cases import GEOM_FLAT, GEOM_NONE, GEOM_SINUSOID, Case2D
+from workloads.cases import GEOM_FLAT, GEOM_MASK, GEOM_NONE, GEOM_SINUSOID, Case2D
 
 KAPPA = 3.0 / (2.0 * math.sqrt(2.0))   # the 3/(2 sqrt 2) factor of Eq. Cahn-Hilliard
 GAMMA0 = 1.5                           # BDF2 weight of Appendix A.1: (3/2 C^{n+1} - C_check)/dt
@@ -149,8 +149,33 @@ def wall_height(case: Case2D, x):
     raise ValueError("unknown wall kind")
 
 
+def mask_alpha(case: Case2D, x, y):
+    """MASK walls (reading R20): the cell-centre fractions alpha_c interpolated bilinearly at
+    (x, y), centres at ((i + 1/2) h, (j + 1/2) h), periodic in x1, the first and last centre
+    rows continued beyond them."""
+    A = np.asarray(case.alpha[0], dtype=np.float64)
+    ny, nx = A.shape
+    h = case.h
+    x, y = np.broadcast_arrays(np.asarray(x, np.float64), np.asarray(y, np.float64))
+    fx = x / h - 0.5
+    fy = y / h - 0.5
+    fx0 = np.floor(fx)
+    fy0 = np.floor(fy)
+    tx = fx - fx0
+    ty = fy - fy0
+    i0 = fx0.astype(np.int64) % nx
+    i1 = (i0 + 1) % nx
+    j0 = np.clip(fy0.astype(np.int64), 0, ny - 1)
+    j1 = np.clip(fy0.astype(np.int64) + 1, 0, ny - 1)
+    a = (1.0 - tx) * A[j0, i0] + tx * A[j0, i1]
+    b = (1.0 - tx) * A[j1, i0] + tx * A[j1, i1]
+    return (1.0 - ty) * a + ty * b
+
+
 def solid(case: Case2D, x, y):
     """True where (x, y) lies inside the solid."""
+    if case.geom_kind == GEOM_MASK:
+        return mask_alpha(case, x, y) < 0.5
     yw = wall_height(case, x)
     if yw is None:
         return np.zeros(np.broadcast(np.asarray(x), np.asarray(y)).shape, dtype=bool)
@@ -325,9 +350,13 @@ def build_geometry(case: Case2D) -> Geometry2D:
     p = case.params
     ii = np.arange(nx, dtype=np.float64)
     jj = np.arange(ny, dtype=np.float64)
-    alpha_c = volume_fractions(case, ii * h, jj * h)
-    alpha_u = volume_fractions(case, (ii - 0.5) * h, jj * h)
-    alpha_v = volume_fractions(case, ii * h, (np.arange(ny + 1, dtype=np.float64) - 0.5) * h)
+    if case.geom_kind == GEOM_MASK:   # the caller's fractions replace the count (R20)
+        alpha_c, alpha_u, alpha_v = (np.asarray(a, dtype=np.float64).reshape(s) for a, s in
+                                     zip(case.alpha, ((ny, nx), (ny, nx), (ny + 1, nx))))
+    else:
+        alpha_c = volume_fractions(case, ii * h, jj * h)
+        alpha_u = volume_fractions(case, (ii - 0.5) * h, jj * h)
+        alpha_v = volume_fractions(case, ii * h, (np.arange(ny + 1, dtype=np.float64) - 0.5) * h)
 
     xc = (ii + 0.5) * h
     yc = (jj + 0.5) * h

@@ -40,7 +40,7 @@ import scipy.fft as sfft
 from oracle.ib_pf2d import KAPPA, GAMMA0, MARCH_DIV, MARCH_MAX, BISECT, EPS0
 from oracle.ib_pf2d import CELL_FLUID, CELL_GHOST, CELL_SOLID
 from oracle.ib_pf2d import contact_angle_ghost, dynamic_contact_ghost, linear_exact_weights
-from workloads.cases import GEOM_FLAT, GEOM_NONE, GEOM_SPHERE, GEOM_SPHERES, Case3D
+from workloads.cases import GEOM_FLAT, GEOM_MASK, GEOM_NONE, GEOM_SPHERE, GEOM_SPHERES, Case3D
 
 NSUB3 = 16     # subgrid points per direction in 3D (reading R12)
 NAP3 = 7       # averaging points per interpolation point in 3D
@@ -61,12 +61,40 @@ def _wrap(d, L):
     return np.where(d < -0.5 * L, d + L, d)
 
 
+def mask_alpha3(case: Case3D, x, y, z):
+    """MASK walls (reading R20): alpha_c interpolated trilinearly at (x, y, z), centres at
+    ((i + 1/2) h, (j + 1/2) h, (k + 1/2) h), periodic in x and y, the first and last centre
+    planes continued beyond them."""
+    A = np.asarray(case.alpha[0], dtype=np.float64)
+    nz, ny, nx = A.shape
+    h = case.h
+    x, y, z = np.broadcast_arrays(np.asarray(x, np.float64), np.asarray(y, np.float64),
+                                  np.asarray(z, np.float64))
+    fx, fy, fz = x / h - 0.5, y / h - 0.5, z / h - 0.5
+    fx0, fy0, fz0 = np.floor(fx), np.floor(fy), np.floor(fz)
+    tx, ty, tz = fx - fx0, fy - fy0, fz - fz0
+    i0 = fx0.astype(np.int64) % nx
+    j0 = fy0.astype(np.int64) % ny
+    i1, j1 = (i0 + 1) % nx, (j0 + 1) % ny
+    k0 = np.clip(fz0.astype(np.int64), 0, nz - 1)
+    k1 = np.clip(fz0.astype(np.int64) + 1, 0, nz - 1)
+
+    def plane(k):
+        a = (1.0 - tx) * A[k, j0, i0] + tx * A[k, j0, i1]
+        b = (1.0 - tx) * A[k, j1, i0] + tx * A[k, j1, i1]
+        return (1.0 - ty) * a + ty * b
+
+    return (1.0 - tz) * plane(k0) + tz * plane(k1)
+
+
 def solid3(case: Case3D, x, y, z, sph=None):
     """True where (x, y, z) lies inside the solid."""
     x, y, z = np.broadcast_arrays(np.asarray(x, np.float64), np.asarray(y, np.float64),
                                   np.asarray(z, np.float64))
     if case.geom_kind == GEOM_NONE:
         return np.zeros(x.shape, dtype=bool)
+    if case.geom_kind == GEOM_MASK:
+        return mask_alpha3(case, x, y, z) < 0.5
     if case.geom_kind == GEOM_FLAT:
         return z < case.geom_p[0]
     sph = _spheres(case) if sph is None else sph
@@ -325,10 +353,15 @@ def build_geometry3(case: Case3D) -> Geometry3D:
     nx, ny, nz, h = case.nx, case.ny, case.nz, case.h
     p = case.params
     sph = _spheres(case)
-    alpha_c = volume_fractions3(case, (0.0, 0.0, 0.0), (nz, ny, nx), sph)
-    alpha_u = volume_fractions3(case, (-0.5, 0.0, 0.0), (nz, ny, nx), sph)
-    alpha_v = volume_fractions3(case, (0.0, -0.5, 0.0), (nz, ny, nx), sph)
-    alpha_w = volume_fractions3(case, (0.0, 0.0, -0.5), (nz + 1, ny, nx), sph)
+    if case.geom_kind == GEOM_MASK:   # the caller's fractions replace the count (R20)
+        alpha_c, alpha_u, alpha_v, alpha_w = (
+            np.asarray(a, dtype=np.float64).reshape(s) for a, s in
+            zip(case.alpha, ((nz, ny, nx), (nz, ny, nx), (nz, ny, nx), (nz + 1, ny, nx))))
+    else:
+        alpha_c = volume_fractions3(case, (0.0, 0.0, 0.0), (nz, ny, nx), sph)
+        alpha_u = volume_fractions3(case, (-0.5, 0.0, 0.0), (nz, ny, nx), sph)
+        alpha_v = volume_fractions3(case, (0.0, -0.5, 0.0), (nz, ny, nx), sph)
+        alpha_w = volume_fractions3(case, (0.0, 0.0, -0.5), (nz + 1, ny, nx), sph)
     cls = classify3(case)
     gk, gj, gi = np.nonzero(cls == CELL_GHOST)
     ng = len(gi)

@@ -18,6 +18,7 @@ Wall descriptors (the solid is the set where the predicate is true)
   GEOM_FLAT      x2 < p0
   GEOM_SINUSOID  x2 < p0 + p1 * sin(2 pi p2 x1)
   GEOM_NONE      no solid anywhere (free droplet; used by closed-form tests)
+  GEOM_MASK      the solid given by caller-supplied volume fractions (Case.alpha), 2D and 3D
 """
 from __future__ import annotations
 
@@ -29,6 +30,7 @@ import numpy as np
 GEOM_FLAT = 0
 GEOM_SINUSOID = 1
 GEOM_NONE = 3
+GEOM_MASK = 6   # alpha = (alpha_c, alpha_u, alpha_v[, alpha_w]) arrays supplied with the case
 
 # field ids shared by the C-ABI, the binding and the tests (inputs/outputs only)
 FIELDS_2D = ("C", "C_old", "u", "u_old", "v", "v_old", "Hu", "Hv", "P", "P_old")
@@ -74,6 +76,7 @@ class Case2D:
     drop_r: float
     params: Params
     steps: int
+    alpha: tuple = ()            # GEOM_MASK: (alpha_c, alpha_u, alpha_v) arrays
 
     @property
     def h(self) -> float:
@@ -246,6 +249,7 @@ class Case3D:
     params: Params
     steps: int
     spheres: tuple = ()          # ((cx, cy, cz, r), ...) for GEOM_SPHERES
+    alpha: tuple = ()            # GEOM_MASK: (alpha_c, alpha_u, alpha_v, alpha_w) arrays
 
     @property
     def h(self) -> float:
