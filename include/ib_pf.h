@@ -110,10 +110,16 @@ typedef enum { IB_PF_NS_EXPLICIT = 0, IB_PF_NS_SEMI_IMPLICIT = 1 } ib_pf_ns_sche
  * against it).  FLAT: x2 < p[0] (2D), z < p[0] (3D).  SINUSOID (2D): x2 < p[0] + p[1]
  * sin(2 pi p[2] x1).  SPHERE (3D): |x - (p[0], p[1], p[2])| < p[3].  SPHERES (3D): the union
  * of the spheres (cx, cy, cz, r) of ib_pf_geometry.spheres.  NONE: no solid.  Sphere
- * distances take the nearest periodic image in x and y. */
+ * distances take the nearest periodic image in x and y.
+ * MASK (2D and 3D): a solid with no analytic form, given by its volume fractions
+ * (ib_pf_geometry.alpha), which replace the subgrid count of Sec. 4.1.1; the solid is where
+ * the cell-centre fractions, interpolated linearly between cell centres (bilinear in 2D,
+ * trilinear in 3D; periodic in x (and y), the first and last centre rows (planes) continued
+ * beyond them), are below 1/2, which decides the solid cell centres and the intersect
+ * points of Sec. 4.1.2. */
 typedef enum {
   IB_PF_WALL_FLAT = 0, IB_PF_WALL_SINUSOID = 1, IB_PF_WALL_NONE = 3, IB_PF_WALL_SPHERE = 4,
-  IB_PF_WALL_SPHERES = 5
+  IB_PF_WALL_SPHERES = 5, IB_PF_WALL_MASK = 6
 } ib_pf_wall_kind;
 
 typedef struct {
@@ -128,6 +134,12 @@ typedef struct {
   const double* spheres;   /* SPHERES: host array of n_spheres x (cx, cy, cz, r), copied by
                               ib_pf_init_geometry (the caller keeps ownership); else NULL */
   int n_spheres;
+  const double* alpha;     /* MASK: host array of the fluid volume fractions, in [0, 1], of
+                              the control volumes in the layout of the alpha tables
+                              (IB_PF_T_ALPHA_*), back to back: 2D alpha_c (ny x nx), alpha_u
+                              (ny x nx), alpha_v ((ny+1) x nx); 3D alpha_c, alpha_u, alpha_v
+                              (nz x ny x nx each), alpha_w ((nz+1) x ny x nx).  Copied by
+                              ib_pf_init_geometry (the caller keeps ownership); else NULL. */
 } ib_pf_geometry;
 
 /* Nondimensional parameters as defined in Sec. 5.1 (Re, Ca, Cn) and Sec. 5.3 (Pe);

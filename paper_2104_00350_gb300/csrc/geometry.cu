@@ -17,9 +17,27 @@ __device__ __forceinline__ double wall_height(const WallDev& w, double x) {
   return w.p0;
 }
 
+// MASK: the cell-centre fractions interpolated bilinearly at (x, y); centres (i + 1/2) h,
+// periodic in x, the first and last centre rows continued beyond them
+__device__ __forceinline__ double mask_alpha(const WallDev& w, double x, double y) {
+  const double fx = x / w.mh - 0.5, fy = y / w.mh - 0.5;
+  const double fx0 = floor(fx), fy0 = floor(fy);
+  const double tx = fx - fx0, ty = fy - fy0;
+  int i0 = (int)fx0 % w.mnx;
+  if (i0 < 0) i0 += w.mnx;
+  const int i1 = (i0 + 1) % w.mnx;
+  const int j0 = min(max((int)fy0, 0), w.mny - 1), j1 = min(max((int)fy0 + 1, 0), w.mny - 1);
+  const double* r0 = w.mask + (size_t)j0 * w.mnx;
+  const double* r1 = w.mask + (size_t)j1 * w.mnx;
+  const double a = (1.0 - tx) * r0[i0] + tx * r0[i1];
+  const double b = (1.0 - tx) * r1[i0] + tx * r1[i1];
+  return (1.0 - ty) * a + ty * b;
+}
+
 // Sec. 4.1.1: "inside or outside the solid wall"
 __device__ __forceinline__ bool is_solid(const WallDev& w, double x, double y) {
   if (w.kind == IB_PF_WALL_NONE) return false;
+  if (w.kind == IB_PF_WALL_MASK) return mask_alpha(w, x, y) < 0.5;
   return y < wall_height(w, x);
 }
 
@@ -342,9 +360,22 @@ cudaError_t geometry_init(Instance& in, cudaStream_t s, std::string& err) {
   IBPF_TRY(dalloc(&t.cmap, ncell));
   dim3 blk(32, 8);
   const double hs = in.h / kNsub;
-  k_alpha<<<dim3((nx + 31) / 32, (ny + 7) / 8), blk, 0, s>>>(in.wall, nx, ny, 0, in.h, hs, t.alpha_c);
-  k_alpha<<<dim3((nx + 31) / 32, (ny + 7) / 8), blk, 0, s>>>(in.wall, nx, ny, 1, in.h, hs, t.alpha_u);
-  k_alpha<<<dim3((nx + 31) / 32, (ny + 8) / 8), blk, 0, s>>>(in.wall, nx, ny + 1, 2, in.h, hs, t.alpha_v);
+  if (in.wall.kind == IB_PF_WALL_MASK) {
+    // the caller's fractions (validated on the host); the predicate reads alpha_c
+    const double* a = in.geom.alpha;
+    IBPF_TRY(cudaMemcpyAsync(t.alpha_c, a, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    IBPF_TRY(cudaMemcpyAsync(t.alpha_u, a + ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    IBPF_TRY(cudaMemcpyAsync(t.alpha_v, a + 2 * ncell, sizeof(double) * (ncell + nx), cudaMemcpyHostToDevice, s));
+    IBPF_TRY(cudaStreamSynchronize(s));
+    in.wall.mask = t.alpha_c;
+    in.wall.mnx = nx;
+    in.wall.mny = ny;
+    in.wall.mh = in.h;
+  } else {
+    k_alpha<<<dim3((nx + 31) / 32, (ny + 7) / 8), blk, 0, s>>>(in.wall, nx, ny, 0, in.h, hs, t.alpha_c);
+    k_alpha<<<dim3((nx + 31) / 32, (ny + 7) / 8), blk, 0, s>>>(in.wall, nx, ny, 1, in.h, hs, t.alpha_u);
+    k_alpha<<<dim3((nx + 31) / 32, (ny + 8) / 8), blk, 0, s>>>(in.wall, nx, ny + 1, 2, in.h, hs, t.alpha_v);
+  }
   k_solid_centres<<<dim3((nx + 31) / 32, (ny + 7) / 8), blk, 0, s>>>(in.wall, nx, ny, in.h, t.solidc);
   IBPF_TRY(cudaGetLastError());
   int *gflag = nullptr, *fuflag = nullptr, *fvflag = nullptr, *idx = nullptr, *cnt = nullptr;

@@ -45,10 +45,33 @@ __device__ __forceinline__ int bin_of(const WallDev& w, double x, double y, doub
   return (bz * s.nb[1] + by) * s.nb[0] + bx;
 }
 
+// MASK: the cell-centre fractions interpolated trilinearly at (x, y, z); centres (i + 1/2) h,
+// periodic in x and y, the first and last centre planes continued beyond them
+__device__ double mask_alpha3(const WallDev& w, double x, double y, double z) {
+  const double fx = x / w.mh - 0.5, fy = y / w.mh - 0.5, fz = z / w.mh - 0.5;
+  const double fx0 = floor(fx), fy0 = floor(fy), fz0 = floor(fz);
+  const double tx = fx - fx0, ty = fy - fy0, tz = fz - fz0;
+  int i0 = (int)fx0 % w.mnx, j0 = (int)fy0 % w.mny;
+  if (i0 < 0) i0 += w.mnx;
+  if (j0 < 0) j0 += w.mny;
+  const int i1 = (i0 + 1) % w.mnx, j1 = (j0 + 1) % w.mny;
+  const int k0 = min(max((int)fz0, 0), w.mnz - 1), k1 = min(max((int)fz0 + 1, 0), w.mnz - 1);
+  const size_t nxy = (size_t)w.mnx * w.mny;
+  const double* p0 = w.mask + (size_t)k0 * nxy;
+  const double* p1 = w.mask + (size_t)k1 * nxy;
+  auto plane = [&](const double* p) {
+    const double a = (1.0 - tx) * p[(size_t)j0 * w.mnx + i0] + tx * p[(size_t)j0 * w.mnx + i1];
+    const double b = (1.0 - tx) * p[(size_t)j1 * w.mnx + i0] + tx * p[(size_t)j1 * w.mnx + i1];
+    return (1.0 - ty) * a + ty * b;
+  };
+  return (1.0 - tz) * plane(p0) + tz * plane(p1);
+}
+
 // Sec. 4.1.1: is (x, y, z) inside the solid?
 __device__ bool is_solid3(const WallDev& w, double x, double y, double z) {
   if (w.kind == IB_PF_WALL_NONE) return false;
   if (w.kind == IB_PF_WALL_FLAT) return z < w.p0;
+  if (w.kind == IB_PF_WALL_MASK) return mask_alpha3(w, x, y, z) < 0.5;
   const int b = bin_of(w, x, y, z);
   for (int q = w.ss.bstart[b]; q < w.ss.bstart[b + 1]; ++q)
     if (in_sphere(w, w.ss.sph[w.ss.blist[q]], x, y, z)) return true;
@@ -537,10 +560,25 @@ cudaError_t geometry3_init(Instance& in, const double* h_spheres, int n_spheres,
   IBPF_TRY3(dalloc3(&t.solidc, ncell));
   IBPF_TRY3(dalloc3(&t.cmap, ncell));
   const int T = 128;
-  k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, 0.0, 0.0, 0.0, h, t.alpha_c);
-  k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, -0.5, 0.0, 0.0, h, t.alpha_u);
-  k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, 0.0, -0.5, 0.0, h, t.alpha_v);
-  k_alpha3<<<blocks_for(nwf, T), T, 0, s>>>(w, nx, ny, nz + 1, 0.0, 0.0, -0.5, h, t.alpha_w);
+  if (w.kind == IB_PF_WALL_MASK) {
+    // the caller's fractions (validated on the host); the predicate reads alpha_c
+    const double* a = in.geom.alpha;
+    IBPF_TRY3(cudaMemcpyAsync(t.alpha_c, a, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    IBPF_TRY3(cudaMemcpyAsync(t.alpha_u, a + ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    IBPF_TRY3(cudaMemcpyAsync(t.alpha_v, a + 2 * ncell, sizeof(double) * ncell, cudaMemcpyHostToDevice, s));
+    IBPF_TRY3(cudaMemcpyAsync(t.alpha_w, a + 3 * ncell, sizeof(double) * nwf, cudaMemcpyHostToDevice, s));
+    IBPF_TRY3(cudaStreamSynchronize(s));
+    w.mask = t.alpha_c;
+    w.mnx = nx;
+    w.mny = ny;
+    w.mnz = nz;
+    w.mh = h;
+  } else {
+    k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, 0.0, 0.0, 0.0, h, t.alpha_c);
+    k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, -0.5, 0.0, 0.0, h, t.alpha_u);
+    k_alpha3<<<blocks_for(ncell, T), T, 0, s>>>(w, nx, ny, nz, 0.0, -0.5, 0.0, h, t.alpha_v);
+    k_alpha3<<<blocks_for(nwf, T), T, 0, s>>>(w, nx, ny, nz + 1, 0.0, 0.0, -0.5, h, t.alpha_w);
+  }
   k_solid_centres3<<<blocks_for(ncell, 256), 256, 0, s>>>(w, nx, ny, nz, h, t.solidc);
   IBPF_TRY3(cudaGetLastError());
   uint8_t *gflag = nullptr, *fflag = nullptr;

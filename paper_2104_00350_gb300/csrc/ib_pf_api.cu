@@ -122,6 +122,20 @@ ib_pf_status fail(ib_pf_ctx* c, ib_pf_status st, const std::string& msg) {
   return st;
 }
 
+// a MASK geometry's volume fractions: present, finite, in [0, 1]
+bool mask_ok(const double* a, size_t n, std::string& why) {
+  if (!a) {
+    why = "MASK needs the volume fractions (ib_pf_geometry.alpha)";
+    return false;
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (!(a[i] >= 0.0 && a[i] <= 1.0)) {
+      why = "MASK volume fraction " + std::to_string(i) + " is not in [0, 1]";
+      return false;
+    }
+  return true;
+}
+
 ib_pf_status validate3(const ib_pf_grid& g, const ib_pf_geometry& w, std::string& why) {
   for (int a = 0; a < 3; ++a) {
     if (!is_pow2(g.n[a]) || g.n[a] < 8 || g.n[a] > 1024) {
@@ -136,9 +150,13 @@ ib_pf_status validate3(const ib_pf_grid& g, const ib_pf_geometry& w, std::string
     return IB_PF_E_ARG;
   }
   if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SPHERE && w.kind != IB_PF_WALL_SPHERES &&
-      w.kind != IB_PF_WALL_NONE) {
-    why = "3D wall kind must be FLAT, SPHERE, SPHERES or NONE";
+      w.kind != IB_PF_WALL_NONE && w.kind != IB_PF_WALL_MASK) {
+    why = "3D wall kind must be FLAT, SPHERE, SPHERES, MASK or NONE";
     return IB_PF_E_ARG;
+  }
+  if (w.kind == IB_PF_WALL_MASK) {
+    const size_t nc = (size_t)g.n[0] * g.n[1] * g.n[2];
+    if (!mask_ok(w.alpha, 4 * nc + (size_t)g.n[0] * g.n[1], why)) return IB_PF_E_ARG;
   }
   if (w.kind == IB_PF_WALL_SPHERE && !(w.p[3] > 0)) { why = "sphere radius must be positive"; return IB_PF_E_ARG; }
   if (w.kind == IB_PF_WALL_SPHERES) {
@@ -202,10 +220,12 @@ ib_pf_status validate(const ib_pf_grid& g, const ib_pf_geometry& w, const ib_pf_
   if (!(g.L[0] > 0) || !(g.L[1] > 0)) { why = "domain lengths must be positive"; return IB_PF_E_ARG; }
   const double hx = g.L[0] / nx, hy = g.L[1] / ny;
   if (std::fabs(hx - hy) > 1e-12 * hx) { why = "cells must be square (lx/nx == ly/ny)"; return IB_PF_E_ARG; }
-  if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SINUSOID && w.kind != IB_PF_WALL_NONE) {
+  if (w.kind != IB_PF_WALL_FLAT && w.kind != IB_PF_WALL_SINUSOID && w.kind != IB_PF_WALL_NONE &&
+      w.kind != IB_PF_WALL_MASK) {
     why = "unknown wall kind";
     return IB_PF_E_ARG;
   }
+  if (w.kind == IB_PF_WALL_MASK && !mask_ok(w.alpha, (size_t)(3 * ny + 1) * nx, why)) return IB_PF_E_ARG;
   if (p.precision == IB_PF_FP32_3XBF16) {
     why = "FP32_3XBF16 (tensor-core z solve) is built for 3D contexts";
     return IB_PF_E_UNSUPPORTED;
@@ -389,6 +409,8 @@ ib_pf_status ib_pf_init_geometry(ib_pf_ctx** out, int n_instances, const ib_pf_g
     std::string gerr;
     const cudaError_t ge = in.dim == 3 ? geometry3_init(in, geoms[k].spheres, geoms[k].n_spheres, ctx->work, gerr)
                                        : geometry_init(in, ctx->work, gerr);
+    in.geom.alpha = nullptr;   // the caller's MASK fractions are copied; drop the pointer
+    in.geom.spheres = nullptr;
     if (ge != cudaSuccess) {
       ctx->err = "geometry: " + gerr;
       return bail(IB_PF_E_CUDA);

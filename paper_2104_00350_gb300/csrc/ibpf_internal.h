@@ -42,6 +42,10 @@ struct WallDev {       // wall predicate parameters as the device sees them
   double p0, p1, w;    // w = (2 pi) * p[2]
   double lx = 0, ly = 0, lz = 0;   // 3D: box (periodic images in x and y)
   SphereSet ss;                    // 3D SPHERE / SPHERES
+  // MASK: the cell-centre fractions (the instance's alpha_c table) and the grid they live on
+  const double* mask = nullptr;
+  int mnx = 0, mny = 0, mnz = 0;
+  double mh = 0;
 };
 
 // geometry tables of one instance (device pointers, FP64 / int)

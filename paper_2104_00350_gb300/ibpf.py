@@ -20,7 +20,7 @@ FP64, FP32, FP32_3XBF16 = 0, 1, 2   # ib_pf_precision
 CH_SEMI_IMPLICIT, CH_EXPLICIT = 0, 1
 W_LINEAR, W_IDW = 0, 1            # ib_pf_weights
 NS_EXPLICIT, NS_SEMI_IMPLICIT = 0, 1   # ib_pf_ns_scheme
-WALL_FLAT, WALL_SINUSOID, WALL_NONE, WALL_SPHERE, WALL_SPHERES = 0, 1, 3, 4, 5
+WALL_FLAT, WALL_SINUSOID, WALL_NONE, WALL_SPHERE, WALL_SPHERES, WALL_MASK = 0, 1, 3, 4, 5, 6
 (F_C, F_C_OLD, F_U, F_U_OLD, F_V, F_V_OLD, F_HU, F_HV, F_P, F_P_OLD, F_PHI, F_Q, F_RHS_P,
  F_C_LO, F_C_OLD_LO, F_W, F_W_OLD, F_HW, F_C_I) = range(19)
 FIELD_IDS = {"C": F_C, "C_old": F_C_OLD, "u": F_U, "u_old": F_U_OLD, "v": F_V, "v_old": F_V_OLD,
@@ -46,7 +46,8 @@ class Grid(ct.Structure):
 
 class Geometry(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("p", ct.c_double * 8),
-                ("spheres", ct.POINTER(ct.c_double)), ("n_spheres", ct.c_int)]
+                ("spheres", ct.POINTER(ct.c_double)), ("n_spheres", ct.c_int),
+                ("alpha", ct.POINTER(ct.c_double))]
 
 
 PARAM_NAMES = ("Re", "Ca", "Cn", "Pe", "S", "rho_ratio", "mu_ratio", "theta_deg", "l_s", "mu_f",
@@ -261,18 +262,25 @@ def make_grid3(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float) -> Gr
     return g
 
 
-def make_geometry(kind: int, p, spheres=()) -> Geometry:
-    """spheres: (cx, cy, cz, r) rows for WALL_SPHERES; the array stays referenced by the
-    returned object, and ib_pf_init_geometry copies it."""
+def make_geometry(kind: int, p, spheres=(), alpha=()) -> Geometry:
+    """spheres: (cx, cy, cz, r) rows for WALL_SPHERES; alpha: the volume-fraction arrays of
+    WALL_MASK (alpha_c, alpha_u, alpha_v[, alpha_w]), concatenated here.  The arrays stay
+    referenced by the returned object, and ib_pf_init_geometry copies them."""
     w = Geometry()
     w.kind = kind
     for k, x in enumerate(p):
         w.p[k] = float(x)
+    keep = []
     if len(spheres):
         arr = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
-        w._keep = arr
+        keep.append(arr)
         w.spheres = arr.ctypes.data_as(ct.POINTER(ct.c_double))
         w.n_spheres = arr.shape[0]
+    if len(alpha):
+        arr = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).ravel() for a in alpha]))
+        keep.append(arr)
+        w.alpha = arr.ctypes.data_as(ct.POINTER(ct.c_double))
+    w._keep = keep
     return w
 
 
@@ -486,7 +494,8 @@ def solver_from_cases(cases, precision: int = FP64, stream: int = 0) -> Solver:
     import of callers)."""
     grids = [make_grid3(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz) if hasattr(c, "nz")
              else make_grid(c.nx, c.ny, c.lx, c.ly) for c in cases]
-    geoms = [make_geometry(c.geom_kind, c.geom_p, getattr(c, "spheres", ())) for c in cases]
+    geoms = [make_geometry(c.geom_kind, c.geom_p, getattr(c, "spheres", ()), getattr(c, "alpha", ()))
+             for c in cases]
     params = [make_params(precision, getattr(c.params, "ch_scheme", CH_SEMI_IMPLICIT),
                           getattr(c.params, "weights", W_LINEAR),
                           getattr(c.params, "ns_scheme", NS_EXPLICIT),

@@ -141,3 +141,29 @@ def test_split_bf16_form_limits_checked_on_host(lib):
     with pytest.raises(lib.IbPfError) as ei:
         lib.ib_pf_init_geometry(g, w, p)
     assert ei.value.status == lib.E_ARG
+
+
+def test_mask_fractions_checked_on_host(lib):
+    import numpy as np
+    g, w, p = _args(lib)
+    w[0] = lib.make_geometry(lib.WALL_MASK, [])                       # no fractions
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_ARG
+    nx, ny = 128, 64
+    bad = [np.ones((ny, nx)), np.ones((ny, nx)), np.ones((ny + 1, nx))]
+    bad[1][3, 5] = 1.5                                                # out of [0, 1]
+    w[0] = lib.make_geometry(lib.WALL_MASK, [], alpha=bad)
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g, w, p)
+    assert ei.value.status == lib.E_ARG
+    assert "MASK" in lib.ib_pf_last_error(None)
+    g3, w3, p3 = _args3(lib)
+    n = 32
+    bad3 = [np.ones((n, n, n))] * 3 + [np.ones((n + 1, n, n))]
+    bad3[3] = bad3[3].copy()
+    bad3[3][0, 0, 0] = np.nan                                         # not finite
+    w3[0] = lib.make_geometry(lib.WALL_MASK, [], alpha=bad3)
+    with pytest.raises(lib.IbPfError) as ei:
+        lib.ib_pf_init_geometry(g3, w3, p3)
+    assert ei.value.status == lib.E_ARG
