@@ -2,6 +2,8 @@
 
     python -m paper_2104_00350_gb300.run --case sphere --n 128 --steps 2 --precision fp32 [--explicit]
 
+``--precision fp32_3xbf16`` runs the split-BF16 tensor-core z solve (3D cases, n = 128 or 256).
+
 Cases: ``sphere`` (droplet on a sphere, n^3), ``porous`` (droplet over a sphere packing,
 n^3), ``sinusoid`` (the six 512 x 256 sinusoidal-wall runs), ``ensemble`` (the 64-instance
 2D ensemble).  ``--explicit`` selects the explicit Cahn-Hilliard variant (Eq. ExpCH).
@@ -27,14 +29,15 @@ def main(argv=None):
     ap.add_argument("--case", choices=("sphere", "porous", "sinusoid", "ensemble"), default="sphere")
     ap.add_argument("--n", type=int, default=128, help="cells per axis (3D cases)")
     ap.add_argument("--steps", type=int, default=2)
-    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--precision", choices=("fp32", "fp64", "fp32_3xbf16"), default="fp32",
+                    help="fp32_3xbf16: the tensor-core z solve (3D, n = 128 or 256)")
     ap.add_argument("--explicit", action="store_true", help="explicit Cahn-Hilliard variant")
     args = ap.parse_args(argv)
     from paper_2104_00350_gb300 import build
     build.build()
     from paper_2104_00350_gb300 import ibpf
     from workloads import cases as W
-    prec = ibpf.FP64 if args.precision == "fp64" else ibpf.FP32
+    prec = {"fp64": ibpf.FP64, "fp32": ibpf.FP32, "fp32_3xbf16": ibpf.FP32_3XBF16}[args.precision]
     dt = np.float64 if prec == ibpf.FP64 else np.float32
     if args.case in ("sphere", "porous"):
         case = W.sphere_case(args.n) if args.case == "sphere" else W.porous_case(args.n)

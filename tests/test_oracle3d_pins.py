@@ -241,3 +241,24 @@ def test_explicit_update_conserves_sum_before_fill_3d():
     st = W.random_state3d(case, seed=9)
     C_pre = O3.ch_explicit3(case, geo, st)
     assert abs(C_pre.sum() - st["C"].sum()) <= 1e-13 * np.abs(st["C"]).sum()
+
+
+def test_face_lists_on_flat_wall_by_hand():
+    # 16 x 8 x 16 cells of h = 1/8 with the wall at z = 0.3: plane k = 0 solid, plane 1
+    # (centres at z = 0.1875) solid with fluid above, so every cell of it is a ghost; plane 2
+    # fluid.  Listed faces (fluid fraction below 1, touching a ghost), derived by hand: all
+    # x- and y-faces of plane 1 (alpha = 0), the z-faces of plane 1 (between plane 0 and the
+    # ghosts, alpha_w = 0) and of plane 2 (between the ghosts and the fluid: of the 16 subgrid
+    # levels (c + 1/2) h/16 above z = 0.1875, the two with c >= 14 lie above the wall, so
+    # alpha_w = 2/16).
+    case = W.flat_wall_case3d(nx=16, ny=8, nz=16, wall_z=0.3)
+    geo = O3.build_geometry3(case)
+    nxy = 16 * 8
+    assert case.h == 0.125
+    assert np.array_equal(geo.gcell, np.arange(nxy) + nxy)
+    assert np.array_equal(np.sort(geo.fu), np.arange(nxy) + nxy)
+    assert np.array_equal(np.sort(geo.fv), np.arange(nxy) + nxy)
+    assert np.array_equal(np.sort(geo.fw), np.r_[np.arange(nxy) + nxy, np.arange(nxy) + 2 * nxy])
+    assert np.all(geo.alpha_w[1] == 0.0) and np.all(geo.alpha_w[2] == 2.0 / 16.0)
+    assert np.all(geo.n == np.array([0.0, 0.0, 1.0]))
+    assert np.allclose(geo.dn, 0.3 - 0.1875, atol=1e-14)
