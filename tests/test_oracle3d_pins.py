@@ -11,7 +11,10 @@
 * geometry: flat-wall fractions exact, sphere fractions against the sphere's volume,
   intersect points on the sphere, normals radial to O(h), x <-> y symmetry of a centred
   sphere;
-* the vector slip formula against the 2D one where the normal lies in a plane.
+* the vector slip formula against the 2D one where the normal lies in a plane, and its
+  closed-form cases (no penetration at I, no slip, free slip, the slip-length law) for
+  normals in any direction;
+* the re-interpolated face lists of a flat wall, derived by hand.
 """
 import math
 
@@ -262,3 +265,33 @@ def test_face_lists_on_flat_wall_by_hand():
     assert np.all(geo.alpha_w[1] == 0.0) and np.all(geo.alpha_w[2] == 2.0 / 16.0)
     assert np.all(geo.n == np.array([0.0, 0.0, 1.0]))
     assert np.allclose(geo.dn, 0.3 - 0.1875, atol=1e-14)
+
+
+def test_slip_ghost3_special_cases_for_any_normal():
+    # Eqs. NoPenetration and UpdateVtan in vector form for normals in any direction: the
+    # normal velocity interpolated linearly between G and M vanishes at I; l_s = 0 gives
+    # u_G = -u_M / gamma; l_s -> inf keeps the tangential vector; in general
+    # V_tI / l_s = (V_tM - V_tG) / ((gamma + 1) dn) with V_tI = (gamma V_tG + V_tM)/(gamma + 1).
+    rng = np.random.default_rng(12)
+    ng = 60
+    n = rng.standard_normal((ng, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    uM, vM, wM = rng.standard_normal((3, ng))
+    gamma = rng.uniform(1.2, 3.0, ng)
+    dn = rng.uniform(0.002, 0.01, ng)
+    VM = np.stack([uM, vM, wM], axis=1)
+    VnM = (VM * n).sum(axis=1)
+    VtM = VM - VnM[:, None] * n
+    for ls in (0.0, 0.004, 0.03, 1e30):
+        case = W.flat_wall_case3d(l_s=ls)
+        VG = np.stack(O3.slip_ghost3(case, uM, vM, wM, n, gamma, dn), axis=1)
+        VnG = (VG * n).sum(axis=1)
+        VtG = VG - VnG[:, None] * n
+        assert np.abs((gamma * VnG + VnM) / (gamma + 1.0)).max() < 1e-12
+        if ls == 0.0:
+            assert np.allclose(VG, -VM / gamma[:, None], atol=1e-14)
+        elif ls > 1e20:
+            assert np.allclose(VtG, VtM, atol=1e-12)
+        else:
+            VtI = (gamma[:, None] * VtG + VtM) / (gamma[:, None] + 1.0)
+            assert np.allclose(VtI / ls, (VtM - VtG) / ((gamma[:, None] + 1.0) * dn[:, None]), rtol=1e-10, atol=1e-10)
