@@ -61,3 +61,26 @@ def test_traffic_lookup_requires_matching_kernel_sources(tmp_path, monkeypatch):
     assert bench.read_traffic("predict", "fp32", "w") == 123.0
     assert bench.read_traffic("correct", "fp32", "w") is None     # taken on other sources
     assert bench.read_traffic("predict", "fp64", "w") is None     # no capture
+
+
+def test_tensor_core_solve_reports_its_tensor_rate():
+    # 256^3: 2 x 256 rows x 130 padded complex columns of the half spectrum = 66560 real
+    # columns; each takes, forward and inverse, 2 products of a 128 x 128 matrix (after the
+    # even/odd step) in 3 split parts: 66560 x 2 x 2 x 3 x 2 x 128^2 flops
+    flops = bench.tc_zsolve_flops(256, 256, 256)
+    assert flops == 66560 * 2 * 2 * 3 * 2 * 128 * 128
+    assert bench.tc_zsolve_flops(128, 128, 128) == (2 * 128 * 66) * 2 * 1 * 3 * 2 * 128 * 128
+
+    class C3:
+        nx = ny = nz = 256
+
+    cells = 256 ** 3
+    ktot = {"predict": 3.0, "z_solve_tc": 1.0}          # ms over 10 steps, 2 launches per step
+    kcount = {"predict": 10, "z_solve_tc": 20}
+    r = bench.roofline(ktot, kcount, 10, cells, 4, C3, 6000.0, "measured", "fp32_3xbf16",
+                       bench.KERNEL_STEP_WORDS_3D, workload="sphere_256", dim=3)
+    e = r["kernels"]["z_solve_tc"]
+    tp, _ = bench.measured_bf16_peak()
+    assert math.isclose(e["tensor_TFLOPs"], round(flops * 20 / 1e-3 / 1e12, 1), rel_tol=1e-9)
+    assert math.isclose(e["tensor_frac"], round(flops * 20 / 1e-3 / 1e12 / tp, 4), rel_tol=1e-9)
+    assert "hbm_frac" in e                                # the same words as the FFT solve
