@@ -14,10 +14,11 @@ Pe = 1e4, FP32 form.  One bench step is one full time step (a1..a8) of the 134M 
   roofline  dominant kernel of a second, event-instrumented pass over the same steps, with
             the per-kernel table (stencil kernels: algorithmic bytes per cell; ghost-cell
             gathers and face kernels: algorithmic bytes per ghost / face).
-  workloads_3d / workloads_2d: the 256^3 droplet on a sphere (FP32, FP64, explicit
-            Cahn-Hilliard variant), the six 512 x 256 sinusoidal-wall runs (FP32, FP64,
-            explicit variant) and the 64-instance batched FP32 ensemble, each with its
-            per-kernel roofline table.
+  workloads_3d / workloads_2d: the 256^3 droplet on a sphere (FP32, FP32_3XBF16, FP64,
+            explicit Cahn-Hilliard variant), the six 512 x 256 sinusoidal-wall runs (FP32,
+            FP64, explicit variant), the 64-instance batched FP32 ensemble and single large
+            2D grids (2048 x 1024, 4096 x 2048, FP32), each with its per-kernel roofline
+            table.
   cpu_baseline / --impl reference: the FP64 CPU oracle (test infrastructure) on a bounded
             sample of the headline workload: the same packing and parameters on a 32^3 grid,
             one oracle process per host core, each advancing its own copy.
@@ -149,6 +150,8 @@ def parse_args():
     ap.add_argument("--no-explicit", action="store_true",
                     help="skip the explicit Cahn-Hilliard variant of the 2D workload")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D workloads")
+    ap.add_argument("--no-2d-large", action="store_true",
+                    help="skip the single large 2D grids (2048 x 1024, 4096 x 2048)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     ap.add_argument("--soak-seconds", type=float, default=1.0,
                     help="busy GPU time before the timed region so clocks settle")
@@ -716,6 +719,36 @@ def run_2d(args, ibpf, W, torch, stream, tm, peak, peak_kind, dist, world):
             "gpu_launches": int(es.query(ibpf.Q_LAUNCHES)) * esteps,
             "workload": "ensemble_2d(64), PCG64 seed 2104, sinusoidal walls", "roofline": eroof}
         es.close()
+    if not args.no_2d_large:
+        # single large 2D grids (the sinusoidal wall with Cn and dt scaled with h), FP32, state
+        # larger than L2: the HBM fractions of the 2D kernels outside the batched setting
+        for nx, ny in ((2048, 1024), (4096, 2048)):
+            name = f"sinusoid_{nx}x{ny}_fp32"
+            try:
+                c = W.sinusoid_wall_512x256(45.0, 0.01, nx=nx, ny=ny)
+                ls = ibpf.solver_from_cases([c], ibpf.FP32, stream=stream.cuda_stream)
+                ls.precompute_weights()
+                ls.write_state(W.initial_state(c), 0)
+                for _ in range(max(3, args.warmup)):
+                    ls.step(1)
+                torch.cuda.synchronize()
+                lsteps = max(1, min(args.steps, 50))
+                lms, _, _ = tm.steps(ls, lsteps)
+                lms = max_over_ranks([lms], dist, "cuda")[0]
+                try:
+                    ktot, kcount = tm.kernels(ls, lsteps)
+                    lroof = roofline(ktot, kcount, lsteps, c.cells, 4, c, peak, peak_kind, "fp32",
+                                     workload=f"sinusoid_{nx}x{ny}", units=sparse_units(ls, ibpf, 1),
+                                     dim=2)
+                except Exception as exc:
+                    lroof = {"error": str(exc)[:200]}
+                out[name] = {"value": aggregate_rate(world, c.cells, lsteps, lms * 1e-3), "unit": UNIT,
+                             "ms_per_step": lms / lsteps, "steps": lsteps, "cells": c.cells,
+                             "dtype": "f32", "gpu_launches": int(ls.query(ibpf.Q_LAUNCHES)) * lsteps,
+                             "l2": "state larger than L2", "roofline": lroof}
+                ls.close()
+            except Exception as exc:
+                out[name] = {"error": str(exc)[:200]}
     return out
 
 
