@@ -26,7 +26,9 @@ with rows 0 and nz on the domain walls.  Readings R1-R11 of ib_pf2d hold unchang
   R14 Periodic images: the sphere test takes the nearest image in x and y
       (dx = x - cx, shifted by -L if dx > L/2 or +L if dx < -L/2).
   With params.ch_scheme = 1, a1 + a2 is the explicit AB2 update of Eq. ExpCH as in the 2D
-  oracle (its reading R15), with the third axis.
+  oracle (its reading R15), with the third axis.  With params.ns_scheme = 1, a5 is the
+  semi-implicit predictor of Appendix A.2 (Eq. predictionSemi) as in the 2D oracle (its
+  reading R19), with the third axis: DST-II along z for u and v, DST-I for w.
 Library primitives used as steps: numpy elementwise arithmetic and scipy's FFT / DCT-II.
 """
 from __future__ import annotations
@@ -607,12 +609,11 @@ def slip_ghost3(case: Case3D, uM, vM, wM, n, gamma, dn, B=None, gt=None, mu_I=No
     return uG, vG, wG
 
 
-def momentum_rhs3(case: Case3D, C1, u, v, w):
-    """H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho) on the x-, y- and z-faces
-    (Eq. PredictionExp; readings R8, R8').  Hw rows 0 and nz are zero."""
-    p = case.params
+def _momentum_brackets3(case: Case3D, C1, u, v, w):
+    """The convective brackets div(u u) and the viscous brackets div(mu (grad u + grad u^T))
+    of the three components (readings R8, R8'); the z-face ones on the interior planes."""
     h, nz = case.h, case.nz
-    rho, mu, _ = _props(case)
+    _, mu, _ = _props(case)
     Cz = np.concatenate([C1[:1], C1, C1[-1:]], axis=0)            # mirror planes
     uz = np.concatenate([-u[:1], u, -u[-1:]], axis=0)              # no-slip ghost planes
     vz = np.concatenate([-v[:1], v, -v[-1:]], axis=0)
@@ -641,11 +642,96 @@ def momentum_rhs3(case: Case3D, C1, u, v, w):
     conv_u = ((uc * uc - _xm(uc * uc)) / h + (_yp(uv) - uv) / h) + (uw[1:] - uw[:-1]) / h
     conv_v = ((_xp(uv) - uv) / h + (vc * vc - _ym(vc * vc)) / h) + (vw[1:] - vw[:-1]) / h
     conv_w = ((_xp(uw) - uw)[1:nz] / h + (_yp(vw) - vw)[1:nz] / h) + (wc[1:] * wc[1:] - wc[:-1] * wc[:-1]) / h
+    return conv_u, conv_v, conv_w, visc_u, visc_v, visc_w
+
+
+def momentum_rhs3(case: Case3D, C1, u, v, w):
+    """H = -div(u u) + div(mu (grad u + grad u^T)) / (Re rho) on the x-, y- and z-faces
+    (Eq. PredictionExp; readings R8, R8').  Hw rows 0 and nz are zero."""
+    p = case.params
+    nz = case.nz
+    rho, _, _ = _props(case)
+    conv_u, conv_v, conv_w, visc_u, visc_v, visc_w = _momentum_brackets3(case, C1, u, v, w)
     Hu = -conv_u + visc_u / (p.Re * rho(0.5 * (_xm(C1) + C1)))
     Hv = -conv_v + visc_v / (p.Re * rho(0.5 * (_ym(C1) + C1)))
     Hw = np.zeros_like(w)
     Hw[1:nz] = -conv_w + visc_w / (p.Re * rho(0.5 * (C1[:-1] + C1[1:])))
     return Hu, Hv, Hw
+
+
+def momentum_terms3(case: Case3D, C1, u, v, w):
+    """The two brackets of momentum_rhs3 separately (the semi-implicit predictor of
+    Appendix A.2, reading R19 of the 2D oracle): N = -div(u u) and
+    V = div(mu (grad u + grad u^T)) / (Re rho), per component; the z-face wall planes zero."""
+    p = case.params
+    nz = case.nz
+    rho, _, _ = _props(case)
+    conv_u, conv_v, conv_w, visc_u, visc_v, visc_w = _momentum_brackets3(case, C1, u, v, w)
+    Nw = np.zeros_like(w)
+    Vw = np.zeros_like(w)
+    Nw[1:nz] = -conv_w
+    Vw[1:nz] = visc_w / (p.Re * rho(0.5 * (C1[:-1] + C1[1:])))
+    return (-conv_u, -conv_v, Nw, visc_u / (p.Re * rho(0.5 * (_xm(C1) + C1))),
+            visc_v / (p.Re * rho(0.5 * (_ym(C1) + C1))), Vw)
+
+
+def mass_flux_term3(case: Case3D, C1, phi, u, v, w):
+    """(rho'/(rho_f Pe)) (grad phi . grad) u on the x-, y- and z-faces (the last term of Eq.
+    predictionSemi, reading R19 of the 2D oracle, with the third axis): rho' = (rho_l -
+    rho_g)/2; the chemical potential's gradient by the face difference across the face and
+    the mean of the two cells' central differences along it (phi continued by mirror planes
+    beyond the z walls); the velocity's by central differences of its own faces (no-slip
+    ghost planes -u, -v at the z walls; w on the interior z-faces, zero on the walls)."""
+    p = case.params
+    h, nz = case.h, case.nz
+    rho, _, _ = _props(case)
+    rp = 0.5 * (1.0 - 1.0 / p.rho_ratio)
+    phx = (_xp(phi) - _xm(phi)) / (2.0 * h)
+    phy = (_yp(phi) - _ym(phi)) / (2.0 * h)
+    phz = (_zp_mirror(phi) - _zm_mirror(phi)) / (2.0 * h)
+    uz = np.concatenate([-u[:1], u, -u[-1:]], axis=0)
+    vz = np.concatenate([-v[:1], v, -v[-1:]], axis=0)
+    mfu = (rp / (rho(0.5 * (_xm(C1) + C1)) * p.Pe)) * (
+        (((phi - _xm(phi)) / h) * ((_xp(u) - _xm(u)) / (2.0 * h))
+         + (0.5 * (phy + _xm(phy))) * ((_yp(u) - _ym(u)) / (2.0 * h)))
+        + (0.5 * (phz + _xm(phz))) * ((uz[2:] - uz[:-2]) / (2.0 * h)))
+    mfv = (rp / (rho(0.5 * (_ym(C1) + C1)) * p.Pe)) * (
+        ((0.5 * (phx + _ym(phx))) * ((_xp(v) - _xm(v)) / (2.0 * h))
+         + ((phi - _ym(phi)) / h) * ((_yp(v) - _ym(v)) / (2.0 * h)))
+        + (0.5 * (phz + _ym(phz))) * ((vz[2:] - vz[:-2]) / (2.0 * h)))
+    mfw = np.zeros_like(w)
+    wi = w[1:nz]
+    mfw[1:nz] = (rp / (rho(0.5 * (C1[:-1] + C1[1:])) * p.Pe)) * (
+        ((0.5 * (phx[1:] + phx[:-1])) * ((_xp(wi) - _xm(wi)) / (2.0 * h))
+         + (0.5 * (phy[1:] + phy[:-1])) * ((_yp(wi) - _ym(wi)) / (2.0 * h)))
+        + ((phi[1:] - phi[:-1]) / h) * ((w[2:] - w[:-2]) / (2.0 * h)))
+    return mfu, mfv, mfw
+
+
+def velocity_helmholtz3(case: Case3D, ru, rv, rw, a):
+    """(1 - a L) d = r for the three velocity components (Appendix A.2, Eq. predictionSemi,
+    the implicit half of nu0 lap u): real Fourier in x, complex Fourier in y, and along z the
+    DST-II of the tangential components (no-slip ghost planes, modes m = 1..nz) and the DST-I
+    of w on the interior z-faces (w = 0 on the walls, modes m = 1..nz-1); eigenvalues
+    -(4/h^2)(sin^2(pi kx/nx) + sin^2(pi ky/ny) + sin^2(pi m/(2 nz)))."""
+    nx, ny, nz, h = case.nx, case.ny, case.nz, case.h
+    lx = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(nx // 2 + 1) / nx) ** 2
+    ly = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(ny) / ny) ** 2
+    lt = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(1, nz + 1) / (2.0 * nz)) ** 2
+    ln = -(4.0 / (h * h)) * np.sin(np.pi * np.arange(1, nz) / (2.0 * nz)) ** 2
+
+    def solve(r, typ, lz):
+        s = sfft.fft(sfft.rfft(r, axis=2), axis=1)
+        t = sfft.dst(s.real, type=typ, axis=0) + 1j * sfft.dst(s.imag, type=typ, axis=0)
+        t = t / (1.0 - a * ((lz[:, None, None] + ly[None, :, None]) + lx[None, None, :]))
+        t = sfft.idst(t.real, type=typ, axis=0) + 1j * sfft.idst(t.imag, type=typ, axis=0)
+        return sfft.irfft(sfft.ifft(t, axis=1), n=nx, axis=2)
+
+    du = solve(ru, 2, lt)
+    dv = solve(rv, 2, lt)
+    dw = np.zeros((nz + 1, ny, nx))
+    dw[1:nz] = solve(rw[1:nz], 1, ln)
+    return du, dv, dw
 
 
 def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
@@ -701,9 +787,14 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     phi = chemical_potential3(case, geo, C1)
     info["phi"] = phi
 
-    # a5
+    # a5: the AB2 predictor (Eq. PredictionExp) or, with params.ns_scheme = 1, the
+    # semi-implicit predictor of Appendix A.2 (Eq. predictionSemi; the history holds N)
     u, v, w = st["u"], st["v"], st["w"]
-    Hu, Hv, Hw = momentum_rhs3(case, C1, u, v, w)
+    semi = getattr(p, "ns_scheme", 0) == 1
+    if semi:
+        Hu, Hv, Hw, Vu, Vv, Vw = momentum_terms3(case, C1, u, v, w)
+    else:
+        Hu, Hv, Hw = momentum_rhs3(case, C1, u, v, w)
     rho_u = rho(0.5 * (_xm(C1) + C1))
     rho_v = rho(0.5 * (_ym(C1) + C1))
     rho_w = rho(0.5 * (C1[:-1] + C1[1:]))
@@ -711,10 +802,22 @@ def step3(case: Case3D, geo: Geometry3D, st: dict) -> tuple[dict, dict]:
     st_u = k_st * (0.5 * (phi + _xm(phi))) * ((C1 - _xm(C1)) / h) / rho_u
     st_v = k_st * (0.5 * (phi + _ym(phi))) * ((C1 - _ym(C1)) / h) / rho_v
     st_w = k_st * (0.5 * (phi[1:] + phi[:-1])) * ((C1[1:] - C1[:-1]) / h) / rho_w
-    u_star = u + p.dt * ((1.5 * Hu - 0.5 * st["Hu"]) + st_u)
-    v_star = v + p.dt * ((1.5 * Hv - 0.5 * st["Hv"]) + st_v)
     w_star = np.zeros_like(w)
-    w_star[1:nz] = w[1:nz] + p.dt * ((1.5 * Hw[1:nz] - 0.5 * st["Hw"][1:nz]) + st_w)
+    if semi:
+        mfu, mfv, mfw = mass_flux_term3(case, C1, phi, u, v, w)
+        Fu = (((1.5 * Hu - 0.5 * st["Hu"]) + st_u) + Vu) + mfu
+        Fv = (((1.5 * Hv - 0.5 * st["Hv"]) + st_v) + Vv) + mfv
+        Fw = np.zeros_like(w)
+        Fw[1:nz] = (((1.5 * Hw[1:nz] - 0.5 * st["Hw"][1:nz]) + st_w) + Vw[1:nz]) + mfw[1:nz]
+        nu0 = 0.5 * (1.0 + (1.0 / p.mu_ratio) / (1.0 / p.rho_ratio)) / p.Re
+        du, dv, dw = velocity_helmholtz3(case, p.dt * Fu, p.dt * Fv, p.dt * Fw, 0.5 * p.dt * nu0)
+        u_star = u + du
+        v_star = v + dv
+        w_star[1:nz] = w[1:nz] + dw[1:nz]
+    else:
+        u_star = u + p.dt * ((1.5 * Hu - 0.5 * st["Hu"]) + st_u)
+        v_star = v + p.dt * ((1.5 * Hv - 0.5 * st["Hv"]) + st_v)
+        w_star[1:nz] = w[1:nz] + p.dt * ((1.5 * Hw[1:nz] - 0.5 * st["Hw"][1:nz]) + st_w)
     uss = geo.alpha_u * u_star
     vss = geo.alpha_v * v_star
     wss = geo.alpha_w * w_star

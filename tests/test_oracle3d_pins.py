@@ -14,7 +14,10 @@
 * the vector slip formula against the 2D one where the normal lies in a plane, and its
   closed-form cases (no penetration at I, no slip, free slip, the slip-length law) for
   normals in any direction;
-* the re-interpolated face lists of a flat wall, derived by hand.
+* the re-interpolated face lists of a flat wall, derived by hand;
+* the semi-implicit predictor (Appendix A.2): the step's reduction to the pinned 2D one,
+  the velocity Helmholtz solves against dense operators, the mass-flux term zero for equal
+  densities and second order on smooth fields.
 """
 import math
 
@@ -61,8 +64,9 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("axis,scheme", [("y", 0), ("x", 0), ("y", 1), ("x", 1)])
-def test_step_reduces_to_2d_plane(axis, scheme):
+@pytest.mark.parametrize("axis,scheme,ns", [("y", 0, 0), ("x", 0, 0), ("y", 1, 0), ("x", 1, 0),
+                                            ("y", 0, 1), ("x", 0, 1)])
+def test_step_reduces_to_2d_plane(axis, scheme, ns):
     import dataclasses
     rng = np.random.default_rng(17)
     n1, n2, nrep = 16, 8, 4
@@ -72,7 +76,7 @@ def test_step_reduces_to_2d_plane(axis, scheme):
         c3 = _free3d(nrep, n1, n2)
         c3 = W.Case3D(c3.name, nrep, n1, n2, nrep * c3.h, n1 * c3.h, n2 * c3.h, c3.geom_kind,
                       c3.geom_p, c3.drop_c, c3.drop_r, c3.params, 1)
-    c3 = dataclasses.replace(c3, params=dataclasses.replace(c3.params, ch_scheme=scheme))
+    c3 = dataclasses.replace(c3, params=dataclasses.replace(c3.params, ch_scheme=scheme, ns_scheme=ns))
     c2 = _case2d_like(c3, n1, n2, n1 * c3.h)
     s2 = _plane_state(rng, n1, n2)
     zero3 = np.zeros((n2, c3.ny, c3.nx))
@@ -295,3 +299,83 @@ def test_slip_ghost3_special_cases_for_any_normal():
         else:
             VtI = (gamma[:, None] * VtG + VtM) / (gamma[:, None] + 1.0)
             assert np.allclose(VtI / ls, (VtM - VtG) / ((gamma[:, None] + 1.0) * dn[:, None]), rtol=1e-10, atol=1e-10)
+
+
+def test_velocity_helmholtz3_against_dense_operator():
+    # (1 - a L) d = r by the transforms against a dense solve of the assembled 7-point
+    # operators: x-faces (and y-faces) with no-slip ghost planes -u beyond the z walls,
+    # z-faces on the interior planes with w = 0 on the walls; periodic x and y
+    rng = np.random.default_rng(31)
+    nx, ny, nz = 8, 4, 6
+    c = W.flat_wall_case3d(nx=nx, ny=ny, nz=nz, geom_kind=W.GEOM_NONE)
+    h, a = c.h, 0.37 * c.h ** 2
+
+    def lap(nzz, ghost):
+        n = nzz * ny * nx
+        L = np.zeros((n, n))
+        idx = lambda k, j, i: (k * ny + j % ny) * nx + i % nx
+        for k in range(nzz):
+            for j in range(ny):
+                for i in range(nx):
+                    r = idx(k, j, i)
+                    L[r, r] -= 6.0
+                    for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+                        L[r, idx(k, j + dj, i + di)] += 1.0
+                    for dk in (1, -1):
+                        kk = k + dk
+                        if 0 <= kk < nzz:
+                            L[r, idx(kk, j, i)] += 1.0
+                        elif ghost:
+                            L[r, r] -= 1.0          # ghost plane -u
+        return L / h ** 2
+
+    ru = rng.standard_normal((nz, ny, nx))
+    rv = rng.standard_normal((nz, ny, nx))
+    rw = np.zeros((nz + 1, ny, nx))
+    rw[1:nz] = rng.standard_normal((nz - 1, ny, nx))
+    du, dv, dw = O3.velocity_helmholtz3(c, ru, rv, rw, a)
+    Lt, Ln = lap(nz, True), lap(nz - 1, False)
+    It, In = np.eye(Lt.shape[0]), np.eye(Ln.shape[0])
+    assert _rel(du.ravel(), np.linalg.solve(It - a * Lt, ru.ravel())) < 1e-12
+    assert _rel(dv.ravel(), np.linalg.solve(It - a * Lt, rv.ravel())) < 1e-12
+    assert _rel(dw[1:nz].ravel(), np.linalg.solve(In - a * Ln, rw[1:nz].ravel())) < 1e-12
+    assert np.all(dw[0] == 0.0) and np.all(dw[nz] == 0.0)
+
+
+def test_mass_flux_term3_vanishes_for_equal_densities_and_is_second_order():
+    # rho' = 0 for equal densities; otherwise the discrete (grad phi . grad) u of smooth
+    # fields converges at second order in h (interior planes, away from the z walls)
+    import dataclasses
+
+    def fields(n):
+        c = W.flat_wall_case3d(nx=n, ny=n, nz=n, geom_kind=W.GEOM_NONE)
+        h = c.h
+        x = (np.arange(n) + 0.5) * h
+        xf = np.arange(n) * h
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        L = n * h
+        k = 2.0 * np.pi / L
+        phi = np.sin(k * X) * np.cos(k * Y) * np.cos(np.pi * Z / L)
+        C = np.zeros_like(phi)
+        Zu, Yu, Xu = np.meshgrid(x, x, xf, indexing="ij")
+        u = np.cos(k * Xu) * np.sin(k * Yu) * np.sin(np.pi * Zu / L)
+        v = np.zeros_like(u)
+        w = np.zeros((n + 1, n, n))
+        exact = (k * np.cos(k * Xu) * np.cos(k * Yu) * np.cos(np.pi * Zu / L)) * (-k * np.sin(k * Xu) * np.sin(k * Yu) * np.sin(np.pi * Zu / L)) \
+            + (-k * np.sin(k * Xu) * np.sin(k * Yu) * np.cos(np.pi * Zu / L)) * (k * np.cos(k * Xu) * np.cos(k * Yu) * np.sin(np.pi * Zu / L)) \
+            + (-(np.pi / L) * np.sin(k * Xu) * np.cos(k * Yu) * np.sin(np.pi * Zu / L)) * ((np.pi / L) * np.cos(k * Xu) * np.sin(k * Yu) * np.cos(np.pi * Zu / L))
+        return c, C, phi, u, v, w, exact
+
+    c, C, phi, u, v, w, _ = fields(16)
+    c1 = dataclasses.replace(c, params=dataclasses.replace(c.params, rho_ratio=1.0))
+    for m in O3.mass_flux_term3(c1, C, phi, u, v, w):
+        assert np.all(m == 0.0)
+    errs = []
+    for n in (16, 32):
+        c, C, phi, u, v, w, exact = fields(n)
+        rho_f = 0.5 * (1.0 + 1.0 / c.params.rho_ratio)    # C = 0: the mean density
+        scale = 0.5 * (1.0 - 1.0 / c.params.rho_ratio) / (rho_f * c.params.Pe)
+        mfu, _, _ = O3.mass_flux_term3(c, C, phi, u, v, w)
+        inner = slice(2, n - 2)
+        errs.append(np.abs(mfu[inner] / scale - exact[inner]).max())
+    assert errs[1] < errs[0] / 3.0, errs
