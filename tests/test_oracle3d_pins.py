@@ -379,3 +379,23 @@ def test_mass_flux_term3_vanishes_for_equal_densities_and_is_second_order():
         inner = slice(2, n - 2)
         errs.append(np.abs(mfu[inner] / scale - exact[inner]).max())
     assert errs[1] < errs[0] / 3.0, errs
+
+
+def test_mirror_value3_of_linear_fields_is_the_value_at_M():
+    # as in 2D: M = G + (1 + gamma) dn n and 2 f(IP1) - f(IP2) = f(M) for a linear f, with the
+    # linear-exact weights every gather exact (the sphere's ghosts lie away from the periodic
+    # edges, so a field linear in x, y and z is linear on every stencil); the phi fill copies it
+    case = W.small_sphere_case(32)
+    geo = O3.build_geometry3(case)
+    nx, ny, h = case.nx, case.ny, case.h
+    gi, gj, gk = geo.gcell % nx, (geo.gcell // nx) % ny, geo.gcell // (nx * ny)
+    G = np.stack([(gi + 0.5) * h, (gj + 0.5) * h, (gk + 0.5) * h], axis=1)
+    M = G + ((1.0 + geo.gamma) * geo.dn)[:, None] * geo.n
+    x = (np.arange(nx) + 0.5) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    f = 0.3 + 0.7 * X - 1.1 * Y + 1.9 * Z
+    fM = O3.mirror_value3(f.reshape(-1), geo)
+    assert np.abs(fM - (0.3 + 0.7 * M[:, 0] - 1.1 * M[:, 1] + 1.9 * M[:, 2])).max() < 1e-12
+    st = W.random_state3d(case, seed=8)
+    phi = O3.chemical_potential3(case, geo, st["C"])
+    assert np.array_equal(phi.reshape(-1)[geo.gcell], O3.mirror_value3(phi.reshape(-1).copy(), geo))

@@ -7,6 +7,7 @@ hand-derived geometry (tests/golden).
 """
 import json
 import math
+from dataclasses import replace
 from pathlib import Path
 
 import numpy as np
@@ -465,3 +466,28 @@ def test_penalisation_zeroes_solid_faces_and_keeps_fluid_faces():
     assert np.array_equal(info["u_ss"][7:], info["u_star"][7:])
     assert np.all(info["v_ss"][:5] == 0.0)
     assert np.array_equal(info["v_ss"][8:], info["v_star"][8:])
+
+
+def test_mirror_value_of_linear_fields_is_the_value_at_M():
+    # Eq. extrapolation with IP1 = M + d2 n, IP2 = M + 2 d2 n: 2 f(IP1) - f(IP2) = f(M) for a
+    # linear f, and M = G + (1 + gamma) dn n (I = G + dn n, M = I + d1 n, gamma = d1/dn);
+    # with the linear-exact weights (R17) every gather is exact, so the mirror value of a
+    # linear field is its value at M -- on the sinusoidal wall, whose ghosts have normals in
+    # every direction.  The phi fill (Sec. 4.2.2) copies that value: phi_G = phi_M.
+    case = cases.sinusoid_wall_512x256(theta_deg=90.0, l_s=0.0)
+    d1, d2 = cases._ghost_lengths(2.0 / 128)
+    case = replace(case, nx=128, ny=64, params=replace(case.params, d1=d1, d2=d2))
+    geo = O.build_geometry(case)
+    nx, ny, h = case.nx, case.ny, case.h
+    gi, gj = geo.gcell % nx, geo.gcell // nx
+    G = np.stack([(gi + 0.5) * h, (gj + 0.5) * h], axis=1)
+    M = G + ((1.0 + geo.gamma) * geo.dn)[:, None] * geo.n
+    xc = (np.arange(nx) + 0.5) * h
+    yc = (np.arange(ny) + 0.5) * h
+    f = 0.3 + 0.0 * xc[None, :] - 1.7 * yc[:, None]           # linear in x2 (x1 is periodic)
+    fM = O.mirror_value(f.reshape(-1), geo)
+    assert np.abs(fM - (0.3 - 1.7 * M[:, 1])).max() < 1e-12
+    rng = np.random.default_rng(4)
+    C = np.tanh(rng.standard_normal((ny, nx)) * 0.1 + (yc[:, None] - 0.5) / 0.05)
+    phi = O.chemical_potential(case, geo, C)
+    assert np.array_equal(phi.reshape(-1)[geo.gcell], O.mirror_value(phi.reshape(-1).copy(), geo))
